@@ -1,0 +1,271 @@
+"""FP64 CPU oracle for population evaluation, selection and variation.
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by ``__graft_entry__.smoke()``
+and by the ``cpu_baseline`` leg of ``bench.py`` -- never by the product path.
+It shares no code with the CUDA library; ``sr_oracle.c`` documents what each
+function computes and which passage of the paper it follows.
+
+Arrays are numpy.  FP32 inputs (X, y, constants) are widened to FP64 before
+the C code sees them, so every arithmetic step below is FP64.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sr_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+MSE, CORR = 0, 1
+
+# program flag bits (documented token format)
+PF_BAD_LENGTH, PF_BAD_TOKEN, PF_BAD_VAR = 1, 2, 4
+PF_BAD_CONST, PF_UNDERFLOW, PF_BAD_FINAL = 8, 16, 32
+# conditioning flag bits
+CF_RANGE, CF_BRANCH, CF_FITRANGE = 1, 2, 4
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``sr_oracle.c`` into ``liboracle.so`` (gcc, OpenMP, no FP
+    contraction so FP32 steps in the variation reference round one by one)."""
+    stale = (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC)
+    if force or stale:
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    lib = ctypes.CDLL(_LIB)
+    P = ctypes.c_void_p
+    i32, i64, f32, f64, u64 = ctypes.c_int, ctypes.c_long, ctypes.c_float, ctypes.c_double, ctypes.c_uint64
+    lib.or_validate.argtypes = [P, i32, i32, i32, i32, P]
+    lib.or_validate.restype = i32
+    lib.or_validate_all.argtypes = [P, P, i32, i32, i32, i32, P, P]
+    lib.or_predict.argtypes = [P, i32, P, P, i64, i64, P]
+    lib.or_eval.argtypes = [P, P, P, i32, i32, i32, P, i64, P, i32, i64, i32, P, P, i32]
+    lib.or_condition.argtypes = [P, P, P, i32, i32, i32, P, i64, P, i32, i64, i32, i32, f64, P, P, P, i32]
+    lib.or_grad.argtypes = [P, P, P, i32, i32, i32, P, i64, P, i32, i64, P, P, P, i32]
+    lib.or_grad_one.argtypes = [P, i32, P, i32, P, i64, P, i64, P, P, P]
+    lib.or_mse_fp64_consts.argtypes = [P, i32, P, P, i64, P, i64]
+    lib.or_mse_fp64_consts.restype = f64
+    lib.or_mse.argtypes = [P, P, i64]
+    lib.or_mse.restype = f64
+    lib.or_corr.argtypes = [P, P, i64]
+    lib.or_corr.restype = f64
+    lib.or_adam.argtypes = [P, P, P, P, i64, i32, f64, f64, f64, f64]
+    lib.or_philox4x32_10.argtypes = [P, P, P]
+    lib.or_tournament.argtypes = [P, i32, i32, u64, u64, P]
+    lib.or_random_programs.argtypes = [P, P, P, i32, i32, i32, i32, i32, f32, f32, u64, u64]
+    lib.or_vary.argtypes = [P, P, P, P, P, P, P, i32, i32, i32, i32, f32, f32, f32, f32, f32, i32, u64, u64]
+    _lib = lib
+    return lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _X(X):
+    X = np.asarray(X)
+    if X.ndim == 1:
+        X = X[None, :]
+    X64 = _c(X, np.float64)
+    return X64, X64.shape[1]
+
+
+# --------------------------------------------------------------------------
+def validate(tokens, Lmax: int, nvars: int, K: int):
+    """Flag bits and maximum stack depth of one program (1-D uint8 tokens)."""
+    t = _c(tokens, np.uint8)
+    md = ctypes.c_int(0)
+    f = _load().or_validate(_ptr(t), len(t), Lmax, nvars, K, ctypes.byref(md))
+    return int(f), int(md.value)
+
+
+def validate_all(programs, lengths, nvars: int, K: int):
+    """Flag bits [P] and maximum stack depth [P] of a population."""
+    prog = _c(programs, np.uint8)
+    P, Lmax = prog.shape
+    lens = _c(lengths, np.int32)
+    flags = np.empty(P, np.int32)
+    md = np.empty(P, np.int32)
+    _load().or_validate_all(_ptr(prog), _ptr(lens), P, Lmax, nvars, K, _ptr(flags), _ptr(md))
+    return flags, md
+
+
+def predict(tokens, consts, X, N: int | None = None) -> np.ndarray:
+    """FP64 output of one valid program on cases [0, N)."""
+    t = _c(tokens, np.uint8)
+    c = np.zeros(16, np.float64)
+    cc = np.asarray(consts, dtype=np.float64).ravel()
+    c[: len(cc)] = cc
+    X64, ldx = _X(X)
+    N = ldx if N is None else N
+    out = np.empty(N, np.float64)
+    _load().or_predict(_ptr(t), len(t), _ptr(c), _ptr(X64), ldx, N, _ptr(out))
+    return out
+
+
+def mse(yhat, y) -> float:
+    a, b = _c(yhat, np.float64), _c(y, np.float64)
+    return float(_load().or_mse(_ptr(a), _ptr(b), len(a)))
+
+
+def corr(yhat, y) -> float:
+    a, b = _c(yhat, np.float64), _c(y, np.float64)
+    return float(_load().or_corr(_ptr(a), _ptr(b), len(a)))
+
+
+def evaluate(programs, lengths, consts, X, y, kind: int, N: int | None = None, nthreads: int = 0):
+    """Fitness (FP64) and flag bits of every program.
+
+    programs [P, Lmax] uint8, lengths [P] int32, consts [P, K] float32,
+    X [nvars, ldx], y [>= N]."""
+    prog = _c(programs, np.uint8)
+    P, Lmax = prog.shape
+    lens = _c(lengths, np.int32)
+    cons = _c(consts, np.float32).reshape(P, -1)
+    K = cons.shape[1]
+    X64, ldx = _X(X)
+    nvars = X64.shape[0]
+    N = ldx if N is None else N
+    y64 = _c(np.asarray(y)[:N], np.float64)
+    fit = np.empty(P, np.float64)
+    flags = np.empty(P, np.int32)
+    _load().or_eval(_ptr(prog), _ptr(lens), _ptr(cons), P, Lmax, K, _ptr(X64), ldx, _ptr(y64),
+                    nvars, N, kind, _ptr(fit), _ptr(flags), nthreads)
+    return fit, flags
+
+
+def condition(programs, lengths, consts, X, y, kind: int, N: int | None = None,
+              trials: int = 3, eps: float = 2.0 ** -22, nthreads: int = 0):
+    """Per-program sensitivity to relative +-eps perturbation of every
+    operator output, conditioning flags and unperturbed fitness."""
+    prog = _c(programs, np.uint8)
+    P, Lmax = prog.shape
+    lens = _c(lengths, np.int32)
+    cons = _c(consts, np.float32).reshape(P, -1)
+    K = cons.shape[1]
+    X64, ldx = _X(X)
+    nvars = X64.shape[0]
+    N = ldx if N is None else N
+    y64 = _c(np.asarray(y)[:N], np.float64)
+    sens = np.empty(P, np.float64)
+    cfl = np.empty(P, np.int32)
+    f0 = np.empty(P, np.float64)
+    _load().or_condition(_ptr(prog), _ptr(lens), _ptr(cons), P, Lmax, K, _ptr(X64), ldx,
+                         _ptr(y64), nvars, N, kind, trials, eps, _ptr(sens), _ptr(cfl),
+                         _ptr(f0), nthreads)
+    return sens, cfl, f0
+
+
+def grad(programs, lengths, consts, X, y, N: int | None = None, nthreads: int = 0):
+    """MSE, dMSE/dconst [P, K] (forward mode, FP64) and the kink distance."""
+    prog = _c(programs, np.uint8)
+    P, Lmax = prog.shape
+    lens = _c(lengths, np.int32)
+    cons = _c(consts, np.float32).reshape(P, -1)
+    K = cons.shape[1]
+    X64, ldx = _X(X)
+    nvars = X64.shape[0]
+    N = ldx if N is None else N
+    y64 = _c(np.asarray(y)[:N], np.float64)
+    m = np.empty(P, np.float64)
+    g = np.empty((P, K), np.float64)
+    kink = np.empty(P, np.float64)
+    _load().or_grad(_ptr(prog), _ptr(lens), _ptr(cons), P, Lmax, K, _ptr(X64), ldx, _ptr(y64),
+                    nvars, N, _ptr(m), _ptr(g), _ptr(kink), nthreads)
+    return m, g, kink
+
+
+def grad_one_fp64(tokens, consts64, X, y, N: int | None = None):
+    """MSE and gradient of one program with FP64 constants (no rounding of c)."""
+    t = _c(tokens, np.uint8)
+    c = _c(consts64, np.float64)
+    K = len(c)
+    X64, ldx = _X(X)
+    N = ldx if N is None else N
+    y64 = _c(np.asarray(y)[:N], np.float64)
+    m = ctypes.c_double(0.0)
+    kink = ctypes.c_double(0.0)
+    g = np.empty(max(K, 1), np.float64)
+    _load().or_grad_one(_ptr(t), len(t), _ptr(c), K, _ptr(X64), ldx, _ptr(y64), N, ctypes.byref(m),
+                        _ptr(g), ctypes.byref(kink))
+    return float(m.value), g[:K], float(kink.value)
+
+
+def mse_fp64_consts(tokens, consts64, X, y, N: int | None = None) -> float:
+    t = _c(tokens, np.uint8)
+    c = np.zeros(16, np.float64)
+    cc = np.asarray(consts64, dtype=np.float64).ravel()
+    c[: len(cc)] = cc
+    X64, ldx = _X(X)
+    N = ldx if N is None else N
+    y64 = _c(np.asarray(y)[:N], np.float64)
+    return float(_load().or_mse_fp64_consts(_ptr(t), len(t), _ptr(c), _ptr(X64), ldx, _ptr(y64), N))
+
+
+def adam(c, g, m, v, t: int, lr=1e-2, b1=0.9, b2=0.999, eps=1e-8):
+    """In-place Adam step on FP32 constants with FP64 moments."""
+    assert c.dtype == np.float32 and c.flags.c_contiguous
+    assert g.dtype == m.dtype == v.dtype == np.float64
+    _load().or_adam(_ptr(c), _ptr(_c(g, np.float64)), _ptr(m), _ptr(v), c.size, t, lr, b1, b2, eps)
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = np.asarray(ctr, dtype=np.uint32)
+    k = np.asarray(key, dtype=np.uint32)
+    out = np.empty(4, np.uint32)
+    _load().or_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def tournament(fitness, k: int, seed: int, gen: int) -> np.ndarray:
+    f = _c(fitness, np.float64)
+    P = len(f)
+    out = np.empty((P, 2), np.int32)
+    _load().or_tournament(_ptr(f), P, k, seed, gen, _ptr(out))
+    return out
+
+
+def random_programs(P, Lmin, Lmax, K, nvars, cmin, cmax, seed, stream):
+    prog = np.empty((P, Lmax), np.uint8)
+    lens = np.empty(P, np.int32)
+    cons = np.empty((P, max(K, 0)), np.float32)
+    _load().or_random_programs(_ptr(prog), _ptr(lens), _ptr(cons), P, Lmin, Lmax, K, nvars,
+                               cmin, cmax, seed, stream)
+    return prog, lens, cons
+
+
+def vary(programs, lengths, consts, parents, K, nvars, p_cross=0.9, p_point=0.1,
+         p_subtree=0.05, p_const=0.1, delta=1.0, max_subtree=8, seed=0, gen=0):
+    prog = _c(programs, np.uint8)
+    P, Lmax = prog.shape
+    lens = _c(lengths, np.int32)
+    cons = _c(consts, np.float32).reshape(P, K) if K > 0 else np.zeros((P, 0), np.float32)
+    par = _c(parents, np.int32)
+    po = np.empty_like(prog)
+    lo = np.empty_like(lens)
+    co = np.empty_like(cons)
+    _load().or_vary(_ptr(prog), _ptr(lens), _ptr(cons), _ptr(par), _ptr(po), _ptr(lo), _ptr(co),
+                    P, Lmax, K, nvars, p_cross, p_point, p_subtree, p_const, delta, max_subtree,
+                    seed, gen)
+    return po, lo, co

@@ -1,0 +1,298 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle:
+hand-evaluated programs, closed forms, library routines, combinatorial
+counts and published known-answer vectors.  CPU only."""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_12292_gb300 import inputs
+from progtext import load_hand_cases, pack, parse
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- operators
+@pytest.mark.parametrize("case", load_hand_cases(os.path.join(GOLDEN, "hand_programs.txt")),
+                         ids=lambda c: f"{c[0]}|{c[2]}")
+def test_hand_programs(case):
+    """Sec. 2.1.4: RPN evaluation on a stack; operator readings in the fixture."""
+    prog, consts, xs, expect = case
+    X = np.array(xs, np.float64).reshape(-1, 1)
+    got = oracle.predict(parse(prog), consts, X, 1)[0]
+    if math.isnan(expect):
+        assert math.isnan(got)
+    else:
+        assert got == pytest.approx(expect, rel=1e-15, abs=1e-300)
+
+
+@pytest.mark.parametrize("name,fn", [("sin", np.sin), ("cos", np.cos), ("sqrt", lambda v: np.sqrt(np.abs(v))),
+                                     ("sq", np.square)])
+def test_single_op_matches_numpy(name, fn):
+    """Single-operator programs reduce to library routines (numpy, FP64)."""
+    rng = np.random.default_rng(1)
+    x = rng.uniform(-50, 50, 2000)
+    got = oracle.predict(parse(f"x0 {name}"), [], x[None, :])
+    np.testing.assert_allclose(got, fn(x), rtol=2e-16, atol=1e-300)
+
+
+def test_exp_log_match_numpy_inside_domain():
+    rng = np.random.default_rng(2)
+    x = rng.uniform(-79, 79, 2000)
+    np.testing.assert_allclose(oracle.predict(parse("x0 exp"), [], x[None, :]), np.exp(x), rtol=4e-16)
+    x = rng.uniform(0.002, 1e6, 2000) * rng.choice([-1, 1], 2000)
+    np.testing.assert_allclose(oracle.predict(parse("x0 log"), [], x[None, :]), np.log(np.abs(x)),
+                               rtol=4e-16, atol=1e-300)
+
+
+# ---------------------------------------------------------------- validator
+def _tree_count(nterm, nun, nbin, n):
+    """Number of postfix programs of exactly n tokens: ordered trees whose
+    internal nodes are unary or binary, counted by the tree recursion
+    T(1) = t, T(n) = u T(n-1) + b sum_{i+j=n-1} T(i) T(j)."""
+    T = [0] * (n + 1)
+    for m in range(1, n + 1):
+        T[m] = (nterm if m == 1 else 0) + nun * T[m - 1] \
+            + nbin * sum(T[i] * T[m - 1 - i] for i in range(1, m - 1))
+    return T
+
+
+@pytest.mark.parametrize("nconst,expected", [(0, 13_989), (1, 23_308)])
+def test_enumeration_counts(nconst, expected):
+    """All token strings of length <= 5 over 3 variables (+ constants), the 6
+    unary and 4 binary ops: exactly the tree-count many are valid."""
+    alphabet = list(range(10)) + [16, 17, 18] + [32 + k for k in range(nconst)]
+    total_valid = 0
+    for n in range(1, 6):
+        seqs = np.array(list(itertools.product(alphabet, repeat=n)), np.uint8)
+        lens = np.full(len(seqs), n, np.int32)
+        flags, _ = oracle.validate_all(seqs, lens, nvars=3, K=nconst)
+        valid = int((flags == 0).sum())
+        assert valid == _tree_count(3 + nconst, 6, 4, n)[n]
+        total_valid += valid
+    assert total_valid == expected
+
+
+def test_validator_flags():
+    cases = [
+        ("x0", 0), ("x0 x1 +", 0),
+        ("x0 +", oracle.PF_UNDERFLOW | oracle.PF_BAD_FINAL),
+        ("x0 x1 + + x2", oracle.PF_UNDERFLOW),
+        ("x0 x1", oracle.PF_BAD_FINAL),
+        ("sin", oracle.PF_UNDERFLOW | oracle.PF_BAD_FINAL),
+        ("x3", oracle.PF_BAD_VAR), ("c4", oracle.PF_BAD_CONST),
+    ]
+    for text, want in cases:
+        f, _ = oracle.validate(parse(text), 8, 3, 4)
+        assert f == want, text
+    f, _ = oracle.validate(np.array([16, 12], np.uint8), 8, 3, 4)
+    assert f == oracle.PF_BAD_TOKEN
+    f, _ = oracle.validate(np.array([], np.uint8), 8, 3, 4)
+    assert f == oracle.PF_BAD_LENGTH
+    f, _ = oracle.validate(parse("x0 x1 + x2 +"), 4, 3, 4)
+    assert f == oracle.PF_BAD_LENGTH
+    # depth is the running sum of effects: x0 x1 x2 + + reaches 3
+    assert oracle.validate(parse("x0 x1 x2 + +"), 8, 3, 4) == (0, 3)
+
+
+def test_invalid_program_gets_inf():
+    progs, lens = pack([parse("x0 x1 +"), parse("x0 +"), parse("x7")], 8)
+    X = np.ones((3, 4), np.float32)
+    y = np.ones(4, np.float32)
+    for kind in (oracle.MSE, oracle.CORR):
+        f, fl = oracle.evaluate(progs, lens, np.zeros((3, 1), np.float32), X, y, kind)
+        assert np.isfinite(f[0]) and np.isinf(f[1]) and np.isinf(f[2])
+        assert fl.tolist() == [0, oracle.PF_UNDERFLOW | oracle.PF_BAD_FINAL, oracle.PF_BAD_VAR]
+
+
+# ---------------------------------------------------------------- fitness closed forms
+@pytest.fixture(scope="module")
+def plain():
+    pr = inputs.plain()
+    y64 = oracle.predict(pr.target, pr.target_consts, pr.X, pr.N)
+    return pr, y64
+
+
+def test_exact_target_mse_is_zero(plain):
+    """An exact target program has MSE exactly 0 (same FP64 evaluation)."""
+    pr, y64 = plain
+    progs, lens = pack([pr.target], 16)
+    f, _ = oracle.evaluate(progs, lens, pr.target_consts[None, :], pr.X, y64, oracle.MSE, pr.N)
+    assert f[0] == 0.0
+
+
+def test_offset_program_mse_is_offset_squared(plain):
+    """f + a scores MSE = a^2 against y = f."""
+    pr, y64 = plain
+    a = np.float32(1.75)
+    prog = np.concatenate([pr.target, parse("c3 +")])
+    c = pr.target_consts.copy()
+    c[3] = a
+    if 32 + 3 in pr.target:
+        pytest.skip("target uses c3")
+    progs, lens = pack([prog], 16)
+    f, _ = oracle.evaluate(progs, lens, c[None, :], pr.X, y64, oracle.MSE, pr.N)
+    assert f[0] == pytest.approx(float(a) ** 2, rel=1e-12)
+
+
+def test_corr_closed_forms(plain):
+    """1 - r^2 (Eq. 1 squared): exact target 0; invariant under yhat -> a yhat + b
+    (a != 0); -f scores 0; a constant program scores 1."""
+    pr, y64 = plain
+    base = pr.target
+    K = pr.K
+    c = np.zeros(K, np.float32)
+    c[: len(pr.target_consts)] = pr.target_consts
+    ks = [k for k in range(K) if (32 + k) not in base]
+    assert len(ks) >= 2 or pytest.skip("target uses the constants")
+    ka, kb = ks[0], ks[1]
+    c2 = c.copy()
+    c2[ka], c2[kb] = np.float32(-3.5), np.float32(12.25)
+    progs, lens = pack([base,
+                        np.concatenate([base, parse(f"c{ka} * c{kb} +")]),
+                        np.concatenate([base, parse(f"c{ka} *")]),
+                        parse(f"c{kb}"),
+                        parse(f"c{kb} sin")], 32)
+    consts = np.stack([c2] * 5)
+    noisy = inputs.add_noise(np.random.default_rng(5), y64, 0.05).astype(np.float64)
+    f, _ = oracle.evaluate(progs, lens, consts, pr.X, y64, oracle.CORR, pr.N)
+    assert abs(f[0]) < 1e-12 and abs(f[1]) < 1e-12 and abs(f[2]) < 1e-12
+    assert f[3] == 1.0 and f[4] == 1.0
+    g, _ = oracle.evaluate(progs, lens, consts, pr.X, noisy, oracle.CORR, pr.N)
+    assert g[0] > 1e-6
+    assert g[1] == pytest.approx(g[0], rel=1e-10) and g[2] == pytest.approx(g[0], rel=1e-10)
+
+
+def test_corr_matches_numpy_corrcoef():
+    """1 - r^2 equals 1 - corrcoef^2 (numpy, FP64) on random programs."""
+    pr = inputs.plain()
+    y = inputs.add_noise(np.random.default_rng(3), oracle.predict(pr.target, pr.target_consts, pr.X,
+                                                                   pr.N), 0.1)
+    f, fl = oracle.evaluate(pr.programs, pr.lengths, pr.consts, pr.X, y, oracle.CORR, pr.N)
+    checked = 0
+    for p in range(pr.P):
+        yh = oracle.predict(pr.programs[p, : pr.lengths[p]], pr.consts[p], pr.X, pr.N)
+        if not np.all(np.isfinite(yh)) or np.std(yh) == 0:
+            assert f[p] == 1.0
+            continue
+        r = np.corrcoef(yh, y.astype(np.float64))[0, 1]
+        if np.std(yh) < 1e-6 * np.abs(yh).max():
+            continue  # constant up to rounding: both sides are noise
+        assert f[p] == pytest.approx(1.0 - r * r, abs=1e-10)
+        checked += 1
+    assert checked > pr.P // 2
+
+
+def test_mse_matches_numpy():
+    pr = inputs.plain()
+    y = oracle.predict(pr.target, pr.target_consts, pr.X, pr.N).astype(np.float32)
+    f, _ = oracle.evaluate(pr.programs, pr.lengths, pr.consts, pr.X, y, oracle.MSE, pr.N)
+    for p in range(0, pr.P, 7):
+        yh = oracle.predict(pr.programs[p, : pr.lengths[p]], pr.consts[p], pr.X, pr.N)
+        want = np.mean((yh - y.astype(np.float64)) ** 2) if np.all(np.isfinite(yh)) else np.inf
+        if np.isfinite(want):
+            assert f[p] == pytest.approx(want, rel=1e-12)
+        else:
+            assert np.isinf(f[p])
+
+
+def test_nonfinite_output_scores_worst():
+    X = np.array([[1.0, 0.0, 2.0, 3.0]], np.float32)
+    y = np.array([1.0, 2.0, 3.0, 4.0], np.float32)
+    progs, lens = pack([parse("x0 x0 x0 - /"), parse("x0 exp exp exp")], 8)
+    # x0 - x0 = 0 -> protected division -> 1: finite; exp(exp(exp(3))) is finite in FP64
+    f, _ = oracle.evaluate(progs, lens, np.zeros((2, 1), np.float32), X, y, oracle.MSE)
+    assert np.isfinite(f).all()
+    X2 = np.array([[np.inf, 1.0, 2.0, 3.0]], np.float32)
+    progs, lens = pack([parse("x0 x0 -")], 4)
+    for kind, worst in ((oracle.MSE, np.inf), (oracle.CORR, 1.0)):
+        f, _ = oracle.evaluate(progs, lens, np.zeros((1, 1), np.float32), X2, y, kind)
+        assert f[0] == worst
+
+
+# ---------------------------------------------------------------- conditioning
+def test_conditioning_separates_good_from_bad():
+    rng = np.random.default_rng(4)
+    X = rng.uniform(1, 5, (2, 512)).astype(np.float32)
+    y = (X[0].astype(np.float64) * 2 + X[1]).astype(np.float32)
+    progs, lens = pack([parse("x0 c0 * x1 +"),      # well conditioned, near exact (MSE tiny)
+                        parse("x0 x1 *"),           # well conditioned
+                        parse("x0 c1 * sin"),       # sin of ~1e6: ill conditioned
+                        parse("x0 exp exp sq")], 8)  # exp(80)^2 is beyond FP32 range
+    consts = np.array([[2.0, 1e6]] * 4, np.float32)
+    sens, cfl, f0 = oracle.condition(progs, lens, consts, X, y, oracle.MSE)
+    assert sens[1] < 1e-5 * f0[1] and cfl[1] == 0
+    assert sens[2] > 1e-5 * f0[2]
+    assert cfl[3] & oracle.CF_RANGE
+
+
+# ---------------------------------------------------------------- gradient
+def test_gradient_closed_form():
+    """yhat = c0 * x0: dMSE/dc0 = (2/N) sum (c0 x0 - y) x0."""
+    rng = np.random.default_rng(6)
+    X = rng.uniform(1, 5, (1, 300))
+    y = rng.normal(size=300)
+    c0 = 1.3
+    m, g, _ = oracle.grad_one_fp64(parse("c0 x0 *"), [c0], X, y)
+    x = X[0]
+    assert g[0] == pytest.approx(2.0 / 300 * np.sum((c0 * x - y) * x), rel=1e-13)
+    assert m == pytest.approx(np.mean((c0 * x - y) ** 2), rel=1e-13)
+
+
+def test_gradient_matches_central_differences():
+    """Forward-mode dMSE/dc vs FP64 central differences (h = 1e-6) on random
+    programs whose branch arguments stay away from their switch points."""
+    pr = inputs.make_problem("fd", 11, P=96, Lmin=3, Lmax=24, nvars=3, K=4, N=200, xlo=1, xhi=5,
+                             target_len=(9, 9))
+    y = oracle.predict(pr.target, pr.target_consts, pr.X, pr.N)
+    h = 1e-6
+    tested = 0
+    for p in range(pr.P):
+        tok = pr.programs[p, : pr.lengths[p]]
+        c = pr.consts[p].astype(np.float64)
+        m, g, kink = oracle.grad_one_fp64(tok, c, pr.X, y, pr.N)
+        if not np.isfinite(m) or kink < 1e-3 or m > 1e12:
+            continue
+        def fd(k, step):
+            cp, cm = c.copy(), c.copy()
+            cp[k] += step
+            cm[k] -= step
+            return (oracle.mse_fp64_consts(tok, cp, pr.X, y, pr.N)
+                    - oracle.mse_fp64_consts(tok, cm, pr.X, y, pr.N)) / (2 * step)
+        ok = True
+        for k in range(pr.K):
+            d1, d2 = fd(k, h), fd(k, h / 2)
+            trunc = abs(d1 - d2) * 4.0 / 3.0  # O(h^2) truncation estimate of d1
+            if trunc > 1e-3 * max(abs(d1), 1e-3):
+                ok = False  # too curved for h = 1e-6: skip this program
+                break
+            assert g[k] == pytest.approx(d1, rel=1e-5, abs=1e-7 * max(1.0, m) + 2 * trunc), (p, k)
+        tested += ok
+    assert tested > 40
+
+
+def test_adam_first_step_closed_form():
+    """Kingma & Ba: after one step from zero moments, mhat = g and
+    vhat = g^2, so c1 = c0 - lr * g / (|g| + eps)."""
+    c = np.array([1.0, -2.0, 0.5], np.float32)
+    g = np.array([0.3, -4.0, 1e-3])
+    m, v = np.zeros(3), np.zeros(3)
+    oracle.adam(c, g, m, v, 1, lr=0.01)
+    want = np.array([1.0, -2.0, 0.5]) - 0.01 * g / (np.abs(g) + 1e-8)
+    np.testing.assert_allclose(c, want.astype(np.float32), rtol=1e-6)
+
+
+# ---------------------------------------------------------------- Philox
+def test_philox_known_answers():
+    """Published Philox4x32-10 known-answer vectors (Salmon et al., SC'11)."""
+    n = 0
+    for line in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        w = [int(v, 16) for v in line.split()]
+        assert oracle.philox4x32_10(w[0:4], w[4:6]).tolist() == w[6:10]
+        n += 1
+    assert n == 3
