@@ -1,0 +1,324 @@
+#!/usr/bin/env python
+"""Benchmark: population evaluation throughput in GPop/s (program nodes x
+fitness cases per second / 1e9) on one GB300.
+
+Workload (default): the paper-shaped single problem -- 4,096 postfix programs
+of length 8..128 over 10 variables, 100,000 fitness cases X ~ U(1, 10), target
+from a random program plus 1% Gaussian noise.  One step = one generation of
+the device-resident hot path: both fitness kinds (MSE and 1 - r^2) from one
+interpreter pass, then (when available in the library) tournament selection
+and variation.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints ONE JSON line (rank 0).  Under torchrun each rank runs its own replica
+of the workload on its GPU (weak scaling, no data-path collective); timing is
+the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GPop/s (nodes x cases / s) at 1 GB300 vs plain eval; % of FP32 issue peak"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def make_workload():
+    """The paper-shaped problem with a finite, non-constant target."""
+    from paper_2603_12292_gb300 import inputs
+    return inputs.paper_shaped
+
+
+# ------------------------------------------------------------------ reference arm (the oracle)
+def run_reference(args, rank, world):
+    import oracle
+    from paper_2603_12292_gb300 import inputs
+    if rank != 0:
+        return 0
+    pr = inputs.paper_shaped()
+    y64 = oracle.predict(pr.target, pr.target_consts, pr.X, pr.N)
+    y = inputs.add_noise(np.random.default_rng(pr.seed + 7), y64, pr.noise)
+    cores = os.cpu_count() or 1
+    # size each step to ~4 s of CPU work: programs sampled from the population, all cases
+    t0 = time.perf_counter()
+    oracle.evaluate(pr.programs[:16], pr.lengths[:16], pr.consts[:16], pr.X, y, oracle.CORR, pr.N)
+    oracle.evaluate(pr.programs[:16], pr.lengths[:16], pr.consts[:16], pr.X, y, oracle.MSE, pr.N)
+    dt16 = max(time.perf_counter() - t0, 1e-3)
+    S = int(min(pr.P, max(16, 16 * 4.0 / dt16)))
+    rng = np.random.default_rng(1)
+    times, units = [], 0.0
+    for step in range(args.warmup + args.steps):
+        idx = np.sort(rng.choice(pr.P, S, replace=False))
+        t0 = time.perf_counter()
+        oracle.evaluate(pr.programs[idx], pr.lengths[idx], pr.consts[idx], pr.X, y, oracle.MSE, pr.N)
+        oracle.evaluate(pr.programs[idx], pr.lengths[idx], pr.consts[idx], pr.X, y, oracle.CORR, pr.N)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+            units += float(pr.lengths[idx].astype(np.int64).sum()) * pr.N
+    total = sum(times)
+    value = units / total / 1e9
+    sample = f"{S} sampled programs x {pr.N} cases per step, MSE and 1-r^2 (two oracle passes)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GPop/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total / len(times) * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": pr.name, "programs": pr.P, "cases": pr.N, "vars": pr.nvars,
+                       "lengths": "8-128", "fitness": "MSE and 1-r^2"},
+            "cpu_baseline": {"value": value, "unit": "GPop/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "GPop/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    from paper_2603_12292_gb300 import binding, inputs
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    ctx = binding.Context(local_rank)
+    stream = torch.cuda.current_stream(dev)
+
+    pr = inputs.paper_shaped()
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    programs, lengths, consts, X = t(pr.programs), t(pr.lengths), t(pr.consts), t(pr.X)
+    # the target on the device with the library's own predict, then 1% noise (host, FP64)
+    tgt = np.zeros((1, pr.Lmax), np.uint8)
+    tgt[0, : len(pr.target)] = pr.target
+    yhat = binding.sr_predict(ctx, t(tgt), t(np.array([len(pr.target)], np.int32)),
+                              t(pr.target_consts[None, :]), X, pr.N)
+    y = torch.from_numpy(inputs.add_noise(np.random.default_rng(pr.seed + 7),
+                                          yhat[0].double().cpu().numpy(), pr.noise)).to(dev)
+    binding.sr_reserve(ctx, pr.P, pr.Lmax, pr.N)
+    fitness = torch.empty((2, pr.P), dtype=torch.float64, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        binding.sr_eval(ctx, programs, lengths, consts, X, y, pr.N, binding.SR_MSE_CORR, fitness=fitness)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    nodes = []
+    sampler = ClockSampler(local_rank)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    launches0 = binding.sr_kernel_launches(ctx)
+    for i in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps (outside the events)
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        nodes.append(int(pr.lengths.astype(np.int64).sum()))
+    torch.cuda.synchronize()
+    launches = binding.sr_kernel_launches(ctx) - launches0
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    units = float(sum(nodes)) * pr.N * world
+    value = units / (total_ms / 1e3) / 1e9
+
+    # roofline of the dominant kernel: FP32 issue bound, one lane-op per node-case
+    pk, src = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * 128 * sm_max * 1e6 / 1e9  # G lane-ops/s
+    per_launch_units = float(nodes[0]) * pr.N
+    achieved = per_launch_units / (statistics.mean(step_ms) / 1e3) / 1e9
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GPop/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz ({src} max clock)"}
+
+    # end to end through the public API: H2D population, evaluate, D2H fitness
+    h_prog = torch.from_numpy(pr.programs).pin_memory()
+    h_len = torch.from_numpy(pr.lengths).pin_memory()
+    h_con = torch.from_numpy(pr.consts).pin_memory()
+    h_fit = torch.empty((2, pr.P), dtype=torch.float64).pin_memory()
+    d_prog, d_len, d_con = torch.empty_like(programs), torch.empty_like(lengths), torch.empty_like(consts)
+    h2d = h_prog.numel() + h_len.numel() * 4 + h_con.numel() * 4
+    d2h = h_fit.numel() * 8
+
+    def e2e_step():
+        d_prog.copy_(h_prog, non_blocking=True)
+        d_len.copy_(h_len, non_blocking=True)
+        d_con.copy_(h_con, non_blocking=True)
+        binding.sr_eval(ctx, d_prog, d_len, d_con, X, y, pr.N, binding.SR_MSE_CORR, fitness=fitness)
+        h_fit.copy_(fitness, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e_val = float(nodes[0]) * pr.N / (statistics.mean(e2e_ms) / 1e3) / 1e9 * world
+
+    line = {"metric": METRIC, "value": value, "unit": "GPop/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": pr.name, "programs": pr.P, "cases": pr.N, "vars": pr.nvars,
+                       "lengths": "8-128", "fitness": "MSE and 1-r^2 from one pass",
+                       "step": "sr_eval(SR_MSE_CORR)", "l2": "flushed between timed steps",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "clocks": clocks,
+            "e2e": {"value": e2e_val, "unit": "GPop/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(launches)}
+
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(pr, y.cpu().numpy())
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def cpu_baseline(pr, y):
+    """The oracle as it stands on all host cores, on a bounded sample (~10-20 s)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.evaluate(pr.programs[:16], pr.lengths[:16], pr.consts[:16], pr.X, y, oracle.MSE, pr.N)
+    dt16 = max(time.perf_counter() - t0, 1e-3)
+    S = int(min(pr.P, max(16, 16 * 6.0 / dt16)))
+    idx = np.sort(np.random.default_rng(2).choice(pr.P, S, replace=False))
+    t0 = time.perf_counter()
+    oracle.evaluate(pr.programs[idx], pr.lengths[idx], pr.consts[idx], pr.X, y, oracle.MSE, pr.N)
+    oracle.evaluate(pr.programs[idx], pr.lengths[idx], pr.consts[idx], pr.X, y, oracle.CORR, pr.N)
+    dt = time.perf_counter() - t0
+    units = float(pr.lengths[idx].astype(np.int64).sum()) * pr.N
+    return {"value": units / dt / 1e9, "unit": "GPop/s", "cores": cores, "kind": "oracle",
+            "sample": f"{S} of {pr.P} programs x {pr.N} cases, MSE and 1-r^2 (two passes), {dt:.1f} s"}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        if args.impl == "reference":
+            return run_reference(args, rank, world)
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -56,6 +56,7 @@ def _load():
     lib.or_validate.restype = i32
     lib.or_validate_all.argtypes = [P, P, i32, i32, i32, i32, P, P]
     lib.or_predict.argtypes = [P, i32, P, P, i64, i64, P]
+    lib.or_predict_sens.argtypes = [P, i32, P, P, i64, i64, i32, f64, P, P, P]
     lib.or_eval.argtypes = [P, P, P, i32, i32, i32, P, i64, P, i32, i64, i32, P, P, i32]
     lib.or_condition.argtypes = [P, P, P, i32, i32, i32, P, i64, P, i32, i64, i32, i32, f64, P, P, P, i32]
     lib.or_grad.argtypes = [P, P, P, i32, i32, i32, P, i64, P, i32, i64, P, P, P, i32]
@@ -122,6 +123,25 @@ def predict(tokens, consts, X, N: int | None = None) -> np.ndarray:
     out = np.empty(N, np.float64)
     _load().or_predict(_ptr(t), len(t), _ptr(c), _ptr(X64), ldx, N, _ptr(out))
     return out
+
+
+def predict_sens(tokens, consts, X, N: int | None = None, trials: int = 4,
+                 eps: float = 2.0 ** -22):
+    """FP64 output of one valid program, its per-case sensitivity to a
+    relative +-eps perturbation of every operator output, and the program's
+    conditioning flags."""
+    t = _c(tokens, np.uint8)
+    c = np.zeros(16, np.float64)
+    cc = np.asarray(consts, dtype=np.float64).ravel()
+    c[: len(cc)] = cc
+    X64, ldx = _X(X)
+    N = ldx if N is None else N
+    out = np.empty(N, np.float64)
+    sens = np.empty(N, np.float64)
+    cf = ctypes.c_int(0)
+    _load().or_predict_sens(_ptr(t), len(t), _ptr(c), _ptr(X64), ldx, N, trials, eps, _ptr(out),
+                            _ptr(sens), ctypes.byref(cf))
+    return out, sens, int(cf.value)
 
 
 def mse(yhat, y) -> float:

@@ -251,6 +251,33 @@ void or_predict(const uint8_t *tok, int len, const double *c, const double *X,
   free(stack);
 }
 
+/*
+ * Per-case rounding sensitivity of one valid program's output: yhat[i] is
+ * the plain FP64 value and sens[i] = max over `trials` of |yhat_trial[i] -
+ * yhat[i]|, a trial perturbing every operator output by a relative +-eps.
+ * *cflags receives CF_RANGE / CF_BRANCH found on the plain evaluation.
+ */
+void or_predict_sens(const uint8_t *tok, int len, const double *c,
+                     const double *X, long ldx, long N, int trials, double eps,
+                     double *yhat, double *sens, int *cflags) {
+  double *stack = (double *)malloc(sizeof(double) * (size_t)(len + 1));
+  int cf = 0;
+  for (long i = 0; i < N; ++i) {
+    yhat[i] = eval_case(tok, len, c, X, ldx, i, stack, 0.0, 0, &cf);
+    double m = fabs(yhat[i]);
+    if (m > FLT_MAX || (m > 0.0 && m < FLT_MIN)) cf |= CF_RANGE;
+    double w = 0.0;
+    for (int tr = 1; tr <= trials; ++tr) {
+      double v = eval_case(tok, len, c, X, ldx, i, stack, eps, tr, NULL);
+      double d = fabs(v - yhat[i]);
+      if (!(d <= w)) w = d; /* NaN differences propagate as NaN */
+    }
+    sens[i] = w;
+  }
+  *cflags = cf;
+  free(stack);
+}
+
 /* ---- fitness ------------------------------------------------------------- */
 /* MSE = (1/N) sum (yhat - y)^2; any non-finite output or sum -> +inf. */
 double or_mse(const double *yhat, const double *y, long N) {

@@ -1,0 +1,168 @@
+"""ctypes binding of libsr (include/sr.h).  Argument marshalling only: every
+step of the computation runs in the CUDA library.  Tensors are torch CUDA
+tensors; their data pointers are passed as device pointers.
+
+The library must have been built (``paper_2603_12292_gb300.build.build()``);
+loading fails loudly otherwise -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libsr.so")
+
+SR_OK, SR_EINVAL, SR_ECUDA, SR_ETIMEOUT, SR_EPROGRAM, SR_ENOMEM = range(6)
+SR_MSE, SR_CORR, SR_MSE_CORR = 0, 1, 2
+SR_MAX_LMAX, SR_MAX_VARS, SR_MAX_CONSTS = 512, 16, 16
+
+# exported names declared by include/sr.h (checked by the tests)
+EXPORTS = ["sr_create", "sr_destroy", "sr_set_stream", "sr_status_string", "sr_last_error",
+           "sr_reserve", "sr_sync", "sr_eval", "sr_predict", "sr_kernel_launches"]
+
+_lib = None
+
+
+class SRError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libsr status {status}: {msg}")
+        self.status = status
+
+
+def lib() -> ctypes.CDLL:
+    """Load libsr.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2603_12292_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, u64, f32, f64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_float, ctypes.c_double
+    L.sr_create.argtypes = [ctypes.POINTER(vp), i32, vp]
+    L.sr_destroy.argtypes = [vp]
+    L.sr_set_stream.argtypes = [vp, vp]
+    L.sr_status_string.argtypes = [i32]
+    L.sr_status_string.restype = ctypes.c_char_p
+    L.sr_last_error.argtypes = [vp]
+    L.sr_last_error.restype = ctypes.c_char_p
+    L.sr_reserve.argtypes = [vp, i32, i32, i32]
+    L.sr_sync.argtypes = [vp]
+    L.sr_kernel_launches.argtypes = [vp]
+    L.sr_kernel_launches.restype = u64
+    L.sr_eval.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp, vp, i32, i32, i32, i32, vp, vp]
+    L.sr_predict.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp, i32, i32, i32, vp, i32, vp]
+    for name in EXPORTS:
+        if name not in ("sr_status_string", "sr_last_error", "sr_kernel_launches"):
+            getattr(L, name).restype = i32
+    _lib = L
+    return L
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _check(ctx, st: int):
+    if st != SR_OK:
+        msg = lib().sr_last_error(ctx.handle if ctx is not None else None)
+        raise SRError(st, (msg or b"").decode() or lib().sr_status_string(st).decode())
+
+
+def _dev(t: torch.Tensor, dtype, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+class Context:
+    """Owns one sr_ctx (device, stream, workspace)."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+        self.device = device
+        h = ctypes.c_void_p()
+        s = (stream or torch.cuda.current_stream(device)).cuda_stream
+        st = lib().sr_create(ctypes.byref(h), device, ctypes.c_void_p(s))
+        if st != SR_OK:
+            raise SRError(st, lib().sr_status_string(st).decode())
+        self.handle = h
+
+    def set_stream(self, stream: torch.cuda.Stream):
+        _check(self, lib().sr_set_stream(self.handle, ctypes.c_void_p(stream.cuda_stream)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().sr_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sr_reserve(ctx: Context, P: int, Lmax: int, N: int):
+    _check(ctx, lib().sr_reserve(ctx.handle, P, Lmax, N))
+
+
+def sr_kernel_launches(ctx: Context) -> int:
+    return int(lib().sr_kernel_launches(ctx.handle))
+
+
+def sr_sync(ctx: Context):
+    _check(ctx, lib().sr_sync(ctx.handle))
+
+
+def sr_eval(ctx: Context, programs, lengths, consts, X, y, N: int, kind: int,
+            fitness: torch.Tensor | None = None, prog_flags: torch.Tensor | None = None):
+    """Fitness of every program (sr_eval in include/sr.h).  Returns fitness
+    (float64 [P], or [2, P] for SR_MSE_CORR)."""
+    _dev(programs, torch.uint8, "programs")
+    _dev(lengths, torch.int32, "lengths")
+    _dev(X, torch.float32, "X")
+    _dev(y, torch.float32, "y")
+    P, Lmax = programs.shape
+    K = 0 if consts is None else (consts.shape[1] if consts.dim() == 2 else 0)
+    if consts is not None and K > 0:
+        _dev(consts, torch.float32, "consts")
+    nvars, ldx = X.shape
+    if fitness is None:
+        shape = (2, P) if kind == SR_MSE_CORR else (P,)
+        fitness = torch.empty(shape, dtype=torch.float64, device=programs.device)
+    _dev(fitness, torch.float64, "fitness")
+    if prog_flags is not None:
+        _dev(prog_flags, torch.int32, "prog_flags")
+    _check(ctx, lib().sr_eval(ctx.handle, _ptr(programs), _ptr(lengths), _ptr(consts) if K else None,
+                              P, Lmax, K, _ptr(X), _ptr(y), nvars, N, ldx, kind, _ptr(fitness),
+                              _ptr(prog_flags)))
+    return fitness
+
+
+def sr_predict(ctx: Context, programs, lengths, consts, X, N: int,
+               yhat: torch.Tensor | None = None, prog_flags: torch.Tensor | None = None):
+    """Outputs of every program on every case (sr_predict); returns yhat
+    float32 [P, ldy]."""
+    _dev(programs, torch.uint8, "programs")
+    _dev(lengths, torch.int32, "lengths")
+    _dev(X, torch.float32, "X")
+    P, Lmax = programs.shape
+    K = 0 if consts is None else (consts.shape[1] if consts.dim() == 2 else 0)
+    if consts is not None and K > 0:
+        _dev(consts, torch.float32, "consts")
+    nvars, ldx = X.shape
+    if yhat is None:
+        yhat = torch.empty((P, N), dtype=torch.float32, device=programs.device)
+    _dev(yhat, torch.float32, "yhat")
+    if prog_flags is not None:
+        _dev(prog_flags, torch.int32, "prog_flags")
+    _check(ctx, lib().sr_predict(ctx.handle, _ptr(programs), _ptr(lengths), _ptr(consts) if K else None,
+                                 P, Lmax, K, _ptr(X), nvars, N, ldx, _ptr(yhat), yhat.shape[1],
+                                 _ptr(prog_flags)))
+    return yhat

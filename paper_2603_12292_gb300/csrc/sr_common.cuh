@@ -1,0 +1,76 @@
+// sr_common.cuh -- internal definitions shared by the libsr translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sr.h"
+
+// ---------------------------------------------------------------- context
+struct sr_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  // growable device workspace (scratch for partial sums, queues, stacks)
+  char *ws = nullptr;
+  size_t ws_bytes = 0;
+  // small permanent device block: [0] latched error word, [1..] spare
+  unsigned *dev_words = nullptr;
+  char msg[512] = {0};
+  uint64_t launches = 0;  // kernels launched by this context
+};
+
+namespace sr {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// token encoding (uint8), see sr.h
+constexpr int TOK_ADD = 0, TOK_SUB = 1, TOK_MUL = 2, TOK_DIV = 3;
+constexpr int TOK_SIN = 4, TOK_COS = 5, TOK_EXP = 6, TOK_LOG = 7, TOK_SQRT = 8,
+              TOK_SQ = 9;
+constexpr int TOK_VAR0 = 16, TOK_CONST0 = 32, TOK_NSLOTS = 16;
+
+// token classes used by the decoders
+constexpr int CLS_VAR = 0, CLS_CONST = 1, CLS_UNARY = 2, CLS_BINARY = 3,
+              CLS_BAD = 4;
+
+__host__ __device__ __forceinline__ int tok_class(int v) {
+  if (v <= TOK_DIV) return CLS_BINARY;
+  if (v <= TOK_SQ) return CLS_UNARY;
+  if (v >= TOK_VAR0 && v < TOK_VAR0 + TOK_NSLOTS) return CLS_VAR;
+  if (v >= TOK_CONST0 && v < TOK_CONST0 + TOK_NSLOTS) return CLS_CONST;
+  return CLS_BAD;
+}
+__host__ __device__ __forceinline__ int cls_effect(int c) {
+  return c == CLS_BINARY ? -1 : (c <= CLS_CONST ? 1 : 0);
+}
+
+// device error word bits (latched; reported and cleared by sr_sync)
+constexpr unsigned ERR_TIMEOUT = 1u;
+
+// status helpers (sr_ctx.cu)
+sr_status fail(sr_ctx *ctx, sr_status s, const char *fmt, ...);
+sr_status cuda_fail(sr_ctx *ctx, cudaError_t e, const char *what);
+// grow the workspace to at least `bytes` (refused during stream capture)
+sr_status ensure_workspace(sr_ctx *ctx, size_t bytes);
+bool stream_capturing(sr_ctx *ctx);
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// sequential carving of the workspace
+struct Carver {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    size_t o = off;
+    off = align_up(off + bytes, 256);
+    return o;
+  }
+};
+
+}  // namespace sr
+
+#define SR_CHECK_CUDA(ctx, call)                                  \
+  do {                                                            \
+    cudaError_t _e = (call);                                      \
+    if (_e != cudaSuccess) return ::sr::cuda_fail(ctx, _e, #call); \
+  } while (0)

@@ -14,3 +14,19 @@ if HERE not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built library")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+
+
+@pytest.fixture(scope="session")
+def ctx():
+    """A libsr context on cuda:0 (GPU tests only)."""
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2603_12292_gb300 import binding, build
+
+    build.build()
+    c = binding.Context(0)
+    yield c
+    torch.cuda.synchronize()
+    c.close()

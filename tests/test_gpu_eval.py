@@ -1,0 +1,247 @@
+"""Parity of the CUDA evaluation path (sr_predict / sr_eval through the C ABI)
+with the FP64 oracle, element by element and fitness by fitness."""
+import itertools
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from helpers import check_fitness, dev, fitness_floor, target_problem, top_fraction_agree
+from paper_2603_12292_gb300 import binding, inputs
+from progtext import load_hand_cases, pack, parse
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def predict_parity(ctx, progs, lens, consts, X, N, max_checked=None):
+    """GPU yhat vs oracle yhat element by element: |diff| <= 4 sens + 2^-22 |yhat|
+    for programs without conditioning flags, where sens is the oracle's
+    per-case sensitivity to 2^-22 relative perturbations of every operator."""
+    P, Lmax = progs.shape
+    d = dict(programs=torch.from_numpy(progs).cuda(), lengths=torch.from_numpy(lens).cuda(),
+             consts=torch.from_numpy(consts).cuda(), X=torch.from_numpy(X).cuda())
+    flags = torch.empty(P, dtype=torch.int32, device="cuda")
+    yh = binding.sr_predict(ctx, d["programs"], d["lengths"], d["consts"], d["X"], N, prog_flags=flags)
+    torch.cuda.synchronize()
+    yh = yh.cpu().numpy()
+    flags = flags.cpu().numpy()
+    want_flags, _ = oracle.validate_all(progs, lens, X.shape[0], consts.shape[1])
+    np.testing.assert_array_equal(flags, want_flags)
+    checked = 0
+    for p in range(P):
+        if flags[p]:
+            assert np.isnan(yh[p]).all()
+            continue
+        ref, sens, cf = oracle.predict_sens(progs[p, : lens[p]], consts[p], X, N)
+        if cf:
+            continue
+        g = yh[p].astype(np.float64)
+        fin = np.isfinite(ref)
+        assert np.array_equal(np.isnan(ref), np.isnan(g)), p
+        tol = 4 * sens + 2.0 ** -22 * np.abs(ref) + 1e-37
+        bad = fin & ~(np.abs(g - ref) <= tol)
+        assert not bad.any(), (p, np.nonzero(bad)[0][:5], g[bad][:5], ref[bad][:5])
+        checked += 1
+        if max_checked and checked >= max_checked:
+            break
+    return checked
+
+
+def test_hand_programs_on_gpu(ctx):
+    """The hand-evaluated fixture through sr_predict (FP32 inputs)."""
+    cases = load_hand_cases(os.path.join(GOLDEN, "hand_programs.txt"))
+    for text, consts, xs, expect in cases:
+        prog = parse(text)
+        progs, lens = pack([prog], 8)
+        c = np.zeros((1, 4), np.float32)
+        c[0, : len(consts)] = consts
+        X = np.zeros((3, 4), np.float32)
+        X[: len(xs), :] = np.array(xs, np.float32)[:, None]
+        d = dict(programs=torch.from_numpy(progs).cuda(), lengths=torch.from_numpy(lens).cuda(),
+                 consts=torch.from_numpy(c).cuda(), X=torch.from_numpy(X).cuda())
+        got = binding.sr_predict(ctx, d["programs"], d["lengths"], d["consts"], d["X"], 4)[0].cpu().numpy()
+        # expected from the FP32 inputs in FP64 (the oracle on the same inputs)
+        ref = oracle.predict(prog, c[0], X, 4)
+        if np.isnan(expect):
+            assert np.isnan(got).all(), text
+        else:
+            np.testing.assert_allclose(got, ref, rtol=4e-7, atol=1e-30, err_msg=text)
+
+
+@pytest.mark.parametrize("nconst", [0, 1])
+def test_brute_force_all_short_programs(ctx, nconst):
+    """Every valid program of length <= 5 over 3 variables (and one constant),
+    on 257 cases (two full steps and a ragged tail)."""
+    alphabet = list(range(10)) + [16, 17, 18] + [32 + k for k in range(nconst)]
+    progs_l = []
+    for n in range(1, 6):
+        seqs = np.array(list(itertools.product(alphabet, repeat=n)), np.uint8)
+        flags, _ = oracle.validate_all(seqs, np.full(len(seqs), n, np.int32), 3, nconst)
+        progs_l += list(seqs[flags == 0])
+    assert len(progs_l) == (13_989 if nconst == 0 else 23_308)
+    progs, lens = pack(progs_l, 8)
+    rng = np.random.default_rng(17)
+    X = inputs.random_X(rng, 3, 257, 1.0, 5.0)
+    consts = np.full((len(progs_l), max(nconst, 1)), np.float32(-2.75))
+    checked = predict_parity(ctx, progs, lens, consts[:, :nconst] if nconst else
+                             np.zeros((len(progs_l), 0), np.float32), X, 257)
+    assert checked > 0.95 * len(progs_l)
+
+
+def test_predict_parity_random_population(ctx):
+    pr = inputs.make_problem("pp", 5, P=300, Lmin=1, Lmax=60, nvars=4, K=4, N=1001, xlo=-3,
+                             xhi=3, target_len=(5, 9))
+    assert predict_parity(ctx, pr.programs, pr.lengths, pr.consts, pr.X, pr.N) > 250
+
+
+def test_invalid_programs_flagged_bit_exact(ctx):
+    pr = inputs.make_problem("inv", 8, P=512, Lmin=1, Lmax=40, nvars=3, K=4, N=300, xlo=1, xhi=5,
+                             target_len=(5, 9))
+    progs = pr.programs.copy()
+    lens = pr.lengths.copy()
+    rng = np.random.default_rng(0)
+    for p in range(0, 512, 3):  # corrupt every third program in some way
+        how = p % 5
+        if how == 0:
+            progs[p, rng.integers(0, lens[p])] = rng.integers(0, 256)
+        elif how == 1:
+            lens[p] = 0
+        elif how == 2:
+            lens[p] = 41 if p % 2 else max(1, lens[p] - 1)
+        elif how == 3:
+            progs[p, rng.integers(0, lens[p])] = 16 + 3 + rng.integers(0, 13)
+        else:
+            progs[p, rng.integers(0, lens[p])] = 32 + 4 + rng.integers(0, 12)
+    d = dev(pr, np.ones(pr.N, np.float32))
+    d["programs"] = torch.from_numpy(progs).cuda()
+    d["lengths"] = torch.from_numpy(lens).cuda()
+    flags = torch.empty(512, dtype=torch.int32, device="cuda")
+    for kind in (binding.SR_MSE, binding.SR_CORR):
+        f = binding.sr_eval(ctx, d["programs"], d["lengths"], d["consts"], d["X"], d["y"], pr.N, kind,
+                            prog_flags=flags)
+        torch.cuda.synchronize()
+        want, _ = oracle.validate_all(progs, lens, 3, 4)
+        np.testing.assert_array_equal(flags.cpu().numpy(), want)
+        fn = f.cpu().numpy()
+        assert np.isinf(fn[want != 0]).all() and (fn[want != 0] > 0).all()
+    assert (want != 0).sum() > 100
+
+
+@pytest.mark.parametrize("kind", [oracle.MSE, oracle.CORR])
+def test_fitness_parity_plain(ctx, kind):
+    """256 programs, 1,000 cases (several steps, ragged tail)."""
+    pr, y = target_problem(inputs.plain)
+    d = dev(pr, y)
+    f = binding.sr_eval(ctx, d["programs"], d["lengths"], d["consts"], d["X"], d["y"], pr.N, kind)
+    torch.cuda.synchronize()
+    f = f.cpu().numpy()
+    sens, cfl, f0 = oracle.condition(pr.programs, pr.lengths, pr.consts, pr.X, y, kind, pr.N)
+    assert check_fitness(kind, f, f0, sens, cfl, y) > 0.8 * pr.P
+    tol = 1e-4 * np.abs(f0) + fitness_floor(kind, y) + 16 * sens
+    assert top_fraction_agree(f, f0, tol)
+
+
+@pytest.mark.parametrize("N", [1, 2, 5, 127, 128, 129, 4099, 20_001])
+def test_fitness_parity_sizes(ctx, N):
+    """Case counts around the 4-case group and 128-case step boundaries."""
+    pr = inputs.make_problem("sz", 30 + N, P=97, Lmin=1, Lmax=48, nvars=5, K=4, N=N, xlo=1, xhi=5,
+                             target_len=(5, 9))
+    y = inputs.add_noise(np.random.default_rng(N), np.sin(pr.X[0, :N].astype(np.float64)) * 3 + 1, 0.1)
+    d = dev(pr, y)
+    for kind in (oracle.MSE, oracle.CORR):
+        f = binding.sr_eval(ctx, d["programs"], d["lengths"], d["consts"], d["X"], d["y"], N, kind)
+        torch.cuda.synchronize()
+        f = f.cpu().numpy()
+        sens, cfl, f0 = oracle.condition(pr.programs, pr.lengths, pr.consts, pr.X, y, kind, N)
+        if N < 2 and kind == oracle.CORR:
+            assert (f[np.isfinite(f0)] == 1.0).all()
+            continue
+        check_fitness(kind, f, f0, sens, cfl, y)
+
+
+def test_both_kinds_in_one_pass_match_separate_calls(ctx):
+    pr, y = target_problem(inputs.plain)
+    d = dev(pr, y)
+    both = binding.sr_eval(ctx, d["programs"], d["lengths"], d["consts"], d["X"], d["y"], pr.N,
+                           binding.SR_MSE_CORR)
+    m = binding.sr_eval(ctx, d["programs"], d["lengths"], d["consts"], d["X"], d["y"], pr.N, binding.SR_MSE)
+    c = binding.sr_eval(ctx, d["programs"], d["lengths"], d["consts"], d["X"], d["y"], pr.N, binding.SR_CORR)
+    torch.cuda.synchronize()
+    assert torch.equal(both[0], m) and torch.equal(both[1], c)
+
+
+def test_deep_and_long_programs(ctx):
+    """Stack depth beyond the shared-memory slots (global scratch path) and
+    Lmax = 512."""
+    deep = np.array([16, 17] * 128 + [0, 1] * 127 + [2], np.uint8)   # depth 256, length 511
+    comb = np.array([16] + [17, 2] * 255 + [4], np.uint8)             # depth 2, length 512
+    wide = np.array([16, 17, 18] * 10 + [3] * 29, np.uint8)           # depth 30
+    progs, lens = pack([deep, comb, wide], 512)
+    X = inputs.random_X(np.random.default_rng(3), 3, 700, 0.98, 1.02)
+    fl, md = oracle.validate_all(progs, lens, 3, 0)
+    assert (fl == 0).all() and md[0] == 256 and md[2] == 30
+    assert predict_parity(ctx, progs, lens, np.zeros((3, 0), np.float32), X, 700) == 3
+
+
+def test_constant_and_single_token_programs(ctx):
+    progs, lens = pack([parse("c0"), parse("x1"), parse("c0 sin c1 *")], 4)
+    c = np.array([[2.5, -1.0]] * 3, np.float32)
+    X = inputs.random_X(np.random.default_rng(4), 2, 333, 1, 5)
+    y = (X[1, :333] * 2).astype(np.float32)
+    d = dict(programs=torch.from_numpy(progs).cuda(), lengths=torch.from_numpy(lens).cuda(),
+             consts=torch.from_numpy(c).cuda(), X=torch.from_numpy(X).cuda(), y=torch.from_numpy(y).cuda())
+    f = binding.sr_eval(ctx, d["programs"], d["lengths"], d["consts"], d["X"], d["y"], 333,
+                        binding.SR_MSE_CORR).cpu().numpy()
+    assert f[1, 0] == 1.0 and f[1, 2] == 1.0 and f[1, 1] == pytest.approx(0.0, abs=1e-6)
+    want = np.mean((2.5 - y.astype(np.float64)) ** 2)
+    assert f[0, 0] == pytest.approx(want, rel=1e-6)
+
+
+def test_nonfinite_outputs_score_worst(ctx):
+    progs, lens = pack([parse("x0 exp exp sq"), parse("x0 x0 -")], 4)
+    X = inputs.random_X(np.random.default_rng(5), 1, 200, 1, 5)
+    X[0, 17] = np.inf
+    y = np.linspace(0, 1, 200).astype(np.float32)
+    d = dict(programs=torch.from_numpy(progs).cuda(), lengths=torch.from_numpy(lens).cuda(),
+             consts=torch.zeros((2, 1), device="cuda"), X=torch.from_numpy(X).cuda(),
+             y=torch.from_numpy(y).cuda())
+    f = binding.sr_eval(ctx, d["programs"], d["lengths"], d["consts"], d["X"], d["y"], 200,
+                        binding.SR_MSE_CORR).cpu().numpy()
+    assert np.isposinf(f[0]).all() and (f[1] == 1.0).all()
+
+
+def test_argument_errors(ctx):
+    x = torch.zeros(3 * 8 + 1, device="cuda")[1:].view(3, 8)  # 4-byte offset: misaligned
+    progs = torch.zeros((1, 4), dtype=torch.uint8, device="cuda")
+    lens = torch.ones(1, dtype=torch.int32, device="cuda")
+    y = torch.zeros(8, device="cuda")
+    with pytest.raises(binding.SRError) as e:
+        binding.sr_eval(ctx, progs, lens, None, x, y, 8, binding.SR_MSE)
+    assert e.value.status == binding.SR_EINVAL
+    X = torch.zeros((3, 8), device="cuda")
+    with pytest.raises(binding.SRError):
+        binding.sr_eval(ctx, progs, lens, None, X, y, 9, binding.SR_MSE)  # ldx < N
+    with pytest.raises(binding.SRError):
+        binding.sr_eval(ctx, progs, lens, None, X, y, 8, 7)  # unknown kind
+    # P = 0 launches nothing and succeeds
+    f = torch.empty(0, dtype=torch.float64, device="cuda")
+    binding.sr_eval(ctx, progs[:0], lens[:0], None, X, y, 8, binding.SR_MSE, fitness=f)
+
+
+def test_full_size_paper_shaped_sampled(ctx):
+    """4,096 programs x 100,000 cases (the bench workload and launch
+    configuration); the oracle checks 48 sampled programs on every case."""
+    pr, y = target_problem(inputs.paper_shaped)
+    d = dev(pr, y)
+    f = binding.sr_eval(ctx, d["programs"], d["lengths"], d["consts"], d["X"], d["y"], pr.N,
+                        binding.SR_MSE_CORR)
+    torch.cuda.synchronize()
+    f = f.cpu().numpy()
+    idx = np.random.default_rng(0).choice(pr.P, 48, replace=False)
+    for row, kind in ((0, oracle.MSE), (1, oracle.CORR)):
+        sens, cfl, f0 = oracle.condition(pr.programs[idx], pr.lengths[idx], pr.consts[idx], pr.X, y,
+                                         kind, pr.N, trials=2)
+        assert check_fitness(kind, f[row, idx], f0, sens, cfl, y) > 24
