@@ -26,7 +26,7 @@ MSE, CORR = 0, 1
 PF_BAD_LENGTH, PF_BAD_TOKEN, PF_BAD_VAR = 1, 2, 4
 PF_BAD_CONST, PF_UNDERFLOW, PF_BAD_FINAL = 8, 16, 32
 # conditioning flag bits
-CF_RANGE, CF_BRANCH, CF_FITRANGE = 1, 2, 4
+CF_RANGE, CF_FITRANGE = 1, 4
 
 _lib = None
 
@@ -56,9 +56,9 @@ def _load():
     lib.or_validate.restype = i32
     lib.or_validate_all.argtypes = [P, P, i32, i32, i32, i32, P, P]
     lib.or_predict.argtypes = [P, i32, P, P, i64, i64, P]
-    lib.or_predict_sens.argtypes = [P, i32, P, P, i64, i64, i32, f64, P, P, P]
+    lib.or_predict_interval.argtypes = [P, i32, P, P, i64, i64, f64, P, P, P, P]
     lib.or_eval.argtypes = [P, P, P, i32, i32, i32, P, i64, P, i32, i64, i32, P, P, i32]
-    lib.or_condition.argtypes = [P, P, P, i32, i32, i32, P, i64, P, i32, i64, i32, i32, f64, P, P, P, i32]
+    lib.or_condition.argtypes = [P, P, P, i32, i32, i32, P, i64, P, i32, i64, i32, f64, P, P, P, i32]
     lib.or_grad.argtypes = [P, P, P, i32, i32, i32, P, i64, P, i32, i64, P, P, P, i32]
     lib.or_grad_one.argtypes = [P, i32, P, i32, P, i64, P, i64, P, P, P]
     lib.or_mse_fp64_consts.argtypes = [P, i32, P, P, i64, P, i64]
@@ -125,11 +125,13 @@ def predict(tokens, consts, X, N: int | None = None) -> np.ndarray:
     return out
 
 
-def predict_sens(tokens, consts, X, N: int | None = None, trials: int = 4,
-                 eps: float = 2.0 ** -22):
-    """FP64 output of one valid program, its per-case sensitivity to a
-    relative +-eps perturbation of every operator output, and the program's
-    conditioning flags."""
+U_FP32 = 2.0 ** -22  # relative error allowed per FP32 operator output (2 ulp)
+
+
+def predict_interval(tokens, consts, X, N: int | None = None, u: float = U_FP32):
+    """FP64 output of one valid program, intervals [lo, hi] enclosing its
+    FP32 output on every case (relative error <= u per operator output), and
+    each case's conditioning flags (CF_RANGE: FP32 could overflow or give NaN)."""
     t = _c(tokens, np.uint8)
     c = np.zeros(16, np.float64)
     cc = np.asarray(consts, dtype=np.float64).ravel()
@@ -137,11 +139,12 @@ def predict_sens(tokens, consts, X, N: int | None = None, trials: int = 4,
     X64, ldx = _X(X)
     N = ldx if N is None else N
     out = np.empty(N, np.float64)
-    sens = np.empty(N, np.float64)
-    cf = ctypes.c_int(0)
-    _load().or_predict_sens(_ptr(t), len(t), _ptr(c), _ptr(X64), ldx, N, trials, eps, _ptr(out),
-                            _ptr(sens), ctypes.byref(cf))
-    return out, sens, int(cf.value)
+    lo = np.empty(N, np.float64)
+    hi = np.empty(N, np.float64)
+    cf = np.empty(N, np.int32)
+    _load().or_predict_interval(_ptr(t), len(t), _ptr(c), _ptr(X64), ldx, N, u, _ptr(out), _ptr(lo),
+                                _ptr(hi), _ptr(cf))
+    return out, lo, hi, cf
 
 
 def mse(yhat, y) -> float:
@@ -176,9 +179,9 @@ def evaluate(programs, lengths, consts, X, y, kind: int, N: int | None = None, n
 
 
 def condition(programs, lengths, consts, X, y, kind: int, N: int | None = None,
-              trials: int = 3, eps: float = 2.0 ** -22, nthreads: int = 0):
-    """Per-program sensitivity to relative +-eps perturbation of every
-    operator output, conditioning flags and unperturbed fitness."""
+              u: float = U_FP32, nthreads: int = 0):
+    """Per program: bound on the fitness change FP32 evaluation can cause,
+    conditioning flags, and the FP64 fitness."""
     prog = _c(programs, np.uint8)
     P, Lmax = prog.shape
     lens = _c(lengths, np.int32)
@@ -188,13 +191,12 @@ def condition(programs, lengths, consts, X, y, kind: int, N: int | None = None,
     nvars = X64.shape[0]
     N = ldx if N is None else N
     y64 = _c(np.asarray(y)[:N], np.float64)
-    sens = np.empty(P, np.float64)
+    errb = np.empty(P, np.float64)
     cfl = np.empty(P, np.int32)
     f0 = np.empty(P, np.float64)
     _load().or_condition(_ptr(prog), _ptr(lens), _ptr(cons), P, Lmax, K, _ptr(X64), ldx,
-                         _ptr(y64), nvars, N, kind, trials, eps, _ptr(sens), _ptr(cfl),
-                         _ptr(f0), nthreads)
-    return sens, cfl, f0
+                         _ptr(y64), nvars, N, kind, u, _ptr(errb), _ptr(cfl), _ptr(f0), nthreads)
+    return errb, cfl, f0
 
 
 def grad(programs, lengths, consts, X, y, N: int | None = None, nthreads: int = 0):

@@ -68,7 +68,6 @@ enum {
 
 /* conditioning flag bits */
 #define CF_RANGE 1     /* an intermediate outside the FP32 normal range      */
-#define CF_BRANCH 2    /* a branch argument close to its switch point        */
 #define CF_FITRANGE 4  /* a fitness term whose FP32 partial sums may overflow */
 
 #define PROTECT_EPS 1e-3
@@ -169,74 +168,178 @@ static double apply_unary(int t, double x) {
   }
 }
 
-/* ---- perturbation sign for the conditioning report --------------------- */
-static uint64_t splitmix64(uint64_t z) {
-  z += 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-
-/*
- * Evaluate one valid program on case i.  When eps != 0 every operator
- * output v is replaced by v * (1 +- eps), the sign drawn from a hash of
- * (trial, token, case): a stochastic-arithmetic estimate of how far rounding
- * at relative size eps can move the result (Vignes' CESTAC idea).  When
- * cond != NULL, range and branch-proximity flags are OR-ed into *cond.
- */
+/* Evaluate one valid program on case i (value stack, Sec. 2.1.4). */
 static double eval_case(const uint8_t *tok, int len, const double *c,
-                        const double *X, long ldx, long i, double *stack,
-                        double eps, int trial, int *cond) {
+                        const double *X, long ldx, long i, double *stack) {
   int sp = 0;
   for (int t = 0; t < len; ++t) {
     int v = tok[t];
-    double r;
     if (is_var(v)) {
       stack[sp++] = X[(long)(v - TK_VAR0) * ldx + i];
-      continue;
-    }
-    if (is_const(v)) {
+    } else if (is_const(v)) {
       stack[sp++] = c[v - TK_CONST0];
-      continue;
-    }
-    if (is_binary(v)) {
+    } else if (is_binary(v)) {
       double b = stack[--sp];
       double a = stack[sp - 1];
-      r = apply_binary(v, a, b);
-      if (cond && v == TK_DIV) {
-        double m = fabs(b);
-        if (fabs(m - PROTECT_EPS) <= 1e-3 * PROTECT_EPS) *cond |= CF_BRANCH;
-      }
-      if (eps != 0.0) {
-        uint64_t h = splitmix64(((uint64_t)trial << 48) ^ ((uint64_t)t << 32) ^
-                                (uint64_t)i);
-        r *= (h >> 63) ? (1.0 - eps) : (1.0 + eps);
-      }
-      stack[sp - 1] = r;
+      stack[sp - 1] = apply_binary(v, a, b);
     } else {
-      double x = stack[sp - 1];
-      r = apply_unary(v, x);
-      if (cond) {
-        if (v == TK_LOG &&
-            fabs(fabs(x) - PROTECT_EPS) <= 1e-3 * PROTECT_EPS)
-          *cond |= CF_BRANCH;
-        if (v == TK_EXP &&
-            fabs(fabs(x) - EXP_CLAMP) <= 1e-3 * EXP_CLAMP)
-          *cond |= CF_BRANCH;
-      }
-      if (eps != 0.0) {
-        uint64_t h = splitmix64(((uint64_t)trial << 48) ^ ((uint64_t)t << 32) ^
-                                (uint64_t)i);
-        r *= (h >> 63) ? (1.0 - eps) : (1.0 + eps);
-      }
-      stack[sp - 1] = r;
-    }
-    if (cond) {
-      double m = fabs(r);
-      if (m > FLT_MAX || (m > 0.0 && m < FLT_MIN)) *cond |= CF_RANGE;
+      stack[sp - 1] = apply_unary(v, stack[sp - 1]);
     }
   }
   return stack[0];
+}
+
+/* ---- interval enclosure of the FP32 evaluation ------------------------- */
+/*
+ * Every FP32 operator output is within a relative u of the exact operator
+ * applied to its FP32 operands (u = 2^-22 covers correctly rounded arithmetic
+ * and library functions accurate to 2 ulp), plus 2^-149 absolute for
+ * subnormal results.  Inputs and constants are exact.  Evaluating the program
+ * on intervals -- each operator's exact range over its operand intervals,
+ * widened by that rounding -- therefore encloses the FP32 result of every
+ * case, whatever the nonlinearity, clamp or protected branch in between.
+ */
+typedef struct {
+  double lo, hi;
+} ival;
+
+#define SUBNORMAL_SLACK 1.401298464324817e-45 /* 2^-149 */
+
+static ival iv(double lo, double hi) {
+  ival r = {lo, hi};
+  return r;
+}
+static double dmin(double a, double b) { return a < b ? a : b; }
+static double dmax(double a, double b) { return a > b ? a : b; }
+static ival widen(ival a, double u) {
+  a.lo -= u * fabs(a.lo) + SUBNORMAL_SLACK;
+  a.hi += u * fabs(a.hi) + SUBNORMAL_SLACK;
+  return a;
+}
+static ival hull(ival a, ival b) { return iv(dmin(a.lo, b.lo), dmax(a.hi, b.hi)); }
+static ival iv_mul(ival a, ival b) {
+  double p1 = a.lo * b.lo, p2 = a.lo * b.hi, p3 = a.hi * b.lo, p4 = a.hi * b.hi;
+  return iv(dmin(dmin(p1, p2), dmin(p3, p4)), dmax(dmax(p1, p2), dmax(p3, p4)));
+}
+/* a / b for b inside [b1, b2] not containing 0 */
+static ival iv_quot(ival a, double b1, double b2) {
+  double q1 = a.lo / b1, q2 = a.lo / b2, q3 = a.hi / b1, q4 = a.hi / b2;
+  return iv(dmin(dmin(q1, q2), dmin(q3, q4)), dmax(dmax(q1, q2), dmax(q3, q4)));
+}
+/* protected division: 1 where |b| <= 1e-3, a / b elsewhere */
+static ival iv_div(ival a, ival b) {
+  int have = 0;
+  ival r = iv(0.0, 0.0);
+  if (b.lo <= PROTECT_EPS && b.hi >= -PROTECT_EPS) {
+    r = iv(1.0, 1.0);
+    have = 1;
+  }
+  if (b.lo < -PROTECT_EPS) {
+    ival q = iv_quot(a, b.lo, dmin(b.hi, -PROTECT_EPS));
+    r = have ? hull(r, q) : q;
+    have = 1;
+  }
+  if (b.hi > PROTECT_EPS) {
+    ival q = iv_quot(a, dmax(b.lo, PROTECT_EPS), b.hi);
+    r = have ? hull(r, q) : q;
+  }
+  return r;
+}
+/* range of sin over [lo, hi] (cos via a shift of pi/2 in the extremum test) */
+static ival iv_trig(ival a, int is_cos) {
+  const double two_pi = 6.283185307179586, half_pi = 1.5707963267948966;
+  if (!(a.hi - a.lo < two_pi)) return iv(-1.0, 1.0);
+  double f1 = is_cos ? cos(a.lo) : sin(a.lo), f2 = is_cos ? cos(a.hi) : sin(a.hi);
+  ival r = iv(dmin(f1, f2), dmax(f1, f2));
+  /* maxima of sin at pi/2 + 2k pi, of cos at 2k pi; minima half a turn on */
+  double pmax = is_cos ? 0.0 : half_pi;
+  double k = ceil((a.lo - pmax) / two_pi);
+  if (pmax + two_pi * k <= a.hi) r.hi = 1.0;
+  k = ceil((a.lo - pmax - 3.141592653589793) / two_pi);
+  if (pmax + 3.141592653589793 + two_pi * k <= a.hi) r.lo = -1.0;
+  /* the extremum tests are done in FP64 near the endpoints: widen a touch */
+  r.lo = dmax(-1.0, r.lo - 1e-15);
+  r.hi = dmin(1.0, r.hi + 1e-15);
+  return r;
+}
+/* range of |x| over [lo, hi] */
+static ival iv_abs(ival a) {
+  if (a.lo <= 0.0 && a.hi >= 0.0) return iv(0.0, dmax(-a.lo, a.hi));
+  return iv(dmin(fabs(a.lo), fabs(a.hi)), dmax(fabs(a.lo), fabs(a.hi)));
+}
+static ival iv_unary(int v, ival a) {
+  switch (v) {
+    case TK_SIN: return iv_trig(a, 0);
+    case TK_COS: return iv_trig(a, 1);
+    case TK_EXP: return iv(op_exp(a.lo), op_exp(a.hi)); /* monotone, clamped */
+    case TK_LOG: {
+      ival m = iv_abs(a);
+      int have = 0;
+      ival r = iv(0.0, 0.0);
+      if (m.lo <= PROTECT_EPS) {
+        r = iv(0.0, 0.0);
+        have = 1;
+      }
+      if (m.hi > PROTECT_EPS) {
+        ival q = iv(log(dmax(m.lo, PROTECT_EPS)), log(m.hi));
+        r = have ? hull(r, q) : q;
+      }
+      return r;
+    }
+    case TK_SQRT: {
+      ival m = iv_abs(a);
+      return iv(sqrt(m.lo), sqrt(m.hi));
+    }
+    default: {
+      ival m = iv_abs(a);
+      return iv(m.lo * m.lo, m.hi * m.hi);
+    }
+  }
+}
+
+/*
+ * Interval enclosure of the FP32 output of one valid program on case i.
+ * Returns the FP64 value; *lo, *hi receive the enclosure.  *cond gets
+ * CF_RANGE when an enclosure reaches beyond the FP32 range (FP32 could
+ * overflow to inf) or is not a number (FP32 could produce NaN).
+ * Work arrays: val [len + 1], box [len + 1].
+ */
+static double case_interval(const uint8_t *tok, int len, const double *c,
+                            const double *X, long ldx, long i, double u,
+                            double *val, ival *box, int *cond, double *lo,
+                            double *hi) {
+  int sp = 0, cf = 0;
+  for (int t = 0; t < len; ++t) {
+    int v = tok[t];
+    if (is_var(v) || is_const(v)) {
+      double x = is_var(v) ? X[(long)(v - TK_VAR0) * ldx + i] : c[v - TK_CONST0];
+      val[sp] = x;
+      box[sp++] = iv(x, x);
+      continue;
+    }
+    ival r;
+    if (is_binary(v)) {
+      --sp;
+      ival a = box[sp - 1], b = box[sp];
+      val[sp - 1] = apply_binary(v, val[sp - 1], val[sp]);
+      switch (v) {
+        case TK_ADD: r = iv(a.lo + b.lo, a.hi + b.hi); break;
+        case TK_SUB: r = iv(a.lo - b.hi, a.hi - b.lo); break;
+        case TK_MUL: r = iv_mul(a, b); break;
+        default: r = iv_div(a, b); break;
+      }
+    } else {
+      val[sp - 1] = apply_unary(v, val[sp - 1]);
+      r = iv_unary(v, box[sp - 1]);
+    }
+    r = widen(r, u);
+    if (!(r.lo >= -FLT_MAX && r.hi <= FLT_MAX)) cf |= CF_RANGE; /* also NaN */
+    box[sp - 1] = r;
+  }
+  if (cond) *cond |= cf;
+  *lo = box[0].lo;
+  *hi = box[0].hi;
+  return val[0];
 }
 
 /*
@@ -247,35 +350,29 @@ void or_predict(const uint8_t *tok, int len, const double *c, const double *X,
                 long ldx, long N, double *yhat) {
   double *stack = (double *)malloc(sizeof(double) * (size_t)(len + 1));
   for (long i = 0; i < N; ++i)
-    yhat[i] = eval_case(tok, len, c, X, ldx, i, stack, 0.0, 0, NULL);
+    yhat[i] = eval_case(tok, len, c, X, ldx, i, stack);
   free(stack);
 }
 
 /*
- * Per-case rounding sensitivity of one valid program's output: yhat[i] is
- * the plain FP64 value and sens[i] = max over `trials` of |yhat_trial[i] -
- * yhat[i]|, a trial perturbing every operator output by a relative +-eps.
- * *cflags receives CF_RANGE / CF_BRANCH found on the plain evaluation.
+ * FP64 output of one valid program on cases [0, N), the interval [lo, hi]
+ * enclosing its FP32 output on every case (see case_interval), and the
+ * conditioning flags of every case.
  */
-void or_predict_sens(const uint8_t *tok, int len, const double *c,
-                     const double *X, long ldx, long N, int trials, double eps,
-                     double *yhat, double *sens, int *cflags) {
-  double *stack = (double *)malloc(sizeof(double) * (size_t)(len + 1));
-  int cf = 0;
+void or_predict_interval(const uint8_t *tok, int len, const double *c,
+                         const double *X, long ldx, long N, double u,
+                         double *yhat, double *lo, double *hi,
+                         int32_t *cflags) {
+  double *val = (double *)malloc(sizeof(double) * (size_t)(len + 1));
+  ival *box = (ival *)malloc(sizeof(ival) * (size_t)(len + 1));
   for (long i = 0; i < N; ++i) {
-    yhat[i] = eval_case(tok, len, c, X, ldx, i, stack, 0.0, 0, &cf);
-    double m = fabs(yhat[i]);
-    if (m > FLT_MAX || (m > 0.0 && m < FLT_MIN)) cf |= CF_RANGE;
-    double w = 0.0;
-    for (int tr = 1; tr <= trials; ++tr) {
-      double v = eval_case(tok, len, c, X, ldx, i, stack, eps, tr, NULL);
-      double d = fabs(v - yhat[i]);
-      if (!(d <= w)) w = d; /* NaN differences propagate as NaN */
-    }
-    sens[i] = w;
+    int cf = 0;
+    yhat[i] = case_interval(tok, len, c, X, ldx, i, u, val, box, &cf, &lo[i],
+                            &hi[i]);
+    cflags[i] = cf;
   }
-  *cflags = cf;
-  free(stack);
+  free(val);
+  free(box);
 }
 
 /* ---- fitness ------------------------------------------------------------- */
@@ -368,56 +465,87 @@ void or_eval(const uint8_t *programs, const int32_t *lengths,
 }
 
 /*
- * Conditioning report for one valid program (FP32 consts widened).
- *   *sens   = max over trials of |f_trial - f_0|, where a trial perturbs
- *             every operator output by a relative +-eps (0 when f_0 is not
- *             finite, or when the program has no operator)
- *   *cflags = CF_RANGE | CF_BRANCH | CF_FITRANGE as found on the unperturbed
- *             evaluation.  CF_FITRANGE: some per-case fitness term exceeds
- *             FLT_MAX / N, so an FP32 partial sum of such terms may overflow
- *             (MSE: (yhat - y)^2; correlation: d^2 and |d * (y - mean y)|
- *             with d = yhat - yhat[0]).
- *   *f0     = the unperturbed fitness
+ * Conditioning report for one valid program (FP32 constants widened).
+ *   *f0     = the fitness (FP64)
+ *   *errb   = bound on how far FP32 evaluation can move the fitness, from
+ *             the per-case enclosures [lo_i, hi_i] of the output (0 when f0
+ *             is not finite; +inf when not finite):
+ *             MSE: the exact range of (1/N) sum (v_i - y_i)^2 over
+ *                  v_i in [lo_i, hi_i], each term's interval widened by the
+ *                  FP32 subtraction, squaring and summation (4u relative);
+ *             1 - r^2 (Eq. 1): with b_i = max(hi_i - yhat_i, yhat_i - lo_i),
+ *                  xc_i = yhat_i - mean yhat, yc_i = y_i - mean y and
+ *                  d_i = yhat_i - yhat_0 (FP32 moments are taken about a
+ *                  shift), Sxy moves by at most A = sum |yc_i| b_i +
+ *                  8u sum |d_i yc_i| and Sxx by at most B = 2 sum |xc_i| b_i
+ *                  + sum b_i^2 + 8u sum d_i^2, so r^2 stays within
+ *                  [(|Sxy| - A)_+^2 / ((Sxx + B) Syy),
+ *                   (|Sxy| + A)^2 / ((Sxx - B) Syy)], widened by 4u r^2
+ *   *cflags = OR of the case flags, plus CF_FITRANGE when some per-case
+ *             fitness term exceeds FLT_MAX / N, so an FP32 partial sum of
+ *             such terms may overflow (MSE: e_i^2; correlation: d_i^2 and
+ *             |d_i yc_i|).
+ * Work arrays yhat, lo, hi [N], cfl [N].
  */
 void or_condition_one(const uint8_t *tok, int len, const double *c,
                       const double *X, long ldx, const double *y, long N,
-                      int kind, int trials, double eps, double *yhat,
-                      double *stack, double *sens, int *cflags, double *f0) {
+                      int kind, double u, double *yhat, double *lo, double *hi,
+                      int32_t *cfl, double *errb, int *cflags, double *f0) {
+  or_predict_interval(tok, len, c, X, ldx, N, u, yhat, lo, hi, cfl);
   int cf = 0;
-  for (long i = 0; i < N; ++i)
-    yhat[i] = eval_case(tok, len, c, X, ldx, i, stack, 0.0, 0, &cf);
-  for (long i = 0; i < N; ++i) {
-    double m = fabs(yhat[i]);
-    if (m > FLT_MAX || (m > 0.0 && m < FLT_MIN)) cf |= CF_RANGE;
-  }
+  for (long i = 0; i < N; ++i) cf |= cfl[i];
   double base = fitness_of(kind, yhat, y, N);
-  /* fitness-term range */
   double lim = (double)FLT_MAX / (double)(N > 0 ? N : 1);
+  double err = 0.0;
   if (kind == KIND_MSE) {
+    double smin = 0.0, smax = 0.0;
     for (long i = 0; i < N; ++i) {
       double e = yhat[i] - y[i];
       if (e * e > lim) cf |= CF_FITRANGE;
+      double elo = lo[i] - y[i], ehi = hi[i] - y[i];
+      double qmax = dmax(elo * elo, ehi * ehi);
+      double qmin = (elo <= 0.0 && ehi >= 0.0) ? 0.0 : dmin(elo * elo, ehi * ehi);
+      smin += qmin * (1.0 - 4.0 * u);
+      smax += qmax * (1.0 + 4.0 * u);
     }
-  } else if (N > 0) {
-    double my = 0.0;
-    for (long i = 0; i < N; ++i) my += y[i];
-    my /= (double)N;
+    smin /= (double)N;
+    smax /= (double)N;
+    err = dmax(smax - base, base - smin);
+  } else if (N >= 2) {
+    double my = 0.0, mh = 0.0;
     for (long i = 0; i < N; ++i) {
-      double d = yhat[i] - yhat[0];
-      if (d * d > lim || fabs(d * (y[i] - my)) > lim) cf |= CF_FITRANGE;
+      my += y[i];
+      mh += yhat[i];
+    }
+    my /= (double)N;
+    mh /= (double)N;
+    double sxy = 0.0, syy = 0.0, sxx = 0.0, A = 0.0, B = 0.0, D2 = 0.0, DY = 0.0;
+    for (long i = 0; i < N; ++i) {
+      double yc = y[i] - my, xc = yhat[i] - mh, d = yhat[i] - yhat[0];
+      double b = dmax(hi[i] - yhat[i], yhat[i] - lo[i]);
+      if (d * d > lim || fabs(d * yc) > lim) cf |= CF_FITRANGE;
+      sxy += yc * xc;
+      syy += yc * yc;
+      sxx += xc * xc;
+      A += fabs(yc) * b;
+      B += 2.0 * fabs(xc) * b + b * b;
+      D2 += d * d;
+      DY += fabs(d * yc);
+    }
+    A += 8.0 * u * DY;
+    B += 8.0 * u * D2;
+    if (sxx > 0.0 && syy > 0.0) {
+      double r2 = sxy * sxy / (sxx * syy);
+      double l = fabs(sxy) - A;
+      l = l > 0.0 ? l * l / ((sxx + B) * syy) : 0.0;
+      double h = sxx - B > 0.0 ? (fabs(sxy) + A) * (fabs(sxy) + A) / ((sxx - B) * syy)
+                               : INFINITY;
+      err = dmax(h - r2, r2 - l) + 4.0 * u * r2;
     }
   }
-  double worst = 0.0;
-  if (isfinite(base)) {
-    for (int tr = 1; tr <= trials; ++tr) {
-      for (long i = 0; i < N; ++i)
-        yhat[i] = eval_case(tok, len, c, X, ldx, i, stack, eps, tr, NULL);
-      double f = fitness_of(kind, yhat, y, N);
-      double d = isfinite(f) ? fabs(f - base) : INFINITY;
-      if (d > worst) worst = d;
-    }
-  }
-  *sens = worst;
+  if (!isfinite(base)) err = 0.0;
+  else if (!isfinite(err)) err = INFINITY;
+  *errb = err;
   *cflags = cf;
   *f0 = base;
 }
@@ -425,32 +553,33 @@ void or_condition_one(const uint8_t *tok, int len, const double *c,
 void or_condition(const uint8_t *programs, const int32_t *lengths,
                   const float *consts, int P, int Lmax, int K,
                   const double *X, long ldx, const double *y, int nvars,
-                  long N, int kind, int trials, double eps, double *sens,
-                  int32_t *cflags, double *f0, int nthreads) {
+                  long N, int kind, double u, double *errb, int32_t *cflags,
+                  double *f0, int nthreads) {
   int nt = thread_count(nthreads);
 #pragma omp parallel num_threads(nt)
   {
-    double *yhat = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
-    double *stack = (double *)malloc(sizeof(double) * (size_t)(Lmax + 1));
+    size_t nn = (size_t)(N > 0 ? N : 1);
+    double *yhat = (double *)malloc(sizeof(double) * nn * 3);
+    int32_t *cfl = (int32_t *)malloc(sizeof(int32_t) * nn);
     double c[TK_NSLOTS];
 #pragma omp for schedule(dynamic, 1)
     for (int p = 0; p < P; ++p) {
       const uint8_t *tok = programs + (size_t)p * Lmax;
       int md;
       if (or_validate(tok, lengths[p], Lmax, nvars, K, &md)) {
-        sens[p] = 0.0;
+        errb[p] = 0.0;
         cflags[p] = 0;
         f0[p] = INFINITY;
         continue;
       }
       widen_consts(consts + (size_t)p * K, K, c);
       int cf;
-      or_condition_one(tok, lengths[p], c, X, ldx, y, N, kind, trials, eps,
-                       yhat, stack, &sens[p], &cf, &f0[p]);
+      or_condition_one(tok, lengths[p], c, X, ldx, y, N, kind, u, yhat,
+                       yhat + nn, yhat + 2 * nn, cfl, &errb[p], &cf, &f0[p]);
       cflags[p] = cf;
     }
     free(yhat);
-    free(stack);
+    free(cfl);
   }
 }
 

@@ -16,10 +16,12 @@ pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
-def predict_parity(ctx, progs, lens, consts, X, N, max_checked=None):
-    """GPU yhat vs oracle yhat element by element: |diff| <= 4 sens + 2^-22 |yhat|
-    for programs without conditioning flags, where sens is the oracle's
-    per-case sensitivity to 2^-22 relative perturbations of every operator."""
+def predict_parity(ctx, progs, lens, consts, X, N):
+    """GPU yhat vs oracle, element by element: on every case whose FP32
+    result cannot overflow or be NaN, the GPU value lies in the oracle's
+    interval enclosure of the FP32 evaluation (2^-22 relative per operator).
+    Flags must match the oracle's validator bit for bit.  Returns the number
+    of cases checked."""
     P, Lmax = progs.shape
     d = dict(programs=torch.from_numpy(progs).cuda(), lengths=torch.from_numpy(lens).cuda(),
              consts=torch.from_numpy(consts).cuda(), X=torch.from_numpy(X).cuda())
@@ -35,18 +37,12 @@ def predict_parity(ctx, progs, lens, consts, X, N, max_checked=None):
         if flags[p]:
             assert np.isnan(yh[p]).all()
             continue
-        ref, sens, cf = oracle.predict_sens(progs[p, : lens[p]], consts[p], X, N)
-        if cf:
-            continue
+        ref, lo, hi, cf = oracle.predict_interval(progs[p, : lens[p]], consts[p], X, N)
         g = yh[p].astype(np.float64)
-        fin = np.isfinite(ref)
-        assert np.array_equal(np.isnan(ref), np.isnan(g)), p
-        tol = 4 * sens + 2.0 ** -22 * np.abs(ref) + 1e-37
-        bad = fin & ~(np.abs(g - ref) <= tol)
-        assert not bad.any(), (p, np.nonzero(bad)[0][:5], g[bad][:5], ref[bad][:5])
-        checked += 1
-        if max_checked and checked >= max_checked:
-            break
+        ok = cf == 0
+        bad = ok & ~((lo <= g) & (g <= hi))
+        assert not bad.any(), (p, np.nonzero(bad)[0][:5], g[bad][:5], lo[bad][:5], hi[bad][:5])
+        checked += int(ok.sum())
     return checked
 
 
@@ -88,13 +84,13 @@ def test_brute_force_all_short_programs(ctx, nconst):
     consts = np.full((len(progs_l), max(nconst, 1)), np.float32(-2.75))
     checked = predict_parity(ctx, progs, lens, consts[:, :nconst] if nconst else
                              np.zeros((len(progs_l), 0), np.float32), X, 257)
-    assert checked > 0.95 * len(progs_l)
+    assert checked > 0.95 * len(progs_l) * 257
 
 
 def test_predict_parity_random_population(ctx):
     pr = inputs.make_problem("pp", 5, P=300, Lmin=1, Lmax=60, nvars=4, K=4, N=1001, xlo=-3,
                              xhi=3, target_len=(5, 9))
-    assert predict_parity(ctx, pr.programs, pr.lengths, pr.consts, pr.X, pr.N) > 250
+    assert predict_parity(ctx, pr.programs, pr.lengths, pr.consts, pr.X, pr.N) > 0.8 * 300 * 1001
 
 
 def test_invalid_programs_flagged_bit_exact(ctx):
@@ -138,9 +134,9 @@ def test_fitness_parity_plain(ctx, kind):
     f = binding.sr_eval(ctx, d["programs"], d["lengths"], d["consts"], d["X"], d["y"], pr.N, kind)
     torch.cuda.synchronize()
     f = f.cpu().numpy()
-    sens, cfl, f0 = oracle.condition(pr.programs, pr.lengths, pr.consts, pr.X, y, kind, pr.N)
-    assert check_fitness(kind, f, f0, sens, cfl, y) > 0.8 * pr.P
-    tol = 1e-4 * np.abs(f0) + fitness_floor(kind, y) + 16 * sens
+    errb, cfl, f0 = oracle.condition(pr.programs, pr.lengths, pr.consts, pr.X, y, kind, pr.N)
+    assert check_fitness(kind, f, f0, errb, cfl, y) > 0.6 * pr.P
+    tol = 1e-4 * np.abs(f0) + fitness_floor(kind, y) + 2 * errb
     assert top_fraction_agree(f, f0, tol)
 
 
@@ -155,11 +151,11 @@ def test_fitness_parity_sizes(ctx, N):
         f = binding.sr_eval(ctx, d["programs"], d["lengths"], d["consts"], d["X"], d["y"], N, kind)
         torch.cuda.synchronize()
         f = f.cpu().numpy()
-        sens, cfl, f0 = oracle.condition(pr.programs, pr.lengths, pr.consts, pr.X, y, kind, N)
+        errb, cfl, f0 = oracle.condition(pr.programs, pr.lengths, pr.consts, pr.X, y, kind, N)
         if N < 2 and kind == oracle.CORR:
             assert (f[np.isfinite(f0)] == 1.0).all()
             continue
-        check_fitness(kind, f, f0, sens, cfl, y)
+        check_fitness(kind, f, f0, errb, cfl, y)
 
 
 def test_both_kinds_in_one_pass_match_separate_calls(ctx):
@@ -183,7 +179,7 @@ def test_deep_and_long_programs(ctx):
     X = inputs.random_X(np.random.default_rng(3), 3, 700, 0.98, 1.02)
     fl, md = oracle.validate_all(progs, lens, 3, 0)
     assert (fl == 0).all() and md[0] == 256 and md[2] == 30
-    assert predict_parity(ctx, progs, lens, np.zeros((3, 0), np.float32), X, 700) == 3
+    assert predict_parity(ctx, progs, lens, np.zeros((3, 0), np.float32), X, 700) == 3 * 700
 
 
 def test_constant_and_single_token_programs(ctx):
@@ -233,15 +229,15 @@ def test_argument_errors(ctx):
 
 def test_full_size_paper_shaped_sampled(ctx):
     """4,096 programs x 100,000 cases (the bench workload and launch
-    configuration); the oracle checks 48 sampled programs on every case."""
+    configuration); the oracle checks 96 sampled programs on every case."""
     pr, y = target_problem(inputs.paper_shaped)
     d = dev(pr, y)
     f = binding.sr_eval(ctx, d["programs"], d["lengths"], d["consts"], d["X"], d["y"], pr.N,
                         binding.SR_MSE_CORR)
     torch.cuda.synchronize()
     f = f.cpu().numpy()
-    idx = np.random.default_rng(0).choice(pr.P, 48, replace=False)
+    idx = np.random.default_rng(0).choice(pr.P, 96, replace=False)
     for row, kind in ((0, oracle.MSE), (1, oracle.CORR)):
-        sens, cfl, f0 = oracle.condition(pr.programs[idx], pr.lengths[idx], pr.consts[idx], pr.X, y,
-                                         kind, pr.N, trials=2)
-        assert check_fitness(kind, f[row, idx], f0, sens, cfl, y) > 24
+        errb, cfl, f0 = oracle.condition(pr.programs[idx], pr.lengths[idx], pr.consts[idx], pr.X, y,
+                                         kind, pr.N)
+        assert check_fitness(kind, f[row, idx], f0, errb, cfl, y) >= 12

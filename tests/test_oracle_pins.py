@@ -214,19 +214,93 @@ def test_nonfinite_output_scores_worst():
 
 
 # ---------------------------------------------------------------- conditioning
-def test_conditioning_separates_good_from_bad():
+def test_interval_hand_values():
+    """Interval enclosure of the FP32 output: inputs exact, each operator's
+    exact range over its operand intervals widened by u |v| + 2^-149."""
+    u, s = oracle.U_FP32, 2.0 ** -149
+    w = lambda lo, hi: (lo - u * abs(lo) - s, hi + u * abs(hi) + s)
+    a, b, c = 1.7, 2.9, -0.4
+    x = np.array([[a], [b], [c], [math.pi / 2], [1e-3]])
+    P = w(a * b, a * b)                              # x0 x1 *
+    S = w(math.sin(P[0]), math.sin(P[1]))            # sin is increasing at 4.93
+    cases = [("x0", (a, a)),
+             ("x0 x1 *", P),
+             ("x0 x1 * x2 +", w(P[0] + c, P[1] + c)),
+             ("x0 x1 * sin", S),
+             ("x2 sq", w(c * c, c * c)),
+             ("x0 x4 /", w(1.0, 1.0)),                 # |divisor| <= 1e-3: protected
+             ("x3 sin", w(1.0, 1.0))]
+    for text, (lo, hi) in cases:
+        y, l, h, cf = oracle.predict_interval(parse(text), [], x, 1)
+        assert cf[0] == 0
+        assert l[0] == pytest.approx(lo, rel=1e-15) and h[0] == pytest.approx(hi, rel=1e-15), text
+    # an interval that straddles pi/2: the maximum 1 is attained inside
+    Q = w(math.pi / 2, math.pi / 2)                  # x3 c0 *  with c0 = 1 (exact)
+    y, l, h, cf = oracle.predict_interval(parse("x3 c0 * sin"), [1.0], x, 1)
+    assert h[0] == pytest.approx(1.0 + u + s, rel=1e-15)
+    assert l[0] == pytest.approx(min(math.sin(Q[0]), math.sin(Q[1])) * (1 - u), rel=1e-12)
+    # protected division whose divisor interval straddles the threshold 1e-3
+    y, l, h, cf = oracle.predict_interval(parse("x0 x4 c0 * /"), [1.0], x, 1)
+    assert l[0] <= 1.0 - u and h[0] == pytest.approx(a / 1e-3 * (1 + u) + s, rel=1e-12)
+
+
+def _round32_eval(tok, X, N):
+    """Every operator computed in FP64 from FP32 operands and rounded to FP32:
+    a correctly rounding FP32 machine (numpy, independent of the oracle)."""
+    f = np.float32
+    st = []
+    for t in tok:
+        t = int(t)
+        if t >= 16:
+            st.append(X[t - 16, :N].astype(np.float32))
+            continue
+        if t < 4:
+            b = st.pop().astype(np.float64)
+            a = st.pop().astype(np.float64)
+            r = [a + b, a - b, a * b, np.where(np.abs(b) <= 1e-3, 1.0, a / np.where(b == 0, 1, b))][t]
+        else:
+            x = st.pop().astype(np.float64)
+            r = [np.sin(x), np.cos(x), np.exp(np.clip(x, -80, 80)),
+                 np.where(np.abs(x) <= 1e-3, 0.0, np.log(np.maximum(np.abs(x), 1e-300))),
+                 np.sqrt(np.abs(x)), x * x][t - 4]
+        st.append(r.astype(f))
+    return st[0].astype(np.float64)
+
+
+def test_interval_contains_fp64_and_rounded_fp32():
+    """On random programs, every case's enclosure contains the FP64 value and
+    the result of a correctly rounding FP32 evaluation, and stays tight
+    (median width within a few hundred u |yhat|)."""
+    pr = inputs.make_problem("eb", 12, P=400, Lmin=1, Lmax=40, nvars=3, K=0, N=500, xlo=-4,
+                             xhi=4, target_len=(3, 5))
+    checked, rel_w = 0, []
+    for p in range(pr.P):
+        tok = pr.programs[p, : pr.lengths[p]]
+        ref, lo, hi, cf = oracle.predict_interval(tok, [], pr.X, pr.N)
+        with np.errstate(all="ignore"):
+            emu = _round32_eval(tok, pr.X, pr.N)
+        ok = cf == 0
+        assert ((lo <= ref) & (ref <= hi))[ok].all(), p
+        assert ((lo <= emu) & (emu <= hi))[ok].all(), p
+        checked += int(ok.sum())
+        nz = ok & (np.abs(ref) > 1e-30)
+        rel_w += list((hi - lo)[nz] / np.abs(ref[nz]))
+    assert checked > 0.8 * pr.P * pr.N
+    assert np.median(rel_w) < 300 * oracle.U_FP32
+
+
+def test_fitness_error_bound_flags_hopeless_programs():
     rng = np.random.default_rng(4)
     X = rng.uniform(1, 5, (2, 512)).astype(np.float32)
     y = (X[0].astype(np.float64) * 2 + X[1]).astype(np.float32)
-    progs, lens = pack([parse("x0 c0 * x1 +"),      # well conditioned, near exact (MSE tiny)
-                        parse("x0 x1 *"),           # well conditioned
-                        parse("x0 c1 * sin"),       # sin of ~1e6: ill conditioned
+    progs, lens = pack([parse("x0 x1 *"),           # well conditioned
+                        parse("x0 c1 * sin"),       # sin of ~1e6: FP32 hopeless
                         parse("x0 exp exp sq")], 8)  # exp(80)^2 is beyond FP32 range
-    consts = np.array([[2.0, 1e6]] * 4, np.float32)
-    sens, cfl, f0 = oracle.condition(progs, lens, consts, X, y, oracle.MSE)
-    assert sens[1] < 1e-5 * f0[1] and cfl[1] == 0
-    assert sens[2] > 1e-5 * f0[2]
-    assert cfl[3] & oracle.CF_RANGE
+    consts = np.array([[2.0, 1e6]] * 3, np.float32)
+    errb, cfl, f0 = oracle.condition(progs, lens, consts, X, y, oracle.MSE)
+    assert errb[0] < 1e-5 * f0[0] and cfl[0] == 0
+    assert errb[1] > 1e-2 * f0[1]
+    assert cfl[2] & oracle.CF_RANGE
 
 
 # ---------------------------------------------------------------- gradient
