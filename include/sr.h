@@ -157,6 +157,37 @@ sr_status sr_predict(sr_ctx *ctx, const uint8_t *programs,
                      int Lmax, int K, const float *X, int nvars, int N, int ldx,
                      float *yhat, int ldy, int32_t *prog_flags);
 
+/*
+ * sr_eval_noalloc -- sr_eval for callers that cannot allocate device memory.
+ * (The paper has no counterpart: this exists for embedding.)  Some host
+ * programs may not call cudaMalloc once they are running -- a serving process
+ * whose device memory is budgeted and carved up at start-up, a plug-in that
+ * lives inside another application's CUDA context, or code that must not
+ * trigger the device-wide synchronisation an allocation can cause.  This
+ * entry point needs no context and allocates nothing: it computes exactly
+ * what sr_eval computes, taking all of its scratch from one static device
+ * array of 16 MiB that the library reserves in every GPU that loads it, for
+ * the life of the process.
+ *   cuda_stream  the cudaStream_t to issue on (NULL = legacy default stream);
+ *                it must belong to the calling thread's current device
+ *   other arguments and results as for sr_eval.
+ * The first call on each device looks up the array's device address (once,
+ * with that device current); make that first call before capturing a stream
+ * into a CUDA graph.  The scratch is shared by every call on a device and
+ * keeps the previous call's contents (each call clears what it needs
+ * cleared), so calls whose work overlaps on the GPU race: issue them on one
+ * stream, or order them with events.
+ * Errors: SR_EINVAL as for sr_eval; SR_ENOMEM when the problem's scratch
+ * (partial sums per program and case chunk, the centred target for 1 - r^2,
+ * stack slots for deep programs) does not fit in 16 MiB even with the
+ * persistent grid shrunk to one SM -- use sr_eval then; SR_ECUDA.
+ */
+sr_status sr_eval_noalloc(void *cuda_stream, const uint8_t *programs,
+                          const int32_t *lengths, const float *consts, int P,
+                          int Lmax, int K, const float *X, const float *y,
+                          int nvars, int N, int ldx, sr_fitness_kind kind,
+                          double *fitness, int32_t *prog_flags);
+
 #ifdef __cplusplus
 }
 #endif

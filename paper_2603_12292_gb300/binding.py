@@ -21,7 +21,8 @@ SR_MAX_LMAX, SR_MAX_VARS, SR_MAX_CONSTS = 512, 16, 16
 
 # exported names declared by include/sr.h (checked by the tests)
 EXPORTS = ["sr_create", "sr_destroy", "sr_set_stream", "sr_status_string", "sr_last_error",
-           "sr_reserve", "sr_sync", "sr_eval", "sr_predict", "sr_kernel_launches"]
+           "sr_reserve", "sr_sync", "sr_eval", "sr_predict", "sr_kernel_launches",
+           "sr_eval_noalloc"]
 
 _lib = None
 
@@ -54,6 +55,7 @@ def lib() -> ctypes.CDLL:
     L.sr_kernel_launches.restype = u64
     L.sr_eval.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp, vp, i32, i32, i32, i32, vp, vp]
     L.sr_predict.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp, i32, i32, i32, vp, i32, vp]
+    L.sr_eval_noalloc.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp, vp, i32, i32, i32, i32, vp, vp]
     for name in EXPORTS:
         if name not in ("sr_status_string", "sr_last_error", "sr_kernel_launches"):
             getattr(L, name).restype = i32
@@ -166,3 +168,26 @@ def sr_predict(ctx: Context, programs, lengths, consts, X, N: int,
                                  P, Lmax, K, _ptr(X), nvars, N, ldx, _ptr(yhat), yhat.shape[1],
                                  _ptr(prog_flags)))
     return yhat
+
+
+def sr_eval_noalloc(programs, lengths, consts, X, y, N: int, kind: int, fitness: torch.Tensor,
+                    prog_flags: torch.Tensor | None = None, stream: torch.cuda.Stream | None = None):
+    """sr_eval without a context and without any device allocation (scratch
+    comes from the library's static 16 MiB array).  Returns the status code;
+    fitness must be preallocated (float64 [P], or [2, P] for SR_MSE_CORR)."""
+    _dev(programs, torch.uint8, "programs")
+    _dev(lengths, torch.int32, "lengths")
+    _dev(X, torch.float32, "X")
+    _dev(y, torch.float32, "y")
+    _dev(fitness, torch.float64, "fitness")
+    P, Lmax = programs.shape
+    K = 0 if consts is None else (consts.shape[1] if consts.dim() == 2 else 0)
+    if consts is not None and K > 0:
+        _dev(consts, torch.float32, "consts")
+    if prog_flags is not None:
+        _dev(prog_flags, torch.int32, "prog_flags")
+    nvars, ldx = X.shape
+    s = (stream or torch.cuda.current_stream(programs.device)).cuda_stream
+    return int(lib().sr_eval_noalloc(ctypes.c_void_p(s), _ptr(programs), _ptr(lengths),
+                                     _ptr(consts) if K else None, P, Lmax, K, _ptr(X), _ptr(y),
+                                     nvars, N, ldx, kind, _ptr(fitness), _ptr(prog_flags)))

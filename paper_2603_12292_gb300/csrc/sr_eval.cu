@@ -662,3 +662,84 @@ sr_status sr_reserve(sr_ctx *ctx, int P, int Lmax, int N) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- allocation-free evaluation
+// sr_eval_noalloc: the same kernels as sr_eval, with every byte of scratch
+// taken from one file-scope device array instead of a context workspace.
+#include <mutex>
+
+namespace sr {
+namespace {
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)16 << 20;  // 16 MiB, held per device until exit
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+__device__ __align__(256) char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_noalloc_mutex;
+void *g_noalloc_addr[NOALLOC_MAX_DEVICES];  // device address of the array, per device
+
+// Looks up the device address of the scratch array on the current device
+// (once per device; the host-side symbol is not a device address).
+sr_status noalloc_scratch(int dev, void **out) {
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return SR_EINVAL;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return SR_ECUDA;
+    }
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return SR_OK;
+}
+
+}  // namespace
+}  // namespace sr
+
+extern "C" sr_status sr_eval_noalloc(void *cuda_stream, const uint8_t *programs,
+                                     const int32_t *lengths, const float *consts, int P, int Lmax,
+                                     int K, const float *X, const float *y, int nvars, int N,
+                                     int ldx, sr_fitness_kind kind, double *fitness,
+                                     int32_t *prog_flags) {
+  using namespace sr;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return SR_ECUDA;
+  }
+  // a context on the stack: nothing is allocated for it, and its workspace
+  // is the static array, so the workspace never needs to grow
+  sr_ctx local;
+  local.device = dev;
+  local.stream = (cudaStream_t)cuda_stream;
+  if (cudaDeviceGetAttribute(&local.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return SR_ECUDA;
+  }
+  sr_status st = check_common(&local, programs, lengths, consts, P, Lmax, K, X, nvars, N, ldx);
+  if (st != SR_OK) return st;
+  if (kind != SR_MSE && kind != SR_CORR && kind != SR_MSE_CORR) return SR_EINVAL;
+  if (P == 0) return SR_OK;
+  if (!y || !fitness || (((uintptr_t)y) & 15)) return SR_EINVAL;
+  const int mode = kind == SR_MSE ? MODE_MSE : (kind == SR_CORR ? MODE_CORR : MODE_BOTH);
+  // fit the plan into the array: fewer SMs' worth of persistent CTAs means
+  // fewer per-warp stacks and partial records
+  Plan pl;
+  for (;;) {
+    st = make_plan(&local, mode, P, Lmax, N, &pl);
+    if (st != SR_OK) return st;
+    if (pl.bytes <= NOALLOC_SCRATCH_BYTES) break;
+    if (local.num_sms == 1) return SR_ENOMEM;  // does not fit even on one SM
+    local.num_sms = local.num_sms / 2 > 0 ? local.num_sms / 2 : 1;
+  }
+  void *scratch = nullptr;
+  st = noalloc_scratch(dev, &scratch);
+  if (st != SR_OK) return st;
+  local.ws = static_cast<char *>(scratch);
+  local.ws_bytes = NOALLOC_SCRATCH_BYTES;
+  return launch_eval(&local, mode, programs, lengths, consts, P, Lmax, K, X, y, nvars, N, ldx,
+                     fitness, prog_flags, nullptr, 0);
+}
