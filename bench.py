@@ -6,8 +6,8 @@ Workload (default): the paper-shaped single problem -- 4,096 postfix programs
 of length 8..128 over 10 variables, 100,000 fitness cases X ~ U(1, 10), target
 from a random program plus 1% Gaussian noise.  One step = one generation of
 the device-resident hot path: both fitness kinds (MSE and 1 - r^2) from one
-interpreter pass, then (when available in the library) tournament selection
-and variation.
+interpreter pass, a 4-way tournament on 1 - r^2, then crossover and mutation
+into the second population buffer.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -110,12 +110,6 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None}
 
 
-def make_workload():
-    """The paper-shaped problem with a finite, non-constant target."""
-    from paper_2603_12292_gb300 import inputs
-    return inputs.paper_shaped
-
-
 # ------------------------------------------------------------------ reference arm (the oracle)
 def run_reference(args, rank, world):
     import oracle
@@ -185,13 +179,33 @@ def run_ours(args, rank, world, local_rank):
                                           yhat[0].double().cpu().numpy(), pr.noise)).to(dev)
     binding.sr_reserve(ctx, pr.P, pr.Lmax, pr.N)
     fitness = torch.empty((2, pr.P), dtype=torch.float64, device=dev)
+    parents = torch.empty((pr.P, 2), dtype=torch.int32, device=dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    cfg = binding.var_cfg()  # p_cross 0.9, p_point 0.1, p_subtree 0.05, p_const 0.1
+    pop = [(programs, lengths, consts),
+           (torch.empty_like(programs), torch.empty_like(lengths), torch.empty_like(consts))]
+    SEED, K_TOURN = 20260312, 4
+    state = {"gen": 0, "cur": 0}
+    ev_eval = []
 
-    def step():
-        binding.sr_eval(ctx, programs, lengths, consts, X, y, pr.N, binding.SR_MSE_CORR, fitness=fitness)
+    def generation(record_eval=False):
+        """One generation: both fitness kinds from one pass, tournament on 1 - r^2, variation."""
+        g, cur = state["gen"], state["cur"]
+        P_, L_, C_ = pop[cur]
+        if record_eval:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        binding.sr_eval(ctx, P_, L_, C_, X, y, pr.N, binding.SR_MSE_CORR, fitness=fitness)
+        if record_eval:
+            e1.record(stream)
+            ev_eval.append((e0, e1))
+        binding.sr_select_tournament(ctx, fitness[1], K_TOURN, SEED, g, parents=parents)
+        binding.sr_vary(ctx, P_, L_, C_, parents, pr.nvars, cfg, SEED, g, out=pop[1 - cur])
+        state["gen"], state["cur"] = g + 1, 1 - cur
+        return L_
 
     for _ in range(args.warmup):
-        step()
+        generation()
     torch.cuda.synchronize()
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -206,15 +220,16 @@ def run_ours(args, rank, world, local_rank):
     for i in range(args.steps):
         flush.zero_()  # L2 flush between timed steps (outside the events)
         ev[i][0].record(stream)
-        step()
+        lens_evaluated = generation(record_eval=True)
         ev[i][1].record(stream)
-        nodes.append(int(pr.lengths.astype(np.int64).sum()))
+        nodes.append(int(lens_evaluated.sum().item()))  # outside the events
     torch.cuda.synchronize()
     launches = binding.sr_kernel_launches(ctx) - launches0
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
+    eval_ms = [a.elapsed_time(b) for a, b in ev_eval]
     total_ms = float(sum(step_ms))
     if world > 1:
         tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
@@ -223,46 +238,61 @@ def run_ours(args, rank, world, local_rank):
     units = float(sum(nodes)) * pr.N * world
     value = units / (total_ms / 1e3) / 1e9
 
-    # roofline of the dominant kernel: FP32 issue bound, one lane-op per node-case
+    # roofline of the dominant kernel (the evaluation call, timed by its own
+    # events inside the timed region): FP32 issue bound, one lane-op per node-case
     pk, src = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = sms * 128 * sm_max * 1e6 / 1e9  # G lane-ops/s
-    per_launch_units = float(nodes[0]) * pr.N
-    achieved = per_launch_units / (statistics.mean(step_ms) / 1e3) / 1e9
+    achieved = float(np.mean([n * pr.N / (ms / 1e3) / 1e9 for n, ms in zip(nodes, eval_ms)]))
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GPop/s",
                 "frac": achieved / peak, "traffic": None,
+                "kernel": "eval_kernel (sr_eval SR_MSE_CORR)",
+                "eval_ms": float(np.mean(eval_ms)),
                 "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz ({src} max clock)"}
 
-    # end to end through the public API: H2D population, evaluate, D2H fitness
-    h_prog = torch.from_numpy(pr.programs).pin_memory()
-    h_len = torch.from_numpy(pr.lengths).pin_memory()
-    h_con = torch.from_numpy(pr.consts).pin_memory()
+    # end to end through the public API with the population held on the host:
+    # H2D population, evaluate + select + vary, D2H children and fitness
+    P_, L_, C_ = pop[state["cur"]]
+    h_prog = P_.cpu().pin_memory()
+    h_len = L_.cpu().pin_memory()
+    h_con = C_.cpu().pin_memory()
     h_fit = torch.empty((2, pr.P), dtype=torch.float64).pin_memory()
-    d_prog, d_len, d_con = torch.empty_like(programs), torch.empty_like(lengths), torch.empty_like(consts)
+    d_in = (torch.empty_like(programs), torch.empty_like(lengths), torch.empty_like(consts))
+    d_out = (torch.empty_like(programs), torch.empty_like(lengths), torch.empty_like(consts))
     h2d = h_prog.numel() + h_len.numel() * 4 + h_con.numel() * 4
-    d2h = h_fit.numel() * 8
+    d2h = h2d + h_fit.numel() * 8
+    e2e_nodes = []
 
-    def e2e_step():
-        d_prog.copy_(h_prog, non_blocking=True)
-        d_len.copy_(h_len, non_blocking=True)
-        d_con.copy_(h_con, non_blocking=True)
-        binding.sr_eval(ctx, d_prog, d_len, d_con, X, y, pr.N, binding.SR_MSE_CORR, fitness=fitness)
+    def e2e_step(g):
+        d_in[0].copy_(h_prog, non_blocking=True)
+        d_in[1].copy_(h_len, non_blocking=True)
+        d_in[2].copy_(h_con, non_blocking=True)
+        binding.sr_eval(ctx, d_in[0], d_in[1], d_in[2], X, y, pr.N, binding.SR_MSE_CORR, fitness=fitness)
+        binding.sr_select_tournament(ctx, fitness[1], K_TOURN, SEED, g, parents=parents)
+        binding.sr_vary(ctx, d_in[0], d_in[1], d_in[2], parents, pr.nvars, cfg, SEED, g, out=d_out)
+        h_prog.copy_(d_out[0], non_blocking=True)
+        h_len.copy_(d_out[1], non_blocking=True)
+        h_con.copy_(d_out[2], non_blocking=True)
         h_fit.copy_(fitness, non_blocking=True)
 
     for _ in range(2):
-        e2e_step()
+        e2e_step(state["gen"])
+        state["gen"] += 1
     torch.cuda.synchronize()
     e2e_ms = []
     for _ in range(max(3, args.steps // 2)):
+        n_in = int(h_len.sum())
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        e2e_step()
+        e2e_step(state["gen"])
         b.record(stream)
         b.synchronize()
+        state["gen"] += 1
         e2e_ms.append(a.elapsed_time(b))
-    e2e_val = float(nodes[0]) * pr.N / (statistics.mean(e2e_ms) / 1e3) / 1e9 * world
+        e2e_nodes.append(n_in)
+    e2e_val = float(sum(e2e_nodes)) * pr.N / (float(sum(e2e_ms)) / 1e3) / 1e9 * world
 
     line = {"metric": METRIC, "value": value, "unit": "GPop/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -270,7 +300,9 @@ def run_ours(args, rank, world, local_rank):
             "data": "synthetic",
             "config": {"workload": pr.name, "programs": pr.P, "cases": pr.N, "vars": pr.nvars,
                        "lengths": "8-128", "fitness": "MSE and 1-r^2 from one pass",
-                       "step": "sr_eval(SR_MSE_CORR)", "l2": "flushed between timed steps",
+                       "step": "one generation: sr_eval(SR_MSE_CORR) + sr_select_tournament(k=4, on 1-r^2)"
+                               " + sr_vary(p_cross 0.9, p_point 0.1, p_subtree 0.05, p_const 0.1)",
+                       "l2": "flushed between timed steps",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "clocks": clocks,
             "e2e": {"value": e2e_val, "unit": "GPop/s", "h2d_bytes_per_step": int(h2d),

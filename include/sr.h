@@ -157,6 +157,102 @@ sr_status sr_predict(sr_ctx *ctx, const uint8_t *programs,
                      int Lmax, int K, const float *X, int nvars, int N, int ldx,
                      float *yhat, int ldy, int32_t *prog_flags);
 
+/* ------------------------------------------------------------------------
+ * Selection and variation on the device (the paper does selection, births
+ * and mutation on the CPU, Sec. 2.1.2, with no crossover; this library keeps
+ * the whole generation on the GPU and adds subtree crossover).
+ *
+ * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key =
+ * (seed low 32 bits, seed high 32 bits), counter = (draw, individual,
+ * purpose, generation low 32 bits).  A word w maps to [0, n) as
+ * floor(w * n / 2^32) (multiply-high, Lemire 2019) and to [0, 1) as
+ * (w >> 8) * 2^-24.  Purposes: 1 tournament for parent A, 2 for parent B,
+ * 3 variation decisions, 4 crossover points, 5 point mutation, 6 subtree
+ * mutation, 7 generated subtree tokens, 8 constant mutation, 9 random
+ * program tokens, 10 random program constants.  Every value below is a pure
+ * function of (seed, generation, inputs): results are bit-identical to a CPU
+ * implementation of the same rules.
+ * ---------------------------------------------------------------------- */
+
+/* Philox4x32-10 on n counters: out[i] = Philox(ctr[i], key).  Device
+ * arrays of n x 4 words. */
+sr_status sr_philox4x32_10(sr_ctx *ctx, const uint32_t *ctr, uint32_t key0,
+                           uint32_t key1, uint32_t *out, int n);
+
+/*
+ * sr_select_tournament -- k-way tournament with replacement.  Child slot i
+ * (0 <= i < P) gets parents[2i] (purpose 1) and parents[2i+1] (purpose 2):
+ * candidate j (0 <= j < k) is word j%4 of Philox(j/4, i, purpose, gen)
+ * mapped to [0, P); the smallest fitness wins, NaN counting as +inf and
+ * equal fitness going to the smaller index.
+ *   fitness  device double [P];  parents  device int32 [P][2], written
+ *   1 <= k <= 64.   Errors: SR_EINVAL.
+ */
+sr_status sr_select_tournament(sr_ctx *ctx, const double *fitness, int P, int k,
+                               uint64_t seed, uint64_t gen, int32_t *parents);
+
+/* Variation parameters (probabilities in [0, 1], FP32). */
+typedef struct {
+  float p_cross;    /* subtree crossover (else the child starts as parent A) */
+  float p_point;    /* point mutation: one token -> another of its arity     */
+  float p_subtree;  /* subtree mutation: one subtree -> a random program     */
+  float p_const;    /* constant mutation: c_k += (u - 1/2) * const_delta     */
+  float const_delta;
+  int max_subtree;  /* generated subtrees have 1..max_subtree tokens         */
+} sr_var_cfg;
+
+/*
+ * sr_vary -- one child per slot i from A = parents[2i], B = parents[2i+1].
+ * Decisions: u_cross, u_point, u_sub, u_const = the four words of
+ * Philox(0, i, 3, gen) in [0, 1).
+ *  1. crossover when u_cross < p_cross: words 0 and 1 of Philox(0, i, 4, gen)
+ *     pick node a in [0, lenA) and b in [0, lenB); with [sa, a] and [sb, b]
+ *     the subtrees rooted there (the shortest suffix ending at the node
+ *     whose stack effect is +1), the child is A[0,sa) ++ B[sb,b] ++ A(a,lenA)
+ *     unless that exceeds Lmax (then the child is A).  Constants start as
+ *     A's; slot k takes B's value when k is read inside the inserted B
+ *     subtree and nowhere in the kept parts of A.  Otherwise child = A.
+ *  2. point mutation when u_point < p_point: Philox(0, i, 5, gen): position
+ *     [0, len); binary -> [0,4), unary -> 4 + [0,6), terminal -> [0, nvars+K)
+ *     (variables first, then constants).
+ *  3. subtree mutation when u_sub < p_subtree: Philox(0, i, 6, gen): position
+ *     t in [0, len), size n = 1 + [0, max_subtree); the subtree rooted at t
+ *     becomes a random program of n tokens whose token q uses
+ *     Philox(q, i, 7, gen) (word 0 picks the class among those allowed --
+ *     terminal if d <= r-1, unary if 1 <= d <= r, binary if 2 <= d <= r+1,
+ *     for depth d and r tokens left -- word 1 the token in the class); skipped
+ *     when the result would exceed Lmax.
+ *  4. constant mutation when u_const < p_const and K > 0: Philox(0, i, 8,
+ *     gen): slot [0, K), u = word 1 in [0, 1);
+ *     c = fl32(c + fl32(fl32(u - 0.5) * const_delta)).
+ * Children of valid parents are valid.  Bytes past each child's length are
+ * zero.  Parent indices outside [0, P) and lengths outside [1, Lmax] are
+ * clamped into range (never read out of bounds).
+ *   prog_in/len_in/c_in  device, the parent population ([P][Lmax], [P], [P][K])
+ *   parents              device int32 [P][2], each in [0, P)
+ *   prog_out/len_out/c_out device, the children (must not alias the inputs)
+ * Errors: SR_EINVAL.
+ */
+sr_status sr_vary(sr_ctx *ctx, const uint8_t *prog_in, const int32_t *len_in,
+                  const float *c_in, const int32_t *parents, uint8_t *prog_out,
+                  int32_t *len_out, float *c_out, int P, int Lmax, int K,
+                  int nvars, const sr_var_cfg *cfg, uint64_t seed,
+                  uint64_t gen);
+
+/*
+ * sr_random_programs -- a random valid population: program i has length
+ * Lmin + [0, Lmax - Lmin] from word 0 of Philox(0, i, 9, stream), token t from
+ * Philox(1 + t, i, 9, stream) (same token rule as generated subtrees), and
+ * constant k = fl32(cmin + fl32(u * fl32(cmax - cmin))) with u from word 0 of
+ * Philox(k, i, 10, stream).  Rows are zero past their length.
+ *   prog device uint8 [P][Lmax], len device int32 [P], c device float [P][K]
+ *   1 <= Lmin <= Lmax <= SR_MAX_LMAX.   Errors: SR_EINVAL.
+ */
+sr_status sr_random_programs(sr_ctx *ctx, uint8_t *prog, int32_t *len, float *c,
+                             int P, int Lmin, int Lmax, int K, int nvars,
+                             float cmin, float cmax, uint64_t seed,
+                             uint64_t stream);
+
 /*
  * sr_eval_noalloc -- sr_eval for callers that cannot allocate device memory.
  * (The paper has no counterpart: this exists for embedding.)  Some host

@@ -22,9 +22,21 @@ SR_MAX_LMAX, SR_MAX_VARS, SR_MAX_CONSTS = 512, 16, 16
 # exported names declared by include/sr.h (checked by the tests)
 EXPORTS = ["sr_create", "sr_destroy", "sr_set_stream", "sr_status_string", "sr_last_error",
            "sr_reserve", "sr_sync", "sr_eval", "sr_predict", "sr_kernel_launches",
-           "sr_eval_noalloc"]
+           "sr_eval_noalloc", "sr_philox4x32_10", "sr_select_tournament", "sr_vary",
+           "sr_random_programs"]
 
 _lib = None
+
+
+class VarCfg(ctypes.Structure):
+    """sr_var_cfg (include/sr.h)."""
+    _fields_ = [("p_cross", ctypes.c_float), ("p_point", ctypes.c_float),
+                ("p_subtree", ctypes.c_float), ("p_const", ctypes.c_float),
+                ("const_delta", ctypes.c_float), ("max_subtree", ctypes.c_int)]
+
+
+def var_cfg(p_cross=0.9, p_point=0.1, p_subtree=0.05, p_const=0.1, const_delta=1.0, max_subtree=8):
+    return VarCfg(p_cross, p_point, p_subtree, p_const, const_delta, max_subtree)
 
 
 class SRError(RuntimeError):
@@ -55,6 +67,11 @@ def lib() -> ctypes.CDLL:
     L.sr_kernel_launches.restype = u64
     L.sr_eval.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp, vp, i32, i32, i32, i32, vp, vp]
     L.sr_predict.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp, i32, i32, i32, vp, i32, vp]
+    L.sr_philox4x32_10.argtypes = [vp, vp, ctypes.c_uint32, ctypes.c_uint32, vp, i32]
+    L.sr_select_tournament.argtypes = [vp, vp, i32, i32, u64, u64, vp]
+    L.sr_vary.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, ctypes.POINTER(VarCfg),
+                          u64, u64]
+    L.sr_random_programs.argtypes = [vp, vp, vp, vp, i32, i32, i32, i32, i32, f32, f32, u64, u64]
     L.sr_eval_noalloc.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp, vp, i32, i32, i32, i32, vp, vp]
     for name in EXPORTS:
         if name not in ("sr_status_string", "sr_last_error", "sr_kernel_launches"):
@@ -191,3 +208,54 @@ def sr_eval_noalloc(programs, lengths, consts, X, y, N: int, kind: int, fitness:
     return int(lib().sr_eval_noalloc(ctypes.c_void_p(s), _ptr(programs), _ptr(lengths),
                                      _ptr(consts) if K else None, P, Lmax, K, _ptr(X), _ptr(y),
                                      nvars, N, ldx, kind, _ptr(fitness), _ptr(prog_flags)))
+
+
+def sr_philox4x32_10(ctx: Context, ctr: torch.Tensor, key0: int, key1: int) -> torch.Tensor:
+    """Philox4x32-10 of n counters (int32 tensor [n, 4] holding uint32 bits)."""
+    _dev(ctr, torch.int32, "ctr")
+    out = torch.empty_like(ctr)
+    _check(ctx, lib().sr_philox4x32_10(ctx.handle, _ptr(ctr), key0, key1, _ptr(out), ctr.shape[0]))
+    return out
+
+
+def sr_select_tournament(ctx: Context, fitness, k: int, seed: int, gen: int,
+                         parents: torch.Tensor | None = None) -> torch.Tensor:
+    _dev(fitness, torch.float64, "fitness")
+    P = fitness.shape[0]
+    if parents is None:
+        parents = torch.empty((P, 2), dtype=torch.int32, device=fitness.device)
+    _dev(parents, torch.int32, "parents")
+    _check(ctx, lib().sr_select_tournament(ctx.handle, _ptr(fitness), P, k, seed, gen, _ptr(parents)))
+    return parents
+
+
+def sr_vary(ctx: Context, programs, lengths, consts, parents, nvars: int, cfg: VarCfg, seed: int,
+            gen: int, out=None):
+    """Children of the parent pairs; returns (programs, lengths, consts)."""
+    _dev(programs, torch.uint8, "programs")
+    _dev(lengths, torch.int32, "lengths")
+    _dev(parents, torch.int32, "parents")
+    P, Lmax = programs.shape
+    K = consts.shape[1] if consts is not None and consts.dim() == 2 else 0
+    if K:
+        _dev(consts, torch.float32, "consts")
+    if out is None:
+        out = (torch.empty_like(programs), torch.empty_like(lengths),
+               torch.empty_like(consts) if K else None)
+    po, lo, co = out
+    _check(ctx, lib().sr_vary(ctx.handle, _ptr(programs), _ptr(lengths), _ptr(consts) if K else None,
+                              _ptr(parents), _ptr(po), _ptr(lo), _ptr(co) if K else None, P, Lmax, K,
+                              nvars, ctypes.byref(cfg), seed, gen))
+    return po, lo, co
+
+
+def sr_random_programs(ctx: Context, P: int, Lmin: int, Lmax: int, K: int, nvars: int, cmin: float,
+                       cmax: float, seed: int, stream: int, device="cuda", out=None):
+    if out is None:
+        out = (torch.empty((P, Lmax), dtype=torch.uint8, device=device),
+               torch.empty(P, dtype=torch.int32, device=device),
+               torch.empty((P, K), dtype=torch.float32, device=device))
+    prog, lens, c = out
+    _check(ctx, lib().sr_random_programs(ctx.handle, _ptr(prog), _ptr(lens), _ptr(c) if K else None, P,
+                                         Lmin, Lmax, K, nvars, cmin, cmax, seed, stream))
+    return prog, lens, c

@@ -1,0 +1,342 @@
+// sr_evolve.cu -- selection and variation on the device: Philox4x32-10,
+// k-way tournament, subtree crossover, point / subtree / constant mutation
+// and random valid programs.  The paper runs selection, births and mutation
+// on the CPU and only evaluation on the GPU (Sec. 2.1.2); here the whole
+// generation stays resident.  Every child is a pure function of (seed,
+// generation, inputs), so a CPU implementation of the same rules (the
+// specification in sr.h) reproduces it bit for bit.
+#include <math.h>
+
+#include "sr_common.cuh"
+
+namespace sr {
+namespace {
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, "Parallel Random Numbers: As Easy as 1, 2, 3"
+// (SC'11): ten rounds of two 32x32 multiplies with a Weyl-sequence key.
+struct Word4 {
+  uint32_t v[4];
+};
+
+__device__ __forceinline__ Word4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                        uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t m0 = 0xD2511F53u * c0, h0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t m1 = 0xCD9E8D57u * c2, h1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = h1 ^ c1 ^ k0, n2 = h0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = m1;
+    c2 = n2;
+    c3 = m0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  Word4 w;
+  w.v[0] = c0;
+  w.v[1] = c1;
+  w.v[2] = c2;
+  w.v[3] = c3;
+  return w;
+}
+
+struct Rng {
+  uint32_t k0, k1, gen;
+  __device__ __forceinline__ Word4 draw(uint32_t d, uint32_t indiv, uint32_t purpose) const {
+    return philox(d, indiv, purpose, gen, k0, k1);
+  }
+};
+
+inline Rng make_rng(uint64_t seed, uint64_t gen) {
+  Rng r;
+  r.k0 = (uint32_t)seed;
+  r.k1 = (uint32_t)(seed >> 32);
+  r.gen = (uint32_t)gen;
+  return r;
+}
+
+// [0, n) by multiply-high (Lemire 2019); [0, 1) from the top 24 bits
+__device__ __forceinline__ uint32_t below(uint32_t w, uint32_t n) { return __umulhi(w, n); }
+__device__ __forceinline__ float unit24(uint32_t w) {
+  return __fmul_rn((float)(w >> 8), 5.9604644775390625e-8f);  // 2^-24, exact
+}
+
+constexpr uint32_t PU_TOURN_A = 1, PU_TOURN_B = 2, PU_DECIDE = 3, PU_CROSS = 4, PU_POINT = 5,
+                   PU_SUBTREE = 6, PU_SUBGEN = 7, PU_CONSTMUT = 8, PU_INIT = 9, PU_INITC = 10;
+
+__device__ __forceinline__ int effect(int v) { return cls_effect(tok_class(v)); }
+
+// token with depth d before it and r tokens left (this one included):
+// terminal if d <= r-1, unary if 1 <= d <= r, binary if 2 <= d <= r+1
+__device__ __forceinline__ int gen_token(int d, int r, int nvars, int K, uint32_t w0, uint32_t w1) {
+  int allowed[3];
+  int na = 0;
+  if (d <= r - 1) allowed[na++] = 0;
+  if (d >= 1 && d <= r) allowed[na++] = 1;
+  if (d >= 2 && d <= r + 1) allowed[na++] = 2;
+  const int cls = allowed[below(w0, (uint32_t)na)];
+  if (cls == 0) {
+    const int q = (int)below(w1, (uint32_t)(nvars + K));
+    return q < nvars ? TOK_VAR0 + q : TOK_CONST0 + (q - nvars);
+  }
+  if (cls == 1) return TOK_SIN + (int)below(w1, 6u);
+  return TOK_ADD + (int)below(w1, 4u);
+}
+
+// first token of the subtree whose root is `end`
+__device__ __forceinline__ int subtree_start(const uint8_t *tok, int end) {
+  int acc = 0;
+  for (int t = end; t >= 0; --t) {
+    acc += effect(tok[t]);
+    if (acc == 1) return t;
+  }
+  return 0;
+}
+
+// ---------------------------------------------------------------- kernels
+__global__ void philox_kernel(const uint32_t *__restrict__ ctr, uint32_t k0, uint32_t k1,
+                              uint32_t *__restrict__ out, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const Word4 w = philox(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3], k0, k1);
+  for (int j = 0; j < 4; ++j) out[4 * i + j] = w.v[j];
+}
+
+__global__ void tournament_kernel(const double *__restrict__ fitness, int P, int k, Rng rng,
+                                  int32_t *__restrict__ parents) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * P) return;
+  const int i = t >> 1, s = t & 1;
+  const double INF = __longlong_as_double(0x7ff0000000000000ll);
+  int best = -1;
+  double bestf = 0.0;
+  Word4 w;
+  for (int j = 0; j < k; ++j) {
+    if ((j & 3) == 0) w = rng.draw((uint32_t)(j >> 2), (uint32_t)i, s ? PU_TOURN_B : PU_TOURN_A);
+    const int cand = (int)below(w.v[j & 3], (uint32_t)P);
+    double f = fitness[cand];
+    if (isnan(f)) f = INF;
+    if (best < 0 || f < bestf || (f == bestf && cand < best)) {
+      best = cand;
+      bestf = f;
+    }
+  }
+  parents[t] = best;
+}
+
+struct VaryParams {
+  const uint8_t *prog_in;
+  const int32_t *len_in;
+  const float *c_in;
+  const int32_t *parents;
+  uint8_t *prog_out;
+  int32_t *len_out;
+  float *c_out;
+  int P, Lmax, K, nvars;
+  sr_var_cfg cfg;
+  Rng rng;
+};
+
+__global__ void vary_kernel(VaryParams p) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= p.P) return;
+  // out-of-range parents and lengths are clamped so that no access leaves
+  // the buffers (valid inputs are unaffected)
+  const int ia = min(max(p.parents[2 * i], 0), p.P - 1);
+  const int ib = min(max(p.parents[2 * i + 1], 0), p.P - 1);
+  const uint8_t *A = p.prog_in + (size_t)ia * p.Lmax;
+  const uint8_t *B = p.prog_in + (size_t)ib * p.Lmax;
+  const int la = min(max(p.len_in[ia], 1), p.Lmax), lb = min(max(p.len_in[ib], 1), p.Lmax);
+  uint8_t *out = p.prog_out + (size_t)i * p.Lmax;
+  float c[TOK_NSLOTS];
+  for (int k = 0; k < p.K; ++k) c[k] = p.c_in[(size_t)ia * p.K + k];
+
+  const Word4 dw = p.rng.draw(0, (uint32_t)i, PU_DECIDE);
+  const float u_cross = unit24(dw.v[0]), u_point = unit24(dw.v[1]);
+  const float u_sub = unit24(dw.v[2]), u_const = unit24(dw.v[3]);
+
+  int len = la;
+  bool crossed = false;
+  if (u_cross < p.cfg.p_cross) {
+    const Word4 w = p.rng.draw(0, (uint32_t)i, PU_CROSS);
+    const int a = (int)below(w.v[0], (uint32_t)la);
+    const int b = (int)below(w.v[1], (uint32_t)lb);
+    const int sa = subtree_start(A, a), sb = subtree_start(B, b);
+    const int nl = la - (a - sa + 1) + (b - sb + 1);
+    if (nl <= p.Lmax) {
+      int q = 0;
+      uint32_t usedA = 0, usedB = 0;
+      for (int t = 0; t < sa; ++t) {
+        const int v = A[t];
+        out[q++] = (uint8_t)v;
+        if (tok_class(v) == CLS_CONST) usedA |= 1u << (v - TOK_CONST0);
+      }
+      for (int t = sb; t <= b; ++t) {
+        const int v = B[t];
+        out[q++] = (uint8_t)v;
+        if (tok_class(v) == CLS_CONST) usedB |= 1u << (v - TOK_CONST0);
+      }
+      for (int t = a + 1; t < la; ++t) {
+        const int v = A[t];
+        out[q++] = (uint8_t)v;
+        if (tok_class(v) == CLS_CONST) usedA |= 1u << (v - TOK_CONST0);
+      }
+      for (int k = 0; k < p.K; ++k)
+        if (((usedB >> k) & 1u) && !((usedA >> k) & 1u)) c[k] = p.c_in[(size_t)ib * p.K + k];
+      len = nl;
+      crossed = true;
+    }
+  }
+  if (!crossed)
+    for (int t = 0; t < la; ++t) out[t] = A[t];
+
+  if (u_point < p.cfg.p_point) {
+    const Word4 w = p.rng.draw(0, (uint32_t)i, PU_POINT);
+    const int t = (int)below(w.v[0], (uint32_t)len);
+    const int cls = tok_class(out[t]);
+    int v;
+    if (cls == CLS_BINARY) {
+      v = TOK_ADD + (int)below(w.v[1], 4u);
+    } else if (cls == CLS_UNARY) {
+      v = TOK_SIN + (int)below(w.v[1], 6u);
+    } else {
+      const int q = (int)below(w.v[1], (uint32_t)(p.nvars + p.K));
+      v = q < p.nvars ? TOK_VAR0 + q : TOK_CONST0 + (q - p.nvars);
+    }
+    out[t] = (uint8_t)v;
+  }
+
+  if (u_sub < p.cfg.p_subtree && p.cfg.max_subtree > 0) {
+    const Word4 w = p.rng.draw(0, (uint32_t)i, PU_SUBTREE);
+    const int t = (int)below(w.v[0], (uint32_t)len);
+    const int n = 1 + (int)below(w.v[1], (uint32_t)p.cfg.max_subtree);
+    const int s = subtree_start(out, t);
+    const int span = t - s + 1;
+    const int nl = len - span + n;
+    if (nl <= p.Lmax) {
+      // move the tail out[t+1, len) to start at s + n
+      if (n > span) {
+        for (int j = len - 1; j > t; --j) out[j + (n - span)] = out[j];
+      } else if (n < span) {
+        for (int j = t + 1; j < len; ++j) out[j - (span - n)] = out[j];
+      }
+      int d = 0;
+      for (int q = 0; q < n; ++q) {
+        const Word4 g = p.rng.draw((uint32_t)q, (uint32_t)i, PU_SUBGEN);
+        const int v = gen_token(d, n - q, p.nvars, p.K, g.v[0], g.v[1]);
+        out[s + q] = (uint8_t)v;
+        d += effect(v);
+      }
+      len = nl;
+    }
+  }
+
+  if (u_const < p.cfg.p_const && p.K > 0) {
+    const Word4 w = p.rng.draw(0, (uint32_t)i, PU_CONSTMUT);
+    const int k = (int)below(w.v[0], (uint32_t)p.K);
+    const float step = __fmul_rn(__fsub_rn(unit24(w.v[1]), 0.5f), p.cfg.const_delta);
+    c[k] = __fadd_rn(c[k], step);
+  }
+
+  for (int t = len; t < p.Lmax; ++t) out[t] = 0;
+  p.len_out[i] = len;
+  for (int k = 0; k < p.K; ++k) p.c_out[(size_t)i * p.K + k] = c[k];
+}
+
+__global__ void random_programs_kernel(uint8_t *prog, int32_t *len, float *c, int P, int Lmin,
+                                       int Lmax, int K, int nvars, float cmin, float cmax, Rng rng) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  const Word4 lw = rng.draw(0, (uint32_t)i, PU_INIT);
+  const int L = Lmin + (int)below(lw.v[0], (uint32_t)(Lmax - Lmin + 1));
+  uint8_t *out = prog + (size_t)i * Lmax;
+  int d = 0;
+  for (int t = 0; t < L; ++t) {
+    const Word4 w = rng.draw((uint32_t)(1 + t), (uint32_t)i, PU_INIT);
+    const int v = gen_token(d, L - t, nvars, K, w.v[0], w.v[1]);
+    out[t] = (uint8_t)v;
+    d += effect(v);
+  }
+  for (int t = L; t < Lmax; ++t) out[t] = 0;
+  len[i] = L;
+  const float span = __fsub_rn(cmax, cmin);
+  for (int k = 0; k < K; ++k) {
+    const Word4 w = rng.draw((uint32_t)k, (uint32_t)i, PU_INITC);
+    c[(size_t)i * K + k] = __fadd_rn(cmin, __fmul_rn(unit24(w.v[0]), span));
+  }
+}
+
+}  // namespace
+}  // namespace sr
+
+extern "C" {
+
+sr_status sr_philox4x32_10(sr_ctx *ctx, const uint32_t *ctr, uint32_t key0, uint32_t key1,
+                           uint32_t *out, int n) {
+  using namespace sr;
+  if (!ctx || n < 0 || (n > 0 && (!ctr || !out))) return fail(ctx, SR_EINVAL, "bad philox arguments");
+  if (n == 0) return SR_OK;
+  SR_CHECK_CUDA(ctx, cudaSetDevice(ctx->device));
+  philox_kernel<<<(n + 255) / 256, 256, 0, ctx->stream>>>(ctr, key0, key1, out, n);
+  SR_CHECK_CUDA(ctx, cudaGetLastError());
+  ctx->launches += 1;
+  return SR_OK;
+}
+
+sr_status sr_select_tournament(sr_ctx *ctx, const double *fitness, int P, int k, uint64_t seed,
+                               uint64_t gen, int32_t *parents) {
+  using namespace sr;
+  if (!ctx) return SR_EINVAL;
+  if (P < 0 || k < 1 || k > 64) return fail(ctx, SR_EINVAL, "P < 0 or k outside [1, 64]");
+  if (P == 0) return SR_OK;
+  if (!fitness || !parents) return fail(ctx, SR_EINVAL, "NULL fitness or parents");
+  SR_CHECK_CUDA(ctx, cudaSetDevice(ctx->device));
+  tournament_kernel<<<(2 * P + 255) / 256, 256, 0, ctx->stream>>>(fitness, P, k, make_rng(seed, gen),
+                                                                    parents);
+  SR_CHECK_CUDA(ctx, cudaGetLastError());
+  ctx->launches += 1;
+  return SR_OK;
+}
+
+sr_status sr_vary(sr_ctx *ctx, const uint8_t *prog_in, const int32_t *len_in, const float *c_in,
+                  const int32_t *parents, uint8_t *prog_out, int32_t *len_out, float *c_out, int P,
+                  int Lmax, int K, int nvars, const sr_var_cfg *cfg, uint64_t seed, uint64_t gen) {
+  using namespace sr;
+  if (!ctx || !cfg) return SR_EINVAL;
+  if (P < 0 || Lmax < 1 || Lmax > SR_MAX_LMAX || K < 0 || K > SR_MAX_CONSTS || nvars < 1 ||
+      nvars > SR_MAX_VARS || cfg->max_subtree < 0 || cfg->max_subtree > Lmax)
+    return fail(ctx, SR_EINVAL, "bad sr_vary shape or configuration");
+  if (P == 0) return SR_OK;
+  if (!prog_in || !len_in || !parents || !prog_out || !len_out || (K > 0 && (!c_in || !c_out)))
+    return fail(ctx, SR_EINVAL, "NULL pointer");
+  if (prog_in == prog_out) return fail(ctx, SR_EINVAL, "prog_out must not alias prog_in");
+  SR_CHECK_CUDA(ctx, cudaSetDevice(ctx->device));
+  VaryParams vp{prog_in, len_in, c_in, parents, prog_out, len_out, c_out, P, Lmax, K, nvars, *cfg,
+                make_rng(seed, gen)};
+  vary_kernel<<<(P + 127) / 128, 128, 0, ctx->stream>>>(vp);
+  SR_CHECK_CUDA(ctx, cudaGetLastError());
+  ctx->launches += 1;
+  return SR_OK;
+}
+
+sr_status sr_random_programs(sr_ctx *ctx, uint8_t *prog, int32_t *len, float *c, int P, int Lmin,
+                             int Lmax, int K, int nvars, float cmin, float cmax, uint64_t seed,
+                             uint64_t stream) {
+  using namespace sr;
+  if (!ctx) return SR_EINVAL;
+  if (P < 0 || Lmin < 1 || Lmin > Lmax || Lmax > SR_MAX_LMAX || K < 0 || K > SR_MAX_CONSTS ||
+      nvars < 1 || nvars > SR_MAX_VARS)
+    return fail(ctx, SR_EINVAL, "bad sr_random_programs shape");
+  if (P == 0) return SR_OK;
+  if (!prog || !len || (K > 0 && !c)) return fail(ctx, SR_EINVAL, "NULL pointer");
+  SR_CHECK_CUDA(ctx, cudaSetDevice(ctx->device));
+  random_programs_kernel<<<(P + 127) / 128, 128, 0, ctx->stream>>>(prog, len, c, P, Lmin, Lmax, K,
+                                                                    nvars, cmin, cmax,
+                                                                    make_rng(seed, stream));
+  SR_CHECK_CUDA(ctx, cudaGetLastError());
+  ctx->launches += 1;
+  return SR_OK;
+}
+
+}  // extern "C"
