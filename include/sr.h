@@ -253,6 +253,51 @@ sr_status sr_random_programs(sr_ctx *ctx, uint8_t *prog, int32_t *len, float *c,
                              float cmin, float cmax, uint64_t seed,
                              uint64_t stream);
 
+/* ------------------------------------------------------------------------
+ * Constant optimisation: reverse-mode derivative of the interpreter and Adam
+ * (Kingma & Ba, 2015).  The paper has no gradient step; it is the
+ * differentiation pattern applied to the same evaluation.
+ * ---------------------------------------------------------------------- */
+
+/*
+ * sr_eval_grad -- MSE of every program and its gradient with respect to the
+ * program's constants: dconst[p][k] = (2/N) sum_i (yhat_i - y_i) dyhat_i/dc_k.
+ * Per (program, case) the forward pass is recomputed into an on-chip tape
+ * (one value per token, shared memory) and swept in reverse with an adjoint
+ * stack.  Derivative conventions: a protected fallback branch, a clamped exp
+ * and sqrt|x| at x = 0 have derivative 0; d log|x|/dx = 1/x; d sqrt|x|/dx =
+ * sign(x) / (2 sqrt|x|).  FP32 per case, FP32 compensated sums per lane,
+ * FP64 across lanes and case chunks.
+ *   arguments as sr_eval; mse device double [P]; dconst device double
+ *   [P][K] (K >= 1).  Invalid programs: mse = +inf, dconst = 0.
+ * Errors: SR_EINVAL, SR_ENOMEM, SR_ECUDA.
+ */
+sr_status sr_eval_grad(sr_ctx *ctx, const uint8_t *programs,
+                       const int32_t *lengths, const float *consts, int P,
+                       int Lmax, int K, const float *X, const float *y,
+                       int nvars, int N, int ldx, double *mse, double *dconst,
+                       int32_t *prog_flags);
+
+typedef struct {
+  double lr;     /* step size (default 1e-2)  */
+  double beta1;  /* default 0.9               */
+  double beta2;  /* default 0.999             */
+  double eps;    /* default 1e-8              */
+} sr_adam_cfg;
+
+/*
+ * sr_adam_step -- one Adam update of n FP32 constants with FP64 moments, step
+ * number t >= 1:  m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g g;
+ * c = fl32(c - lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps)), each FP64
+ * operation rounded in that order (b^t as a product of t factors).  A
+ * non-finite g leaves c, m, v unchanged.
+ *   consts device float [n] (updated), grad device double [n],
+ *   m, v device double [n] (updated).   Errors: SR_EINVAL.
+ */
+sr_status sr_adam_step(sr_ctx *ctx, float *consts, const double *grad,
+                       double *m, double *v, int n, int t,
+                       const sr_adam_cfg *cfg);
+
 /*
  * sr_eval_noalloc -- sr_eval for callers that cannot allocate device memory.
  * (The paper has no counterpart: this exists for embedding.)  Some host

@@ -59,8 +59,8 @@ def _load():
     lib.or_predict_interval.argtypes = [P, i32, P, P, i64, i64, f64, P, P, P, P]
     lib.or_eval.argtypes = [P, P, P, i32, i32, i32, P, i64, P, i32, i64, i32, P, P, i32]
     lib.or_condition.argtypes = [P, P, P, i32, i32, i32, P, i64, P, i32, i64, i32, f64, P, P, P, i32]
-    lib.or_grad.argtypes = [P, P, P, i32, i32, i32, P, i64, P, i32, i64, P, P, P, i32]
-    lib.or_grad_one.argtypes = [P, i32, P, i32, P, i64, P, i64, P, P, P]
+    lib.or_grad.argtypes = [P, P, P, i32, i32, i32, P, i64, P, i32, i64, P, P, P, P, i32]
+    lib.or_grad_one.argtypes = [P, i32, P, i32, P, i64, P, i64, P, P, P, P]
     lib.or_mse_fp64_consts.argtypes = [P, i32, P, P, i64, P, i64]
     lib.or_mse_fp64_consts.restype = f64
     lib.or_mse.argtypes = [P, P, i64]
@@ -200,7 +200,8 @@ def condition(programs, lengths, consts, X, y, kind: int, N: int | None = None,
 
 
 def grad(programs, lengths, consts, X, y, N: int | None = None, nthreads: int = 0):
-    """MSE, dMSE/dconst [P, K] (forward mode, FP64) and the kink distance."""
+    """MSE, dMSE/dconst [P, K] (forward mode, FP64), the kink distance, and
+    (2/N) sum |e dyhat/dc_k| [P, K] (the scale of the sum)."""
     prog = _c(programs, np.uint8)
     P, Lmax = prog.shape
     lens = _c(lengths, np.int32)
@@ -213,9 +214,10 @@ def grad(programs, lengths, consts, X, y, N: int | None = None, nthreads: int = 
     m = np.empty(P, np.float64)
     g = np.empty((P, K), np.float64)
     kink = np.empty(P, np.float64)
+    gabs = np.empty((P, K), np.float64)
     _load().or_grad(_ptr(prog), _ptr(lens), _ptr(cons), P, Lmax, K, _ptr(X64), ldx, _ptr(y64),
-                    nvars, N, _ptr(m), _ptr(g), _ptr(kink), nthreads)
-    return m, g, kink
+                    nvars, N, _ptr(m), _ptr(g), _ptr(kink), _ptr(gabs), nthreads)
+    return m, g, kink, gabs
 
 
 def grad_one_fp64(tokens, consts64, X, y, N: int | None = None):
@@ -230,7 +232,7 @@ def grad_one_fp64(tokens, consts64, X, y, N: int | None = None):
     kink = ctypes.c_double(0.0)
     g = np.empty(max(K, 1), np.float64)
     _load().or_grad_one(_ptr(t), len(t), _ptr(c), K, _ptr(X64), ldx, _ptr(y64), N, ctypes.byref(m),
-                        _ptr(g), ctypes.byref(kink))
+                        _ptr(g), ctypes.byref(kink), None)
     return float(m.value), g[:K], float(kink.value)
 
 
@@ -278,7 +280,7 @@ def random_programs(P, Lmin, Lmax, K, nvars, cmin, cmax, seed, stream):
 
 
 def vary(programs, lengths, consts, parents, K, nvars, p_cross=0.9, p_point=0.1,
-         p_subtree=0.05, p_const=0.1, delta=1.0, max_subtree=8, seed=0, gen=0):
+         p_subtree=0.05, p_const=0.1, const_delta=1.0, max_subtree=8, seed=0, gen=0):
     prog = _c(programs, np.uint8)
     P, Lmax = prog.shape
     lens = _c(lengths, np.int32)
@@ -288,6 +290,6 @@ def vary(programs, lengths, consts, parents, K, nvars, p_cross=0.9, p_point=0.1,
     lo = np.empty_like(lens)
     co = np.empty_like(cons)
     _load().or_vary(_ptr(prog), _ptr(lens), _ptr(cons), _ptr(par), _ptr(po), _ptr(lo), _ptr(co),
-                    P, Lmax, K, nvars, p_cross, p_point, p_subtree, p_const, delta, max_subtree,
+                    P, Lmax, K, nvars, p_cross, p_point, p_subtree, p_const, const_delta, max_subtree,
                     seed, gen)
     return po, lo, co

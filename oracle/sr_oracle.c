@@ -590,18 +590,22 @@ void or_condition(const uint8_t *programs, const int32_t *lengths,
  * a different method from the device's reverse sweep, on purpose.
  * Derivative conventions: d|x|/dx = sign(x) (0 at 0); a protected fallback
  * branch and a clamped exp have derivative 0; d sqrt|x| / dx = 0 at x = 0.
+ * gabs (optional) receives (2/N) sum_i |e_i dyhat_i/dc_k|, the scale of the
+ * sum's rounding error.
  * *kink receives the smallest distance, over all cases, of a branch
  * argument to its switch point (|b| - 1e-3 for division, |x| - 1e-3 for
  * log, |x| for sqrt|x|, |x| - 80 for exp).
  */
 void or_grad_one(const uint8_t *tok, int len, const double *c, int K,
                  const double *X, long ldx, const double *y, long N,
-                 double *mse_out, double *grad, double *kink) {
+                 double *mse_out, double *grad, double *kink, double *gabs) {
   double *val = (double *)malloc(sizeof(double) * (size_t)(len + 1));
   double *tan_ = (double *)malloc(sizeof(double) * (size_t)(len + 1) *
                                   (size_t)(K > 0 ? K : 1));
   double s = 0.0, kmin = INFINITY;
   for (int k = 0; k < K; ++k) grad[k] = 0.0;
+  if (gabs)
+    for (int k = 0; k < K; ++k) gabs[k] = 0.0;
   int finite = 1;
   for (long i = 0; i < N; ++i) {
     int sp = 0;
@@ -677,8 +681,12 @@ void or_grad_one(const uint8_t *tok, int len, const double *c, int K,
     double e = yh - y[i];
     s += e * e;
     for (int k = 0; k < K; ++k) grad[k] += 2.0 * e * tan_[k];
+    if (gabs)
+      for (int k = 0; k < K; ++k) gabs[k] += fabs(2.0 * e * tan_[k]);
   }
   for (int k = 0; k < K; ++k) grad[k] /= (double)N;
+  if (gabs)
+    for (int k = 0; k < K; ++k) gabs[k] /= (double)N;
   *mse_out = (finite && isfinite(s)) ? s / (double)N : INFINITY;
   if (kink) *kink = kmin;
   free(val);
@@ -698,7 +706,7 @@ double or_mse_fp64_consts(const uint8_t *tok, int len, const double *c,
 void or_grad(const uint8_t *programs, const int32_t *lengths,
              const float *consts, int P, int Lmax, int K, const double *X,
              long ldx, const double *y, int nvars, long N, double *mse,
-             double *grad, double *kink, int nthreads) {
+             double *grad, double *kink, double *gabs, int nthreads) {
   int nt = thread_count(nthreads);
 #pragma omp parallel for num_threads(nt) schedule(dynamic, 1)
   for (int p = 0; p < P; ++p) {
@@ -708,12 +716,15 @@ void or_grad(const uint8_t *programs, const int32_t *lengths,
     if (or_validate(tok, lengths[p], Lmax, nvars, K, &md)) {
       mse[p] = INFINITY;
       for (int k = 0; k < K; ++k) grad[(size_t)p * K + k] = 0.0;
+      if (gabs)
+        for (int k = 0; k < K; ++k) gabs[(size_t)p * K + k] = 0.0;
       if (kink) kink[p] = 0.0;
       continue;
     }
     widen_consts(consts + (size_t)p * K, K, c);
     or_grad_one(tok, lengths[p], c, K, X, ldx, y, N, &mse[p],
-                grad + (size_t)p * K, kink ? &kink[p] : NULL);
+                grad + (size_t)p * K, kink ? &kink[p] : NULL,
+                gabs ? gabs + (size_t)p * K : NULL);
   }
 }
 

@@ -23,7 +23,7 @@ SR_MAX_LMAX, SR_MAX_VARS, SR_MAX_CONSTS = 512, 16, 16
 EXPORTS = ["sr_create", "sr_destroy", "sr_set_stream", "sr_status_string", "sr_last_error",
            "sr_reserve", "sr_sync", "sr_eval", "sr_predict", "sr_kernel_launches",
            "sr_eval_noalloc", "sr_philox4x32_10", "sr_select_tournament", "sr_vary",
-           "sr_random_programs"]
+           "sr_random_programs", "sr_eval_grad", "sr_adam_step"]
 
 _lib = None
 
@@ -33,6 +33,16 @@ class VarCfg(ctypes.Structure):
     _fields_ = [("p_cross", ctypes.c_float), ("p_point", ctypes.c_float),
                 ("p_subtree", ctypes.c_float), ("p_const", ctypes.c_float),
                 ("const_delta", ctypes.c_float), ("max_subtree", ctypes.c_int)]
+
+
+class AdamCfg(ctypes.Structure):
+    """sr_adam_cfg (include/sr.h)."""
+    _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double)]
+
+
+def adam_cfg(lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8):
+    return AdamCfg(lr, beta1, beta2, eps)
 
 
 def var_cfg(p_cross=0.9, p_point=0.1, p_subtree=0.05, p_const=0.1, const_delta=1.0, max_subtree=8):
@@ -72,6 +82,8 @@ def lib() -> ctypes.CDLL:
     L.sr_vary.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, ctypes.POINTER(VarCfg),
                           u64, u64]
     L.sr_random_programs.argtypes = [vp, vp, vp, vp, i32, i32, i32, i32, i32, f32, f32, u64, u64]
+    L.sr_eval_grad.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp, vp, i32, i32, i32, vp, vp, vp]
+    L.sr_adam_step.argtypes = [vp, vp, vp, vp, vp, i32, i32, ctypes.POINTER(AdamCfg)]
     L.sr_eval_noalloc.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp, vp, i32, i32, i32, i32, vp, vp]
     for name in EXPORTS:
         if name not in ("sr_status_string", "sr_last_error", "sr_kernel_launches"):
@@ -259,3 +271,34 @@ def sr_random_programs(ctx: Context, P: int, Lmin: int, Lmax: int, K: int, nvars
     _check(ctx, lib().sr_random_programs(ctx.handle, _ptr(prog), _ptr(lens), _ptr(c) if K else None, P,
                                          Lmin, Lmax, K, nvars, cmin, cmax, seed, stream))
     return prog, lens, c
+
+
+def sr_eval_grad(ctx: Context, programs, lengths, consts, X, y, N: int, mse=None, dconst=None,
+                 prog_flags=None):
+    """MSE [P] and dMSE/dconst [P, K] (float64)."""
+    _dev(programs, torch.uint8, "programs")
+    _dev(lengths, torch.int32, "lengths")
+    _dev(consts, torch.float32, "consts")
+    _dev(X, torch.float32, "X")
+    _dev(y, torch.float32, "y")
+    P, Lmax = programs.shape
+    K = consts.shape[1]
+    nvars, ldx = X.shape
+    if mse is None:
+        mse = torch.empty(P, dtype=torch.float64, device=programs.device)
+    if dconst is None:
+        dconst = torch.empty((P, K), dtype=torch.float64, device=programs.device)
+    _check(ctx, lib().sr_eval_grad(ctx.handle, _ptr(programs), _ptr(lengths), _ptr(consts), P, Lmax, K,
+                                   _ptr(X), _ptr(y), nvars, N, ldx, _ptr(mse), _ptr(dconst),
+                                   _ptr(prog_flags)))
+    return mse, dconst
+
+
+def sr_adam_step(ctx: Context, consts, grad, m, v, t: int, cfg: AdamCfg):
+    """In-place Adam update of consts (float32) with float64 grad / moments."""
+    _dev(consts, torch.float32, "consts")
+    _dev(grad, torch.float64, "grad")
+    _dev(m, torch.float64, "m")
+    _dev(v, torch.float64, "v")
+    _check(ctx, lib().sr_adam_step(ctx.handle, _ptr(consts), _ptr(grad), _ptr(m), _ptr(v),
+                                   consts.numel(), t, ctypes.byref(cfg)))

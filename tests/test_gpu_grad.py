@@ -1,0 +1,166 @@
+"""Reverse-mode dMSE/dconst (sr_eval_grad) against a closed form, the oracle's
+forward-mode FP64 gradient and FP64 central differences; Adam bit for bit
+against the oracle; the autograd wrapper."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from helpers import dev
+from paper_2603_12292_gb300 import binding, inputs
+from paper_2603_12292_gb300.autograd import program_mse
+from progtext import pack, parse
+
+pytestmark = pytest.mark.gpu
+
+
+def test_closed_form_linear_program(ctx):
+    """yhat = c0 x0:  dMSE/dc0 = (2/N) sum (c0 x0 - y) x0."""
+    rng = np.random.default_rng(0)
+    N = 3001
+    X = inputs.random_X(rng, 1, N, 1.0, 5.0)
+    y = rng.normal(size=N).astype(np.float32)
+    progs, lens = pack([parse("c0 x0 *"), parse("x0 c0 *"), parse("x0 c0 - c1 /")], 8)
+    c = np.array([[1.3, 0.7], [1.3, 0.7], [0.25, 2.0]], np.float32)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    mse, g = binding.sr_eval_grad(ctx, t(progs), t(lens), t(c), t(X), t(y), N)
+    mse, g = mse.cpu().numpy(), g.cpu().numpy()
+    x, yy, c0 = X[0, :N].astype(np.float64), y.astype(np.float64), float(c[0, 0])
+    want = 2.0 / N * np.sum((c0 * x - yy) * x)
+    assert g[0, 0] == pytest.approx(want, rel=1e-5) and g[1, 0] == pytest.approx(want, rel=1e-5)
+    assert g[0, 1] == 0.0
+    # (x0 - c0) / c1:  d/dc0 = -(2/N) sum e / c1,  d/dc1 = -(2/N) sum e (x0 - c0) / c1^2
+    c0, c1 = float(c[2, 0]), float(c[2, 1])
+    e = (x - c0) / c1 - yy
+    assert g[2, 0] == pytest.approx(-2.0 / N * np.sum(e) / c1, rel=1e-5)
+    assert g[2, 1] == pytest.approx(-2.0 / N * np.sum(e * (x - c0)) / c1 ** 2, rel=1e-5)
+    assert mse[0] == pytest.approx(np.mean((float(c[0, 0]) * x - yy) ** 2), rel=1e-5)
+
+
+@pytest.fixture(scope="module")
+def adjoint_problem():
+    """Adjoint-shaped workload at a size the oracle finishes in seconds:
+    programs of length <= 96 with 8 constants over 5 variables."""
+    pr = inputs.make_problem("adj", 314, P=512, Lmin=4, Lmax=96, nvars=5, K=8, N=4099, xlo=1.0,
+                             xhi=5.0, target_len=(5, 15))
+    y = oracle.predict(pr.target, pr.target_consts, pr.X, pr.N)
+    return pr, inputs.add_noise(np.random.default_rng(1), y, 0.01)
+
+
+def test_gradient_matches_oracle(ctx, adjoint_problem):
+    """On programs whose MSE the FP32 evaluation reproduces to 1e-6 (interval
+    bound), every constant's gradient agrees with the FP64 forward-mode
+    gradient within 2e-4 of its absolute-sum scale (2/N) sum |e dyhat/dc|."""
+    pr, y = adjoint_problem
+    d = dev(pr, y)
+    mse_g, g_g = binding.sr_eval_grad(ctx, d["programs"], d["lengths"], d["consts"], d["X"], d["y"], pr.N)
+    mse_g, g_g = mse_g.cpu().numpy(), g_g.cpu().numpy()
+    mse_o, g_o, kink, gabs = oracle.grad(pr.programs, pr.lengths, pr.consts, pr.X, y, pr.N)
+    errb, cfl, f0 = oracle.condition(pr.programs, pr.lengths, pr.consts, pr.X, y, oracle.MSE, pr.N)
+    well = (cfl == 0) & np.isfinite(f0) & (errb <= 1e-6 * np.abs(f0)) & (kink > 1e-3)
+    assert well.sum() > 100
+    err = np.abs(g_g - g_o)
+    tol = 2e-4 * gabs + 1e-12
+    bad = well[:, None] & ~(err <= tol)
+    assert not bad.any(), (np.argwhere(bad)[:5], g_g[bad][:5], g_o[bad][:5], gabs[bad][:5])
+    fin = np.isfinite(f0)
+    np.testing.assert_allclose(mse_g[well], mse_o[well], rtol=1e-5)
+    assert np.isinf(mse_g[~fin]).all() if (~fin).any() else True
+
+
+def test_gradient_matches_central_differences(ctx, adjoint_problem):
+    """The device gradient vs FP64 central differences (h = 1e-6) of the
+    oracle's MSE on 256 sampled programs (those away from kinks and not too
+    curved for h)."""
+    pr, y = adjoint_problem
+    d = dev(pr, y)
+    _, g_g = binding.sr_eval_grad(ctx, d["programs"], d["lengths"], d["consts"], d["X"], d["y"], pr.N)
+    g_g = g_g.cpu().numpy()
+    _, _, kink, gabs = oracle.grad(pr.programs, pr.lengths, pr.consts, pr.X, y, pr.N)
+    errb, cfl, f0 = oracle.condition(pr.programs, pr.lengths, pr.consts, pr.X, y, oracle.MSE, pr.N)
+    idx = np.random.default_rng(5).choice(pr.P, 256, replace=False)
+    h, tested = 1e-6, 0
+    for p in idx:
+        if cfl[p] or not np.isfinite(f0[p]) or errb[p] > 1e-6 * abs(f0[p]) or kink[p] < 1e-3:
+            continue
+        tok = pr.programs[p, : pr.lengths[p]]
+        c = pr.consts[p].astype(np.float64)
+
+        def fd(k, step):
+            cp, cm = c.copy(), c.copy()
+            cp[k] += step
+            cm[k] -= step
+            return (oracle.mse_fp64_consts(tok, cp, pr.X, y, pr.N)
+                    - oracle.mse_fp64_consts(tok, cm, pr.X, y, pr.N)) / (2 * step)
+
+        ok = True
+        for k in range(pr.K):
+            d1, d2 = fd(k, h), fd(k, h / 2)
+            trunc = abs(d1 - d2) * 4 / 3
+            if trunc > 1e-4 * max(abs(d1), gabs[p, k], 1e-12):
+                ok = False
+                break
+            assert abs(g_g[p, k] - d1) <= 2e-4 * gabs[p, k] + 2 * trunc + 1e-10, (p, k, g_g[p, k], d1)
+        tested += ok
+    assert tested >= 40
+
+
+def test_adam_bit_exact(ctx):
+    rng = np.random.default_rng(7)
+    n = 5000
+    c = rng.uniform(-5, 5, n).astype(np.float32)
+    g = rng.normal(size=n) * 10.0 ** rng.uniform(-6, 3, n)
+    g[::97] = np.nan
+    g[::101] = np.inf
+    m = np.zeros(n)
+    v = np.zeros(n)
+    cd, gd, md, vd = (torch.from_numpy(a.copy()).cuda() for a in (c, g, m, v))
+    cfg = dict(lr=0.05, beta1=0.9, beta2=0.999, eps=1e-8)
+    for t in range(1, 21):
+        binding.sr_adam_step(ctx, cd, gd, md, vd, t, binding.adam_cfg(**cfg))
+        oracle.adam(c, g, m, v, t, **cfg)
+        g = g * 0.9 + 0.1 * rng.normal(size=n)
+        gd.copy_(torch.from_numpy(g))
+    np.testing.assert_array_equal(cd.cpu().numpy().view(np.uint32), c.view(np.uint32))
+    np.testing.assert_array_equal(md.cpu().numpy().view(np.uint64), m.view(np.uint64))
+    np.testing.assert_array_equal(vd.cpu().numpy().view(np.uint64), v.view(np.uint64))
+
+
+def test_autograd_function_and_adam_descend(ctx):
+    """program_mse is differentiable in the constants; 20 Adam steps driven by
+    sr_eval_grad lower the MSE of a program whose constants are off."""
+    rng = np.random.default_rng(9)
+    N = 2000
+    X = inputs.random_X(rng, 2, N, 1.0, 3.0)
+    y = (2.5 * X[0, :N] + np.sin(X[1, :N]) * 1.5 - 0.75).astype(np.float32)
+    progs, lens = pack([parse("c0 x0 * c1 x1 sin * + c2 +"), parse("x0 c0 * c1 +")], 12)
+    c = np.array([[1.0, 0.0, 0.0], [1.0, 0.0, 0.0]], np.float32)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    P_, L_, X_, y_ = t(progs), t(lens), t(X), t(y)
+    consts = t(c).requires_grad_(True)
+    mse = program_mse(consts, P_, L_, X_, y_, N, ctx)
+    mse.sum().backward()
+    _, g = binding.sr_eval_grad(ctx, P_, L_, consts.detach(), X_, y_, N)
+    torch.testing.assert_close(consts.grad, g.float())
+    cc = consts.detach().clone()
+    m = torch.zeros((2, 3), dtype=torch.float64, device="cuda")
+    v = torch.zeros_like(m)
+    start = binding.sr_eval(ctx, P_, L_, cc, X_, y_, N, binding.SR_MSE).cpu().numpy()
+    for step in range(1, 21):
+        _, g = binding.sr_eval_grad(ctx, P_, L_, cc, X_, y_, N)
+        binding.sr_adam_step(ctx, cc, g, m, v, step, binding.adam_cfg(lr=0.1))
+    end = binding.sr_eval(ctx, P_, L_, cc, X_, y_, N, binding.SR_MSE).cpu().numpy()
+    assert (end < 0.5 * start).all()
+
+
+def test_invalid_programs_in_gradient(ctx):
+    progs, lens = pack([parse("x0 +"), parse("c0 x0 *")], 4)
+    X = np.ones((1, 64), np.float32)
+    y = np.ones(64, np.float32)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    flags = torch.empty(2, dtype=torch.int32, device="cuda")
+    mse, g = binding.sr_eval_grad(ctx, t(progs), t(lens), t(np.ones((2, 1), np.float32)), t(X), t(y), 64,
+                                  prog_flags=flags)
+    assert np.isinf(mse[0].item()) and g[0, 0].item() == 0.0
+    assert flags.cpu().tolist() == [oracle.PF_UNDERFLOW | oracle.PF_BAD_FINAL, 0]
+    assert mse[1].item() == 0.0 and g[1, 0].item() == 0.0

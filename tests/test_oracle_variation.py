@@ -215,7 +215,7 @@ def test_constant_mutation_bound(pop):
     prog, lens, c, par, K, nv = pop
     delta = 0.75
     po, lo, co = oracle.vary(prog, lens, c, par, K, nv, p_cross=0, p_point=0, p_subtree=0,
-                             p_const=1.0, delta=delta, seed=17, gen=5)
+                             p_const=1.0, const_delta=delta, seed=17, gen=5)
     base = c[par[:, 0]]
     d = co.astype(np.float64) - base.astype(np.float64)
     assert ((d != 0).sum(1) <= 1).all()
