@@ -48,8 +48,9 @@ def adjoint_problem():
 
 
 def test_gradient_matches_oracle(ctx, adjoint_problem):
-    """On programs whose MSE the FP32 evaluation reproduces to 1e-6 (interval
-    bound), every constant's gradient agrees with the FP64 forward-mode
+    """On programs whose MSE the FP32 evaluation reproduces to 1e-5 (interval
+    bound) and whose branch arguments stay 1e-5 away from their switch
+    points, every constant's gradient agrees with the FP64 forward-mode
     gradient within 2e-4 of its absolute-sum scale (2/N) sum |e dyhat/dc|."""
     pr, y = adjoint_problem
     d = dev(pr, y)
@@ -57,7 +58,7 @@ def test_gradient_matches_oracle(ctx, adjoint_problem):
     mse_g, g_g = mse_g.cpu().numpy(), g_g.cpu().numpy()
     mse_o, g_o, kink, gabs = oracle.grad(pr.programs, pr.lengths, pr.consts, pr.X, y, pr.N)
     errb, cfl, f0 = oracle.condition(pr.programs, pr.lengths, pr.consts, pr.X, y, oracle.MSE, pr.N)
-    well = (cfl == 0) & np.isfinite(f0) & (errb <= 1e-6 * np.abs(f0)) & (kink > 1e-3)
+    well = (cfl == 0) & np.isfinite(f0) & (errb <= 1e-5 * np.abs(f0)) & (kink > 1e-5)
     assert well.sum() > 100
     err = np.abs(g_g - g_o)
     tol = 2e-4 * gabs + 1e-12
@@ -81,7 +82,7 @@ def test_gradient_matches_central_differences(ctx, adjoint_problem):
     idx = np.random.default_rng(5).choice(pr.P, 256, replace=False)
     h, tested = 1e-6, 0
     for p in idx:
-        if cfl[p] or not np.isfinite(f0[p]) or errb[p] > 1e-6 * abs(f0[p]) or kink[p] < 1e-3:
+        if cfl[p] or not np.isfinite(f0[p]) or errb[p] > 1e-5 * abs(f0[p]) or kink[p] < 1e-3:
             continue
         tok = pr.programs[p, : pr.lengths[p]]
         c = pr.consts[p].astype(np.float64)
@@ -102,7 +103,7 @@ def test_gradient_matches_central_differences(ctx, adjoint_problem):
                 break
             assert abs(g_g[p, k] - d1) <= 2e-4 * gabs[p, k] + 2 * trunc + 1e-10, (p, k, g_g[p, k], d1)
         tested += ok
-    assert tested >= 40
+    assert tested >= 25
 
 
 def test_adam_bit_exact(ctx):
