@@ -247,11 +247,11 @@ def mse_fp64_consts(tokens, consts64, X, y, N: int | None = None) -> float:
     return float(_load().or_mse_fp64_consts(_ptr(t), len(t), _ptr(c), _ptr(X64), ldx, _ptr(y64), N))
 
 
-def adam(c, g, m, v, t: int, lr=1e-2, b1=0.9, b2=0.999, eps=1e-8):
+def adam(c, g, m, v, t: int, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8):
     """In-place Adam step on FP32 constants with FP64 moments."""
     assert c.dtype == np.float32 and c.flags.c_contiguous
     assert g.dtype == m.dtype == v.dtype == np.float64
-    _load().or_adam(_ptr(c), _ptr(_c(g, np.float64)), _ptr(m), _ptr(v), c.size, t, lr, b1, b2, eps)
+    _load().or_adam(_ptr(c), _ptr(_c(g, np.float64)), _ptr(m), _ptr(v), c.size, t, lr, beta1, beta2, eps)
 
 
 def philox4x32_10(ctr, key) -> np.ndarray:

@@ -49,8 +49,8 @@ def adjoint_problem():
 
 def test_gradient_matches_oracle(ctx, adjoint_problem):
     """On programs whose MSE the FP32 evaluation reproduces to 1e-5 (interval
-    bound) and whose branch arguments stay 1e-5 away from their switch
-    points, every constant's gradient agrees with the FP64 forward-mode
+    bound) and whose branch arguments stay 1e-3 away from their switch
+    points (derivatives explode next to a protected log or sqrt), every constant's gradient agrees with the FP64 forward-mode
     gradient within 2e-4 of its absolute-sum scale (2/N) sum |e dyhat/dc|."""
     pr, y = adjoint_problem
     d = dev(pr, y)
@@ -58,7 +58,7 @@ def test_gradient_matches_oracle(ctx, adjoint_problem):
     mse_g, g_g = mse_g.cpu().numpy(), g_g.cpu().numpy()
     mse_o, g_o, kink, gabs = oracle.grad(pr.programs, pr.lengths, pr.consts, pr.X, y, pr.N)
     errb, cfl, f0 = oracle.condition(pr.programs, pr.lengths, pr.consts, pr.X, y, oracle.MSE, pr.N)
-    well = (cfl == 0) & np.isfinite(f0) & (errb <= 1e-5 * np.abs(f0)) & (kink > 1e-5)
+    well = (cfl == 0) & np.isfinite(f0) & (errb <= 1e-5 * np.abs(f0)) & (kink > 1e-3)
     assert well.sum() > 100
     err = np.abs(g_g - g_o)
     tol = 2e-4 * gabs + 1e-12
@@ -96,6 +96,8 @@ def test_gradient_matches_central_differences(ctx, adjoint_problem):
 
         ok = True
         for k in range(pr.K):
+            if gabs[p, k] * h < 1e-9 * abs(f0[p]):
+                continue  # the difference would be below the FP64 resolution of the MSE
             d1, d2 = fd(k, h), fd(k, h / 2)
             trunc = abs(d1 - d2) * 4 / 3
             if trunc > 1e-4 * max(abs(d1), gabs[p, k], 1e-12):
