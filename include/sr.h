@@ -144,6 +144,42 @@ sr_status sr_eval(sr_ctx *ctx, const uint8_t *programs, const int32_t *lengths,
                   const float *y, int nvars, int N, int ldx,
                   sr_fitness_kind kind, double *fitness, int32_t *prog_flags);
 
+/* One problem of a batch: its own population, data, kind and outputs. */
+typedef struct {
+  const uint8_t *programs;  /* device [P][Lmax]                          */
+  const int32_t *lengths;   /* device [P]                                */
+  const float *consts;      /* device [P][K] (NULL when K == 0)          */
+  int P, Lmax, K;
+  const float *X;           /* device [nvars][ldx], 16-byte aligned      */
+  const float *y;           /* device [N], 16-byte aligned               */
+  int nvars, N, ldx;
+  sr_fitness_kind kind;
+  double *fitness;          /* device [P] ([2][P] for SR_MSE_CORR)       */
+  int32_t *prog_flags;      /* device [P] or NULL                        */
+  int cases_per_tile;       /* cases per work item; 0 = automatic        */
+} sr_problem;
+
+/*
+ * sr_eval_batched -- sr_eval of many independent problems (different case
+ * counts, variable counts, population sizes, lengths and kinds) in one
+ * persistent launch: a single atomic work counter hands out (problem, case
+ * chunk, program) items, longest items first, to the warps of one grid.
+ * Up to 64 problems share a launch (more are split into groups of 64); the
+ * problem table travels in the kernel parameters, so the call can be
+ * captured in a CUDA graph once the workspace has grown (call it once, or
+ * sr_reserve, before capturing).  Results equal those of sr_eval per
+ * problem up to the summation order of the case chunks.
+ *   problems  host array of nprob entries (copied during the call)
+ * Errors: SR_EINVAL (first bad problem is named in sr_last_error),
+ * SR_ENOMEM, SR_ECUDA.
+ */
+sr_status sr_eval_batched(sr_ctx *ctx, const sr_problem *problems, int nprob);
+
+/* Cases per evaluation work item for later sr_eval / sr_predict calls on
+ * this context (rounded up to a multiple of 128); 0 restores the automatic
+ * choice (about eight items per resident warp).  Set by the autotuner. */
+sr_status sr_set_tile(sr_ctx *ctx, int cases_per_tile);
+
 /*
  * sr_predict -- the output yhat of every program on every case (the value
  * left on the stack, Sec. 2.1.4), FP32.
@@ -238,6 +274,16 @@ sr_status sr_vary(sr_ctx *ctx, const uint8_t *prog_in, const int32_t *len_in,
                   int32_t *len_out, float *c_out, int P, int Lmax, int K,
                   int nvars, const sr_var_cfg *cfg, uint64_t seed,
                   uint64_t gen);
+
+/*
+ * sr_set_generation_source -- make later sr_select_tournament and sr_vary
+ * calls on this context read the generation from device memory: the
+ * generation used is *gen_dev + gen (gen = the call's argument), read when
+ * the kernel runs.  This lets a captured CUDA graph advance the generation
+ * on every replay (increment *gen_dev inside the graph).  NULL restores the
+ * argument-only behaviour.  gen_dev: device uint64, caller-owned.
+ */
+sr_status sr_set_generation_source(sr_ctx *ctx, const uint64_t *gen_dev);
 
 /*
  * sr_random_programs -- a random valid population: program i has length

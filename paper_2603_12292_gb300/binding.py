@@ -23,7 +23,8 @@ SR_MAX_LMAX, SR_MAX_VARS, SR_MAX_CONSTS = 512, 16, 16
 EXPORTS = ["sr_create", "sr_destroy", "sr_set_stream", "sr_status_string", "sr_last_error",
            "sr_reserve", "sr_sync", "sr_eval", "sr_predict", "sr_kernel_launches",
            "sr_eval_noalloc", "sr_philox4x32_10", "sr_select_tournament", "sr_vary",
-           "sr_random_programs", "sr_eval_grad", "sr_adam_step"]
+           "sr_random_programs", "sr_eval_grad", "sr_adam_step", "sr_eval_batched", "sr_set_tile",
+           "sr_set_generation_source"]
 
 _lib = None
 
@@ -33,6 +34,16 @@ class VarCfg(ctypes.Structure):
     _fields_ = [("p_cross", ctypes.c_float), ("p_point", ctypes.c_float),
                 ("p_subtree", ctypes.c_float), ("p_const", ctypes.c_float),
                 ("const_delta", ctypes.c_float), ("max_subtree", ctypes.c_int)]
+
+
+class Problem(ctypes.Structure):
+    """sr_problem (include/sr.h)."""
+    _fields_ = [("programs", ctypes.c_void_p), ("lengths", ctypes.c_void_p), ("consts", ctypes.c_void_p),
+                ("P", ctypes.c_int), ("Lmax", ctypes.c_int), ("K", ctypes.c_int),
+                ("X", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("nvars", ctypes.c_int), ("N", ctypes.c_int), ("ldx", ctypes.c_int),
+                ("kind", ctypes.c_int), ("fitness", ctypes.c_void_p), ("prog_flags", ctypes.c_void_p),
+                ("cases_per_tile", ctypes.c_int)]
 
 
 class AdamCfg(ctypes.Structure):
@@ -84,6 +95,9 @@ def lib() -> ctypes.CDLL:
     L.sr_random_programs.argtypes = [vp, vp, vp, vp, i32, i32, i32, i32, i32, f32, f32, u64, u64]
     L.sr_eval_grad.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp, vp, i32, i32, i32, vp, vp, vp]
     L.sr_adam_step.argtypes = [vp, vp, vp, vp, vp, i32, i32, ctypes.POINTER(AdamCfg)]
+    L.sr_eval_batched.argtypes = [vp, ctypes.POINTER(Problem), i32]
+    L.sr_set_tile.argtypes = [vp, i32]
+    L.sr_set_generation_source.argtypes = [vp, vp]
     L.sr_eval_noalloc.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp, vp, i32, i32, i32, i32, vp, vp]
     for name in EXPORTS:
         if name not in ("sr_status_string", "sr_last_error", "sr_kernel_launches"):
@@ -302,3 +316,43 @@ def sr_adam_step(ctx: Context, consts, grad, m, v, t: int, cfg: AdamCfg):
     _dev(v, torch.float64, "v")
     _check(ctx, lib().sr_adam_step(ctx.handle, _ptr(consts), _ptr(grad), _ptr(m), _ptr(v),
                                    consts.numel(), t, ctypes.byref(cfg)))
+
+
+def sr_set_tile(ctx: Context, cases_per_tile: int):
+    _check(ctx, lib().sr_set_tile(ctx.handle, cases_per_tile))
+
+
+def make_problem(programs, lengths, consts, X, y, N: int, kind: int, fitness=None, prog_flags=None,
+                 cases_per_tile: int = 0):
+    """An sr_problem over torch tensors (kept alive by the returned tuple)."""
+    _dev(programs, torch.uint8, "programs")
+    _dev(lengths, torch.int32, "lengths")
+    _dev(X, torch.float32, "X")
+    _dev(y, torch.float32, "y")
+    P, Lmax = programs.shape
+    K = 0 if consts is None else (consts.shape[1] if consts.dim() == 2 else 0)
+    if K:
+        _dev(consts, torch.float32, "consts")
+    if fitness is None:
+        shape = (2, P) if kind == SR_MSE_CORR else (P,)
+        fitness = torch.empty(shape, dtype=torch.float64, device=programs.device)
+    _dev(fitness, torch.float64, "fitness")
+    nvars, ldx = X.shape
+    pr = Problem(programs.data_ptr(), lengths.data_ptr(), consts.data_ptr() if K else None, P, Lmax, K,
+                 X.data_ptr(), y.data_ptr(), nvars, N, ldx, kind, fitness.data_ptr(),
+                 prog_flags.data_ptr() if prog_flags is not None else None, cases_per_tile)
+    return pr, (programs, lengths, consts, X, y, fitness, prog_flags)
+
+
+def sr_eval_batched(ctx: Context, problems):
+    """problems: list of make_problem results; returns the fitness tensors."""
+    arr = (Problem * len(problems))(*[p[0] for p in problems])
+    _check(ctx, lib().sr_eval_batched(ctx.handle, arr, len(problems)))
+    return [p[1][5] for p in problems]
+
+
+def sr_set_generation_source(ctx: Context, gen_dev: torch.Tensor | None):
+    """Selection / variation read the generation from gen_dev (int64 [1]) + gen."""
+    if gen_dev is not None:
+        _dev(gen_dev, torch.int64, "gen_dev")
+    _check(ctx, lib().sr_set_generation_source(ctx.handle, _ptr(gen_dev)))

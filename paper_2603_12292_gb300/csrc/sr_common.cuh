@@ -18,6 +18,8 @@ struct sr_ctx {
   unsigned *dev_words = nullptr;
   char msg[512] = {0};
   uint64_t launches = 0;  // kernels launched by this context
+  int tile_cases = 0;     // cases per evaluation work item (0: automatic)
+  const uint64_t *gen_dev = nullptr;  // device generation counter for selection / variation
 };
 
 namespace sr {

@@ -27,6 +27,9 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "sr_common.cuh"
 
 namespace sr {
@@ -263,19 +266,110 @@ __device__ __forceinline__ float4 load_y4(const float *__restrict__ y, int c0, i
   return r;
 }
 
-// ---------------------------------------------------------------- main kernel
+// ---------------------------------------------------------------- one work item
+struct WarpSmem {
+  float4 *stk_s;    // shared stack slots, [DSM][32] float4
+  float *cvals;     // the program's constants
+  uint32_t *code;   // decoded instructions
+  float4 *stk_g;    // this warp's global stack slots for deep programs
+};
+
+__device__ __forceinline__ WarpSmem warp_smem(unsigned char *smem, int warp, int warp_bytes,
+                                              float4 *deep_stack, int deep_slots) {
+  unsigned char *wbase = smem + (size_t)warp * warp_bytes;
+  WarpSmem w;
+  w.stk_s = reinterpret_cast<float4 *>(wbase);
+  w.cvals = reinterpret_cast<float *>(wbase + DSM * 32 * 16);
+  w.code = reinterpret_cast<uint32_t *>(wbase + DSM * 32 * 16 + 64);
+  const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
+  w.stk_g = deep_stack ? deep_stack + (size_t)gw * deep_slots * 32 : nullptr;
+  return w;
+}
+
+// Evaluates program `prog` of problem p on case chunk `c` with the calling
+// warp.  MODE_BOTH accumulates the sums selected by `want` (bit 0: squared
+// error, bit 1: correlation moments); the other modes ignore `want`.
+template <int MODE>
+__device__ __forceinline__ void eval_item(const EvalParams &p, int c, int prog, const WarpSmem &w,
+                                          int lane, int want) {
+  const bool do_mse = MODE == MODE_MSE || (MODE == MODE_BOTH && (want & 1));
+  const bool do_corr = MODE == MODE_CORR || (MODE == MODE_BOTH && (want & 2));
+  __syncwarp();  // the previous item is done reading code/cvals
+  const Decoded dec = decode_program(p.programs + (size_t)prog * p.Lmax, p.lengths[prog], p.Lmax,
+                                     p.nvars, p.K, w.code, lane);
+  if (lane == 0 && c == 0) p.flags[prog] = dec.flags;
+  const int cbeg = c * p.chunk;
+  const int cend = min(p.N, cbeg + p.chunk);
+
+  if (dec.flags) {
+    if (MODE == MODE_PREDICT) {
+      float *row = p.yhat + (size_t)prog * p.ldy;
+      for (int i = cbeg + lane; i < cend; i += 32) row[i] = __int_as_float(0x7fc00000);
+    }
+    return;
+  }
+  if (lane < p.K) w.cvals[lane] = p.consts[(size_t)prog * p.K + lane];
+  __syncwarp();
+
+  float4 *stk = (dec.maxd - 1 <= DSM) ? w.stk_s + lane : w.stk_g + lane;
+  const int last_group = (cend - 1) & ~3;
+
+  Kahan se, s1, s2, s3;
+  float shift = 0.f;
+  for (int base = cbeg; base < cend; base += STEP) {
+    const int c0 = base + 4 * lane;
+    const int cl = c0 < cend ? c0 : last_group;  // clamped, always readable
+    const float4 T = interpret(w.code, dec.n, w.cvals, stk, p.X, p.ldx, cl);
+    const bool v0 = c0 < cend, v1 = c0 + 1 < cend, v2 = c0 + 2 < cend, v3 = c0 + 3 < cend;
+    if (MODE == MODE_PREDICT) {
+      float *row = p.yhat + (size_t)prog * p.ldy;
+      if (v0) row[c0] = T.x;
+      if (v1) row[c0 + 1] = T.y;
+      if (v2) row[c0 + 2] = T.z;
+      if (v3) row[c0 + 3] = T.w;
+    }
+    if (do_mse) {
+      const float4 yv = load_y4(p.y, cl, p.N);
+      const float e0 = sel(v0, T.x - yv.x), e1 = sel(v1, T.y - yv.y);
+      const float e2 = sel(v2, T.z - yv.z), e3 = sel(v3, T.w - yv.w);
+      se.add((e0 * e0 + e1 * e1) + (e2 * e2 + e3 * e3));
+    }
+    if (do_corr) {
+      if (base == cbeg) shift = __shfl_sync(FULL, T.x, 0);
+      const float4 yv = ldx4(p.yc + cl);
+      const float d0 = sel(v0, T.x - shift), d1 = sel(v1, T.y - shift);
+      const float d2 = sel(v2, T.z - shift), d3 = sel(v3, T.w - shift);
+      s1.add((d0 + d1) + (d2 + d3));
+      s2.add((d0 * d0 + d1 * d1) + (d2 * d2 + d3 * d3));
+      s3.add((d0 * yv.x + d1 * yv.y) + (d2 * yv.z + d3 * yv.w));
+    }
+  }
+  if (MODE != MODE_PREDICT) {
+    double *rec = p.partials + ((size_t)prog * p.nchunks + c) * PSTRIDE;
+    if (do_mse) {
+      const double v = warp_sum(se.value());
+      if (lane == 0) rec[0] = v;
+    }
+    if (do_corr) {
+      const double a = warp_sum(s1.value());
+      const double b = warp_sum(s2.value());
+      const double d = warp_sum(s3.value());
+      if (lane == 0) {
+        rec[1] = (double)shift;
+        rec[2] = a;
+        rec[3] = b;
+        rec[4] = d;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- single problem
 template <int MODE>
 __global__ void __launch_bounds__(WARPS * 32) eval_kernel(EvalParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char *wbase = smem + (size_t)warp * p.warp_bytes;
-  float4 *stk_s = reinterpret_cast<float4 *>(wbase);
-  float *cvals = reinterpret_cast<float *>(wbase + DSM * 32 * 16);
-  uint32_t *code = reinterpret_cast<uint32_t *>(wbase + DSM * 32 * 16 + 64);
-  float4 *stk_g = p.deep_stack
-                      ? p.deep_stack + ((size_t)blockIdx.x * WARPS + warp) * p.deep_slots * 32
-                      : nullptr;
-
+  const WarpSmem w = warp_smem(smem, warp, p.warp_bytes, p.deep_stack, p.deep_slots);
   for (;;) {
     unsigned long long item = 0;
     if (lane == 0) item = atomicAdd(p.queue, 1ull);
@@ -283,75 +377,84 @@ __global__ void __launch_bounds__(WARPS * 32) eval_kernel(EvalParams p) {
     if ((long long)item >= p.total_items) break;
     const int c = (int)(item / (unsigned long long)p.P);
     const int prog = (int)(item % (unsigned long long)p.P);
+    eval_item<MODE>(p, c, prog, w, lane, 3);
+  }
+}
 
-    __syncwarp();  // the previous item is done reading code/cvals
-    const Decoded dec = decode_program(p.programs + (size_t)prog * p.Lmax, p.lengths[prog],
-                                       p.Lmax, p.nvars, p.K, code, lane);
-    if (lane == 0 && c == 0) p.flags[prog] = dec.flags;
-    const int cbeg = c * p.chunk;
-    const int cend = min(p.N, cbeg + p.chunk);
+// ---------------------------------------------------------------- many problems, one launch
+constexpr int MAX_BATCH = 64;
 
-    if (dec.flags) {
-      if (MODE == MODE_PREDICT) {
-        float *row = p.yhat + (size_t)prog * p.ldy;
-        for (int i = cbeg + lane; i < cend; i += 32) row[i] = __int_as_float(0x7fc00000);
-      }
-      continue;
+struct BatchProblem {
+  const uint8_t *programs;
+  const int32_t *lengths;
+  const float *consts;
+  const float *X;
+  const float *y;
+  float *yc;           // centred target (1 - r^2), padded
+  double *partials;    // [P * nchunks][PSTRIDE]
+  int32_t *flags;      // [P]
+  double *fitness;     // [P] or [2][P]
+  double *ychunk;      // [nchunks][2]
+  double *stats;       // [8]
+  long long ldx;
+  long long item_begin;  // first work item of this problem in the launch
+  int P, Lmax, K, nvars, N, chunk, nchunks;
+  int mode;            // MODE_MSE, MODE_CORR or MODE_BOTH
+  int corr_chunk_begin;  // first block of this problem in the batched centring launch (-1: none)
+};
+
+struct BatchParams {
+  BatchProblem prob[MAX_BATCH];
+  int nprob;
+  int corr_list[MAX_BATCH];  // problems that need the centred target, in order
+  int ncorr;
+  long long total_items;
+  unsigned long long *queue;
+  float4 *deep_stack;
+  int deep_slots;
+  int warp_bytes;
+};
+
+// Work items of every problem come from one atomic counter: problem q owns
+// items [item_begin_q, item_begin_q + P_q * nchunks_q), chunk-major inside.
+__global__ void __launch_bounds__(WARPS * 32) eval_batched_kernel(const __grid_constant__ BatchParams b) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const WarpSmem w = warp_smem(smem, warp, b.warp_bytes, b.deep_stack, b.deep_slots);
+  for (;;) {
+    unsigned long long item = 0;
+    if (lane == 0) item = atomicAdd(b.queue, 1ull);
+    item = __shfl_sync(FULL, item, 0);
+    if ((long long)item >= b.total_items) break;
+    int lo = 0, hi = b.nprob - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (b.prob[mid].item_begin <= (long long)item) lo = mid;
+      else hi = mid - 1;
     }
-    if (lane < p.K) cvals[lane] = p.consts[(size_t)prog * p.K + lane];
-    __syncwarp();
-
-    float4 *stk = (dec.maxd - 1 <= DSM) ? stk_s + lane : stk_g + lane;
-    const int last_group = (cend - 1) & ~3;
-
-    Kahan se, s1, s2, s3;
-    float shift = 0.f;
-    for (int base = cbeg; base < cend; base += STEP) {
-      const int c0 = base + 4 * lane;
-      const int cl = c0 < cend ? c0 : last_group;  // clamped, always readable
-      const float4 T = interpret(code, dec.n, cvals, stk, p.X, p.ldx, cl);
-      const bool v0 = c0 < cend, v1 = c0 + 1 < cend, v2 = c0 + 2 < cend, v3 = c0 + 3 < cend;
-      if (MODE == MODE_PREDICT) {
-        float *row = p.yhat + (size_t)prog * p.ldy;
-        if (v0) row[c0] = T.x;
-        if (v1) row[c0 + 1] = T.y;
-        if (v2) row[c0 + 2] = T.z;
-        if (v3) row[c0 + 3] = T.w;
-      }
-      if (MODE == MODE_MSE || MODE == MODE_BOTH) {
-        const float4 yv = load_y4(p.y, cl, p.N);
-        const float e0 = sel(v0, T.x - yv.x), e1 = sel(v1, T.y - yv.y);
-        const float e2 = sel(v2, T.z - yv.z), e3 = sel(v3, T.w - yv.w);
-        se.add((e0 * e0 + e1 * e1) + (e2 * e2 + e3 * e3));
-      }
-      if (MODE == MODE_CORR || MODE == MODE_BOTH) {
-        if (base == cbeg) shift = __shfl_sync(FULL, T.x, 0);
-        const float4 yv = ldx4(p.yc + cl);
-        const float d0 = sel(v0, T.x - shift), d1 = sel(v1, T.y - shift);
-        const float d2 = sel(v2, T.z - shift), d3 = sel(v3, T.w - shift);
-        s1.add((d0 + d1) + (d2 + d3));
-        s2.add((d0 * d0 + d1 * d1) + (d2 * d2 + d3 * d3));
-        s3.add((d0 * yv.x + d1 * yv.y) + (d2 * yv.z + d3 * yv.w));
-      }
-    }
-    if (MODE != MODE_PREDICT) {
-      double *rec = p.partials + ((size_t)prog * p.nchunks + c) * PSTRIDE;
-      if (MODE == MODE_MSE || MODE == MODE_BOTH) {
-        const double v = warp_sum(se.value());
-        if (lane == 0) rec[0] = v;
-      }
-      if (MODE == MODE_CORR || MODE == MODE_BOTH) {
-        const double a = warp_sum(s1.value());
-        const double b = warp_sum(s2.value());
-        const double d = warp_sum(s3.value());
-        if (lane == 0) {
-          rec[1] = (double)shift;
-          rec[2] = a;
-          rec[3] = b;
-          rec[4] = d;
-        }
-      }
-    }
+    const BatchProblem &q = b.prob[lo];
+    EvalParams p;
+    p.programs = q.programs;
+    p.lengths = q.lengths;
+    p.consts = q.consts;
+    p.P = q.P;
+    p.Lmax = q.Lmax;
+    p.K = q.K;
+    p.X = q.X;
+    p.y = q.y;
+    p.yc = q.yc;
+    p.nvars = q.nvars;
+    p.N = q.N;
+    p.ldx = q.ldx;
+    p.chunk = q.chunk;
+    p.nchunks = q.nchunks;
+    p.partials = q.partials;
+    p.flags = q.flags;
+    const long long local = (long long)item - q.item_begin;
+    const int c = (int)(local / q.P);
+    const int prog = (int)(local % q.P);
+    const int want = q.mode == MODE_MSE ? 1 : (q.mode == MODE_CORR ? 2 : 3);
+    eval_item<MODE_BOTH>(p, c, prog, w, lane, want);
   }
 }
 
@@ -414,6 +517,42 @@ struct FinalParams {
   double *fitness;  // [P] or [2][P]
 };
 
+// 1 - r^2 of one program from its chunk records.
+// chunk c: n_c cases, shift s_c, S1 = sum d, S2 = sum d^2, S3 = sum d yc with
+// d = yhat - s_c.  Chunk mean m_c = s_c + S1/n_c, chunk M2 = S2 - S1^2/n_c;
+// merged (Chan et al.): Shh = sum M2_c + n_c (m_c - m)^2.
+// sum yhat*yc = sum (S3_c + s_c Yc_c); Shy = that - m * Y1; Syy = Y2 - Y1^2/N.
+__device__ double corr_fitness(const double *rec, const double *ychunk, int Nc, int chunk,
+                               int nchunks) {
+  const double N = (double)Nc;
+  double y1 = 0.0, y2 = 0.0, tot = 0.0;
+  for (int c = 0; c < nchunks; ++c) {
+    y1 += ychunk[2 * c];
+    y2 += ychunk[2 * c + 1];
+    const double nc = (double)min(chunk, Nc - c * chunk);
+    tot += nc * rec[c * PSTRIDE + 1] + rec[c * PSTRIDE + 2];
+  }
+  const double m = tot / N;
+  double shh = 0.0, g = 0.0;
+  for (int c = 0; c < nchunks; ++c) {
+    const double nc = (double)min(chunk, Nc - c * chunk);
+    const double s = rec[c * PSTRIDE + 1], a = rec[c * PSTRIDE + 2];
+    const double b = rec[c * PSTRIDE + 3], d = rec[c * PSTRIDE + 4];
+    const double mc = s + a / nc;
+    shh += (b - a * a / nc) + nc * (mc - m) * (mc - m);
+    g += d + s * ychunk[2 * c];
+  }
+  const double shy = g - m * y1;
+  const double syy = y2 - y1 * y1 / N;
+  double fit = 1.0;
+  if (isfinite(shh) && isfinite(shy) && isfinite(syy) && shh > 0.0 && syy > 0.0 && Nc >= 2) {
+    const double r2 = (shy * shy) / (syy * shh);
+    fit = 1.0 - r2;
+    fit = fit < 0.0 ? 0.0 : (fit > 1.0 ? 1.0 : fit);
+  }
+  return fit;
+}
+
 template <int MODE>
 __global__ void finalize_kernel(FinalParams f) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -433,37 +572,72 @@ __global__ void finalize_kernel(FinalParams f) {
     for (int c = 0; c < f.nchunks; ++c) se += rec[c * PSTRIDE];
     mse_out[p] = isfinite(se) ? se / N : INF;
   }
-  if (MODE == MODE_CORR || MODE == MODE_BOTH) {
-    // chunk c: n_c cases, shift s_c, S1 = sum d, S2 = sum d^2, S3 = sum d yc
-    // with d = yhat - s_c.  Chunk mean m_c = s_c + S1/n_c, chunk M2 =
-    // S2 - S1^2/n_c; merged (Chan et al.): Shh = sum M2_c + n_c (m_c - m)^2.
-    // sum yhat*yc = sum (S3_c + s_c Yc_c); Shy = that - m * Y1; Syy = Y2 - Y1^2/N.
-    double y1 = 0.0, y2 = 0.0, tot = 0.0;
-    for (int c = 0; c < f.nchunks; ++c) {
-      y1 += f.ychunk[2 * c];
-      y2 += f.ychunk[2 * c + 1];
-      const double nc = (double)min(f.chunk, f.N - c * f.chunk);
-      tot += nc * rec[c * PSTRIDE + 1] + rec[c * PSTRIDE + 2];
+  if (MODE == MODE_CORR || MODE == MODE_BOTH)
+    corr_out[p] = corr_fitness(rec, f.ychunk, f.N, f.chunk, f.nchunks);
+}
+
+// ---------------------------------------------------------------- batched prep / finalize
+// one block per problem that needs the centred target: its FP64 mean
+__global__ void __launch_bounds__(PREP_THREADS) ymean_batched_kernel(const __grid_constant__ BatchParams b) {
+  __shared__ double red[PREP_THREADS / 32];
+  const BatchProblem &q = b.prob[b.corr_list[blockIdx.x]];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < q.N; i += blockDim.x) s += (double)q.y[i];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) q.stats[0] = s / (double)q.N;
+}
+
+// one block per (problem, chunk): centred target and its chunk sums
+__global__ void __launch_bounds__(PREP_THREADS) ycenter_batched_kernel(const __grid_constant__ BatchParams b) {
+  __shared__ double red[PREP_THREADS / 32];
+  int r = 0;
+  while (r + 1 < b.ncorr && b.prob[b.corr_list[r + 1]].corr_chunk_begin <= (int)blockIdx.x) ++r;
+  const BatchProblem &q = b.prob[b.corr_list[r]];
+  const int c = (int)blockIdx.x - q.corr_chunk_begin;
+  const double ybar = q.stats[0];
+  const int beg = c * q.chunk, end = min(q.N, beg + q.chunk);
+  double a = 0.0, bb = 0.0;
+  for (int i = beg + threadIdx.x; i < end; i += blockDim.x) {
+    const float v = (float)((double)q.y[i] - ybar);
+    q.yc[i] = v;
+    a += (double)v;
+    bb += (double)v * (double)v;
+  }
+  if (c == q.nchunks - 1) {
+    const int padded = (q.N + STEP - 1) / STEP * STEP;
+    for (int i = q.N + threadIdx.x; i < padded; i += blockDim.x) q.yc[i] = 0.0f;
+  }
+  a = block_sum(a, red);
+  bb = block_sum(bb, red);
+  if (threadIdx.x == 0) {
+    q.ychunk[2 * c] = a;
+    q.ychunk[2 * c + 1] = bb;
+  }
+}
+
+// one block per problem, threads over its programs
+__global__ void finalize_batched_kernel(const __grid_constant__ BatchParams b) {
+  const BatchProblem &q = b.prob[blockIdx.x];
+  FinalParams f{q.partials, q.flags, q.ychunk, q.P, q.N, q.chunk, q.nchunks, q.fitness};
+  for (int p0 = 0; p0 < q.P; p0 += blockDim.x) {
+    const int p = p0 + threadIdx.x;
+    if (p >= q.P) break;
+    const double INF = __longlong_as_double(0x7ff0000000000000ll);
+    double *mse_out = f.fitness;
+    double *corr_out = q.mode == MODE_BOTH ? f.fitness + f.P : f.fitness;
+    if (f.flags[p]) {
+      if (q.mode != MODE_CORR) mse_out[p] = INF;
+      if (q.mode != MODE_MSE) corr_out[p] = INF;
+      continue;
     }
-    const double m = tot / N;
-    double shh = 0.0, g = 0.0;
-    for (int c = 0; c < f.nchunks; ++c) {
-      const double nc = (double)min(f.chunk, f.N - c * f.chunk);
-      const double s = rec[c * PSTRIDE + 1], a = rec[c * PSTRIDE + 2];
-      const double b = rec[c * PSTRIDE + 3], d = rec[c * PSTRIDE + 4];
-      const double mc = s + a / nc;
-      shh += (b - a * a / nc) + nc * (mc - m) * (mc - m);
-      g += d + s * f.ychunk[2 * c];
+    const double *rec = f.partials + (size_t)p * f.nchunks * PSTRIDE;
+    const double N = (double)f.N;
+    if (q.mode != MODE_CORR) {
+      double se = 0.0;
+      for (int c = 0; c < f.nchunks; ++c) se += rec[c * PSTRIDE];
+      mse_out[p] = isfinite(se) ? se / N : INF;
     }
-    const double shy = g - m * y1;
-    const double syy = y2 - y1 * y1 / N;
-    double fit = 1.0;
-    if (isfinite(shh) && isfinite(shy) && isfinite(syy) && shh > 0.0 && syy > 0.0 && f.N >= 2) {
-      const double r2 = (shy * shy) / (syy * shh);
-      fit = 1.0 - r2;
-      fit = fit < 0.0 ? 0.0 : (fit > 1.0 ? 1.0 : fit);
-    }
-    corr_out[p] = fit;
+    if (q.mode != MODE_MSE) corr_out[p] = corr_fitness(rec, f.ychunk, f.N, f.chunk, f.nchunks);
   }
 }
 
@@ -510,6 +684,7 @@ sr_status make_plan(sr_ctx *ctx, int mode, int P, int Lmax, int N, Plan *pl) {
   const int max_chunks = (N + 1023) / 1024;
   nch = nch < 1 ? 1 : (nch > max_chunks ? max_chunks : nch);
   int chunk = (N + nch - 1) / nch;
+  if (ctx->tile_cases > 0) chunk = ctx->tile_cases;  // autotuned cases per work item
   chunk = (chunk + STEP - 1) / STEP * STEP;
   pl->chunk = chunk;
   pl->nchunks = (N + chunk - 1) / chunk;
@@ -614,6 +789,178 @@ sr_status launch_eval(sr_ctx *ctx, int mode, const uint8_t *programs, const int3
   return SR_OK;
 }
 
+// ---------------------------------------------------------------- batched host side
+struct BatchPlan {
+  int grid, smem, deep_slots, maxL;
+};
+
+sr_status batched_grid(sr_ctx *ctx, int smem, int *grid) {
+  static int configured = 0;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(eval_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         227 * 1024);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute(eval_batched_kernel)");
+    configured = 1;
+  }
+  int nb = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_batched_kernel, WARPS * 32, smem);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  if (nb < 1) return fail(ctx, SR_EINVAL, "Lmax too large for shared memory");
+  *grid = nb * ctx->num_sms;
+  return SR_OK;
+}
+
+int mode_of(sr_fitness_kind k) {
+  return k == SR_MSE ? MODE_MSE : (k == SR_CORR ? MODE_CORR : MODE_BOTH);
+}
+
+sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
+  SR_CHECK_CUDA(ctx, cudaSetDevice(ctx->device));
+  int maxL = 1;
+  double work = 0.0;
+  for (int i = 0; i < nprob; ++i) {
+    const sr_problem &q = pr[i];
+    sr_status st = check_common(ctx, q.programs, q.lengths, q.consts, q.P, q.Lmax, q.K, q.X, q.nvars,
+                                q.N, q.ldx);
+    if (st != SR_OK) return fail(ctx, st, "problem %d: %s", i, ctx->msg);
+    if (q.kind != SR_MSE && q.kind != SR_CORR && q.kind != SR_MSE_CORR)
+      return fail(ctx, SR_EINVAL, "problem %d: unknown fitness kind", i);
+    if (q.P > 0 && (!q.y || !q.fitness || (((uintptr_t)q.y) & 15)))
+      return fail(ctx, SR_EINVAL, "problem %d: y NULL or not 16-byte aligned, or fitness NULL", i);
+    if (q.cases_per_tile < 0) return fail(ctx, SR_EINVAL, "problem %d: cases_per_tile < 0", i);
+    maxL = q.Lmax > maxL ? q.Lmax : maxL;
+    work += (double)q.P * (double)q.N;
+  }
+  BatchPlan bp;
+  bp.maxL = maxL;
+  bp.smem = WARPS * warp_smem_bytes(maxL);
+  sr_status st = batched_grid(ctx, bp.smem, &bp.grid);
+  if (st != SR_OK) return st;
+  const long long warps = (long long)bp.grid * WARPS;
+  const double want = (double)warps * TARGET_ITEMS_PER_WARP;
+  const int max_depth = (maxL + 1) / 2;
+  bp.deep_slots = max_depth - 1 > DSM ? max_depth - 1 : 0;
+
+  // chunking per problem: items in proportion to its share of the work
+  std::vector<int> chunk(nprob), nch(nprob), order;
+  for (int i = 0; i < nprob; ++i) {
+    const sr_problem &q = pr[i];
+    if (q.P == 0) continue;
+    int c;
+    if (q.cases_per_tile > 0) {
+      c = q.cases_per_tile;
+    } else {
+      const double share = want * ((double)q.P * (double)q.N) / (work > 0 ? work : 1.0);
+      int n = (int)ceil(share / q.P);
+      const int max_chunks = (q.N + 1023) / 1024;
+      n = n < 1 ? 1 : (n > max_chunks ? max_chunks : n);
+      c = (q.N + n - 1) / n;
+    }
+    c = (c + STEP - 1) / STEP * STEP;
+    chunk[i] = c;
+    nch[i] = (q.N + c - 1) / c;
+    order.push_back(i);
+  }
+  // longest items first (cases per item x longest program), so the tail of
+  // the launch is made of short items
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return (double)chunk[a] * pr[a].Lmax > (double)chunk[b] * pr[b].Lmax;
+  });
+
+  // workspace: the largest group decides (all groups reuse it in turn)
+  auto group_bytes = [&](size_t g0, size_t g1, BatchParams *bpar) -> size_t {
+    Carver cv;
+    const size_t off_q = cv.take(256);
+    const size_t off_deep = cv.take((size_t)warps * bp.deep_slots * 32 * 16);
+    long long items = 0;
+    int corr_chunks = 0, ncorr = 0;
+    for (size_t g = g0; g < g1; ++g) {
+      const int i = order[g];
+      const sr_problem &q = pr[i];
+      const int mode = mode_of(q.kind);
+      const size_t off_f = q.prog_flags ? 0 : cv.take((size_t)q.P * 4);
+      const size_t off_p = cv.take((size_t)q.P * nch[i] * PSTRIDE * 8);
+      size_t off_yc = 0, off_ych = 0, off_st = 0;
+      const bool corr = mode != MODE_MSE;
+      if (corr) {
+        off_yc = cv.take(align_up((size_t)q.N, STEP) * 4);
+        off_ych = cv.take((size_t)nch[i] * 16);
+        off_st = cv.take(64);
+      }
+      if (bpar) {
+        BatchProblem &b = bpar->prob[g - g0];
+        char *ws = ctx->ws;
+        b.programs = q.programs;
+        b.lengths = q.lengths;
+        b.consts = q.consts;
+        b.X = q.X;
+        b.y = q.y;
+        b.yc = corr ? reinterpret_cast<float *>(ws + off_yc) : nullptr;
+        b.partials = reinterpret_cast<double *>(ws + off_p);
+        b.flags = q.prog_flags ? q.prog_flags : reinterpret_cast<int32_t *>(ws + off_f);
+        b.fitness = q.fitness;
+        b.ychunk = corr ? reinterpret_cast<double *>(ws + off_ych) : nullptr;
+        b.stats = corr ? reinterpret_cast<double *>(ws + off_st) : nullptr;
+        b.ldx = q.ldx;
+        b.item_begin = items;
+        b.P = q.P;
+        b.Lmax = q.Lmax;
+        b.K = q.K;
+        b.nvars = q.nvars;
+        b.N = q.N;
+        b.chunk = chunk[i];
+        b.nchunks = nch[i];
+        b.mode = mode;
+        b.corr_chunk_begin = corr ? corr_chunks : -1;
+        if (corr) bpar->corr_list[ncorr] = (int)(g - g0);
+      }
+      items += (long long)q.P * nch[i];
+      if (corr) {
+        corr_chunks += nch[i];
+        ++ncorr;
+      }
+    }
+    if (bpar) {
+      bpar->nprob = (int)(g1 - g0);
+      bpar->ncorr = ncorr;
+      bpar->total_items = items;
+      bpar->queue = reinterpret_cast<unsigned long long *>(ctx->ws + off_q);
+      bpar->deep_stack = bp.deep_slots ? reinterpret_cast<float4 *>(ctx->ws + off_deep) : nullptr;
+      bpar->deep_slots = bp.deep_slots;
+      bpar->warp_bytes = warp_smem_bytes(maxL);
+    }
+    return cv.off;
+  };
+  size_t need = 0;
+  for (size_t g0 = 0; g0 < order.size(); g0 += MAX_BATCH) {
+    const size_t g1 = std::min(order.size(), g0 + MAX_BATCH);
+    need = std::max(need, group_bytes(g0, g1, nullptr));
+  }
+  if (order.empty()) return SR_OK;
+  st = ensure_workspace(ctx, need);
+  if (st != SR_OK) return st;
+
+  cudaStream_t s = ctx->stream;
+  for (size_t g0 = 0; g0 < order.size(); g0 += MAX_BATCH) {
+    const size_t g1 = std::min(order.size(), g0 + MAX_BATCH);
+    BatchParams b;
+    group_bytes(g0, g1, &b);
+    int corr_blocks = 0;
+    for (int r = 0; r < b.ncorr; ++r) corr_blocks += b.prob[b.corr_list[r]].nchunks;
+    SR_CHECK_CUDA(ctx, cudaMemsetAsync(b.queue, 0, sizeof(unsigned long long), s));
+    if (b.ncorr > 0) {
+      ymean_batched_kernel<<<b.ncorr, PREP_THREADS, 0, s>>>(b);
+      ycenter_batched_kernel<<<corr_blocks, PREP_THREADS, 0, s>>>(b);
+      ctx->launches += 2;
+    }
+    eval_batched_kernel<<<bp.grid, WARPS * 32, bp.smem, s>>>(b);
+    finalize_batched_kernel<<<b.nprob, 256, 0, s>>>(b);
+    SR_CHECK_CUDA(ctx, cudaGetLastError());
+    ctx->launches += 2;
+  }
+  return SR_OK;
+}
+
 }  // namespace
 }  // namespace sr
 
@@ -645,6 +992,20 @@ sr_status sr_predict(sr_ctx *ctx, const uint8_t *programs, const int32_t *length
   if (!yhat || ldy < N) return fail(ctx, SR_EINVAL, "yhat NULL or ldy < N");
   return launch_eval(ctx, MODE_PREDICT, programs, lengths, consts, P, Lmax, K, X, nullptr, nvars,
                      N, ldx, nullptr, prog_flags, yhat, ldy);
+}
+
+sr_status sr_eval_batched(sr_ctx *ctx, const sr_problem *problems, int nprob) {
+  using namespace sr;
+  if (!ctx) return SR_EINVAL;
+  if (nprob < 0 || (nprob > 0 && !problems)) return fail(ctx, SR_EINVAL, "bad problem list");
+  if (nprob == 0) return SR_OK;
+  return launch_batched(ctx, problems, nprob);
+}
+
+sr_status sr_set_tile(sr_ctx *ctx, int cases_per_tile) {
+  if (!ctx || cases_per_tile < 0) return SR_EINVAL;
+  ctx->tile_cases = cases_per_tile;
+  return SR_OK;
 }
 
 sr_status sr_reserve(sr_ctx *ctx, int P, int Lmax, int N) {

@@ -43,16 +43,24 @@ __device__ __forceinline__ Word4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
 
 struct Rng {
   uint32_t k0, k1, gen;
+  const uint64_t *gen_dev;  // when set, the generation is *gen_dev + gen (read on the device)
   __device__ __forceinline__ Word4 draw(uint32_t d, uint32_t indiv, uint32_t purpose) const {
     return philox(d, indiv, purpose, gen, k0, k1);
   }
+  __device__ __forceinline__ Rng resolved() const {
+    Rng r = *this;
+    if (gen_dev) r.gen = (uint32_t)(*gen_dev + (uint64_t)gen);
+    r.gen_dev = nullptr;
+    return r;
+  }
 };
 
-inline Rng make_rng(uint64_t seed, uint64_t gen) {
+inline Rng make_rng(uint64_t seed, uint64_t gen, const uint64_t *gen_dev = nullptr) {
   Rng r;
   r.k0 = (uint32_t)seed;
   r.k1 = (uint32_t)(seed >> 32);
   r.gen = (uint32_t)gen;
+  r.gen_dev = gen_dev;
   return r;
 }
 
@@ -103,10 +111,11 @@ __global__ void philox_kernel(const uint32_t *__restrict__ ctr, uint32_t k0, uin
   for (int j = 0; j < 4; ++j) out[4 * i + j] = w.v[j];
 }
 
-__global__ void tournament_kernel(const double *__restrict__ fitness, int P, int k, Rng rng,
+__global__ void tournament_kernel(const double *__restrict__ fitness, int P, int k, Rng rng_in,
                                   int32_t *__restrict__ parents) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 2 * P) return;
+  const Rng rng = rng_in.resolved();
   const int i = t >> 1, s = t & 1;
   const double INF = __longlong_as_double(0x7ff0000000000000ll);
   int best = -1;
@@ -141,6 +150,7 @@ struct VaryParams {
 __global__ void vary_kernel(VaryParams p) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= p.P) return;
+  p.rng = p.rng.resolved();
   // out-of-range parents and lengths are clamped so that no access leaves
   // the buffers (valid inputs are unaffected)
   const int ia = min(max(p.parents[2 * i], 0), p.P - 1);
@@ -292,8 +302,8 @@ sr_status sr_select_tournament(sr_ctx *ctx, const double *fitness, int P, int k,
   if (P == 0) return SR_OK;
   if (!fitness || !parents) return fail(ctx, SR_EINVAL, "NULL fitness or parents");
   SR_CHECK_CUDA(ctx, cudaSetDevice(ctx->device));
-  tournament_kernel<<<(2 * P + 255) / 256, 256, 0, ctx->stream>>>(fitness, P, k, make_rng(seed, gen),
-                                                                    parents);
+  tournament_kernel<<<(2 * P + 255) / 256, 256, 0, ctx->stream>>>(
+      fitness, P, k, make_rng(seed, gen, ctx->gen_dev), parents);
   SR_CHECK_CUDA(ctx, cudaGetLastError());
   ctx->launches += 1;
   return SR_OK;
@@ -313,10 +323,16 @@ sr_status sr_vary(sr_ctx *ctx, const uint8_t *prog_in, const int32_t *len_in, co
   if (prog_in == prog_out) return fail(ctx, SR_EINVAL, "prog_out must not alias prog_in");
   SR_CHECK_CUDA(ctx, cudaSetDevice(ctx->device));
   VaryParams vp{prog_in, len_in, c_in, parents, prog_out, len_out, c_out, P, Lmax, K, nvars, *cfg,
-                make_rng(seed, gen)};
+                make_rng(seed, gen, ctx->gen_dev)};
   vary_kernel<<<(P + 127) / 128, 128, 0, ctx->stream>>>(vp);
   SR_CHECK_CUDA(ctx, cudaGetLastError());
   ctx->launches += 1;
+  return SR_OK;
+}
+
+sr_status sr_set_generation_source(sr_ctx *ctx, const uint64_t *gen_dev) {
+  if (!ctx) return SR_EINVAL;
+  ctx->gen_dev = gen_dev;
   return SR_OK;
 }
 
