@@ -62,9 +62,10 @@ def test_const_opt_inside_graph(ctx):
     cfg = EvolveConfig(const_steps=5, eval_kind=binding.SR_MSE, select_kind=binding.SR_MSE)
     eager = Evolver(ctx, [_pop(31, P=128, cfg=cfg)])
     graph = Evolver(ctx, [_pop(31, P=128, cfg=cfg)])
-    for _ in range(3):
+    for _ in range(5):
         eager.step()
-    graph.capture(2)
+    graph.capture(2)          # one eager generation, two captured
+    graph.run(4)              # two replays
     torch.cuda.synchronize()
     _same(_state(eager.pops), _state(graph.pops))
 
