@@ -75,6 +75,9 @@ typedef enum { SR_MSE = 0, SR_CORR = 1, SR_MSE_CORR = 2 } sr_fitness_kind;
 #define SR_PF_BAD_CONST 8  /* constant index >= K                           */
 #define SR_PF_UNDERFLOW 16 /* depth after some token below 1                */
 #define SR_PF_BAD_FINAL 32 /* depth after the last token is not 1           */
+#define SR_PF_TOO_DEEP 64  /* evaluation would need more than 9 live values;
+                              cannot happen for valid programs of up to
+                              SR_MAX_LMAX tokens (reported, never evaluated) */
 
 #define SR_MAX_LMAX 512  /* largest supported Lmax                           */
 #define SR_MAX_VARS 16

@@ -1,29 +1,35 @@
 // sr_eval.cu -- population evaluation: the postfix interpreter with fused
-// MSE / 1 - r^2 reductions (sr_eval) and the raw program outputs (sr_predict).
+// MSE / 1 - r^2 reductions (sr_eval, sr_eval_batched) and the raw program
+// outputs (sr_predict).
 //
 // Paper: all genomes of a generation go to the GPU together, each runs a
 // batch of fitness cases and one aggregate per genome comes back (Sec.
 // 2.1.2); genomes are RPN programs (Sec. 2.1.4); correlation fitness is r of
 // Eq. 1, scored here as 1 - r^2 (Sec. 2.1.5).
 //
-// Layout on the device
-//   - A work item is (case chunk c, program p).  Items are handed out
-//     chunk-major by an atomic counter to single warps of a persistent grid,
-//     so warps running at the same time read the same X columns (L1/L2 hits)
-//     and short and long programs balance out dynamically.
-//   - A warp decodes its program once per item (warp-parallel scan of the
-//     stack effects: validation, stack slots, max depth) into shared memory,
-//     then interprets it with lanes over cases, 4 cases per lane (one float4
-//     of each X row), 128 cases per step.  The op stream is warp-uniform:
-//     no divergence.
-//   - Top of stack lives in registers; the rest of the stack in per-warp
-//     shared memory slots [slot][lane] (conflict-free float4), or in global
-//     scratch for programs deeper than the shared slots.
-//   - A terminal followed by a binary op is fused into one instruction
-//     "top = top op terminal" (no push, no pop).
-//   - Per lane, FP32 Kahan-compensated sums over the item's cases; then FP64
-//     warp reduction; one FP64 partial per (program, chunk); a finalize
-//     kernel merges the chunks of each program in a fixed order.
+// Design on the device
+//   1. Decode pre-pass, one thread per program: validation, then the
+//      expression tree is rescheduled Sethi-Ullman style -- at every binary
+//      node the child that needs more stack is evaluated first (a reversed
+//      opcode keeps a - b and a / b exact when the right child goes first).
+//      The stack depth of any program is then at most floor(log2(leaves)) + 1
+//      (9 for 512 tokens), so a fixed 8 shared-memory slots always suffice.
+//      A terminal evaluated second is fused into its binary operator
+//      ("top = top op x_j"), and every operand is resolved here (constant
+//      value, X row offset, stack-slot byte offset): the interpreter does no
+//      per-token address or index arithmetic.  Values are bit-identical to
+//      plain left-to-right evaluation (same operation on the same operands).
+//   2. Evaluation, persistent grid: a work item is (case chunk, program),
+//      handed out chunk-major by one atomic counter to single warps, so
+//      warps running together share X columns in L1/L2 and uneven program
+//      lengths balance out.  The warp copies the program's code into shared
+//      memory and interprets it with lanes over cases, 8 cases per lane (two
+//      float4 per operand), 256 cases per step; the op stream is
+//      warp-uniform (no divergence).  Top of stack in registers, the slots
+//      below in shared memory [slot][half][lane] (conflict-free float4).
+//   3. Per lane, FP32 Kahan-compensated sums over the item's cases; FP64 warp
+//      reduction; one FP64 partial per (program, chunk); a finalize kernel
+//      merges the chunks of each program in a fixed order.
 #include <math.h>
 #include <stdio.h>
 
@@ -35,38 +41,50 @@
 namespace sr {
 namespace {
 
-constexpr int WARPS = 8;        // warps per CTA
-constexpr int STEP = 128;       // cases per warp step (32 lanes x float4)
-constexpr int DSM = 16;         // stack slots below the top kept in shared memory
+constexpr int WARPS = 4;        // warps per CTA
+constexpr int CPL = 8;          // cases per lane per dispatched instruction (two float4)
+constexpr int STEP = 32 * CPL;  // cases per warp step
+constexpr int SLOT_BYTES = 32 * CPL * 4;  // one stack slot of a warp: [2][32 lanes] float4
+// stack slots below the top: the Sethi-Ullman schedule needs at most
+// floor(log2(SR_MAX_LMAX / 2)) + 1 values live, i.e. 8 slots below the top
+constexpr int DSM = 8;
+static_assert(SR_MAX_LMAX <= 512, "DSM = 8 covers programs of up to 512 tokens");
 constexpr int PSTRIDE = 8;      // doubles per partial record
 constexpr int TARGET_ITEMS_PER_WARP = 8;
 
 enum Mode { MODE_PREDICT = 0, MODE_MSE = 1, MODE_CORR = 2, MODE_BOTH = 3 };
 
-// decoded instruction: bits 0..7 opcode, 8..15 operand index, 16..31 slot
+// decoded instruction (uint2): x = opcode | stack-slot byte offset << 8;
+// y = operand: the constant's FP32 bits, or the variable's row offset j * ldx
 enum Op : uint32_t {
-  OP_LDV = 0,   // top = x_j                      (first token, empty stack)
+  OP_LDV = 0,   // top = x_j                        (stack empty)
   OP_LDC,       // top = c_k
   OP_PUSHV,     // stack[slot] = top; top = x_j
   OP_PUSHC,     // stack[slot] = top; top = c_k
-  OP_ADD,       // top = stack[slot] op top
+  OP_ADD,       // top = stack[slot] op top         (left operand evaluated first)
   OP_SUB,
   OP_MUL,
   OP_DIV,
+  OP_RSUB,      // top = top - stack[slot]          (right operand evaluated first)
+  OP_RDIV,      // top = top / stack[slot]
   OP_SIN,       // top = f(top)
   OP_COS,
   OP_EXP,
   OP_LOG,
   OP_SQRT,
   OP_SQ,
-  OP_VADD,      // top = top op x_j   (terminal fused with the binary op after it)
+  OP_VADD,      // top = top op x_j   (terminal right operand, evaluated second)
   OP_VSUB,
   OP_VMUL,
   OP_VDIV,
+  OP_VRSUB,     // top = x_j - top    (terminal left operand, evaluated second)
+  OP_VRDIV,     // top = x_j / top
   OP_CADD,      // top = top op c_k
   OP_CSUB,
   OP_CMUL,
   OP_CDIV,
+  OP_CRSUB,     // top = c_k - top
+  OP_CRDIV,     // top = c_k / top
 };
 
 struct EvalParams {
@@ -83,17 +101,20 @@ struct EvalParams {
   long long total_items;
   double *partials;        // [P * nchunks][PSTRIDE]
   int32_t *flags;          // [P]
+  uint2 *code;             // [P][Lmax] decoded instructions
+  int32_t *ncode;          // [P]
+  int16_t *s_start;        // decode scratch [P][Lmax]: first token of each subtree
+  uint8_t *s_need;         // decode scratch [P][Lmax]: stack need of each subtree
+  int16_t *s_task;         // decode scratch [P][Lmax]: work stack
   unsigned long long *queue;
   float *yhat;             // predict: [P][ldy]
   long long ldy;
-  float4 *deep_stack;      // per warp: deep_slots * 32 float4
-  int deep_slots;
   int warp_bytes;          // shared memory per warp
 };
 
 __host__ __device__ inline int warp_smem_bytes(int Lmax) {
-  // stack slots | 16 constants | decoded code
-  return DSM * 32 * 16 + 64 + ((Lmax * 4 + 15) / 16) * 16;
+  // stack slots | decoded code (8 bytes per token)
+  return DSM * SLOT_BYTES + ((Lmax * 8 + 15) / 16) * 16;
 }
 
 // ---------------------------------------------------------------- operators
@@ -116,6 +137,22 @@ __device__ __forceinline__ float f_add(float a, float b) { return a + b; }
 __device__ __forceinline__ float f_sub(float a, float b) { return a - b; }
 __device__ __forceinline__ float f_mul(float a, float b) { return a * b; }
 __device__ __forceinline__ float f_sqrt(float x) { return sqrtf(fabsf(x)); }
+
+// sinf / cosf carry a long path for large arguments; keep one out-of-line
+// copy of it and let the inlined copies assume a moderate argument (NaN and
+// +-inf also take the out-of-line call)
+__device__ __noinline__ float sin_wide(float x) { return sinf(x); }
+__device__ __noinline__ float cos_wide(float x) { return cosf(x); }
+__device__ __forceinline__ float f_sin(float x) {
+  if (!(fabsf(x) <= 4.0e4f)) return sin_wide(x);
+  __builtin_assume(fabsf(x) <= 4.0e4f);
+  return sinf(x);
+}
+__device__ __forceinline__ float f_cos(float x) {
+  if (!(fabsf(x) <= 4.0e4f)) return cos_wide(x);
+  __builtin_assume(fabsf(x) <= 4.0e4f);
+  return cosf(x);
+}
 __device__ __forceinline__ float f_sq(float x) { return x * x; }
 
 __device__ __forceinline__ float4 splat(float c) { return make_float4(c, c, c, c); }
@@ -123,114 +160,266 @@ __device__ __forceinline__ float4 ldx4(const float *p) {
   return __ldg(reinterpret_cast<const float4 *>(p));
 }
 
-// ---------------------------------------------------------------- decode
-struct Decoded {
-  int n;      // instructions
-  int maxd;   // largest stack depth
-  int flags;  // SR_PF_* bits
-};
+// ---------------------------------------------------------------- decode pre-pass
+__device__ __forceinline__ bool is_term(int v) {
+  const int c = tok_class(v);
+  return c == CLS_VAR || c == CLS_CONST;
+}
 
-// Warp-cooperative validation and decoding of one program into `code`.
-__device__ Decoded decode_program(const uint8_t *__restrict__ tok, int L, int Lmax,
-                                  int nvars, int K, uint32_t *code, int lane) {
-  Decoded d{0, 0, 0};
-  if (L < 1 || L > Lmax) {
-    d.flags = SR_PF_BAD_LENGTH;
-    return d;
-  }
-  int depth = 0, maxd = 0, n = 0, flags = 0;
-  const unsigned lt_mask = (1u << lane) - 1u;
-  for (int base = 0; base < L; base += 32) {
-    const int t = base + lane;
-    const bool act = t < L;
-    const int v = act ? tok[t] : 255;
-    const int vprev = (act && t > 0) ? tok[t - 1] : 255;
-    const int vnext = (act && t + 1 < L) ? tok[t + 1] : 255;
-    const int cls = tok_class(v);
-    const int eff = act ? cls_effect(cls) : 0;
-    if (act) {
+__device__ __forceinline__ uint32_t operand_of(int v, const float *crow, long long ldx) {
+  return tok_class(v) == CLS_VAR ? (uint32_t)((long long)(v - TOK_VAR0) * ldx)
+                                 : __float_as_uint(crow[v - TOK_CONST0]);
+}
+
+// Validation and scheduled decoding of program `prog` (one thread).
+// Flag rules: length outside [1, Lmax]; bad byte; variable / constant index
+// out of range; depth (running sum of +1 terminal, 0 unary or bad byte, -1
+// binary) below 1 after some token; final depth not 1.
+__device__ void decode_one(const EvalParams &p, int prog) {
+  const uint8_t *tok = p.programs + (size_t)prog * p.Lmax;
+  const int L = p.lengths[prog];
+  int flags = 0;
+  if (L < 1 || L > p.Lmax) {
+    flags = SR_PF_BAD_LENGTH;
+  } else {
+    int depth = 0;
+    for (int t = 0; t < L; ++t) {
+      const int v = tok[t];
+      const int cls = tok_class(v);
       if (cls == CLS_BAD) flags |= SR_PF_BAD_TOKEN;
-      if (cls == CLS_VAR && v - TOK_VAR0 >= nvars) flags |= SR_PF_BAD_VAR;
-      if (cls == CLS_CONST && v - TOK_CONST0 >= K) flags |= SR_PF_BAD_CONST;
+      if (cls == CLS_VAR && v - TOK_VAR0 >= p.nvars) flags |= SR_PF_BAD_VAR;
+      if (cls == CLS_CONST && v - TOK_CONST0 >= p.K) flags |= SR_PF_BAD_CONST;
+      depth += cls_effect(cls);
+      if (depth < 1) flags |= SR_PF_UNDERFLOW;
     }
-    int s = eff;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      int u = __shfl_up_sync(FULL, s, o);
-      if (lane >= o) s += u;
-    }
-    const int after = depth + s;
-    const int before = after - eff;
-    if (act && after < 1) flags |= SR_PF_UNDERFLOW;
-    maxd = max(maxd, __reduce_max_sync(FULL, act ? after : 0));
-    const int cn = tok_class(vnext), cp = tok_class(vprev);
-    const bool term = cls == CLS_VAR || cls == CLS_CONST;
-    const bool head = act && term && cn == CLS_BINARY;
-    const bool absorbed = act && cls == CLS_BINARY && (cp == CLS_VAR || cp == CLS_CONST);
-    const bool emit = act && !absorbed;
-    uint32_t ins = 0;
-    if (term) {
-      const uint32_t arg = cls == CLS_VAR ? (uint32_t)(v - TOK_VAR0) : (uint32_t)(v - TOK_CONST0);
-      if (head) {
-        ins = (uint32_t)((cls == CLS_VAR ? OP_VADD : OP_CADD) + vnext) | (arg << 8);
-      } else if (before == 0) {
-        ins = (uint32_t)(cls == CLS_VAR ? OP_LDV : OP_LDC) | (arg << 8);
-      } else {
-        ins = (uint32_t)(cls == CLS_VAR ? OP_PUSHV : OP_PUSHC) | (arg << 8) |
-              ((uint32_t)(before - 1) << 16);
-      }
-    } else if (cls == CLS_UNARY) {
-      ins = (uint32_t)(OP_SIN + (v - TOK_SIN));
-    } else if (cls == CLS_BINARY) {
-      ins = (uint32_t)(OP_ADD + v) | ((uint32_t)max(before - 2, 0) << 16);
-    }
-    const unsigned bal = __ballot_sync(FULL, emit);
-    if (emit) code[n + __popc(bal & lt_mask)] = ins;
-    n += __popc(bal);
-    depth = __shfl_sync(FULL, after, 31);
+    if (depth != 1) flags |= SR_PF_BAD_FINAL;
   }
-  flags = __reduce_or_sync(FULL, flags);
-  if (depth != 1) flags |= SR_PF_BAD_FINAL;
-  d.n = n;
-  d.maxd = maxd;
-  d.flags = flags;
-  return d;
+  p.flags[prog] = flags;
+  if (flags) {
+    p.ncode[prog] = 0;
+    return;
+  }
+  int16_t *start = p.s_start + (size_t)prog * p.Lmax;
+  uint8_t *need = p.s_need + (size_t)prog * p.Lmax;
+  int16_t *task = p.s_task + (size_t)prog * p.Lmax;
+  // pass 1, postfix order is bottom-up: subtree starts and stack needs
+  // (terminal 1; unary as its child; binary max of the children, +1 on a tie)
+  int sp = 0;
+  for (int t = 0; t < L; ++t) {
+    const int cls = tok_class(tok[t]);
+    if (cls == CLS_VAR || cls == CLS_CONST) {
+      start[t] = (int16_t)t;
+      need[t] = 1;
+      task[sp++] = (int16_t)t;
+    } else if (cls == CLS_UNARY) {
+      const int c = task[sp - 1];
+      start[t] = start[c];
+      need[t] = need[c];
+      task[sp - 1] = (int16_t)t;
+    } else {
+      const int b = task[--sp], a = task[sp - 1];
+      const int na = need[a], nb = need[b];
+      start[t] = start[a];
+      need[t] = (uint8_t)(na == nb ? na + 1 : (na > nb ? na : nb));
+      task[sp - 1] = (int16_t)t;
+    }
+  }
+  // pass 2, emission: depth-first from the root, larger-need child first;
+  // work stack entries are node << 2 | phase.  d counts the live values
+  // (top included): a terminal pushes the old top into slot d - 1, a binary
+  // operator pops slot d - 2.
+  const float *crow = p.consts + (size_t)prog * p.K;
+  uint2 *code = p.code + (size_t)prog * p.Lmax;
+  int n = 0, d = 0;
+  sp = 0;
+  task[sp++] = (int16_t)((L - 1) << 2);
+  while (sp > 0) {
+    const int e = task[sp - 1];
+    const int node = e >> 2, ph = e & 3;
+    const int v = tok[node];
+    const int cls = tok_class(v);
+    if (cls == CLS_VAR || cls == CLS_CONST) {
+      --sp;
+      if (d > DSM) {  // cannot happen (depth <= 9 for <= 512 tokens); never write past the slots
+        p.flags[prog] = SR_PF_TOO_DEEP;
+        p.ncode[prog] = 0;
+        return;
+      }
+      const bool var = cls == CLS_VAR;
+      uint32_t op = var ? OP_LDV : OP_LDC;
+      if (d > 0) op = (uint32_t)(var ? OP_PUSHV : OP_PUSHC) | ((uint32_t)((d - 1) * SLOT_BYTES) << 8);
+      code[n++] = make_uint2(op, operand_of(v, crow, p.ldx));
+      ++d;
+    } else if (cls == CLS_UNARY) {
+      if (ph == 0) {
+        task[sp - 1] = (int16_t)(e | 1);
+        task[sp++] = (int16_t)((node - 1) << 2);
+      } else {
+        --sp;
+        code[n++] = make_uint2((uint32_t)(OP_SIN + (v - TOK_SIN)), 0u);
+      }
+    } else {
+      const int b = node - 1, a = start[b] - 1;
+      const bool rev = need[b] > need[a];
+      const int first = rev ? b : a, second = rev ? a : b;
+      if (ph == 0) {
+        task[sp - 1] = (int16_t)(e | 1);
+        task[sp++] = (int16_t)(first << 2);
+      } else if (ph == 1 && is_term(tok[second])) {
+        --sp;
+        const int w = tok[second];
+        const bool var = tok_class(w) == CLS_VAR;
+        uint32_t op;
+        if (rev && v == TOK_SUB) op = var ? OP_VRSUB : OP_CRSUB;
+        else if (rev && v == TOK_DIV) op = var ? OP_VRDIV : OP_CRDIV;
+        else op = (uint32_t)((var ? OP_VADD : OP_CADD) + v);  // + and * commute exactly
+        code[n++] = make_uint2(op, operand_of(w, crow, p.ldx));
+      } else if (ph == 1) {
+        task[sp - 1] = (int16_t)((e & ~3) | 2);
+        task[sp++] = (int16_t)(second << 2);
+      } else {
+        --sp;
+        uint32_t op;
+        if (rev && v == TOK_SUB) op = OP_RSUB;
+        else if (rev && v == TOK_DIV) op = OP_RDIV;
+        else op = (uint32_t)(OP_ADD + v);
+        code[n++] = make_uint2(op | ((uint32_t)((d - 2) * SLOT_BYTES) << 8), 0u);
+        --d;
+      }
+    }
+  }
+  p.ncode[prog] = n;
+}
+
+__global__ void decode_kernel(EvalParams p) {
+  const int prog = blockIdx.x * blockDim.x + threadIdx.x;
+  if (prog < p.P) decode_one(p, prog);
 }
 
 // ---------------------------------------------------------------- interpreter
-// Runs the decoded program for this lane's 4 cases starting at c0.
-// `stk` points at this lane's slot-0 entry; slot s is stk[32 * s].
-__device__ __forceinline__ float4 interpret(const uint32_t *__restrict__ code, int n,
-                                            const float *__restrict__ cv, float4 *stk,
-                                            const float *__restrict__ X, long long ldx, int c0) {
-  float4 T = make_float4(0.f, 0.f, 0.f, 0.f);
+// CPL = 8 cases per lane: the value on top of the stack is two float4 (a: the
+// lane's cases 0-3, b: cases 4-7); a stack slot holds the same for every
+// lane as [slot][half][lane] float4, so each 128-bit access of a warp covers
+// 512 contiguous bytes (no bank conflicts).
+struct V8 {
+  float4 a, b;
+};
+
+__device__ __forceinline__ V8 splat8(float c) {
+  V8 r;
+  r.a = splat(c);
+  r.b = r.a;
+  return r;
+}
+#define MAP8(f, v) V8{MAP4(f, (v).a), MAP4(f, (v).b)}
+#define ZIP8(f, p, q) V8{ZIP4(f, (p).a, (q).a), ZIP4(f, (p).b, (q).b)}
+
+__device__ __forceinline__ V8 ld8(const char *stk, uint32_t off) {
+  V8 r;
+  r.a = *reinterpret_cast<const float4 *>(stk + off);
+  r.b = *reinterpret_cast<const float4 *>(stk + off + 32 * 16);
+  return r;
+}
+__device__ __forceinline__ void st8(char *stk, uint32_t off, const V8 &v) {
+  *reinterpret_cast<float4 *>(stk + off) = v.a;
+  *reinterpret_cast<float4 *>(stk + off + 32 * 16) = v.b;
+}
+__device__ __forceinline__ V8 ldX8(const float *xa, const float *xb, uint32_t off) {
+  return V8{ldx4(xa + off), ldx4(xb + off)};
+}
+
+#ifndef SR_OUTLINE_MATH
+#define SR_OUTLINE_MATH 1
+#endif
+#ifndef SR_MATH_UNROLL
+#define SR_MATH_UNROLL 8
+#endif
+constexpr int MATH_UNROLL = SR_MATH_UNROLL;
+#if SR_OUTLINE_MATH
+// The costly operators (the FP32 math library routines and IEEE division)
+// live out of line, one copy each, so the interpreter's dispatch loop stays
+// small enough for the instruction cache; inside, SR_MATH_UNROLL values are
+// in flight at a time.  Measured on the 4096 x 100,000 mixed population:
+// everything inlined ~1,450 GPop/s, out of line with 4 in flight ~1,530,
+// with 8 in flight ~2,200.
+struct FSin { __device__ __forceinline__ float operator()(float x) const { return f_sin(x); } };
+struct FCos { __device__ __forceinline__ float operator()(float x) const { return f_cos(x); } };
+struct FExp { __device__ __forceinline__ float operator()(float x) const { return op_exp(x); } };
+struct FLog { __device__ __forceinline__ float operator()(float x) const { return op_log(x); } };
+struct FSqrt { __device__ __forceinline__ float operator()(float x) const { return f_sqrt(x); } };
+
+template <typename F>
+__device__ __forceinline__ V8 map8_unrolled(V8 v, F f) {
+  float t[8] = {v.a.x, v.a.y, v.a.z, v.a.w, v.b.x, v.b.y, v.b.z, v.b.w};
+#pragma unroll MATH_UNROLL
+  for (int i = 0; i < 8; ++i) t[i] = f(t[i]);
+  return V8{make_float4(t[0], t[1], t[2], t[3]), make_float4(t[4], t[5], t[6], t[7])};
+}
+__device__ __noinline__ V8 sin8(V8 v) { return map8_unrolled(v, FSin()); }
+__device__ __noinline__ V8 cos8(V8 v) { return map8_unrolled(v, FCos()); }
+__device__ __noinline__ V8 exp8(V8 v) { return map8_unrolled(v, FExp()); }
+__device__ __noinline__ V8 log8(V8 v) { return map8_unrolled(v, FLog()); }
+__device__ __noinline__ V8 sqrt8(V8 v) { return map8_unrolled(v, FSqrt()); }
+__device__ __noinline__ V8 div8(V8 a, V8 b) {
+  float x[8] = {a.a.x, a.a.y, a.a.z, a.a.w, a.b.x, a.b.y, a.b.z, a.b.w};
+  const float y[8] = {b.a.x, b.a.y, b.a.z, b.a.w, b.b.x, b.b.y, b.b.z, b.b.w};
+#pragma unroll MATH_UNROLL
+  for (int i = 0; i < 8; ++i) x[i] = op_div(x[i], y[i]);
+  return V8{make_float4(x[0], x[1], x[2], x[3]), make_float4(x[4], x[5], x[6], x[7])};
+}
+#define SIN8(v) sin8(v)
+#define COS8(v) cos8(v)
+#define EXP8(v) exp8(v)
+#define LOG8(v) log8(v)
+#define SQRT8(v) sqrt8(v)
+#define DIV8(p, q) div8(p, q)
+#else
+#define SIN8(v) MAP8(f_sin, v)
+#define COS8(v) MAP8(f_cos, v)
+#define EXP8(v) MAP8(op_exp, v)
+#define LOG8(v) MAP8(op_log, v)
+#define SQRT8(v) MAP8(f_sqrt, v)
+#define DIV8(p, q) ZIP8(op_div, p, q)
+#endif
+
+// Runs the decoded program for this lane's 8 cases.  xa / xb point at the
+// lane's first and second case group in row 0 of X; `stk` at this lane's
+// entry of stack slot 0 in shared memory.
+__device__ __forceinline__ V8 interpret(const uint2 *__restrict__ code, int n, char *stk,
+                                        const float *__restrict__ xa, const float *__restrict__ xb) {
+  V8 T = splat8(0.f);
   for (int ip = 0; ip < n; ++ip) {
-    const uint32_t w = code[ip];
-    const int arg = (w >> 8) & 0xff;
-    float4 *sp = stk + 32 * (int)(w >> 16);
-    switch (w & 0xff) {
-      case OP_LDV: T = ldx4(X + arg * ldx + c0); break;
-      case OP_LDC: T = splat(cv[arg]); break;
-      case OP_PUSHV: *sp = T; T = ldx4(X + arg * ldx + c0); break;
-      case OP_PUSHC: *sp = T; T = splat(cv[arg]); break;
-      case OP_ADD: { float4 a = *sp; T = ZIP4(f_add, a, T); } break;
-      case OP_SUB: { float4 a = *sp; T = ZIP4(f_sub, a, T); } break;
-      case OP_MUL: { float4 a = *sp; T = ZIP4(f_mul, a, T); } break;
-      case OP_DIV: { float4 a = *sp; T = ZIP4(op_div, a, T); } break;
-      case OP_SIN: T = MAP4(sinf, T); break;
-      case OP_COS: T = MAP4(cosf, T); break;
-      case OP_EXP: T = MAP4(op_exp, T); break;
-      case OP_LOG: T = MAP4(op_log, T); break;
-      case OP_SQRT: T = MAP4(f_sqrt, T); break;
-      case OP_SQ: T = MAP4(f_sq, T); break;
-      case OP_VADD: { float4 v = ldx4(X + arg * ldx + c0); T = ZIP4(f_add, T, v); } break;
-      case OP_VSUB: { float4 v = ldx4(X + arg * ldx + c0); T = ZIP4(f_sub, T, v); } break;
-      case OP_VMUL: { float4 v = ldx4(X + arg * ldx + c0); T = ZIP4(f_mul, T, v); } break;
-      case OP_VDIV: { float4 v = ldx4(X + arg * ldx + c0); T = ZIP4(op_div, T, v); } break;
-      case OP_CADD: { float4 v = splat(cv[arg]); T = ZIP4(f_add, T, v); } break;
-      case OP_CSUB: { float4 v = splat(cv[arg]); T = ZIP4(f_sub, T, v); } break;
-      case OP_CMUL: { float4 v = splat(cv[arg]); T = ZIP4(f_mul, T, v); } break;
-      case OP_CDIV: { float4 v = splat(cv[arg]); T = ZIP4(op_div, T, v); } break;
+    const uint2 w = code[ip];
+    const uint32_t off = w.x >> 8;
+    switch (w.x & 0xffu) {
+      case OP_LDV: T = ldX8(xa, xb, w.y); break;
+      case OP_LDC: T = splat8(__uint_as_float(w.y)); break;
+      case OP_PUSHV: st8(stk, off, T); T = ldX8(xa, xb, w.y); break;
+      case OP_PUSHC: st8(stk, off, T); T = splat8(__uint_as_float(w.y)); break;
+      case OP_ADD: { const V8 a = ld8(stk, off); T = ZIP8(f_add, a, T); } break;
+      case OP_SUB: { const V8 a = ld8(stk, off); T = ZIP8(f_sub, a, T); } break;
+      case OP_MUL: { const V8 a = ld8(stk, off); T = ZIP8(f_mul, a, T); } break;
+      case OP_DIV: { const V8 a = ld8(stk, off); T = DIV8(a, T); } break;
+      case OP_RSUB: { const V8 b = ld8(stk, off); T = ZIP8(f_sub, T, b); } break;
+      case OP_RDIV: { const V8 b = ld8(stk, off); T = DIV8(T, b); } break;
+      case OP_SIN: T = SIN8(T); break;
+      case OP_COS: T = COS8(T); break;
+      case OP_EXP: T = EXP8(T); break;
+      case OP_LOG: T = LOG8(T); break;
+      case OP_SQRT: T = SQRT8(T); break;
+      case OP_SQ: T = MAP8(f_sq, T); break;
+      case OP_VADD: { const V8 v = ldX8(xa, xb, w.y); T = ZIP8(f_add, T, v); } break;
+      case OP_VSUB: { const V8 v = ldX8(xa, xb, w.y); T = ZIP8(f_sub, T, v); } break;
+      case OP_VMUL: { const V8 v = ldX8(xa, xb, w.y); T = ZIP8(f_mul, T, v); } break;
+      case OP_VDIV: { const V8 v = ldX8(xa, xb, w.y); T = DIV8(T, v); } break;
+      case OP_VRSUB: { const V8 v = ldX8(xa, xb, w.y); T = ZIP8(f_sub, v, T); } break;
+      case OP_VRDIV: { const V8 v = ldX8(xa, xb, w.y); T = DIV8(v, T); } break;
+      case OP_CADD: { const V8 v = splat8(__uint_as_float(w.y)); T = ZIP8(f_add, T, v); } break;
+      case OP_CSUB: { const V8 v = splat8(__uint_as_float(w.y)); T = ZIP8(f_sub, T, v); } break;
+      case OP_CMUL: { const V8 v = splat8(__uint_as_float(w.y)); T = ZIP8(f_mul, T, v); } break;
+      case OP_CDIV: { const V8 v = splat8(__uint_as_float(w.y)); T = DIV8(T, v); } break;
+      case OP_CRSUB: { const V8 v = splat8(__uint_as_float(w.y)); T = ZIP8(f_sub, v, T); } break;
+      case OP_CRDIV: { const V8 v = splat8(__uint_as_float(w.y)); T = DIV8(v, T); } break;
       default: break;
     }
   }
@@ -268,21 +457,15 @@ __device__ __forceinline__ float4 load_y4(const float *__restrict__ y, int c0, i
 
 // ---------------------------------------------------------------- one work item
 struct WarpSmem {
-  float4 *stk_s;    // shared stack slots, [DSM][32] float4
-  float *cvals;     // the program's constants
-  uint32_t *code;   // decoded instructions
-  float4 *stk_g;    // this warp's global stack slots for deep programs
+  char *stk;        // shared stack slots of this warp, [DSM][2][32] float4
+  uint2 *code;      // this warp's copy of the program's code
 };
 
-__device__ __forceinline__ WarpSmem warp_smem(unsigned char *smem, int warp, int warp_bytes,
-                                              float4 *deep_stack, int deep_slots) {
+__device__ __forceinline__ WarpSmem warp_smem(unsigned char *smem, int warp, int warp_bytes) {
   unsigned char *wbase = smem + (size_t)warp * warp_bytes;
   WarpSmem w;
-  w.stk_s = reinterpret_cast<float4 *>(wbase);
-  w.cvals = reinterpret_cast<float *>(wbase + DSM * 32 * 16);
-  w.code = reinterpret_cast<uint32_t *>(wbase + DSM * 32 * 16 + 64);
-  const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
-  w.stk_g = deep_stack ? deep_stack + (size_t)gw * deep_slots * 32 : nullptr;
+  w.stk = reinterpret_cast<char *>(wbase);
+  w.code = reinterpret_cast<uint2 *>(wbase + DSM * SLOT_BYTES);
   return w;
 }
 
@@ -294,54 +477,62 @@ __device__ __forceinline__ void eval_item(const EvalParams &p, int c, int prog, 
                                           int lane, int want) {
   const bool do_mse = MODE == MODE_MSE || (MODE == MODE_BOTH && (want & 1));
   const bool do_corr = MODE == MODE_CORR || (MODE == MODE_BOTH && (want & 2));
-  __syncwarp();  // the previous item is done reading code/cvals
-  const Decoded dec = decode_program(p.programs + (size_t)prog * p.Lmax, p.lengths[prog], p.Lmax,
-                                     p.nvars, p.K, w.code, lane);
-  if (lane == 0 && c == 0) p.flags[prog] = dec.flags;
   const int cbeg = c * p.chunk;
   const int cend = min(p.N, cbeg + p.chunk);
-
-  if (dec.flags) {
+  if (p.flags[prog]) {
     if (MODE == MODE_PREDICT) {
       float *row = p.yhat + (size_t)prog * p.ldy;
       for (int i = cbeg + lane; i < cend; i += 32) row[i] = __int_as_float(0x7fc00000);
     }
     return;
   }
-  if (lane < p.K) w.cvals[lane] = p.consts[(size_t)prog * p.K + lane];
+  const int n = p.ncode[prog];
+  __syncwarp();  // the previous item is done reading the code
+  const uint2 *src = p.code + (size_t)prog * p.Lmax;
+  for (int i = lane; i < n; i += 32) w.code[i] = src[i];
   __syncwarp();
 
-  float4 *stk = (dec.maxd - 1 <= DSM) ? w.stk_s + lane : w.stk_g + lane;
-  const int last_group = (cend - 1) & ~3;
+  char *stk = w.stk + lane * 16;
+  const int last_group = (cend - 1) & ~(CPL - 1);
 
   Kahan se, s1, s2, s3;
   float shift = 0.f;
   for (int base = cbeg; base < cend; base += STEP) {
-    const int c0 = base + 4 * lane;
-    const int cl = c0 < cend ? c0 : last_group;  // clamped, always readable
-    const float4 T = interpret(w.code, dec.n, w.cvals, stk, p.X, p.ldx, cl);
-    const bool v0 = c0 < cend, v1 = c0 + 1 < cend, v2 = c0 + 2 < cend, v3 = c0 + 3 < cend;
+    const int c0 = base + CPL * lane;
+    const int cl = c0 < cend ? c0 : last_group;           // first 4 cases, always readable
+    const int cl4 = cl + 4 < cend ? cl + 4 : cl;          // second 4, or a re-read when none valid
+    const V8 T = interpret(w.code, n, stk, p.X + cl, p.X + cl4);
+    const float tv[CPL] = {T.a.x, T.a.y, T.a.z, T.a.w, T.b.x, T.b.y, T.b.z, T.b.w};
+    bool ok[CPL];
+#pragma unroll
+    for (int i = 0; i < CPL; ++i) ok[i] = c0 + i < cend;
     if (MODE == MODE_PREDICT) {
       float *row = p.yhat + (size_t)prog * p.ldy;
-      if (v0) row[c0] = T.x;
-      if (v1) row[c0 + 1] = T.y;
-      if (v2) row[c0 + 2] = T.z;
-      if (v3) row[c0 + 3] = T.w;
+#pragma unroll
+      for (int i = 0; i < CPL; ++i)
+        if (ok[i]) row[c0 + i] = tv[i];
     }
     if (do_mse) {
-      const float4 yv = load_y4(p.y, cl, p.N);
-      const float e0 = sel(v0, T.x - yv.x), e1 = sel(v1, T.y - yv.y);
-      const float e2 = sel(v2, T.z - yv.z), e3 = sel(v3, T.w - yv.w);
-      se.add((e0 * e0 + e1 * e1) + (e2 * e2 + e3 * e3));
+      const float4 ya = load_y4(p.y, cl, p.N), yb = load_y4(p.y, cl4, p.N);
+      const float yv[CPL] = {ya.x, ya.y, ya.z, ya.w, yb.x, yb.y, yb.z, yb.w};
+      float e[CPL];
+#pragma unroll
+      for (int i = 0; i < CPL; ++i) e[i] = sel(ok[i], tv[i] - yv[i]);
+      se.add(((e[0] * e[0] + e[1] * e[1]) + (e[2] * e[2] + e[3] * e[3])) +
+             ((e[4] * e[4] + e[5] * e[5]) + (e[6] * e[6] + e[7] * e[7])));
     }
     if (do_corr) {
-      if (base == cbeg) shift = __shfl_sync(FULL, T.x, 0);
-      const float4 yv = ldx4(p.yc + cl);
-      const float d0 = sel(v0, T.x - shift), d1 = sel(v1, T.y - shift);
-      const float d2 = sel(v2, T.z - shift), d3 = sel(v3, T.w - shift);
-      s1.add((d0 + d1) + (d2 + d3));
-      s2.add((d0 * d0 + d1 * d1) + (d2 * d2 + d3 * d3));
-      s3.add((d0 * yv.x + d1 * yv.y) + (d2 * yv.z + d3 * yv.w));
+      if (base == cbeg) shift = __shfl_sync(FULL, T.a.x, 0);
+      const float4 ya = ldx4(p.yc + cl), yb = ldx4(p.yc + cl4);
+      const float yv[CPL] = {ya.x, ya.y, ya.z, ya.w, yb.x, yb.y, yb.z, yb.w};
+      float d[CPL];
+#pragma unroll
+      for (int i = 0; i < CPL; ++i) d[i] = sel(ok[i], tv[i] - shift);
+      s1.add(((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])));
+      s2.add(((d[0] * d[0] + d[1] * d[1]) + (d[2] * d[2] + d[3] * d[3])) +
+             ((d[4] * d[4] + d[5] * d[5]) + (d[6] * d[6] + d[7] * d[7])));
+      s3.add(((d[0] * yv[0] + d[1] * yv[1]) + (d[2] * yv[2] + d[3] * yv[3])) +
+             ((d[4] * yv[4] + d[5] * yv[5]) + (d[6] * yv[6] + d[7] * yv[7])));
     }
   }
   if (MODE != MODE_PREDICT) {
@@ -369,7 +560,7 @@ template <int MODE>
 __global__ void __launch_bounds__(WARPS * 32) eval_kernel(EvalParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const WarpSmem w = warp_smem(smem, warp, p.warp_bytes, p.deep_stack, p.deep_slots);
+  const WarpSmem w = warp_smem(smem, warp, p.warp_bytes);
   for (;;) {
     unsigned long long item = 0;
     if (lane == 0) item = atomicAdd(p.queue, 1ull);
@@ -393,13 +584,19 @@ struct BatchProblem {
   float *yc;           // centred target (1 - r^2), padded
   double *partials;    // [P * nchunks][PSTRIDE]
   int32_t *flags;      // [P]
+  uint2 *code;         // [P][Lmax]
+  int32_t *ncode;      // [P]
+  int16_t *s_start;
+  uint8_t *s_need;
+  int16_t *s_task;
   double *fitness;     // [P] or [2][P]
   double *ychunk;      // [nchunks][2]
   double *stats;       // [8]
   long long ldx;
   long long item_begin;  // first work item of this problem in the launch
+  int prog_begin;        // first program of this problem in the decode launch
   int P, Lmax, K, nvars, N, chunk, nchunks;
-  int mode;            // MODE_MSE, MODE_CORR or MODE_BOTH
+  int mode;              // MODE_MSE, MODE_CORR or MODE_BOTH
   int corr_chunk_begin;  // first block of this problem in the batched centring launch (-1: none)
 };
 
@@ -408,19 +605,58 @@ struct BatchParams {
   int nprob;
   int corr_list[MAX_BATCH];  // problems that need the centred target, in order
   int ncorr;
+  int total_progs;
   long long total_items;
   unsigned long long *queue;
-  float4 *deep_stack;
-  int deep_slots;
   int warp_bytes;
 };
+
+__device__ __forceinline__ EvalParams view(const BatchProblem &q) {
+  EvalParams p;
+  p.programs = q.programs;
+  p.lengths = q.lengths;
+  p.consts = q.consts;
+  p.P = q.P;
+  p.Lmax = q.Lmax;
+  p.K = q.K;
+  p.X = q.X;
+  p.y = q.y;
+  p.yc = q.yc;
+  p.nvars = q.nvars;
+  p.N = q.N;
+  p.ldx = q.ldx;
+  p.chunk = q.chunk;
+  p.nchunks = q.nchunks;
+  p.partials = q.partials;
+  p.flags = q.flags;
+  p.code = q.code;
+  p.ncode = q.ncode;
+  p.s_start = q.s_start;
+  p.s_need = q.s_need;
+  p.s_task = q.s_task;
+  return p;
+}
+
+// one thread per program of every problem in the batch
+__global__ void decode_batched_kernel(const __grid_constant__ BatchParams b) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= b.total_progs) return;
+  int lo = 0, hi = b.nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (b.prob[mid].prog_begin <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  const EvalParams p = view(b.prob[lo]);
+  decode_one(p, g - b.prob[lo].prog_begin);
+}
 
 // Work items of every problem come from one atomic counter: problem q owns
 // items [item_begin_q, item_begin_q + P_q * nchunks_q), chunk-major inside.
 __global__ void __launch_bounds__(WARPS * 32) eval_batched_kernel(const __grid_constant__ BatchParams b) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const WarpSmem w = warp_smem(smem, warp, b.warp_bytes, b.deep_stack, b.deep_slots);
+  const WarpSmem w = warp_smem(smem, warp, b.warp_bytes);
   for (;;) {
     unsigned long long item = 0;
     if (lane == 0) item = atomicAdd(b.queue, 1ull);
@@ -433,23 +669,7 @@ __global__ void __launch_bounds__(WARPS * 32) eval_batched_kernel(const __grid_c
       else hi = mid - 1;
     }
     const BatchProblem &q = b.prob[lo];
-    EvalParams p;
-    p.programs = q.programs;
-    p.lengths = q.lengths;
-    p.consts = q.consts;
-    p.P = q.P;
-    p.Lmax = q.Lmax;
-    p.K = q.K;
-    p.X = q.X;
-    p.y = q.y;
-    p.yc = q.yc;
-    p.nvars = q.nvars;
-    p.N = q.N;
-    p.ldx = q.ldx;
-    p.chunk = q.chunk;
-    p.nchunks = q.nchunks;
-    p.partials = q.partials;
-    p.flags = q.flags;
+    const EvalParams p = view(q);
     const long long local = (long long)item - q.item_begin;
     const int c = (int)(local / q.P);
     const int prog = (int)(local % q.P);
@@ -483,14 +703,11 @@ __global__ void __launch_bounds__(PREP_THREADS) ymean_kernel(const float *__rest
   if (threadIdx.x == 0) stats[0] = s / (double)N;
 }
 
-// yc = fl32(y - ybar) per chunk, with its FP64 sum and sum of squares
-__global__ void __launch_bounds__(PREP_THREADS) ycenter_kernel(const float *__restrict__ y, int N,
-                                                               int chunk, int padded,
-                                                               const double *stats, float *yc,
-                                                               double *ychunk) {
-  __shared__ double red[PREP_THREADS / 32];
+// yc = fl32(y - ybar) on one chunk, with its FP64 sum and sum of squares
+__device__ void ycenter_chunk(const float *__restrict__ y, int N, int chunk, int nchunks, int c,
+                              const double *stats, float *yc, double *ychunk, double *red) {
   const double ybar = stats[0];
-  const int beg = blockIdx.x * chunk, end = min(N, beg + chunk);
+  const int beg = c * chunk, end = min(N, beg + chunk);
   double a = 0.0, b = 0.0;
   for (int i = beg + threadIdx.x; i < end; i += blockDim.x) {
     const float v = (float)((double)y[i] - ybar);
@@ -498,25 +715,27 @@ __global__ void __launch_bounds__(PREP_THREADS) ycenter_kernel(const float *__re
     a += (double)v;
     b += (double)v * (double)v;
   }
-  if (blockIdx.x == gridDim.x - 1)
+  if (c == nchunks - 1) {
+    const int padded = (N + STEP - 1) / STEP * STEP;
     for (int i = N + threadIdx.x; i < padded; i += blockDim.x) yc[i] = 0.0f;
+  }
   a = block_sum(a, red);
   b = block_sum(b, red);
   if (threadIdx.x == 0) {
-    ychunk[2 * blockIdx.x] = a;
-    ychunk[2 * blockIdx.x + 1] = b;
+    ychunk[2 * c] = a;
+    ychunk[2 * c + 1] = b;
   }
 }
 
-// ---------------------------------------------------------------- finalize
-struct FinalParams {
-  const double *partials;
-  const int32_t *flags;
-  const double *ychunk;
-  int P, N, chunk, nchunks;
-  double *fitness;  // [P] or [2][P]
-};
+__global__ void __launch_bounds__(PREP_THREADS) ycenter_kernel(const float *__restrict__ y, int N,
+                                                               int chunk, int nchunks,
+                                                               const double *stats, float *yc,
+                                                               double *ychunk) {
+  __shared__ double red[PREP_THREADS / 32];
+  ycenter_chunk(y, N, chunk, nchunks, blockIdx.x, stats, yc, ychunk, red);
+}
 
+// ---------------------------------------------------------------- finalize
 // 1 - r^2 of one program from its chunk records.
 // chunk c: n_c cases, shift s_c, S1 = sum d, S2 = sum d^2, S3 = sum d yc with
 // d = yhat - s_c.  Chunk mean m_c = s_c + S1/n_c, chunk M2 = S2 - S1^2/n_c;
@@ -553,27 +772,39 @@ __device__ double corr_fitness(const double *rec, const double *ychunk, int Nc, 
   return fit;
 }
 
-template <int MODE>
+// fitness of program p from its partial records (mode picks the outputs)
+__device__ void finalize_one(int mode, const double *partials, const int32_t *flags,
+                             const double *ychunk, int P, int N, int chunk, int nchunks,
+                             double *fitness, int p) {
+  const double INF = __longlong_as_double(0x7ff0000000000000ll);
+  double *mse_out = fitness;
+  double *corr_out = mode == MODE_BOTH ? fitness + P : fitness;
+  if (flags[p]) {
+    if (mode != MODE_CORR) mse_out[p] = INF;
+    if (mode != MODE_MSE) corr_out[p] = INF;
+    return;
+  }
+  const double *rec = partials + (size_t)p * nchunks * PSTRIDE;
+  if (mode != MODE_CORR) {
+    double se = 0.0;
+    for (int c = 0; c < nchunks; ++c) se += rec[c * PSTRIDE];
+    mse_out[p] = isfinite(se) ? se / (double)N : INF;
+  }
+  if (mode != MODE_MSE) corr_out[p] = corr_fitness(rec, ychunk, N, chunk, nchunks);
+}
+
+struct FinalParams {
+  const double *partials;
+  const int32_t *flags;
+  const double *ychunk;
+  int P, N, chunk, nchunks, mode;
+  double *fitness;  // [P] or [2][P]
+};
+
 __global__ void finalize_kernel(FinalParams f) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= f.P) return;
-  const double INF = __longlong_as_double(0x7ff0000000000000ll);
-  double *mse_out = f.fitness;
-  double *corr_out = MODE == MODE_BOTH ? f.fitness + f.P : f.fitness;
-  if (f.flags[p]) {
-    if (MODE == MODE_MSE || MODE == MODE_BOTH) mse_out[p] = INF;
-    if (MODE == MODE_CORR || MODE == MODE_BOTH) corr_out[p] = INF;
-    return;
-  }
-  const double *rec = f.partials + (size_t)p * f.nchunks * PSTRIDE;
-  const double N = (double)f.N;
-  if (MODE == MODE_MSE || MODE == MODE_BOTH) {
-    double se = 0.0;
-    for (int c = 0; c < f.nchunks; ++c) se += rec[c * PSTRIDE];
-    mse_out[p] = isfinite(se) ? se / N : INF;
-  }
-  if (MODE == MODE_CORR || MODE == MODE_BOTH)
-    corr_out[p] = corr_fitness(rec, f.ychunk, f.N, f.chunk, f.nchunks);
+  finalize_one(f.mode, f.partials, f.flags, f.ychunk, f.P, f.N, f.chunk, f.nchunks, f.fitness, p);
 }
 
 // ---------------------------------------------------------------- batched prep / finalize
@@ -593,52 +824,15 @@ __global__ void __launch_bounds__(PREP_THREADS) ycenter_batched_kernel(const __g
   int r = 0;
   while (r + 1 < b.ncorr && b.prob[b.corr_list[r + 1]].corr_chunk_begin <= (int)blockIdx.x) ++r;
   const BatchProblem &q = b.prob[b.corr_list[r]];
-  const int c = (int)blockIdx.x - q.corr_chunk_begin;
-  const double ybar = q.stats[0];
-  const int beg = c * q.chunk, end = min(q.N, beg + q.chunk);
-  double a = 0.0, bb = 0.0;
-  for (int i = beg + threadIdx.x; i < end; i += blockDim.x) {
-    const float v = (float)((double)q.y[i] - ybar);
-    q.yc[i] = v;
-    a += (double)v;
-    bb += (double)v * (double)v;
-  }
-  if (c == q.nchunks - 1) {
-    const int padded = (q.N + STEP - 1) / STEP * STEP;
-    for (int i = q.N + threadIdx.x; i < padded; i += blockDim.x) q.yc[i] = 0.0f;
-  }
-  a = block_sum(a, red);
-  bb = block_sum(bb, red);
-  if (threadIdx.x == 0) {
-    q.ychunk[2 * c] = a;
-    q.ychunk[2 * c + 1] = bb;
-  }
+  ycenter_chunk(q.y, q.N, q.chunk, q.nchunks, (int)blockIdx.x - q.corr_chunk_begin, q.stats, q.yc,
+                q.ychunk, red);
 }
 
 // one block per problem, threads over its programs
 __global__ void finalize_batched_kernel(const __grid_constant__ BatchParams b) {
   const BatchProblem &q = b.prob[blockIdx.x];
-  FinalParams f{q.partials, q.flags, q.ychunk, q.P, q.N, q.chunk, q.nchunks, q.fitness};
-  for (int p0 = 0; p0 < q.P; p0 += blockDim.x) {
-    const int p = p0 + threadIdx.x;
-    if (p >= q.P) break;
-    const double INF = __longlong_as_double(0x7ff0000000000000ll);
-    double *mse_out = f.fitness;
-    double *corr_out = q.mode == MODE_BOTH ? f.fitness + f.P : f.fitness;
-    if (f.flags[p]) {
-      if (q.mode != MODE_CORR) mse_out[p] = INF;
-      if (q.mode != MODE_MSE) corr_out[p] = INF;
-      continue;
-    }
-    const double *rec = f.partials + (size_t)p * f.nchunks * PSTRIDE;
-    const double N = (double)f.N;
-    if (q.mode != MODE_CORR) {
-      double se = 0.0;
-      for (int c = 0; c < f.nchunks; ++c) se += rec[c * PSTRIDE];
-      mse_out[p] = isfinite(se) ? se / N : INF;
-    }
-    if (q.mode != MODE_MSE) corr_out[p] = corr_fitness(rec, f.ychunk, f.N, f.chunk, f.nchunks);
-  }
+  for (int p = threadIdx.x; p < q.P; p += blockDim.x)
+    finalize_one(q.mode, q.partials, q.flags, q.ychunk, q.P, q.N, q.chunk, q.nchunks, q.fitness, p);
 }
 
 // ---------------------------------------------------------------- host side
@@ -669,9 +863,10 @@ sr_status grid_for(sr_ctx *ctx, int mode, int smem, int *grid) {
 }
 
 struct Plan {
-  int grid, smem, chunk, nchunks, deep_slots;
+  int grid, smem, chunk, nchunks;
   long long items;
-  size_t off_queue, off_flags, off_part, off_yc, off_ych, off_stats, off_deep, bytes;
+  size_t off_queue, off_flags, off_ncode, off_code, off_start, off_need, off_task, off_part, off_yc,
+      off_ych, off_stats, bytes;
 };
 
 sr_status make_plan(sr_ctx *ctx, int mode, int P, int Lmax, int N, Plan *pl) {
@@ -689,17 +884,19 @@ sr_status make_plan(sr_ctx *ctx, int mode, int P, int Lmax, int N, Plan *pl) {
   pl->chunk = chunk;
   pl->nchunks = (N + chunk - 1) / chunk;
   pl->items = (long long)P * pl->nchunks;
-  const int max_depth = (Lmax + 1) / 2;
-  pl->deep_slots = max_depth - 1 > DSM ? max_depth - 1 : 0;
+  const size_t tokens = (size_t)P * Lmax;
   Carver cv;
   pl->off_queue = cv.take(256);
   pl->off_flags = cv.take((size_t)P * 4);
+  pl->off_ncode = cv.take((size_t)P * 4);
+  pl->off_code = cv.take(tokens * 8);
+  pl->off_start = cv.take(tokens * 2);
+  pl->off_need = cv.take(tokens);
+  pl->off_task = cv.take(tokens * 2);
   pl->off_part = cv.take((size_t)pl->items * PSTRIDE * 8);
-  const size_t padded = align_up((size_t)N, STEP);
-  pl->off_yc = cv.take(padded * 4);
+  pl->off_yc = cv.take(align_up((size_t)N, STEP) * 4);
   pl->off_ych = cv.take((size_t)pl->nchunks * 16);
   pl->off_stats = cv.take(64);
-  pl->off_deep = cv.take((size_t)warps * pl->deep_slots * 32 * 16);
   pl->bytes = cv.off;
   return SR_OK;
 }
@@ -714,10 +911,16 @@ sr_status check_common(sr_ctx *ctx, const uint8_t *programs, const int32_t *leng
   if (nvars < 1 || nvars > SR_MAX_VARS) return fail(ctx, SR_EINVAL, "nvars %d outside [1, %d]", nvars, SR_MAX_VARS);
   if (N < 1) return fail(ctx, SR_EINVAL, "N must be >= 1");
   if (ldx < N || ldx % 4) return fail(ctx, SR_EINVAL, "ldx %d must be >= N and a multiple of 4", ldx);
+  if ((long long)ldx * nvars > 0xFFFFFFFFll)
+    return fail(ctx, SR_EINVAL, "X too large: nvars * ldx must stay below 2^32 elements");
   if (P > 0 && (!programs || !lengths || (K > 0 && !consts) || !X))
     return fail(ctx, SR_EINVAL, "NULL input pointer");
   if (((uintptr_t)X) & 15) return fail(ctx, SR_EINVAL, "X must be 16-byte aligned");
   return SR_OK;
+}
+
+int mode_of(sr_fitness_kind k) {
+  return k == SR_MSE ? MODE_MSE : (k == SR_CORR ? MODE_CORR : MODE_BOTH);
 }
 
 sr_status launch_eval(sr_ctx *ctx, int mode, const uint8_t *programs, const int32_t *lengths,
@@ -751,19 +954,24 @@ sr_status launch_eval(sr_ctx *ctx, int mode, const uint8_t *programs, const int3
   ep.total_items = pl.items;
   ep.partials = reinterpret_cast<double *>(ws + pl.off_part);
   ep.flags = prog_flags ? prog_flags : reinterpret_cast<int32_t *>(ws + pl.off_flags);
+  ep.code = reinterpret_cast<uint2 *>(ws + pl.off_code);
+  ep.ncode = reinterpret_cast<int32_t *>(ws + pl.off_ncode);
+  ep.s_start = reinterpret_cast<int16_t *>(ws + pl.off_start);
+  ep.s_need = reinterpret_cast<uint8_t *>(ws + pl.off_need);
+  ep.s_task = reinterpret_cast<int16_t *>(ws + pl.off_task);
   ep.queue = reinterpret_cast<unsigned long long *>(ws + pl.off_queue);
   ep.yhat = yhat;
   ep.ldy = ldy;
-  ep.deep_stack = pl.deep_slots ? reinterpret_cast<float4 *>(ws + pl.off_deep) : nullptr;
-  ep.deep_slots = pl.deep_slots;
   ep.warp_bytes = warp_smem_bytes(Lmax);
 
   SR_CHECK_CUDA(ctx, cudaMemsetAsync(ep.queue, 0, sizeof(unsigned long long), s));
+  decode_kernel<<<(P + 127) / 128, 128, 0, s>>>(ep);
+  ctx->launches += 1;
   double *ych = reinterpret_cast<double *>(ws + pl.off_ych);
   if (mode == MODE_CORR || mode == MODE_BOTH) {
     double *stats = reinterpret_cast<double *>(ws + pl.off_stats);
     ymean_kernel<<<1, PREP_THREADS, 0, s>>>(y, N, stats);
-    ycenter_kernel<<<pl.nchunks, PREP_THREADS, 0, s>>>(y, N, pl.chunk, (int)align_up(N, STEP), stats,
+    ycenter_kernel<<<pl.nchunks, PREP_THREADS, 0, s>>>(y, N, pl.chunk, pl.nchunks, stats,
                                                       const_cast<float *>(ep.yc), ych);
     ctx->launches += 2;
   }
@@ -776,13 +984,8 @@ sr_status launch_eval(sr_ctx *ctx, int mode, const uint8_t *programs, const int3
   SR_CHECK_CUDA(ctx, cudaGetLastError());
   ctx->launches += 1;
   if (mode != MODE_PREDICT) {
-    FinalParams fp{ep.partials, ep.flags, ych, P, N, pl.chunk, pl.nchunks, fitness};
-    const int nb = (P + 255) / 256;
-    switch (mode) {
-      case MODE_MSE: finalize_kernel<MODE_MSE><<<nb, 256, 0, s>>>(fp); break;
-      case MODE_CORR: finalize_kernel<MODE_CORR><<<nb, 256, 0, s>>>(fp); break;
-      default: finalize_kernel<MODE_BOTH><<<nb, 256, 0, s>>>(fp); break;
-    }
+    FinalParams fp{ep.partials, ep.flags, ych, P, N, pl.chunk, pl.nchunks, mode, fitness};
+    finalize_kernel<<<(P + 255) / 256, 256, 0, s>>>(fp);
     SR_CHECK_CUDA(ctx, cudaGetLastError());
     ctx->launches += 1;
   }
@@ -790,10 +993,6 @@ sr_status launch_eval(sr_ctx *ctx, int mode, const uint8_t *programs, const int3
 }
 
 // ---------------------------------------------------------------- batched host side
-struct BatchPlan {
-  int grid, smem, deep_slots, maxL;
-};
-
 sr_status batched_grid(sr_ctx *ctx, int smem, int *grid) {
   static int configured = 0;
   if (!configured) {
@@ -808,10 +1007,6 @@ sr_status batched_grid(sr_ctx *ctx, int smem, int *grid) {
   if (nb < 1) return fail(ctx, SR_EINVAL, "Lmax too large for shared memory");
   *grid = nb * ctx->num_sms;
   return SR_OK;
-}
-
-int mode_of(sr_fitness_kind k) {
-  return k == SR_MSE ? MODE_MSE : (k == SR_CORR ? MODE_CORR : MODE_BOTH);
 }
 
 sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
@@ -831,15 +1026,12 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
     maxL = q.Lmax > maxL ? q.Lmax : maxL;
     work += (double)q.P * (double)q.N;
   }
-  BatchPlan bp;
-  bp.maxL = maxL;
-  bp.smem = WARPS * warp_smem_bytes(maxL);
-  sr_status st = batched_grid(ctx, bp.smem, &bp.grid);
+  const int smem = WARPS * warp_smem_bytes(maxL);
+  int grid = 0;
+  sr_status st = batched_grid(ctx, smem, &grid);
   if (st != SR_OK) return st;
-  const long long warps = (long long)bp.grid * WARPS;
+  const long long warps = (long long)grid * WARPS;
   const double want = (double)warps * TARGET_ITEMS_PER_WARP;
-  const int max_depth = (maxL + 1) / 2;
-  bp.deep_slots = max_depth - 1 > DSM ? max_depth - 1 : 0;
 
   // chunking per problem: items in proportion to its share of the work
   std::vector<int> chunk(nprob), nch(nprob), order;
@@ -871,14 +1063,19 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
   auto group_bytes = [&](size_t g0, size_t g1, BatchParams *bpar) -> size_t {
     Carver cv;
     const size_t off_q = cv.take(256);
-    const size_t off_deep = cv.take((size_t)warps * bp.deep_slots * 32 * 16);
     long long items = 0;
-    int corr_chunks = 0, ncorr = 0;
+    int corr_chunks = 0, ncorr = 0, progs = 0;
     for (size_t g = g0; g < g1; ++g) {
       const int i = order[g];
       const sr_problem &q = pr[i];
       const int mode = mode_of(q.kind);
+      const size_t tokens = (size_t)q.P * q.Lmax;
       const size_t off_f = q.prog_flags ? 0 : cv.take((size_t)q.P * 4);
+      const size_t off_nc = cv.take((size_t)q.P * 4);
+      const size_t off_code = cv.take(tokens * 8);
+      const size_t off_start = cv.take(tokens * 2);
+      const size_t off_need = cv.take(tokens);
+      const size_t off_task = cv.take(tokens * 2);
       const size_t off_p = cv.take((size_t)q.P * nch[i] * PSTRIDE * 8);
       size_t off_yc = 0, off_ych = 0, off_st = 0;
       const bool corr = mode != MODE_MSE;
@@ -898,11 +1095,17 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
         b.yc = corr ? reinterpret_cast<float *>(ws + off_yc) : nullptr;
         b.partials = reinterpret_cast<double *>(ws + off_p);
         b.flags = q.prog_flags ? q.prog_flags : reinterpret_cast<int32_t *>(ws + off_f);
+        b.code = reinterpret_cast<uint2 *>(ws + off_code);
+        b.ncode = reinterpret_cast<int32_t *>(ws + off_nc);
+        b.s_start = reinterpret_cast<int16_t *>(ws + off_start);
+        b.s_need = reinterpret_cast<uint8_t *>(ws + off_need);
+        b.s_task = reinterpret_cast<int16_t *>(ws + off_task);
         b.fitness = q.fitness;
         b.ychunk = corr ? reinterpret_cast<double *>(ws + off_ych) : nullptr;
         b.stats = corr ? reinterpret_cast<double *>(ws + off_st) : nullptr;
         b.ldx = q.ldx;
         b.item_begin = items;
+        b.prog_begin = progs;
         b.P = q.P;
         b.Lmax = q.Lmax;
         b.K = q.K;
@@ -915,6 +1118,7 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
         if (corr) bpar->corr_list[ncorr] = (int)(g - g0);
       }
       items += (long long)q.P * nch[i];
+      progs += q.P;
       if (corr) {
         corr_chunks += nch[i];
         ++ncorr;
@@ -923,10 +1127,9 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
     if (bpar) {
       bpar->nprob = (int)(g1 - g0);
       bpar->ncorr = ncorr;
+      bpar->total_progs = progs;
       bpar->total_items = items;
       bpar->queue = reinterpret_cast<unsigned long long *>(ctx->ws + off_q);
-      bpar->deep_stack = bp.deep_slots ? reinterpret_cast<float4 *>(ctx->ws + off_deep) : nullptr;
-      bpar->deep_slots = bp.deep_slots;
       bpar->warp_bytes = warp_smem_bytes(maxL);
     }
     return cv.off;
@@ -948,12 +1151,14 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
     int corr_blocks = 0;
     for (int r = 0; r < b.ncorr; ++r) corr_blocks += b.prob[b.corr_list[r]].nchunks;
     SR_CHECK_CUDA(ctx, cudaMemsetAsync(b.queue, 0, sizeof(unsigned long long), s));
+    decode_batched_kernel<<<(b.total_progs + 127) / 128, 128, 0, s>>>(b);
+    ctx->launches += 1;
     if (b.ncorr > 0) {
       ymean_batched_kernel<<<b.ncorr, PREP_THREADS, 0, s>>>(b);
       ycenter_batched_kernel<<<corr_blocks, PREP_THREADS, 0, s>>>(b);
       ctx->launches += 2;
     }
-    eval_batched_kernel<<<bp.grid, WARPS * 32, bp.smem, s>>>(b);
+    eval_batched_kernel<<<grid, WARPS * 32, smem, s>>>(b);
     finalize_batched_kernel<<<b.nprob, 256, 0, s>>>(b);
     SR_CHECK_CUDA(ctx, cudaGetLastError());
     ctx->launches += 2;
@@ -977,8 +1182,7 @@ sr_status sr_eval(sr_ctx *ctx, const uint8_t *programs, const int32_t *lengths, 
   if (P == 0) return SR_OK;
   if (!y || !fitness) return fail(ctx, SR_EINVAL, "NULL y or fitness");
   if (((uintptr_t)y) & 15) return fail(ctx, SR_EINVAL, "y must be 16-byte aligned");
-  const int mode = kind == SR_MSE ? MODE_MSE : (kind == SR_CORR ? MODE_CORR : MODE_BOTH);
-  return launch_eval(ctx, mode, programs, lengths, consts, P, Lmax, K, X, y, nvars, N, ldx,
+  return launch_eval(ctx, mode_of(kind), programs, lengths, consts, P, Lmax, K, X, y, nvars, N, ldx,
                      fitness, prog_flags, nullptr, 0);
 }
 
@@ -1085,9 +1289,9 @@ extern "C" sr_status sr_eval_noalloc(void *cuda_stream, const uint8_t *programs,
   if (kind != SR_MSE && kind != SR_CORR && kind != SR_MSE_CORR) return SR_EINVAL;
   if (P == 0) return SR_OK;
   if (!y || !fitness || (((uintptr_t)y) & 15)) return SR_EINVAL;
-  const int mode = kind == SR_MSE ? MODE_MSE : (kind == SR_CORR ? MODE_CORR : MODE_BOTH);
+  const int mode = mode_of(kind);
   // fit the plan into the array: fewer SMs' worth of persistent CTAs means
-  // fewer per-warp stacks and partial records
+  // fewer work items and partial records
   Plan pl;
   for (;;) {
     st = make_plan(&local, mode, P, Lmax, N, &pl);
