@@ -42,6 +42,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="paper", choices=["paper", "batched", "adjoint", "large", "plain"],
+                    help="paper (default, the headline): 4096 x 100k; batched: 64 problems in one launch "
+                         "vs a loop of single calls; adjoint: Adam constant optimisation; large: "
+                         "262,144 x 1M; plain: 256 x 1k, CUDA graph vs eager")
     return ap.parse_args()
 
 
@@ -335,8 +339,176 @@ def cpu_baseline(pr, y):
             "sample": f"{S} of {pr.P} programs x {pr.N} cases, MSE and 1-r^2 (two passes), {dt:.1f} s"}
 
 
+# ------------------------------------------------------------------ other workloads
+def _timed(fn, reps, stream):
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def _device_problem(pr, dev, binding, ctx, noise_seed=7):
+    """Device copies of a problem with y from the library's own predict of
+    the target (plus the problem's noise, FP64 on the host)."""
+    import torch
+    from paper_2603_12292_gb300 import inputs
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    X = t(pr.X)
+    tgt = np.zeros((1, max(pr.Lmax, len(pr.target))), np.uint8)
+    tgt[0, : len(pr.target)] = pr.target
+    yh = binding.sr_predict(ctx, t(tgt), t(np.array([len(pr.target)], np.int32)),
+                            t(pr.target_consts[None, :]), X, pr.N)[0].double().cpu().numpy()
+    if not np.all(np.isfinite(yh)):
+        yh = np.nan_to_num(yh, nan=0.0, posinf=1e6, neginf=-1e6)
+    y = inputs.add_noise(np.random.default_rng(pr.seed + noise_seed), yh, pr.noise) if pr.noise \
+        else yh.astype(np.float32)
+    return t(pr.programs), t(pr.lengths), t(pr.consts), X, t(y)
+
+
+def run_workload(args, local_rank):
+    import torch
+
+    import __graft_entry__
+    from paper_2603_12292_gb300 import binding, inputs
+    from paper_2603_12292_gb300.evolve import EvolveConfig, Evolver, Population
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    ctx = binding.Context(local_rank)
+    stream = torch.cuda.current_stream(dev)
+    line = {"higher_is_better": True, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "steps": args.steps, "warmup": args.warmup}
+
+    if args.workload == "batched":
+        shapes = inputs.batched_shapes()
+        pops, work = [], 0.0
+        for sh in shapes:
+            pr = inputs.batched_problem(sh)
+            pg, ln, cs, X, y = _device_problem(pr, dev, binding, ctx)
+            kind = binding.SR_CORR if sh["kind"] else binding.SR_MSE
+            cfg = EvolveConfig(select_kind=kind, eval_kind=kind)
+            pops.append(Population(pg, ln, cs, X, y, pr.N, cfg))
+        nodes = lambda: sum(float(p.current[1].sum()) * p.N for p in pops)
+        # (a) plain loop: one sr_eval call per problem, eager
+        def plain_loop():
+            for p in pops:
+                binding.sr_eval(ctx, *p.current, p.X, p.y, p.N, p.cfg.eval_kind, fitness=p.fitness[0])
+        # (b) one persistent launch over all problems
+        probs = [binding.make_problem(*p.current, p.X, p.y, p.N, p.cfg.eval_kind, fitness=p.fitness[0])
+                 for p in pops]
+        def batched():
+            binding.sr_eval_batched(ctx, probs)
+        n0 = nodes()
+        for f in (plain_loop, batched):
+            for _ in range(args.warmup):
+                f()
+        t_plain = _timed(plain_loop, args.steps, stream)
+        t_batch = _timed(batched, args.steps, stream)
+        # (c) the whole generation loop, batched and captured as a CUDA graph
+        ev = Evolver(ctx, pops, batched=True)
+        ev.capture(2)
+        torch.cuda.synchronize()
+        gens = 2 * max(1, args.steps // 2)
+        n_gen = nodes()
+        t_graph = _timed(lambda: ev.run(gens), 1, stream) / gens
+        line.update(metric="GPop/s, 64 problems per generation (batched + graph vs plain loop)",
+                    value=n_gen / (t_graph / 1e3) / 1e9, unit="GPop/s", ms_per_step=t_graph,
+                    scaling="weak",
+                    config={"workload": "batched-64: nvars 1-10, N log-uniform 1k-1M, P 512-8192, "
+                                        "L 4-256, MSE/1-r^2 mixed",
+                            "problems": len(pops), "node_cases_per_eval": n0},
+                    batched_eval_gpops=n0 / (t_batch / 1e3) / 1e9,
+                    plain_loop_eval_gpops=n0 / (t_plain / 1e3) / 1e9,
+                    batched_over_plain=t_plain / t_batch,
+                    generation_graph_ms=t_graph, eval_batched_ms=t_batch, eval_plain_loop_ms=t_plain)
+    elif args.workload == "adjoint":
+        pr = inputs.adjoint()
+        pg, ln, cs, X, y = _device_problem(pr, dev, binding, ctx)
+        P, K, N = pr.P, pr.K, pr.N
+        mse = torch.empty(P, dtype=torch.float64, device=dev)
+        g = torch.empty((P, K), dtype=torch.float64, device=dev)
+        m, v = torch.zeros_like(g), torch.zeros_like(g)
+        cfg = binding.adam_cfg()
+        state = {"t": 0}
+        def adam_step():
+            state["t"] += 1
+            binding.sr_eval_grad(ctx, pg, ln, cs, X, y, N, mse=mse, dconst=g)
+            binding.sr_adam_step(ctx, cs, g, m, v, state["t"], cfg)
+        # plain alternative: central differences with 2K + 1 plain evaluations
+        f0 = torch.empty(P, dtype=torch.float64, device=dev)
+        fp, fm = torch.empty_like(f0), torch.empty_like(f0)
+        c2 = cs.clone()
+        def fd_step():
+            binding.sr_eval(ctx, pg, ln, cs, X, y, N, binding.SR_MSE, fitness=f0)
+            for k in range(K):
+                c2.copy_(cs)
+                c2[:, k] += 1e-3
+                binding.sr_eval(ctx, pg, ln, c2, X, y, N, binding.SR_MSE, fitness=fp)
+                c2[:, k] -= 2e-3
+                binding.sr_eval(ctx, pg, ln, c2, X, y, N, binding.SR_MSE, fitness=fm)
+                g[:, k] = (fp - fm) / 2e-3
+            state["t"] += 1
+            binding.sr_adam_step(ctx, cs, g, m, v, state["t"], cfg)
+        for _ in range(max(1, args.warmup)):
+            adam_step()
+        steps = max(1, args.steps)
+        t_adj = _timed(adam_step, steps, stream)
+        t_fd = _timed(fd_step, 1, stream)
+        nodes = float(ln.sum()) * N
+        line.update(metric="constant-optimisation steps/s (adjoint + Adam) vs plain finite differences",
+                    value=1e3 / t_adj, unit="steps/s", ms_per_step=t_adj, scaling="weak",
+                    config={"workload": "adjoint-16384x1M: K=8, L<=96, 5 vars, 1e6 cases, Adam"},
+                    grad_gpops=nodes / (t_adj / 1e3) / 1e9,
+                    fd_steps_per_s=1e3 / t_fd, adjoint_over_fd=t_fd / t_adj)
+    elif args.workload == "large":
+        pr = inputs.large()
+        pg, ln, cs, X, y = _device_problem(pr, dev, binding, ctx)
+        cfg = EvolveConfig(select_kind=binding.SR_CORR, eval_kind=binding.SR_CORR)
+        ev = Evolver(ctx, [Population(pg, ln, cs, X, y, pr.N, cfg)])
+        for _ in range(max(1, args.warmup)):
+            ev.step()
+        torch.cuda.synchronize()
+        steps = max(1, args.steps)
+        n_before = float(ev.pops[0].current[1].sum()) * pr.N
+        t = _timed(ev.step, steps, stream)
+        line.update(metric="GPop/s (nodes x cases / s), one generation (1-r^2, selection, variation)",
+                    value=n_before / (t / 1e3) / 1e9, unit="GPop/s", ms_per_step=t, scaling="weak",
+                    config={"workload": pr.name, "programs": pr.P, "cases": pr.N, "lengths": "4-256"})
+    else:  # plain: launch-bound, CUDA graph vs eager
+        pr = inputs.plain()
+        pg, ln, cs, X, y = _device_problem(pr, dev, binding, ctx)
+        pe = Population(pg.clone(), ln.clone(), cs.clone(), X, y, pr.N,
+                        EvolveConfig(select_kind=binding.SR_MSE, eval_kind=binding.SR_MSE))
+        pgr = Population(pg.clone(), ln.clone(), cs.clone(), X, y, pr.N,
+                         EvolveConfig(select_kind=binding.SR_MSE, eval_kind=binding.SR_MSE))
+        eager, graph = Evolver(ctx, [pe]), Evolver(ctx, [pgr])
+        for _ in range(max(3, args.warmup)):
+            eager.step()
+        graph.capture(2)
+        graph.run(4)
+        torch.cuda.synchronize()
+        gens = 2 * max(5, args.steps)
+        t_e = _timed(lambda: [eager.step() for _ in range(gens)], 1, stream) / gens
+        t_g = _timed(lambda: graph.run(gens), 1, stream) / gens
+        n = float(pgr.current[1].sum()) * pr.N
+        line.update(metric="generations/s, 256 x 1k (CUDA graph vs eager launches)",
+                    value=1e3 / t_g, unit="generations/s", ms_per_step=t_g, scaling="weak",
+                    config={"workload": pr.name}, eager_generations_per_s=1e3 / t_e,
+                    graph_gpops=n / (t_g / 1e3) / 1e9, graph_over_eager=t_e / t_g)
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload != "paper" and args.impl == "ours":
+        return run_workload(args, int(os.environ.get("LOCAL_RANK", "0")))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -201,7 +201,8 @@ def condition(programs, lengths, consts, X, y, kind: int, N: int | None = None,
 
 def grad(programs, lengths, consts, X, y, N: int | None = None, nthreads: int = 0):
     """MSE, dMSE/dconst [P, K] (forward mode, FP64), the kink distance, and
-    (2/N) sum |e dyhat/dc_k| [P, K] (the scale of the sum)."""
+    gabs [P, K] = (2/N) sum |e| times the derivative propagated with absolute
+    partials (the rounding-error scale of any chain-rule evaluation order)."""
     prog = _c(programs, np.uint8)
     P, Lmax = prog.shape
     lens = _c(lengths, np.int32)

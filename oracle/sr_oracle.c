@@ -590,8 +590,12 @@ void or_condition(const uint8_t *programs, const int32_t *lengths,
  * a different method from the device's reverse sweep, on purpose.
  * Derivative conventions: d|x|/dx = sign(x) (0 at 0); a protected fallback
  * branch and a clamped exp have derivative 0; d sqrt|x| / dx = 0 at x = 0.
- * gabs (optional) receives (2/N) sum_i |e_i dyhat_i/dc_k|, the scale of the
- * sum's rounding error.
+ * gabs (optional) receives (2/N) sum_i |e_i| a_ik, where a_ik is the
+ * derivative propagated with absolute values (|da| a_a + |db| a_b at every
+ * operator): the sum of the magnitudes of all chain-rule path products, which
+ * bounds (up to a factor of the operation count times the unit roundoff) the
+ * rounding error of any evaluation order of the chain rule -- including one
+ * whose contributions cancel exactly in exact arithmetic, as for c / c.
  * *kink receives the smallest distance, over all cases, of a branch
  * argument to its switch point (|b| - 1e-3 for division, |x| - 1e-3 for
  * log, |x| for sqrt|x|, |x| - 80 for exp).
@@ -602,6 +606,8 @@ void or_grad_one(const uint8_t *tok, int len, const double *c, int K,
   double *val = (double *)malloc(sizeof(double) * (size_t)(len + 1));
   double *tan_ = (double *)malloc(sizeof(double) * (size_t)(len + 1) *
                                   (size_t)(K > 0 ? K : 1));
+  double *tab = (double *)malloc(sizeof(double) * (size_t)(len + 1) *
+                                 (size_t)(K > 0 ? K : 1));
   double s = 0.0, kmin = INFINITY;
   for (int k = 0; k < K; ++k) grad[k] = 0.0;
   if (gabs)
@@ -613,12 +619,12 @@ void or_grad_one(const uint8_t *tok, int len, const double *c, int K,
       int v = tok[t];
       if (is_var(v)) {
         val[sp] = X[(long)(v - TK_VAR0) * ldx + i];
-        for (int k = 0; k < K; ++k) tan_[sp * K + k] = 0.0;
+        for (int k = 0; k < K; ++k) tan_[sp * K + k] = tab[sp * K + k] = 0.0;
         ++sp;
       } else if (is_const(v)) {
         val[sp] = c[v - TK_CONST0];
         for (int k = 0; k < K; ++k)
-          tan_[sp * K + k] = (k == v - TK_CONST0) ? 1.0 : 0.0;
+          tan_[sp * K + k] = tab[sp * K + k] = (k == v - TK_CONST0) ? 1.0 : 0.0;
         ++sp;
       } else if (is_binary(v)) {
         --sp;
@@ -640,6 +646,8 @@ void or_grad_one(const uint8_t *tok, int len, const double *c, int K,
           }
         }
         for (int k = 0; k < K; ++k) ta[k] = da * ta[k] + db * tb[k];
+        double *aa = &tab[(sp - 1) * K], *ab = &tab[sp * K];
+        for (int k = 0; k < K; ++k) aa[k] = fabs(da) * aa[k] + fabs(db) * ab[k];
         val[sp - 1] = r;
       } else {
         double x = val[sp - 1];
@@ -673,6 +681,7 @@ void or_grad_one(const uint8_t *tok, int len, const double *c, int K,
           default: r = x * x; dx = 2.0 * x; break;
         }
         for (int k = 0; k < K; ++k) tx[k] = dx * tx[k];
+        for (int k = 0; k < K; ++k) tab[(sp - 1) * K + k] *= fabs(dx);
         val[sp - 1] = r;
       }
     }
@@ -682,7 +691,7 @@ void or_grad_one(const uint8_t *tok, int len, const double *c, int K,
     s += e * e;
     for (int k = 0; k < K; ++k) grad[k] += 2.0 * e * tan_[k];
     if (gabs)
-      for (int k = 0; k < K; ++k) gabs[k] += fabs(2.0 * e * tan_[k]);
+      for (int k = 0; k < K; ++k) gabs[k] += 2.0 * fabs(e) * tab[k];
   }
   for (int k = 0; k < K; ++k) grad[k] /= (double)N;
   if (gabs)
@@ -691,6 +700,7 @@ void or_grad_one(const uint8_t *tok, int len, const double *c, int K,
   if (kink) *kink = kmin;
   free(val);
   free(tan_);
+  free(tab);
 }
 
 /* FP64-constant evaluation of MSE for one program (finite differences). */

@@ -37,6 +37,7 @@
 #include <vector>
 
 #include "sr_common.cuh"
+#include "sr_interp.cuh"
 
 namespace sr {
 namespace {
@@ -45,47 +46,10 @@ constexpr int WARPS = 4;        // warps per CTA
 constexpr int CPL = 8;          // cases per lane per dispatched instruction (two float4)
 constexpr int STEP = 32 * CPL;  // cases per warp step
 constexpr int SLOT_BYTES = 32 * CPL * 4;  // one stack slot of a warp: [2][32 lanes] float4
-// stack slots below the top: the Sethi-Ullman schedule needs at most
-// floor(log2(SR_MAX_LMAX / 2)) + 1 values live, i.e. 8 slots below the top
-constexpr int DSM = 8;
-static_assert(SR_MAX_LMAX <= 512, "DSM = 8 covers programs of up to 512 tokens");
 constexpr int PSTRIDE = 8;      // doubles per partial record
 constexpr int TARGET_ITEMS_PER_WARP = 8;
 
 enum Mode { MODE_PREDICT = 0, MODE_MSE = 1, MODE_CORR = 2, MODE_BOTH = 3 };
-
-// decoded instruction (uint2): x = opcode | stack-slot byte offset << 8;
-// y = operand: the constant's FP32 bits, or the variable's row offset j * ldx
-enum Op : uint32_t {
-  OP_LDV = 0,   // top = x_j                        (stack empty)
-  OP_LDC,       // top = c_k
-  OP_PUSHV,     // stack[slot] = top; top = x_j
-  OP_PUSHC,     // stack[slot] = top; top = c_k
-  OP_ADD,       // top = stack[slot] op top         (left operand evaluated first)
-  OP_SUB,
-  OP_MUL,
-  OP_DIV,
-  OP_RSUB,      // top = top - stack[slot]          (right operand evaluated first)
-  OP_RDIV,      // top = top / stack[slot]
-  OP_SIN,       // top = f(top)
-  OP_COS,
-  OP_EXP,
-  OP_LOG,
-  OP_SQRT,
-  OP_SQ,
-  OP_VADD,      // top = top op x_j   (terminal right operand, evaluated second)
-  OP_VSUB,
-  OP_VMUL,
-  OP_VDIV,
-  OP_VRSUB,     // top = x_j - top    (terminal left operand, evaluated second)
-  OP_VRDIV,     // top = x_j / top
-  OP_CADD,      // top = top op c_k
-  OP_CSUB,
-  OP_CMUL,
-  OP_CDIV,
-  OP_CRSUB,     // top = c_k - top
-  OP_CRDIV,     // top = c_k / top
-};
 
 struct EvalParams {
   const uint8_t *programs;
@@ -118,41 +82,12 @@ __host__ __device__ inline int warp_smem_bytes(int Lmax) {
 }
 
 // ---------------------------------------------------------------- operators
-__device__ __forceinline__ float op_div(float a, float b) {
-  // |b| < 1e-3f in FP32 is exactly "|b| <= 1e-3" for FP32 values of b
-  return fabsf(b) < 1e-3f ? 1.0f : a / b;
-}
-__device__ __forceinline__ float op_log(float x) {
-  return fabsf(x) < 1e-3f ? 0.0f : logf(fabsf(x));
-}
-__device__ __forceinline__ float op_exp(float x) {
-  x = x > 80.0f ? 80.0f : (x < -80.0f ? -80.0f : x);  // NaN passes through
-  return expf(x);
-}
-
 #define MAP4(f, v) make_float4(f((v).x), f((v).y), f((v).z), f((v).w))
 #define ZIP4(f, a, b) make_float4(f((a).x, (b).x), f((a).y, (b).y), f((a).z, (b).z), f((a).w, (b).w))
 
 __device__ __forceinline__ float f_add(float a, float b) { return a + b; }
 __device__ __forceinline__ float f_sub(float a, float b) { return a - b; }
 __device__ __forceinline__ float f_mul(float a, float b) { return a * b; }
-__device__ __forceinline__ float f_sqrt(float x) { return sqrtf(fabsf(x)); }
-
-// sinf / cosf carry a long path for large arguments; keep one out-of-line
-// copy of it and let the inlined copies assume a moderate argument (NaN and
-// +-inf also take the out-of-line call)
-__device__ __noinline__ float sin_wide(float x) { return sinf(x); }
-__device__ __noinline__ float cos_wide(float x) { return cosf(x); }
-__device__ __forceinline__ float f_sin(float x) {
-  if (!(fabsf(x) <= 4.0e4f)) return sin_wide(x);
-  __builtin_assume(fabsf(x) <= 4.0e4f);
-  return sinf(x);
-}
-__device__ __forceinline__ float f_cos(float x) {
-  if (!(fabsf(x) <= 4.0e4f)) return cos_wide(x);
-  __builtin_assume(fabsf(x) <= 4.0e4f);
-  return cosf(x);
-}
 __device__ __forceinline__ float f_sq(float x) { return x * x; }
 
 __device__ __forceinline__ float4 splat(float c) { return make_float4(c, c, c, c); }
@@ -161,139 +96,28 @@ __device__ __forceinline__ float4 ldx4(const float *p) {
 }
 
 // ---------------------------------------------------------------- decode pre-pass
-__device__ __forceinline__ bool is_term(int v) {
-  const int c = tok_class(v);
-  return c == CLS_VAR || c == CLS_CONST;
-}
-
-__device__ __forceinline__ uint32_t operand_of(int v, const float *crow, long long ldx) {
-  return tok_class(v) == CLS_VAR ? (uint32_t)((long long)(v - TOK_VAR0) * ldx)
-                                 : __float_as_uint(crow[v - TOK_CONST0]);
-}
-
-// Validation and scheduled decoding of program `prog` (one thread).
-// Flag rules: length outside [1, Lmax]; bad byte; variable / constant index
-// out of range; depth (running sum of +1 terminal, 0 unary or bad byte, -1
-// binary) below 1 after some token; final depth not 1.
-__device__ void decode_one(const EvalParams &p, int prog) {
-  const uint8_t *tok = p.programs + (size_t)prog * p.Lmax;
-  const int L = p.lengths[prog];
-  int flags = 0;
-  if (L < 1 || L > p.Lmax) {
-    flags = SR_PF_BAD_LENGTH;
-  } else {
-    int depth = 0;
-    for (int t = 0; t < L; ++t) {
-      const int v = tok[t];
-      const int cls = tok_class(v);
-      if (cls == CLS_BAD) flags |= SR_PF_BAD_TOKEN;
-      if (cls == CLS_VAR && v - TOK_VAR0 >= p.nvars) flags |= SR_PF_BAD_VAR;
-      if (cls == CLS_CONST && v - TOK_CONST0 >= p.K) flags |= SR_PF_BAD_CONST;
-      depth += cls_effect(cls);
-      if (depth < 1) flags |= SR_PF_UNDERFLOW;
-    }
-    if (depth != 1) flags |= SR_PF_BAD_FINAL;
-  }
-  p.flags[prog] = flags;
-  if (flags) {
-    p.ncode[prog] = 0;
-    return;
-  }
-  int16_t *start = p.s_start + (size_t)prog * p.Lmax;
-  uint8_t *need = p.s_need + (size_t)prog * p.Lmax;
-  int16_t *task = p.s_task + (size_t)prog * p.Lmax;
-  // pass 1, postfix order is bottom-up: subtree starts and stack needs
-  // (terminal 1; unary as its child; binary max of the children, +1 on a tie)
-  int sp = 0;
-  for (int t = 0; t < L; ++t) {
-    const int cls = tok_class(tok[t]);
-    if (cls == CLS_VAR || cls == CLS_CONST) {
-      start[t] = (int16_t)t;
-      need[t] = 1;
-      task[sp++] = (int16_t)t;
-    } else if (cls == CLS_UNARY) {
-      const int c = task[sp - 1];
-      start[t] = start[c];
-      need[t] = need[c];
-      task[sp - 1] = (int16_t)t;
-    } else {
-      const int b = task[--sp], a = task[sp - 1];
-      const int na = need[a], nb = need[b];
-      start[t] = start[a];
-      need[t] = (uint8_t)(na == nb ? na + 1 : (na > nb ? na : nb));
-      task[sp - 1] = (int16_t)t;
-    }
-  }
-  // pass 2, emission: depth-first from the root, larger-need child first;
-  // work stack entries are node << 2 | phase.  d counts the live values
-  // (top included): a terminal pushes the old top into slot d - 1, a binary
-  // operator pops slot d - 2.
-  const float *crow = p.consts + (size_t)prog * p.K;
-  uint2 *code = p.code + (size_t)prog * p.Lmax;
-  int n = 0, d = 0;
-  sp = 0;
-  task[sp++] = (int16_t)((L - 1) << 2);
-  while (sp > 0) {
-    const int e = task[sp - 1];
-    const int node = e >> 2, ph = e & 3;
-    const int v = tok[node];
-    const int cls = tok_class(v);
-    if (cls == CLS_VAR || cls == CLS_CONST) {
-      --sp;
-      if (d > DSM) {  // cannot happen (depth <= 9 for <= 512 tokens); never write past the slots
-        p.flags[prog] = SR_PF_TOO_DEEP;
-        p.ncode[prog] = 0;
-        return;
-      }
-      const bool var = cls == CLS_VAR;
-      uint32_t op = var ? OP_LDV : OP_LDC;
-      if (d > 0) op = (uint32_t)(var ? OP_PUSHV : OP_PUSHC) | ((uint32_t)((d - 1) * SLOT_BYTES) << 8);
-      code[n++] = make_uint2(op, operand_of(v, crow, p.ldx));
-      ++d;
-    } else if (cls == CLS_UNARY) {
-      if (ph == 0) {
-        task[sp - 1] = (int16_t)(e | 1);
-        task[sp++] = (int16_t)((node - 1) << 2);
-      } else {
-        --sp;
-        code[n++] = make_uint2((uint32_t)(OP_SIN + (v - TOK_SIN)), 0u);
-      }
-    } else {
-      const int b = node - 1, a = start[b] - 1;
-      const bool rev = need[b] > need[a];
-      const int first = rev ? b : a, second = rev ? a : b;
-      if (ph == 0) {
-        task[sp - 1] = (int16_t)(e | 1);
-        task[sp++] = (int16_t)(first << 2);
-      } else if (ph == 1 && is_term(tok[second])) {
-        --sp;
-        const int w = tok[second];
-        const bool var = tok_class(w) == CLS_VAR;
-        uint32_t op;
-        if (rev && v == TOK_SUB) op = var ? OP_VRSUB : OP_CRSUB;
-        else if (rev && v == TOK_DIV) op = var ? OP_VRDIV : OP_CRDIV;
-        else op = (uint32_t)((var ? OP_VADD : OP_CADD) + v);  // + and * commute exactly
-        code[n++] = make_uint2(op, operand_of(w, crow, p.ldx));
-      } else if (ph == 1) {
-        task[sp - 1] = (int16_t)((e & ~3) | 2);
-        task[sp++] = (int16_t)(second << 2);
-      } else {
-        --sp;
-        uint32_t op;
-        if (rev && v == TOK_SUB) op = OP_RSUB;
-        else if (rev && v == TOK_DIV) op = OP_RDIV;
-        else op = (uint32_t)(OP_ADD + v);
-        code[n++] = make_uint2(op | ((uint32_t)((d - 2) * SLOT_BYTES) << 8), 0u);
-        --d;
-      }
-    }
-  }
-  p.ncode[prog] = n;
+__device__ __forceinline__ DecodeArgs decode_args(const EvalParams &p) {
+  DecodeArgs a;
+  a.programs = p.programs;
+  a.lengths = p.lengths;
+  a.consts = p.consts;
+  a.Lmax = p.Lmax;
+  a.K = p.K;
+  a.nvars = p.nvars;
+  a.ldx = p.ldx;
+  a.slot_bytes = SLOT_BYTES;
+  a.code = p.code;
+  a.ncode = p.ncode;
+  a.flags = p.flags;
+  a.s_start = p.s_start;
+  a.s_need = p.s_need;
+  a.s_task = p.s_task;
+  return a;
 }
 
 __global__ void decode_kernel(EvalParams p) {
   const int prog = blockIdx.x * blockDim.x + threadIdx.x;
-  if (prog < p.P) decode_one(p, prog);
+  if (prog < p.P) decode_one(decode_args(p), prog);
 }
 
 // ---------------------------------------------------------------- interpreter
@@ -390,8 +214,8 @@ __device__ __forceinline__ V8 interpret(const uint2 *__restrict__ code, int n, c
   V8 T = splat8(0.f);
   for (int ip = 0; ip < n; ++ip) {
     const uint2 w = code[ip];
-    const uint32_t off = w.x >> 8;
-    switch (w.x & 0xffu) {
+    const uint32_t off = ins_off(w);
+    switch (ins_op(w)) {
       case OP_LDV: T = ldX8(xa, xb, w.y); break;
       case OP_LDC: T = splat8(__uint_as_float(w.y)); break;
       case OP_PUSHV: st8(stk, off, T); T = ldX8(xa, xb, w.y); break;
@@ -648,7 +472,7 @@ __global__ void decode_batched_kernel(const __grid_constant__ BatchParams b) {
     else hi = mid - 1;
   }
   const EvalParams p = view(b.prob[lo]);
-  decode_one(p, g - b.prob[lo].prog_begin);
+  decode_one(decode_args(p), g - b.prob[lo].prog_begin);
 }
 
 // Work items of every problem come from one atomic counter: problem q owns

@@ -1,38 +1,45 @@
 // sr_grad.cu -- reverse-mode derivative of the interpreter (dMSE/dconst) and
 // the Adam update of the constants.
 //
-// Layout: a work item is (case chunk, program), handed to one warp by an
-// atomic counter, as for evaluation.  Lane 0 decodes the program into
-// shared memory: per token its operator and, for a binary operator, the
-// token that produced its left operand (the right operand is always the
-// token just before).  Each lane then takes one case at a time:
-//   forward  -- every token's output goes to a per-lane tape in shared
-//               memory, tape[t][lane] (conflict-free), operands read back
-//               from the tape;
-//   reverse  -- tokens from last to first with the current adjoint in a
-//               register and a per-lane adjoint stack for pending left
-//               subtrees: a binary op pushes adj * d/da and continues into
-//               its right operand with adj * d/db; a unary op multiplies
-//               by its derivative; a constant terminal adds adj into its
-//               slot's gradient; after any terminal the next adjoint is
-//               popped.  No tape leaves the chip: the forward pass is
-//               recomputed instead of stored.
-// Sums: per lane FP32 compensated (Kahan) over the item's cases, FP64 across
-// lanes (shuffles) and chunks (fixed-order finalize).
+// The adjoint runs over the same scheduled instruction stream as evaluation
+// (sr_interp.cuh: Sethi-Ullman order, at most 8 stack slots, fused terminal
+// operators).  Work item = (case chunk, program), one warp, 2 cases per lane
+// (one float2 per value), 64 cases per step.  Per step:
+//   forward  -- the program runs with the top of stack in registers and the
+//               slots below in shared memory.  What the reverse sweep needs
+//               goes on a LIFO tape: for a unary operator its local
+//               derivative, computed here next to the value (cos x with
+//               sin x from one sincos, exp x, 1/x, +-1/(2 sqrt|x|), 2x), so
+//               that the reverse step is one multiply; for a product both
+//               factors; for a quotient the denominator and the result.  A
+//               terminal operand fused into * or / needs no entry (x_j is
+//               re-read, c_k is in the instruction).  The tape lives in
+//               shared memory up to a capacity chosen per launch and in this
+//               warp's global scratch beyond it.
+//   reverse  -- the instructions are walked backwards with the adjoint of
+//               the top in registers; a binary operator writes the adjoint
+//               of the operand it popped into that operand's stack slot (the
+//               values there are dead by then), and the push that produced
+//               the operand reads it back; constants add their adjoint into
+//               their gradient sum.
+// Nothing is kept between an evaluation and this call: the forward pass is
+// recomputed.  Sums: per lane FP32 compensated (Kahan) over the item's
+// cases, FP64 across lanes (shuffles) and chunks (fixed-order finalize).
 #include <math.h>
 
 #include "sr_common.cuh"
+#include "sr_interp.cuh"
 
 namespace sr {
 namespace {
 
-constexpr int GWARPS = 4;         // warps per CTA
-constexpr int GSTRIDE = 32;       // doubles per partial record: [0] sum e^2, [1 + k] sum e dyhat/dc_k
-constexpr int TARGET_ITEMS_PER_WARP = 8;
-
-// decoded token: bits 0..7 class/op, 8..15 operand index, 16..31 left operand token
-enum GOp : uint32_t { G_VAR = 0, G_CONST, G_ADD, G_SUB, G_MUL, G_DIV, G_SIN, G_COS, G_EXP, G_LOG,
-                      G_SQRT, G_SQ };
+constexpr int GWARPS = 4;                // warps per CTA
+constexpr int GCPL = 2;                  // cases per lane (one float2)
+constexpr int GSTEP = 32 * GCPL;         // cases per warp step
+constexpr int GSLOT = GSTEP * 4;         // bytes of one stack slot / tape entry of a warp
+constexpr int GSTRIDE = 32;              // doubles per partial record: [0] sum e^2, [1 + k] sum e dyhat/dc_k
+constexpr int GTARGET_ITEMS_PER_WARP = 24;
+constexpr int GCTAS_PER_SM = 3;          // shared-memory budget: 12 warps per SM
 
 struct GradParams {
   const uint8_t *programs;
@@ -47,26 +54,100 @@ struct GradParams {
   long long total_items;
   double *partials;   // [P * nchunks][GSTRIDE]
   int32_t *flags;     // [P]
+  uint2 *code;        // [P][Lmax] scheduled instructions (slot bytes GSLOT)
+  int32_t *ncode;     // [P]
+  int16_t *s_start;
+  uint8_t *s_need;
+  int16_t *s_task;
   unsigned long long *queue;
+  char *gtape;        // per warp: (Lmax - tcap) entries of GSLOT bytes
+  int tcap;           // tape entries in shared memory
   int warp_bytes;
-  int adj_slots;
 };
 
-__host__ __device__ inline int grad_warp_bytes(int Lmax) {
-  const int adj_slots = (Lmax + 1) / 2 + 1;
-  // tape [Lmax][32] | adjoint stack [adj_slots][32] | gradient sums and
-  // compensations [2][16][32] | code [Lmax] | constants [16]
-  return Lmax * 128 + adj_slots * 128 + 2 * 16 * 128 + ((Lmax * 4 + 15) / 16) * 16 + 64;
+// shared memory of one warp: stack slots [DSM] | gradient sums and
+// compensations [2][K][32] | code [Lmax] | tape [tcap]
+__host__ __device__ inline int grad_fixed_bytes(int Lmax, int K) {
+  return DSM * GSLOT + 2 * K * 128 + ((Lmax * 8 + 15) / 16) * 16;
 }
 
-__device__ __forceinline__ float op_div(float a, float b) {
-  return fabsf(b) < 1e-3f ? 1.0f : a / b;
+__device__ __forceinline__ DecodeArgs grad_decode_args(const GradParams &p) {
+  DecodeArgs a;
+  a.programs = p.programs;
+  a.lengths = p.lengths;
+  a.consts = p.consts;
+  a.Lmax = p.Lmax;
+  a.K = p.K;
+  a.nvars = p.nvars;
+  a.ldx = p.ldx;
+  a.slot_bytes = GSLOT;
+  a.code = p.code;
+  a.ncode = p.ncode;
+  a.flags = p.flags;
+  a.s_start = p.s_start;
+  a.s_need = p.s_need;
+  a.s_task = p.s_task;
+  return a;
 }
-__device__ __forceinline__ float op_log(float x) { return fabsf(x) < 1e-3f ? 0.0f : logf(fabsf(x)); }
-__device__ __forceinline__ float op_exp(float x) {
-  x = x > 80.0f ? 80.0f : (x < -80.0f ? -80.0f : x);
-  return expf(x);
+
+__global__ void grad_decode_kernel(GradParams p) {
+  const int prog = blockIdx.x * blockDim.x + threadIdx.x;
+  if (prog < p.P) decode_one(grad_decode_args(p), prog);
 }
+
+// ---------------------------------------------------------------- float2 helpers
+__device__ __forceinline__ float2 splat2(float c) { return make_float2(c, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return make_float2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 lo2(float4 r) { return make_float2(r.x, r.y); }
+__device__ __forceinline__ float2 hi2(float4 r) { return make_float2(r.z, r.w); }
+
+// Out-of-line operators (one copy of each long body keeps the interpreter
+// loop inside the instruction cache).  fwd_* return (value.x, value.y,
+// derivative.x, derivative.y) under the derivative conventions of the
+// oracle: a protected fallback, a clamped exp and sqrt|x| at 0 have
+// derivative 0.
+static __device__ __noinline__ float2 sincos_wide(float x) {
+  float s, c;
+  sincosf(x, &s, &c);
+  return make_float2(s, c);
+}
+__device__ __forceinline__ float2 f_sincos(float x) {
+  if (!(fabsf(x) <= 4.0e4f)) return sincos_wide(x);
+  __builtin_assume(fabsf(x) <= 4.0e4f);
+  float s, c;
+  sincosf(x, &s, &c);
+  return make_float2(s, c);
+}
+__device__ __noinline__ float4 fwd_sin(float2 x) {
+  const float2 a = f_sincos(x.x), b = f_sincos(x.y);
+  return make_float4(a.x, b.x, a.y, b.y);
+}
+__device__ __noinline__ float4 fwd_cos(float2 x) {
+  const float2 a = f_sincos(x.x), b = f_sincos(x.y);
+  return make_float4(a.y, b.y, -a.x, -b.x);
+}
+__device__ __forceinline__ float d_exp(float x, float v) { return (x > 80.0f || x < -80.0f) ? 0.0f : v; }
+__device__ __noinline__ float4 fwd_exp(float2 x) {
+  const float a = op_exp(x.x), b = op_exp(x.y);
+  return make_float4(a, b, d_exp(x.x, a), d_exp(x.y, b));
+}
+__device__ __forceinline__ float d_log(float x) { return fabsf(x) < 1e-3f ? 0.0f : 1.0f / x; }
+__device__ __noinline__ float4 fwd_log(float2 x) {
+  return make_float4(op_log(x.x), op_log(x.y), d_log(x.x), d_log(x.y));
+}
+__device__ __forceinline__ float d_sqrt(float x, float v) { return x == 0.0f ? 0.0f : copysignf(0.5f / v, x); }
+__device__ __noinline__ float4 fwd_sqrt(float2 x) {
+  const float a = f_sqrt(x.x), b = f_sqrt(x.y);
+  return make_float4(a, b, d_sqrt(x.x, a), d_sqrt(x.y, b));
+}
+// protected quotient (the interpreter's operator)
+__device__ __noinline__ float2 pdiv2(float2 a, float2 b) { return make_float2(op_div(a.x, b.x), op_div(a.y, b.y)); }
+// adjoint through a protected quotient: a / den, 0 where the fallback was taken
+__device__ __forceinline__ float qdiv(float a, float d) { return fabsf(d) < 1e-3f ? 0.0f : a / d; }
+__device__ __noinline__ float2 qdiv2(float2 a, float2 d) { return make_float2(qdiv(a.x, d.x), qdiv(a.y, d.y)); }
 
 struct Kahan {
   float s = 0.f, c = 0.f;
@@ -85,53 +166,53 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Serial decode by the calling lane: validation flags (same rules as the
-// evaluation path), operator codes and left-operand tokens.  `last` is
-// scratch of (Lmax + 2) ints.
-__device__ int decode_serial(const uint8_t *__restrict__ tok, int L, int Lmax, int nvars, int K,
-                             uint32_t *code, int *last) {
-  if (L < 1 || L > Lmax) return SR_PF_BAD_LENGTH;
-  int flags = 0, depth = 0;
-  for (int t = 0; t < L; ++t) {
-    const int v = tok[t];
-    const int cls = tok_class(v);
-    uint32_t op = 0, arg = 0, left = 0;
-    if (cls == CLS_VAR) {
-      op = G_VAR;
-      arg = (uint32_t)(v - TOK_VAR0);
-      if ((int)arg >= nvars) flags |= SR_PF_BAD_VAR;
-    } else if (cls == CLS_CONST) {
-      op = G_CONST;
-      arg = (uint32_t)(v - TOK_CONST0);
-      if ((int)arg >= K) flags |= SR_PF_BAD_CONST;
-    } else if (cls == CLS_UNARY) {
-      op = G_SIN + (uint32_t)(v - TOK_SIN);
-    } else if (cls == CLS_BINARY) {
-      op = G_ADD + (uint32_t)v;
-    } else {
-      flags |= SR_PF_BAD_TOKEN;
-    }
-    depth += cls_effect(cls);
-    if (depth < 1) flags |= SR_PF_UNDERFLOW;
-    if (cls == CLS_BINARY && depth >= 1 && depth <= Lmax) left = (uint32_t)last[depth];
-    if (depth >= 0 && depth <= Lmax + 1) last[depth] = t;
-    code[t] = op | (arg << 8) | (left << 16);
-  }
-  if (depth != 1) flags |= SR_PF_BAD_FINAL;
-  return flags;
+struct GradWarp {
+  char *slot;    // this lane's entry of stack slot 0 (shared)
+  float *gs;     // gradient sums [K][32] (shared)
+  float *gc;     // their compensations [K][32]
+  uint2 *code;   // this warp's code (shared)
+  char *ts;      // this lane's entry of tape entry 0 (shared)
+  char *tg;      // this lane's entry of the first global tape entry
+  int tcap;
+  int lane;
+};
+
+__device__ __forceinline__ float2 *slot_at(const GradWarp &w, uint32_t off) {
+  return reinterpret_cast<float2 *>(w.slot + off);
+}
+__device__ __forceinline__ float2 *tape_at(const GradWarp &w, int i) {
+  return i < w.tcap ? reinterpret_cast<float2 *>(w.ts + (size_t)i * GSLOT)
+                    : reinterpret_cast<float2 *>(w.tg + (size_t)(i - w.tcap) * GSLOT);
+}
+// add this lane's valid cases of v into constant k's compensated sum
+__device__ __forceinline__ void gacc(const GradWarp &w, int k, float2 v, bool ok0, bool ok1) {
+  const float x = (ok0 ? v.x : 0.0f) + (ok1 ? v.y : 0.0f);
+  float *s = w.gs + k * 32 + w.lane, *c = w.gc + k * 32 + w.lane;
+  const float sv = *s, cv = *c;
+  const float yv = x - cv;
+  const float t = sv + yv;
+  *c = (t - sv) - yv;
+  *s = t;
+}
+__device__ __forceinline__ float2 ldx2(const float *xr, uint32_t off) {
+  return __ldg(reinterpret_cast<const float2 *>(xr + off));
 }
 
 __global__ void __launch_bounds__(GWARPS * 32) grad_kernel(GradParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned char *wb = smem + (size_t)warp * p.warp_bytes;
-  float *tape = reinterpret_cast<float *>(wb);                          // [Lmax][32]
-  float *astk = tape + (size_t)p.Lmax * 32;                             // [adj_slots][32]
-  float *gs = astk + (size_t)p.adj_slots * 32;                          // [16][32]
-  float *gc = gs + 16 * 32;                                             // [16][32]
-  uint32_t *code = reinterpret_cast<uint32_t *>(gc + 16 * 32);          // [Lmax]
-  float *cv = reinterpret_cast<float *>(code + ((p.Lmax * 4 + 15) / 16) * 4);  // [16]
-  // `last` for the serial decode reuses this lane's adjoint-stack column
+  GradWarp w;
+  w.slot = reinterpret_cast<char *>(wb) + lane * 8;
+  w.gs = reinterpret_cast<float *>(wb + DSM * GSLOT);
+  w.gc = w.gs + p.K * 32;
+  w.code = reinterpret_cast<uint2 *>(wb + DSM * GSLOT + 2 * p.K * 128);
+  w.ts = reinterpret_cast<char *>(wb + grad_fixed_bytes(p.Lmax, p.K)) + lane * 8;
+  const int gw = blockIdx.x * GWARPS + warp;
+  w.tg = p.gtape ? p.gtape + (size_t)gw * (p.Lmax - p.tcap) * GSLOT + lane * 8 : nullptr;
+  w.tcap = p.tcap;
+  w.lane = lane;
+
   for (;;) {
     unsigned long long item = 0;
     if (lane == 0) item = atomicAdd(p.queue, 1ull);
@@ -139,102 +220,146 @@ __global__ void __launch_bounds__(GWARPS * 32) grad_kernel(GradParams p) {
     if ((long long)item >= p.total_items) break;
     const int c = (int)(item / (unsigned long long)p.P);
     const int prog = (int)(item % (unsigned long long)p.P);
-    const int L = p.lengths[prog];
+    if (p.flags[prog]) continue;
+    const int n = p.ncode[prog];
     __syncwarp();
-    int flags = 0;
-    if (lane == 0) {
-      // astk (adj_slots * 32 ints) is free here and larger than Lmax + 2
-      flags = decode_serial(p.programs + (size_t)prog * p.Lmax, L, p.Lmax, p.nvars, p.K, code,
-                            reinterpret_cast<int *>(astk));
-      if (c == 0) p.flags[prog] = flags;
-    }
-    flags = __shfl_sync(FULL, flags, 0);
-    double *rec = p.partials + ((size_t)prog * p.nchunks + c) * GSTRIDE;
-    if (flags) continue;
-    if (lane < p.K) cv[lane] = p.consts[(size_t)prog * p.K + lane];
+    const uint2 *src = p.code + (size_t)prog * p.Lmax;
+    for (int i = lane; i < n; i += 32) w.code[i] = src[i];
     for (int k = 0; k < p.K; ++k) {
-      gs[k * 32 + lane] = 0.f;
-      gc[k * 32 + lane] = 0.f;
+      w.gs[k * 32 + lane] = 0.f;
+      w.gc[k * 32 + lane] = 0.f;
     }
     __syncwarp();
 
     const int cbeg = c * p.chunk, cend = min(p.N, cbeg + p.chunk);
+    const int last_pair = (cend - 1) & ~1;
     Kahan se;
-    for (int i = cbeg + lane; i < cend; i += 32) {
-      // forward: tape[t] = output of token t
-      for (int t = 0; t < L; ++t) {
-        const uint32_t w = code[t];
-        const int arg = (w >> 8) & 0xff;
-        float r;
-        switch (w & 0xff) {
-          case G_VAR: r = __ldg(p.X + arg * p.ldx + i); break;
-          case G_CONST: r = cv[arg]; break;
-          case G_ADD: r = tape[(w >> 16) * 32 + lane] + tape[(t - 1) * 32 + lane]; break;
-          case G_SUB: r = tape[(w >> 16) * 32 + lane] - tape[(t - 1) * 32 + lane]; break;
-          case G_MUL: r = tape[(w >> 16) * 32 + lane] * tape[(t - 1) * 32 + lane]; break;
-          case G_DIV: r = op_div(tape[(w >> 16) * 32 + lane], tape[(t - 1) * 32 + lane]); break;
-          case G_SIN: r = sinf(tape[(t - 1) * 32 + lane]); break;
-          case G_COS: r = cosf(tape[(t - 1) * 32 + lane]); break;
-          case G_EXP: r = op_exp(tape[(t - 1) * 32 + lane]); break;
-          case G_LOG: r = op_log(tape[(t - 1) * 32 + lane]); break;
-          case G_SQRT: r = sqrtf(fabsf(tape[(t - 1) * 32 + lane])); break;
-          default: { const float x = tape[(t - 1) * 32 + lane]; r = x * x; } break;
+    for (int base = cbeg; base < cend; base += GSTEP) {
+      const int c0 = base + 2 * lane;
+      const bool ok0 = c0 < cend, ok1 = c0 + 1 < cend;
+      const float *xr = p.X + (ok0 ? c0 : last_pair);
+      int tp = 0;
+      auto push = [&](float2 v) { *tape_at(w, tp++) = v; };
+      auto pop = [&]() { return *tape_at(w, --tp); };
+      // ---- forward
+      float2 T = splat2(0.f);
+      for (int ip = 0; ip < n; ++ip) {
+        const uint2 ins = w.code[ip];
+        const uint32_t off = ins_off(ins);
+        const float cv = __uint_as_float(ins.y);
+        switch (ins_op(ins)) {
+          case OP_LDV: T = ldx2(xr, ins.y); break;
+          case OP_LDC: T = splat2(cv); break;
+          case OP_PUSHV: *slot_at(w, off) = T; T = ldx2(xr, ins.y); break;
+          case OP_PUSHC: *slot_at(w, off) = T; T = splat2(cv); break;
+          case OP_ADD: { const float2 a = *slot_at(w, off); T = add2(a, T); } break;
+          case OP_SUB: { const float2 a = *slot_at(w, off); T = sub2(a, T); } break;
+          case OP_RSUB: { const float2 b = *slot_at(w, off); T = sub2(T, b); } break;
+          case OP_MUL: { const float2 a = *slot_at(w, off); push(a); push(T); T = mul2(a, T); } break;
+          case OP_DIV: { const float2 a = *slot_at(w, off); push(T); T = pdiv2(a, T); push(T); } break;
+          case OP_RDIV: { const float2 b = *slot_at(w, off); push(b); T = pdiv2(T, b); push(T); } break;
+          case OP_SIN: { const float4 r = fwd_sin(T); push(hi2(r)); T = lo2(r); } break;
+          case OP_COS: { const float4 r = fwd_cos(T); push(hi2(r)); T = lo2(r); } break;
+          case OP_EXP: { const float4 r = fwd_exp(T); push(hi2(r)); T = lo2(r); } break;
+          case OP_LOG: { const float4 r = fwd_log(T); push(hi2(r)); T = lo2(r); } break;
+          case OP_SQRT: { const float4 r = fwd_sqrt(T); push(hi2(r)); T = lo2(r); } break;
+          case OP_SQ: push(add2(T, T)); T = mul2(T, T); break;
+          case OP_VADD: T = add2(T, ldx2(xr, ins.y)); break;
+          case OP_VSUB: T = sub2(T, ldx2(xr, ins.y)); break;
+          case OP_VRSUB: T = sub2(ldx2(xr, ins.y), T); break;
+          case OP_VMUL: T = mul2(T, ldx2(xr, ins.y)); break;
+          case OP_VDIV: T = pdiv2(T, ldx2(xr, ins.y)); break;
+          case OP_VRDIV: push(T); T = pdiv2(ldx2(xr, ins.y), T); push(T); break;
+          case OP_CADD: T = add2(T, splat2(cv)); break;
+          case OP_CSUB: T = sub2(T, splat2(cv)); break;
+          case OP_CRSUB: T = sub2(splat2(cv), T); break;
+          case OP_CMUL: push(T); T = mul2(T, splat2(cv)); break;
+          case OP_CDIV: T = pdiv2(T, splat2(cv)); push(T); break;
+          case OP_CRDIV: push(T); T = pdiv2(splat2(cv), T); push(T); break;
+          default: break;
         }
-        tape[t * 32 + lane] = r;
       }
-      const float e = tape[(L - 1) * 32 + lane] - __ldg(p.y + i);
-      se.add(e * e);
-      // reverse sweep
-      float adj = e;
-      int sp = 0;
-      for (int t = L - 1; t >= 0; --t) {
-        const uint32_t w = code[t];
-        const int op = w & 0xff;
-        if (op == G_VAR || op == G_CONST) {
-          if (op == G_CONST) {
-            const int k = (w >> 8) & 0xff;
-            // compensated per-lane accumulation of this constant's gradient
-            const float yv = adj - gc[k * 32 + lane];
-            const float s0 = gs[k * 32 + lane];
-            const float tt = s0 + yv;
-            gc[k * 32 + lane] = (tt - s0) - yv;
-            gs[k * 32 + lane] = tt;
-          }
-          if (sp > 0) adj = astk[(--sp) * 32 + lane];
-          continue;
-        }
-        const float out = tape[t * 32 + lane];
-        const float b = tape[(t - 1) * 32 + lane];  // right operand, or the unary argument
-        switch (op) {
-          case G_ADD: astk[(sp++) * 32 + lane] = adj; break;
-          case G_SUB: astk[(sp++) * 32 + lane] = adj; adj = -adj; break;
-          case G_MUL: {
-            const float a = tape[(w >> 16) * 32 + lane];
-            astk[(sp++) * 32 + lane] = adj * b;
-            adj = adj * a;
+      // ---- loss and seed: e = yhat - y on valid cases, 0 elsewhere
+      const float y0 = ok0 ? __ldg(p.y + c0) : 0.0f, y1 = ok1 ? __ldg(p.y + c0 + 1) : 0.0f;
+      const float2 e = make_float2(ok0 ? T.x - y0 : 0.0f, ok1 ? T.y - y1 : 0.0f);
+      se.add(e.x * e.x + e.y * e.y);
+      // ---- reverse
+      float2 aT = e;
+      for (int ip = n - 1; ip >= 0; --ip) {
+        const uint2 ins = w.code[ip];
+        const uint32_t off = ins_off(ins);
+        const float cv = __uint_as_float(ins.y);
+        const int k = ins_k(ins);
+        switch (ins_op(ins)) {
+          case OP_LDV: break;
+          case OP_LDC: gacc(w, k, aT, ok0, ok1); break;
+          case OP_PUSHV: aT = *slot_at(w, off); break;
+          case OP_PUSHC: gacc(w, k, aT, ok0, ok1); aT = *slot_at(w, off); break;
+          case OP_ADD: *slot_at(w, off) = aT; break;
+          case OP_SUB: *slot_at(w, off) = aT; aT = neg2(aT); break;
+          case OP_RSUB: *slot_at(w, off) = neg2(aT); break;
+          case OP_MUL: {  // T = a t
+            const float2 t = pop(), a = pop();
+            *slot_at(w, off) = mul2(aT, t);
+            aT = mul2(aT, a);
           } break;
-          case G_DIV: {
-            if (fabsf(b) < 1e-3f) {
-              astk[(sp++) * 32 + lane] = 0.f;
-              adj = 0.f;
-            } else {
-              astk[(sp++) * 32 + lane] = adj / b;
-              adj = -adj * out / b;
-            }
+          case OP_DIV: {  // T = a / t: dT/da = 1/t, dT/dt = -T/t
+            const float2 Tn = pop(), t = pop();
+            const float2 q = qdiv2(aT, t);
+            *slot_at(w, off) = q;
+            aT = neg2(mul2(q, Tn));
           } break;
-          case G_SIN: adj = adj * cosf(b); break;
-          case G_COS: adj = -adj * sinf(b); break;
-          case G_EXP: adj = (b > 80.0f || b < -80.0f) ? 0.f : adj * out; break;
-          case G_LOG: adj = fabsf(b) < 1e-3f ? 0.f : adj / b; break;
-          case G_SQRT: adj = b == 0.0f ? 0.f : (b > 0.0f ? adj * 0.5f / out : -adj * 0.5f / out); break;
-          default: adj = adj * 2.0f * b; break;
+          case OP_RDIV: {  // T = t / b
+            const float2 Tn = pop(), b = pop();
+            const float2 q = qdiv2(aT, b);
+            *slot_at(w, off) = neg2(mul2(q, Tn));
+            aT = q;
+          } break;
+          case OP_SIN:
+          case OP_COS:
+          case OP_EXP:
+          case OP_LOG:
+          case OP_SQRT:
+          case OP_SQ: { const float2 d = pop(); aT = mul2(aT, d); } break;
+          case OP_VADD:
+          case OP_VSUB: break;
+          case OP_VRSUB: aT = neg2(aT); break;
+          case OP_VMUL: aT = mul2(aT, ldx2(xr, ins.y)); break;
+          case OP_VDIV: aT = qdiv2(aT, ldx2(xr, ins.y)); break;
+          case OP_VRDIV: {  // T = v / t
+            const float2 Tn = pop(), t = pop();
+            aT = neg2(mul2(qdiv2(aT, t), Tn));
+          } break;
+          case OP_CADD: gacc(w, k, aT, ok0, ok1); break;
+          case OP_CSUB: gacc(w, k, neg2(aT), ok0, ok1); break;
+          case OP_CRSUB: gacc(w, k, aT, ok0, ok1); aT = neg2(aT); break;
+          case OP_CMUL: {  // T = t c
+            const float2 t = pop();
+            gacc(w, k, mul2(aT, t), ok0, ok1);
+            aT = mul2(aT, splat2(cv));
+          } break;
+          case OP_CDIV: {  // T = t / c: dT/dt = 1/c, dT/dc = -T/c
+            const float2 Tn = pop();
+            const float2 q = qdiv2(aT, splat2(cv));
+            gacc(w, k, neg2(mul2(q, Tn)), ok0, ok1);
+            aT = q;
+          } break;
+          case OP_CRDIV: {  // T = c / t: dT/dc = 1/t, dT/dt = -T/t
+            const float2 Tn = pop(), t = pop();
+            const float2 q = qdiv2(aT, t);
+            gacc(w, k, q, ok0, ok1);
+            aT = neg2(mul2(q, Tn));
+          } break;
+          default: break;
         }
       }
     }
+    double *rec = p.partials + ((size_t)prog * p.nchunks + c) * GSTRIDE;
     const double sv = warp_sum(se.value());
     if (lane == 0) rec[0] = sv;
+    __syncwarp();
     for (int k = 0; k < p.K; ++k) {
-      const double g = warp_sum((double)gs[k * 32 + lane] - (double)gc[k * 32 + lane]);
+      const double g = warp_sum((double)w.gs[k * 32 + lane] - (double)w.gc[k * 32 + lane]);
       if (lane == 0) rec[1 + k] = g;
     }
   }
@@ -293,37 +418,49 @@ sr_status sr_eval_grad(sr_ctx *ctx, const uint8_t *programs, const int32_t *leng
   using namespace sr;
   if (!ctx) return SR_EINVAL;
   if (P < 0 || Lmax < 1 || Lmax > SR_MAX_LMAX || K < 1 || K > SR_MAX_CONSTS || nvars < 1 ||
-      nvars > SR_MAX_VARS || N < 1 || ldx < N)
+      nvars > SR_MAX_VARS || N < 1 || ldx < N || ldx % 4 || (long long)ldx * nvars > 0xFFFFFFFFll)
     return fail(ctx, SR_EINVAL, "bad sr_eval_grad shape");
   if (P == 0) return SR_OK;
   if (!programs || !lengths || !consts || !X || !y || !mse || !dconst)
     return fail(ctx, SR_EINVAL, "NULL pointer");
+  if (((uintptr_t)X) & 15) return fail(ctx, SR_EINVAL, "X must be 16-byte aligned");
   SR_CHECK_CUDA(ctx, cudaSetDevice(ctx->device));
-  const int warp_bytes = grad_warp_bytes(Lmax);
+  // tape entries in shared memory: what is left of a warp's share when
+  // GCTAS_PER_SM blocks fill the SM
+  int sm_bytes = 0, blk_max = 0, blk_reserved = 0;
+  SR_CHECK_CUDA(ctx, cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device));
+  SR_CHECK_CUDA(ctx, cudaDeviceGetAttribute(&blk_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+  SR_CHECK_CUDA(ctx, cudaDeviceGetAttribute(&blk_reserved, cudaDevAttrReservedSharedMemoryPerBlock, ctx->device));
+  const int fixed = grad_fixed_bytes(Lmax, K);
+  const int budget = (sm_bytes / GCTAS_PER_SM - blk_reserved) / GWARPS;
+  int tcap = (budget - fixed) / GSLOT;
+  tcap = tcap < 4 ? 4 : (tcap > Lmax ? Lmax : tcap);
+  const int warp_bytes = fixed + tcap * GSLOT;
   const int smem = GWARPS * warp_bytes;
-  static int configured = 0;
-  if (!configured) {
-    SR_CHECK_CUDA(ctx, cudaFuncSetAttribute(grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            227 * 1024));
-    configured = 1;
-  }
+  if (smem > blk_max) return fail(ctx, SR_EINVAL, "Lmax %d, K %d too large for the gradient kernel", Lmax, K);
+  SR_CHECK_CUDA(ctx, cudaFuncSetAttribute(grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   int nb = 0;
   SR_CHECK_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, grad_kernel, GWARPS * 32, smem));
-  if (nb < 1) return fail(ctx, SR_EINVAL, "Lmax %d too large for the gradient tape", Lmax);
+  if (nb < 1) return fail(ctx, SR_EINVAL, "Lmax %d, K %d too large for the gradient kernel", Lmax, K);
   const int grid = nb * ctx->num_sms;
   const long long warps = (long long)grid * GWARPS;
-  int nch = (int)((warps * TARGET_ITEMS_PER_WARP + P - 1) / P);
+  int nch = (int)((warps * GTARGET_ITEMS_PER_WARP + P - 1) / P);
   const int max_chunks = (N + 1023) / 1024;
   nch = nch < 1 ? 1 : (nch > max_chunks ? max_chunks : nch);
   int chunk = (N + nch - 1) / nch;
-  chunk = (chunk + 31) / 32 * 32;
+  chunk = (chunk + GSTEP - 1) / GSTEP * GSTEP;
   const int nchunks = (N + chunk - 1) / chunk;
   const long long items = (long long)P * nchunks;
+  const size_t tokens = (size_t)P * Lmax;
   Carver cv;
-  const size_t off_q = cv.take(256), off_f = cv.take((size_t)P * 4),
-               off_p = cv.take((size_t)items * GSTRIDE * 8);
+  const size_t off_q = cv.take(256), off_f = cv.take((size_t)P * 4), off_nc = cv.take((size_t)P * 4),
+               off_code = cv.take(tokens * 8), off_start = cv.take(tokens * 2),
+               off_need = cv.take(tokens), off_task = cv.take(tokens * 2),
+               off_p = cv.take((size_t)items * GSTRIDE * 8),
+               off_t = cv.take(Lmax > tcap ? (size_t)warps * (Lmax - tcap) * GSLOT : 0);
   sr_status st = ensure_workspace(ctx, cv.off);
   if (st != SR_OK) return st;
+  char *ws = ctx->ws;
   GradParams gp;
   gp.programs = programs;
   gp.lengths = lengths;
@@ -339,18 +476,26 @@ sr_status sr_eval_grad(sr_ctx *ctx, const uint8_t *programs, const int32_t *leng
   gp.chunk = chunk;
   gp.nchunks = nchunks;
   gp.total_items = items;
-  gp.partials = reinterpret_cast<double *>(ctx->ws + off_p);
-  gp.flags = prog_flags ? prog_flags : reinterpret_cast<int32_t *>(ctx->ws + off_f);
-  gp.queue = reinterpret_cast<unsigned long long *>(ctx->ws + off_q);
+  gp.partials = reinterpret_cast<double *>(ws + off_p);
+  gp.flags = prog_flags ? prog_flags : reinterpret_cast<int32_t *>(ws + off_f);
+  gp.code = reinterpret_cast<uint2 *>(ws + off_code);
+  gp.ncode = reinterpret_cast<int32_t *>(ws + off_nc);
+  gp.s_start = reinterpret_cast<int16_t *>(ws + off_start);
+  gp.s_need = reinterpret_cast<uint8_t *>(ws + off_need);
+  gp.s_task = reinterpret_cast<int16_t *>(ws + off_task);
+  gp.queue = reinterpret_cast<unsigned long long *>(ws + off_q);
+  gp.gtape = Lmax > tcap ? ws + off_t : nullptr;
+  gp.tcap = tcap;
   gp.warp_bytes = warp_bytes;
-  gp.adj_slots = (Lmax + 1) / 2 + 1;
-  SR_CHECK_CUDA(ctx, cudaMemsetAsync(gp.queue, 0, 8, ctx->stream));
-  grad_kernel<<<grid, GWARPS * 32, smem, ctx->stream>>>(gp);
+  cudaStream_t s = ctx->stream;
+  SR_CHECK_CUDA(ctx, cudaMemsetAsync(gp.queue, 0, 8, s));
+  grad_decode_kernel<<<(P + 127) / 128, 128, 0, s>>>(gp);
+  grad_kernel<<<grid, GWARPS * 32, smem, s>>>(gp);
   SR_CHECK_CUDA(ctx, cudaGetLastError());
   GradFinal gf{gp.partials, gp.flags, P, N, K, nchunks, mse, dconst};
-  grad_finalize_kernel<<<(P + 255) / 256, 256, 0, ctx->stream>>>(gf);
+  grad_finalize_kernel<<<(P + 255) / 256, 256, 0, s>>>(gf);
   SR_CHECK_CUDA(ctx, cudaGetLastError());
-  ctx->launches += 2;
+  ctx->launches += 3;
   return SR_OK;
 }
 

@@ -1,0 +1,239 @@
+// sr_interp.cuh -- the scheduled instruction stream shared by the evaluation
+// kernels (sr_eval.cu) and the adjoint kernel (sr_grad.cu).
+//
+// A program (RPN, paper Sec. 2.1.4) is decoded once per call by a pre-pass,
+// one thread per program: validation, then the expression tree is
+// rescheduled Sethi-Ullman style -- at every binary node the child that needs
+// more stack is evaluated first, with a reversed opcode keeping a - b and
+// a / b exact when the right child goes first.  The number of live values is
+// then at most floor(log2(leaves)) + 1: 9 for 512 tokens, so 8 stack slots
+// below the top always suffice.  A terminal evaluated second is fused into
+// its binary operator ("top = top op x_j").  Values are bit-identical to
+// plain left-to-right evaluation: every operator sees the same operands.
+#pragma once
+
+#include "sr_common.cuh"
+
+namespace sr {
+
+// stack slots below the top register (see above)
+constexpr int DSM = 8;
+static_assert(SR_MAX_LMAX <= 512, "8 slots cover programs of up to 512 tokens");
+
+// Instruction (uint2):
+//   x bits 0..7   opcode
+//   x bits 8..23  byte offset of the stack slot it pushes to / pops from
+//   x bits 24..27 constant index k (constant operands only)
+//   y             operand: FP32 bits of c_k, or the row offset j * ldx of x_j
+enum Op : uint32_t {
+  OP_LDV = 0,   // top = x_j                        (stack empty)
+  OP_LDC,       // top = c_k
+  OP_PUSHV,     // stack[slot] = top; top = x_j
+  OP_PUSHC,     // stack[slot] = top; top = c_k
+  OP_ADD,       // top = stack[slot] op top         (left operand evaluated first)
+  OP_SUB,
+  OP_MUL,
+  OP_DIV,
+  OP_RSUB,      // top = top - stack[slot]          (right operand evaluated first)
+  OP_RDIV,      // top = top / stack[slot]
+  OP_SIN,       // top = f(top)
+  OP_COS,
+  OP_EXP,
+  OP_LOG,
+  OP_SQRT,
+  OP_SQ,
+  OP_VADD,      // top = top op x_j   (terminal right operand, evaluated second)
+  OP_VSUB,
+  OP_VMUL,
+  OP_VDIV,
+  OP_VRSUB,     // top = x_j - top    (terminal left operand, evaluated second)
+  OP_VRDIV,     // top = x_j / top
+  OP_CADD,      // top = top op c_k
+  OP_CSUB,
+  OP_CMUL,
+  OP_CDIV,
+  OP_CRSUB,     // top = c_k - top
+  OP_CRDIV,     // top = c_k / top
+};
+
+__device__ __forceinline__ uint32_t ins_op(uint2 w) { return w.x & 0xffu; }
+__device__ __forceinline__ uint32_t ins_off(uint2 w) { return (w.x >> 8) & 0xffffu; }
+__device__ __forceinline__ int ins_k(uint2 w) { return (int)((w.x >> 24) & 0xfu); }
+
+struct DecodeArgs {
+  const uint8_t *programs;  // [P][Lmax]
+  const int32_t *lengths;
+  const float *consts;      // [P][K]
+  int Lmax, K, nvars;
+  long long ldx;
+  int slot_bytes;           // bytes between consecutive stack slots of a warp
+  uint2 *code;              // [P][Lmax] out
+  int32_t *ncode;           // [P] out
+  int32_t *flags;           // [P] out
+  int16_t *s_start;         // scratch [P][Lmax]: first token of each subtree
+  uint8_t *s_need;          // scratch [P][Lmax]: stack need of each subtree
+  int16_t *s_task;          // scratch [P][Lmax]: work stack
+};
+
+__device__ __forceinline__ bool is_term(int v) {
+  const int c = tok_class(v);
+  return c == CLS_VAR || c == CLS_CONST;
+}
+
+__device__ __forceinline__ uint2 with_operand(uint32_t x, int v, const float *crow, long long ldx) {
+  if (tok_class(v) == CLS_VAR) return make_uint2(x, (uint32_t)((long long)(v - TOK_VAR0) * ldx));
+  const int k = v - TOK_CONST0;
+  return make_uint2(x | ((uint32_t)k << 24), __float_as_uint(crow[k]));
+}
+
+// Validation and scheduled decoding of program `prog` (one thread).
+// Flag rules: length outside [1, Lmax]; bad byte; variable / constant index
+// out of range; depth (running sum of +1 terminal, 0 unary or bad byte, -1
+// binary) below 1 after some token; final depth not 1.
+__device__ inline void decode_one(const DecodeArgs &p, int prog) {
+  const uint8_t *tok = p.programs + (size_t)prog * p.Lmax;
+  const int L = p.lengths[prog];
+  int flags = 0;
+  if (L < 1 || L > p.Lmax) {
+    flags = SR_PF_BAD_LENGTH;
+  } else {
+    int depth = 0;
+    for (int t = 0; t < L; ++t) {
+      const int v = tok[t];
+      const int cls = tok_class(v);
+      if (cls == CLS_BAD) flags |= SR_PF_BAD_TOKEN;
+      if (cls == CLS_VAR && v - TOK_VAR0 >= p.nvars) flags |= SR_PF_BAD_VAR;
+      if (cls == CLS_CONST && v - TOK_CONST0 >= p.K) flags |= SR_PF_BAD_CONST;
+      depth += cls_effect(cls);
+      if (depth < 1) flags |= SR_PF_UNDERFLOW;
+    }
+    if (depth != 1) flags |= SR_PF_BAD_FINAL;
+  }
+  p.flags[prog] = flags;
+  if (flags) {
+    p.ncode[prog] = 0;
+    return;
+  }
+  int16_t *start = p.s_start + (size_t)prog * p.Lmax;
+  uint8_t *need = p.s_need + (size_t)prog * p.Lmax;
+  int16_t *task = p.s_task + (size_t)prog * p.Lmax;
+  // pass 1, postfix order is bottom-up: subtree starts and stack needs
+  // (terminal 1; unary as its child; binary max of the children, +1 on a tie)
+  int sp = 0;
+  for (int t = 0; t < L; ++t) {
+    const int cls = tok_class(tok[t]);
+    if (cls == CLS_VAR || cls == CLS_CONST) {
+      start[t] = (int16_t)t;
+      need[t] = 1;
+      task[sp++] = (int16_t)t;
+    } else if (cls == CLS_UNARY) {
+      const int c = task[sp - 1];
+      start[t] = start[c];
+      need[t] = need[c];
+      task[sp - 1] = (int16_t)t;
+    } else {
+      const int b = task[--sp], a = task[sp - 1];
+      const int na = need[a], nb = need[b];
+      start[t] = start[a];
+      need[t] = (uint8_t)(na == nb ? na + 1 : (na > nb ? na : nb));
+      task[sp - 1] = (int16_t)t;
+    }
+  }
+  // pass 2, emission: depth-first from the root, larger-need child first;
+  // work stack entries are node << 2 | phase.  d counts the live values
+  // (top included): a terminal pushes the old top into slot d - 1, a binary
+  // operator pops slot d - 2.
+  const float *crow = p.consts + (size_t)prog * p.K;
+  uint2 *code = p.code + (size_t)prog * p.Lmax;
+  int n = 0, d = 0;
+  sp = 0;
+  task[sp++] = (int16_t)((L - 1) << 2);
+  while (sp > 0) {
+    const int e = task[sp - 1];
+    const int node = e >> 2, ph = e & 3;
+    const int v = tok[node];
+    const int cls = tok_class(v);
+    if (cls == CLS_VAR || cls == CLS_CONST) {
+      --sp;
+      if (d > DSM) {  // cannot happen (depth <= 9 for <= 512 tokens); never write past the slots
+        p.flags[prog] = SR_PF_TOO_DEEP;
+        p.ncode[prog] = 0;
+        return;
+      }
+      const bool var = cls == CLS_VAR;
+      uint32_t op = var ? OP_LDV : OP_LDC;
+      if (d > 0) op = (uint32_t)(var ? OP_PUSHV : OP_PUSHC) | ((uint32_t)((d - 1) * p.slot_bytes) << 8);
+      code[n++] = with_operand(op, v, crow, p.ldx);
+      ++d;
+    } else if (cls == CLS_UNARY) {
+      if (ph == 0) {
+        task[sp - 1] = (int16_t)(e | 1);
+        task[sp++] = (int16_t)((node - 1) << 2);
+      } else {
+        --sp;
+        code[n++] = make_uint2((uint32_t)(OP_SIN + (v - TOK_SIN)), 0u);
+      }
+    } else {
+      const int b = node - 1, a = start[b] - 1;
+      const bool rev = need[b] > need[a];
+      const int first = rev ? b : a, second = rev ? a : b;
+      if (ph == 0) {
+        task[sp - 1] = (int16_t)(e | 1);
+        task[sp++] = (int16_t)(first << 2);
+      } else if (ph == 1 && is_term(tok[second])) {
+        --sp;
+        const int w = tok[second];
+        const bool var = tok_class(w) == CLS_VAR;
+        uint32_t op;
+        if (rev && v == TOK_SUB) op = var ? OP_VRSUB : OP_CRSUB;
+        else if (rev && v == TOK_DIV) op = var ? OP_VRDIV : OP_CRDIV;
+        else op = (uint32_t)((var ? OP_VADD : OP_CADD) + v);  // + and * commute exactly
+        code[n++] = with_operand(op, w, crow, p.ldx);
+      } else if (ph == 1) {
+        task[sp - 1] = (int16_t)((e & ~3) | 2);
+        task[sp++] = (int16_t)(second << 2);
+      } else {
+        --sp;
+        uint32_t op;
+        if (rev && v == TOK_SUB) op = OP_RSUB;
+        else if (rev && v == TOK_DIV) op = OP_RDIV;
+        else op = (uint32_t)(OP_ADD + v);
+        code[n++] = make_uint2(op | ((uint32_t)((d - 2) * p.slot_bytes) << 8), 0u);
+        --d;
+      }
+    }
+  }
+  p.ncode[prog] = n;
+}
+
+// ---------------------------------------------------------------- operators (FP32)
+__device__ __forceinline__ float op_div(float a, float b) {
+  // |b| < 1e-3f in FP32 is exactly "|b| <= 1e-3" for FP32 values of b
+  return fabsf(b) < 1e-3f ? 1.0f : a / b;
+}
+__device__ __forceinline__ float op_log(float x) {
+  return fabsf(x) < 1e-3f ? 0.0f : logf(fabsf(x));
+}
+__device__ __forceinline__ float op_exp(float x) {
+  x = x > 80.0f ? 80.0f : (x < -80.0f ? -80.0f : x);  // NaN passes through
+  return expf(x);
+}
+__device__ __forceinline__ float f_sqrt(float x) { return sqrtf(fabsf(x)); }
+
+// sinf / cosf carry a long path for large arguments; keep one out-of-line
+// copy of it and let the inlined copies assume a moderate argument (NaN and
+// +-inf also take the out-of-line call)
+static __device__ __noinline__ float sin_wide(float x) { return sinf(x); }
+static __device__ __noinline__ float cos_wide(float x) { return cosf(x); }
+__device__ __forceinline__ float f_sin(float x) {
+  if (!(fabsf(x) <= 4.0e4f)) return sin_wide(x);
+  __builtin_assume(fabsf(x) <= 4.0e4f);
+  return sinf(x);
+}
+__device__ __forceinline__ float f_cos(float x) {
+  if (!(fabsf(x) <= 4.0e4f)) return cos_wide(x);
+  __builtin_assume(fabsf(x) <= 4.0e4f);
+  return cosf(x);
+}
+
+}  // namespace sr

@@ -316,6 +316,27 @@ def test_gradient_closed_form():
     assert m == pytest.approx(np.mean((c0 * x - y) ** 2), rel=1e-13)
 
 
+def test_gradient_absolute_scale():
+    """gabs propagates absolute partials: for c0 x0 it is (2/N) sum |e| |x0|;
+    for c0 / c0 the derivative is exactly 0 while gabs = (2/N) sum |e| 2/|c0|
+    (the two chain-rule paths 1/c and -c/c^2 cancel, their magnitudes add)."""
+    rng = np.random.default_rng(8)
+    N = 257
+    X = rng.uniform(-3, 5, (1, N))
+    y = rng.normal(size=N)
+    progs, lens = pack([parse("c0 x0 *"), parse("c0 c0 /"), parse("x0 c0 c0 / *")], 8)
+    c = np.array([[1.7], [-0.6], [2.5]], np.float32)
+    m, g, kink, gabs = oracle.grad(progs, lens, c, X, y, N)
+    x, c0 = X[0], float(c[0, 0])
+    assert gabs[0, 0] == pytest.approx(2.0 / N * np.sum(np.abs(c0 * x - y) * np.abs(x)), rel=1e-13)
+    c1 = float(c[1, 0])
+    assert g[1, 0] == 0.0
+    assert gabs[1, 0] == pytest.approx(2.0 / N * np.sum(np.abs(1.0 - y)) * 2.0 / abs(c1), rel=1e-13)
+    c2 = float(c[2, 0])
+    assert g[2, 0] == 0.0
+    assert gabs[2, 0] == pytest.approx(2.0 / N * np.sum(np.abs(x - y) * np.abs(x)) * 2.0 / abs(c2), rel=1e-13)
+
+
 def test_gradient_matches_central_differences():
     """Forward-mode dMSE/dc vs FP64 central differences (h = 1e-6) on random
     programs whose branch arguments stay away from their switch points."""
