@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--small", action="store_true",
+                    help="reduced sizes of the adjoint / large / batched workloads (2,048 x 131,072; "
+                         "16,384 x 131,072; the first 8 problems), for profiler captures")
     ap.add_argument("--workload", default="paper", choices=["paper", "batched", "adjoint", "large", "plain"],
                     help="paper (default, the headline): 4096 x 100k; batched: 64 problems in one launch "
                          "vs a loop of single calls; adjoint: Adam constant optimisation; large: "
@@ -163,7 +166,7 @@ def run_ours(args, rank, world, local_rank):
     import torch.distributed as dist
 
     import __graft_entry__
-    from paper_2603_12292_gb300 import binding, inputs
+    from paper_2603_12292_gb300 import binding, inputs, shard
 
     __graft_entry__.build()
     torch.cuda.set_device(local_rank)
@@ -188,7 +191,7 @@ def run_ours(args, rank, world, local_rank):
     cfg = binding.var_cfg()  # p_cross 0.9, p_point 0.1, p_subtree 0.05, p_const 0.1
     pop = [(programs, lengths, consts),
            (torch.empty_like(programs), torch.empty_like(lengths), torch.empty_like(consts))]
-    SEED, K_TOURN = 20260312, 4
+    SEED, K_TOURN = 20260312 + rank, 4  # each rank evolves its own population (an island)
     state = {"gen": 0, "cur": 0}
     ev_eval = []
 
@@ -235,11 +238,10 @@ def run_ours(args, rank, world, local_rank):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     eval_ms = [a.elapsed_time(b) for a, b in ev_eval]
     total_ms = float(sum(step_ms))
+    units = float(sum(nodes)) * pr.N
     if world > 1:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    units = float(sum(nodes)) * pr.N * world
+        total_ms = shard.max_over_ranks(total_ms, dev)
+        units = shard.sum_over_ranks(units, dev)
     value = units / (total_ms / 1e3) / 1e9
 
     # roofline of the dominant kernel (the evaluation call, timed by its own
@@ -296,7 +298,11 @@ def run_ours(args, rank, world, local_rank):
         state["gen"] += 1
         e2e_ms.append(a.elapsed_time(b))
         e2e_nodes.append(n_in)
-    e2e_val = float(sum(e2e_nodes)) * pr.N / (float(sum(e2e_ms)) / 1e3) / 1e9 * world
+    e2e_units, e2e_total = float(sum(e2e_nodes)) * pr.N, float(sum(e2e_ms))
+    if world > 1:
+        e2e_total = shard.max_over_ranks(e2e_total, dev)
+        e2e_units = shard.sum_over_ranks(e2e_units, dev)
+    e2e_val = e2e_units / (e2e_total / 1e3) / 1e9
 
     line = {"metric": METRIC, "value": value, "unit": "GPop/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -307,7 +313,7 @@ def run_ours(args, rank, world, local_rank):
                        "step": "one generation: sr_eval(SR_MSE_CORR) + sr_select_tournament(k=4, on 1-r^2)"
                                " + sr_vary(p_cross 0.9, p_point 0.1, p_subtree 0.05, p_const 0.1)",
                        "l2": "flushed between timed steps",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"islands x{world}: one population per rank, own seed, no exchange"},
             "roofline": roofline, "clocks": clocks,
             "e2e": {"value": e2e_val, "unit": "GPop/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
@@ -385,7 +391,7 @@ def run_workload(args, local_rank):
             "vs_baseline": None, "steps": args.steps, "warmup": args.warmup}
 
     if args.workload == "batched":
-        shapes = inputs.batched_shapes()
+        shapes = inputs.batched_shapes()[: 8 if args.small else None]
         pops, work = [], 0.0
         for sh in shapes:
             pr = inputs.batched_problem(sh)
@@ -416,10 +422,10 @@ def run_workload(args, local_rank):
         gens = 2 * max(1, args.steps // 2)
         n_gen = nodes()
         t_graph = _timed(lambda: ev.run(gens), 1, stream) / gens
-        line.update(metric="GPop/s, 64 problems per generation (batched + graph vs plain loop)",
+        line.update(metric=f"GPop/s, {len(shapes)} problems per generation (batched + graph vs plain loop)",
                     value=n_gen / (t_graph / 1e3) / 1e9, unit="GPop/s", ms_per_step=t_graph,
                     scaling="weak",
-                    config={"workload": "batched-64: nvars 1-10, N log-uniform 1k-1M, P 512-8192, "
+                    config={"workload": f"batched-{len(shapes)}: nvars 1-10, N log-uniform 1k-1M, P 512-8192, "
                                         "L 4-256, MSE/1-r^2 mixed",
                             "problems": len(pops), "node_cases_per_eval": n0},
                     batched_eval_gpops=n0 / (t_batch / 1e3) / 1e9,
@@ -427,7 +433,7 @@ def run_workload(args, local_rank):
                     batched_over_plain=t_plain / t_batch,
                     generation_graph_ms=t_graph, eval_batched_ms=t_batch, eval_plain_loop_ms=t_plain)
     elif args.workload == "adjoint":
-        pr = inputs.adjoint()
+        pr = inputs.adjoint(P=2048, N=131072) if args.small else inputs.adjoint()
         pg, ln, cs, X, y = _device_problem(pr, dev, binding, ctx)
         P, K, N = pr.P, pr.K, pr.N
         mse = torch.empty(P, dtype=torch.float64, device=dev)
@@ -458,15 +464,16 @@ def run_workload(args, local_rank):
             adam_step()
         steps = max(1, args.steps)
         t_adj = _timed(adam_step, steps, stream)
+        fd_step()  # untimed: first-call costs of the plain path stay out of the comparison
         t_fd = _timed(fd_step, 1, stream)
         nodes = float(ln.sum()) * N
         line.update(metric="constant-optimisation steps/s (adjoint + Adam) vs plain finite differences",
                     value=1e3 / t_adj, unit="steps/s", ms_per_step=t_adj, scaling="weak",
-                    config={"workload": "adjoint-16384x1M: K=8, L<=96, 5 vars, 1e6 cases, Adam"},
+                    config={"workload": f"{pr.name}: K=8, L<=96, 5 vars, Adam"},
                     grad_gpops=nodes / (t_adj / 1e3) / 1e9,
                     fd_steps_per_s=1e3 / t_fd, adjoint_over_fd=t_fd / t_adj)
     elif args.workload == "large":
-        pr = inputs.large()
+        pr = inputs.large(P=16384, N=131072) if args.small else inputs.large()
         pg, ln, cs, X, y = _device_problem(pr, dev, binding, ctx)
         cfg = EvolveConfig(select_kind=binding.SR_CORR, eval_kind=binding.SR_CORR)
         ev = Evolver(ctx, [Population(pg, ln, cs, X, y, pr.N, cfg)])

@@ -37,7 +37,10 @@
  * (Salmon, Moraes, Dror, Shaw, "Parallel Random Numbers: As Easy as 1, 2, 3",
  * SC'11); integer ranges by the 32x32->64 multiply-high map (Lemire 2019).
  * Selection and variation follow the specification in include/sr.h so that
- * the device kernels can be checked bit for bit.
+ * the device kernels can be checked bit for bit.  The paper prints no values
+ * for them (Beagle has no crossover and selects by rank on the CPU), so their
+ * parity is unpinned by the paper: tests pin them to invariants (validity,
+ * whole-subtree swaps, the tournament rank law) and to the specification.
  */
 #include <float.h>
 #include <math.h>

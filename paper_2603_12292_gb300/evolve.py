@@ -36,7 +36,11 @@ class Population:
         self.X, self.y, self.N, self.cfg = X, y, N, cfg
         self.buf = [(programs, lengths, consts),
                     (torch.empty_like(programs), torch.empty_like(lengths), torch.empty_like(consts))]
-        P = programs.shape[0]
+        P, Lmax = programs.shape
+        v = cfg.var
+        # a random subtree longer than the programs can be is never wanted
+        self.var = binding.VarCfg(v.p_cross, v.p_point, v.p_subtree, v.p_const, v.const_delta,
+                                  min(v.max_subtree, Lmax))
         rows = 2 if cfg.eval_kind == binding.SR_MSE_CORR else 1
         self.fitness = torch.empty((rows, P), dtype=torch.float64, device=programs.device)
         self.parents = torch.empty((P, 2), dtype=torch.int32, device=programs.device)
@@ -104,7 +108,7 @@ class Evolver:
                 P_, L_, C_ = p.current
                 binding.sr_select_tournament(self.ctx, p.select_row(), p.cfg.tournament_k, p.cfg.seed, 0,
                                              parents=p.parents)
-                binding.sr_vary(self.ctx, P_, L_, C_, p.parents, p.X.shape[0], p.cfg.var, p.cfg.seed, 0,
+                binding.sr_vary(self.ctx, P_, L_, C_, p.parents, p.X.shape[0], p.var, p.cfg.seed, 0,
                                 out=p.buf[1 - p.cur])
                 p.cur = 1 - p.cur
             self.gen += 1

@@ -176,11 +176,12 @@ def paper_shaped(attempt: int = 0, kind: int = 1) -> Problem:
                         target_len=(5, 25), noise=0.01, kind=kind)
 
 
-def adjoint(attempt: int = 0) -> Problem:
+def adjoint(attempt: int = 0, P: int = 16384, N: int = 1_000_000) -> Problem:
     """16,384 programs of length <= 96 with 8 constants, 5 variables,
     1,000,000 cases X ~ U(1, 5); MSE."""
-    return make_problem("adjoint-16384x1M", ROOT_SEED + 3 + 1000 * attempt, P=16384, Lmin=4,
-                        Lmax=96, nvars=5, K=8, N=1_000_000, xlo=1.0, xhi=5.0,
+    name = "adjoint-16384x1M" if (P, N) == (16384, 1_000_000) else f"adjoint-{P}x{N}"
+    return make_problem(name, ROOT_SEED + 3 + 1000 * attempt, P=P, Lmin=4,
+                        Lmax=96, nvars=5, K=8, N=N, xlo=1.0, xhi=5.0,
                         target_len=(5, 25), kind=0)
 
 
