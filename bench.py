@@ -45,10 +45,12 @@ def parse():
     ap.add_argument("--small", action="store_true",
                     help="reduced sizes of the adjoint / large / batched workloads (2,048 x 131,072; "
                          "16,384 x 131,072; the first 8 problems), for profiler captures")
-    ap.add_argument("--workload", default="paper", choices=["paper", "batched", "adjoint", "large", "plain"],
+    ap.add_argument("--workload", default="paper",
+                    choices=["paper", "batched", "adjoint", "large", "plain", "beagle"],
                     help="paper (default, the headline): 4096 x 100k; batched: 64 problems in one launch "
                          "vs a loop of single calls; adjoint: Adam constant optimisation; large: "
-                         "262,144 x 1M; plain: 256 x 1k, CUDA graph vs eager")
+                         "262,144 x 1M; plain: 256 x 1k, CUDA graph vs eager; beagle: 4096 x 100k with "
+                         "1%% invalid targets, the r^4 score of Eq. 2 (and Eq. 3 timed beside it)")
     return ap.parse_args()
 
 
@@ -486,6 +488,64 @@ def run_workload(args, local_rank):
         line.update(metric="GPop/s (nodes x cases / s), one generation (1-r^2, selection, variation)",
                     value=n_before / (t / 1e3) / 1e9, unit="GPop/s", ms_per_step=t, scaling="weak",
                     config={"workload": pr.name, "programs": pr.P, "cases": pr.N, "lengths": "4-256"})
+    elif args.workload == "beagle":
+        pr = inputs.paper_shaped()
+        pg, ln, cs, X, y = _device_problem(pr, dev, binding, ctx)
+        # 1 % invalid targets (NaN, +inf, -inf in turn) at seeded cases
+        bad = np.sort(np.random.default_rng(pr.seed + 11).choice(pr.N, pr.N // 100, replace=False))
+        yv = y.clone()
+        vals = torch.tensor([float("nan"), float("inf"), float("-inf")], dtype=torch.float32, device=dev)
+        yv[torch.from_numpy(bad).to(dev)] = vals[torch.arange(len(bad), device=dev) % 3]
+        P, M, SEED = pr.P, 1000, 20260312
+        score = torch.empty(P, dtype=torch.float64, device=dev)
+        counts = torch.empty((P, 2), dtype=torch.int32, device=dev)
+        parents = torch.empty((P, 2), dtype=torch.int32, device=dev)
+        flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+        vcfg = binding.var_cfg()
+        pop = [(pg, ln, cs), (torch.empty_like(pg), torch.empty_like(ln), torch.empty_like(cs))]
+        state = {"gen": 0, "cur": 0}
+
+        def generation():
+            g, cur = state["gen"], state["cur"]
+            P_, L_, C_ = pop[cur]
+            binding.sr_eval_score(ctx, P_, L_, C_, X, yv, pr.N, binding.SR_SCORE_R4, M, score=score,
+                                  pair_counts=counts)
+            binding.sr_select_tournament_max(ctx, score, 4, SEED, g, parents=parents)
+            binding.sr_vary(ctx, P_, L_, C_, parents, pr.nvars, vcfg, SEED, g, out=pop[1 - cur])
+            state["gen"], state["cur"] = g + 1, 1 - cur
+
+        for _ in range(max(3, args.warmup)):
+            generation()
+        torch.cuda.synchronize()
+        steps = max(1, args.steps)
+        ms, nodes = [], []
+        for _ in range(steps):
+            nodes.append(float(pop[state["cur"]][1].sum()) * pr.N)
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            generation()
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        # evaluation alone on the current population: Eq. 2, Eq. 3, and MSE + 1 - r^2
+        P_, L_, C_ = pop[state["cur"]]
+        n_cur = float(L_.sum()) * pr.N
+        f2 = torch.empty((2, P), dtype=torch.float64, device=dev)
+        t_r4 = _timed(lambda: binding.sr_eval_score(ctx, P_, L_, C_, X, yv, pr.N, binding.SR_SCORE_R4, M,
+                                                    score=score, pair_counts=counts), steps, stream)
+        t_p2p = _timed(lambda: binding.sr_eval_score(ctx, P_, L_, C_, X, yv, pr.N, binding.SR_SCORE_P2P, M,
+                                                     score=score, pair_counts=counts), steps, stream)
+        t_both = _timed(lambda: binding.sr_eval(ctx, P_, L_, C_, X, y, pr.N, binding.SR_MSE_CORR, fitness=f2),
+                        steps, stream)
+        line.update(metric="GPop/s, one generation scored by Beagle's r^4 score (Eq. 2) with invalid targets",
+                    value=sum(nodes) / (sum(ms) / 1e3) / 1e9, unit="GPop/s", ms_per_step=sum(ms) / steps,
+                    scaling="weak",
+                    config={"workload": "beagle-4096x100k: paper shapes, 1% invalid targets, M = 1000",
+                            "step": "sr_eval_score(R4) + sr_select_tournament_max(k=4) + sr_vary",
+                            "l2": "flushed between timed generations"},
+                    r4_eval_gpops=n_cur / (t_r4 / 1e3) / 1e9, p2p_eval_gpops=n_cur / (t_p2p / 1e3) / 1e9,
+                    mse_corr_eval_gpops=n_cur / (t_both / 1e3) / 1e9)
     else:  # plain: launch-bound, CUDA graph vs eager
         pr = inputs.plain()
         pg, ln, cs, X, y = _device_problem(pr, dev, binding, ctx)

@@ -147,6 +147,44 @@ sr_status sr_eval(sr_ctx *ctx, const uint8_t *programs, const int32_t *lengths,
                   const float *y, int nvars, int N, int ldx,
                   sr_fitness_kind kind, double *fitness, int32_t *prog_flags);
 
+/* Beagle's own scores (Sec. 2.1.5); both are maximised.
+ *   SR_SCORE_R4  (Eq. 2) score = M r^4 (N - (c1 + c2)) - M (c1 - c2), with r
+ *                the Pearson correlation of Eq. 1 over the valid pairs only.
+ *   SR_SCORE_P2P (Eq. 3) score = sum over cases of the point-to-point
+ *                fitness: M when max(|yhat|, |y|) = 0; otherwise
+ *                round(M min(|yhat|,|y|) / max(|yhat|,|y|)), less M/11
+ *                inside the round when yhat y < 0; M when both values are
+ *                invalid, -M when exactly one is.
+ * A value is invalid when it is not finite (NaN, +inf, -inf).  A pair is
+ * valid when both yhat and y are; c1 counts the pairs with exactly one
+ * invalid value, c2 those with two. */
+typedef enum { SR_SCORE_R4 = 0, SR_SCORE_P2P = 1 } sr_score_kind;
+
+/*
+ * sr_eval_score -- Beagle's scores of every program (Eq. 2 or Eq. 3).
+ *   y            device float [N], 16-byte aligned; may hold NaN / +-inf
+ *                (invalid target values)
+ *   kind         SR_SCORE_R4 or SR_SCORE_P2P
+ *   M            the maximum score per case, 1 <= M <= 2^24
+ *   score        device double [P], written (larger is better)
+ *   pair_counts  device int32 [P][2] (c1, c2) or NULL
+ *   other arguments as for sr_eval.
+ * Arithmetic.  Eq. 3 per case in FP32, each operation rounded on its own:
+ * q = min / max, v = M q, v = v - M/11 (M/11 rounded to FP32) when the signs
+ * differ, rounded to an integer half to even; the integer scores are summed
+ * exactly.  Eq. 2: per-lane FP32 compensated sums over the valid pairs of
+ * yhat - s (s: a finite output of the tile) and of y - ybar (ybar: the FP64
+ * mean of the finite targets), merged in FP64; r^2 is clamped to [0, 1] and
+ * is 0 when fewer than two pairs are valid, either variance is zero, or an
+ * FP32 moment sum overflows (outputs beyond ~1e18; as for SR_CORR).
+ * An invalid program scores -inf with counts (0, 0).
+ * Errors: as sr_eval; SR_EINVAL for an unknown kind or M out of range.
+ */
+sr_status sr_eval_score(sr_ctx *ctx, const uint8_t *programs, const int32_t *lengths,
+                        const float *consts, int P, int Lmax, int K, const float *X,
+                        const float *y, int nvars, int N, int ldx, sr_score_kind kind,
+                        int M, double *score, int32_t *pair_counts, int32_t *prog_flags);
+
 /* One problem of a batch: its own population, data, kind and outputs. */
 typedef struct {
   const uint8_t *programs;  /* device [P][Lmax]                          */
@@ -229,6 +267,12 @@ sr_status sr_philox4x32_10(sr_ctx *ctx, const uint32_t *ctr, uint32_t key0,
  */
 sr_status sr_select_tournament(sr_ctx *ctx, const double *fitness, int P, int k,
                                uint64_t seed, uint64_t gen, int32_t *parents);
+
+/* sr_select_tournament_max -- the same draws; the largest score wins (for
+ * the scores of sr_eval_score), NaN counting as -inf and equal scores going
+ * to the smaller index. */
+sr_status sr_select_tournament_max(sr_ctx *ctx, const double *score, int P, int k,
+                                   uint64_t seed, uint64_t gen, int32_t *parents);
 
 /* Variation parameters (probabilities in [0, 1], FP32). */
 typedef struct {

@@ -21,6 +21,7 @@ _SRC = os.path.join(_HERE, "sr_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 MSE, CORR = 0, 1
+SCORE_R4, SCORE_P2P = 0, 1  # Eq. 2, Eq. 3
 
 # program flag bits (documented token format)
 PF_BAD_LENGTH, PF_BAD_TOKEN, PF_BAD_VAR = 1, 2, 4
@@ -70,6 +71,15 @@ def _load():
     lib.or_adam.argtypes = [P, P, P, P, i64, i32, f64, f64, f64, f64]
     lib.or_philox4x32_10.argtypes = [P, P, P]
     lib.or_tournament.argtypes = [P, i32, i32, u64, u64, P]
+    lib.or_tournament_max.argtypes = [P, i32, i32, u64, u64, P]
+    lib.or_p2p_case32.argtypes = [f32, f32, i32]
+    lib.or_p2p_case32.restype = i32
+    lib.or_score_p2p.argtypes = [P, P, i64, i32, P]
+    lib.or_score_p2p.restype = f64
+    lib.or_score_r4.argtypes = [P, P, i64, i32, P]
+    lib.or_score_r4.restype = f64
+    lib.or_eval_score.argtypes = [P, P, P, i32, i32, i32, P, i64, P, i32, i64, i32, i32, P, P, P, i32]
+    lib.or_p2p_range.argtypes = [P, P, P, i32, i32, i32, P, i64, P, i32, i64, f64, i32, P, P, P, i32]
     lib.or_random_programs.argtypes = [P, P, P, i32, i32, i32, i32, i32, f32, f32, u64, u64]
     lib.or_vary.argtypes = [P, P, P, P, P, P, P, i32, i32, i32, i32, f32, f32, f32, f32, f32, i32, u64, u64]
     _lib = lib
@@ -294,3 +304,72 @@ def vary(programs, lengths, consts, parents, K, nvars, p_cross=0.9, p_point=0.1,
                     P, Lmax, K, nvars, p_cross, p_point, p_subtree, p_const, const_delta, max_subtree,
                     seed, gen)
     return po, lo, co
+
+
+# ---------------------------------------------------------------- Beagle scores (Eq. 2, Eq. 3)
+def p2p_case32(yhat: float, y: float, M: int) -> int:
+    """Eq. 3 on one case, decided in FP32."""
+    return int(_load().or_p2p_case32(float(np.float32(yhat)), float(np.float32(y)), M))
+
+
+def score_from_outputs(yhat, y, kind: int, M: int):
+    """Eq. 2 (kind SCORE_R4) or Eq. 3 (SCORE_P2P) of one program's outputs
+    yhat [N] against y [N]; returns (score, c1, c2)."""
+    yh = _c(yhat, np.float64)
+    yy = _c(y, np.float64)
+    c12 = np.zeros(2, np.float64)
+    f = _load().or_score_r4 if kind == SCORE_R4 else _load().or_score_p2p
+    s = f(_ptr(yh), _ptr(yy), len(yh), M, _ptr(c12))
+    return float(s), int(c12[0]), int(c12[1])
+
+
+def evaluate_score(programs, lengths, consts, X, y, kind: int, M: int, N: int | None = None,
+                   nthreads: int = 0):
+    """Scores [P] (FP64; -inf for invalid programs), pair counts [P, 2] and
+    flag bits of every program."""
+    prog = _c(programs, np.uint8)
+    P, Lmax = prog.shape
+    lens = _c(lengths, np.int32)
+    cons = _c(consts, np.float32).reshape(P, -1)
+    K = cons.shape[1]
+    X64, ldx = _X(X)
+    nvars = X64.shape[0]
+    N = ldx if N is None else N
+    y64 = _c(np.asarray(y)[:N], np.float64)
+    sc = np.empty(P, np.float64)
+    cnt = np.empty((P, 2), np.float64)
+    flags = np.empty(P, np.int32)
+    _load().or_eval_score(_ptr(prog), _ptr(lens), _ptr(cons), P, Lmax, K, _ptr(X64), ldx, _ptr(y64),
+                          nvars, N, kind, M, _ptr(sc), _ptr(cnt), _ptr(flags), nthreads)
+    return sc, cnt.astype(np.int64), flags
+
+
+def p2p_range(programs, lengths, consts, X, y, M: int, N: int | None = None, u: float = U_FP32,
+              nthreads: int = 0):
+    """Per program: the least and greatest Eq. 3 score any FP32 evaluation
+    within the interval enclosure can produce, and whether an intermediate
+    may leave the FP32 range (then the range is not guaranteed)."""
+    prog = _c(programs, np.uint8)
+    P, Lmax = prog.shape
+    lens = _c(lengths, np.int32)
+    cons = _c(consts, np.float32).reshape(P, -1)
+    K = cons.shape[1]
+    X64, ldx = _X(X)
+    nvars = X64.shape[0]
+    N = ldx if N is None else N
+    y64 = _c(np.asarray(y)[:N], np.float64)
+    lo = np.empty(P, np.float64)
+    hi = np.empty(P, np.float64)
+    rf = np.empty(P, np.int32)
+    _load().or_p2p_range(_ptr(prog), _ptr(lens), _ptr(cons), P, Lmax, K, _ptr(X64), ldx, _ptr(y64), nvars,
+                         N, u, M, _ptr(lo), _ptr(hi), _ptr(rf), nthreads)
+    return lo, hi, rf
+
+
+def tournament_max(score, k: int, seed: int, gen: int) -> np.ndarray:
+    """k-way tournament on scores (largest wins, NaN = -inf)."""
+    f = _c(score, np.float64)
+    P = len(f)
+    out = np.empty((P, 2), np.int32)
+    _load().or_tournament_max(_ptr(f), P, k, seed, gen, _ptr(out))
+    return out

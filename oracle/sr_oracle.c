@@ -586,6 +586,212 @@ void or_condition(const uint8_t *programs, const int32_t *lengths,
   }
 }
 
+/* ---- Beagle's scores (Sec. 2.1.5, Eq. 2 and Eq. 3) ---------------------- */
+/*
+ * Readings (also in the design notes):
+ *   - a value is invalid when it is not finite (NaN, +inf, -inf); a model
+ *     output is FP32, so an FP64 output at or beyond the FP32 overflow
+ *     threshold (2^128 - 2^103) counts as invalid;
+ *   - a pair is valid when both values are; c1 counts pairs with exactly one
+ *     invalid value, c2 pairs with two;
+ *   - Eq. 3 is decided in FP32 (the precision of the outputs), every
+ *     operation rounded on its own, "round" = half to even; the case scores
+ *     are integers summed exactly;
+ *   - Eq. 2: r is Eq. 1 over the valid pairs (two-pass, FP64); r^2 = 0 when
+ *     fewer than two pairs are valid or either sum of squares is 0; r^2 is
+ *     at most 1.
+ */
+#define OVF32 3.4028235677973366e38 /* 2^128 - 2^103: FP32 rounds to inf from here */
+
+static int valid_output(double v) { return !isnan(v) && fabs(v) < OVF32; }
+
+/* Eq. 3 on one case (FP32). */
+int or_p2p_case32(float yh, float y, int M) {
+  int vh = isfinite(yh), vy = isfinite(y);
+  if (!(vh && vy)) return (vh || vy) ? -M : M;
+  float a = fabsf(yh), b = fabsf(y);
+  float mx = a > b ? a : b, mn = a > b ? b : a;
+  if (mx == 0.0f) return M;
+  float Mf = (float)M;
+  float pen = Mf / 11.0f;
+  float v = Mf * (mn / mx);
+  if ((yh < 0.0f && y > 0.0f) || (yh > 0.0f && y < 0.0f)) v = v - pen;
+  return (int)rintf(v);
+}
+
+/* Eq. 3 summed over N cases of FP64 outputs (rounded to FP32) and FP32-valued
+ * targets; pair counts in c12[0], c12[1]. */
+double or_score_p2p(const double *yhat, const double *y, long N, int M, double *c12) {
+  double s = 0.0, c1 = 0.0, c2 = 0.0;
+  for (long i = 0; i < N; ++i) {
+    float yh = valid_output(yhat[i]) ? (float)yhat[i] : NAN;
+    float yt = (float)y[i];
+    int vh = isfinite(yh), vy = isfinite(yt);
+    c1 += vh != vy;
+    c2 += !vh && !vy;
+    s += (double)or_p2p_case32(yh, yt, M);
+  }
+  if (c12) {
+    c12[0] = c1;
+    c12[1] = c2;
+  }
+  return s;
+}
+
+/* Eq. 2: M r^4 (N - (c1 + c2)) - M (c1 - c2), r over the valid pairs. */
+double or_score_r4(const double *yhat, const double *y, long N, int M, double *c12) {
+  double c1 = 0.0, c2 = 0.0, n = 0.0, mh = 0.0, my = 0.0;
+  for (long i = 0; i < N; ++i) {
+    int vh = valid_output(yhat[i]), vy = isfinite(y[i]);
+    c1 += vh != vy;
+    c2 += !vh && !vy;
+    if (vh && vy) {
+      n += 1.0;
+      mh += yhat[i];
+      my += y[i];
+    }
+  }
+  double r2 = 0.0;
+  if (n >= 2.0) {
+    mh /= n;
+    my /= n;
+    double sxy = 0.0, syy = 0.0, shh = 0.0;
+    for (long i = 0; i < N; ++i) {
+      if (!(valid_output(yhat[i]) && isfinite(y[i]))) continue;
+      double dy = y[i] - my, dh = yhat[i] - mh;
+      sxy += dy * dh;
+      syy += dy * dy;
+      shh += dh * dh;
+    }
+    if (isfinite(sxy) && isfinite(syy) && isfinite(shh) && syy > 0.0 && shh > 0.0) {
+      r2 = (sxy * sxy) / (syy * shh);
+      if (r2 > 1.0) r2 = 1.0;
+    }
+  }
+  if (c12) {
+    c12[0] = c1;
+    c12[1] = c2;
+  }
+  return (double)M * (r2 * r2) * n - (double)M * (c1 - c2);
+}
+
+/*
+ * Whole-population scores (kind 0: Eq. 2, kind 1: Eq. 3).  Invalid programs
+ * score -inf with counts (0, 0).  counts [P][2] may be NULL.
+ */
+void or_eval_score(const uint8_t *programs, const int32_t *lengths, const float *consts, int P,
+                   int Lmax, int K, const double *X, long ldx, const double *y, int nvars, long N,
+                   int kind, int M, double *score, double *counts, int32_t *flags, int nthreads) {
+  int nt = thread_count(nthreads);
+#pragma omp parallel num_threads(nt)
+  {
+    double *yhat = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+    double c[TK_NSLOTS], c12[2];
+#pragma omp for schedule(dynamic, 1)
+    for (int p = 0; p < P; ++p) {
+      const uint8_t *tok = programs + (size_t)p * Lmax;
+      int md;
+      int f = or_validate(tok, lengths[p], Lmax, nvars, K, &md);
+      if (flags) flags[p] = f;
+      c12[0] = c12[1] = 0.0;
+      if (f) {
+        score[p] = -INFINITY;
+      } else {
+        widen_consts(consts + (size_t)p * K, K, c);
+        or_predict(tok, lengths[p], c, X, ldx, N, yhat);
+        score[p] = kind == 0 ? or_score_r4(yhat, y, N, M, c12) : or_score_p2p(yhat, y, N, M, c12);
+      }
+      if (counts) {
+        counts[2 * p] = c12[0];
+        counts[2 * p + 1] = c12[1];
+      }
+    }
+    free(yhat);
+  }
+}
+
+/*
+ * Range of the Eq. 3 score that any FP32 evaluation can produce.  Per case
+ * the FP32 output lies in the enclosure [lo, hi] (case_interval).  With y
+ * fixed, min(|v|,|y|) / max(|v|,|y|) is monotone in v between the breakpoints
+ * -|y|, 0 and |y|, the sign penalty is constant on each side of 0, and the
+ * FP32 operations that follow are monotone; so the case score's extremes over
+ * [lo, hi] are among its values at the ends, at the breakpoints inside, and
+ * at the nearest nonzero FP32 values on either side of 0.  When the enclosure
+ * reaches past the FP32 range, the invalid-output score joins the candidates.
+ * *smin, *smax: sums over the cases; returns 1 when some intermediate of some
+ * case may leave the FP32 range (the enclosure then does not model FP32
+ * overflow inside the program, and the range is not guaranteed).
+ */
+int or_p2p_range_one(const uint8_t *tok, int len, const double *c, const double *X, long ldx,
+                     const double *y, long N, double u, int M, double *smin, double *smax) {
+  double *val = (double *)malloc(sizeof(double) * (size_t)(len + 1));
+  ival *box = (ival *)malloc(sizeof(ival) * (size_t)(len + 1));
+  double tmin = 0.0, tmax = 0.0;
+  int any = 0;
+  for (long i = 0; i < N; ++i) {
+    int cf = 0;
+    double lo, hi;
+    case_interval(tok, len, c, X, ldx, i, u, val, box, &cf, &lo, &hi);
+    any |= cf & CF_RANGE;
+    float yt = (float)y[i];
+    float cand[8];
+    int nc = 0;
+    if (!(lo >= -FLT_MAX && hi <= FLT_MAX)) cand[nc++] = NAN;
+    double l = lo < -FLT_MAX ? -FLT_MAX : lo, h = hi > FLT_MAX ? FLT_MAX : hi;
+    if (l <= h) {
+      cand[nc++] = (float)l;
+      cand[nc++] = (float)h;
+      double ay = fabs((double)yt);
+      if (isfinite(ay)) {
+        if (-ay >= l && -ay <= h) cand[nc++] = (float)-ay;
+        if (ay >= l && ay <= h) cand[nc++] = (float)ay;
+      }
+      if (l <= 0.0 && h >= 0.0) {
+        cand[nc++] = 0.0f;
+        if (l < 0.0) cand[nc++] = -FLT_TRUE_MIN;
+        if (h > 0.0) cand[nc++] = FLT_TRUE_MIN;
+      }
+    }
+    int mn = 0, mx = 0;
+    for (int k = 0; k < nc; ++k) {
+      int v = or_p2p_case32(cand[k], yt, M);
+      if (k == 0 || v < mn) mn = v;
+      if (k == 0 || v > mx) mx = v;
+    }
+    tmin += mn;
+    tmax += mx;
+  }
+  free(val);
+  free(box);
+  *smin = tmin;
+  *smax = tmax;
+  return any;
+}
+
+/* or_p2p_range_one for every program (invalid programs: -inf, -inf, 0). */
+void or_p2p_range(const uint8_t *programs, const int32_t *lengths, const float *consts, int P,
+                  int Lmax, int K, const double *X, long ldx, const double *y, int nvars, long N,
+                  double u, int M, double *smin, double *smax, int32_t *range_flag, int nthreads) {
+  int nt = thread_count(nthreads);
+#pragma omp parallel num_threads(nt)
+  {
+    double c[TK_NSLOTS];
+#pragma omp for schedule(dynamic, 1)
+    for (int p = 0; p < P; ++p) {
+      const uint8_t *tok = programs + (size_t)p * Lmax;
+      int md;
+      if (or_validate(tok, lengths[p], Lmax, nvars, K, &md)) {
+        smin[p] = smax[p] = -INFINITY;
+        range_flag[p] = 0;
+        continue;
+      }
+      widen_consts(consts + (size_t)p * K, K, c);
+      range_flag[p] = or_p2p_range_one(tok, lengths[p], c, X, ldx, y, N, u, M, &smin[p], &smax[p]);
+    }
+  }
+}
+
 /* ---- gradient of MSE with respect to the constants (forward mode) ------ */
 /*
  * Forward-mode (tangent) differentiation: every stack entry carries its
@@ -833,8 +1039,11 @@ static float unit24(uint32_t u) { return (float)(u >> 8) * (1.0f / 16777216.0f);
  * mapped to [0, P).  The smallest fitness wins; NaN counts as +inf; equal
  * fitness goes to the smaller index.  Parent A uses purpose 1, B purpose 2.
  */
-void or_tournament(const double *fitness, int P, int k, uint64_t seed,
-                   uint64_t gen, int32_t *parents) {
+/* k-way tournament; maximise = 0: the smallest fitness wins (NaN = +inf),
+ * maximise = 1: the largest score wins (NaN = -inf); ties to the smaller
+ * index in both. */
+static void tournament_dir(const double *fitness, int P, int k, uint64_t seed, uint64_t gen,
+                           int maximise, int32_t *parents) {
   for (int i = 0; i < P; ++i) {
     for (int s = 0; s < 2; ++s) {
       int best = -1;
@@ -846,8 +1055,9 @@ void or_tournament(const double *fitness, int P, int k, uint64_t seed,
                 s == 0 ? PU_TOURN_A : PU_TOURN_B, gen, w);
         int cand = (int)below(w[j % 4], (uint32_t)P);
         double f = fitness[cand];
-        if (isnan(f)) f = INFINITY;
-        if (best < 0 || f < bestf || (f == bestf && cand < best)) {
+        if (isnan(f)) f = maximise ? -INFINITY : INFINITY;
+        int better = maximise ? f > bestf : f < bestf;
+        if (best < 0 || better || (f == bestf && cand < best)) {
           best = cand;
           bestf = f;
         }
@@ -855,6 +1065,16 @@ void or_tournament(const double *fitness, int P, int k, uint64_t seed,
       parents[2 * i + s] = best;
     }
   }
+}
+
+void or_tournament(const double *fitness, int P, int k, uint64_t seed,
+                   uint64_t gen, int32_t *parents) {
+  tournament_dir(fitness, P, k, seed, gen, 0, parents);
+}
+
+void or_tournament_max(const double *score, int P, int k, uint64_t seed,
+                       uint64_t gen, int32_t *parents) {
+  tournament_dir(score, P, k, seed, gen, 1, parents);
 }
 
 /* ---- random program generation ------------------------------------------ */

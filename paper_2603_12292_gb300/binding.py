@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(PKG, "libsr.so")
 
 SR_OK, SR_EINVAL, SR_ECUDA, SR_ETIMEOUT, SR_EPROGRAM, SR_ENOMEM = range(6)
 SR_MSE, SR_CORR, SR_MSE_CORR = 0, 1, 2
+SR_SCORE_R4, SR_SCORE_P2P = 0, 1
 SR_MAX_LMAX, SR_MAX_VARS, SR_MAX_CONSTS = 512, 16, 16
 
 # exported names declared by include/sr.h (checked by the tests)
@@ -24,6 +25,7 @@ EXPORTS = ["sr_create", "sr_destroy", "sr_set_stream", "sr_status_string", "sr_l
            "sr_reserve", "sr_sync", "sr_eval", "sr_predict", "sr_kernel_launches",
            "sr_eval_noalloc", "sr_philox4x32_10", "sr_select_tournament", "sr_vary",
            "sr_random_programs", "sr_eval_grad", "sr_adam_step", "sr_eval_batched", "sr_set_tile",
+           "sr_eval_score", "sr_select_tournament_max",
            "sr_set_generation_source"]
 
 _lib = None
@@ -90,6 +92,8 @@ def lib() -> ctypes.CDLL:
     L.sr_predict.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp, i32, i32, i32, vp, i32, vp]
     L.sr_philox4x32_10.argtypes = [vp, vp, ctypes.c_uint32, ctypes.c_uint32, vp, i32]
     L.sr_select_tournament.argtypes = [vp, vp, i32, i32, u64, u64, vp]
+    L.sr_select_tournament_max.argtypes = [vp, vp, i32, i32, u64, u64, vp]
+    L.sr_eval_score.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp, vp, i32, i32, i32, i32, i32, vp, vp, vp]
     L.sr_vary.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, ctypes.POINTER(VarCfg),
                           u64, u64]
     L.sr_random_programs.argtypes = [vp, vp, vp, vp, i32, i32, i32, i32, i32, f32, f32, u64, u64]
@@ -190,6 +194,35 @@ def sr_eval(ctx: Context, programs, lengths, consts, X, y, N: int, kind: int,
     return fitness
 
 
+def sr_eval_score(ctx: Context, programs, lengths, consts, X, y, N: int, kind: int, M: int,
+                  score: torch.Tensor | None = None, pair_counts: torch.Tensor | None = None,
+                  prog_flags: torch.Tensor | None = None):
+    """Beagle's scores (sr_eval_score: Eq. 2 for SR_SCORE_R4, Eq. 3 for
+    SR_SCORE_P2P).  Returns score (float64 [P], larger is better) and the
+    pair counts (int32 [P, 2]: c1, c2)."""
+    _dev(programs, torch.uint8, "programs")
+    _dev(lengths, torch.int32, "lengths")
+    _dev(X, torch.float32, "X")
+    _dev(y, torch.float32, "y")
+    P, Lmax = programs.shape
+    K = 0 if consts is None else (consts.shape[1] if consts.dim() == 2 else 0)
+    if consts is not None and K > 0:
+        _dev(consts, torch.float32, "consts")
+    nvars, ldx = X.shape
+    if score is None:
+        score = torch.empty(P, dtype=torch.float64, device=programs.device)
+    if pair_counts is None:
+        pair_counts = torch.empty((P, 2), dtype=torch.int32, device=programs.device)
+    _dev(score, torch.float64, "score")
+    _dev(pair_counts, torch.int32, "pair_counts")
+    if prog_flags is not None:
+        _dev(prog_flags, torch.int32, "prog_flags")
+    _check(ctx, lib().sr_eval_score(ctx.handle, _ptr(programs), _ptr(lengths), _ptr(consts) if K else None,
+                                    P, Lmax, K, _ptr(X), _ptr(y), nvars, N, ldx, kind, M, _ptr(score),
+                                    _ptr(pair_counts), _ptr(prog_flags)))
+    return score, pair_counts
+
+
 def sr_predict(ctx: Context, programs, lengths, consts, X, N: int,
                yhat: torch.Tensor | None = None, prog_flags: torch.Tensor | None = None):
     """Outputs of every program on every case (sr_predict); returns yhat
@@ -252,6 +285,18 @@ def sr_select_tournament(ctx: Context, fitness, k: int, seed: int, gen: int,
         parents = torch.empty((P, 2), dtype=torch.int32, device=fitness.device)
     _dev(parents, torch.int32, "parents")
     _check(ctx, lib().sr_select_tournament(ctx.handle, _ptr(fitness), P, k, seed, gen, _ptr(parents)))
+    return parents
+
+
+def sr_select_tournament_max(ctx: Context, score, k: int, seed: int, gen: int,
+                             parents: torch.Tensor | None = None) -> torch.Tensor:
+    """The same draws as sr_select_tournament; the largest score wins."""
+    _dev(score, torch.float64, "score")
+    P = score.shape[0]
+    if parents is None:
+        parents = torch.empty((P, 2), dtype=torch.int32, device=score.device)
+    _dev(parents, torch.int32, "parents")
+    _check(ctx, lib().sr_select_tournament_max(ctx.handle, _ptr(score), P, k, seed, gen, _ptr(parents)))
     return parents
 
 

@@ -49,7 +49,7 @@ constexpr int SLOT_BYTES = 32 * CPL * 4;  // one stack slot of a warp: [2][32 la
 constexpr int PSTRIDE = 8;      // doubles per partial record
 constexpr int TARGET_ITEMS_PER_WARP = 8;
 
-enum Mode { MODE_PREDICT = 0, MODE_MSE = 1, MODE_CORR = 2, MODE_BOTH = 3 };
+enum Mode { MODE_PREDICT = 0, MODE_MSE = 1, MODE_CORR = 2, MODE_BOTH = 3, MODE_R4 = 4, MODE_P2P = 5 };
 
 struct EvalParams {
   const uint8_t *programs;
@@ -74,6 +74,7 @@ struct EvalParams {
   float *yhat;             // predict: [P][ldy]
   long long ldy;
   int warp_bytes;          // shared memory per warp
+  int score_M;             // Beagle scores: the maximum score per case
 };
 
 __host__ __device__ inline int warp_smem_bytes(int Lmax) {
@@ -279,6 +280,19 @@ __device__ __forceinline__ float4 load_y4(const float *__restrict__ y, int c0, i
   return r;
 }
 
+// Eq. 3 on one case, FP32, every operation rounded on its own (no
+// contraction), the result rounded half to even.
+__device__ __forceinline__ int p2p_case(float yh, float y, int M, float Mf, float pen) {
+  const bool vh = isfinite(yh), vy = isfinite(y);
+  if (!(vh && vy)) return (vh || vy) ? -M : M;
+  const float a = fabsf(yh), b = fabsf(y);
+  const float mx = fmaxf(a, b), mn = fminf(a, b);
+  if (mx == 0.0f) return M;
+  float v = __fmul_rn(Mf, __fdiv_rn(mn, mx));
+  if ((yh < 0.0f && y > 0.0f) || (yh > 0.0f && y < 0.0f)) v = __fsub_rn(v, pen);
+  return (int)rintf(v);
+}
+
 // ---------------------------------------------------------------- one work item
 struct WarpSmem {
   char *stk;        // shared stack slots of this warp, [DSM][2][32] float4
@@ -319,8 +333,11 @@ __device__ __forceinline__ void eval_item(const EvalParams &p, int c, int prog, 
   char *stk = w.stk + lane * 16;
   const int last_group = (cend - 1) & ~(CPL - 1);
 
-  Kahan se, s1, s2, s3;
+  Kahan se, s1, s2, s3, s4, s5;
   float shift = 0.f;
+  long long score = 0;
+  int c1 = 0, c2 = 0;
+  const float Mf = (float)p.score_M, pen = __fdiv_rn(Mf, 11.0f);
   for (int base = cbeg; base < cend; base += STEP) {
     const int c0 = base + CPL * lane;
     const int cl = c0 < cend ? c0 : last_group;           // first 4 cases, always readable
@@ -358,6 +375,46 @@ __device__ __forceinline__ void eval_item(const EvalParams &p, int c, int prog, 
       s3.add(((d[0] * yv[0] + d[1] * yv[1]) + (d[2] * yv[2] + d[3] * yv[3])) +
              ((d[4] * yv[4] + d[5] * yv[5]) + (d[6] * yv[6] + d[7] * yv[7])));
     }
+    if (MODE == MODE_R4) {
+      // pairs: both finite -> moments; one invalid -> c1; both -> c2.  yc
+      // holds y - ybar for finite y and NaN for invalid targets.
+      if (base == cbeg) {
+        const unsigned fin = __ballot_sync(FULL, isfinite(T.a.x));
+        shift = fin ? __shfl_sync(FULL, T.a.x, __ffs(fin) - 1) : 0.0f;
+      }
+      const float4 ya = ldx4(p.yc + cl), yb = ldx4(p.yc + cl4);
+      const float yv[CPL] = {ya.x, ya.y, ya.z, ya.w, yb.x, yb.y, yb.z, yb.w};
+      float d[CPL], e[CPL];
+#pragma unroll
+      for (int i = 0; i < CPL; ++i) {
+        const bool vh = isfinite(tv[i]), vy = isfinite(yv[i]);
+        const bool pair = ok[i] && vh && vy;
+        c1 += (ok[i] && vh != vy) ? 1 : 0;
+        c2 += (ok[i] && !vh && !vy) ? 1 : 0;
+        d[i] = pair ? tv[i] - shift : 0.0f;
+        e[i] = pair ? yv[i] : 0.0f;
+      }
+      s1.add(((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])));
+      s2.add(((d[0] * d[0] + d[1] * d[1]) + (d[2] * d[2] + d[3] * d[3])) +
+             ((d[4] * d[4] + d[5] * d[5]) + (d[6] * d[6] + d[7] * d[7])));
+      s3.add(((d[0] * e[0] + d[1] * e[1]) + (d[2] * e[2] + d[3] * e[3])) +
+             ((d[4] * e[4] + d[5] * e[5]) + (d[6] * e[6] + d[7] * e[7])));
+      s4.add(((e[0] + e[1]) + (e[2] + e[3])) + ((e[4] + e[5]) + (e[6] + e[7])));
+      s5.add(((e[0] * e[0] + e[1] * e[1]) + (e[2] * e[2] + e[3] * e[3])) +
+             ((e[4] * e[4] + e[5] * e[5]) + (e[6] * e[6] + e[7] * e[7])));
+    }
+    if (MODE == MODE_P2P) {
+      const float4 ya = load_y4(p.y, cl, p.N), yb = load_y4(p.y, cl4, p.N);
+      const float yv[CPL] = {ya.x, ya.y, ya.z, ya.w, yb.x, yb.y, yb.z, yb.w};
+#pragma unroll
+      for (int i = 0; i < CPL; ++i) {
+        if (!ok[i]) continue;
+        const bool vh = isfinite(tv[i]), vy = isfinite(yv[i]);
+        c1 += vh != vy ? 1 : 0;
+        c2 += (!vh && !vy) ? 1 : 0;
+        score += p2p_case(tv[i], yv[i], p.score_M, Mf, pen);
+      }
+    }
   }
   if (MODE != MODE_PREDICT) {
     double *rec = p.partials + ((size_t)prog * p.nchunks + c) * PSTRIDE;
@@ -374,6 +431,32 @@ __device__ __forceinline__ void eval_item(const EvalParams &p, int c, int prog, 
         rec[2] = a;
         rec[3] = b;
         rec[4] = d;
+      }
+    }
+    if (MODE == MODE_R4) {
+      // [shift, sum d, sum d^2, sum d e, sum e, sum e^2, c1, c2]
+      const double v1 = warp_sum(s1.value()), v2 = warp_sum(s2.value()), v3 = warp_sum(s3.value());
+      const double v4 = warp_sum(s4.value()), v5 = warp_sum(s5.value());
+      const double n1 = warp_sum((double)c1), n2 = warp_sum((double)c2);
+      if (lane == 0) {
+        rec[0] = (double)shift;
+        rec[1] = v1;
+        rec[2] = v2;
+        rec[3] = v3;
+        rec[4] = v4;
+        rec[5] = v5;
+        rec[6] = n1;
+        rec[7] = n2;
+      }
+    }
+    if (MODE == MODE_P2P) {
+      // [sum of the integer scores (exact), c1, c2]
+      const double v = warp_sum((double)score);
+      const double n1 = warp_sum((double)c1), n2 = warp_sum((double)c2);
+      if (lane == 0) {
+        rec[0] = v;
+        rec[6] = n1;
+        rec[7] = n2;
       }
     }
   }
@@ -415,7 +498,7 @@ struct BatchProblem {
   int16_t *s_task;
   double *fitness;     // [P] or [2][P]
   double *ychunk;      // [nchunks][2]
-  double *stats;       // [8]
+  double *ysum;        // [nchunks][2]: FP64 sum and count of y per chunk
   long long ldx;
   long long item_begin;  // first work item of this problem in the launch
   int prog_begin;        // first program of this problem in the decode launch
@@ -517,24 +600,59 @@ __device__ double block_sum(double v, double *red) {
   return s;  // valid in thread 0
 }
 
-// ybar = sum(y) / N in FP64 (one block, fixed order)
-__global__ void __launch_bounds__(PREP_THREADS) ymean_kernel(const float *__restrict__ y, int N,
-                                                             double *stats) {
-  __shared__ double red[PREP_THREADS / 32];
-  double s = 0.0;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) s += (double)y[i];
-  s = block_sum(s, red);
-  if (threadIdx.x == 0) stats[0] = s / (double)N;
+// FP64 sum and count of one chunk of y: every value, or (finite_only) the
+// finite ones.  ysum [nchunks][2].
+__device__ void ysum_chunk(const float *__restrict__ y, int N, int chunk, int c, bool finite_only,
+                           double *ysum, double *red) {
+  const int beg = c * chunk, end = min(N, beg + chunk);
+  double a = 0.0, n = 0.0;
+  for (int i = beg + threadIdx.x; i < end; i += blockDim.x) {
+    const float v = y[i];
+    if (!finite_only || isfinite(v)) {
+      a += (double)v;
+      n += 1.0;
+    }
+  }
+  a = block_sum(a, red);
+  n = block_sum(n, red);
+  if (threadIdx.x == 0) {
+    ysum[2 * c] = a;
+    ysum[2 * c + 1] = n;
+  }
 }
 
-// yc = fl32(y - ybar) on one chunk, with its FP64 sum and sum of squares
+__global__ void __launch_bounds__(PREP_THREADS) ysum_kernel(const float *__restrict__ y, int N, int chunk,
+                                                            int finite_only, double *ysum) {
+  __shared__ double red[PREP_THREADS / 32];
+  ysum_chunk(y, N, chunk, blockIdx.x, finite_only != 0, ysum, red);
+}
+
+// ybar = (sum of the chunk sums) / (their count), chunks in order; then
+// yc = fl32(y - ybar) on one chunk (NaN at invalid targets when
+// nan_invalid) with the chunk's FP64 sum and sum of squares of yc
 __device__ void ycenter_chunk(const float *__restrict__ y, int N, int chunk, int nchunks, int c,
-                              const double *stats, float *yc, double *ychunk, double *red) {
-  const double ybar = stats[0];
+                              const double *ysum, bool nan_invalid, float *yc, double *ychunk,
+                              double *red) {
+  __shared__ double ybar_s;
+  if (threadIdx.x == 0) {
+    double t = 0.0, n = 0.0;
+    for (int k = 0; k < nchunks; ++k) {
+      t += ysum[2 * k];
+      n += ysum[2 * k + 1];
+    }
+    ybar_s = n > 0.0 ? t / n : 0.0;
+  }
+  __syncthreads();
+  const double ybar = ybar_s;
   const int beg = c * chunk, end = min(N, beg + chunk);
   double a = 0.0, b = 0.0;
   for (int i = beg + threadIdx.x; i < end; i += blockDim.x) {
-    const float v = (float)((double)y[i] - ybar);
+    const float yi = y[i];
+    if (nan_invalid && !isfinite(yi)) {
+      yc[i] = __int_as_float(0x7fc00000);
+      continue;
+    }
+    const float v = (float)((double)yi - ybar);
     yc[i] = v;
     a += (double)v;
     b += (double)v * (double)v;
@@ -553,10 +671,10 @@ __device__ void ycenter_chunk(const float *__restrict__ y, int N, int chunk, int
 
 __global__ void __launch_bounds__(PREP_THREADS) ycenter_kernel(const float *__restrict__ y, int N,
                                                                int chunk, int nchunks,
-                                                               const double *stats, float *yc,
-                                                               double *ychunk) {
+                                                               const double *ysum, int nan_invalid,
+                                                               float *yc, double *ychunk) {
   __shared__ double red[PREP_THREADS / 32];
-  ycenter_chunk(y, N, chunk, nchunks, blockIdx.x, stats, yc, ychunk, red);
+  ycenter_chunk(y, N, chunk, nchunks, blockIdx.x, ysum, nan_invalid != 0, yc, ychunk, red);
 }
 
 // ---------------------------------------------------------------- finalize
@@ -596,11 +714,75 @@ __device__ double corr_fitness(const double *rec, const double *ychunk, int Nc, 
   return fit;
 }
 
+// Eq. 2 of one program from its chunk records [shift s, S1 = sum d,
+// S2 = sum d^2, X = sum d e, E1 = sum e, E2 = sum e^2, c1, c2] over the
+// valid pairs (d = yhat - s, e = y - ybar).  Valid pairs of chunk c:
+// n_c = cases - c1 - c2.  Shh merges the chunks by Chan et al.; e shares one
+// centre, so See = E2 - E1^2 / n; Seh = sum (X_c + s_c E1_c) - m E1.
+__device__ double r4_score(const double *rec, int Nc, int chunk, int nchunks, double M, double *c1o,
+                           double *c2o) {
+  double c1 = 0.0, c2 = 0.0, n = 0.0, tot = 0.0, e1 = 0.0, e2 = 0.0;
+  for (int c = 0; c < nchunks; ++c) {
+    const double *r = rec + c * PSTRIDE;
+    const double nv = (double)min(chunk, Nc - c * chunk) - r[6] - r[7];
+    c1 += r[6];
+    c2 += r[7];
+    n += nv;
+    tot += r[1] + nv * r[0];
+    e1 += r[4];
+    e2 += r[5];
+  }
+  double r2 = 0.0;
+  if (n >= 2.0) {
+    const double m = tot / n;
+    double shh = 0.0, seh = 0.0;
+    for (int c = 0; c < nchunks; ++c) {
+      const double *r = rec + c * PSTRIDE;
+      const double nv = (double)min(chunk, Nc - c * chunk) - r[6] - r[7];
+      if (nv <= 0.0) continue;
+      const double mc = r[0] + r[1] / nv;
+      shh += (r[2] - r[1] * r[1] / nv) + nv * (mc - m) * (mc - m);
+      seh += r[3] + r[0] * r[4];
+    }
+    seh -= m * e1;
+    const double see = e2 - e1 * e1 / n;
+    if (isfinite(shh) && isfinite(seh) && isfinite(see) && shh > 0.0 && see > 0.0) {
+      r2 = (seh * seh) / (shh * see);
+      r2 = r2 < 0.0 ? 0.0 : (r2 > 1.0 ? 1.0 : r2);
+    }
+  }
+  *c1o = c1;
+  *c2o = c2;
+  return M * (r2 * r2) * n - M * (c1 - c2);
+}
+
 // fitness of program p from its partial records (mode picks the outputs)
 __device__ void finalize_one(int mode, const double *partials, const int32_t *flags,
                              const double *ychunk, int P, int N, int chunk, int nchunks,
-                             double *fitness, int p) {
+                             double *fitness, int p, int M = 0, int32_t *counts = nullptr) {
   const double INF = __longlong_as_double(0x7ff0000000000000ll);
+  if (mode == MODE_R4 || mode == MODE_P2P) {
+    double c1 = 0.0, c2 = 0.0, sc = -INF;
+    if (!flags[p]) {
+      const double *rec = partials + (size_t)p * nchunks * PSTRIDE;
+      if (mode == MODE_R4) {
+        sc = r4_score(rec, N, chunk, nchunks, (double)M, &c1, &c2);
+      } else {
+        sc = 0.0;
+        for (int c = 0; c < nchunks; ++c) {
+          sc += rec[c * PSTRIDE];
+          c1 += rec[c * PSTRIDE + 6];
+          c2 += rec[c * PSTRIDE + 7];
+        }
+      }
+    }
+    fitness[p] = sc;
+    if (counts) {
+      counts[2 * p] = (int32_t)c1;
+      counts[2 * p + 1] = (int32_t)c2;
+    }
+    return;
+  }
   double *mse_out = fitness;
   double *corr_out = mode == MODE_BOTH ? fitness + P : fitness;
   if (flags[p]) {
@@ -623,32 +805,36 @@ struct FinalParams {
   const double *ychunk;
   int P, N, chunk, nchunks, mode;
   double *fitness;  // [P] or [2][P]
+  int M;            // Beagle scores
+  int32_t *counts;  // Beagle scores: [P][2] (c1, c2) or NULL
 };
 
 __global__ void finalize_kernel(FinalParams f) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= f.P) return;
-  finalize_one(f.mode, f.partials, f.flags, f.ychunk, f.P, f.N, f.chunk, f.nchunks, f.fitness, p);
+  finalize_one(f.mode, f.partials, f.flags, f.ychunk, f.P, f.N, f.chunk, f.nchunks, f.fitness, p, f.M,
+               f.counts);
 }
 
 // ---------------------------------------------------------------- batched prep / finalize
-// one block per problem that needs the centred target: its FP64 mean
-__global__ void __launch_bounds__(PREP_THREADS) ymean_batched_kernel(const __grid_constant__ BatchParams b) {
-  __shared__ double red[PREP_THREADS / 32];
-  const BatchProblem &q = b.prob[b.corr_list[blockIdx.x]];
-  double s = 0.0;
-  for (int i = threadIdx.x; i < q.N; i += blockDim.x) s += (double)q.y[i];
-  s = block_sum(s, red);
-  if (threadIdx.x == 0) q.stats[0] = s / (double)q.N;
-}
-
-// one block per (problem, chunk): centred target and its chunk sums
-__global__ void __launch_bounds__(PREP_THREADS) ycenter_batched_kernel(const __grid_constant__ BatchParams b) {
-  __shared__ double red[PREP_THREADS / 32];
+// one block per (problem, chunk) of the problems that need the centred
+// target: the chunk sums of y, then (next launch) the centred target
+__device__ __forceinline__ int corr_problem_of_block(const BatchParams &b) {
   int r = 0;
   while (r + 1 < b.ncorr && b.prob[b.corr_list[r + 1]].corr_chunk_begin <= (int)blockIdx.x) ++r;
-  const BatchProblem &q = b.prob[b.corr_list[r]];
-  ycenter_chunk(q.y, q.N, q.chunk, q.nchunks, (int)blockIdx.x - q.corr_chunk_begin, q.stats, q.yc,
+  return b.corr_list[r];
+}
+
+__global__ void __launch_bounds__(PREP_THREADS) ysum_batched_kernel(const __grid_constant__ BatchParams b) {
+  __shared__ double red[PREP_THREADS / 32];
+  const BatchProblem &q = b.prob[corr_problem_of_block(b)];
+  ysum_chunk(q.y, q.N, q.chunk, (int)blockIdx.x - q.corr_chunk_begin, false, q.ysum, red);
+}
+
+__global__ void __launch_bounds__(PREP_THREADS) ycenter_batched_kernel(const __grid_constant__ BatchParams b) {
+  __shared__ double red[PREP_THREADS / 32];
+  const BatchProblem &q = b.prob[corr_problem_of_block(b)];
+  ycenter_chunk(q.y, q.N, q.chunk, q.nchunks, (int)blockIdx.x - q.corr_chunk_begin, q.ysum, false, q.yc,
                 q.ychunk, red);
 }
 
@@ -682,6 +868,8 @@ sr_status grid_for(sr_ctx *ctx, int mode, int smem, int *grid) {
     case MODE_PREDICT: return occupancy_grid<MODE_PREDICT>(ctx, smem, grid);
     case MODE_MSE: return occupancy_grid<MODE_MSE>(ctx, smem, grid);
     case MODE_CORR: return occupancy_grid<MODE_CORR>(ctx, smem, grid);
+    case MODE_R4: return occupancy_grid<MODE_R4>(ctx, smem, grid);
+    case MODE_P2P: return occupancy_grid<MODE_P2P>(ctx, smem, grid);
     default: return occupancy_grid<MODE_BOTH>(ctx, smem, grid);
   }
 }
@@ -690,7 +878,7 @@ struct Plan {
   int grid, smem, chunk, nchunks;
   long long items;
   size_t off_queue, off_flags, off_ncode, off_code, off_start, off_need, off_task, off_part, off_yc,
-      off_ych, off_stats, bytes;
+      off_ych, off_ysum, bytes;
 };
 
 sr_status make_plan(sr_ctx *ctx, int mode, int P, int Lmax, int N, Plan *pl) {
@@ -720,7 +908,7 @@ sr_status make_plan(sr_ctx *ctx, int mode, int P, int Lmax, int N, Plan *pl) {
   pl->off_part = cv.take((size_t)pl->items * PSTRIDE * 8);
   pl->off_yc = cv.take(align_up((size_t)N, STEP) * 4);
   pl->off_ych = cv.take((size_t)pl->nchunks * 16);
-  pl->off_stats = cv.take(64);
+  pl->off_ysum = cv.take((size_t)pl->nchunks * 16);
   pl->bytes = cv.off;
   return SR_OK;
 }
@@ -750,7 +938,7 @@ int mode_of(sr_fitness_kind k) {
 sr_status launch_eval(sr_ctx *ctx, int mode, const uint8_t *programs, const int32_t *lengths,
                       const float *consts, int P, int Lmax, int K, const float *X, const float *y,
                       int nvars, int N, int ldx, double *fitness, int32_t *prog_flags, float *yhat,
-                      int ldy) {
+                      int ldy, int M = 0, int32_t *counts = nullptr) {
   SR_CHECK_CUDA(ctx, cudaSetDevice(ctx->device));
   Plan pl;
   sr_status st = make_plan(ctx, mode, P, Lmax, N, &pl);
@@ -787,15 +975,18 @@ sr_status launch_eval(sr_ctx *ctx, int mode, const uint8_t *programs, const int3
   ep.yhat = yhat;
   ep.ldy = ldy;
   ep.warp_bytes = warp_smem_bytes(Lmax);
+  ep.score_M = M;
 
   SR_CHECK_CUDA(ctx, cudaMemsetAsync(ep.queue, 0, sizeof(unsigned long long), s));
-  decode_kernel<<<(P + 127) / 128, 128, 0, s>>>(ep);
+  // one warp per block spreads the serial per-program decode over the SMs
+  decode_kernel<<<(P + 31) / 32, 32, 0, s>>>(ep);
   ctx->launches += 1;
   double *ych = reinterpret_cast<double *>(ws + pl.off_ych);
-  if (mode == MODE_CORR || mode == MODE_BOTH) {
-    double *stats = reinterpret_cast<double *>(ws + pl.off_stats);
-    ymean_kernel<<<1, PREP_THREADS, 0, s>>>(y, N, stats);
-    ycenter_kernel<<<pl.nchunks, PREP_THREADS, 0, s>>>(y, N, pl.chunk, pl.nchunks, stats,
+  if (mode == MODE_CORR || mode == MODE_BOTH || mode == MODE_R4) {
+    double *ysum = reinterpret_cast<double *>(ws + pl.off_ysum);
+    const int r4 = mode == MODE_R4;
+    ysum_kernel<<<pl.nchunks, PREP_THREADS, 0, s>>>(y, N, pl.chunk, r4, ysum);
+    ycenter_kernel<<<pl.nchunks, PREP_THREADS, 0, s>>>(y, N, pl.chunk, pl.nchunks, ysum, r4,
                                                       const_cast<float *>(ep.yc), ych);
     ctx->launches += 2;
   }
@@ -803,12 +994,14 @@ sr_status launch_eval(sr_ctx *ctx, int mode, const uint8_t *programs, const int3
     case MODE_PREDICT: eval_kernel<MODE_PREDICT><<<pl.grid, WARPS * 32, pl.smem, s>>>(ep); break;
     case MODE_MSE: eval_kernel<MODE_MSE><<<pl.grid, WARPS * 32, pl.smem, s>>>(ep); break;
     case MODE_CORR: eval_kernel<MODE_CORR><<<pl.grid, WARPS * 32, pl.smem, s>>>(ep); break;
+    case MODE_R4: eval_kernel<MODE_R4><<<pl.grid, WARPS * 32, pl.smem, s>>>(ep); break;
+    case MODE_P2P: eval_kernel<MODE_P2P><<<pl.grid, WARPS * 32, pl.smem, s>>>(ep); break;
     default: eval_kernel<MODE_BOTH><<<pl.grid, WARPS * 32, pl.smem, s>>>(ep); break;
   }
   SR_CHECK_CUDA(ctx, cudaGetLastError());
   ctx->launches += 1;
   if (mode != MODE_PREDICT) {
-    FinalParams fp{ep.partials, ep.flags, ych, P, N, pl.chunk, pl.nchunks, mode, fitness};
+    FinalParams fp{ep.partials, ep.flags, ych, P, N, pl.chunk, pl.nchunks, mode, fitness, M, counts};
     finalize_kernel<<<(P + 255) / 256, 256, 0, s>>>(fp);
     SR_CHECK_CUDA(ctx, cudaGetLastError());
     ctx->launches += 1;
@@ -906,7 +1099,7 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
       if (corr) {
         off_yc = cv.take(align_up((size_t)q.N, STEP) * 4);
         off_ych = cv.take((size_t)nch[i] * 16);
-        off_st = cv.take(64);
+        off_st = cv.take((size_t)nch[i] * 16);
       }
       if (bpar) {
         BatchProblem &b = bpar->prob[g - g0];
@@ -926,7 +1119,7 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
         b.s_task = reinterpret_cast<int16_t *>(ws + off_task);
         b.fitness = q.fitness;
         b.ychunk = corr ? reinterpret_cast<double *>(ws + off_ych) : nullptr;
-        b.stats = corr ? reinterpret_cast<double *>(ws + off_st) : nullptr;
+        b.ysum = corr ? reinterpret_cast<double *>(ws + off_st) : nullptr;
         b.ldx = q.ldx;
         b.item_begin = items;
         b.prog_begin = progs;
@@ -978,7 +1171,7 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
     decode_batched_kernel<<<(b.total_progs + 127) / 128, 128, 0, s>>>(b);
     ctx->launches += 1;
     if (b.ncorr > 0) {
-      ymean_batched_kernel<<<b.ncorr, PREP_THREADS, 0, s>>>(b);
+      ysum_batched_kernel<<<corr_blocks, PREP_THREADS, 0, s>>>(b);
       ycenter_batched_kernel<<<corr_blocks, PREP_THREADS, 0, s>>>(b);
       ctx->launches += 2;
     }
@@ -1008,6 +1201,25 @@ sr_status sr_eval(sr_ctx *ctx, const uint8_t *programs, const int32_t *lengths, 
   if (((uintptr_t)y) & 15) return fail(ctx, SR_EINVAL, "y must be 16-byte aligned");
   return launch_eval(ctx, mode_of(kind), programs, lengths, consts, P, Lmax, K, X, y, nvars, N, ldx,
                      fitness, prog_flags, nullptr, 0);
+}
+
+sr_status sr_eval_score(sr_ctx *ctx, const uint8_t *programs, const int32_t *lengths,
+                        const float *consts, int P, int Lmax, int K, const float *X, const float *y,
+                        int nvars, int N, int ldx, sr_score_kind kind, int M, double *score,
+                        int32_t *pair_counts, int32_t *prog_flags) {
+  using namespace sr;
+  sr_status st = check_common(ctx, programs, lengths, consts, P, Lmax, K, X, nvars, N, ldx);
+  if (st != SR_OK) return st;
+  if (kind != SR_SCORE_R4 && kind != SR_SCORE_P2P)
+    return fail(ctx, SR_EINVAL, "unknown score kind %d", (int)kind);
+  if (M < 1 || M > (1 << 24)) return fail(ctx, SR_EINVAL, "M %d outside [1, 2^24]", M);
+  if ((double)M * (double)N > 9007199254740992.0)
+    return fail(ctx, SR_EINVAL, "M * N above 2^53: the score sum would not be exact");
+  if (P == 0) return SR_OK;
+  if (!y || !score) return fail(ctx, SR_EINVAL, "NULL y or score");
+  if (((uintptr_t)y) & 15) return fail(ctx, SR_EINVAL, "y must be 16-byte aligned");
+  return launch_eval(ctx, kind == SR_SCORE_R4 ? MODE_R4 : MODE_P2P, programs, lengths, consts, P, Lmax, K,
+                     X, y, nvars, N, ldx, score, prog_flags, nullptr, 0, M, pair_counts);
 }
 
 sr_status sr_predict(sr_ctx *ctx, const uint8_t *programs, const int32_t *lengths,

@@ -111,6 +111,9 @@ __global__ void philox_kernel(const uint32_t *__restrict__ ctr, uint32_t k0, uin
   for (int j = 0; j < 4; ++j) out[4 * i + j] = w.v[j];
 }
 
+// MAXIMISE = 0: the smallest fitness wins, NaN counting as +inf;
+// MAXIMISE = 1: the largest score wins, NaN counting as -inf.
+template <int MAXIMISE>
 __global__ void tournament_kernel(const double *__restrict__ fitness, int P, int k, Rng rng_in,
                                   int32_t *__restrict__ parents) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -125,8 +128,9 @@ __global__ void tournament_kernel(const double *__restrict__ fitness, int P, int
     if ((j & 3) == 0) w = rng.draw((uint32_t)(j >> 2), (uint32_t)i, s ? PU_TOURN_B : PU_TOURN_A);
     const int cand = (int)below(w.v[j & 3], (uint32_t)P);
     double f = fitness[cand];
-    if (isnan(f)) f = INF;
-    if (best < 0 || f < bestf || (f == bestf && cand < best)) {
+    if (isnan(f)) f = MAXIMISE ? -INF : INF;
+    const bool better = MAXIMISE ? f > bestf : f < bestf;
+    if (best < 0 || better || (f == bestf && cand < best)) {
       best = cand;
       bestf = f;
     }
@@ -294,19 +298,32 @@ sr_status sr_philox4x32_10(sr_ctx *ctx, const uint32_t *ctr, uint32_t key0, uint
   return SR_OK;
 }
 
-sr_status sr_select_tournament(sr_ctx *ctx, const double *fitness, int P, int k, uint64_t seed,
-                               uint64_t gen, int32_t *parents) {
+static sr_status select_tournament(sr_ctx *ctx, const double *fitness, int P, int k, uint64_t seed,
+                                   uint64_t gen, int32_t *parents, bool maximise) {
   using namespace sr;
   if (!ctx) return SR_EINVAL;
   if (P < 0 || k < 1 || k > 64) return fail(ctx, SR_EINVAL, "P < 0 or k outside [1, 64]");
   if (P == 0) return SR_OK;
   if (!fitness || !parents) return fail(ctx, SR_EINVAL, "NULL fitness or parents");
   SR_CHECK_CUDA(ctx, cudaSetDevice(ctx->device));
-  tournament_kernel<<<(2 * P + 255) / 256, 256, 0, ctx->stream>>>(
-      fitness, P, k, make_rng(seed, gen, ctx->gen_dev), parents);
+  const Rng rng = make_rng(seed, gen, ctx->gen_dev);
+  if (maximise)
+    tournament_kernel<1><<<(2 * P + 255) / 256, 256, 0, ctx->stream>>>(fitness, P, k, rng, parents);
+  else
+    tournament_kernel<0><<<(2 * P + 255) / 256, 256, 0, ctx->stream>>>(fitness, P, k, rng, parents);
   SR_CHECK_CUDA(ctx, cudaGetLastError());
   ctx->launches += 1;
   return SR_OK;
+}
+
+sr_status sr_select_tournament(sr_ctx *ctx, const double *fitness, int P, int k, uint64_t seed,
+                               uint64_t gen, int32_t *parents) {
+  return select_tournament(ctx, fitness, P, k, seed, gen, parents, false);
+}
+
+sr_status sr_select_tournament_max(sr_ctx *ctx, const double *score, int P, int k, uint64_t seed,
+                                   uint64_t gen, int32_t *parents) {
+  return select_tournament(ctx, score, P, k, seed, gen, parents, true);
 }
 
 sr_status sr_vary(sr_ctx *ctx, const uint8_t *prog_in, const int32_t *len_in, const float *c_in,
