@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ops", default="base", choices=["base", "table1"],
+                    help="operator set of the paper / beagle populations: base (+ - * / sin cos exp log "
+                         "sqrt sq) or table1 (adds 1/x tan asin acos atan tanh, Table 1)")
     ap.add_argument("--small", action="store_true",
                     help="reduced sizes of the adjoint / large / batched workloads (2,048 x 131,072; "
                          "16,384 x 131,072; the first 8 problems), for profiler captures")
@@ -125,7 +128,7 @@ def run_reference(args, rank, world):
     from paper_2603_12292_gb300 import inputs
     if rank != 0:
         return 0
-    pr = inputs.paper_shaped()
+    pr = inputs.paper_shaped(unary_ops=12 if args.ops == "table1" else 6)
     y64 = oracle.predict(pr.target, pr.target_consts, pr.X, pr.N)
     y = inputs.add_noise(np.random.default_rng(pr.seed + 7), y64, pr.noise)
     cores = os.cpu_count() or 1
@@ -176,7 +179,8 @@ def run_ours(args, rank, world, local_rank):
     ctx = binding.Context(local_rank)
     stream = torch.cuda.current_stream(dev)
 
-    pr = inputs.paper_shaped()
+    nun = 12 if args.ops == "table1" else 6
+    pr = inputs.paper_shaped(unary_ops=nun)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     programs, lengths, consts, X = t(pr.programs), t(pr.lengths), t(pr.consts), t(pr.X)
     # the target on the device with the library's own predict, then 1% noise (host, FP64)
@@ -190,7 +194,7 @@ def run_ours(args, rank, world, local_rank):
     fitness = torch.empty((2, pr.P), dtype=torch.float64, device=dev)
     parents = torch.empty((pr.P, 2), dtype=torch.int32, device=dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-    cfg = binding.var_cfg()  # p_cross 0.9, p_point 0.1, p_subtree 0.05, p_const 0.1
+    cfg = binding.var_cfg(unary_ops=nun)  # p_cross 0.9, p_point 0.1, p_subtree 0.05, p_const 0.1
     pop = [(programs, lengths, consts),
            (torch.empty_like(programs), torch.empty_like(lengths), torch.empty_like(consts))]
     SEED, K_TOURN = 20260312 + rank, 4  # each rank evolves its own population (an island)
@@ -489,7 +493,8 @@ def run_workload(args, local_rank):
                     value=n_before / (t / 1e3) / 1e9, unit="GPop/s", ms_per_step=t, scaling="weak",
                     config={"workload": pr.name, "programs": pr.P, "cases": pr.N, "lengths": "4-256"})
     elif args.workload == "beagle":
-        pr = inputs.paper_shaped()
+        nun = 12 if args.ops == "table1" else 6
+        pr = inputs.paper_shaped(unary_ops=nun)
         pg, ln, cs, X, y = _device_problem(pr, dev, binding, ctx)
         # 1 % invalid targets (NaN, +inf, -inf in turn) at seeded cases
         bad = np.sort(np.random.default_rng(pr.seed + 11).choice(pr.N, pr.N // 100, replace=False))
@@ -501,7 +506,7 @@ def run_workload(args, local_rank):
         counts = torch.empty((P, 2), dtype=torch.int32, device=dev)
         parents = torch.empty((P, 2), dtype=torch.int32, device=dev)
         flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-        vcfg = binding.var_cfg()
+        vcfg = binding.var_cfg(unary_ops=nun)
         pop = [(pg, ln, cs), (torch.empty_like(pg), torch.empty_like(ln), torch.empty_like(cs))]
         state = {"gen": 0, "cur": 0}
 
@@ -541,7 +546,8 @@ def run_workload(args, local_rank):
         line.update(metric="GPop/s, one generation scored by Beagle's r^4 score (Eq. 2) with invalid targets",
                     value=sum(nodes) / (sum(ms) / 1e3) / 1e9, unit="GPop/s", ms_per_step=sum(ms) / steps,
                     scaling="weak",
-                    config={"workload": "beagle-4096x100k: paper shapes, 1% invalid targets, M = 1000",
+                    config={"workload": f"beagle-4096x100k{'-table1' if nun == 12 else ''}: paper shapes, "
+                                        "1% invalid targets, M = 1000",
                             "step": "sr_eval_score(R4) + sr_select_tournament_max(k=4) + sr_vary",
                             "l2": "flushed between timed generations"},
                     r4_eval_gpops=n_cur / (t_r4 / 1e3) / 1e9, p2p_eval_gpops=n_cur / (t_p2p / 1e3) / 1e9,

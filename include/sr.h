@@ -24,6 +24,7 @@
  * Token format (uint8), one byte per program node:
  *     0 ADD  1 SUB  2 MUL  3 DIV (protected)          binary
  *     4 SIN  5 COS  6 EXP (clamped)  7 LOG (protected) 8 SQRT|.|  9 SQ   unary
+ *    10 INV (1/x, protected)  11 TAN  12 ASIN  13 ACOS  14 ATAN  15 TANH  unary
  *     16 + j   variable x_j   (j < nvars <= 16)
  *     32 + k   constant c_k   (k < K <= 16)
  *   any other byte is invalid.  A binary op pops b, then a, and pushes a op b
@@ -34,7 +35,11 @@
  *     SQRT x    = sqrt(|x|)
  *     EXP x     = exp(min(max(x, -80), 80))
  *     SQ x      = x * x
- *   NaN operands propagate through every operator.  Evaluation is FP32.
+ *     INV x     = 1 DIV x
+ *     TAN, ASIN, ACOS, ATAN, TANH as the FP32 math library computes them;
+ *     ASIN / ACOS outside [-1, 1] give NaN (a non-real result, Sec. 2.1.5)
+ *   Tokens 0-15 are the operator set of Table 1.  NaN operands propagate
+ *   through every operator.  Evaluation is FP32.
  *
  * Program layout: programs [P][Lmax] bytes (row p = program p, bytes past
  * lengths[p] are ignored), lengths [P] int32, consts [P][K] float.
@@ -282,6 +287,7 @@ typedef struct {
   float p_const;    /* constant mutation: c_k += (u - 1/2) * const_delta     */
   float const_delta;
   int max_subtree;  /* generated subtrees have 1..max_subtree tokens         */
+  int unary_ops;    /* unary operators drawn: 6 (tokens 4-9) or 12 (4-15)  */
 } sr_var_cfg;
 
 /*
@@ -296,14 +302,16 @@ typedef struct {
  *     A's; slot k takes B's value when k is read inside the inserted B
  *     subtree and nowhere in the kept parts of A.  Otherwise child = A.
  *  2. point mutation when u_point < p_point: Philox(0, i, 5, gen): position
- *     [0, len); binary -> [0,4), unary -> 4 + [0,6), terminal -> [0, nvars+K)
+ *     [0, len); binary -> [0,4), unary -> 4 + [0,unary_ops), terminal ->
+ *     [0, nvars+K)
  *     (variables first, then constants).
  *  3. subtree mutation when u_sub < p_subtree: Philox(0, i, 6, gen): position
  *     t in [0, len), size n = 1 + [0, max_subtree); the subtree rooted at t
  *     becomes a random program of n tokens whose token q uses
  *     Philox(q, i, 7, gen) (word 0 picks the class among those allowed --
  *     terminal if d <= r-1, unary if 1 <= d <= r, binary if 2 <= d <= r+1,
- *     for depth d and r tokens left -- word 1 the token in the class); skipped
+ *     for depth d and r tokens left -- word 1 the token in the class: binary
+ *     [0, 4), unary 4 + [0, unary_ops), terminal as for point mutation); skipped
  *     when the result would exceed Lmax.
  *  4. constant mutation when u_const < p_const and K > 0: Philox(0, i, 8,
  *     gen): slot [0, K), u = word 1 in [0, 1);
@@ -339,10 +347,11 @@ sr_status sr_set_generation_source(sr_ctx *ctx, const uint64_t *gen_dev);
  * constant k = fl32(cmin + fl32(u * fl32(cmax - cmin))) with u from word 0 of
  * Philox(k, i, 10, stream).  Rows are zero past their length.
  *   prog device uint8 [P][Lmax], len device int32 [P], c device float [P][K]
- *   1 <= Lmin <= Lmax <= SR_MAX_LMAX.   Errors: SR_EINVAL.
+ *   1 <= Lmin <= Lmax <= SR_MAX_LMAX;  unary_ops 6 or 12 (as in sr_var_cfg).
+ * Errors: SR_EINVAL.
  */
 sr_status sr_random_programs(sr_ctx *ctx, uint8_t *prog, int32_t *len, float *c,
-                             int P, int Lmin, int Lmax, int K, int nvars,
+                             int P, int Lmin, int Lmax, int K, int nvars, int unary_ops,
                              float cmin, float cmax, uint64_t seed,
                              uint64_t stream);
 

@@ -80,8 +80,9 @@ def _load():
     lib.or_score_r4.restype = f64
     lib.or_eval_score.argtypes = [P, P, P, i32, i32, i32, P, i64, P, i32, i64, i32, i32, P, P, P, i32]
     lib.or_p2p_range.argtypes = [P, P, P, i32, i32, i32, P, i64, P, i32, i64, f64, i32, P, P, P, i32]
-    lib.or_random_programs.argtypes = [P, P, P, i32, i32, i32, i32, i32, f32, f32, u64, u64]
-    lib.or_vary.argtypes = [P, P, P, P, P, P, P, i32, i32, i32, i32, f32, f32, f32, f32, f32, i32, u64, u64]
+    lib.or_random_programs.argtypes = [P, P, P, i32, i32, i32, i32, i32, i32, f32, f32, u64, u64]
+    lib.or_vary.argtypes = [P, P, P, P, P, P, P, i32, i32, i32, i32, f32, f32, f32, f32, f32, i32, i32, u64,
+                            u64]
     _lib = lib
     return lib
 
@@ -281,17 +282,17 @@ def tournament(fitness, k: int, seed: int, gen: int) -> np.ndarray:
     return out
 
 
-def random_programs(P, Lmin, Lmax, K, nvars, cmin, cmax, seed, stream):
+def random_programs(P, Lmin, Lmax, K, nvars, cmin, cmax, seed, stream, unary_ops=6):
     prog = np.empty((P, Lmax), np.uint8)
     lens = np.empty(P, np.int32)
     cons = np.empty((P, max(K, 0)), np.float32)
-    _load().or_random_programs(_ptr(prog), _ptr(lens), _ptr(cons), P, Lmin, Lmax, K, nvars,
+    _load().or_random_programs(_ptr(prog), _ptr(lens), _ptr(cons), P, Lmin, Lmax, K, nvars, unary_ops,
                                cmin, cmax, seed, stream)
     return prog, lens, cons
 
 
 def vary(programs, lengths, consts, parents, K, nvars, p_cross=0.9, p_point=0.1,
-         p_subtree=0.05, p_const=0.1, const_delta=1.0, max_subtree=8, seed=0, gen=0):
+         p_subtree=0.05, p_const=0.1, const_delta=1.0, max_subtree=8, seed=0, gen=0, unary_ops=6):
     prog = _c(programs, np.uint8)
     P, Lmax = prog.shape
     lens = _c(lengths, np.int32)
@@ -302,7 +303,7 @@ def vary(programs, lengths, consts, parents, K, nvars, p_cross=0.9, p_point=0.1,
     co = np.empty_like(cons)
     _load().or_vary(_ptr(prog), _ptr(lens), _ptr(cons), _ptr(par), _ptr(po), _ptr(lo), _ptr(co),
                     P, Lmax, K, nvars, p_cross, p_point, p_subtree, p_const, const_delta, max_subtree,
-                    seed, gen)
+                    unary_ops, seed, gen)
     return po, lo, co
 
 

@@ -55,7 +55,9 @@
 /* ---- token encoding (own copy of the documented uint8 format) ---------- */
 enum {
   TK_ADD = 0, TK_SUB = 1, TK_MUL = 2, TK_DIV = 3,
-  TK_SIN = 4, TK_COS = 5, TK_EXP = 6, TK_LOG = 7, TK_SQRT = 8, TK_SQ = 9
+  TK_SIN = 4, TK_COS = 5, TK_EXP = 6, TK_LOG = 7, TK_SQRT = 8, TK_SQ = 9,
+  /* the rest of the operator set of Table 1 */
+  TK_INV = 10, TK_TAN = 11, TK_ASIN = 12, TK_ACOS = 13, TK_ATAN = 14, TK_TANH = 15
 };
 #define TK_VAR0 16
 #define TK_CONST0 32
@@ -80,7 +82,7 @@ enum { KIND_MSE = 0, KIND_CORR = 1 };
 
 /* ---- token classes ----------------------------------------------------- */
 static int is_binary(int t) { return t >= TK_ADD && t <= TK_DIV; }
-static int is_unary(int t) { return t >= TK_SIN && t <= TK_SQ; }
+static int is_unary(int t) { return t >= TK_SIN && t <= TK_TANH; }
 static int is_var(int t) { return t >= TK_VAR0 && t < TK_VAR0 + TK_NSLOTS; }
 static int is_const(int t) { return t >= TK_CONST0 && t < TK_CONST0 + TK_NSLOTS; }
 
@@ -167,7 +169,16 @@ static double apply_unary(int t, double x) {
     case TK_EXP: return op_exp(x);
     case TK_LOG: return op_log(x);
     case TK_SQRT: return sqrt(fabs(x));
-    default: return x * x;
+    case TK_SQ: return x * x;
+    /* Table 1's other operators: 1/x protected like division; asin and acos
+     * outside [-1, 1] are not real (NaN), as the paper's NaN-aware fitness
+     * expects (Sec. 2.1.5) */
+    case TK_INV: return op_div(1.0, x);
+    case TK_TAN: return tan(x);
+    case TK_ASIN: return asin(x);
+    case TK_ACOS: return acos(x);
+    case TK_ATAN: return atan(x);
+    default: return tanh(x);
   }
 }
 
@@ -196,7 +207,8 @@ static double eval_case(const uint8_t *tok, int len, const double *c,
 /*
  * Every FP32 operator output is within a relative u of the exact operator
  * applied to its FP32 operands (u = 2^-22 covers correctly rounded arithmetic
- * and library functions accurate to 2 ulp), plus 2^-149 absolute for
+ * and library functions accurate to 2 ulp; tan, asin, acos, atan and tanh
+ * are allowed 4u), plus 2^-149 absolute for
  * subnormal results.  Inputs and constants are exact.  Evaluating the program
  * on intervals -- each operator's exact range over its operand intervals,
  * widened by that rounding -- therefore encloses the FP32 result of every
@@ -293,10 +305,28 @@ static ival iv_unary(int v, ival a) {
       ival m = iv_abs(a);
       return iv(sqrt(m.lo), sqrt(m.hi));
     }
-    default: {
+    case TK_SQ: {
       ival m = iv_abs(a);
       return iv(m.lo * m.lo, m.hi * m.hi);
     }
+    case TK_INV: return iv_div(iv(1.0, 1.0), a);
+    case TK_TAN: {
+      /* increasing between the poles pi/2 + k pi; a pole inside (or within
+       * FP64 reach of an end) makes the range unbounded */
+      const double pi = 3.141592653589793, half_pi = 1.5707963267948966;
+      double k = ceil((a.lo - half_pi) / pi - 1e-12);
+      if (!(a.hi - a.lo < pi) || half_pi + k * pi <= a.hi + 1e-12 * (1.0 + fabs(a.hi)))
+        return iv(-INFINITY, INFINITY);
+      return iv(tan(a.lo), tan(a.hi));
+    }
+    case TK_ASIN:
+    case TK_ACOS: {
+      /* outside [-1, 1] the result may be NaN */
+      if (!(a.lo >= -1.0 && a.hi <= 1.0)) return iv(NAN, NAN);
+      return v == TK_ASIN ? iv(asin(a.lo), asin(a.hi)) : iv(acos(a.hi), acos(a.lo));
+    }
+    case TK_ATAN: return iv(atan(a.lo), atan(a.hi));
+    default: return iv(tanh(a.lo), tanh(a.hi));
   }
 }
 
@@ -335,7 +365,9 @@ static double case_interval(const uint8_t *tok, int len, const double *c,
       val[sp - 1] = apply_unary(v, val[sp - 1]);
       r = iv_unary(v, box[sp - 1]);
     }
-    r = widen(r, u);
+    /* tan and the inverse trigonometric / hyperbolic routines get a wider
+     * allowance (8 ulp) than the other library functions */
+    r = widen(r, (v >= TK_TAN && v <= TK_TANH) ? 4.0 * u : u);
     if (!(r.lo >= -FLT_MAX && r.hi <= FLT_MAX)) cf |= CF_RANGE; /* also NaN */
     box[sp - 1] = r;
   }
@@ -806,8 +838,9 @@ void or_p2p_range(const uint8_t *programs, const int32_t *lengths, const float *
  * rounding error of any evaluation order of the chain rule -- including one
  * whose contributions cancel exactly in exact arithmetic, as for c / c.
  * *kink receives the smallest distance, over all cases, of a branch
- * argument to its switch point (|b| - 1e-3 for division, |x| - 1e-3 for
- * log, |x| for sqrt|x|, |x| - 80 for exp).
+ * argument to its switch point (|b| - 1e-3 for division and 1/x, |x| - 1e-3
+ * for log, |x| for sqrt|x|, |x| - 80 for exp) or of an argument to a point
+ * where the derivative explodes (|cos x| for tan, 1 - |x| for asin and acos).
  */
 void or_grad_one(const uint8_t *tok, int len, const double *c, int K,
                  const double *X, long ldx, const double *y, long N,
@@ -887,7 +920,36 @@ void or_grad_one(const uint8_t *tok, int len, const double *c, int K,
             r = sqrt(fabs(x));
             dx = (x == 0.0) ? 0.0 : (x > 0.0 ? 0.5 / r : -0.5 / r);
             break;
-          default: r = x * x; dx = 2.0 * x; break;
+          case TK_SQ: r = x * x; dx = 2.0 * x; break;
+          case TK_INV:
+            if (fabs(fabs(x) - PROTECT_EPS) < kmin) kmin = fabs(fabs(x) - PROTECT_EPS);
+            if (fabs(x) <= PROTECT_EPS) {
+              r = 1.0; dx = 0.0;
+            } else {
+              r = 1.0 / x; dx = -1.0 / (x * x);
+            }
+            break;
+          case TK_TAN:
+            /* the derivative explodes at the poles: distance |cos x| */
+            if (fabs(cos(x)) < kmin) kmin = fabs(cos(x));
+            r = tan(x); dx = 1.0 + r * r;
+            break;
+          case TK_ASIN:
+          case TK_ACOS:
+            /* and at the ends of the domain: distance 1 - |x| */
+            if (fabs(1.0 - fabs(x)) < kmin) kmin = fabs(1.0 - fabs(x));
+            r = v == TK_ASIN ? asin(x) : acos(x);
+            /* 1 - x^2 as (1 - x)(1 + x): exact factors near |x| = 1 */
+            dx = (v == TK_ASIN ? 1.0 : -1.0) / sqrt((1.0 - x) * (1.0 + x));
+            break;
+          case TK_ATAN: r = atan(x); dx = 1.0 / (1.0 + x * x); break;
+          default: {
+            /* d tanh / dx = sech^2 x, evaluated directly (1 - tanh^2 cancels) */
+            double ch = cosh(x);
+            r = tanh(x);
+            dx = 1.0 / (ch * ch);
+            break;
+          }
         }
         for (int k = 0; k < K; ++k) tx[k] = dx * tx[k];
         for (int k = 0; k < K; ++k) tab[(sp - 1) * K + k] *= fabs(dx);
@@ -1091,7 +1153,7 @@ static int token_effect(int v) {
  * 2 <= d <= r + 1.  Word w0 picks the class among the allowed ones, word w1
  * the token inside the class (terminal: [0, nvars + K), variables first).
  */
-static int gen_token(int d, int r, int nvars, int K, uint32_t w0, uint32_t w1) {
+static int gen_token(int d, int r, int nvars, int K, int nun, uint32_t w0, uint32_t w1) {
   int allowed[3], na = 0;
   if (d <= r - 1) allowed[na++] = 0;
   if (d >= 1 && d <= r) allowed[na++] = 1;
@@ -1101,7 +1163,7 @@ static int gen_token(int d, int r, int nvars, int K, uint32_t w0, uint32_t w1) {
     int q = (int)below(w1, (uint32_t)(nvars + K));
     return q < nvars ? TK_VAR0 + q : TK_CONST0 + (q - nvars);
   }
-  if (cls == 1) return TK_SIN + (int)below(w1, 6u);
+  if (cls == 1) return TK_SIN + (int)below(w1, (uint32_t)nun);
   return TK_ADD + (int)below(w1, 4u);
 }
 
@@ -1112,8 +1174,8 @@ static int gen_token(int d, int r, int nvars, int K, uint32_t w0, uint32_t w1) {
  * of Philox(k, i, 10, stream).  Bytes past L are zero.
  */
 void or_random_programs(uint8_t *prog, int32_t *len, float *c, int P,
-                        int Lmin, int Lmax, int K, int nvars, float cmin,
-                        float cmax, uint64_t seed, uint64_t stream) {
+                        int Lmin, int Lmax, int K, int nvars, int unary_ops,
+                        float cmin, float cmax, uint64_t seed, uint64_t stream) {
   volatile float span = cmax - cmin;
   for (int i = 0; i < P; ++i) {
     uint32_t w[4];
@@ -1124,7 +1186,7 @@ void or_random_programs(uint8_t *prog, int32_t *len, float *c, int P,
     int d = 0;
     for (int t = 0; t < L; ++t) {
       draw4(seed, (uint32_t)(1 + t), (uint32_t)i, PU_INIT, stream, w);
-      int v = gen_token(d, L - t, nvars, K, w[0], w[1]);
+      int v = gen_token(d, L - t, nvars, K, unary_ops, w[0], w[1]);
       out[t] = (uint8_t)v;
       d += token_effect(v);
     }
@@ -1177,7 +1239,7 @@ void or_vary(const uint8_t *prog_in, const int32_t *len_in, const float *c_in,
              const int32_t *parents, uint8_t *prog_out, int32_t *len_out,
              float *c_out, int P, int Lmax, int K, int nvars, float p_cross,
              float p_point, float p_subtree, float p_const, float delta,
-             int max_subtree, uint64_t seed, uint64_t gen) {
+             int max_subtree, int unary_ops, uint64_t seed, uint64_t gen) {
   uint8_t *buf = (uint8_t *)malloc((size_t)Lmax + (size_t)max_subtree + 8);
   uint8_t *tmp = (uint8_t *)malloc((size_t)Lmax + (size_t)max_subtree + 8);
   for (int i = 0; i < P; ++i) {
@@ -1222,7 +1284,7 @@ void or_vary(const uint8_t *prog_in, const int32_t *len_in, const float *c_in,
       if (is_binary(v)) {
         buf[t] = (uint8_t)(TK_ADD + (int)below(w[1], 4u));
       } else if (is_unary(v)) {
-        buf[t] = (uint8_t)(TK_SIN + (int)below(w[1], 6u));
+        buf[t] = (uint8_t)(TK_SIN + (int)below(w[1], (uint32_t)unary_ops));
       } else {
         int q = (int)below(w[1], (uint32_t)(nvars + K));
         buf[t] = (uint8_t)(q < nvars ? TK_VAR0 + q : TK_CONST0 + (q - nvars));
@@ -1241,7 +1303,7 @@ void or_vary(const uint8_t *prog_in, const int32_t *len_in, const float *c_in,
         for (int j = 0; j < n; ++j) {
           uint32_t g[4];
           draw4(seed, (uint32_t)j, (uint32_t)i, PU_SUBGEN, gen, g);
-          int v = gen_token(d, n - j, nvars, K, g[0], g[1]);
+          int v = gen_token(d, n - j, nvars, K, unary_ops, g[0], g[1]);
           tmp[q++] = (uint8_t)v;
           d += token_effect(v);
         }

@@ -35,7 +35,8 @@ class VarCfg(ctypes.Structure):
     """sr_var_cfg (include/sr.h)."""
     _fields_ = [("p_cross", ctypes.c_float), ("p_point", ctypes.c_float),
                 ("p_subtree", ctypes.c_float), ("p_const", ctypes.c_float),
-                ("const_delta", ctypes.c_float), ("max_subtree", ctypes.c_int)]
+                ("const_delta", ctypes.c_float), ("max_subtree", ctypes.c_int),
+                ("unary_ops", ctypes.c_int)]
 
 
 class Problem(ctypes.Structure):
@@ -58,8 +59,12 @@ def adam_cfg(lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8):
     return AdamCfg(lr, beta1, beta2, eps)
 
 
-def var_cfg(p_cross=0.9, p_point=0.1, p_subtree=0.05, p_const=0.1, const_delta=1.0, max_subtree=8):
-    return VarCfg(p_cross, p_point, p_subtree, p_const, const_delta, max_subtree)
+UNARY_BASE, UNARY_ALL = 6, 12  # sin cos exp log sqrt sq; plus 1/x tan asin acos atan tanh (Table 1)
+
+
+def var_cfg(p_cross=0.9, p_point=0.1, p_subtree=0.05, p_const=0.1, const_delta=1.0, max_subtree=8,
+            unary_ops=UNARY_BASE):
+    return VarCfg(p_cross, p_point, p_subtree, p_const, const_delta, max_subtree, unary_ops)
 
 
 class SRError(RuntimeError):
@@ -96,7 +101,7 @@ def lib() -> ctypes.CDLL:
     L.sr_eval_score.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp, vp, i32, i32, i32, i32, i32, vp, vp, vp]
     L.sr_vary.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, ctypes.POINTER(VarCfg),
                           u64, u64]
-    L.sr_random_programs.argtypes = [vp, vp, vp, vp, i32, i32, i32, i32, i32, f32, f32, u64, u64]
+    L.sr_random_programs.argtypes = [vp, vp, vp, vp, i32, i32, i32, i32, i32, i32, f32, f32, u64, u64]
     L.sr_eval_grad.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp, vp, i32, i32, i32, vp, vp, vp]
     L.sr_adam_step.argtypes = [vp, vp, vp, vp, vp, i32, i32, ctypes.POINTER(AdamCfg)]
     L.sr_eval_batched.argtypes = [vp, ctypes.POINTER(Problem), i32]
@@ -321,14 +326,15 @@ def sr_vary(ctx: Context, programs, lengths, consts, parents, nvars: int, cfg: V
 
 
 def sr_random_programs(ctx: Context, P: int, Lmin: int, Lmax: int, K: int, nvars: int, cmin: float,
-                       cmax: float, seed: int, stream: int, device="cuda", out=None):
+                       cmax: float, seed: int, stream: int, device="cuda", out=None,
+                       unary_ops: int = UNARY_BASE):
     if out is None:
         out = (torch.empty((P, Lmax), dtype=torch.uint8, device=device),
                torch.empty(P, dtype=torch.int32, device=device),
                torch.empty((P, K), dtype=torch.float32, device=device))
     prog, lens, c = out
     _check(ctx, lib().sr_random_programs(ctx.handle, _ptr(prog), _ptr(lens), _ptr(c) if K else None, P,
-                                         Lmin, Lmax, K, nvars, cmin, cmax, seed, stream))
+                                         Lmin, Lmax, K, nvars, unary_ops, cmin, cmax, seed, stream))
     return prog, lens, c
 
 

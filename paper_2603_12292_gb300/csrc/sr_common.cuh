@@ -30,6 +30,10 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int TOK_ADD = 0, TOK_SUB = 1, TOK_MUL = 2, TOK_DIV = 3;
 constexpr int TOK_SIN = 4, TOK_COS = 5, TOK_EXP = 6, TOK_LOG = 7, TOK_SQRT = 8,
               TOK_SQ = 9;
+// the rest of the operator set of Table 1
+constexpr int TOK_INV = 10, TOK_TAN = 11, TOK_ASIN = 12, TOK_ACOS = 13, TOK_ATAN = 14,
+              TOK_TANH = 15;
+constexpr int UNARY_BASE = 6, UNARY_ALL = 12;  // operator sets of the generators
 constexpr int TOK_VAR0 = 16, TOK_CONST0 = 32, TOK_NSLOTS = 16;
 
 // token classes used by the decoders
@@ -38,7 +42,7 @@ constexpr int CLS_VAR = 0, CLS_CONST = 1, CLS_UNARY = 2, CLS_BINARY = 3,
 
 __host__ __device__ __forceinline__ int tok_class(int v) {
   if (v <= TOK_DIV) return CLS_BINARY;
-  if (v <= TOK_SQ) return CLS_UNARY;
+  if (v <= TOK_TANH) return CLS_UNARY;
   if (v >= TOK_VAR0 && v < TOK_VAR0 + TOK_NSLOTS) return CLS_VAR;
   if (v >= TOK_CONST0 && v < TOK_CONST0 + TOK_NSLOTS) return CLS_CONST;
   return CLS_BAD;

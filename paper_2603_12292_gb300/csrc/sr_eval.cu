@@ -70,7 +70,7 @@ struct EvalParams {
   int16_t *s_start;        // decode scratch [P][Lmax]: first token of each subtree
   uint8_t *s_need;         // decode scratch [P][Lmax]: stack need of each subtree
   int16_t *s_task;         // decode scratch [P][Lmax]: work stack
-  unsigned long long *queue;
+  unsigned long long *queue;  // [0] work counter, [1] work counter of the EXT pass, [2] EXT programs
   float *yhat;             // predict: [P][ldy]
   long long ldy;
   int warp_bytes;          // shared memory per warp
@@ -113,6 +113,7 @@ __device__ __forceinline__ DecodeArgs decode_args(const EvalParams &p) {
   a.s_start = p.s_start;
   a.s_need = p.s_need;
   a.s_task = p.s_task;
+  a.ext_count = p.queue ? p.queue + 2 : nullptr;
   return a;
 }
 
@@ -172,6 +173,12 @@ struct FCos { __device__ __forceinline__ float operator()(float x) const { retur
 struct FExp { __device__ __forceinline__ float operator()(float x) const { return op_exp(x); } };
 struct FLog { __device__ __forceinline__ float operator()(float x) const { return op_log(x); } };
 struct FSqrt { __device__ __forceinline__ float operator()(float x) const { return f_sqrt(x); } };
+struct FInv { __device__ __forceinline__ float operator()(float x) const { return op_inv(x); } };
+struct FTan { __device__ __forceinline__ float operator()(float x) const { return f_tan(x); } };
+struct FAsin { __device__ __forceinline__ float operator()(float x) const { return f_asin(x); } };
+struct FAcos { __device__ __forceinline__ float operator()(float x) const { return f_acos(x); } };
+struct FAtan { __device__ __forceinline__ float operator()(float x) const { return f_atan(x); } };
+struct FTanh { __device__ __forceinline__ float operator()(float x) const { return f_tanh(x); } };
 
 template <typename F>
 __device__ __forceinline__ V8 map8_unrolled(V8 v, F f) {
@@ -185,6 +192,18 @@ __device__ __noinline__ V8 cos8(V8 v) { return map8_unrolled(v, FCos()); }
 __device__ __noinline__ V8 exp8(V8 v) { return map8_unrolled(v, FExp()); }
 __device__ __noinline__ V8 log8(V8 v) { return map8_unrolled(v, FLog()); }
 __device__ __noinline__ V8 sqrt8(V8 v) { return map8_unrolled(v, FSqrt()); }
+// The rest of Table 1 goes through one out-of-line entry, so the hot
+// dispatch switch keeps the size it has for the base operators.
+__device__ __noinline__ V8 ext8(uint32_t op, V8 v) {
+  switch (op) {
+    case OP_INV: return map8_unrolled(v, FInv());
+    case OP_TAN: return map8_unrolled(v, FTan());
+    case OP_ASIN: return map8_unrolled(v, FAsin());
+    case OP_ACOS: return map8_unrolled(v, FAcos());
+    case OP_ATAN: return map8_unrolled(v, FAtan());
+    default: return map8_unrolled(v, FTanh());
+  }
+}
 __device__ __noinline__ V8 div8(V8 a, V8 b) {
   float x[8] = {a.a.x, a.a.y, a.a.z, a.a.w, a.b.x, a.b.y, a.b.z, a.b.w};
   const float y[8] = {b.a.x, b.a.y, b.a.z, b.a.w, b.b.x, b.b.y, b.b.z, b.b.w};
@@ -198,6 +217,7 @@ __device__ __noinline__ V8 div8(V8 a, V8 b) {
 #define LOG8(v) log8(v)
 #define SQRT8(v) sqrt8(v)
 #define DIV8(p, q) div8(p, q)
+#define EXT8(op, v) ext8(op, v)
 #else
 #define SIN8(v) MAP8(f_sin, v)
 #define COS8(v) MAP8(f_cos, v)
@@ -205,11 +225,24 @@ __device__ __noinline__ V8 div8(V8 a, V8 b) {
 #define LOG8(v) MAP8(op_log, v)
 #define SQRT8(v) MAP8(f_sqrt, v)
 #define DIV8(p, q) ZIP8(op_div, p, q)
+__device__ __forceinline__ V8 ext8_inline(uint32_t op, V8 v) {
+  switch (op) {
+    case OP_INV: return MAP8(op_inv, v);
+    case OP_TAN: return MAP8(f_tan, v);
+    case OP_ASIN: return MAP8(f_asin, v);
+    case OP_ACOS: return MAP8(f_acos, v);
+    case OP_ATAN: return MAP8(f_atan, v);
+    default: return MAP8(f_tanh, v);
+  }
+}
+#define EXT8(op, v) ext8_inline(op, v)
 #endif
 
 // Runs the decoded program for this lane's 8 cases.  xa / xb point at the
 // lane's first and second case group in row 0 of X; `stk` at this lane's
 // entry of stack slot 0 in shared memory.
+// EXT: the copy of the loop that also runs 1/x, tan, asin, acos, atan, tanh
+template <bool EXT>
 __device__ __forceinline__ V8 interpret(const uint2 *__restrict__ code, int n, char *stk,
                                         const float *__restrict__ xa, const float *__restrict__ xb) {
   V8 T = splat8(0.f);
@@ -233,6 +266,14 @@ __device__ __forceinline__ V8 interpret(const uint2 *__restrict__ code, int n, c
       case OP_LOG: T = LOG8(T); break;
       case OP_SQRT: T = SQRT8(T); break;
       case OP_SQ: T = MAP8(f_sq, T); break;
+      case OP_INV:
+      case OP_TAN:
+      case OP_ASIN:
+      case OP_ACOS:
+      case OP_ATAN:
+      case OP_TANH:
+        if (EXT) T = EXT8(ins_op(w), T);
+        break;
       case OP_VADD: { const V8 v = ldX8(xa, xb, w.y); T = ZIP8(f_add, T, v); } break;
       case OP_VSUB: { const V8 v = ldX8(xa, xb, w.y); T = ZIP8(f_sub, T, v); } break;
       case OP_VMUL: { const V8 v = ldX8(xa, xb, w.y); T = ZIP8(f_mul, T, v); } break;
@@ -310,7 +351,7 @@ __device__ __forceinline__ WarpSmem warp_smem(unsigned char *smem, int warp, int
 // Evaluates program `prog` of problem p on case chunk `c` with the calling
 // warp.  MODE_BOTH accumulates the sums selected by `want` (bit 0: squared
 // error, bit 1: correlation moments); the other modes ignore `want`.
-template <int MODE>
+template <int MODE, bool EXT>
 __device__ __forceinline__ void eval_item(const EvalParams &p, int c, int prog, const WarpSmem &w,
                                           int lane, int want) {
   const bool do_mse = MODE == MODE_MSE || (MODE == MODE_BOTH && (want & 1));
@@ -324,7 +365,7 @@ __device__ __forceinline__ void eval_item(const EvalParams &p, int c, int prog, 
     }
     return;
   }
-  const int n = p.ncode[prog];
+  const int n = ncode_count(p.ncode[prog]);
   __syncwarp();  // the previous item is done reading the code
   const uint2 *src = p.code + (size_t)prog * p.Lmax;
   for (int i = lane; i < n; i += 32) w.code[i] = src[i];
@@ -342,7 +383,7 @@ __device__ __forceinline__ void eval_item(const EvalParams &p, int c, int prog, 
     const int c0 = base + CPL * lane;
     const int cl = c0 < cend ? c0 : last_group;           // first 4 cases, always readable
     const int cl4 = cl + 4 < cend ? cl + 4 : cl;          // second 4, or a re-read when none valid
-    const V8 T = interpret(w.code, n, stk, p.X + cl, p.X + cl4);
+    const V8 T = interpret<EXT>(w.code, n, stk, p.X + cl, p.X + cl4);
     const float tv[CPL] = {T.a.x, T.a.y, T.a.z, T.a.w, T.b.x, T.b.y, T.b.z, T.b.w};
     bool ok[CPL];
 #pragma unroll
@@ -463,19 +504,27 @@ __device__ __forceinline__ void eval_item(const EvalParams &p, int c, int prog, 
 }
 
 // ---------------------------------------------------------------- single problem
-template <int MODE>
+// Two passes over the work items: EXT = false takes the programs of the base
+// operators (and the invalid ones), EXT = true those that use 1/x, tan,
+// asin, acos, atan or tanh; it returns at once when the decoder counted
+// none.  Keeping the extended operators out of the first kernel keeps its
+// loop (and its speed) what it is for the base operators.
+template <int MODE, bool EXT>
 __global__ void __launch_bounds__(WARPS * 32) eval_kernel(EvalParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
+  if (EXT && p.queue[2] == 0) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const WarpSmem w = warp_smem(smem, warp, p.warp_bytes);
+  unsigned long long *q = p.queue + (EXT ? 1 : 0);
   for (;;) {
     unsigned long long item = 0;
-    if (lane == 0) item = atomicAdd(p.queue, 1ull);
+    if (lane == 0) item = atomicAdd(q, 1ull);
     item = __shfl_sync(FULL, item, 0);
     if ((long long)item >= p.total_items) break;
     const int c = (int)(item / (unsigned long long)p.P);
     const int prog = (int)(item % (unsigned long long)p.P);
-    eval_item<MODE>(p, c, prog, w, lane, 3);
+    if (ncode_ext(p.ncode[prog]) != EXT) continue;
+    eval_item<MODE, EXT>(p, c, prog, w, lane, 3);
   }
 }
 
@@ -554,19 +603,25 @@ __global__ void decode_batched_kernel(const __grid_constant__ BatchParams b) {
     if (b.prob[mid].prog_begin <= g) lo = mid;
     else hi = mid - 1;
   }
-  const EvalParams p = view(b.prob[lo]);
+  EvalParams p = view(b.prob[lo]);
+  p.queue = b.queue;
   decode_one(decode_args(p), g - b.prob[lo].prog_begin);
 }
 
 // Work items of every problem come from one atomic counter: problem q owns
 // items [item_begin_q, item_begin_q + P_q * nchunks_q), chunk-major inside.
+// EXT as for eval_kernel (the extended programs of every problem in a
+// second launch).
+template <bool EXT>
 __global__ void __launch_bounds__(WARPS * 32) eval_batched_kernel(const __grid_constant__ BatchParams b) {
   extern __shared__ __align__(16) unsigned char smem[];
+  if (EXT && b.queue[2] == 0) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const WarpSmem w = warp_smem(smem, warp, b.warp_bytes);
+  unsigned long long *qc = b.queue + (EXT ? 1 : 0);
   for (;;) {
     unsigned long long item = 0;
-    if (lane == 0) item = atomicAdd(b.queue, 1ull);
+    if (lane == 0) item = atomicAdd(qc, 1ull);
     item = __shfl_sync(FULL, item, 0);
     if ((long long)item >= b.total_items) break;
     int lo = 0, hi = b.nprob - 1;
@@ -580,8 +635,9 @@ __global__ void __launch_bounds__(WARPS * 32) eval_batched_kernel(const __grid_c
     const long long local = (long long)item - q.item_begin;
     const int c = (int)(local / q.P);
     const int prog = (int)(local % q.P);
+    if (ncode_ext(q.ncode[prog]) != EXT) continue;
     const int want = q.mode == MODE_MSE ? 1 : (q.mode == MODE_CORR ? 2 : 3);
-    eval_item<MODE_BOTH>(p, c, prog, w, lane, want);
+    eval_item<MODE_BOTH, EXT>(p, c, prog, w, lane, want);
   }
 }
 
@@ -846,31 +902,46 @@ __global__ void finalize_batched_kernel(const __grid_constant__ BatchParams b) {
 }
 
 // ---------------------------------------------------------------- host side
-template <int MODE>
+template <int MODE, bool EXT>
 sr_status occupancy_grid(sr_ctx *ctx, int smem, int *grid) {
   static int configured = 0;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(eval_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(eval_kernel<MODE, EXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          227 * 1024);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute(eval_kernel)");
     configured = 1;
   }
   int nb = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_kernel<MODE>, WARPS * 32, smem);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_kernel<MODE, EXT>, WARPS * 32, smem);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   if (nb < 1) return fail(ctx, SR_EINVAL, "Lmax too large for shared memory");
   *grid = nb * ctx->num_sms;
   return SR_OK;
 }
 
-sr_status grid_for(sr_ctx *ctx, int mode, int smem, int *grid) {
+template <bool EXT>
+sr_status grid_for_t(sr_ctx *ctx, int mode, int smem, int *grid) {
   switch (mode) {
-    case MODE_PREDICT: return occupancy_grid<MODE_PREDICT>(ctx, smem, grid);
-    case MODE_MSE: return occupancy_grid<MODE_MSE>(ctx, smem, grid);
-    case MODE_CORR: return occupancy_grid<MODE_CORR>(ctx, smem, grid);
-    case MODE_R4: return occupancy_grid<MODE_R4>(ctx, smem, grid);
-    case MODE_P2P: return occupancy_grid<MODE_P2P>(ctx, smem, grid);
-    default: return occupancy_grid<MODE_BOTH>(ctx, smem, grid);
+    case MODE_PREDICT: return occupancy_grid<MODE_PREDICT, EXT>(ctx, smem, grid);
+    case MODE_MSE: return occupancy_grid<MODE_MSE, EXT>(ctx, smem, grid);
+    case MODE_CORR: return occupancy_grid<MODE_CORR, EXT>(ctx, smem, grid);
+    case MODE_R4: return occupancy_grid<MODE_R4, EXT>(ctx, smem, grid);
+    case MODE_P2P: return occupancy_grid<MODE_P2P, EXT>(ctx, smem, grid);
+    default: return occupancy_grid<MODE_BOTH, EXT>(ctx, smem, grid);
+  }
+}
+
+sr_status grid_for(sr_ctx *ctx, int mode, int smem, int *grid) { return grid_for_t<false>(ctx, mode, smem, grid); }
+
+template <bool EXT>
+void launch_mode(int mode, int grid, int smem, cudaStream_t s, const EvalParams &ep) {
+  switch (mode) {
+    case MODE_PREDICT: eval_kernel<MODE_PREDICT, EXT><<<grid, WARPS * 32, smem, s>>>(ep); break;
+    case MODE_MSE: eval_kernel<MODE_MSE, EXT><<<grid, WARPS * 32, smem, s>>>(ep); break;
+    case MODE_CORR: eval_kernel<MODE_CORR, EXT><<<grid, WARPS * 32, smem, s>>>(ep); break;
+    case MODE_R4: eval_kernel<MODE_R4, EXT><<<grid, WARPS * 32, smem, s>>>(ep); break;
+    case MODE_P2P: eval_kernel<MODE_P2P, EXT><<<grid, WARPS * 32, smem, s>>>(ep); break;
+    default: eval_kernel<MODE_BOTH, EXT><<<grid, WARPS * 32, smem, s>>>(ep); break;
   }
 }
 
@@ -977,7 +1048,10 @@ sr_status launch_eval(sr_ctx *ctx, int mode, const uint8_t *programs, const int3
   ep.warp_bytes = warp_smem_bytes(Lmax);
   ep.score_M = M;
 
-  SR_CHECK_CUDA(ctx, cudaMemsetAsync(ep.queue, 0, sizeof(unsigned long long), s));
+  int grid_ext = 0;
+  st = grid_for_t<true>(ctx, mode, pl.smem, &grid_ext);
+  if (st != SR_OK) return st;
+  SR_CHECK_CUDA(ctx, cudaMemsetAsync(ep.queue, 0, 3 * sizeof(unsigned long long), s));
   // one warp per block spreads the serial per-program decode over the SMs
   decode_kernel<<<(P + 31) / 32, 32, 0, s>>>(ep);
   ctx->launches += 1;
@@ -990,16 +1064,10 @@ sr_status launch_eval(sr_ctx *ctx, int mode, const uint8_t *programs, const int3
                                                       const_cast<float *>(ep.yc), ych);
     ctx->launches += 2;
   }
-  switch (mode) {
-    case MODE_PREDICT: eval_kernel<MODE_PREDICT><<<pl.grid, WARPS * 32, pl.smem, s>>>(ep); break;
-    case MODE_MSE: eval_kernel<MODE_MSE><<<pl.grid, WARPS * 32, pl.smem, s>>>(ep); break;
-    case MODE_CORR: eval_kernel<MODE_CORR><<<pl.grid, WARPS * 32, pl.smem, s>>>(ep); break;
-    case MODE_R4: eval_kernel<MODE_R4><<<pl.grid, WARPS * 32, pl.smem, s>>>(ep); break;
-    case MODE_P2P: eval_kernel<MODE_P2P><<<pl.grid, WARPS * 32, pl.smem, s>>>(ep); break;
-    default: eval_kernel<MODE_BOTH><<<pl.grid, WARPS * 32, pl.smem, s>>>(ep); break;
-  }
+  launch_mode<false>(mode, pl.grid, pl.smem, s, ep);
+  launch_mode<true>(mode, grid_ext, pl.smem, s, ep);
   SR_CHECK_CUDA(ctx, cudaGetLastError());
-  ctx->launches += 1;
+  ctx->launches += 2;
   if (mode != MODE_PREDICT) {
     FinalParams fp{ep.partials, ep.flags, ych, P, N, pl.chunk, pl.nchunks, mode, fitness, M, counts};
     finalize_kernel<<<(P + 255) / 256, 256, 0, s>>>(fp);
@@ -1010,16 +1078,17 @@ sr_status launch_eval(sr_ctx *ctx, int mode, const uint8_t *programs, const int3
 }
 
 // ---------------------------------------------------------------- batched host side
+template <bool EXT>
 sr_status batched_grid(sr_ctx *ctx, int smem, int *grid) {
   static int configured = 0;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(eval_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(eval_batched_kernel<EXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          227 * 1024);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute(eval_batched_kernel)");
     configured = 1;
   }
   int nb = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_batched_kernel, WARPS * 32, smem);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_batched_kernel<EXT>, WARPS * 32, smem);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   if (nb < 1) return fail(ctx, SR_EINVAL, "Lmax too large for shared memory");
   *grid = nb * ctx->num_sms;
@@ -1044,8 +1113,10 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
     work += (double)q.P * (double)q.N;
   }
   const int smem = WARPS * warp_smem_bytes(maxL);
-  int grid = 0;
-  sr_status st = batched_grid(ctx, smem, &grid);
+  int grid = 0, grid_ext = 0;
+  sr_status st = batched_grid<false>(ctx, smem, &grid);
+  if (st != SR_OK) return st;
+  st = batched_grid<true>(ctx, smem, &grid_ext);
   if (st != SR_OK) return st;
   const long long warps = (long long)grid * WARPS;
   const double want = (double)warps * TARGET_ITEMS_PER_WARP;
@@ -1167,7 +1238,7 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
     group_bytes(g0, g1, &b);
     int corr_blocks = 0;
     for (int r = 0; r < b.ncorr; ++r) corr_blocks += b.prob[b.corr_list[r]].nchunks;
-    SR_CHECK_CUDA(ctx, cudaMemsetAsync(b.queue, 0, sizeof(unsigned long long), s));
+    SR_CHECK_CUDA(ctx, cudaMemsetAsync(b.queue, 0, 3 * sizeof(unsigned long long), s));
     decode_batched_kernel<<<(b.total_progs + 127) / 128, 128, 0, s>>>(b);
     ctx->launches += 1;
     if (b.ncorr > 0) {
@@ -1175,10 +1246,11 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
       ycenter_batched_kernel<<<corr_blocks, PREP_THREADS, 0, s>>>(b);
       ctx->launches += 2;
     }
-    eval_batched_kernel<<<grid, WARPS * 32, smem, s>>>(b);
+    eval_batched_kernel<false><<<grid, WARPS * 32, smem, s>>>(b);
+    eval_batched_kernel<true><<<grid_ext, WARPS * 32, smem, s>>>(b);
     finalize_batched_kernel<<<b.nprob, 256, 0, s>>>(b);
     SR_CHECK_CUDA(ctx, cudaGetLastError());
-    ctx->launches += 2;
+    ctx->launches += 3;
   }
   return SR_OK;
 }

@@ -77,7 +77,7 @@ __device__ __forceinline__ int effect(int v) { return cls_effect(tok_class(v)); 
 
 // token with depth d before it and r tokens left (this one included):
 // terminal if d <= r-1, unary if 1 <= d <= r, binary if 2 <= d <= r+1
-__device__ __forceinline__ int gen_token(int d, int r, int nvars, int K, uint32_t w0, uint32_t w1) {
+__device__ __forceinline__ int gen_token(int d, int r, int nvars, int K, int nun, uint32_t w0, uint32_t w1) {
   int allowed[3];
   int na = 0;
   if (d <= r - 1) allowed[na++] = 0;
@@ -88,7 +88,7 @@ __device__ __forceinline__ int gen_token(int d, int r, int nvars, int K, uint32_
     const int q = (int)below(w1, (uint32_t)(nvars + K));
     return q < nvars ? TOK_VAR0 + q : TOK_CONST0 + (q - nvars);
   }
-  if (cls == 1) return TOK_SIN + (int)below(w1, 6u);
+  if (cls == 1) return TOK_SIN + (int)below(w1, (uint32_t)nun);
   return TOK_ADD + (int)below(w1, 4u);
 }
 
@@ -213,7 +213,7 @@ __global__ void vary_kernel(VaryParams p) {
     if (cls == CLS_BINARY) {
       v = TOK_ADD + (int)below(w.v[1], 4u);
     } else if (cls == CLS_UNARY) {
-      v = TOK_SIN + (int)below(w.v[1], 6u);
+      v = TOK_SIN + (int)below(w.v[1], (uint32_t)p.cfg.unary_ops);
     } else {
       const int q = (int)below(w.v[1], (uint32_t)(p.nvars + p.K));
       v = q < p.nvars ? TOK_VAR0 + q : TOK_CONST0 + (q - p.nvars);
@@ -238,7 +238,7 @@ __global__ void vary_kernel(VaryParams p) {
       int d = 0;
       for (int q = 0; q < n; ++q) {
         const Word4 g = p.rng.draw((uint32_t)q, (uint32_t)i, PU_SUBGEN);
-        const int v = gen_token(d, n - q, p.nvars, p.K, g.v[0], g.v[1]);
+        const int v = gen_token(d, n - q, p.nvars, p.K, p.cfg.unary_ops, g.v[0], g.v[1]);
         out[s + q] = (uint8_t)v;
         d += effect(v);
       }
@@ -259,7 +259,8 @@ __global__ void vary_kernel(VaryParams p) {
 }
 
 __global__ void random_programs_kernel(uint8_t *prog, int32_t *len, float *c, int P, int Lmin,
-                                       int Lmax, int K, int nvars, float cmin, float cmax, Rng rng) {
+                                       int Lmax, int K, int nvars, int nun, float cmin, float cmax,
+                                       Rng rng) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P) return;
   const Word4 lw = rng.draw(0, (uint32_t)i, PU_INIT);
@@ -268,7 +269,7 @@ __global__ void random_programs_kernel(uint8_t *prog, int32_t *len, float *c, in
   int d = 0;
   for (int t = 0; t < L; ++t) {
     const Word4 w = rng.draw((uint32_t)(1 + t), (uint32_t)i, PU_INIT);
-    const int v = gen_token(d, L - t, nvars, K, w.v[0], w.v[1]);
+    const int v = gen_token(d, L - t, nvars, K, nun, w.v[0], w.v[1]);
     out[t] = (uint8_t)v;
     d += effect(v);
   }
@@ -332,7 +333,8 @@ sr_status sr_vary(sr_ctx *ctx, const uint8_t *prog_in, const int32_t *len_in, co
   using namespace sr;
   if (!ctx || !cfg) return SR_EINVAL;
   if (P < 0 || Lmax < 1 || Lmax > SR_MAX_LMAX || K < 0 || K > SR_MAX_CONSTS || nvars < 1 ||
-      nvars > SR_MAX_VARS || cfg->max_subtree < 0 || cfg->max_subtree > Lmax)
+      nvars > SR_MAX_VARS || cfg->max_subtree < 0 || cfg->max_subtree > Lmax ||
+      (cfg->unary_ops != UNARY_BASE && cfg->unary_ops != UNARY_ALL))
     return fail(ctx, SR_EINVAL, "bad sr_vary shape or configuration");
   if (P == 0) return SR_OK;
   if (!prog_in || !len_in || !parents || !prog_out || !len_out || (K > 0 && (!c_in || !c_out)))
@@ -354,18 +356,18 @@ sr_status sr_set_generation_source(sr_ctx *ctx, const uint64_t *gen_dev) {
 }
 
 sr_status sr_random_programs(sr_ctx *ctx, uint8_t *prog, int32_t *len, float *c, int P, int Lmin,
-                             int Lmax, int K, int nvars, float cmin, float cmax, uint64_t seed,
-                             uint64_t stream) {
+                             int Lmax, int K, int nvars, int unary_ops, float cmin, float cmax,
+                             uint64_t seed, uint64_t stream) {
   using namespace sr;
   if (!ctx) return SR_EINVAL;
   if (P < 0 || Lmin < 1 || Lmin > Lmax || Lmax > SR_MAX_LMAX || K < 0 || K > SR_MAX_CONSTS ||
-      nvars < 1 || nvars > SR_MAX_VARS)
+      nvars < 1 || nvars > SR_MAX_VARS || (unary_ops != UNARY_BASE && unary_ops != UNARY_ALL))
     return fail(ctx, SR_EINVAL, "bad sr_random_programs shape");
   if (P == 0) return SR_OK;
   if (!prog || !len || (K > 0 && !c)) return fail(ctx, SR_EINVAL, "NULL pointer");
   SR_CHECK_CUDA(ctx, cudaSetDevice(ctx->device));
   random_programs_kernel<<<(P + 127) / 128, 128, 0, ctx->stream>>>(prog, len, c, P, Lmin, Lmax, K,
-                                                                    nvars, cmin, cmax,
+                                                                    nvars, unary_ops, cmin, cmax,
                                                                     make_rng(seed, stream));
   SR_CHECK_CUDA(ctx, cudaGetLastError());
   ctx->launches += 1;

@@ -9,7 +9,8 @@
 //               slots below in shared memory.  What the reverse sweep needs
 //               goes on a LIFO tape: for a unary operator its local
 //               derivative, computed here next to the value (cos x with
-//               sin x from one sincos, exp x, 1/x, +-1/(2 sqrt|x|), 2x), so
+//               sin x from one sincos, exp x, 1/x, +-1/(2 sqrt|x|), 2x,
+//               1 + tan^2 x, ...), so
 //               that the reverse step is one multiply; for a product both
 //               factors; for a quotient the denominator and the result.  A
 //               terminal operand fused into * or / needs no entry (x_j is
@@ -87,6 +88,7 @@ __device__ __forceinline__ DecodeArgs grad_decode_args(const GradParams &p) {
   a.s_start = p.s_start;
   a.s_need = p.s_need;
   a.s_task = p.s_task;
+  a.ext_count = nullptr;
   return a;
 }
 
@@ -142,6 +144,50 @@ __device__ __forceinline__ float d_sqrt(float x, float v) { return x == 0.0f ? 0
 __device__ __noinline__ float4 fwd_sqrt(float2 x) {
   const float a = f_sqrt(x.x), b = f_sqrt(x.y);
   return make_float4(a, b, d_sqrt(x.x, a), d_sqrt(x.y, b));
+}
+// the rest of Table 1: 1/x (derivative -1/x^2, 0 where the fallback was
+// taken), tan (1 + tan^2), asin (1/sqrt(1 - x^2)), acos (-1/sqrt(1 - x^2)),
+// atan (1/(1 + x^2)), tanh (sech^2)
+__device__ __forceinline__ float d_inv(float x, float v) { return fabsf(x) < 1e-3f ? 0.0f : -(v * v); }
+__device__ __forceinline__ float4 fwd_inv(float2 x) {
+  const float a = op_inv(x.x), b = op_inv(x.y);
+  return make_float4(a, b, d_inv(x.x, a), d_inv(x.y, b));
+}
+__device__ __forceinline__ float4 fwd_tan(float2 x) {
+  const float a = f_tan(x.x), b = f_tan(x.y);
+  return make_float4(a, b, 1.0f + a * a, 1.0f + b * b);
+}
+// 1 - x^2 as (1 - x)(1 + x): no cancellation near |x| = 1
+__device__ __forceinline__ float d_asin(float x) { return 1.0f / sqrtf((1.0f - x) * (1.0f + x)); }
+__device__ __forceinline__ float4 fwd_asin(float2 x) {
+  return make_float4(f_asin(x.x), f_asin(x.y), d_asin(x.x), d_asin(x.y));
+}
+__device__ __forceinline__ float4 fwd_acos(float2 x) {
+  return make_float4(f_acos(x.x), f_acos(x.y), -d_asin(x.x), -d_asin(x.y));
+}
+__device__ __forceinline__ float4 fwd_atan(float2 x) {
+  return make_float4(f_atan(x.x), f_atan(x.y), 1.0f / (1.0f + x.x * x.x), 1.0f / (1.0f + x.y * x.y));
+}
+// sech^2 x = 4e / (1 + e)^2 with e = exp(-2|x|): 1 - tanh^2 would cancel
+// to 0 long before the derivative underflows
+__device__ __forceinline__ float d_tanh(float x) {
+  const float e = expf(-2.0f * fabsf(x));
+  const float q = 1.0f + e;
+  return 4.0f * e / (q * q);
+}
+__device__ __forceinline__ float4 fwd_tanh(float2 x) {
+  return make_float4(f_tanh(x.x), f_tanh(x.y), d_tanh(x.x), d_tanh(x.y));
+}
+// one out-of-line entry for all of them keeps the forward switch small
+__device__ __noinline__ float4 fwd_ext(uint32_t op, float2 x) {
+  switch (op) {
+    case OP_INV: return fwd_inv(x);
+    case OP_TAN: return fwd_tan(x);
+    case OP_ASIN: return fwd_asin(x);
+    case OP_ACOS: return fwd_acos(x);
+    case OP_ATAN: return fwd_atan(x);
+    default: return fwd_tanh(x);
+  }
 }
 // protected quotient (the interpreter's operator)
 __device__ __noinline__ float2 pdiv2(float2 a, float2 b) { return make_float2(op_div(a.x, b.x), op_div(a.y, b.y)); }
@@ -221,7 +267,7 @@ __global__ void __launch_bounds__(GWARPS * 32) grad_kernel(GradParams p) {
     const int c = (int)(item / (unsigned long long)p.P);
     const int prog = (int)(item % (unsigned long long)p.P);
     if (p.flags[prog]) continue;
-    const int n = p.ncode[prog];
+    const int n = ncode_count(p.ncode[prog]);
     __syncwarp();
     const uint2 *src = p.code + (size_t)prog * p.Lmax;
     for (int i = lane; i < n; i += 32) w.code[i] = src[i];
@@ -264,6 +310,12 @@ __global__ void __launch_bounds__(GWARPS * 32) grad_kernel(GradParams p) {
           case OP_LOG: { const float4 r = fwd_log(T); push(hi2(r)); T = lo2(r); } break;
           case OP_SQRT: { const float4 r = fwd_sqrt(T); push(hi2(r)); T = lo2(r); } break;
           case OP_SQ: push(add2(T, T)); T = mul2(T, T); break;
+          case OP_INV:
+          case OP_TAN:
+          case OP_ASIN:
+          case OP_ACOS:
+          case OP_ATAN:
+          case OP_TANH: { const float4 r = fwd_ext(ins_op(ins), T); push(hi2(r)); T = lo2(r); } break;
           case OP_VADD: T = add2(T, ldx2(xr, ins.y)); break;
           case OP_VSUB: T = sub2(T, ldx2(xr, ins.y)); break;
           case OP_VRSUB: T = sub2(ldx2(xr, ins.y), T); break;
@@ -320,7 +372,13 @@ __global__ void __launch_bounds__(GWARPS * 32) grad_kernel(GradParams p) {
           case OP_EXP:
           case OP_LOG:
           case OP_SQRT:
-          case OP_SQ: { const float2 d = pop(); aT = mul2(aT, d); } break;
+          case OP_SQ:
+          case OP_INV:
+          case OP_TAN:
+          case OP_ASIN:
+          case OP_ACOS:
+          case OP_ATAN:
+          case OP_TANH: { const float2 d = pop(); aT = mul2(aT, d); } break;
           case OP_VADD:
           case OP_VSUB: break;
           case OP_VRSUB: aT = neg2(aT); break;

@@ -42,6 +42,12 @@ enum Op : uint32_t {
   OP_LOG,
   OP_SQRT,
   OP_SQ,
+  OP_INV,       // 1 / top (protected as /)
+  OP_TAN,
+  OP_ASIN,
+  OP_ACOS,
+  OP_ATAN,
+  OP_TANH,
   OP_VADD,      // top = top op x_j   (terminal right operand, evaluated second)
   OP_VSUB,
   OP_VMUL,
@@ -60,6 +66,14 @@ __device__ __forceinline__ uint32_t ins_op(uint2 w) { return w.x & 0xffu; }
 __device__ __forceinline__ uint32_t ins_off(uint2 w) { return (w.x >> 8) & 0xffffu; }
 __device__ __forceinline__ int ins_k(uint2 w) { return (int)((w.x >> 24) & 0xfu); }
 
+// ncode[p] holds the instruction count in its low 16 bits; NCODE_EXT is set
+// when the program uses one of 1/x, tan, asin, acos, atan, tanh, so that
+// the kernels can run those programs in a separate copy of their loop and
+// keep the loop of the base operators free of the extra call site.
+constexpr int NCODE_EXT = 1 << 30;
+__device__ __forceinline__ int ncode_count(int v) { return v & 0xffff; }
+__device__ __forceinline__ bool ncode_ext(int v) { return (v & NCODE_EXT) != 0; }
+
 struct DecodeArgs {
   const uint8_t *programs;  // [P][Lmax]
   const int32_t *lengths;
@@ -73,6 +87,7 @@ struct DecodeArgs {
   int16_t *s_start;         // scratch [P][Lmax]: first token of each subtree
   uint8_t *s_need;          // scratch [P][Lmax]: stack need of each subtree
   int16_t *s_task;          // scratch [P][Lmax]: work stack
+  unsigned long long *ext_count;  // programs with NCODE_EXT are counted here (or NULL)
 };
 
 __device__ __forceinline__ bool is_term(int v) {
@@ -117,6 +132,7 @@ __device__ inline void decode_one(const DecodeArgs &p, int prog) {
   int16_t *start = p.s_start + (size_t)prog * p.Lmax;
   uint8_t *need = p.s_need + (size_t)prog * p.Lmax;
   int16_t *task = p.s_task + (size_t)prog * p.Lmax;
+  int ext = 0;
   // pass 1, postfix order is bottom-up: subtree starts and stack needs
   // (terminal 1; unary as its child; binary max of the children, +1 on a tie)
   int sp = 0;
@@ -127,6 +143,7 @@ __device__ inline void decode_one(const DecodeArgs &p, int prog) {
       need[t] = 1;
       task[sp++] = (int16_t)t;
     } else if (cls == CLS_UNARY) {
+      ext |= tok[t] > TOK_SQ;
       const int c = task[sp - 1];
       start[t] = start[c];
       need[t] = need[c];
@@ -203,7 +220,8 @@ __device__ inline void decode_one(const DecodeArgs &p, int prog) {
       }
     }
   }
-  p.ncode[prog] = n;
+  p.ncode[prog] = n | (ext ? NCODE_EXT : 0);
+  if (ext && p.ext_count) atomicAdd(p.ext_count, 1ull);
 }
 
 // ---------------------------------------------------------------- operators (FP32)
@@ -235,5 +253,20 @@ __device__ __forceinline__ float f_cos(float x) {
   __builtin_assume(fabsf(x) <= 4.0e4f);
   return cosf(x);
 }
+static __device__ __noinline__ float tan_wide(float x) { return tanf(x); }
+__device__ __forceinline__ float f_tan(float x) {
+  if (!(fabsf(x) <= 4.0e4f)) return tan_wide(x);
+  __builtin_assume(fabsf(x) <= 4.0e4f);
+  return tanf(x);
+}
+// The rest of Table 1: 1/x protected like division; tan, asin, acos, atan,
+// tanh as the FP32 library computes them (asin / acos outside [-1, 1] give
+// NaN: a non-real result, which the NaN-aware scores of Eq. 2 / Eq. 3 take
+// as an invalid output and MSE / 1 - r^2 as the worst fitness).
+__device__ __forceinline__ float op_inv(float x) { return op_div(1.0f, x); }
+__device__ __forceinline__ float f_asin(float x) { return asinf(x); }
+__device__ __forceinline__ float f_acos(float x) { return acosf(x); }
+__device__ __forceinline__ float f_atan(float x) { return atanf(x); }
+__device__ __forceinline__ float f_tanh(float x) { return tanhf(x); }
 
 }  // namespace sr

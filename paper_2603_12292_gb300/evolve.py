@@ -40,7 +40,7 @@ class Population:
         v = cfg.var
         # a random subtree longer than the programs can be is never wanted
         self.var = binding.VarCfg(v.p_cross, v.p_point, v.p_subtree, v.p_const, v.const_delta,
-                                  min(v.max_subtree, Lmax))
+                                  min(v.max_subtree, Lmax), v.unary_ops)
         rows = 2 if cfg.eval_kind == binding.SR_MSE_CORR else 1
         self.fitness = torch.empty((rows, P), dtype=torch.float64, device=programs.device)
         self.parents = torch.empty((P, 2), dtype=torch.int32, device=programs.device)

@@ -20,6 +20,7 @@ from dataclasses import dataclass
 import numpy as np
 
 N_BINARY, N_UNARY = 4, 6
+UNARY_ALL = 12  # with 1/x, tan, asin, acos, atan, tanh: the operator set of Table 1
 VAR0, CONST0 = 16, 32
 ROOT_SEED = 20260312
 
@@ -29,7 +30,8 @@ def round_up(n: int, m: int) -> int:
 
 
 def random_programs(rng: np.random.Generator, P: int, Lmin: int, Lmax: int, nvars: int,
-                    K: int, width: int | None = None, var_weight: float | None = None):
+                    K: int, width: int | None = None, var_weight: float | None = None,
+                    unary_ops: int = N_UNARY):
     """P valid postfix programs with lengths uniform in [Lmin, Lmax].
 
     Each token is drawn as a random walk on the stack depth d with r tokens
@@ -38,7 +40,8 @@ def random_programs(rng: np.random.Generator, P: int, Lmin: int, Lmax: int, nvar
     walk able to end at depth exactly 1.  The class is uniform over the
     allowed ones; the token is uniform inside its class (terminals over the
     nvars variables and K constants, or variables with probability
-    ``var_weight`` when it is given).  Returns tokens [P, width] (zero padded),
+    ``var_weight`` when it is given; unary operators over the first
+    ``unary_ops`` of tokens 4-15).  Returns tokens [P, width] (zero padded),
     lengths [P] int32.
     """
     width = Lmax if width is None else width
@@ -70,7 +73,7 @@ def random_programs(rng: np.random.Generator, P: int, Lmin: int, Lmax: int, nvar
             isvar = rng.random(P) < var_weight
             term = np.where(isvar, VAR0 + rng.integers(0, nvars, P),
                             CONST0 + rng.integers(0, K, P))
-        un = 4 + rng.integers(0, N_UNARY, P)
+        un = 4 + rng.integers(0, unary_ops, P)
         bi = rng.integers(0, N_BINARY, P)
         tok = np.where(cls == 0, term, np.where(cls == 1, un, bi))
         prog[act, t] = tok[act].astype(np.uint8)
@@ -142,10 +145,10 @@ class Problem:
 
 def make_problem(name: str, seed: int, P: int, Lmin: int, Lmax: int, nvars: int, K: int, N: int,
                  xlo: float, xhi: float, target_len: tuple[int, int], noise: float = 0.0,
-                 kind: int = 0) -> Problem:
+                 kind: int = 0, unary_ops: int = N_UNARY) -> Problem:
     rng = np.random.default_rng(seed)
     X = random_X(rng, nvars, N, xlo, xhi)
-    prog, lens = random_programs(rng, P, Lmin, Lmax, nvars, K)
+    prog, lens = random_programs(rng, P, Lmin, Lmax, nvars, K, unary_ops=unary_ops)
     consts = random_consts(rng, P, K)
     # target: a random program that reads at least one variable
     while True:
@@ -168,12 +171,14 @@ def plain(attempt: int = 0) -> Problem:
                         nvars=3, K=4, N=1000, xlo=1.0, xhi=5.0, target_len=(9, 9), kind=0)
 
 
-def paper_shaped(attempt: int = 0, kind: int = 1) -> Problem:
+def paper_shaped(attempt: int = 0, kind: int = 1, unary_ops: int = N_UNARY) -> Problem:
     """4,096 programs of length 8..128, 10 variables, 100,000 cases
-    X ~ U(1, 10); target of length <= 25 plus 1% Gaussian noise."""
-    return make_problem("paper-4096x100k", ROOT_SEED + 1 + 1000 * attempt, P=4096, Lmin=8,
+    X ~ U(1, 10); target of length <= 25 plus 1% Gaussian noise.  With
+    unary_ops = 12 the programs draw from the whole operator set of Table 1."""
+    name = "paper-4096x100k" if unary_ops == N_UNARY else "paper-4096x100k-table1"
+    return make_problem(name, ROOT_SEED + 1 + 1000 * attempt, P=4096, Lmin=8,
                         Lmax=128, nvars=10, K=4, N=100_000, xlo=1.0, xhi=10.0,
-                        target_len=(5, 25), noise=0.01, kind=kind)
+                        target_len=(5, 25), noise=0.01, kind=kind, unary_ops=unary_ops)
 
 
 def adjoint(attempt: int = 0, P: int = 16384, N: int = 1_000_000) -> Problem:

@@ -1,7 +1,8 @@
 """Text form of postfix programs for tests: "x0 c1 * sin" -> uint8 tokens."""
 import numpy as np
 
-OPS = {"+": 0, "-": 1, "*": 2, "/": 3, "sin": 4, "cos": 5, "exp": 6, "log": 7, "sqrt": 8, "sq": 9}
+OPS = {"+": 0, "-": 1, "*": 2, "/": 3, "sin": 4, "cos": 5, "exp": 6, "log": 7, "sqrt": 8, "sq": 9,
+       "inv": 10, "tan": 11, "asin": 12, "acos": 13, "atan": 14, "tanh": 15}
 NAMES = {v: k for k, v in OPS.items()}
 
 

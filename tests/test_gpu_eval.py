@@ -87,10 +87,41 @@ def test_brute_force_all_short_programs(ctx, nconst):
     assert checked > 0.95 * len(progs_l) * 257
 
 
-def test_predict_parity_random_population(ctx):
+def test_brute_force_table1_programs(ctx):
+    """Every valid program of length <= 4 over 3 variables with all 12 unary
+    operators of Table 1 (6,987 programs) on 257 cases, X in [-1.5, 1.5]
+    (asin / acos both inside and outside their domain)."""
+    alphabet = list(range(16)) + [16, 17, 18]
+    progs_l = []
+    for n in range(1, 5):
+        seqs = np.array(list(itertools.product(alphabet, repeat=n)), np.uint8)
+        flags, _ = oracle.validate_all(seqs, np.full(len(seqs), n, np.int32), 3, 0)
+        progs_l += list(seqs[flags == 0])
+    assert len(progs_l) == 6_987
+    progs, lens = pack(progs_l, 8)
+    X = inputs.random_X(np.random.default_rng(18), 3, 257, -1.5, 1.5)
+    checked = predict_parity(ctx, progs, lens, np.zeros((len(progs_l), 0), np.float32), X, 257)
+    assert checked > 0.7 * len(progs_l) * 257
+
+
+@pytest.mark.parametrize("unary_ops,frac", [(6, 0.8), (12, 0.4)])
+def test_predict_parity_random_population(ctx, unary_ops, frac):
     pr = inputs.make_problem("pp", 5, P=300, Lmin=1, Lmax=60, nvars=4, K=4, N=1001, xlo=-3,
-                             xhi=3, target_len=(5, 9))
-    assert predict_parity(ctx, pr.programs, pr.lengths, pr.consts, pr.X, pr.N) > 0.8 * 300 * 1001
+                             xhi=3, target_len=(5, 9), unary_ops=unary_ops)
+    assert predict_parity(ctx, pr.programs, pr.lengths, pr.consts, pr.X, pr.N) > frac * 300 * 1001
+
+
+@pytest.mark.parametrize("kind", [oracle.MSE, oracle.CORR])
+def test_fitness_parity_table1(ctx, kind):
+    """Fitness of a population drawn from the whole operator set of Table 1."""
+    pr, y = target_problem(inputs.make_problem, "t1", 61, P=512, Lmin=1, Lmax=48, nvars=3, K=4, N=3001,
+                           xlo=0.1, xhi=0.9, target_len=(5, 9), unary_ops=12)
+    d = dev(pr, y)
+    f = binding.sr_eval(ctx, d["programs"], d["lengths"], d["consts"], d["X"], d["y"], pr.N, kind)
+    torch.cuda.synchronize()
+    f = f.cpu().numpy()
+    errb, cfl, f0 = oracle.condition(pr.programs, pr.lengths, pr.consts, pr.X, y, kind, pr.N)
+    assert check_fitness(kind, f, f0, errb, cfl, y) > 0.3 * pr.P
 
 
 def test_invalid_programs_flagged_bit_exact(ctx):

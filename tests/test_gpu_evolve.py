@@ -53,11 +53,15 @@ def test_tournament_bit_exact(ctx, k):
         np.testing.assert_array_equal(got, want)
 
 
-def test_random_programs_bit_exact(ctx):
+@pytest.mark.parametrize("unary_ops", [6, 12])
+def test_random_programs_bit_exact(ctx, unary_ops):
     for (P, Lmin, Lmax, K, nv, seed, stream) in [(3000, 1, 40, 4, 3, 7, 1), (517, 8, 128, 8, 10, 2 ** 40 + 3, 9),
                                                  (64, 256, 256, 0, 1, 5, 0)]:
-        prog, lens, c = binding.sr_random_programs(ctx, P, Lmin, Lmax, K, nv, -5.0, 5.0, seed, stream)
-        want = oracle.random_programs(P, Lmin, Lmax, K, nv, -5.0, 5.0, seed, stream)
+        prog, lens, c = binding.sr_random_programs(ctx, P, Lmin, Lmax, K, nv, -5.0, 5.0, seed, stream,
+                                                   unary_ops=unary_ops)
+        want = oracle.random_programs(P, Lmin, Lmax, K, nv, -5.0, 5.0, seed, stream, unary_ops=unary_ops)
+        un = want[0][(want[0] >= 4) & (want[0] < 16)]
+        assert un.max() == 3 + unary_ops  # every unary operator of the set is drawn
         np.testing.assert_array_equal(prog.cpu().numpy(), want[0])
         np.testing.assert_array_equal(lens.cpu().numpy(), want[1])
         if K:
@@ -67,10 +71,12 @@ def test_random_programs_bit_exact(ctx):
 CFGS = [dict(p_cross=0.9, p_point=0.1, p_subtree=0.05, p_const=0.1, const_delta=1.0, max_subtree=8),
         dict(p_cross=1.0, p_point=1.0, p_subtree=1.0, p_const=1.0, const_delta=0.37, max_subtree=12),
         dict(p_cross=0.0, p_point=0.0, p_subtree=0.0, p_const=0.0, const_delta=1.0, max_subtree=8),
-        dict(p_cross=0.5, p_point=0.5, p_subtree=0.5, p_const=0.5, const_delta=3.0, max_subtree=1)]
+        dict(p_cross=0.5, p_point=0.5, p_subtree=0.5, p_const=0.5, const_delta=3.0, max_subtree=1),
+        dict(p_cross=0.5, p_point=1.0, p_subtree=1.0, p_const=0.5, const_delta=1.0, max_subtree=8,
+             unary_ops=12)]
 
 
-@pytest.mark.parametrize("cfg", CFGS, ids=["default", "all", "none", "half"])
+@pytest.mark.parametrize("cfg", CFGS, ids=["default", "all", "none", "half", "table1"])
 def test_vary_bit_exact(ctx, cfg):
     pr = inputs.make_problem("vary", 99, P=2048, Lmin=1, Lmax=60, nvars=5, K=4, N=8, xlo=0, xhi=1,
                              target_len=(3, 5))

@@ -37,6 +37,29 @@ def test_closed_form_linear_program(ctx):
     assert mse[0] == pytest.approx(np.mean((float(c[0, 0]) * x - yy) ** 2), rel=1e-5)
 
 
+def test_gradient_table1_operators(ctx):
+    """The adjoint through 1/x, tan, asin, acos, atan and tanh against the
+    oracle's forward mode on well-conditioned programs away from poles,
+    domain ends and switch points."""
+    pr = inputs.make_problem("adj1", 315, P=512, Lmin=4, Lmax=48, nvars=3, K=4, N=2049, xlo=0.1, xhi=0.9,
+                             target_len=(5, 11), unary_ops=12)
+    y = oracle.predict(pr.target, pr.target_consts, pr.X, pr.N)
+    y = np.nan_to_num(y, nan=0.0, posinf=0.0, neginf=0.0)
+    d = dev(pr, y)
+    mse_g, g_g = binding.sr_eval_grad(ctx, d["programs"], d["lengths"], d["consts"], d["X"], d["y"], pr.N)
+    mse_g, g_g = mse_g.cpu().numpy(), g_g.cpu().numpy()
+    mse_o, g_o, kink, gabs = oracle.grad(pr.programs, pr.lengths, pr.consts, pr.X, y, pr.N)
+    errb, cfl, f0 = oracle.condition(pr.programs, pr.lengths, pr.consts, pr.X, y, oracle.MSE, pr.N)
+    well = (cfl == 0) & np.isfinite(f0) & (errb <= 1e-5 * np.abs(f0)) & (kink > 1e-2)
+    assert well.sum() > 50
+    has_new = np.array([((pr.programs[p, : pr.lengths[p]] >= 10) & (pr.programs[p, : pr.lengths[p]] < 16)).any()
+                        for p in range(pr.P)])
+    assert (well & has_new).sum() > 20
+    bad = well[:, None] & ~(np.abs(g_g - g_o) <= 2e-4 * gabs + 1e-12)
+    assert not bad.any(), (np.argwhere(bad)[:5], g_g[bad][:5], g_o[bad][:5], gabs[bad][:5])
+    np.testing.assert_allclose(mse_g[well], mse_o[well], rtol=1e-5)
+
+
 @pytest.fixture(scope="module")
 def adjoint_problem():
     """Adjoint-shaped workload at a size the oracle finishes in seconds:

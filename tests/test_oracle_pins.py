@@ -30,13 +30,41 @@ def test_hand_programs(case):
 
 
 @pytest.mark.parametrize("name,fn", [("sin", np.sin), ("cos", np.cos), ("sqrt", lambda v: np.sqrt(np.abs(v))),
-                                     ("sq", np.square)])
+                                     ("sq", np.square), ("tan", np.tan), ("atan", np.arctan),
+                                     ("tanh", np.tanh)])
 def test_single_op_matches_numpy(name, fn):
     """Single-operator programs reduce to library routines (numpy, FP64)."""
     rng = np.random.default_rng(1)
     x = rng.uniform(-50, 50, 2000)
     got = oracle.predict(parse(f"x0 {name}"), [], x[None, :])
-    np.testing.assert_allclose(got, fn(x), rtol=2e-16, atol=1e-300)
+    # C's libm and numpy agree within an ulp or two, not bit for bit
+    np.testing.assert_allclose(got, fn(x), rtol=4.5e-16, atol=1e-300)
+
+
+def test_table1_domain_operators_match_numpy():
+    """1/x is 1 DIV x (1 where |x| <= 1e-3); asin and acos follow numpy on
+    [-1, 1] and are NaN outside (non-real results)."""
+    rng = np.random.default_rng(3)
+    x = np.concatenate([rng.uniform(-3, 3, 1000), [1e-3, -1e-3, 0.0, 1.5e-3]])
+    with np.errstate(all="ignore"):
+        want = np.where(np.abs(x) <= 1e-3, 1.0, 1.0 / np.where(x == 0, 1, x))
+    np.testing.assert_allclose(oracle.predict(parse("x0 inv"), [], x[None, :]), want, rtol=2e-16)
+    x = rng.uniform(-1.5, 1.5, 2000)
+    inside = np.abs(x) <= 1
+    for name, fn in (("asin", np.arcsin), ("acos", np.arccos)):
+        got = oracle.predict(parse(f"x0 {name}"), [], x[None, :])
+        np.testing.assert_allclose(got[inside], fn(x[inside]), rtol=4.5e-16)  # libm vs numpy: ulps
+        assert np.isnan(got[~inside]).all()
+
+
+def test_enumeration_counts_table1():
+    """All token strings of length <= 4 over 2 variables with the 12 unary
+    operators of Table 1: the tree-count many are valid."""
+    alphabet = list(range(16)) + [16, 17]
+    for n in range(1, 5):
+        seqs = np.array(list(itertools.product(alphabet, repeat=n)), np.uint8)
+        flags, _ = oracle.validate_all(seqs, np.full(len(seqs), n, np.int32), nvars=2, K=0)
+        assert int((flags == 0).sum()) == _tree_count(2, 12, 4, n)[n]
 
 
 def test_exp_log_match_numpy_inside_domain():
@@ -88,8 +116,10 @@ def test_validator_flags():
     for text, want in cases:
         f, _ = oracle.validate(parse(text), 8, 3, 4)
         assert f == want, text
-    f, _ = oracle.validate(np.array([16, 12], np.uint8), 8, 3, 4)
+    f, _ = oracle.validate(np.array([16, 60], np.uint8), 8, 3, 4)
     assert f == oracle.PF_BAD_TOKEN
+    for t in range(10, 16):  # the rest of Table 1: unary operators
+        assert oracle.validate(np.array([16, t], np.uint8), 8, 3, 4) == (0, 1)
     f, _ = oracle.validate(np.array([], np.uint8), 8, 3, 4)
     assert f == oracle.PF_BAD_LENGTH
     f, _ = oracle.validate(parse("x0 x1 + x2 +"), 4, 3, 4)
@@ -262,17 +292,22 @@ def _round32_eval(tok, X, N):
             x = st.pop().astype(np.float64)
             r = [np.sin(x), np.cos(x), np.exp(np.clip(x, -80, 80)),
                  np.where(np.abs(x) <= 1e-3, 0.0, np.log(np.maximum(np.abs(x), 1e-300))),
-                 np.sqrt(np.abs(x)), x * x][t - 4]
+                 np.sqrt(np.abs(x)), x * x,
+                 np.where(np.abs(x) <= 1e-3, 1.0, 1.0 / np.where(x == 0, 1, x)), np.tan(x),
+                 np.arcsin(x), np.arccos(x), np.arctan(x), np.tanh(x)][t - 4]
         st.append(r.astype(f))
     return st[0].astype(np.float64)
 
 
-def test_interval_contains_fp64_and_rounded_fp32():
-    """On random programs, every case's enclosure contains the FP64 value and
-    the result of a correctly rounding FP32 evaluation, and stays tight
-    (median width within a few hundred u |yhat|)."""
+@pytest.mark.parametrize("unary_ops,min_frac", [(6, 0.8), (12, 0.4)])
+def test_interval_contains_fp64_and_rounded_fp32(unary_ops, min_frac):
+    """On random programs (base operators; all of Table 1), every case's
+    enclosure contains the FP64 value and the result of a correctly rounding
+    FP32 evaluation, and stays tight (median width within a few hundred
+    u |yhat|).  Cases that may leave the FP32 range or the domain of asin /
+    acos are flagged instead."""
     pr = inputs.make_problem("eb", 12, P=400, Lmin=1, Lmax=40, nvars=3, K=0, N=500, xlo=-4,
-                             xhi=4, target_len=(3, 5))
+                             xhi=4, target_len=(3, 5), unary_ops=unary_ops)
     checked, rel_w = 0, []
     for p in range(pr.P):
         tok = pr.programs[p, : pr.lengths[p]]
@@ -285,7 +320,7 @@ def test_interval_contains_fp64_and_rounded_fp32():
         checked += int(ok.sum())
         nz = ok & (np.abs(ref) > 1e-30)
         rel_w += list((hi - lo)[nz] / np.abs(ref[nz]))
-    assert checked > 0.8 * pr.P * pr.N
+    assert checked > min_frac * pr.P * pr.N
     assert np.median(rel_w) < 300 * oracle.U_FP32
 
 
@@ -337,11 +372,13 @@ def test_gradient_absolute_scale():
     assert gabs[2, 0] == pytest.approx(2.0 / N * np.sum(np.abs(x - y) * np.abs(x)) * 2.0 / abs(c2), rel=1e-13)
 
 
-def test_gradient_matches_central_differences():
+@pytest.mark.parametrize("unary_ops", [6, 12])
+def test_gradient_matches_central_differences(unary_ops):
     """Forward-mode dMSE/dc vs FP64 central differences (h = 1e-6) on random
-    programs whose branch arguments stay away from their switch points."""
+    programs (base operators; all of Table 1) whose branch arguments stay
+    away from their switch points and poles."""
     pr = inputs.make_problem("fd", 11, P=96, Lmin=3, Lmax=24, nvars=3, K=4, N=200, xlo=1, xhi=5,
-                             target_len=(9, 9))
+                             target_len=(9, 9), unary_ops=unary_ops)
     y = oracle.predict(pr.target, pr.target_consts, pr.X, pr.N)
     h = 1e-6
     tested = 0

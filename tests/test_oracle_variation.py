@@ -7,7 +7,7 @@ import pytest
 import oracle
 from progtext import pack, parse
 
-BIN, UN = set(range(4)), set(range(4, 10))
+BIN, UN = set(range(4)), set(range(4, 16))  # unary: the 12 of Table 1
 
 
 def _cls(t):
@@ -195,6 +195,22 @@ def test_point_mutation_keeps_arity(pop):
             nchanged += 1
     assert nchanged > 0.6 * len(lo)
     assert np.array_equal(co, c[par[:, 0]])
+
+
+def test_table1_operator_set_in_variation(pop):
+    """With unary_ops = 12, point and subtree mutation draw all 12 unary
+    operators (tokens 4-15) and every child stays valid; with 6 only 4-9."""
+    prog, lens, c, par, K, nv = pop
+    for nun in (6, 12):
+        seen = set()
+        for g in range(6):
+            po, lo, co = oracle.vary(prog, lens, c, par, K, nv, p_cross=0, p_point=1.0, p_subtree=1.0,
+                                     p_const=0, seed=21, gen=g, unary_ops=nun)
+            flags, _ = oracle.validate_all(po, lo, nv, K)
+            assert (flags == 0).all()
+            for i in range(len(lo)):
+                seen |= {int(t) for t in po[i, : lo[i]] if 4 <= t < 16}
+        assert seen == set(range(4, 4 + nun))
 
 
 def test_subtree_mutation_replaces_one_subtree(pop):
