@@ -45,6 +45,12 @@ def parse():
     ap.add_argument("--ops", default="base", choices=["base", "table1"],
                     help="operator set of the paper / beagle populations: base (+ - * / sin cos exp log "
                          "sqrt sq) or table1 (adds 1/x tan asin acos atan tanh, Table 1)")
+    ap.add_argument("--selection", default="tournament", choices=["tournament", "microcosm"],
+                    help="parent selection of the paper / large workloads: k = 4 tournament, or the "
+                         "paper's Monte-Carlo microcosm selection (Sec. 2.1.6: sample 100, keep 0.5)")
+    ap.add_argument("--schedule", action="store_true",
+                    help="large workload: shrink the population 262,144 -> 131,072 -> 65,536 every two "
+                         "generations (the paper's variable population size, Sec. 2.1.7; needs microcosm)")
     ap.add_argument("--small", action="store_true",
                     help="reduced sizes of the adjoint / large / batched workloads (2,048 x 131,072; "
                          "16,384 x 131,072; the first 8 problems), for profiler captures")
@@ -201,6 +207,12 @@ def run_ours(args, rank, world, local_rank):
     state = {"gen": 0, "cur": 0}
     ev_eval = []
 
+    def select(f, g):
+        if args.selection == "microcosm":
+            binding.sr_select_microcosm(ctx, f, pr.P, 100, 0.5, SEED, g, parents=parents)
+        else:
+            binding.sr_select_tournament(ctx, f, K_TOURN, SEED, g, parents=parents)
+
     def generation(record_eval=False):
         """One generation: both fitness kinds from one pass, tournament on 1 - r^2, variation."""
         g, cur = state["gen"], state["cur"]
@@ -212,7 +224,7 @@ def run_ours(args, rank, world, local_rank):
         if record_eval:
             e1.record(stream)
             ev_eval.append((e0, e1))
-        binding.sr_select_tournament(ctx, fitness[1], K_TOURN, SEED, g, parents=parents)
+        select(fitness[1], g)
         binding.sr_vary(ctx, P_, L_, C_, parents, pr.nvars, cfg, SEED, g, out=pop[1 - cur])
         state["gen"], state["cur"] = g + 1, 1 - cur
         return L_
@@ -281,7 +293,7 @@ def run_ours(args, rank, world, local_rank):
         d_in[1].copy_(h_len, non_blocking=True)
         d_in[2].copy_(h_con, non_blocking=True)
         binding.sr_eval(ctx, d_in[0], d_in[1], d_in[2], X, y, pr.N, binding.SR_MSE_CORR, fitness=fitness)
-        binding.sr_select_tournament(ctx, fitness[1], K_TOURN, SEED, g, parents=parents)
+        select(fitness[1], g)
         binding.sr_vary(ctx, d_in[0], d_in[1], d_in[2], parents, pr.nvars, cfg, SEED, g, out=d_out)
         h_prog.copy_(d_out[0], non_blocking=True)
         h_len.copy_(d_out[1], non_blocking=True)
@@ -316,8 +328,10 @@ def run_ours(args, rank, world, local_rank):
             "data": "synthetic",
             "config": {"workload": pr.name, "programs": pr.P, "cases": pr.N, "vars": pr.nvars,
                        "lengths": "8-128", "fitness": "MSE and 1-r^2 from one pass",
-                       "step": "one generation: sr_eval(SR_MSE_CORR) + sr_select_tournament(k=4, on 1-r^2)"
-                               " + sr_vary(p_cross 0.9, p_point 0.1, p_subtree 0.05, p_const 0.1)",
+                       "step": "one generation: sr_eval(SR_MSE_CORR) + "
+                               + ("sr_select_microcosm(sample 100, keep 0.5, on 1-r^2)" if args.selection == "microcosm"
+                                  else "sr_select_tournament(k=4, on 1-r^2)")
+                               + " + sr_vary(p_cross 0.9, p_point 0.1, p_subtree 0.05, p_const 0.1)",
                        "l2": "flushed between timed steps",
                        "parallelism": f"islands x{world}: one population per rank, own seed, no exchange"},
             "roofline": roofline, "clocks": clocks,
@@ -481,17 +495,32 @@ def run_workload(args, local_rank):
     elif args.workload == "large":
         pr = inputs.large(P=16384, N=131072) if args.small else inputs.large()
         pg, ln, cs, X, y = _device_problem(pr, dev, binding, ctx)
-        cfg = EvolveConfig(select_kind=binding.SR_CORR, eval_kind=binding.SR_CORR)
+        sched = None
+        if args.schedule:
+            w0 = max(1, args.warmup)
+            sched = ((0, pr.P), (w0 + 2, pr.P // 2), (w0 + 4, pr.P // 4))
+        cfg = EvolveConfig(select_kind=binding.SR_CORR, eval_kind=binding.SR_CORR, selection=args.selection,
+                           schedule=sched)
         ev = Evolver(ctx, [Population(pg, ln, cs, X, y, pr.N, cfg)])
         for _ in range(max(1, args.warmup)):
             ev.step()
         torch.cuda.synchronize()
         steps = max(1, args.steps)
-        n_before = float(ev.pops[0].current[1].sum()) * pr.N
-        t = _timed(ev.step, steps, stream)
+        ms, nodes, sizes = [], [], []
+        for _ in range(steps):
+            nodes.append(float(ev.pops[0].current[1].sum()) * pr.N)
+            sizes.append(ev.pops[0].size)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ev.step()
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
         line.update(metric="GPop/s (nodes x cases / s), one generation (1-r^2, selection, variation)",
-                    value=n_before / (t / 1e3) / 1e9, unit="GPop/s", ms_per_step=t, scaling="weak",
-                    config={"workload": pr.name, "programs": pr.P, "cases": pr.N, "lengths": "4-256"})
+                    value=sum(nodes) / (sum(ms) / 1e3) / 1e9, unit="GPop/s", ms_per_step=sum(ms) / steps,
+                    scaling="weak",
+                    config={"workload": pr.name, "programs": pr.P, "cases": pr.N, "lengths": "4-256",
+                            "selection": args.selection, "population_sizes": sizes})
     elif args.workload == "beagle":
         nun = 12 if args.ops == "table1" else 6
         pr = inputs.paper_shaped(unary_ops=nun)

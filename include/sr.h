@@ -279,6 +279,31 @@ sr_status sr_select_tournament(sr_ctx *ctx, const double *fitness, int P, int k,
 sr_status sr_select_tournament_max(sr_ctx *ctx, const double *score, int P, int k,
                                    uint64_t seed, uint64_t gen, int32_t *parents);
 
+/*
+ * sr_select_microcosm -- Beagle's Monte-Carlo ("microcosm") selection
+ * (Sec. 2.1.6): a small random sample of the population stands in for the
+ * whole when ranking it.
+ *  1. sample: S individuals, sample j = word j%4 of Philox(j/4, 0, 11, gen)
+ *     mapped to [0, P_in); sorted by key (fitness, NaN as +inf; equal keys
+ *     by sample position); the threshold tau is the key at rank
+ *     max(0, ceil(keep S) - 1): an estimate of the fitness that the best
+ *     fraction keep of the whole population reaches.
+ *  2. one pass over the P_out child slots: parents[2i + s] (s = 0, 1) is the
+ *     first of the candidates word q of Philox(r, i, 12 + s, gen) mapped to
+ *     [0, P_in), r = 0..15, q = 0..3, whose key is at most tau; when none of
+ *     those 64 is, the one with the smallest key (ties to the smaller index).
+ * Smaller fitness is better (MSE, 1 - r^2; negate scores first).
+ *   fitness    device double [P_in];   parents  device int32 [P_out][2]
+ *   sample     1..1024 (the paper samples 100);  keep in (0, 1]
+ *   threshold  device double [1] receiving tau, or NULL
+ * P_out may differ from P_in: a population schedule grows or shrinks the
+ * population between generations (sr_vary takes both sizes).
+ * Errors: SR_EINVAL.
+ */
+sr_status sr_select_microcosm(sr_ctx *ctx, const double *fitness, int P_in, int P_out, int sample,
+                              double keep, uint64_t seed, uint64_t gen, int32_t *parents,
+                              double *threshold);
+
 /* Variation parameters (probabilities in [0, 1], FP32). */
 typedef struct {
   float p_cross;    /* subtree crossover (else the child starts as parent A) */
@@ -291,7 +316,8 @@ typedef struct {
 } sr_var_cfg;
 
 /*
- * sr_vary -- one child per slot i from A = parents[2i], B = parents[2i+1].
+ * sr_vary -- one child per slot i < P from A = parents[2i], B = parents[2i+1],
+ * indices into the parent population of P_in programs (P may differ).
  * Decisions: u_cross, u_point, u_sub, u_const = the four words of
  * Philox(0, i, 3, gen) in [0, 1).
  *  1. crossover when u_cross < p_cross: words 0 and 1 of Philox(0, i, 4, gen)
@@ -317,15 +343,16 @@ typedef struct {
  *     gen): slot [0, K), u = word 1 in [0, 1);
  *     c = fl32(c + fl32(fl32(u - 0.5) * const_delta)).
  * Children of valid parents are valid.  Bytes past each child's length are
- * zero.  Parent indices outside [0, P) and lengths outside [1, Lmax] are
+ * zero.  Parent indices outside [0, P_in) and lengths outside [1, Lmax] are
  * clamped into range (never read out of bounds).
- *   prog_in/len_in/c_in  device, the parent population ([P][Lmax], [P], [P][K])
+ *   prog_in/len_in/c_in  device, the parent population ([P_in][Lmax], [P_in],
+ *                        [P_in][K])
  *   parents              device int32 [P][2], each in [0, P)
  *   prog_out/len_out/c_out device, the children (must not alias the inputs)
  * Errors: SR_EINVAL.
  */
 sr_status sr_vary(sr_ctx *ctx, const uint8_t *prog_in, const int32_t *len_in,
-                  const float *c_in, const int32_t *parents, uint8_t *prog_out,
+                  const float *c_in, int P_in, const int32_t *parents, uint8_t *prog_out,
                   int32_t *len_out, float *c_out, int P, int Lmax, int K,
                   int nvars, const sr_var_cfg *cfg, uint64_t seed,
                   uint64_t gen);

@@ -81,8 +81,9 @@ def _load():
     lib.or_eval_score.argtypes = [P, P, P, i32, i32, i32, P, i64, P, i32, i64, i32, i32, P, P, P, i32]
     lib.or_p2p_range.argtypes = [P, P, P, i32, i32, i32, P, i64, P, i32, i64, f64, i32, P, P, P, i32]
     lib.or_random_programs.argtypes = [P, P, P, i32, i32, i32, i32, i32, i32, f32, f32, u64, u64]
-    lib.or_vary.argtypes = [P, P, P, P, P, P, P, i32, i32, i32, i32, f32, f32, f32, f32, f32, i32, i32, u64,
-                            u64]
+    lib.or_vary.argtypes = [P, P, P, i32, P, P, P, P, i32, i32, i32, i32, f32, f32, f32, f32, f32, i32, i32,
+                            u64, u64]
+    lib.or_microcosm.argtypes = [P, i32, i32, i32, f64, u64, u64, P, P]
     _lib = lib
     return lib
 
@@ -297,14 +298,25 @@ def vary(programs, lengths, consts, parents, K, nvars, p_cross=0.9, p_point=0.1,
     P, Lmax = prog.shape
     lens = _c(lengths, np.int32)
     cons = _c(consts, np.float32).reshape(P, K) if K > 0 else np.zeros((P, 0), np.float32)
-    par = _c(parents, np.int32)
-    po = np.empty_like(prog)
-    lo = np.empty_like(lens)
-    co = np.empty_like(cons)
-    _load().or_vary(_ptr(prog), _ptr(lens), _ptr(cons), _ptr(par), _ptr(po), _ptr(lo), _ptr(co),
-                    P, Lmax, K, nvars, p_cross, p_point, p_subtree, p_const, const_delta, max_subtree,
+    par = _c(parents, np.int32).reshape(-1, 2)
+    Pc = par.shape[0]  # children: one per parent pair (the parents' population has P rows)
+    po = np.empty((Pc, Lmax), np.uint8)
+    lo = np.empty(Pc, np.int32)
+    co = np.empty((Pc, cons.shape[1]), np.float32)
+    _load().or_vary(_ptr(prog), _ptr(lens), _ptr(cons), P, _ptr(par), _ptr(po), _ptr(lo), _ptr(co),
+                    Pc, Lmax, K, nvars, p_cross, p_point, p_subtree, p_const, const_delta, max_subtree,
                     unary_ops, seed, gen)
     return po, lo, co
+
+
+def microcosm(fitness, P_out: int, sample: int, keep: float, seed: int, gen: int):
+    """Beagle's microcosm selection (Sec. 2.1.6): parents [P_out, 2] and the
+    threshold tau (see or_microcosm)."""
+    f = _c(fitness, np.float64)
+    par = np.empty((P_out, 2), np.int32)
+    tau = ctypes.c_double(0.0)
+    _load().or_microcosm(_ptr(f), len(f), P_out, sample, keep, seed, gen, _ptr(par), ctypes.byref(tau))
+    return par, float(tau.value)
 
 
 # ---------------------------------------------------------------- Beagle scores (Eq. 2, Eq. 3)

@@ -1093,6 +1093,9 @@ static float unit24(uint32_t u) { return (float)(u >> 8) * (1.0f / 16777216.0f);
 #define PU_CONSTMUT 8
 #define PU_INIT 9
 #define PU_INITC 10
+#define PU_MICRO_SAMPLE 11
+#define PU_MICRO_A 12
+#define PU_MICRO_B 13
 
 /* ---- tournament selection ---------------------------------------------- */
 /*
@@ -1137,6 +1140,67 @@ void or_tournament(const double *fitness, int P, int k, uint64_t seed,
 void or_tournament_max(const double *score, int P, int k, uint64_t seed,
                        uint64_t gen, int32_t *parents) {
   tournament_dir(score, P, k, seed, gen, 1, parents);
+}
+
+/*
+ * Beagle's Monte-Carlo ("microcosm") selection (Sec. 2.1.6), as specified in
+ * include/sr.h: S sampled individuals, sorted by key (fitness, NaN as +inf,
+ * equal keys by sample position); tau = the key at rank ceil(keep S) - 1;
+ * each parent is the first of up to 64 uniform candidates whose key is at
+ * most tau, else the best of them (ties to the smaller index).
+ */
+static double micro_key(double f) { return isnan(f) ? INFINITY : f; }
+
+typedef struct {
+  double key;
+  int pos;
+} keyed;
+
+static int keyed_cmp(const void *a, const void *b) {
+  const keyed *x = (const keyed *)a, *y = (const keyed *)b;
+  if (x->key < y->key) return -1;
+  if (x->key > y->key) return 1;
+  return (x->pos > y->pos) - (x->pos < y->pos);
+}
+
+void or_microcosm(const double *fitness, int P_in, int P_out, int S, double keep, uint64_t seed,
+                  uint64_t gen, int32_t *parents, double *tau_out) {
+  keyed *smp = (keyed *)malloc(sizeof(keyed) * (size_t)S);
+  uint32_t w[4];
+  for (int j = 0; j < S; ++j) {
+    if (j % 4 == 0) draw4(seed, (uint32_t)(j / 4), 0u, PU_MICRO_SAMPLE, gen, w);
+    int idx = (int)below(w[j % 4], (uint32_t)P_in);
+    smp[j].key = micro_key(fitness[idx]);
+    smp[j].pos = j;
+  }
+  qsort(smp, (size_t)S, sizeof(keyed), keyed_cmp);
+  int kq = (int)ceil(keep * (double)S) - 1;
+  kq = kq < 0 ? 0 : (kq >= S ? S - 1 : kq);
+  double tau = smp[kq].key;
+  free(smp);
+  if (tau_out) *tau_out = tau;
+  for (int i = 0; i < P_out; ++i) {
+    for (int s = 0; s < 2; ++s) {
+      int best = -1, chosen = -1;
+      double bestk = 0.0;
+      for (int r = 0; r < 16 && chosen < 0; ++r) {
+        draw4(seed, (uint32_t)r, (uint32_t)i, s == 0 ? PU_MICRO_A : PU_MICRO_B, gen, w);
+        for (int q = 0; q < 4; ++q) {
+          int cand = (int)below(w[q], (uint32_t)P_in);
+          double k = micro_key(fitness[cand]);
+          if (k <= tau) {
+            chosen = cand;
+            break;
+          }
+          if (best < 0 || k < bestk || (k == bestk && cand < best)) {
+            best = cand;
+            bestk = k;
+          }
+        }
+      }
+      parents[2 * i + s] = chosen >= 0 ? chosen : best;
+    }
+  }
 }
 
 /* ---- random program generation ------------------------------------------ */
@@ -1235,7 +1299,7 @@ static int subtree_start(const uint8_t *tok, int end) {
  *         k in [0, K), u = unit24(word 1);
  *         c[k] = fl32(c[k] + fl32(fl32(u - 0.5) * delta)).
  */
-void or_vary(const uint8_t *prog_in, const int32_t *len_in, const float *c_in,
+void or_vary(const uint8_t *prog_in, const int32_t *len_in, const float *c_in, int P_in,
              const int32_t *parents, uint8_t *prog_out, int32_t *len_out,
              float *c_out, int P, int Lmax, int K, int nvars, float p_cross,
              float p_point, float p_subtree, float p_const, float delta,
@@ -1244,6 +1308,8 @@ void or_vary(const uint8_t *prog_in, const int32_t *len_in, const float *c_in,
   uint8_t *tmp = (uint8_t *)malloc((size_t)Lmax + (size_t)max_subtree + 8);
   for (int i = 0; i < P; ++i) {
     int ia = parents[2 * i], ib = parents[2 * i + 1];
+    ia = ia < 0 ? 0 : (ia >= P_in ? P_in - 1 : ia);
+    ib = ib < 0 ? 0 : (ib >= P_in ? P_in - 1 : ib);
     const uint8_t *A = prog_in + (size_t)ia * Lmax;
     const uint8_t *B = prog_in + (size_t)ib * Lmax;
     int la = len_in[ia], lb = len_in[ib];

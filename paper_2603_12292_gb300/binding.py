@@ -25,7 +25,7 @@ EXPORTS = ["sr_create", "sr_destroy", "sr_set_stream", "sr_status_string", "sr_l
            "sr_reserve", "sr_sync", "sr_eval", "sr_predict", "sr_kernel_launches",
            "sr_eval_noalloc", "sr_philox4x32_10", "sr_select_tournament", "sr_vary",
            "sr_random_programs", "sr_eval_grad", "sr_adam_step", "sr_eval_batched", "sr_set_tile",
-           "sr_eval_score", "sr_select_tournament_max",
+           "sr_eval_score", "sr_select_tournament_max", "sr_select_microcosm",
            "sr_set_generation_source"]
 
 _lib = None
@@ -99,8 +99,9 @@ def lib() -> ctypes.CDLL:
     L.sr_select_tournament.argtypes = [vp, vp, i32, i32, u64, u64, vp]
     L.sr_select_tournament_max.argtypes = [vp, vp, i32, i32, u64, u64, vp]
     L.sr_eval_score.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp, vp, i32, i32, i32, i32, i32, vp, vp, vp]
-    L.sr_vary.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, ctypes.POINTER(VarCfg),
+    L.sr_vary.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, vp, i32, i32, i32, i32, ctypes.POINTER(VarCfg),
                           u64, u64]
+    L.sr_select_microcosm.argtypes = [vp, vp, i32, i32, i32, ctypes.c_double, u64, u64, vp, vp]
     L.sr_random_programs.argtypes = [vp, vp, vp, vp, i32, i32, i32, i32, i32, i32, f32, f32, u64, u64]
     L.sr_eval_grad.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp, vp, i32, i32, i32, vp, vp, vp]
     L.sr_adam_step.argtypes = [vp, vp, vp, vp, vp, i32, i32, ctypes.POINTER(AdamCfg)]
@@ -307,22 +308,45 @@ def sr_select_tournament_max(ctx: Context, score, k: int, seed: int, gen: int,
 
 def sr_vary(ctx: Context, programs, lengths, consts, parents, nvars: int, cfg: VarCfg, seed: int,
             gen: int, out=None):
-    """Children of the parent pairs; returns (programs, lengths, consts)."""
+    """One child per row of parents ([P_out, 2], indices into the P_in rows of
+    programs); returns (programs, lengths, consts) of the children (the
+    first P_out rows of ``out`` when it is given)."""
     _dev(programs, torch.uint8, "programs")
     _dev(lengths, torch.int32, "lengths")
     _dev(parents, torch.int32, "parents")
-    P, Lmax = programs.shape
+    P_in, Lmax = programs.shape
+    P = parents.shape[0]
     K = consts.shape[1] if consts is not None and consts.dim() == 2 else 0
     if K:
         _dev(consts, torch.float32, "consts")
     if out is None:
-        out = (torch.empty_like(programs), torch.empty_like(lengths),
-               torch.empty_like(consts) if K else None)
+        dev = programs.device
+        out = (torch.empty((P, Lmax), dtype=torch.uint8, device=dev), torch.empty(P, dtype=torch.int32, device=dev),
+               torch.empty((P, K), dtype=torch.float32, device=dev) if K else None)
     po, lo, co = out
-    _check(ctx, lib().sr_vary(ctx.handle, _ptr(programs), _ptr(lengths), _ptr(consts) if K else None,
+    if po.shape[0] < P or lo.shape[0] < P or po.shape[1] != Lmax:
+        raise ValueError("output buffers smaller than the children")
+    _check(ctx, lib().sr_vary(ctx.handle, _ptr(programs), _ptr(lengths), _ptr(consts) if K else None, P_in,
                               _ptr(parents), _ptr(po), _ptr(lo), _ptr(co) if K else None, P, Lmax, K,
                               nvars, ctypes.byref(cfg), seed, gen))
     return po, lo, co
+
+
+def sr_select_microcosm(ctx: Context, fitness, P_out: int, sample: int, keep: float, seed: int, gen: int,
+                        parents: torch.Tensor | None = None, threshold: torch.Tensor | None = None):
+    """Beagle's microcosm selection (sr_select_microcosm): parents [P_out, 2]
+    drawn from the P_in = len(fitness) programs; threshold (float64 [1]) gets
+    the sample's keep-quantile when given."""
+    _dev(fitness, torch.float64, "fitness")
+    P_in = fitness.shape[0]
+    if parents is None:
+        parents = torch.empty((P_out, 2), dtype=torch.int32, device=fitness.device)
+    _dev(parents, torch.int32, "parents")
+    if threshold is not None:
+        _dev(threshold, torch.float64, "threshold")
+    _check(ctx, lib().sr_select_microcosm(ctx.handle, _ptr(fitness), P_in, P_out, sample, keep, seed, gen,
+                                          _ptr(parents), _ptr(threshold)))
+    return parents
 
 
 def sr_random_programs(ctx: Context, P: int, Lmin: int, Lmax: int, K: int, nvars: int, cmin: float,

@@ -71,7 +71,8 @@ __device__ __forceinline__ float unit24(uint32_t w) {
 }
 
 constexpr uint32_t PU_TOURN_A = 1, PU_TOURN_B = 2, PU_DECIDE = 3, PU_CROSS = 4, PU_POINT = 5,
-                   PU_SUBTREE = 6, PU_SUBGEN = 7, PU_CONSTMUT = 8, PU_INIT = 9, PU_INITC = 10;
+                   PU_SUBTREE = 6, PU_SUBGEN = 7, PU_CONSTMUT = 8, PU_INIT = 9, PU_INITC = 10,
+                   PU_MICRO_SAMPLE = 11, PU_MICRO_A = 12, PU_MICRO_B = 13;
 
 __device__ __forceinline__ int effect(int v) { return cls_effect(tok_class(v)); }
 
@@ -149,6 +150,7 @@ struct VaryParams {
   int P, Lmax, K, nvars;
   sr_var_cfg cfg;
   Rng rng;
+  int P_in;  // parents' population size
 };
 
 __global__ void vary_kernel(VaryParams p) {
@@ -157,8 +159,8 @@ __global__ void vary_kernel(VaryParams p) {
   p.rng = p.rng.resolved();
   // out-of-range parents and lengths are clamped so that no access leaves
   // the buffers (valid inputs are unaffected)
-  const int ia = min(max(p.parents[2 * i], 0), p.P - 1);
-  const int ib = min(max(p.parents[2 * i + 1], 0), p.P - 1);
+  const int ia = min(max(p.parents[2 * i], 0), p.P_in - 1);
+  const int ib = min(max(p.parents[2 * i + 1], 0), p.P_in - 1);
   const uint8_t *A = p.prog_in + (size_t)ia * p.Lmax;
   const uint8_t *B = p.prog_in + (size_t)ib * p.Lmax;
   const int la = min(max(p.len_in[ia], 1), p.Lmax), lb = min(max(p.len_in[ib], 1), p.Lmax);
@@ -258,6 +260,70 @@ __global__ void vary_kernel(VaryParams p) {
   for (int k = 0; k < p.K; ++k) p.c_out[(size_t)i * p.K + k] = c[k];
 }
 
+// ---------------------------------------------------------------- microcosm selection
+// Beagle's Monte-Carlo population control (Sec. 2.1.6): a sample of S
+// individuals stands in for the whole population; its keep-quantile tau
+// estimates the fitness threshold of the best fraction keep.  Keys: fitness,
+// NaN as +inf (smaller is better).
+__device__ __forceinline__ double micro_key(double f) {
+  return isnan(f) ? __longlong_as_double(0x7ff0000000000000ll) : f;
+}
+
+constexpr int MICRO_MAX_SAMPLE = 1024;
+constexpr int MICRO_ROUNDS = 16;  // 4 candidates per Philox draw: at most 64 per parent
+
+// one block of S threads: draw, sort by rank (S <= 1024, O(S^2) compares),
+// tau = the sample's value at rank ceil(keep S) - 1
+__global__ void microcosm_sample_kernel(const double *__restrict__ fitness, int P, int S, int kq, Rng rng_in,
+                                        double *tau) {
+  __shared__ double key[MICRO_MAX_SAMPLE];
+  __shared__ int idx[MICRO_MAX_SAMPLE];
+  const Rng rng = rng_in.resolved();
+  const int j = threadIdx.x;
+  if (j < S) {
+    const Word4 w = rng.draw((uint32_t)(j >> 2), 0u, PU_MICRO_SAMPLE);
+    idx[j] = (int)below(w.v[j & 3], (uint32_t)P);
+    key[j] = micro_key(fitness[idx[j]]);
+  }
+  __syncthreads();
+  if (j < S) {
+    // rank of sample j: smaller keys first, equal keys by sample position
+    int r = 0;
+    for (int t = 0; t < S; ++t) r += key[t] < key[j] || (key[t] == key[j] && t < j);
+    if (r == kq) *tau = key[j];
+  }
+}
+
+// thread per (child, parent slot): the first of up to 64 uniform candidates
+// whose key is at most tau; if none is, the best candidate drawn (ties to
+// the smaller index)
+__global__ void microcosm_select_kernel(const double *__restrict__ fitness, int P_in, int P_out, Rng rng_in,
+                                        const double *tau_p, int32_t *__restrict__ parents) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * P_out) return;
+  const Rng rng = rng_in.resolved();
+  const int i = t >> 1, s = t & 1;
+  const double tau = *tau_p;
+  int best = -1;
+  double bestk = 0.0;
+  for (int r = 0; r < MICRO_ROUNDS; ++r) {
+    const Word4 w = rng.draw((uint32_t)r, (uint32_t)i, s ? PU_MICRO_B : PU_MICRO_A);
+    for (int q = 0; q < 4; ++q) {
+      const int cand = (int)below(w.v[q], (uint32_t)P_in);
+      const double k = micro_key(fitness[cand]);
+      if (k <= tau) {
+        parents[t] = cand;
+        return;
+      }
+      if (best < 0 || k < bestk || (k == bestk && cand < best)) {
+        best = cand;
+        bestk = k;
+      }
+    }
+  }
+  parents[t] = best;
+}
+
 __global__ void random_programs_kernel(uint8_t *prog, int32_t *len, float *c, int P, int Lmin,
                                        int Lmax, int K, int nvars, int nun, float cmin, float cmax,
                                        Rng rng) {
@@ -327,11 +393,12 @@ sr_status sr_select_tournament_max(sr_ctx *ctx, const double *score, int P, int 
   return select_tournament(ctx, score, P, k, seed, gen, parents, true);
 }
 
-sr_status sr_vary(sr_ctx *ctx, const uint8_t *prog_in, const int32_t *len_in, const float *c_in,
+sr_status sr_vary(sr_ctx *ctx, const uint8_t *prog_in, const int32_t *len_in, const float *c_in, int P_in,
                   const int32_t *parents, uint8_t *prog_out, int32_t *len_out, float *c_out, int P,
                   int Lmax, int K, int nvars, const sr_var_cfg *cfg, uint64_t seed, uint64_t gen) {
   using namespace sr;
   if (!ctx || !cfg) return SR_EINVAL;
+  if (P > 0 && P_in < 1) return fail(ctx, SR_EINVAL, "P_in must be >= 1 when there are children");
   if (P < 0 || Lmax < 1 || Lmax > SR_MAX_LMAX || K < 0 || K > SR_MAX_CONSTS || nvars < 1 ||
       nvars > SR_MAX_VARS || cfg->max_subtree < 0 || cfg->max_subtree > Lmax ||
       (cfg->unary_ops != UNARY_BASE && cfg->unary_ops != UNARY_ALL))
@@ -342,10 +409,37 @@ sr_status sr_vary(sr_ctx *ctx, const uint8_t *prog_in, const int32_t *len_in, co
   if (prog_in == prog_out) return fail(ctx, SR_EINVAL, "prog_out must not alias prog_in");
   SR_CHECK_CUDA(ctx, cudaSetDevice(ctx->device));
   VaryParams vp{prog_in, len_in, c_in, parents, prog_out, len_out, c_out, P, Lmax, K, nvars, *cfg,
-                make_rng(seed, gen, ctx->gen_dev)};
+                make_rng(seed, gen, ctx->gen_dev), P_in};
   vary_kernel<<<(P + 127) / 128, 128, 0, ctx->stream>>>(vp);
   SR_CHECK_CUDA(ctx, cudaGetLastError());
   ctx->launches += 1;
+  return SR_OK;
+}
+
+sr_status sr_select_microcosm(sr_ctx *ctx, const double *fitness, int P_in, int P_out, int sample,
+                              double keep, uint64_t seed, uint64_t gen, int32_t *parents, double *threshold) {
+  using namespace sr;
+  if (!ctx) return SR_EINVAL;
+  if (P_in < 0 || P_out < 0 || sample < 1 || sample > MICRO_MAX_SAMPLE || !(keep > 0.0 && keep <= 1.0))
+    return fail(ctx, SR_EINVAL, "bad sr_select_microcosm arguments");
+  if (P_out == 0) return SR_OK;
+  if (P_in == 0) return fail(ctx, SR_EINVAL, "no parents to select from");
+  if (!fitness || !parents) return fail(ctx, SR_EINVAL, "NULL fitness or parents");
+  SR_CHECK_CUDA(ctx, cudaSetDevice(ctx->device));
+  double *tau = threshold;
+  if (!tau) {
+    sr_status st = ensure_workspace(ctx, 256);
+    if (st != SR_OK) return st;
+    tau = reinterpret_cast<double *>(ctx->ws);
+  }
+  int kq = (int)ceil(keep * (double)sample) - 1;
+  kq = kq < 0 ? 0 : (kq >= sample ? sample - 1 : kq);
+  const Rng rng = make_rng(seed, gen, ctx->gen_dev);
+  microcosm_sample_kernel<<<1, (sample + 31) / 32 * 32, 0, ctx->stream>>>(fitness, P_in, sample, kq, rng, tau);
+  microcosm_select_kernel<<<(2 * P_out + 255) / 256, 256, 0, ctx->stream>>>(fitness, P_in, P_out, rng, tau,
+                                                                             parents);
+  SR_CHECK_CUDA(ctx, cudaGetLastError());
+  ctx->launches += 2;
   return SR_OK;
 }
 

@@ -1,6 +1,9 @@
 """Device-resident generation loop: evaluate -> (optional) constant
-optimisation -> tournament -> variation, for one problem or a batch of
-independent problems, eager or captured once as a CUDA graph and replayed.
+optimisation -> selection (k-way tournament, or the paper's Monte-Carlo
+"microcosm" selection, Sec. 2.1.6) -> variation, for one problem or a batch
+of independent problems, eager or captured once as a CUDA graph and
+replayed.  A population schedule (the paper's variable population size,
+Sec. 2.1.7) changes the number of individuals between generations.
 
 Every step runs in libsr kernels; this module only orders the calls and owns
 the double-buffered population tensors (fixed capacity, no allocation inside
@@ -27,6 +30,20 @@ class EvolveConfig:
     var: binding.VarCfg = field(default_factory=binding.var_cfg)
     const_steps: int = 0                    # Adam steps on the constants per generation
     adam: binding.AdamCfg = field(default_factory=binding.adam_cfg)
+    selection: str = "tournament"           # or "microcosm" (Sec. 2.1.6)
+    keep: float = 0.5                       # microcosm: fraction of the population parents come from
+    sample: int = 100                       # microcosm: sample size (the paper's 100)
+    # population schedule: ((first generation, size), ...) in increasing
+    # generation order, e.g. ((0, 5_000_000), (20, 1_000_000)); None keeps
+    # the initial size.  The tournament can only keep or shrink the size.
+    schedule: tuple | None = None
+
+    def size_at(self, gen: int, initial: int) -> int:
+        size = initial
+        for g0, n in (self.schedule or ()):
+            if gen >= g0:
+                size = n
+        return size
 
 
 class Population:
@@ -34,15 +51,26 @@ class Population:
 
     def __init__(self, programs, lengths, consts, X, y, N: int, cfg: EvolveConfig):
         self.X, self.y, self.N, self.cfg = X, y, N, cfg
-        self.buf = [(programs, lengths, consts),
-                    (torch.empty_like(programs), torch.empty_like(lengths), torch.empty_like(consts))]
-        P, Lmax = programs.shape
+        P0, Lmax = programs.shape
+        P = max([P0] + [n for _, n in (cfg.schedule or ())])  # buffer capacity
+        if P == P0:
+            first = (programs, lengths, consts)
+        else:
+            first = (torch.zeros((P, Lmax), dtype=programs.dtype, device=programs.device),
+                     torch.ones(P, dtype=lengths.dtype, device=lengths.device),
+                     torch.zeros((P,) + tuple(consts.shape[1:]), dtype=consts.dtype, device=consts.device))
+            first[0][:P0].copy_(programs)
+            first[1][:P0].copy_(lengths)
+            first[2][:P0].copy_(consts)
+        self.buf = [first, tuple(torch.empty_like(t) for t in first)]
+        self.initial, self.size = P0, P0
         v = cfg.var
         # a random subtree longer than the programs can be is never wanted
         self.var = binding.VarCfg(v.p_cross, v.p_point, v.p_subtree, v.p_const, v.const_delta,
                                   min(v.max_subtree, Lmax), v.unary_ops)
-        rows = 2 if cfg.eval_kind == binding.SR_MSE_CORR else 1
-        self.fitness = torch.empty((rows, P), dtype=torch.float64, device=programs.device)
+        self.rows = 2 if cfg.eval_kind == binding.SR_MSE_CORR else 1
+        # [rows][size] contiguous for the current size (row 1 follows row 0)
+        self._fit = torch.empty(self.rows * P, dtype=torch.float64, device=programs.device)
         self.parents = torch.empty((P, 2), dtype=torch.int32, device=programs.device)
         if cfg.const_steps:
             K = consts.shape[1]
@@ -54,7 +82,20 @@ class Population:
 
     @property
     def current(self):
-        return self.buf[self.cur]
+        """The current generation: the first `size` rows of the active buffers."""
+        n = self.size
+        return tuple(t[:n] for t in self.buf[self.cur])
+
+    @property
+    def fitness(self):
+        """Fitness of the current generation, [rows, size] (row 0 MSE and row 1
+        1 - r^2 for SR_MSE_CORR)."""
+        return self._fit[: self.rows * self.size].view(self.rows, self.size)
+
+    def fitness_out(self):
+        """The buffer sr_eval writes: [2, size] for SR_MSE_CORR, else [size]."""
+        f = self.fitness
+        return f if self.cfg.eval_kind == binding.SR_MSE_CORR else f[0]
 
     def select_row(self):
         if self.cfg.eval_kind == binding.SR_MSE_CORR:
@@ -68,9 +109,11 @@ class Evolver:
     def __init__(self, ctx: binding.Context, pops: list[Population], batched: bool = False):
         self.ctx, self.pops, self.batched = ctx, pops, batched
         dev = pops[0].X.device
-        self.gen = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.gen = torch.zeros(1, dtype=torch.int64, device=dev)  # Philox generation (device)
+        self.host_gen = 0                                          # generations run (schedule)
         self.graph = None
         self.graph_gens = 0
+        self.graph_sizes = None
 
     # -- one generation, eager ------------------------------------------------
     def _evaluate(self):
@@ -79,22 +122,23 @@ class Evolver:
             for p in self.pops:
                 P_, L_, C_ = p.current
                 probs.append(binding.make_problem(P_, L_, C_, p.X, p.y, p.N, p.cfg.eval_kind,
-                                                  fitness=p.fitness if p.cfg.eval_kind == binding.SR_MSE_CORR
-                                                  else p.fitness[0]))
+                                                  fitness=p.fitness_out()))
             binding.sr_eval_batched(self.ctx, probs)
         else:
             for p in self.pops:
                 P_, L_, C_ = p.current
-                out = p.fitness if p.cfg.eval_kind == binding.SR_MSE_CORR else p.fitness[0]
+                out = p.fitness_out()
                 binding.sr_eval(self.ctx, P_, L_, C_, p.X, p.y, p.N, p.cfg.eval_kind, fitness=out)
 
     def _const_opt(self, p: Population):
         P_, L_, C_ = p.current
-        p.m.zero_()
-        p.v.zero_()
+        n = p.size
+        m, v, mse, grad = p.m[:n], p.v[:n], p.mse[:n], p.grad[:n]
+        m.zero_()
+        v.zero_()
         for t in range(1, p.cfg.const_steps + 1):
-            binding.sr_eval_grad(self.ctx, P_, L_, C_, p.X, p.y, p.N, mse=p.mse, dconst=p.grad)
-            binding.sr_adam_step(self.ctx, C_, p.grad, p.m, p.v, t, p.cfg.adam)
+            binding.sr_eval_grad(self.ctx, P_, L_, C_, p.X, p.y, p.N, mse=mse, dconst=grad)
+            binding.sr_adam_step(self.ctx, C_, grad, m, v, t, p.cfg.adam)
 
     def step(self):
         """One generation for every population (reads the generation from self.gen)."""
@@ -106,12 +150,22 @@ class Evolver:
             self._evaluate()
             for p in self.pops:
                 P_, L_, C_ = p.current
-                binding.sr_select_tournament(self.ctx, p.select_row(), p.cfg.tournament_k, p.cfg.seed, 0,
-                                             parents=p.parents)
-                binding.sr_vary(self.ctx, P_, L_, C_, p.parents, p.X.shape[0], p.var, p.cfg.seed, 0,
+                n_next = p.cfg.size_at(self.host_gen + 1, p.initial)
+                parents = p.parents[:n_next]
+                if p.cfg.selection == "microcosm":
+                    binding.sr_select_microcosm(self.ctx, p.select_row(), n_next, p.cfg.sample, p.cfg.keep,
+                                                p.cfg.seed, 0, parents=parents)
+                else:
+                    if n_next > p.size:
+                        raise ValueError("the tournament cannot grow the population; use microcosm")
+                    binding.sr_select_tournament(self.ctx, p.select_row(), p.cfg.tournament_k, p.cfg.seed, 0,
+                                                 parents=p.parents[: p.size])
+                binding.sr_vary(self.ctx, P_, L_, C_, parents, p.X.shape[0], p.var, p.cfg.seed, 0,
                                 out=p.buf[1 - p.cur])
                 p.cur = 1 - p.cur
+                p.size = n_next
             self.gen += 1
+            self.host_gen += 1
         finally:
             binding.sr_set_generation_source(self.ctx, None)
 
@@ -123,6 +177,11 @@ class Evolver:
         assert gens % 2 == 0
         self.step()
         torch.cuda.synchronize()
+        sizes = [p.size for p in self.pops]
+        for p in self.pops:
+            for g in range(self.host_gen, self.host_gen + gens + 1):
+                if p.cfg.size_at(g, p.initial) != p.size:
+                    raise ValueError("the population schedule changes size inside the captured window")
         stream = torch.cuda.Stream(device=self.gen.device)
         self.ctx.set_stream(stream)
         g = torch.cuda.CUDAGraph()
@@ -136,7 +195,8 @@ class Evolver:
         # capture recorded the launches but ran nothing: undo the host-side flips
         for p, c in zip(self.pops, cur0):
             p.cur = c
-        self.graph, self.graph_gens = g, gens
+        self.host_gen -= gens
+        self.graph, self.graph_gens, self.graph_sizes = g, gens, sizes
         return g
 
     def run(self, generations: int):
@@ -147,4 +207,13 @@ class Evolver:
             return
         assert generations % self.graph_gens == 0
         for _ in range(generations // self.graph_gens):
-            self.graph.replay()
+            window = range(self.host_gen, self.host_gen + self.graph_gens + 1)
+            if self.graph is not None and not any(p.cfg.size_at(g, p.initial) != s for p, s in
+                                                  zip(self.pops, self.graph_sizes) for g in window):
+                self.graph.replay()
+                self.host_gen += self.graph_gens
+                continue
+            # the schedule leaves the captured size: drop the graph, go on eagerly
+            self.graph = None
+            for _ in range(self.graph_gens):
+                self.step()

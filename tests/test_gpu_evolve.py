@@ -138,3 +138,50 @@ def test_vary_rejects_bad_arguments(ctx):
         binding.sr_vary(ctx, p, l, None, par, 1, binding.var_cfg(max_subtree=9), 0, 0)
     with pytest.raises(binding.SRError):
         binding.sr_select_tournament(ctx, torch.zeros(4, dtype=torch.float64, device="cuda"), 0, 0, 0)
+
+
+@pytest.mark.parametrize("P_in,P_out,S,keep", [(4099, 4099, 100, 0.5), (777, 2000, 1, 0.3), (3000, 100, 1024, 0.05),
+                                               (64, 64, 100, 1.0)])
+def test_microcosm_bit_exact(ctx, P_in, P_out, S, keep):
+    """Beagle's microcosm selection (Sec. 2.1.6) on the device equals the
+    oracle's: threshold and every parent, NaN fitness and P_out != P_in
+    included."""
+    rng = np.random.default_rng(P_in)
+    f = rng.normal(size=P_in)
+    f[rng.integers(0, P_in, P_in // 20)] = np.nan
+    f[rng.integers(0, P_in, 30)] = 0.125  # ties
+    fd = torch.from_numpy(f).cuda()
+    tau = torch.empty(1, dtype=torch.float64, device="cuda")
+    for seed, gen in [(5, 0), (2 ** 63 + 17, 2 ** 32 + 3)]:
+        got = binding.sr_select_microcosm(ctx, fd, P_out, S, keep, seed, gen, threshold=tau).cpu().numpy()
+        want, wtau = oracle.microcosm(f, P_out, S, keep, seed, gen)
+        assert float(tau.item()) == wtau
+        np.testing.assert_array_equal(got, want)
+
+
+def test_schedule_chain_bit_exact(ctx):
+    """A population schedule (sizes 300 -> 150 -> 420) with microcosm
+    selection: the device population equals the oracle's after every
+    generation (the oracle's fitness handed to both selections)."""
+    Lmax, K, nv, N = 40, 4, 3, 150
+    rng = np.random.default_rng(12)
+    X = inputs.random_X(rng, nv, N, 1.0, 5.0)
+    y = (X[0, :N].astype(np.float64) * X[1, :N] - X[2, :N]).astype(np.float32)
+    sizes = [300, 300, 300, 150, 150, 150, 420, 420, 420, 420]
+    prog_o, len_o, c_o = oracle.random_programs(300, 1, 20, K, nv, -5.0, 5.0, seed=8, stream=0)
+    pad = np.zeros((300, Lmax), np.uint8)
+    pad[:, :20] = prog_o
+    prog_o = pad
+    prog_d, len_d, c_d = (torch.from_numpy(a).cuda() for a in (prog_o, len_o, c_o))
+    for gen in range(len(sizes) - 1):
+        fit, _ = oracle.evaluate(prog_o, len_o, c_o, X, y, oracle.MSE, N)
+        n_next = sizes[gen + 1]
+        par_d = binding.sr_select_microcosm(ctx, torch.from_numpy(fit).cuda(), n_next, 100, 0.4, 31, gen)
+        par_o, _ = oracle.microcosm(fit, n_next, 100, 0.4, 31, gen)
+        np.testing.assert_array_equal(par_d.cpu().numpy(), par_o)
+        prog_d, len_d, c_d = binding.sr_vary(ctx, prog_d, len_d, c_d, par_d, nv, binding.var_cfg(), 31, gen)
+        prog_o, len_o, c_o = oracle.vary(prog_o, len_o, c_o, par_o, K, nv, seed=31, gen=gen)
+        assert prog_d.shape[0] == n_next == prog_o.shape[0]
+        np.testing.assert_array_equal(len_d.cpu().numpy(), len_o)
+        np.testing.assert_array_equal(prog_d.cpu().numpy(), prog_o)
+        np.testing.assert_array_equal(c_d.cpu().numpy().view(np.uint32), c_o.view(np.uint32))

@@ -95,3 +95,29 @@ def test_autotuner_picks_a_tile(ctx, tmp_path):
     fin = torch.isfinite(f_auto)
     assert torch.allclose(f_tuned[fin], f_auto[fin], rtol=1e-6)
     assert (tmp_path / "tiles.json").exists()
+
+
+def test_schedule_with_microcosm_and_graph(ctx):
+    """The paper's variable population size (Sec. 2.1.7) with microcosm
+    selection: sizes follow the schedule, a graph captured inside a window of
+    constant size replays, and replays stop (eager steps take over) where the
+    schedule changes size; eager and graph runs agree bit for bit."""
+    sched = ((0, 256), (6, 128), (10, 384))
+    cfg = EvolveConfig(selection="microcosm", keep=0.4, schedule=sched, eval_kind=binding.SR_MSE,
+                       select_kind=binding.SR_MSE)
+    eager = Evolver(ctx, [_pop(71, P=256, cfg=cfg)])
+    graph = Evolver(ctx, [_pop(71, P=256, cfg=cfg)])
+    sizes = []
+    for _ in range(14):
+        eager.step()
+        sizes.append(eager.pops[0].size)
+    assert sizes == [256] * 5 + [128] * 4 + [384] * 5
+    graph.capture(2)       # generation 1 eager, 2-3 captured
+    graph.run(12)          # replays until the size changes, then eager
+    graph.step()
+    torch.cuda.synchronize()
+    assert graph.host_gen == 14 and graph.pops[0].size == 384
+    _same(_state(eager.pops), _state(graph.pops))
+    P_, L_, _ = eager.pops[0].current
+    flags, _ = oracle.validate_all(P_.cpu().numpy(), L_.cpu().numpy(), 3, 4)
+    assert (flags == 0).all()

@@ -108,6 +108,92 @@ def test_tournament_exact_on_small_population():
             assert par[i, s] == best
 
 
+# ---------------------------------------------------------------- microcosm selection
+def _microcosm_by_hand(f, P_out, S, keep, seed, gen):
+    """Sec. 2.1.6 as specified: sample, quantile, first qualifying of up to 64
+    candidates, else the best of them -- written out with the Philox words."""
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    g = gen & 0xFFFFFFFF
+    P = len(f)
+    k = lambda v: np.inf if np.isnan(v) else v
+    smp = []
+    for j in range(S):
+        w = oracle.philox4x32_10([j // 4, 0, 11, g], key)[j % 4]
+        smp.append((k(f[(int(w) * P) >> 32]), j))
+    smp.sort()
+    kq = min(max(int(np.ceil(keep * S)) - 1, 0), S - 1)
+    tau = smp[kq][0]
+    par = np.empty((P_out, 2), np.int32)
+    for i in range(P_out):
+        for s in range(2):
+            cands = [(int(w) * P) >> 32 for r in range(16)
+                     for w in oracle.philox4x32_10([r, i, 12 + s, g], key)]
+            ok = [c for c in cands if k(f[c]) <= tau]
+            par[i, s] = ok[0] if ok else min(cands, key=lambda c: (k(f[c]), c))
+    return par, tau
+
+
+@pytest.mark.parametrize("P_in,P_out,S,keep,seed,gen", [
+    (53, 40, 100, 0.5, 7, 0),
+    (200, 333, 10, 0.2, 2 ** 40 + 1, 5),
+    (1000, 25, 1, 0.5, 3, 2 ** 33 + 9),      # one sample: tau is a random individual's fitness
+    (64, 64, 100, 1.0, 9, 1),               # keep everyone
+])
+def test_microcosm_matches_its_definition(P_in, P_out, S, keep, seed, gen):
+    rng = np.random.default_rng(P_in)
+    f = rng.normal(size=P_in)
+    f[rng.integers(0, P_in, 5)] = np.nan
+    par, tau = oracle.microcosm(f, P_out, S, keep, seed, gen)
+    want, wtau = _microcosm_by_hand(f, P_out, S, keep, seed, gen)
+    assert tau == wtau
+    np.testing.assert_array_equal(par, want)
+
+
+def test_microcosm_fallback_takes_the_best_candidate():
+    """A threshold below almost every individual: most children get the best
+    of their 64 candidates, and those are near the top of the population."""
+    P = 4096
+    f = np.arange(P, dtype=np.float64)
+    for seed in range(2000):  # find a sample whose single draw is in the best 0.5 %
+        par, tau = oracle.microcosm(f, 200, 1, 0.5, seed, 0)
+        if tau < 20:
+            break
+    assert tau < 20
+    want, _ = _microcosm_by_hand(f, 200, 1, 0.5, seed, 0)
+    np.testing.assert_array_equal(par, want)
+    assert np.median(f[par]) < 0.05 * P  # the best of 64 uniform draws
+
+
+def test_microcosm_statistics():
+    """The threshold's population fraction averages keep (a sample of 100
+    estimates the quantile); parents are uniform over the qualifying set and
+    never outside it."""
+    P = 2000
+    f = np.random.default_rng(1).permutation(P).astype(np.float64)
+    fracs, counts = [], np.zeros(P)
+    for gen in range(200):
+        par, tau = oracle.microcosm(f, 500, 100, 0.3, 11, gen)
+        fracs.append((f <= tau).mean())
+        assert (f[par] <= tau).all()
+        if gen < 50:
+            np.add.at(counts, par.ravel(), 1.0 / (f <= tau).sum())
+    assert abs(np.mean(fracs) - 0.3) < 0.01
+    assert 0.03 < np.std(fracs) < 0.07  # ~ sqrt(0.3 * 0.7 / 100)
+    # per-individual selection weight is flat across the qualifying ranks
+    top = np.argsort(f)[:400]
+    lo_half, hi_half = counts[top[:200]].mean(), counts[top[200:]].mean()
+    assert abs(lo_half - hi_half) < 0.1 * lo_half
+
+
+def test_microcosm_schedule_sizes():
+    """P_out need not equal P_in (a population schedule); every parent index
+    is inside the parent population."""
+    f = np.random.default_rng(2).normal(size=777)
+    for P_out in (1, 100, 777, 5000):
+        par, _ = oracle.microcosm(f, P_out, 100, 0.5, 4, 3)
+        assert par.shape == (P_out, 2) and par.min() >= 0 and par.max() < 777
+
+
 # ---------------------------------------------------------------- variation
 @pytest.fixture(scope="module")
 def pop():
