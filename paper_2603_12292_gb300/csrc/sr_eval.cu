@@ -13,7 +13,8 @@
 //      node the child that needs more stack is evaluated first (a reversed
 //      opcode keeps a - b and a / b exact when the right child goes first).
 //      The stack depth of any program is then at most floor(log2(leaves)) + 1
-//      (9 for 512 tokens), so a fixed 8 shared-memory slots always suffice.
+//      (9 for 512 tokens), so floor(log2((Lmax + 1) / 2)) shared-memory slots
+//      always suffice (6 for Lmax = 128; fewer slots, more warps per SM).
 //      A terminal evaluated second is fused into its binary operator
 //      ("top = top op x_j"), and every operand is resolved here (constant
 //      value, X row offset, stack-slot byte offset): the interpreter does no
@@ -74,12 +75,13 @@ struct EvalParams {
   float *yhat;             // predict: [P][ldy]
   long long ldy;
   int warp_bytes;          // shared memory per warp
+  int slots;               // stack slots per warp
   int score_M;             // Beagle scores: the maximum score per case
 };
 
 __host__ __device__ inline int warp_smem_bytes(int Lmax) {
   // stack slots | decoded code (8 bytes per token)
-  return DSM * SLOT_BYTES + ((Lmax * 8 + 15) / 16) * 16;
+  return slots_for(Lmax) * SLOT_BYTES + ((Lmax * 8 + 15) / 16) * 16;
 }
 
 // ---------------------------------------------------------------- operators
@@ -114,6 +116,7 @@ __device__ __forceinline__ DecodeArgs decode_args(const EvalParams &p) {
   a.s_need = p.s_need;
   a.s_task = p.s_task;
   a.ext_count = p.queue ? p.queue + 2 : nullptr;
+  a.max_slots = slots_for(p.Lmax);
   return a;
 }
 
@@ -340,11 +343,11 @@ struct WarpSmem {
   uint2 *code;      // this warp's copy of the program's code
 };
 
-__device__ __forceinline__ WarpSmem warp_smem(unsigned char *smem, int warp, int warp_bytes) {
+__device__ __forceinline__ WarpSmem warp_smem(unsigned char *smem, int warp, int warp_bytes, int slots) {
   unsigned char *wbase = smem + (size_t)warp * warp_bytes;
   WarpSmem w;
   w.stk = reinterpret_cast<char *>(wbase);
-  w.code = reinterpret_cast<uint2 *>(wbase + DSM * SLOT_BYTES);
+  w.code = reinterpret_cast<uint2 *>(wbase + slots * SLOT_BYTES);
   return w;
 }
 
@@ -514,7 +517,7 @@ __global__ void __launch_bounds__(WARPS * 32) eval_kernel(EvalParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (EXT && p.queue[2] == 0) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const WarpSmem w = warp_smem(smem, warp, p.warp_bytes);
+  const WarpSmem w = warp_smem(smem, warp, p.warp_bytes, p.slots);
   unsigned long long *q = p.queue + (EXT ? 1 : 0);
   for (;;) {
     unsigned long long item = 0;
@@ -565,6 +568,7 @@ struct BatchParams {
   long long total_items;
   unsigned long long *queue;
   int warp_bytes;
+  int slots;
 };
 
 __device__ __forceinline__ EvalParams view(const BatchProblem &q) {
@@ -617,7 +621,7 @@ __global__ void __launch_bounds__(WARPS * 32) eval_batched_kernel(const __grid_c
   extern __shared__ __align__(16) unsigned char smem[];
   if (EXT && b.queue[2] == 0) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const WarpSmem w = warp_smem(smem, warp, b.warp_bytes);
+  const WarpSmem w = warp_smem(smem, warp, b.warp_bytes, b.slots);
   unsigned long long *qc = b.queue + (EXT ? 1 : 0);
   for (;;) {
     unsigned long long item = 0;
@@ -1046,6 +1050,7 @@ sr_status launch_eval(sr_ctx *ctx, int mode, const uint8_t *programs, const int3
   ep.yhat = yhat;
   ep.ldy = ldy;
   ep.warp_bytes = warp_smem_bytes(Lmax);
+  ep.slots = slots_for(Lmax);
   ep.score_M = M;
 
   int grid_ext = 0;
@@ -1219,6 +1224,7 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
       bpar->total_items = items;
       bpar->queue = reinterpret_cast<unsigned long long *>(ctx->ws + off_q);
       bpar->warp_bytes = warp_smem_bytes(maxL);
+      bpar->slots = slots_for(maxL);
     }
     return cv.off;
   };

@@ -66,10 +66,10 @@ struct GradParams {
   int warp_bytes;
 };
 
-// shared memory of one warp: stack slots [DSM] | gradient sums and
-// compensations [2][K][32] | code [Lmax] | tape [tcap]
+// shared memory of one warp: stack slots [slots_for(Lmax)] | gradient sums
+// and compensations [2][K][32] | code [Lmax] | tape [tcap]
 __host__ __device__ inline int grad_fixed_bytes(int Lmax, int K) {
-  return DSM * GSLOT + 2 * K * 128 + ((Lmax * 8 + 15) / 16) * 16;
+  return slots_for(Lmax) * GSLOT + 2 * K * 128 + ((Lmax * 8 + 15) / 16) * 16;
 }
 
 __device__ __forceinline__ DecodeArgs grad_decode_args(const GradParams &p) {
@@ -89,6 +89,7 @@ __device__ __forceinline__ DecodeArgs grad_decode_args(const GradParams &p) {
   a.s_need = p.s_need;
   a.s_task = p.s_task;
   a.ext_count = nullptr;
+  a.max_slots = slots_for(p.Lmax);
   return a;
 }
 
@@ -250,9 +251,10 @@ __global__ void __launch_bounds__(GWARPS * 32) grad_kernel(GradParams p) {
   unsigned char *wb = smem + (size_t)warp * p.warp_bytes;
   GradWarp w;
   w.slot = reinterpret_cast<char *>(wb) + lane * 8;
-  w.gs = reinterpret_cast<float *>(wb + DSM * GSLOT);
+  const int slot_bytes = slots_for(p.Lmax) * GSLOT;
+  w.gs = reinterpret_cast<float *>(wb + slot_bytes);
   w.gc = w.gs + p.K * 32;
-  w.code = reinterpret_cast<uint2 *>(wb + DSM * GSLOT + 2 * p.K * 128);
+  w.code = reinterpret_cast<uint2 *>(wb + slot_bytes + 2 * p.K * 128);
   w.ts = reinterpret_cast<char *>(wb + grad_fixed_bytes(p.Lmax, p.K)) + lane * 8;
   const int gw = blockIdx.x * GWARPS + warp;
   w.tg = p.gtape ? p.gtape + (size_t)gw * (p.Lmax - p.tcap) * GSLOT + lane * 8 : nullptr;

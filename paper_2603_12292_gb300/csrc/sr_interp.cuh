@@ -20,6 +20,15 @@ namespace sr {
 constexpr int DSM = 8;
 static_assert(SR_MAX_LMAX <= 512, "8 slots cover programs of up to 512 tokens");
 
+// The slots programs of up to Lmax tokens can need: floor(log2(leaves)) with
+// leaves <= (Lmax + 1) / 2.  Kernels size their shared stack by it (6 slots
+// for Lmax = 128 instead of 8 -- more warps per SM).
+__host__ __device__ inline int slots_for(int Lmax) {
+  int leaves = (Lmax + 1) / 2, s = 0;
+  while ((2 << s) <= leaves) ++s;
+  return s < 1 ? 1 : (s > DSM ? DSM : s);
+}
+
 // Instruction (uint2):
 //   x bits 0..7   opcode
 //   x bits 8..23  byte offset of the stack slot it pushes to / pops from
@@ -88,6 +97,7 @@ struct DecodeArgs {
   uint8_t *s_need;          // scratch [P][Lmax]: stack need of each subtree
   int16_t *s_task;          // scratch [P][Lmax]: work stack
   unsigned long long *ext_count;  // programs with NCODE_EXT are counted here (or NULL)
+  int max_slots;            // stack slots the kernel provides (<= DSM)
 };
 
 __device__ __forceinline__ bool is_term(int v) {
@@ -172,7 +182,7 @@ __device__ inline void decode_one(const DecodeArgs &p, int prog) {
     const int cls = tok_class(v);
     if (cls == CLS_VAR || cls == CLS_CONST) {
       --sp;
-      if (d > DSM) {  // cannot happen (depth <= 9 for <= 512 tokens); never write past the slots
+      if (d > p.max_slots) {  // cannot happen for programs of <= Lmax tokens; never write past the slots
         p.flags[prog] = SR_PF_TOO_DEEP;
         p.ncode[prog] = 0;
         return;
