@@ -120,9 +120,10 @@ __device__ __forceinline__ DecodeArgs decode_args(const EvalParams &p) {
   return a;
 }
 
+// one warp per 32 programs, scratch in shared memory (decode_warp)
 __global__ void decode_kernel(EvalParams p) {
-  const int prog = blockIdx.x * blockDim.x + threadIdx.x;
-  if (prog < p.P) decode_one(decode_args(p), prog);
+  extern __shared__ __align__(16) unsigned char dsm[];
+  decode_warp(decode_args(p), p.P, dsm);
 }
 
 // ---------------------------------------------------------------- interpreter
@@ -952,7 +953,7 @@ void launch_mode(int mode, int grid, int smem, cudaStream_t s, const EvalParams 
 struct Plan {
   int grid, smem, chunk, nchunks;
   long long items;
-  size_t off_queue, off_flags, off_ncode, off_code, off_start, off_need, off_task, off_part, off_yc,
+  size_t off_queue, off_flags, off_ncode, off_code, off_part, off_yc,
       off_ych, off_ysum, bytes;
 };
 
@@ -977,9 +978,6 @@ sr_status make_plan(sr_ctx *ctx, int mode, int P, int Lmax, int N, Plan *pl) {
   pl->off_flags = cv.take((size_t)P * 4);
   pl->off_ncode = cv.take((size_t)P * 4);
   pl->off_code = cv.take(tokens * 8);
-  pl->off_start = cv.take(tokens * 2);
-  pl->off_need = cv.take(tokens);
-  pl->off_task = cv.take(tokens * 2);
   pl->off_part = cv.take((size_t)pl->items * PSTRIDE * 8);
   pl->off_yc = cv.take(align_up((size_t)N, STEP) * 4);
   pl->off_ych = cv.take((size_t)pl->nchunks * 16);
@@ -1043,9 +1041,9 @@ sr_status launch_eval(sr_ctx *ctx, int mode, const uint8_t *programs, const int3
   ep.flags = prog_flags ? prog_flags : reinterpret_cast<int32_t *>(ws + pl.off_flags);
   ep.code = reinterpret_cast<uint2 *>(ws + pl.off_code);
   ep.ncode = reinterpret_cast<int32_t *>(ws + pl.off_ncode);
-  ep.s_start = reinterpret_cast<int16_t *>(ws + pl.off_start);
-  ep.s_need = reinterpret_cast<uint8_t *>(ws + pl.off_need);
-  ep.s_task = reinterpret_cast<int16_t *>(ws + pl.off_task);
+  ep.s_start = nullptr;  // the warp decoder keeps its scratch in shared memory
+  ep.s_need = nullptr;
+  ep.s_task = nullptr;
   ep.queue = reinterpret_cast<unsigned long long *>(ws + pl.off_queue);
   ep.yhat = yhat;
   ep.ldy = ldy;
@@ -1058,7 +1056,12 @@ sr_status launch_eval(sr_ctx *ctx, int mode, const uint8_t *programs, const int3
   if (st != SR_OK) return st;
   SR_CHECK_CUDA(ctx, cudaMemsetAsync(ep.queue, 0, 3 * sizeof(unsigned long long), s));
   // one warp per block spreads the serial per-program decode over the SMs
-  decode_kernel<<<(P + 31) / 32, 32, 0, s>>>(ep);
+  static int decode_configured = 0;
+  if (!decode_configured) {
+    SR_CHECK_CUDA(ctx, cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    decode_configured = 1;
+  }
+  decode_kernel<<<(P + 31) / 32, 32, decode_smem_bytes(Lmax), s>>>(ep);
   ctx->launches += 1;
   double *ych = reinterpret_cast<double *>(ws + pl.off_ych);
   if (mode == MODE_CORR || mode == MODE_BOTH || mode == MODE_R4) {

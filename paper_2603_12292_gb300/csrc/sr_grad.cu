@@ -101,8 +101,8 @@ __device__ __forceinline__ DecodeArgs grad_decode_args(const GradParams &p) {
 }
 
 __global__ void grad_decode_kernel(GradParams p) {
-  const int prog = blockIdx.x * blockDim.x + threadIdx.x;
-  if (prog < p.P) decode_one(grad_decode_args(p), prog);
+  extern __shared__ __align__(16) unsigned char dsm[];
+  decode_warp(grad_decode_args(p), p.P, dsm);
 }
 
 // ---------------------------------------------------------------- float2 helpers
@@ -521,8 +521,7 @@ sr_status sr_eval_grad(sr_ctx *ctx, const uint8_t *programs, const int32_t *leng
   const size_t tokens = (size_t)P * Lmax;
   Carver cv;
   const size_t off_q = cv.take(256), off_f = cv.take((size_t)P * 4), off_nc = cv.take((size_t)P * 4),
-               off_code = cv.take(tokens * 8), off_start = cv.take(tokens * 2),
-               off_need = cv.take(tokens), off_task = cv.take(tokens * 2),
+               off_code = cv.take(tokens * 8),
                off_p = cv.take((size_t)items * GSTRIDE * 8),
                off_t = cv.take(Lmax > tcap ? (size_t)warps * (Lmax - tcap) * GSLOT : 0);
   sr_status st = ensure_workspace(ctx, cv.off);
@@ -547,16 +546,22 @@ sr_status sr_eval_grad(sr_ctx *ctx, const uint8_t *programs, const int32_t *leng
   gp.flags = prog_flags ? prog_flags : reinterpret_cast<int32_t *>(ws + off_f);
   gp.code = reinterpret_cast<uint2 *>(ws + off_code);
   gp.ncode = reinterpret_cast<int32_t *>(ws + off_nc);
-  gp.s_start = reinterpret_cast<int16_t *>(ws + off_start);
-  gp.s_need = reinterpret_cast<uint8_t *>(ws + off_need);
-  gp.s_task = reinterpret_cast<int16_t *>(ws + off_task);
+  gp.s_start = nullptr;  // the warp decoder keeps its scratch in shared memory
+  gp.s_need = nullptr;
+  gp.s_task = nullptr;
   gp.queue = reinterpret_cast<unsigned long long *>(ws + off_q);
   gp.gtape = Lmax > tcap ? ws + off_t : nullptr;
   gp.tcap = tcap;
   gp.warp_bytes = warp_bytes;
   cudaStream_t s = ctx->stream;
   SR_CHECK_CUDA(ctx, cudaMemsetAsync(gp.queue, 0, 8, s));
-  grad_decode_kernel<<<(P + 127) / 128, 128, 0, s>>>(gp);
+  static int decode_configured = 0;
+  if (!decode_configured) {
+    SR_CHECK_CUDA(ctx, cudaFuncSetAttribute(grad_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            227 * 1024));
+    decode_configured = 1;
+  }
+  grad_decode_kernel<<<(P + 31) / 32, 32, decode_smem_bytes(Lmax), s>>>(gp);
   grad_kernel<<<grid, GWARPS * 32, smem, s>>>(gp);
   SR_CHECK_CUDA(ctx, cudaGetLastError());
   GradFinal gf{gp.partials, gp.flags, P, N, K, nchunks, mse, dconst};

@@ -111,12 +111,14 @@ __device__ __forceinline__ uint2 with_operand(uint32_t x, int v, const float *cr
   return make_uint2(x | ((uint32_t)k << 24), __float_as_uint(crow[k]));
 }
 
-// Validation and scheduled decoding of program `prog` (one thread).
+// Validation and scheduled decoding of program `prog` (one thread), reading
+// its tokens from `tok` and using the scratch rows start / need / task (Lmax
+// entries each).
 // Flag rules: length outside [1, Lmax]; bad byte; variable / constant index
 // out of range; depth (running sum of +1 terminal, 0 unary or bad byte, -1
 // binary) below 1 after some token; final depth not 1.
-__device__ inline void decode_one(const DecodeArgs &p, int prog) {
-  const uint8_t *tok = p.programs + (size_t)prog * p.Lmax;
+__device__ inline void decode_one(const DecodeArgs &p, int prog, const uint8_t *tok, int16_t *start,
+                                  uint8_t *need, int16_t *task) {
   const int L = p.lengths[prog];
   int flags = 0;
   if (L < 1 || L > p.Lmax) {
@@ -139,9 +141,6 @@ __device__ inline void decode_one(const DecodeArgs &p, int prog) {
     p.ncode[prog] = 0;
     return;
   }
-  int16_t *start = p.s_start + (size_t)prog * p.Lmax;
-  uint8_t *need = p.s_need + (size_t)prog * p.Lmax;
-  int16_t *task = p.s_task + (size_t)prog * p.Lmax;
   int ext = 0;
   // pass 1, postfix order is bottom-up: subtree starts and stack needs
   // (terminal 1; unary as its child; binary max of the children, +1 on a tie)
@@ -232,6 +231,40 @@ __device__ inline void decode_one(const DecodeArgs &p, int prog) {
   }
   p.ncode[prog] = n | (ext ? NCODE_EXT : 0);
   if (ext && p.ext_count) atomicAdd(p.ext_count, 1ull);
+}
+
+// decode_one with the scratch of the global workspace
+__device__ inline void decode_one(const DecodeArgs &p, int prog) {
+  const size_t row = (size_t)prog * p.Lmax;
+  decode_one(p, prog, p.programs + row, p.s_start + row, p.s_need + row, p.s_task + row);
+}
+
+// Decoding by warps in shared memory: one warp per 32 programs.  The warp
+// first copies its programs' token rows (contiguous in global memory) with
+// coalesced loads, then every lane decodes one program with its scratch in
+// shared memory.  Row strides are padded (tokens and need: Lmax + 4 bytes,
+// start and task: Lmax + 2 entries) so that lanes working on the same token
+// index fall in different banks.  Dynamic shared memory: decode_smem_bytes.
+__host__ __device__ inline int decode_row_bytes(int Lmax) { return (Lmax + 4) * 2 + (Lmax + 2) * 4; }
+__host__ __device__ inline int decode_smem_bytes(int Lmax) { return 32 * decode_row_bytes(Lmax); }
+
+__device__ inline void decode_warp(const DecodeArgs &p, int P, unsigned char *smem) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int prog0 = (blockIdx.x * (blockDim.x >> 5) + warp) * 32;
+  if (prog0 >= P) return;
+  const int nprog = min(32, P - prog0);
+  const int Lt = p.Lmax + 4, Ls = p.Lmax + 2;
+  unsigned char *base = smem + (size_t)warp * decode_smem_bytes(p.Lmax);
+  uint8_t *toks = base;                                          // [32][Lt]
+  uint8_t *need = base + 32 * Lt;                                // [32][Lt]
+  int16_t *start = reinterpret_cast<int16_t *>(base + 64 * Lt);  // [32][Ls]
+  int16_t *task = start + 32 * Ls;                               // [32][Ls]
+  const uint8_t *src = p.programs + (size_t)prog0 * p.Lmax;
+  const int total = nprog * p.Lmax;
+  for (int b = lane; b < total; b += 32) toks[(b / p.Lmax) * Lt + b % p.Lmax] = src[b];
+  __syncwarp();
+  if (lane < nprog)
+    decode_one(p, prog0 + lane, toks + lane * Lt, start + lane * Ls, need + lane * Lt, task + lane * Ls);
 }
 
 // ---------------------------------------------------------------- operators (FP32)
