@@ -33,6 +33,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "GPop/s (nodes x cases / s) at 1 GB300 vs plain eval; % of FP32 issue peak"
 L2_BYTES = 129 * 1024 * 1024
+# eval_kernel<3, 0> on this workload, from one ncu --set full capture
+# (profiles/eval_kernel_paper-4096x100k.md): dram__bytes_read.sum +
+# dram__bytes_write.sum per launch, and smsp__issue_active
+EVAL_NCU = {"dram_bytes": 7.41e6 + 0.36e6, "issue_active": 0.804}
 
 
 def parse():
@@ -269,10 +273,13 @@ def run_ours(args, rank, world, local_rank):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = sms * 128 * sm_max * 1e6 / 1e9  # G lane-ops/s
     achieved = float(np.mean([n * pr.N / (ms / 1e3) / 1e9 for n, ms in zip(nodes, eval_ms)]))
+    # DRAM bytes per launch and issue-slot use of this kernel: one ncu capture
+    # of the same command (profiles/eval_kernel_paper-4096x100k.md)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GPop/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": EVAL_NCU["dram_bytes"] if args.ops == "base" else None,
                 "kernel": "eval_kernel (sr_eval SR_MSE_CORR)",
                 "eval_ms": float(np.mean(eval_ms)),
+                "issue_active_ncu": EVAL_NCU["issue_active"] if args.ops == "base" else None,
                 "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz ({src} max clock)"}
 
     # end to end through the public API with the population held on the host:
