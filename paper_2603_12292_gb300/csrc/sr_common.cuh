@@ -60,6 +60,10 @@ sr_status cuda_fail(sr_ctx *ctx, cudaError_t e, const char *what);
 // grow the workspace to at least `bytes` (refused during stream capture)
 sr_status ensure_workspace(sr_ctx *ctx, size_t bytes);
 bool stream_capturing(sr_ctx *ctx);
+// Let `kernel` use up to 227 KB of dynamic shared memory on the context's
+// device.  Function attributes belong to a device; this sets each (kernel,
+// device) pair once per process (thread-safe).
+sr_status allow_dynamic_smem(sr_ctx *ctx, const void *kernel);
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 

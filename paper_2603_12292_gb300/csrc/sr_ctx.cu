@@ -3,6 +3,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
+#include <utility>
+#include <vector>
+
 #include "sr_common.cuh"
 
 namespace sr {
@@ -25,6 +29,18 @@ bool stream_capturing(sr_ctx *ctx) {
   cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(ctx->stream, &st) != cudaSuccess) return false;
   return st != cudaStreamCaptureStatusNone;
+}
+
+sr_status allow_dynamic_smem(sr_ctx *ctx, const void *kernel) {
+  static std::mutex mu;
+  static std::vector<std::pair<const void *, int>> done;
+  std::lock_guard<std::mutex> lock(mu);
+  for (const auto &d : done)
+    if (d.first == kernel && d.second == ctx->device) return SR_OK;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute");
+  done.emplace_back(kernel, ctx->device);
+  return SR_OK;
 }
 
 sr_status ensure_workspace(sr_ctx *ctx, size_t bytes) {

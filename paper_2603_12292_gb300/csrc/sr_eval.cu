@@ -909,13 +909,8 @@ __global__ void finalize_batched_kernel(const __grid_constant__ BatchParams b) {
 // ---------------------------------------------------------------- host side
 template <int MODE, bool EXT>
 sr_status occupancy_grid(sr_ctx *ctx, int smem, int *grid) {
-  static int configured = 0;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(eval_kernel<MODE, EXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         227 * 1024);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute(eval_kernel)");
-    configured = 1;
-  }
+  sr_status st = allow_dynamic_smem(ctx, reinterpret_cast<const void *>(eval_kernel<MODE, EXT>));
+  if (st != SR_OK) return st;
   int nb = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_kernel<MODE, EXT>, WARPS * 32, smem);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
@@ -1056,11 +1051,8 @@ sr_status launch_eval(sr_ctx *ctx, int mode, const uint8_t *programs, const int3
   if (st != SR_OK) return st;
   SR_CHECK_CUDA(ctx, cudaMemsetAsync(ep.queue, 0, 3 * sizeof(unsigned long long), s));
   // one warp per block spreads the serial per-program decode over the SMs
-  static int decode_configured = 0;
-  if (!decode_configured) {
-    SR_CHECK_CUDA(ctx, cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    decode_configured = 1;
-  }
+  st = allow_dynamic_smem(ctx, reinterpret_cast<const void *>(decode_kernel));
+  if (st != SR_OK) return st;
   decode_kernel<<<(P + 31) / 32, 32, decode_smem_bytes(Lmax), s>>>(ep);
   ctx->launches += 1;
   double *ych = reinterpret_cast<double *>(ws + pl.off_ych);
@@ -1088,13 +1080,8 @@ sr_status launch_eval(sr_ctx *ctx, int mode, const uint8_t *programs, const int3
 // ---------------------------------------------------------------- batched host side
 template <bool EXT>
 sr_status batched_grid(sr_ctx *ctx, int smem, int *grid) {
-  static int configured = 0;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(eval_batched_kernel<EXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         227 * 1024);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute(eval_batched_kernel)");
-    configured = 1;
-  }
+  sr_status st = allow_dynamic_smem(ctx, reinterpret_cast<const void *>(eval_batched_kernel<EXT>));
+  if (st != SR_OK) return st;
   int nb = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_batched_kernel<EXT>, WARPS * 32, smem);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");

@@ -555,12 +555,8 @@ sr_status sr_eval_grad(sr_ctx *ctx, const uint8_t *programs, const int32_t *leng
   gp.warp_bytes = warp_bytes;
   cudaStream_t s = ctx->stream;
   SR_CHECK_CUDA(ctx, cudaMemsetAsync(gp.queue, 0, 8, s));
-  static int decode_configured = 0;
-  if (!decode_configured) {
-    SR_CHECK_CUDA(ctx, cudaFuncSetAttribute(grad_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            227 * 1024));
-    decode_configured = 1;
-  }
+  st = allow_dynamic_smem(ctx, reinterpret_cast<const void *>(grad_decode_kernel));
+  if (st != SR_OK) return st;
   grad_decode_kernel<<<(P + 31) / 32, 32, decode_smem_bytes(Lmax), s>>>(gp);
   grad_kernel<<<grid, GWARPS * 32, smem, s>>>(gp);
   SR_CHECK_CUDA(ctx, cudaGetLastError());
