@@ -158,14 +158,10 @@ __device__ __forceinline__ V8 ldX8(const float *xa, const float *xb, uint32_t of
   return V8{ldx4(xa + off), ldx4(xb + off)};
 }
 
-#ifndef SR_OUTLINE_MATH
-#define SR_OUTLINE_MATH 1
-#endif
 #ifndef SR_MATH_UNROLL
 #define SR_MATH_UNROLL 8
 #endif
 constexpr int MATH_UNROLL = SR_MATH_UNROLL;
-#if SR_OUTLINE_MATH
 // The costly operators (the FP32 math library routines and IEEE division)
 // live out of line, one copy each, so the interpreter's dispatch loop stays
 // small enough for the instruction cache; inside, SR_MATH_UNROLL values are
@@ -196,16 +192,47 @@ __device__ __noinline__ V8 cos8(V8 v) { return map8_unrolled(v, FCos()); }
 __device__ __noinline__ V8 exp8(V8 v) { return map8_unrolled(v, FExp()); }
 __device__ __noinline__ V8 log8(V8 v) { return map8_unrolled(v, FLog()); }
 __device__ __noinline__ V8 sqrt8(V8 v) { return map8_unrolled(v, FSqrt()); }
-// The rest of Table 1 goes through one out-of-line entry, so the hot
-// dispatch switch keeps the size it has for the base operators.
+// The EXT instantiation of the interpreter (programs that use 1/x, tan, asin,
+// acos, atan, tanh) runs twelve library routines: unrolled 8-wide they no
+// longer fit the instruction cache (ncu: 26 cycles per issue stalled on
+// instruction fetch, 23 % of issue slots used).  There the extended routines
+// run one case at a time and the base ones two at a time: 707 -> 1,380
+// GPop/s on a Table 1 population; the base instantiation keeps its 8-wide
+// copies.
+template <typename F>
+__device__ __forceinline__ V8 map8_small(V8 v, F f) {
+  float t[8] = {v.a.x, v.a.y, v.a.z, v.a.w, v.b.x, v.b.y, v.b.z, v.b.w};
+#pragma unroll 1
+  for (int i = 0; i < 8; ++i) t[i] = f(t[i]);
+  return V8{make_float4(t[0], t[1], t[2], t[3]), make_float4(t[4], t[5], t[6], t[7])};
+}
+template <typename F>
+__device__ __forceinline__ V8 map8_base_small(V8 v, F f) {  // 2 in flight
+  float t[8] = {v.a.x, v.a.y, v.a.z, v.a.w, v.b.x, v.b.y, v.b.z, v.b.w};
+#pragma unroll 2
+  for (int i = 0; i < 8; ++i) t[i] = f(t[i]);
+  return V8{make_float4(t[0], t[1], t[2], t[3]), make_float4(t[4], t[5], t[6], t[7])};
+}
+__device__ __noinline__ V8 sin8s(V8 v) { return map8_base_small(v, FSin()); }
+__device__ __noinline__ V8 cos8s(V8 v) { return map8_base_small(v, FCos()); }
+__device__ __noinline__ V8 exp8s(V8 v) { return map8_base_small(v, FExp()); }
+__device__ __noinline__ V8 log8s(V8 v) { return map8_base_small(v, FLog()); }
+__device__ __noinline__ V8 sqrt8s(V8 v) { return map8_base_small(v, FSqrt()); }
+__device__ __noinline__ V8 div8s(V8 a, V8 b) {
+  float x[8] = {a.a.x, a.a.y, a.a.z, a.a.w, a.b.x, a.b.y, a.b.z, a.b.w};
+  const float y[8] = {b.a.x, b.a.y, b.a.z, b.a.w, b.b.x, b.b.y, b.b.z, b.b.w};
+#pragma unroll 2
+  for (int i = 0; i < 8; ++i) x[i] = op_div(x[i], y[i]);
+  return V8{make_float4(x[0], x[1], x[2], x[3]), make_float4(x[4], x[5], x[6], x[7])};
+}
 __device__ __noinline__ V8 ext8(uint32_t op, V8 v) {
   switch (op) {
-    case OP_INV: return map8_unrolled(v, FInv());
-    case OP_TAN: return map8_unrolled(v, FTan());
-    case OP_ASIN: return map8_unrolled(v, FAsin());
-    case OP_ACOS: return map8_unrolled(v, FAcos());
-    case OP_ATAN: return map8_unrolled(v, FAtan());
-    default: return map8_unrolled(v, FTanh());
+    case OP_INV: return map8_small(v, FInv());
+    case OP_TAN: return map8_small(v, FTan());
+    case OP_ASIN: return map8_small(v, FAsin());
+    case OP_ACOS: return map8_small(v, FAcos());
+    case OP_ATAN: return map8_small(v, FAtan());
+    default: return map8_small(v, FTanh());
   }
 }
 __device__ __noinline__ V8 div8(V8 a, V8 b) {
@@ -222,25 +249,6 @@ __device__ __noinline__ V8 div8(V8 a, V8 b) {
 #define SQRT8(v) sqrt8(v)
 #define DIV8(p, q) div8(p, q)
 #define EXT8(op, v) ext8(op, v)
-#else
-#define SIN8(v) MAP8(f_sin, v)
-#define COS8(v) MAP8(f_cos, v)
-#define EXP8(v) MAP8(op_exp, v)
-#define LOG8(v) MAP8(op_log, v)
-#define SQRT8(v) MAP8(f_sqrt, v)
-#define DIV8(p, q) ZIP8(op_div, p, q)
-__device__ __forceinline__ V8 ext8_inline(uint32_t op, V8 v) {
-  switch (op) {
-    case OP_INV: return MAP8(op_inv, v);
-    case OP_TAN: return MAP8(f_tan, v);
-    case OP_ASIN: return MAP8(f_asin, v);
-    case OP_ACOS: return MAP8(f_acos, v);
-    case OP_ATAN: return MAP8(f_atan, v);
-    default: return MAP8(f_tanh, v);
-  }
-}
-#define EXT8(op, v) ext8_inline(op, v)
-#endif
 
 // Runs the decoded program for this lane's 8 cases.  xa / xb point at the
 // lane's first and second case group in row 0 of X; `stk` at this lane's
@@ -261,14 +269,14 @@ __device__ __forceinline__ V8 interpret(const uint2 *__restrict__ code, int n, c
       case OP_ADD: { const V8 a = ld8(stk, off); T = ZIP8(f_add, a, T); } break;
       case OP_SUB: { const V8 a = ld8(stk, off); T = ZIP8(f_sub, a, T); } break;
       case OP_MUL: { const V8 a = ld8(stk, off); T = ZIP8(f_mul, a, T); } break;
-      case OP_DIV: { const V8 a = ld8(stk, off); T = DIV8(a, T); } break;
+      case OP_DIV: { const V8 a = ld8(stk, off); T = EXT ? div8s(a, T) : DIV8(a, T); } break;
       case OP_RSUB: { const V8 b = ld8(stk, off); T = ZIP8(f_sub, T, b); } break;
-      case OP_RDIV: { const V8 b = ld8(stk, off); T = DIV8(T, b); } break;
-      case OP_SIN: T = SIN8(T); break;
-      case OP_COS: T = COS8(T); break;
-      case OP_EXP: T = EXP8(T); break;
-      case OP_LOG: T = LOG8(T); break;
-      case OP_SQRT: T = SQRT8(T); break;
+      case OP_RDIV: { const V8 b = ld8(stk, off); T = EXT ? div8s(T, b) : DIV8(T, b); } break;
+      case OP_SIN: T = EXT ? sin8s(T) : SIN8(T); break;
+      case OP_COS: T = EXT ? cos8s(T) : COS8(T); break;
+      case OP_EXP: T = EXT ? exp8s(T) : EXP8(T); break;
+      case OP_LOG: T = EXT ? log8s(T) : LOG8(T); break;
+      case OP_SQRT: T = EXT ? sqrt8s(T) : SQRT8(T); break;
       case OP_SQ: T = MAP8(f_sq, T); break;
       case OP_INV:
       case OP_TAN:
@@ -281,15 +289,15 @@ __device__ __forceinline__ V8 interpret(const uint2 *__restrict__ code, int n, c
       case OP_VADD: { const V8 v = ldX8(xa, xb, w.y); T = ZIP8(f_add, T, v); } break;
       case OP_VSUB: { const V8 v = ldX8(xa, xb, w.y); T = ZIP8(f_sub, T, v); } break;
       case OP_VMUL: { const V8 v = ldX8(xa, xb, w.y); T = ZIP8(f_mul, T, v); } break;
-      case OP_VDIV: { const V8 v = ldX8(xa, xb, w.y); T = DIV8(T, v); } break;
+      case OP_VDIV: { const V8 v = ldX8(xa, xb, w.y); T = EXT ? div8s(T, v) : DIV8(T, v); } break;
       case OP_VRSUB: { const V8 v = ldX8(xa, xb, w.y); T = ZIP8(f_sub, v, T); } break;
-      case OP_VRDIV: { const V8 v = ldX8(xa, xb, w.y); T = DIV8(v, T); } break;
+      case OP_VRDIV: { const V8 v = ldX8(xa, xb, w.y); T = EXT ? div8s(v, T) : DIV8(v, T); } break;
       case OP_CADD: { const V8 v = splat8(__uint_as_float(w.y)); T = ZIP8(f_add, T, v); } break;
       case OP_CSUB: { const V8 v = splat8(__uint_as_float(w.y)); T = ZIP8(f_sub, T, v); } break;
       case OP_CMUL: { const V8 v = splat8(__uint_as_float(w.y)); T = ZIP8(f_mul, T, v); } break;
-      case OP_CDIV: { const V8 v = splat8(__uint_as_float(w.y)); T = DIV8(T, v); } break;
+      case OP_CDIV: { const V8 v = splat8(__uint_as_float(w.y)); T = EXT ? div8s(T, v) : DIV8(T, v); } break;
       case OP_CRSUB: { const V8 v = splat8(__uint_as_float(w.y)); T = ZIP8(f_sub, v, T); } break;
-      case OP_CRDIV: { const V8 v = splat8(__uint_as_float(w.y)); T = DIV8(v, T); } break;
+      case OP_CRDIV: { const V8 v = splat8(__uint_as_float(w.y)); T = EXT ? div8s(v, T) : DIV8(v, T); } break;
       default: break;
     }
   }
