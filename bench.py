@@ -609,7 +609,8 @@ def run_workload(args, local_rank):
                     value=1e3 / t_g, unit="generations/s", ms_per_step=t_g, scaling="weak",
                     config={"workload": pr.name}, eager_generations_per_s=1e3 / t_e,
                     graph_gpops=n / (t_g / 1e3) / 1e9, graph_over_eager=t_e / t_g)
-    print(json.dumps(line), flush=True)
+    if int(os.environ.get("RANK", "0")) == 0:
+        print(json.dumps(line), flush=True)
     ctx.close()
     return 0
 
@@ -628,6 +629,10 @@ def main():
             return run_reference(args, rank, world)
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
+        try:
+            return run_ours(args, rank, world, local_rank)
+        finally:
+            dist.destroy_process_group()
     if args.impl == "reference":
         return run_reference(args, rank, world)
     return run_ours(args, rank, world, local_rank)
