@@ -138,8 +138,11 @@ def run_reference(args, rank, world):
     from paper_2603_12292_gb300 import inputs
     if rank != 0:
         return 0
-    pr = inputs.paper_shaped(unary_ops=12 if args.ops == "table1" else 6)
-    y64 = oracle.predict(pr.target, pr.target_consts, pr.X, pr.N)
+    for attempt in range(20):  # the same usable-target rule as our arm
+        pr = inputs.paper_shaped(attempt=attempt, unary_ops=12 if args.ops == "table1" else 6)
+        y64 = oracle.predict(pr.target, pr.target_consts, pr.X, pr.N)
+        if np.all(np.isfinite(y64)) and np.abs(y64).max() < 1e15 and np.std(y64) > 1e-6 * (1 + np.abs(y64).max()):
+            break
     y = inputs.add_noise(np.random.default_rng(pr.seed + 7), y64, pr.noise)
     cores = os.cpu_count() or 1
     # size each step to ~4 s of CPU work: programs sampled from the population, all cases
@@ -190,16 +193,9 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
 
     nun = 12 if args.ops == "table1" else 6
-    pr = inputs.paper_shaped(unary_ops=nun)
-    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-    programs, lengths, consts, X = t(pr.programs), t(pr.lengths), t(pr.consts), t(pr.X)
     # the target on the device with the library's own predict, then 1% noise (host, FP64)
-    tgt = np.zeros((1, pr.Lmax), np.uint8)
-    tgt[0, : len(pr.target)] = pr.target
-    yhat = binding.sr_predict(ctx, t(tgt), t(np.array([len(pr.target)], np.int32)),
-                              t(pr.target_consts[None, :]), X, pr.N)
-    y = torch.from_numpy(inputs.add_noise(np.random.default_rng(pr.seed + 7),
-                                          yhat[0].double().cpu().numpy(), pr.noise)).to(dev)
+    pr, programs, lengths, consts, X, y = _device_problem(
+        lambda a: inputs.paper_shaped(attempt=a, unary_ops=nun), dev, binding, ctx)
     binding.sr_reserve(ctx, pr.P, pr.Lmax, pr.N)
     fitness = torch.empty((2, pr.P), dtype=torch.float64, device=dev)
     parents = torch.empty((pr.P, 2), dtype=torch.int32, device=dev)
@@ -384,22 +380,29 @@ def _timed(fn, reps, stream):
     return a.elapsed_time(b) / reps
 
 
-def _device_problem(pr, dev, binding, ctx, noise_seed=7):
-    """Device copies of a problem with y from the library's own predict of
-    the target (plus the problem's noise, FP64 on the host)."""
+def _device_problem(make, dev, binding, ctx, noise_seed=7):
+    """A problem from make(attempt) whose target, evaluated by the library's
+    own predict, is finite, not constant and below 1e15 in magnitude (the
+    recipe redraws with the next attempt otherwise), and its device copies
+    with y = that output plus the problem's noise (FP64 on the host).
+    Returns (problem, programs, lengths, consts, X, y)."""
     import torch
     from paper_2603_12292_gb300 import inputs
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-    X = t(pr.X)
-    tgt = np.zeros((1, max(pr.Lmax, len(pr.target))), np.uint8)
-    tgt[0, : len(pr.target)] = pr.target
-    yh = binding.sr_predict(ctx, t(tgt), t(np.array([len(pr.target)], np.int32)),
-                            t(pr.target_consts[None, :]), X, pr.N)[0].double().cpu().numpy()
-    if not np.all(np.isfinite(yh)):
-        yh = np.nan_to_num(yh, nan=0.0, posinf=1e6, neginf=-1e6)
+    for attempt in range(20):
+        pr = make(attempt)
+        X = t(pr.X)
+        tgt = np.zeros((1, max(pr.Lmax, len(pr.target))), np.uint8)
+        tgt[0, : len(pr.target)] = pr.target
+        yh = binding.sr_predict(ctx, t(tgt), t(np.array([len(pr.target)], np.int32)),
+                                t(pr.target_consts[None, :]), X, pr.N)[0, : pr.N].double().cpu().numpy()
+        if np.all(np.isfinite(yh)) and np.abs(yh).max() < 1e15 and np.std(yh) > 1e-6 * (1 + np.abs(yh).max()):
+            break
+    else:
+        raise RuntimeError(f"no usable target for {pr.name}")
     y = inputs.add_noise(np.random.default_rng(pr.seed + noise_seed), yh, pr.noise) if pr.noise \
         else yh.astype(np.float32)
-    return t(pr.programs), t(pr.lengths), t(pr.consts), X, t(y)
+    return pr, t(pr.programs), t(pr.lengths), t(pr.consts), X, t(y)
 
 
 def run_workload(args, local_rank):
@@ -421,8 +424,8 @@ def run_workload(args, local_rank):
         shapes = inputs.batched_shapes()[: 8 if args.small else None]
         pops, work = [], 0.0
         for sh in shapes:
-            pr = inputs.batched_problem(sh)
-            pg, ln, cs, X, y = _device_problem(pr, dev, binding, ctx)
+            pr, pg, ln, cs, X, y = _device_problem(lambda a, sh=sh: inputs.batched_problem(sh, attempt=a),
+                                                   dev, binding, ctx)
             kind = binding.SR_CORR if sh["kind"] else binding.SR_MSE
             cfg = EvolveConfig(select_kind=kind, eval_kind=kind)
             pops.append(Population(pg, ln, cs, X, y, pr.N, cfg))
@@ -460,8 +463,9 @@ def run_workload(args, local_rank):
                     batched_over_plain=t_plain / t_batch,
                     generation_graph_ms=t_graph, eval_batched_ms=t_batch, eval_plain_loop_ms=t_plain)
     elif args.workload == "adjoint":
-        pr = inputs.adjoint(P=2048, N=131072) if args.small else inputs.adjoint()
-        pg, ln, cs, X, y = _device_problem(pr, dev, binding, ctx)
+        pr, pg, ln, cs, X, y = _device_problem(
+            lambda a: inputs.adjoint(attempt=a, P=2048, N=131072) if args.small else inputs.adjoint(attempt=a),
+            dev, binding, ctx)
         P, K, N = pr.P, pr.K, pr.N
         mse = torch.empty(P, dtype=torch.float64, device=dev)
         g = torch.empty((P, K), dtype=torch.float64, device=dev)
@@ -500,8 +504,9 @@ def run_workload(args, local_rank):
                     grad_gpops=nodes / (t_adj / 1e3) / 1e9,
                     fd_steps_per_s=1e3 / t_fd, adjoint_over_fd=t_fd / t_adj)
     elif args.workload == "large":
-        pr = inputs.large(P=16384, N=131072) if args.small else inputs.large()
-        pg, ln, cs, X, y = _device_problem(pr, dev, binding, ctx)
+        pr, pg, ln, cs, X, y = _device_problem(
+            lambda a: inputs.large(attempt=a, P=16384, N=131072) if args.small else inputs.large(attempt=a),
+            dev, binding, ctx)
         sched = None
         if args.schedule:
             w0 = max(1, args.warmup)
@@ -530,8 +535,8 @@ def run_workload(args, local_rank):
                             "selection": args.selection, "population_sizes": sizes})
     elif args.workload == "beagle":
         nun = 12 if args.ops == "table1" else 6
-        pr = inputs.paper_shaped(unary_ops=nun)
-        pg, ln, cs, X, y = _device_problem(pr, dev, binding, ctx)
+        pr, pg, ln, cs, X, y = _device_problem(lambda a: inputs.paper_shaped(attempt=a, unary_ops=nun),
+                                               dev, binding, ctx)
         # 1 % invalid targets (NaN, +inf, -inf in turn) at seeded cases
         bad = np.sort(np.random.default_rng(pr.seed + 11).choice(pr.N, pr.N // 100, replace=False))
         yv = y.clone()
@@ -589,8 +594,7 @@ def run_workload(args, local_rank):
                     r4_eval_gpops=n_cur / (t_r4 / 1e3) / 1e9, p2p_eval_gpops=n_cur / (t_p2p / 1e3) / 1e9,
                     mse_corr_eval_gpops=n_cur / (t_both / 1e3) / 1e9)
     else:  # plain: launch-bound, CUDA graph vs eager
-        pr = inputs.plain()
-        pg, ln, cs, X, y = _device_problem(pr, dev, binding, ctx)
+        pr, pg, ln, cs, X, y = _device_problem(lambda a: inputs.plain(attempt=a), dev, binding, ctx)
         pe = Population(pg.clone(), ln.clone(), cs.clone(), X, y, pr.N,
                         EvolveConfig(select_kind=binding.SR_MSE, eval_kind=binding.SR_MSE))
         pgr = Population(pg.clone(), ln.clone(), cs.clone(), X, y, pr.N,

@@ -272,3 +272,21 @@ def test_full_size_paper_shaped_sampled(ctx):
         errb, cfl, f0 = oracle.condition(pr.programs[idx], pr.lengths[idx], pr.consts[idx], pr.X, y,
                                          kind, pr.N)
         assert check_fitness(kind, f[row, idx], f0, errb, cfl, y) >= 12
+
+
+def test_full_size_large_sampled(ctx):
+    """262,144 programs of length <= 256 x 1,000,000 cases (the large
+    workload and its launch configuration), 1 - r^2: sampled programs
+    against the oracle on every case.  Long programs over 10^6 cases mostly
+    reach values whose FP32 moment sums may overflow (flagged, not
+    compared), so the sample is drawn from the programs of <= 24 tokens."""
+    pr, y = target_problem(inputs.large)  # the usable target the bench uses (attempt 1)
+    d = dev(pr, y)
+    f = binding.sr_eval(ctx, d["programs"], d["lengths"], d["consts"], d["X"], d["y"], pr.N, binding.SR_CORR)
+    torch.cuda.synchronize()
+    f = f.cpu().numpy()
+    short = np.nonzero(pr.lengths <= 24)[0]
+    idx = np.sort(np.random.default_rng(5).choice(short, 24, replace=False))
+    errb, cfl, f0 = oracle.condition(pr.programs[idx], pr.lengths[idx], pr.consts[idx], pr.X, y, oracle.CORR,
+                                     pr.N)
+    assert check_fitness(oracle.CORR, f[idx], f0, errb, cfl, y) >= 6

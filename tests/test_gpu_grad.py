@@ -190,3 +190,27 @@ def test_invalid_programs_in_gradient(ctx):
     assert np.isinf(mse[0].item()) and g[0, 0].item() == 0.0
     assert flags.cpu().tolist() == [oracle.PF_UNDERFLOW | oracle.PF_BAD_FINAL, 0]
     assert mse[1].item() == 0.0 and g[1, 0].item() == 0.0
+
+
+def test_full_size_adjoint_sampled(ctx):
+    """16,384 programs x 1,000,000 cases, K = 8 (the adjoint workload and the
+    launch configuration the bench times): sampled programs against the
+    oracle's forward-mode gradient on every case.  Over 10^6 cases nearly
+    every program with a protected operator has some case next to a switch
+    point, so the sample is drawn from the short programs (<= 16 tokens)."""
+    pr = inputs.adjoint()
+    y = oracle.predict(pr.target, pr.target_consts, pr.X, pr.N)
+    y = inputs.add_noise(np.random.default_rng(3), y, 0.01)
+    d = dev(pr, y)
+    mse_g, g_g = binding.sr_eval_grad(ctx, d["programs"], d["lengths"], d["consts"], d["X"], d["y"], pr.N)
+    mse_g, g_g = mse_g.cpu().numpy(), g_g.cpu().numpy()
+    short = np.nonzero(pr.lengths <= 16)[0]
+    idx = np.sort(np.random.default_rng(4).choice(short, 48, replace=False))
+    sub = (pr.programs[idx], pr.lengths[idx], pr.consts[idx])
+    mse_o, g_o, kink, gabs = oracle.grad(*sub, pr.X, y, pr.N)
+    errb, cfl, f0 = oracle.condition(*sub, pr.X, y, oracle.MSE, pr.N)
+    well = (cfl == 0) & np.isfinite(f0) & (errb <= 1e-5 * np.abs(f0)) & (kink > 1e-3)
+    assert well.sum() >= 8
+    bad = well[:, None] & ~(np.abs(g_g[idx] - g_o) <= 2e-4 * gabs + 1e-12)
+    assert not bad.any(), (np.argwhere(bad)[:5], g_g[idx][bad][:5], g_o[bad][:5])
+    np.testing.assert_allclose(mse_g[idx][well], mse_o[well], rtol=1e-5)
