@@ -36,7 +36,26 @@ L2_BYTES = 129 * 1024 * 1024
 # eval_kernel<3, 0> on this workload, from one ncu --set full capture
 # (profiles/eval_kernel_paper-4096x100k.md): dram__bytes_read.sum +
 # dram__bytes_write.sum per launch, and smsp__issue_active
-EVAL_NCU = {"dram_bytes": 7.41e6 + 0.36e6, "issue_active": 0.804}
+EVAL_NCU = {"dram_bytes": 7.45e6 + 0.51e6, "issue_active": 0.811}
+# the other workloads' dominant kernels, each from one ncu --set full capture
+# (profiles/): the captured workload, DRAM bytes (read + write) of the
+# captured launch, the units (node-evaluations) it processed, and
+# smsp__issue_active.  Traffic is reported for the captured workload, and for
+# another size only where it grows with the units (scale).
+KERNEL_NCU = {
+    # grad_kernel: the tape write-back evicted from L2 grows with the units
+    "grad": {"workload": "adjoint-2048x131072", "dram_bytes": 0.282e9 + 9.761e9, "units": 1.3324e10,
+             "issue_active": 0.819, "scale": True},
+    # eval_kernel<R4>: inputs read once (L2-resident), at the full size
+    "beagle": {"workload": "beagle-4096x100k", "dram_bytes": 6.935e6 + 0.515e6, "units": 2.3977e10,
+               "issue_active": 0.692, "scale": False},
+    # eval_batched_kernel: the first 8 problems; inputs read once
+    "batched": {"workload": "batched-8", "dram_bytes": 44.33e6 + 0.88e6, "units": 4.0723e11,
+                "issue_active": 0.747, "scale": False},
+    # eval_kernel<CORR> at Lmax 256: inputs read once
+    "large": {"workload": "large-16384x131072", "dram_bytes": 20.72e6 + 0.52e6, "units": 2.5087e11,
+              "issue_active": 0.729, "scale": False},
+}
 
 
 def parse():
@@ -380,6 +399,51 @@ def _timed(fn, reps, stream):
     return a.elapsed_time(b) / reps
 
 
+def _alu_peak(dev):
+    """FP32 lane-op peak of the device: SMs x 128 lanes x the measured max SM clock."""
+    import torch
+    pk, src = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    return sms * 128 * sm_max * 1e-3, f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz ({src} max clock)"
+
+
+def _roofline(dev, achieved, kernel, timing, workload, ncu_key=None, units_per_launch=None):
+    """ALU roofline of a workload's dominant kernel.  achieved: GPop/s of that
+    kernel from CUDA events; traffic: DRAM bytes per launch from its ncu
+    capture (scaled by units where it grows with them), else null."""
+    peak, src = _alu_peak(dev)
+    cap = KERNEL_NCU.get(ncu_key) if ncu_key else None
+    same = cap is not None and workload.split(":")[0] == cap["workload"]
+    traffic = None
+    if cap is not None and (same or cap["scale"]):
+        traffic = cap["dram_bytes"] * (units_per_launch / cap["units"] if units_per_launch else 1.0)
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GPop/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": kernel, "timing": timing,
+            "issue_active_ncu": cap["issue_active"] if same else None, "peak_source": src}
+
+
+class _Region:
+    """Clock samples and the library's launch count over a timed region."""
+
+    def __init__(self, binding, ctx, index):
+        self.binding, self.ctx, self.sampler = binding, ctx, ClockSampler(index)
+
+    def __enter__(self):
+        import torch
+        torch.cuda.synchronize()
+        self.sampler.start()
+        self.l0 = self.binding.sr_kernel_launches(self.ctx)
+        return self
+
+    def __exit__(self, *exc):
+        import torch
+        torch.cuda.synchronize()
+        self.launches = int(self.binding.sr_kernel_launches(self.ctx) - self.l0)
+        self.clocks = self.sampler.stop()
+        return False
+
+
 def _device_problem(make, dev, binding, ctx, noise_seed=7):
     """A problem from make(attempt) whose target, evaluated by the library's
     own predict, is finite, not constant and below 1e15 in magnitude (the
@@ -447,17 +511,25 @@ def run_workload(args, local_rank):
         t_batch = _timed(batched, args.steps, stream)
         # (c) the whole generation loop, batched and captured as a CUDA graph
         ev = Evolver(ctx, pops, batched=True)
+        l0 = binding.sr_kernel_launches(ctx)
+        ev.step()  # one eager generation: the launches a replayed generation makes
+        per_gen = binding.sr_kernel_launches(ctx) - l0
         ev.capture(2)
         torch.cuda.synchronize()
         gens = 2 * max(1, args.steps // 2)
         n_gen = nodes()
-        t_graph = _timed(lambda: ev.run(gens), 1, stream) / gens
+        with _Region(binding, ctx, local_rank) as region:
+            t_graph = _timed(lambda: ev.run(gens), 1, stream) / gens
         line.update(metric=f"GPop/s, {len(shapes)} problems per generation (batched + graph vs plain loop)",
                     value=n_gen / (t_graph / 1e3) / 1e9, unit="GPop/s", ms_per_step=t_graph,
                     scaling="weak",
                     config={"workload": f"batched-{len(shapes)}: nvars 1-10, N log-uniform 1k-1M, P 512-8192, "
                                         "L 4-256, MSE/1-r^2 mixed",
                             "problems": len(pops), "node_cases_per_eval": n0},
+                    roofline=_roofline(dev, n0 / (t_batch / 1e3) / 1e9, "eval_batched_kernel (sr_eval_batched)",
+                                       "one batched evaluation, CUDA events over a loop of calls",
+                                       f"batched-{len(shapes)}", "batched", n0),
+                    clocks=region.clocks, gpu_launches=int(per_gen * gens),
                     batched_eval_gpops=n0 / (t_batch / 1e3) / 1e9,
                     plain_loop_eval_gpops=n0 / (t_plain / 1e3) / 1e9,
                     batched_over_plain=t_plain / t_batch,
@@ -472,9 +544,15 @@ def run_workload(args, local_rank):
         m, v = torch.zeros_like(g), torch.zeros_like(g)
         cfg = binding.adam_cfg()
         state = {"t": 0}
-        def adam_step():
+        grad_ev = []
+        def adam_step(record=False):
             state["t"] += 1
+            if record:
+                grad_ev.append((torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)))
+                grad_ev[-1][0].record(stream)
             binding.sr_eval_grad(ctx, pg, ln, cs, X, y, N, mse=mse, dconst=g)
+            if record:
+                grad_ev[-1][1].record(stream)
             binding.sr_adam_step(ctx, cs, g, m, v, state["t"], cfg)
         # plain alternative: central differences with 2K + 1 plain evaluations
         f0 = torch.empty(P, dtype=torch.float64, device=dev)
@@ -494,14 +572,20 @@ def run_workload(args, local_rank):
         for _ in range(max(1, args.warmup)):
             adam_step()
         steps = max(1, args.steps)
-        t_adj = _timed(adam_step, steps, stream)
+        with _Region(binding, ctx, local_rank) as region:
+            t_adj = _timed(lambda: adam_step(True), steps, stream)
+        grad_ms = float(np.mean([a.elapsed_time(b) for a, b in grad_ev]))
         fd_step()  # untimed: first-call costs of the plain path stay out of the comparison
         t_fd = _timed(fd_step, 1, stream)
         nodes = float(ln.sum()) * N
         line.update(metric="constant-optimisation steps/s (adjoint + Adam) vs plain finite differences",
                     value=1e3 / t_adj, unit="steps/s", ms_per_step=t_adj, scaling="weak",
                     config={"workload": f"{pr.name}: K=8, L<=96, 5 vars, Adam"},
-                    grad_gpops=nodes / (t_adj / 1e3) / 1e9,
+                    roofline=_roofline(dev, nodes / (grad_ms / 1e3) / 1e9, "grad_kernel (sr_eval_grad)",
+                                       "sr_eval_grad call inside each timed Adam step, CUDA events",
+                                       pr.name, "grad", nodes),
+                    clocks=region.clocks, gpu_launches=region.launches,
+                    grad_ms=grad_ms, grad_gpops=nodes / (t_adj / 1e3) / 1e9,
                     fd_steps_per_s=1e3 / t_fd, adjoint_over_fd=t_fd / t_adj)
     elif args.workload == "large":
         pr, pg, ln, cs, X, y = _device_problem(
@@ -519,20 +603,29 @@ def run_workload(args, local_rank):
         torch.cuda.synchronize()
         steps = max(1, args.steps)
         ms, nodes, sizes = [], [], []
-        for _ in range(steps):
-            nodes.append(float(ev.pops[0].current[1].sum()) * pr.N)
-            sizes.append(ev.pops[0].size)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            ev.step()
-            b.record(stream)
-            b.synchronize()
-            ms.append(a.elapsed_time(b))
+        ev.eval_events = []
+        with _Region(binding, ctx, local_rank) as region:
+            for _ in range(steps):
+                nodes.append(float(ev.pops[0].current[1].sum()) * pr.N)
+                sizes.append(ev.pops[0].size)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ev.step()
+                b.record(stream)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+        eval_ms = [a.elapsed_time(b) for a, b in ev.eval_events]
         line.update(metric="GPop/s (nodes x cases / s), one generation (1-r^2, selection, variation)",
                     value=sum(nodes) / (sum(ms) / 1e3) / 1e9, unit="GPop/s", ms_per_step=sum(ms) / steps,
                     scaling="weak",
                     config={"workload": pr.name, "programs": pr.P, "cases": pr.N, "lengths": "4-256",
-                            "selection": args.selection, "population_sizes": sizes})
+                            "selection": args.selection, "population_sizes": sizes},
+                    roofline=_roofline(dev, float(np.mean([n / (t / 1e3) / 1e9 for n, t in zip(nodes, eval_ms)])),
+                                       "eval_kernel (sr_eval SR_CORR)",
+                                       "sr_eval call inside each timed generation, CUDA events",
+                                       pr.name, "large", float(np.mean(nodes))),
+                    clocks=region.clocks, gpu_launches=region.launches,
+                    eval_ms=float(np.mean(eval_ms)))
     elif args.workload == "beagle":
         nun = 12 if args.ops == "table1" else 6
         pr, pg, ln, cs, X, y = _device_problem(lambda a: inputs.paper_shaped(attempt=a, unary_ops=nun),
@@ -551,11 +644,18 @@ def run_workload(args, local_rank):
         pop = [(pg, ln, cs), (torch.empty_like(pg), torch.empty_like(ln), torch.empty_like(cs))]
         state = {"gen": 0, "cur": 0}
 
-        def generation():
+        score_ev = []
+
+        def generation(record=False):
             g, cur = state["gen"], state["cur"]
             P_, L_, C_ = pop[cur]
+            if record:
+                score_ev.append((torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)))
+                score_ev[-1][0].record(stream)
             binding.sr_eval_score(ctx, P_, L_, C_, X, yv, pr.N, binding.SR_SCORE_R4, M, score=score,
                                   pair_counts=counts)
+            if record:
+                score_ev[-1][1].record(stream)
             binding.sr_select_tournament_max(ctx, score, 4, SEED, g, parents=parents)
             binding.sr_vary(ctx, P_, L_, C_, parents, pr.nvars, vcfg, SEED, g, out=pop[1 - cur])
             state["gen"], state["cur"] = g + 1, 1 - cur
@@ -565,15 +665,17 @@ def run_workload(args, local_rank):
         torch.cuda.synchronize()
         steps = max(1, args.steps)
         ms, nodes = [], []
-        for _ in range(steps):
-            nodes.append(float(pop[state["cur"]][1].sum()) * pr.N)
-            flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            generation()
-            b.record(stream)
-            b.synchronize()
-            ms.append(a.elapsed_time(b))
+        with _Region(binding, ctx, local_rank) as region:
+            for _ in range(steps):
+                nodes.append(float(pop[state["cur"]][1].sum()) * pr.N)
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                generation(record=True)
+                b.record(stream)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+        score_ms = [a.elapsed_time(b) for a, b in score_ev]
         # evaluation alone on the current population: Eq. 2, Eq. 3, and MSE + 1 - r^2
         P_, L_, C_ = pop[state["cur"]]
         n_cur = float(L_.sum()) * pr.N
@@ -591,6 +693,12 @@ def run_workload(args, local_rank):
                                         "1% invalid targets, M = 1000",
                             "step": "sr_eval_score(R4) + sr_select_tournament_max(k=4) + sr_vary",
                             "l2": "flushed between timed generations"},
+                    roofline=_roofline(dev, float(np.mean([n / (t / 1e3) / 1e9 for n, t in zip(nodes, score_ms)])),
+                                       "eval_kernel (sr_eval_score SR_SCORE_R4)",
+                                       "sr_eval_score call inside each timed generation, CUDA events",
+                                       f"beagle-4096x100k{'-table1' if nun == 12 else ''}", "beagle",
+                                       float(np.mean(nodes))),
+                    clocks=region.clocks, gpu_launches=region.launches,
                     r4_eval_gpops=n_cur / (t_r4 / 1e3) / 1e9, p2p_eval_gpops=n_cur / (t_p2p / 1e3) / 1e9,
                     mse_corr_eval_gpops=n_cur / (t_both / 1e3) / 1e9)
     else:  # plain: launch-bound, CUDA graph vs eager
@@ -602,16 +710,30 @@ def run_workload(args, local_rank):
         eager, graph = Evolver(ctx, [pe]), Evolver(ctx, [pgr])
         for _ in range(max(3, args.warmup)):
             eager.step()
+        l0 = binding.sr_kernel_launches(ctx)
+        eager.step()  # one eager generation: the launches a replayed generation makes
+        per_gen = binding.sr_kernel_launches(ctx) - l0
         graph.capture(2)
         graph.run(4)
         torch.cuda.synchronize()
         gens = 2 * max(5, args.steps)
         t_e = _timed(lambda: [eager.step() for _ in range(gens)], 1, stream) / gens
-        t_g = _timed(lambda: graph.run(gens), 1, stream) / gens
+        gens_g = 2 * max(1000, args.steps)  # long enough for the clock sampler
+        with _Region(binding, ctx, local_rank) as region:
+            t_g = _timed(lambda: graph.run(gens_g), 1, stream) / gens_g
         n = float(pgr.current[1].sum()) * pr.N
+        P_, L_, C_ = pgr.current
+        f1 = torch.empty(pr.P, dtype=torch.float64, device=dev)
+        t_eval = _timed(lambda: binding.sr_eval(ctx, P_, L_, C_, X, y, pr.N, binding.SR_MSE, fitness=f1),
+                        gens, stream)
         line.update(metric="generations/s, 256 x 1k (CUDA graph vs eager launches)",
                     value=1e3 / t_g, unit="generations/s", ms_per_step=t_g, scaling="weak",
-                    config={"workload": pr.name}, eager_generations_per_s=1e3 / t_e,
+                    config={"workload": pr.name},
+                    roofline=_roofline(dev, n / (t_eval / 1e3) / 1e9, "eval_kernel (sr_eval SR_MSE)",
+                                       "sr_eval calls in a loop, CUDA events; launch-bound at 1,000 cases",
+                                       pr.name),
+                    clocks=region.clocks, gpu_launches=int(per_gen * gens_g),
+                    eager_generations_per_s=1e3 / t_e,
                     graph_gpops=n / (t_g / 1e3) / 1e9, graph_over_eager=t_e / t_g)
     if int(os.environ.get("RANK", "0")) == 0:
         print(json.dumps(line), flush=True)

@@ -142,14 +142,15 @@ class Context:
     def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
         self.device = device
         h = ctypes.c_void_p()
-        s = (stream or torch.cuda.current_stream(device)).cuda_stream
-        st = lib().sr_create(ctypes.byref(h), device, ctypes.c_void_p(s))
+        self.stream = stream or torch.cuda.current_stream(device)  # where every call is enqueued
+        st = lib().sr_create(ctypes.byref(h), device, ctypes.c_void_p(self.stream.cuda_stream))
         if st != SR_OK:
             raise SRError(st, lib().sr_status_string(st).decode())
         self.handle = h
 
     def set_stream(self, stream: torch.cuda.Stream):
         _check(self, lib().sr_set_stream(self.handle, ctypes.c_void_p(stream.cuda_stream)))
+        self.stream = stream
 
     def close(self):
         if getattr(self, "handle", None):

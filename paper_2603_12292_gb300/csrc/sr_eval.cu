@@ -48,7 +48,15 @@ constexpr int CPL = 8;          // cases per lane per dispatched instruction (tw
 constexpr int STEP = 32 * CPL;  // cases per warp step
 constexpr int SLOT_BYTES = 32 * CPL * 4;  // one stack slot of a warp: [2][32 lanes] float4
 constexpr int PSTRIDE = 8;      // doubles per partial record
-constexpr int TARGET_ITEMS_PER_WARP = 8;
+constexpr int TARGET_ITEMS_PER_WARP = 20;  // balances the launch tail; measured best of 8 to 28 at 4,096 x 100k
+// Occupancy variants of the evaluation kernel: MINB CTAs of WARPS warps per
+// SM.  Shared memory per CTA that leaves room for MINB of them (228 KB per
+// SM, 1 KB of it reserved per CTA); the registers are bounded to match
+// (5 CTAs: 48 registers).  Measured on 4,096 programs x 100,000 cases
+// (Lmax 128): 5 CTAs with 4 stack slots 2,579 -> 2,649 GPop/s, Table 1
+// operators 1,432 -> 1,592; at Lmax 256 the 48-register bound costs more than
+// it gives (2,810 -> 2,625), so there it stays at 4 CTAs.
+__host__ __device__ constexpr int smem_target(int minb) { return minb == 5 ? 45568 : 57344; }
 
 enum Mode { MODE_PREDICT = 0, MODE_MSE = 1, MODE_CORR = 2, MODE_BOTH = 3, MODE_R4 = 4, MODE_P2P = 5 };
 
@@ -71,17 +79,40 @@ struct EvalParams {
   int16_t *s_start;        // decode scratch [P][Lmax]: first token of each subtree
   uint8_t *s_need;         // decode scratch [P][Lmax]: stack need of each subtree
   int16_t *s_task;         // decode scratch [P][Lmax]: work stack
-  unsigned long long *queue;  // [0] work counter, [1] work counter of the EXT pass, [2] EXT programs
+  // [0] work counter, [1] work counter of the EXT pass, [2] EXT programs,
+  // [3] work counter of the deep pass, [4] deep programs
+  unsigned long long *queue;
   float *yhat;             // predict: [P][ldy]
   long long ldy;
   int warp_bytes;          // shared memory per warp
   int slots;               // stack slots per warp
+  int deep;                // 1: this launch is the pass of the NCODE_DEEP programs
   int score_M;             // Beagle scores: the maximum score per case
 };
 
-__host__ __device__ inline int warp_smem_bytes(int Lmax) {
+__host__ __device__ inline int code_smem_bytes(int Lmax) { return ((Lmax * 8 + 15) / 16) * 16; }
+
+__host__ __device__ inline int warp_smem_bytes(int slots, int Lmax) {
   // stack slots | decoded code (8 bytes per token)
-  return slots_for(Lmax) * SLOT_BYTES + ((Lmax * 8 + 15) / 16) * 16;
+  return slots * SLOT_BYTES + code_smem_bytes(Lmax);
+}
+
+// Stack slots of the main evaluation passes: as many as fit smem_target(minb),
+// at most slots_for(Lmax) and at least min(slots_for(Lmax), 4).  Programs of
+// up to 256 tokens, random or evolved, rarely need more than 4 (Sethi-Ullman
+// order) while slots_for(256) = 7 would leave room for only 3 CTAs per SM;
+// the few that need more than the main passes give (NCODE_DEEP) run in a
+// third pass with slots_for(Lmax) slots.
+__host__ __device__ inline int shallow_slots(int Lmax, int minb) {
+  const int full = slots_for(Lmax), lo = full < 4 ? full : 4;
+  const int s = (smem_target(minb) / WARPS - code_smem_bytes(Lmax)) / SLOT_BYTES;
+  return s < lo ? lo : (s > full ? full : s);
+}
+
+// 5 CTAs per SM where they fit with at least min(slots_for(Lmax), 4) slots
+// (Lmax <= 200), else 4.
+inline int minb_for(int Lmax) {
+  return WARPS * warp_smem_bytes(shallow_slots(Lmax, 5), Lmax) <= smem_target(5) ? 5 : 4;
 }
 
 // ---------------------------------------------------------------- operators
@@ -99,7 +130,9 @@ __device__ __forceinline__ float4 ldx4(const float *p) {
 }
 
 // ---------------------------------------------------------------- decode pre-pass
-__device__ __forceinline__ DecodeArgs decode_args(const EvalParams &p) {
+// cap_slots: programs that need more get NCODE_DEEP, counted in deep_count
+__device__ __forceinline__ DecodeArgs decode_args(const EvalParams &p, int cap_slots,
+                                                  unsigned long long *deep_count) {
   DecodeArgs a;
   a.programs = p.programs;
   a.lengths = p.lengths;
@@ -117,13 +150,15 @@ __device__ __forceinline__ DecodeArgs decode_args(const EvalParams &p) {
   a.s_task = p.s_task;
   a.ext_count = p.queue ? p.queue + 2 : nullptr;
   a.max_slots = slots_for(p.Lmax);
+  a.cap_slots = cap_slots;
+  a.deep_count = deep_count;
   return a;
 }
 
 // one warp per 32 programs, scratch in shared memory (decode_warp)
 __global__ void decode_kernel(EvalParams p) {
   extern __shared__ __align__(16) unsigned char dsm[];
-  decode_warp(decode_args(p), p.P, dsm);
+  decode_warp(decode_args(p, p.slots, p.queue + 4), p.P, dsm);
 }
 
 // ---------------------------------------------------------------- interpreter
@@ -346,6 +381,40 @@ __device__ __forceinline__ int p2p_case(float yh, float y, int M, float Mf, floa
   return (int)rintf(v);
 }
 
+// Eq. 2 sums over one lane's 8 cases (nvalid of them inside the chunk):
+// pairs with both values finite give the moments of the shifted output d
+// and the centred target e; one invalid value counts in n1, both in n2.
+// Out of line: the copy inside the interpreter loop measured 1.7 % slower.
+struct R4Part { float s1, s2, s3, s4, s5; int n1, n2; };
+__device__ __noinline__ R4Part r4_part(V8 T, float4 ya, float4 yb, int nvalid, float shift) {
+  const float tv[CPL] = {T.a.x, T.a.y, T.a.z, T.a.w, T.b.x, T.b.y, T.b.z, T.b.w};
+  const float yv[CPL] = {ya.x, ya.y, ya.z, ya.w, yb.x, yb.y, yb.z, yb.w};
+  float d[CPL], e[CPL];
+  int c1 = 0, c2 = 0;
+#pragma unroll
+  for (int i = 0; i < CPL; ++i) {
+    const bool ok = i < nvalid;
+    const bool vh = isfinite(tv[i]), vy = isfinite(yv[i]);
+    const bool pair = ok && vh && vy;
+    c1 += (ok && vh != vy) ? 1 : 0;
+    c2 += (ok && !vh && !vy) ? 1 : 0;
+    d[i] = pair ? tv[i] - shift : 0.0f;
+    e[i] = pair ? yv[i] : 0.0f;
+  }
+  R4Part r;
+  r.s1 = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7]));
+  r.s2 = ((d[0] * d[0] + d[1] * d[1]) + (d[2] * d[2] + d[3] * d[3])) +
+         ((d[4] * d[4] + d[5] * d[5]) + (d[6] * d[6] + d[7] * d[7]));
+  r.s3 = ((d[0] * e[0] + d[1] * e[1]) + (d[2] * e[2] + d[3] * e[3])) +
+         ((d[4] * e[4] + d[5] * e[5]) + (d[6] * e[6] + d[7] * e[7]));
+  r.s4 = ((e[0] + e[1]) + (e[2] + e[3])) + ((e[4] + e[5]) + (e[6] + e[7]));
+  r.s5 = ((e[0] * e[0] + e[1] * e[1]) + (e[2] * e[2] + e[3] * e[3])) +
+         ((e[4] * e[4] + e[5] * e[5]) + (e[6] * e[6] + e[7] * e[7]));
+  r.n1 = c1;
+  r.n2 = c2;
+  return r;
+}
+
 // ---------------------------------------------------------------- one work item
 struct WarpSmem {
   char *stk;        // shared stack slots of this warp, [DSM][2][32] float4
@@ -436,36 +505,30 @@ __device__ __forceinline__ void eval_item(const EvalParams &p, int c, int prog, 
         shift = fin ? __shfl_sync(FULL, T.a.x, __ffs(fin) - 1) : 0.0f;
       }
       const float4 ya = ldx4(p.yc + cl), yb = ldx4(p.yc + cl4);
-      const float yv[CPL] = {ya.x, ya.y, ya.z, ya.w, yb.x, yb.y, yb.z, yb.w};
-      float d[CPL], e[CPL];
-#pragma unroll
-      for (int i = 0; i < CPL; ++i) {
-        const bool vh = isfinite(tv[i]), vy = isfinite(yv[i]);
-        const bool pair = ok[i] && vh && vy;
-        c1 += (ok[i] && vh != vy) ? 1 : 0;
-        c2 += (ok[i] && !vh && !vy) ? 1 : 0;
-        d[i] = pair ? tv[i] - shift : 0.0f;
-        e[i] = pair ? yv[i] : 0.0f;
-      }
-      s1.add(((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])));
-      s2.add(((d[0] * d[0] + d[1] * d[1]) + (d[2] * d[2] + d[3] * d[3])) +
-             ((d[4] * d[4] + d[5] * d[5]) + (d[6] * d[6] + d[7] * d[7])));
-      s3.add(((d[0] * e[0] + d[1] * e[1]) + (d[2] * e[2] + d[3] * e[3])) +
-             ((d[4] * e[4] + d[5] * e[5]) + (d[6] * e[6] + d[7] * e[7])));
-      s4.add(((e[0] + e[1]) + (e[2] + e[3])) + ((e[4] + e[5]) + (e[6] + e[7])));
-      s5.add(((e[0] * e[0] + e[1] * e[1]) + (e[2] * e[2] + e[3] * e[3])) +
-             ((e[4] * e[4] + e[5] * e[5]) + (e[6] * e[6] + e[7] * e[7])));
+      const R4Part q = r4_part(T, ya, yb, cend - c0, shift);
+      s1.add(q.s1);
+      s2.add(q.s2);
+      s3.add(q.s3);
+      s4.add(q.s4);
+      s5.add(q.s5);
+      c1 += q.n1;
+      c2 += q.n2;
     }
     if (MODE == MODE_P2P) {
       const float4 ya = load_y4(p.y, cl, p.N), yb = load_y4(p.y, cl4, p.N);
-      const float yv[CPL] = {ya.x, ya.y, ya.z, ya.w, yb.x, yb.y, yb.z, yb.w};
-#pragma unroll
+      // one copy of the per-case body: the values rotate through it
+      float t0 = T.a.x, t1 = T.a.y, t2 = T.a.z, t3 = T.a.w, t4 = T.b.x, t5 = T.b.y, t6 = T.b.z, t7 = T.b.w;
+      float y0 = ya.x, y1 = ya.y, y2 = ya.z, y3 = ya.w, y4 = yb.x, y5 = yb.y, y6 = yb.z, y7 = yb.w;
+#pragma unroll 1
       for (int i = 0; i < CPL; ++i) {
-        if (!ok[i]) continue;
-        const bool vh = isfinite(tv[i]), vy = isfinite(yv[i]);
-        c1 += vh != vy ? 1 : 0;
-        c2 += (!vh && !vy) ? 1 : 0;
-        score += p2p_case(tv[i], yv[i], p.score_M, Mf, pen);
+        if (c0 + i < cend) {
+          const bool vh = isfinite(t0), vy = isfinite(y0);
+          c1 += vh != vy ? 1 : 0;
+          c2 += (!vh && !vy) ? 1 : 0;
+          score += p2p_case(t0, y0, p.score_M, Mf, pen);
+        }
+        t0 = t1; t1 = t2; t2 = t3; t3 = t4; t4 = t5; t5 = t6; t6 = t7;
+        y0 = y1; y1 = y2; y2 = y3; y3 = y4; y4 = y5; y5 = y6; y6 = y7;
       }
     }
   }
@@ -516,18 +579,22 @@ __device__ __forceinline__ void eval_item(const EvalParams &p, int c, int prog, 
 }
 
 // ---------------------------------------------------------------- single problem
-// Two passes over the work items: EXT = false takes the programs of the base
-// operators (and the invalid ones), EXT = true those that use 1/x, tan,
-// asin, acos, atan or tanh; it returns at once when the decoder counted
+// Up to three passes over the work items: EXT = false takes the programs of
+// the base operators (and the invalid ones), EXT = true those that use 1/x,
+// tan, asin, acos, atan or tanh; it returns at once when the decoder counted
 // none.  Keeping the extended operators out of the first kernel keeps its
-// loop (and its speed) what it is for the base operators.
-template <int MODE, bool EXT>
-__global__ void __launch_bounds__(WARPS * 32) eval_kernel(EvalParams p) {
+// loop (and its speed) what it is for the base operators.  Both give each
+// warp shallow_slots(Lmax, MINB) stack slots; the programs that need more
+// (NCODE_DEEP) run in a third launch of the EXT kernel with deep = 1 and
+// slots_for(Lmax) slots, made only when the two differ.
+template <int MODE, bool EXT, int MINB>
+__global__ void __launch_bounds__(WARPS * 32, MINB) eval_kernel(EvalParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
-  if (EXT && p.queue[2] == 0) return;
+  const bool deep = EXT && p.deep;  // the deep pass runs the EXT copy of the loop
+  if (deep ? p.queue[4] == 0 : (EXT && p.queue[2] == 0)) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const WarpSmem w = warp_smem(smem, warp, p.warp_bytes, p.slots);
-  unsigned long long *q = p.queue + (EXT ? 1 : 0);
+  unsigned long long *q = p.queue + (deep ? 3 : (EXT ? 1 : 0));
   for (;;) {
     unsigned long long item = 0;
     if (lane == 0) item = atomicAdd(q, 1ull);
@@ -535,7 +602,8 @@ __global__ void __launch_bounds__(WARPS * 32) eval_kernel(EvalParams p) {
     if ((long long)item >= p.total_items) break;
     const int c = (int)(item / (unsigned long long)p.P);
     const int prog = (int)(item % (unsigned long long)p.P);
-    if (ncode_ext(p.ncode[prog]) != EXT) continue;
+    const int nc = p.ncode[prog];
+    if (deep ? !ncode_deep(nc) : (nc & (NCODE_EXT | NCODE_DEEP)) != (EXT ? NCODE_EXT : 0)) continue;
     eval_item<MODE, EXT>(p, c, prog, w, lane, 3);
   }
 }
@@ -575,9 +643,10 @@ struct BatchParams {
   int ncorr;
   int total_progs;
   long long total_items;
-  unsigned long long *queue;
+  unsigned long long *queue;  // as EvalParams::queue
   int warp_bytes;
   int slots;
+  int deep;                   // as EvalParams::deep
 };
 
 __device__ __forceinline__ EvalParams view(const BatchProblem &q) {
@@ -618,20 +687,23 @@ __global__ void decode_batched_kernel(const __grid_constant__ BatchParams b) {
   }
   EvalParams p = view(b.prob[lo]);
   p.queue = b.queue;
-  decode_one(decode_args(p), g - b.prob[lo].prog_begin);
+  decode_one(decode_args(p, b.slots, b.queue + 4), g - b.prob[lo].prog_begin);
 }
 
 // Work items of every problem come from one atomic counter: problem q owns
 // items [item_begin_q, item_begin_q + P_q * nchunks_q), chunk-major inside.
-// EXT as for eval_kernel (the extended programs of every problem in a
-// second launch).
+// EXT and deep as for eval_kernel (the extended programs of every problem
+// in a second launch, the deep ones in a third).
+// At most 64 registers, so that 4 CTAs fit an SM (75 unbounded, 3 CTAs):
+// 2,608 -> 2,949 GPop/s on the 64-problem batch despite a few spilled values.
 template <bool EXT>
-__global__ void __launch_bounds__(WARPS * 32) eval_batched_kernel(const __grid_constant__ BatchParams b) {
+__global__ void __launch_bounds__(WARPS * 32, 4) eval_batched_kernel(const __grid_constant__ BatchParams b) {
   extern __shared__ __align__(16) unsigned char smem[];
-  if (EXT && b.queue[2] == 0) return;
+  const bool deep = EXT && b.deep;
+  if (deep ? b.queue[4] == 0 : (EXT && b.queue[2] == 0)) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const WarpSmem w = warp_smem(smem, warp, b.warp_bytes, b.slots);
-  unsigned long long *qc = b.queue + (EXT ? 1 : 0);
+  unsigned long long *qc = b.queue + (deep ? 3 : (EXT ? 1 : 0));
   for (;;) {
     unsigned long long item = 0;
     if (lane == 0) item = atomicAdd(qc, 1ull);
@@ -648,7 +720,8 @@ __global__ void __launch_bounds__(WARPS * 32) eval_batched_kernel(const __grid_c
     const long long local = (long long)item - q.item_begin;
     const int c = (int)(local / q.P);
     const int prog = (int)(local % q.P);
-    if (ncode_ext(q.ncode[prog]) != EXT) continue;
+    const int nc = q.ncode[prog];
+    if (deep ? !ncode_deep(nc) : (nc & (NCODE_EXT | NCODE_DEEP)) != (EXT ? NCODE_EXT : 0)) continue;
     const int want = q.mode == MODE_MSE ? 1 : (q.mode == MODE_CORR ? 2 : 3);
     eval_item<MODE_BOTH, EXT>(p, c, prog, w, lane, want);
   }
@@ -915,54 +988,69 @@ __global__ void finalize_batched_kernel(const __grid_constant__ BatchParams b) {
 }
 
 // ---------------------------------------------------------------- host side
-template <int MODE, bool EXT>
+template <int MODE, bool EXT, int MINB>
 sr_status occupancy_grid(sr_ctx *ctx, int smem, int *grid) {
-  sr_status st = allow_dynamic_smem(ctx, reinterpret_cast<const void *>(eval_kernel<MODE, EXT>));
+  sr_status st = allow_dynamic_smem(ctx, reinterpret_cast<const void *>(eval_kernel<MODE, EXT, MINB>));
   if (st != SR_OK) return st;
   int nb = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_kernel<MODE, EXT>, WARPS * 32, smem);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_kernel<MODE, EXT, MINB>, WARPS * 32, smem);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   if (nb < 1) return fail(ctx, SR_EINVAL, "Lmax too large for shared memory");
   *grid = nb * ctx->num_sms;
   return SR_OK;
 }
 
-template <bool EXT>
-sr_status grid_for_t(sr_ctx *ctx, int mode, int smem, int *grid) {
+template <bool EXT, int MINB>
+sr_status grid_for_m(sr_ctx *ctx, int mode, int smem, int *grid) {
   switch (mode) {
-    case MODE_PREDICT: return occupancy_grid<MODE_PREDICT, EXT>(ctx, smem, grid);
-    case MODE_MSE: return occupancy_grid<MODE_MSE, EXT>(ctx, smem, grid);
-    case MODE_CORR: return occupancy_grid<MODE_CORR, EXT>(ctx, smem, grid);
-    case MODE_R4: return occupancy_grid<MODE_R4, EXT>(ctx, smem, grid);
-    case MODE_P2P: return occupancy_grid<MODE_P2P, EXT>(ctx, smem, grid);
-    default: return occupancy_grid<MODE_BOTH, EXT>(ctx, smem, grid);
+    case MODE_PREDICT: return occupancy_grid<MODE_PREDICT, EXT, MINB>(ctx, smem, grid);
+    case MODE_MSE: return occupancy_grid<MODE_MSE, EXT, MINB>(ctx, smem, grid);
+    case MODE_CORR: return occupancy_grid<MODE_CORR, EXT, MINB>(ctx, smem, grid);
+    case MODE_R4: return occupancy_grid<MODE_R4, EXT, MINB>(ctx, smem, grid);
+    case MODE_P2P: return occupancy_grid<MODE_P2P, EXT, MINB>(ctx, smem, grid);
+    default: return occupancy_grid<MODE_BOTH, EXT, MINB>(ctx, smem, grid);
   }
 }
 
-sr_status grid_for(sr_ctx *ctx, int mode, int smem, int *grid) { return grid_for_t<false>(ctx, mode, smem, grid); }
+template <bool EXT>
+sr_status grid_for_t(sr_ctx *ctx, int mode, int minb, int smem, int *grid) {
+  return minb == 5 ? grid_for_m<EXT, 5>(ctx, mode, smem, grid) : grid_for_m<EXT, 4>(ctx, mode, smem, grid);
+}
+
+template <bool EXT, int MINB>
+void launch_mode_m(int mode, int grid, int smem, cudaStream_t s, const EvalParams &ep) {
+  switch (mode) {
+    case MODE_PREDICT: eval_kernel<MODE_PREDICT, EXT, MINB><<<grid, WARPS * 32, smem, s>>>(ep); break;
+    case MODE_MSE: eval_kernel<MODE_MSE, EXT, MINB><<<grid, WARPS * 32, smem, s>>>(ep); break;
+    case MODE_CORR: eval_kernel<MODE_CORR, EXT, MINB><<<grid, WARPS * 32, smem, s>>>(ep); break;
+    case MODE_R4: eval_kernel<MODE_R4, EXT, MINB><<<grid, WARPS * 32, smem, s>>>(ep); break;
+    case MODE_P2P: eval_kernel<MODE_P2P, EXT, MINB><<<grid, WARPS * 32, smem, s>>>(ep); break;
+    default: eval_kernel<MODE_BOTH, EXT, MINB><<<grid, WARPS * 32, smem, s>>>(ep); break;
+  }
+}
 
 template <bool EXT>
-void launch_mode(int mode, int grid, int smem, cudaStream_t s, const EvalParams &ep) {
-  switch (mode) {
-    case MODE_PREDICT: eval_kernel<MODE_PREDICT, EXT><<<grid, WARPS * 32, smem, s>>>(ep); break;
-    case MODE_MSE: eval_kernel<MODE_MSE, EXT><<<grid, WARPS * 32, smem, s>>>(ep); break;
-    case MODE_CORR: eval_kernel<MODE_CORR, EXT><<<grid, WARPS * 32, smem, s>>>(ep); break;
-    case MODE_R4: eval_kernel<MODE_R4, EXT><<<grid, WARPS * 32, smem, s>>>(ep); break;
-    case MODE_P2P: eval_kernel<MODE_P2P, EXT><<<grid, WARPS * 32, smem, s>>>(ep); break;
-    default: eval_kernel<MODE_BOTH, EXT><<<grid, WARPS * 32, smem, s>>>(ep); break;
-  }
+void launch_mode(int mode, int minb, int grid, int smem, cudaStream_t s, const EvalParams &ep) {
+  if (minb == 5) launch_mode_m<EXT, 5>(mode, grid, smem, s, ep);
+  else launch_mode_m<EXT, 4>(mode, grid, smem, s, ep);
 }
 
 struct Plan {
+  int minb;       // CTAs per SM of the main passes (eval_kernel's MINB)
+  int slots;      // stack slots per warp of the main passes
   int grid, smem, chunk, nchunks;
+  int smem_deep;  // shared memory of the deep pass (0: none)
   long long items;
   size_t off_queue, off_flags, off_ncode, off_code, off_part, off_yc,
       off_ych, off_ysum, bytes;
 };
 
 sr_status make_plan(sr_ctx *ctx, int mode, int P, int Lmax, int N, Plan *pl) {
-  pl->smem = WARPS * warp_smem_bytes(Lmax);
-  sr_status st = grid_for(ctx, mode, pl->smem, &pl->grid);
+  pl->minb = minb_for(Lmax);
+  pl->slots = shallow_slots(Lmax, pl->minb);
+  pl->smem = WARPS * warp_smem_bytes(pl->slots, Lmax);
+  pl->smem_deep = slots_for(Lmax) > pl->slots ? WARPS * warp_smem_bytes(slots_for(Lmax), Lmax) : 0;
+  sr_status st = grid_for_t<false>(ctx, mode, pl->minb, pl->smem, &pl->grid);
   if (st != SR_OK) return st;
   const long long warps = (long long)pl->grid * WARPS;
   const long long want = warps * TARGET_ITEMS_PER_WARP;
@@ -1050,14 +1138,19 @@ sr_status launch_eval(sr_ctx *ctx, int mode, const uint8_t *programs, const int3
   ep.queue = reinterpret_cast<unsigned long long *>(ws + pl.off_queue);
   ep.yhat = yhat;
   ep.ldy = ldy;
-  ep.warp_bytes = warp_smem_bytes(Lmax);
-  ep.slots = slots_for(Lmax);
+  ep.slots = pl.slots;
+  ep.warp_bytes = warp_smem_bytes(pl.slots, Lmax);
+  ep.deep = 0;
   ep.score_M = M;
 
-  int grid_ext = 0;
-  st = grid_for_t<true>(ctx, mode, pl.smem, &grid_ext);
+  int grid_ext = 0, grid_deep = 0;
+  st = grid_for_t<true>(ctx, mode, pl.minb, pl.smem, &grid_ext);
   if (st != SR_OK) return st;
-  SR_CHECK_CUDA(ctx, cudaMemsetAsync(ep.queue, 0, 3 * sizeof(unsigned long long), s));
+  if (pl.smem_deep) {
+    st = grid_for_t<true>(ctx, mode, 4, pl.smem_deep, &grid_deep);
+    if (st != SR_OK) return st;
+  }
+  SR_CHECK_CUDA(ctx, cudaMemsetAsync(ep.queue, 0, 5 * sizeof(unsigned long long), s));
   // one warp per block spreads the serial per-program decode over the SMs
   st = allow_dynamic_smem(ctx, reinterpret_cast<const void *>(decode_kernel));
   if (st != SR_OK) return st;
@@ -1072,10 +1165,18 @@ sr_status launch_eval(sr_ctx *ctx, int mode, const uint8_t *programs, const int3
                                                       const_cast<float *>(ep.yc), ych);
     ctx->launches += 2;
   }
-  launch_mode<false>(mode, pl.grid, pl.smem, s, ep);
-  launch_mode<true>(mode, grid_ext, pl.smem, s, ep);
-  SR_CHECK_CUDA(ctx, cudaGetLastError());
+  launch_mode<false>(mode, pl.minb, pl.grid, pl.smem, s, ep);
+  launch_mode<true>(mode, pl.minb, grid_ext, pl.smem, s, ep);
   ctx->launches += 2;
+  if (pl.smem_deep) {
+    EvalParams ed = ep;
+    ed.deep = 1;
+    ed.slots = slots_for(Lmax);
+    ed.warp_bytes = warp_smem_bytes(ed.slots, Lmax);
+    launch_mode<true>(mode, 4, grid_deep, pl.smem_deep, s, ed);
+    ctx->launches += 1;
+  }
+  SR_CHECK_CUDA(ctx, cudaGetLastError());
   if (mode != MODE_PREDICT) {
     FinalParams fp{ep.partials, ep.flags, ych, P, N, pl.chunk, pl.nchunks, mode, fitness, M, counts};
     finalize_kernel<<<(P + 255) / 256, 256, 0, s>>>(fp);
@@ -1115,12 +1216,18 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
     maxL = q.Lmax > maxL ? q.Lmax : maxL;
     work += (double)q.P * (double)q.N;
   }
-  const int smem = WARPS * warp_smem_bytes(maxL);
-  int grid = 0, grid_ext = 0;
+  const int bslots = shallow_slots(maxL, 4);  // eval_batched_kernel: 4 CTAs per SM
+  const int smem = WARPS * warp_smem_bytes(bslots, maxL);
+  const int smem_deep = slots_for(maxL) > bslots ? WARPS * warp_smem_bytes(slots_for(maxL), maxL) : 0;
+  int grid = 0, grid_ext = 0, grid_deep = 0;
   sr_status st = batched_grid<false>(ctx, smem, &grid);
   if (st != SR_OK) return st;
   st = batched_grid<true>(ctx, smem, &grid_ext);
   if (st != SR_OK) return st;
+  if (smem_deep) {
+    st = batched_grid<true>(ctx, smem_deep, &grid_deep);
+    if (st != SR_OK) return st;
+  }
   const long long warps = (long long)grid * WARPS;
   const double want = (double)warps * TARGET_ITEMS_PER_WARP;
 
@@ -1221,8 +1328,9 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
       bpar->total_progs = progs;
       bpar->total_items = items;
       bpar->queue = reinterpret_cast<unsigned long long *>(ctx->ws + off_q);
-      bpar->warp_bytes = warp_smem_bytes(maxL);
-      bpar->slots = slots_for(maxL);
+      bpar->slots = bslots;
+      bpar->warp_bytes = warp_smem_bytes(bpar->slots, maxL);
+      bpar->deep = 0;
     }
     return cv.off;
   };
@@ -1242,7 +1350,7 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
     group_bytes(g0, g1, &b);
     int corr_blocks = 0;
     for (int r = 0; r < b.ncorr; ++r) corr_blocks += b.prob[b.corr_list[r]].nchunks;
-    SR_CHECK_CUDA(ctx, cudaMemsetAsync(b.queue, 0, 3 * sizeof(unsigned long long), s));
+    SR_CHECK_CUDA(ctx, cudaMemsetAsync(b.queue, 0, 5 * sizeof(unsigned long long), s));
     decode_batched_kernel<<<(b.total_progs + 127) / 128, 128, 0, s>>>(b);
     ctx->launches += 1;
     if (b.ncorr > 0) {
@@ -1252,9 +1360,18 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
     }
     eval_batched_kernel<false><<<grid, WARPS * 32, smem, s>>>(b);
     eval_batched_kernel<true><<<grid_ext, WARPS * 32, smem, s>>>(b);
+    ctx->launches += 2;
+    if (smem_deep) {
+      BatchParams bd = b;
+      bd.deep = 1;
+      bd.slots = slots_for(maxL);
+      bd.warp_bytes = warp_smem_bytes(bd.slots, maxL);
+      eval_batched_kernel<true><<<grid_deep, WARPS * 32, smem_deep, s>>>(bd);
+      ctx->launches += 1;
+    }
     finalize_batched_kernel<<<b.nprob, 256, 0, s>>>(b);
     SR_CHECK_CUDA(ctx, cudaGetLastError());
-    ctx->launches += 3;
+    ctx->launches += 1;
   }
   return SR_OK;
 }

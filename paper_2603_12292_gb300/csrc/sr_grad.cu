@@ -97,6 +97,8 @@ __device__ __forceinline__ DecodeArgs grad_decode_args(const GradParams &p) {
   a.s_task = p.s_task;
   a.ext_count = nullptr;
   a.max_slots = slots_for(p.Lmax);
+  a.cap_slots = a.max_slots;  // one pass: no program is deep
+  a.deep_count = nullptr;
   return a;
 }
 

@@ -80,8 +80,13 @@ __device__ __forceinline__ int ins_k(uint2 w) { return (int)((w.x >> 24) & 0xfu)
 // the kernels can run those programs in a separate copy of their loop and
 // keep the loop of the base operators free of the extra call site.
 constexpr int NCODE_EXT = 1 << 30;
+// NCODE_DEEP is set when the program needs more stack slots than the
+// decoder's cap_slots: the evaluation kernels give most programs a few slots
+// (more warps fit on an SM) and run the rare deeper ones in a separate pass.
+constexpr int NCODE_DEEP = 1 << 29;
 __device__ __forceinline__ int ncode_count(int v) { return v & 0xffff; }
 __device__ __forceinline__ bool ncode_ext(int v) { return (v & NCODE_EXT) != 0; }
+__device__ __forceinline__ bool ncode_deep(int v) { return (v & NCODE_DEEP) != 0; }
 
 struct DecodeArgs {
   const uint8_t *programs;  // [P][Lmax]
@@ -98,6 +103,8 @@ struct DecodeArgs {
   int16_t *s_task;          // scratch [P][Lmax]: work stack
   unsigned long long *ext_count;  // programs with NCODE_EXT are counted here (or NULL)
   int max_slots;            // stack slots the kernel provides (<= DSM)
+  int cap_slots;            // programs that need more than this get NCODE_DEEP (<= max_slots)
+  unsigned long long *deep_count;  // programs with NCODE_DEEP are counted here (or NULL)
 };
 
 __device__ __forceinline__ bool is_term(int v) {
@@ -171,7 +178,7 @@ __device__ inline void decode_one(const DecodeArgs &p, int prog, const uint8_t *
   // operator pops slot d - 2.
   const float *crow = p.consts + (size_t)prog * p.K;
   uint2 *code = p.code + (size_t)prog * p.Lmax;
-  int n = 0, d = 0;
+  int n = 0, d = 0, used = 0;
   sp = 0;
   task[sp++] = (int16_t)((L - 1) << 2);
   while (sp > 0) {
@@ -189,6 +196,7 @@ __device__ inline void decode_one(const DecodeArgs &p, int prog, const uint8_t *
       const bool var = cls == CLS_VAR;
       uint32_t op = var ? OP_LDV : OP_LDC;
       if (d > 0) op = (uint32_t)(var ? OP_PUSHV : OP_PUSHC) | ((uint32_t)((d - 1) * p.slot_bytes) << 8);
+      used = d > used ? d : used;  // slots 0 .. d - 1 are in use
       code[n++] = with_operand(op, v, crow, p.ldx);
       ++d;
     } else if (cls == CLS_UNARY) {
@@ -229,8 +237,10 @@ __device__ inline void decode_one(const DecodeArgs &p, int prog, const uint8_t *
       }
     }
   }
-  p.ncode[prog] = n | (ext ? NCODE_EXT : 0);
+  const bool deep = used > p.cap_slots;
+  p.ncode[prog] = n | (ext ? NCODE_EXT : 0) | (deep ? NCODE_DEEP : 0);
   if (ext && p.ext_count) atomicAdd(p.ext_count, 1ull);
+  if (deep && p.deep_count) atomicAdd(p.deep_count, 1ull);
 }
 
 // decode_one with the scratch of the global workspace

@@ -114,6 +114,9 @@ class Evolver:
         self.graph = None
         self.graph_gens = 0
         self.graph_sizes = None
+        # eager steps append (start, end) CUDA events around the evaluation
+        # when this is a list (timing of the dominant kernel inside a step)
+        self.eval_events = None
 
     # -- one generation, eager ------------------------------------------------
     def _evaluate(self):
@@ -147,7 +150,15 @@ class Evolver:
             for p in self.pops:
                 if p.cfg.const_steps:
                     self._const_opt(p)
-            self._evaluate()
+            if self.eval_events is not None:
+                stream = self.ctx.stream
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                self._evaluate()
+                b.record(stream)
+                self.eval_events.append((a, b))
+            else:
+                self._evaluate()
             for p in self.pops:
                 P_, L_, C_ = p.current
                 n_next = p.cfg.size_at(self.host_gen + 1, p.initial)

@@ -213,6 +213,74 @@ def test_deep_and_long_programs(ctx):
     assert predict_parity(ctx, progs, lens, np.zeros((3, 0), np.float32), X, 700) == 3 * 700
 
 
+def balanced(k, level=0, leaf=None, wrap=False):
+    """RPN of the balanced binary tree with 2^k leaves.  Operators cycle
+    + * - over the levels, leaves over x0, x1, x2, c0, c1 (a period prime to
+    2, so that no two sibling subtrees are equal); wrap puts sin or cos on
+    every leaf.  In Sethi-Ullman order, with a terminal second operand fused
+    into its operator, it needs k - 1 stack slots below the top, or k with
+    wrapped leaves."""
+    leaf = leaf if leaf is not None else iter(range(1 << 20))
+    if k == 0:
+        i = next(leaf)
+        t = [16 + i % 5] if i % 5 < 3 else [32 + i % 5 - 3]
+        return t + [4 if i % 2 else 5] if wrap else t
+    return (balanced(k - 1, level + 1, leaf, wrap) + balanced(k - 1, level + 1, leaf, wrap)
+            + [(0, 2, 1)[level % 3]])
+
+
+def test_programs_beyond_the_main_pass_slots(ctx):
+    """At Lmax = 256 the main passes give each warp 5 stack slots and the
+    programs that need 6 run in a separate pass: predict, MSE, 1 - r^2 and
+    both Beagle scores of a population that mixes them (base and extended
+    operators) against the oracle, and the fitness bit for bit what the
+    batched launch gives."""
+    hand = [balanced(5, wrap=True), balanced(6, wrap=True), balanced(7), balanced(6, wrap=True) + [14],
+            balanced(4, wrap=True) + [14], balanced(6), balanced(6, wrap=True)[:-1] + [2]]
+    # slots needed: 5, 6, 6, 6 (atan: extended), 4 (extended), 5, 6
+    assert [len(h) for h in hand] == [95, 191, 255, 192, 48, 127, 191]
+    pr, y = target_problem(inputs.make_problem, "deep", 91, P=57, Lmin=1, Lmax=256, nvars=3, K=4, N=2053,
+                           xlo=0.9, xhi=1.1, target_len=(5, 9))
+    progs_l = hand + [pr.programs[i, : pr.lengths[i]] for i in range(pr.P)]
+    progs, lens = pack(progs_l, 256)
+    consts = np.concatenate([np.tile(np.array([[0.75, 1.25, 0.5, 2.0]], np.float32), (len(hand), 1)), pr.consts])
+    assert predict_parity(ctx, progs, lens, consts, pr.X, pr.N) > 0.8 * len(progs_l) * pr.N
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    d = dict(programs=t(progs), lengths=t(lens), consts=t(consts), X=t(pr.X), y=t(y))
+    binding.sr_set_tile(ctx, 1024)
+    try:
+        for kind in (oracle.MSE, oracle.CORR):
+            f = binding.sr_eval(ctx, d["programs"], d["lengths"], d["consts"], d["X"], d["y"], pr.N, kind)
+            (fb,) = binding.sr_eval_batched(ctx, [binding.make_problem(d["programs"], d["lengths"], d["consts"],
+                                                                      d["X"], d["y"], pr.N, kind,
+                                                                      cases_per_tile=1024)])
+            torch.cuda.synchronize()
+            assert torch.equal(f, fb)
+            errb, cfl, f0 = oracle.condition(progs, lens, consts, pr.X, y, kind, pr.N)
+            assert check_fitness(kind, f.cpu().numpy(), f0, errb, cfl, y) > 0.4 * len(progs_l)
+    finally:
+        binding.sr_set_tile(ctx, 0)
+    # Beagle's scores from the device's own outputs: Eq. 3 and the counts exact
+    yv = y.astype(np.float32).copy()
+    yv[::97] = np.nan
+    d["y"] = t(yv)
+    yh = binding.sr_predict(ctx, d["programs"], d["lengths"], d["consts"], d["X"], pr.N)
+    for kind, okind in ((binding.SR_SCORE_R4, oracle.SCORE_R4), (binding.SR_SCORE_P2P, oracle.SCORE_P2P)):
+        s, cnt = binding.sr_eval_score(ctx, d["programs"], d["lengths"], d["consts"], d["X"], d["y"], pr.N,
+                                       kind, 1000)
+        torch.cuda.synchronize()
+        s, cnt, yhn = s.cpu().numpy(), cnt.cpu().numpy(), yh.cpu().numpy()[:, : pr.N]
+        for p in range(len(progs_l)):
+            want, c1, c2 = oracle.score_from_outputs(yhn[p].astype(np.float64), yv.astype(np.float64), okind,
+                                                     1000)
+            assert tuple(cnt[p]) == (c1, c2), p
+            if kind == binding.SR_SCORE_P2P:
+                assert s[p] == want, (p, s[p], want)
+            elif np.abs(np.nan_to_num(yhn[p], posinf=0, neginf=0)).max() < 1e15:  # FP32 moment sums fit
+                n = pr.N - c1 - c2
+                assert abs(s[p] - want) <= 1e-4 * 1000 * n, (p, s[p], want)
+
+
 def test_constant_and_single_token_programs(ctx):
     progs, lens = pack([parse("c0"), parse("x1"), parse("c0 sin c1 *")], 4)
     c = np.array([[2.5, -1.0]] * 3, np.float32)
