@@ -155,7 +155,7 @@ __device__ __forceinline__ DecodeArgs decode_args(const EvalParams &p, int cap_s
   return a;
 }
 
-// one warp per 32 programs, scratch in shared memory (decode_warp)
+// one warp per program, scratch in shared memory (decode_warp)
 __global__ void decode_kernel(EvalParams p) {
   extern __shared__ __align__(16) unsigned char dsm[];
   decode_warp(decode_args(p, p.slots, p.queue + 4), p.P, dsm);
@@ -231,13 +231,15 @@ __device__ __noinline__ V8 sqrt8(V8 v) { return map8_unrolled(v, FSqrt()); }
 // acos, atan, tanh) runs twelve library routines: unrolled 8-wide they no
 // longer fit the instruction cache (ncu: 26 cycles per issue stalled on
 // instruction fetch, 23 % of issue slots used).  There the extended routines
-// run one case at a time and the base ones two at a time: 707 -> 1,380
-// GPop/s on a Table 1 population; the base instantiation keeps its 8-wide
-// copies.
+// run four cases at a time and the base ones two.  On a Table 1 population
+// (GPop/s, at 5 CTAs per SM): extended one at a time 1,600, two 1,708, four
+// 1,756, eight 1,383; base four at a time with extended four 1,309: the
+// instruction cache decides.  The base instantiation keeps its 8-wide copies
+// (4-wide: 2,662 -> 1,930 on base populations).
 template <typename F>
 __device__ __forceinline__ V8 map8_small(V8 v, F f) {
   float t[8] = {v.a.x, v.a.y, v.a.z, v.a.w, v.b.x, v.b.y, v.b.z, v.b.w};
-#pragma unroll 1
+#pragma unroll 4
   for (int i = 0; i < 8; ++i) t[i] = f(t[i]);
   return V8{make_float4(t[0], t[1], t[2], t[3]), make_float4(t[4], t[5], t[6], t[7])};
 }
@@ -1060,7 +1062,9 @@ sr_status make_plan(sr_ctx *ctx, int mode, int P, int Lmax, int N, Plan *pl) {
   const long long warps = (long long)pl->grid * WARPS;
   const long long want = warps * TARGET_ITEMS_PER_WARP;
   int nch = (int)((want + P - 1) / (P > 0 ? P : 1));
-  const int max_chunks = (N + 1023) / 1024;
+  // chunks of at least one warp step: a small problem (few programs, few
+  // cases) then still spreads over many warps, its items one step each
+  const int max_chunks = (N + STEP - 1) / STEP;
   nch = nch < 1 ? 1 : (nch > max_chunks ? max_chunks : nch);
   int chunk = (N + nch - 1) / nch;
   if (ctx->tile_cases > 0) chunk = ctx->tile_cases;  // autotuned cases per work item
@@ -1159,7 +1163,8 @@ sr_status launch_eval(sr_ctx *ctx, int mode, const uint8_t *programs, const int3
   // one warp per block spreads the serial per-program decode over the SMs
   st = allow_dynamic_smem(ctx, reinterpret_cast<const void *>(decode_kernel));
   if (st != SR_OK) return st;
-  decode_kernel<<<(P + 31) / 32, 32, decode_smem_bytes(Lmax), s>>>(ep);
+  decode_kernel<<<(P + DECODE_WARPS - 1) / DECODE_WARPS, DECODE_WARPS * 32, DECODE_WARPS * decode_warp_bytes(Lmax),
+                  s>>>(ep);
   ctx->launches += 1;
   double *ych = reinterpret_cast<double *>(ws + pl.off_ych);
   if (mode == MODE_CORR || mode == MODE_BOTH || mode == MODE_R4) {
@@ -1247,7 +1252,7 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
     } else {
       const double share = want * ((double)q.P * (double)q.N) / (work > 0 ? work : 1.0);
       int n = (int)ceil(share / q.P);
-      const int max_chunks = (q.N + 1023) / 1024;
+      const int max_chunks = (q.N + STEP - 1) / STEP;
       n = n < 1 ? 1 : (n > max_chunks ? max_chunks : n);
       c = (q.N + n - 1) / n;
     }

@@ -153,18 +153,48 @@ struct VaryParams {
   int P_in;  // parents' population size
 };
 
+// One warp per child: the warp copies both parents' token rows into shared
+// memory with coalesced loads, lane 0 builds the child there (the steps below
+// are serial), and the warp writes the child's row back.  A thread per child
+// walked the rows in global memory byte by byte: 18 us for 256 children of
+// <= 32 tokens, latency-bound.
+constexpr int VARY_WARPS = 4;
+__host__ __device__ inline int vary_row_bytes(int Lmax) { return (Lmax + 15) & ~15; }
+__device__ int vary_child(VaryParams &p, int i, int ia, int ib, const uint8_t *A, int la, const uint8_t *B,
+                          int lb, uint8_t *out);
+
 __global__ void vary_kernel(VaryParams p) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  extern __shared__ __align__(16) uint8_t vsm[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = blockIdx.x * VARY_WARPS + warp;
   if (i >= p.P) return;
-  p.rng = p.rng.resolved();
   // out-of-range parents and lengths are clamped so that no access leaves
   // the buffers (valid inputs are unaffected)
   const int ia = min(max(p.parents[2 * i], 0), p.P_in - 1);
   const int ib = min(max(p.parents[2 * i + 1], 0), p.P_in - 1);
-  const uint8_t *A = p.prog_in + (size_t)ia * p.Lmax;
-  const uint8_t *B = p.prog_in + (size_t)ib * p.Lmax;
   const int la = min(max(p.len_in[ia], 1), p.Lmax), lb = min(max(p.len_in[ib], 1), p.Lmax);
-  uint8_t *out = p.prog_out + (size_t)i * p.Lmax;
+  const int R = vary_row_bytes(p.Lmax);
+  uint8_t *sA = vsm + (size_t)warp * 3 * R, *sB = sA + R, *out = sB + R;
+  {
+    const uint8_t *gA = p.prog_in + (size_t)ia * p.Lmax, *gB = p.prog_in + (size_t)ib * p.Lmax;
+    for (int t = lane; t < la; t += 32) sA[t] = gA[t];
+    for (int t = lane; t < lb; t += 32) sB[t] = gB[t];
+  }
+  __syncwarp();
+  int len = 0;
+  if (lane == 0) len = vary_child(p, i, ia, ib, sA, la, sB, lb, out);
+  len = __shfl_sync(FULL, len, 0);
+  __syncwarp();
+  uint8_t *g_out = p.prog_out + (size_t)i * p.Lmax;
+  for (int t = lane; t < p.Lmax; t += 32) g_out[t] = t < len ? out[t] : 0;
+}
+
+// Builds child i from parents A (row ia, la tokens) and B (row ib) into out
+// (shared memory, Lmax bytes); writes its length and constants and returns
+// the length.
+__device__ int vary_child(VaryParams &p, int i, int ia, int ib, const uint8_t *A, int la, const uint8_t *B,
+                          int lb, uint8_t *out) {
+  p.rng = p.rng.resolved();
   float c[TOK_NSLOTS];
   for (int k = 0; k < p.K; ++k) c[k] = p.c_in[(size_t)ia * p.K + k];
 
@@ -255,9 +285,9 @@ __global__ void vary_kernel(VaryParams p) {
     c[k] = __fadd_rn(c[k], step);
   }
 
-  for (int t = len; t < p.Lmax; ++t) out[t] = 0;
   p.len_out[i] = len;
   for (int k = 0; k < p.K; ++k) p.c_out[(size_t)i * p.K + k] = c[k];
+  return len;
 }
 
 // ---------------------------------------------------------------- microcosm selection
@@ -410,7 +440,8 @@ sr_status sr_vary(sr_ctx *ctx, const uint8_t *prog_in, const int32_t *len_in, co
   SR_CHECK_CUDA(ctx, cudaSetDevice(ctx->device));
   VaryParams vp{prog_in, len_in, c_in, parents, prog_out, len_out, c_out, P, Lmax, K, nvars, *cfg,
                 make_rng(seed, gen, ctx->gen_dev), P_in};
-  vary_kernel<<<(P + 127) / 128, 128, 0, ctx->stream>>>(vp);
+  vary_kernel<<<(P + VARY_WARPS - 1) / VARY_WARPS, VARY_WARPS * 32, VARY_WARPS * 3 * vary_row_bytes(Lmax),
+                ctx->stream>>>(vp);
   SR_CHECK_CUDA(ctx, cudaGetLastError());
   ctx->launches += 1;
   return SR_OK;

@@ -559,7 +559,8 @@ sr_status sr_eval_grad(sr_ctx *ctx, const uint8_t *programs, const int32_t *leng
   SR_CHECK_CUDA(ctx, cudaMemsetAsync(gp.queue, 0, 8, s));
   st = allow_dynamic_smem(ctx, reinterpret_cast<const void *>(grad_decode_kernel));
   if (st != SR_OK) return st;
-  grad_decode_kernel<<<(P + 31) / 32, 32, decode_smem_bytes(Lmax), s>>>(gp);
+  grad_decode_kernel<<<(P + DECODE_WARPS - 1) / DECODE_WARPS, DECODE_WARPS * 32,
+                       DECODE_WARPS * decode_warp_bytes(Lmax), s>>>(gp);
   grad_kernel<<<grid, GWARPS * 32, smem, s>>>(gp);
   SR_CHECK_CUDA(ctx, cudaGetLastError());
   GradFinal gf{gp.partials, gp.flags, P, N, K, nchunks, mse, dconst};

@@ -119,14 +119,13 @@ __device__ __forceinline__ uint2 with_operand(uint32_t x, int v, const float *cr
 }
 
 // Validation and scheduled decoding of program `prog` (one thread), reading
-// its tokens from `tok` and using the scratch rows start / need / task (Lmax
-// entries each).
+// its tokens from `tok`, its constants from `crow` and using the scratch rows
+// start / need / task (Lmax entries each).
 // Flag rules: length outside [1, Lmax]; bad byte; variable / constant index
 // out of range; depth (running sum of +1 terminal, 0 unary or bad byte, -1
 // binary) below 1 after some token; final depth not 1.
 __device__ inline void decode_one(const DecodeArgs &p, int prog, const uint8_t *tok, int16_t *start,
-                                  uint8_t *need, int16_t *task) {
-  const int L = p.lengths[prog];
+                                  uint8_t *need, int16_t *task, const float *crow, int L) {
   int flags = 0;
   if (L < 1 || L > p.Lmax) {
     flags = SR_PF_BAD_LENGTH;
@@ -176,7 +175,6 @@ __device__ inline void decode_one(const DecodeArgs &p, int prog, const uint8_t *
   // work stack entries are node << 2 | phase.  d counts the live values
   // (top included): a terminal pushes the old top into slot d - 1, a binary
   // operator pops slot d - 2.
-  const float *crow = p.consts + (size_t)prog * p.K;
   uint2 *code = p.code + (size_t)prog * p.Lmax;
   int n = 0, d = 0, used = 0;
   sp = 0;
@@ -246,35 +244,43 @@ __device__ inline void decode_one(const DecodeArgs &p, int prog, const uint8_t *
 // decode_one with the scratch of the global workspace
 __device__ inline void decode_one(const DecodeArgs &p, int prog) {
   const size_t row = (size_t)prog * p.Lmax;
-  decode_one(p, prog, p.programs + row, p.s_start + row, p.s_need + row, p.s_task + row);
+  decode_one(p, prog, p.programs + row, p.s_start + row, p.s_need + row, p.s_task + row,
+             p.consts + (size_t)prog * p.K, p.lengths[prog]);
 }
 
-// Decoding by warps in shared memory: one warp per 32 programs.  The warp
-// first copies its programs' token rows (contiguous in global memory) with
-// coalesced loads, then every lane decodes one program with its scratch in
-// shared memory.  Row strides are padded (tokens and need: Lmax + 4 bytes,
-// start and task: Lmax + 2 entries) so that lanes working on the same token
-// index fall in different banks.  Dynamic shared memory: decode_smem_bytes.
-__host__ __device__ inline int decode_row_bytes(int Lmax) { return (Lmax + 4) * 2 + (Lmax + 2) * 4; }
-__host__ __device__ inline int decode_smem_bytes(int Lmax) { return 32 * decode_row_bytes(Lmax); }
+// Decoding by warps in shared memory: one warp per program.  The warp copies
+// the program's token row and constants with coalesced loads, then lane 0
+// decodes it with its scratch in shared memory.  The tree walk is serial and
+// branchy: a lane per program of a 32-program warp serialised the lanes'
+// different paths (9 of 32 threads active on average) and left one warp per
+// SM; a warp per program spreads the programs over every SM and keeps
+// several warps per scheduler to hide the walk's latency.
+// Dynamic shared memory per warp: decode_warp_bytes.
+// layout: tokens [Lmax + 4] | need [Lmax + 4] | start [Lmax + 2] int16 |
+// task [Lmax + 2] int16 | constants [SR_MAX_CONSTS] float (4-byte aligned)
+__host__ __device__ inline int decode_consts_offset(int Lmax) { return (6 * Lmax + 16 + 3) & ~3; }
+__host__ __device__ inline int decode_warp_bytes(int Lmax) {
+  return (decode_consts_offset(Lmax) + SR_MAX_CONSTS * 4 + 15) & ~15;
+}
+constexpr int DECODE_WARPS = 4;  // warps (programs) per block of the decode kernels
 
 __device__ inline void decode_warp(const DecodeArgs &p, int P, unsigned char *smem) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int prog0 = (blockIdx.x * (blockDim.x >> 5) + warp) * 32;
-  if (prog0 >= P) return;
-  const int nprog = min(32, P - prog0);
+  const int prog = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (prog >= P) return;
   const int Lt = p.Lmax + 4, Ls = p.Lmax + 2;
-  unsigned char *base = smem + (size_t)warp * decode_smem_bytes(p.Lmax);
-  uint8_t *toks = base;                                          // [32][Lt]
-  uint8_t *need = base + 32 * Lt;                                // [32][Lt]
-  int16_t *start = reinterpret_cast<int16_t *>(base + 64 * Lt);  // [32][Ls]
-  int16_t *task = start + 32 * Ls;                               // [32][Ls]
-  const uint8_t *src = p.programs + (size_t)prog0 * p.Lmax;
-  const int total = nprog * p.Lmax;
-  for (int b = lane; b < total; b += 32) toks[(b / p.Lmax) * Lt + b % p.Lmax] = src[b];
+  unsigned char *base = smem + (size_t)warp * decode_warp_bytes(p.Lmax);
+  uint8_t *toks = base;                                          // [Lt]
+  uint8_t *need = base + Lt;                                     // [Lt]
+  int16_t *start = reinterpret_cast<int16_t *>(base + 2 * Lt);   // [Ls]
+  int16_t *task = start + Ls;                                    // [Ls]
+  float *cs = reinterpret_cast<float *>(base + decode_consts_offset(p.Lmax));
+  const uint8_t *src = p.programs + (size_t)prog * p.Lmax;
+  for (int b = lane; b < p.Lmax; b += 32) toks[b] = src[b];
+  if (lane < p.K) cs[lane] = p.consts[(size_t)prog * p.K + lane];
+  const int L = p.lengths[prog];
   __syncwarp();
-  if (lane < nprog)
-    decode_one(p, prog0 + lane, toks + lane * Lt, start + lane * Ls, need + lane * Lt, task + lane * Ls);
+  if (lane == 0) decode_one(p, prog, toks, start, need, task, cs, L);
 }
 
 // ---------------------------------------------------------------- operators (FP32)
