@@ -15,8 +15,8 @@
 //               factors; for a quotient the denominator and the result.  A
 //               terminal operand fused into * or / needs no entry (x_j is
 //               re-read, c_k is in the instruction).  The tape lives in
-//               shared memory up to a capacity chosen per launch and in this
-//               warp's global scratch beyond it: most of it is in L2, its
+//               shared memory when a whole one (Lmax entries) fits there,
+//               else in this warp's global scratch: most of it is in L2, its
 //               latency hidden by 48 warps per SM.
 //   reverse  -- the instructions are walked backwards with the adjoint of
 //               the top in registers; a binary operator writes the adjoint
@@ -42,11 +42,12 @@ constexpr int GSLOT = GSTEP * 4;         // bytes of one stack slot / tape entry
 constexpr int GSTRIDE = 32;              // doubles per partial record: [0] sum e^2, [1 + k] sum e dyhat/dc_k
 constexpr int GTARGET_ITEMS_PER_WARP = 24;
 // Shared-memory budget: 6 CTAs x 8 warps = 48 warps per SM (the register
-// limit at 40 registers).  That leaves a few tape entries per warp in shared
-// memory; the rest of the tape goes to the warp's scratch, which stays in
-// L2 (~50 MB touched on the 16,384 x 1e6 workload).  Measured on 2,048 x
-// 131,072 (K = 8, L <= 96): 12 warps per SM with a 56-entry shared tape
-// 366 GPop/s, 24 -> 579, 32 -> 674, 40 -> 747, 48 -> 791.
+// limit at 40 registers).  Unless a whole tape fits in a warp's share, the
+// tape goes to the warp's scratch, which stays in L2 (~50 MB touched on the
+// 16,384 x 1e6 workload).  Measured on 2,048 x 131,072 (K = 8, L <= 96):
+// 12 warps per SM with a 56-entry shared tape 366 GPop/s, 24 -> 579, 32 ->
+// 674, 40 -> 747, 48 -> 791; 48 with the tape wholly in the scratch instead
+// of its first 2 entries in shared memory (no per-access choice) 831.
 constexpr int GCTAS_PER_SM = 6;
 
 struct GradParams {
@@ -68,13 +69,12 @@ struct GradParams {
   uint8_t *s_need;
   int16_t *s_task;
   unsigned long long *queue;
-  char *gtape;        // per warp: (Lmax - tcap) entries of GSLOT bytes
-  int tcap;           // tape entries in shared memory
+  char *gtape;        // per warp: Lmax entries of GSLOT bytes (tape off chip), else NULL
   int warp_bytes;
 };
 
 // shared memory of one warp: stack slots [slots_for(Lmax)] | gradient sums
-// and compensations [2][K][32] | code [Lmax] | tape [tcap]
+// and compensations [2][K][32] | code [Lmax] | tape [Lmax] (tape on chip only)
 __host__ __device__ inline int grad_fixed_bytes(int Lmax, int K) {
   return slots_for(Lmax) * GSLOT + 2 * K * 128 + ((Lmax * 8 + 15) / 16) * 16;
 }
@@ -227,18 +227,18 @@ struct GradWarp {
   float *gs;     // gradient sums [K][32] (shared)
   float *gc;     // their compensations [K][32]
   uint2 *code;   // this warp's code (shared)
-  char *ts;      // this lane's entry of tape entry 0 (shared)
-  char *tg;      // this lane's entry of the first global tape entry
-  int tcap;
+  char *ts;      // this lane's entry of tape entry 0 (shared; ONCHIP)
+  char *tg;      // this lane's entry of tape entry 0 (the warp's global scratch; !ONCHIP)
   int lane;
 };
 
 __device__ __forceinline__ float2 *slot_at(const GradWarp &w, uint32_t off) {
   return reinterpret_cast<float2 *>(w.slot + off);
 }
+// ONCHIP: the whole tape is in shared memory, else wholly in the scratch
+template <bool ONCHIP>
 __device__ __forceinline__ float2 *tape_at(const GradWarp &w, int i) {
-  return i < w.tcap ? reinterpret_cast<float2 *>(w.ts + (size_t)i * GSLOT)
-                    : reinterpret_cast<float2 *>(w.tg + (size_t)(i - w.tcap) * GSLOT);
+  return reinterpret_cast<float2 *>((ONCHIP ? w.ts : w.tg) + (size_t)i * GSLOT);
 }
 // add this lane's valid cases of v into constant k's compensated sum
 __device__ __forceinline__ void gacc(const GradWarp &w, int k, float2 v, bool ok0, bool ok1) {
@@ -254,6 +254,7 @@ __device__ __forceinline__ float2 ldx2(const float *xr, uint32_t off) {
   return __ldg(reinterpret_cast<const float2 *>(xr + off));
 }
 
+template <bool ONCHIP>
 __global__ void __launch_bounds__(GWARPS * 32) grad_kernel(GradParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -266,8 +267,7 @@ __global__ void __launch_bounds__(GWARPS * 32) grad_kernel(GradParams p) {
   w.code = reinterpret_cast<uint2 *>(wb + slot_bytes + 2 * p.K * 128);
   w.ts = reinterpret_cast<char *>(wb + grad_fixed_bytes(p.Lmax, p.K)) + lane * 8;
   const int gw = blockIdx.x * GWARPS + warp;
-  w.tg = p.gtape ? p.gtape + (size_t)gw * (p.Lmax - p.tcap) * GSLOT + lane * 8 : nullptr;
-  w.tcap = p.tcap;
+  w.tg = ONCHIP ? nullptr : p.gtape + (size_t)gw * p.Lmax * GSLOT + lane * 8;
   w.lane = lane;
 
   for (;;) {
@@ -296,8 +296,8 @@ __global__ void __launch_bounds__(GWARPS * 32) grad_kernel(GradParams p) {
       const bool ok0 = c0 < cend, ok1 = c0 + 1 < cend;
       const float *xr = p.X + (ok0 ? c0 : last_pair);
       int tp = 0;
-      auto push = [&](float2 v) { *tape_at(w, tp++) = v; };
-      auto pop = [&]() { return *tape_at(w, --tp); };
+      auto push = [&](float2 v) { *tape_at<ONCHIP>(w, tp++) = v; };
+      auto pop = [&]() { return *tape_at<ONCHIP>(w, --tp); };
       // ---- forward
       float2 T = splat2(0.f);
       for (int ip = 0; ip < n; ++ip) {
@@ -502,14 +502,15 @@ sr_status sr_eval_grad(sr_ctx *ctx, const uint8_t *programs, const int32_t *leng
   SR_CHECK_CUDA(ctx, cudaDeviceGetAttribute(&blk_reserved, cudaDevAttrReservedSharedMemoryPerBlock, ctx->device));
   const int fixed = grad_fixed_bytes(Lmax, K);
   const int budget = (sm_bytes / GCTAS_PER_SM - blk_reserved) / GWARPS;
-  int tcap = (budget - fixed) / GSLOT;
-  tcap = tcap < 0 ? 0 : (tcap > Lmax ? Lmax : tcap);
-  const int warp_bytes = fixed + tcap * GSLOT;
+  const bool onchip = fixed + Lmax * GSLOT <= budget;  // a whole tape fits a warp's share
+  const int warp_bytes = fixed + (onchip ? Lmax * GSLOT : 0);
   const int smem = GWARPS * warp_bytes;
   if (smem > blk_max) return fail(ctx, SR_EINVAL, "Lmax %d, K %d too large for the gradient kernel", Lmax, K);
-  SR_CHECK_CUDA(ctx, cudaFuncSetAttribute(grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  const void *kern = onchip ? reinterpret_cast<const void *>(grad_kernel<true>)
+                            : reinterpret_cast<const void *>(grad_kernel<false>);
+  SR_CHECK_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   int nb = 0;
-  SR_CHECK_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, grad_kernel, GWARPS * 32, smem));
+  SR_CHECK_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, GWARPS * 32, smem));
   if (nb < 1) return fail(ctx, SR_EINVAL, "Lmax %d, K %d too large for the gradient kernel", Lmax, K);
   const int grid = nb * ctx->num_sms;
   const long long warps = (long long)grid * GWARPS;
@@ -525,7 +526,7 @@ sr_status sr_eval_grad(sr_ctx *ctx, const uint8_t *programs, const int32_t *leng
   const size_t off_q = cv.take(256), off_f = cv.take((size_t)P * 4), off_nc = cv.take((size_t)P * 4),
                off_code = cv.take(tokens * 8),
                off_p = cv.take((size_t)items * GSTRIDE * 8),
-               off_t = cv.take(Lmax > tcap ? (size_t)warps * (Lmax - tcap) * GSLOT : 0);
+               off_t = cv.take(onchip ? 0 : (size_t)warps * Lmax * GSLOT);
   sr_status st = ensure_workspace(ctx, cv.off);
   if (st != SR_OK) return st;
   char *ws = ctx->ws;
@@ -552,8 +553,7 @@ sr_status sr_eval_grad(sr_ctx *ctx, const uint8_t *programs, const int32_t *leng
   gp.s_need = nullptr;
   gp.s_task = nullptr;
   gp.queue = reinterpret_cast<unsigned long long *>(ws + off_q);
-  gp.gtape = Lmax > tcap ? ws + off_t : nullptr;
-  gp.tcap = tcap;
+  gp.gtape = onchip ? nullptr : ws + off_t;
   gp.warp_bytes = warp_bytes;
   cudaStream_t s = ctx->stream;
   SR_CHECK_CUDA(ctx, cudaMemsetAsync(gp.queue, 0, 8, s));
@@ -561,7 +561,8 @@ sr_status sr_eval_grad(sr_ctx *ctx, const uint8_t *programs, const int32_t *leng
   if (st != SR_OK) return st;
   grad_decode_kernel<<<(P + DECODE_WARPS - 1) / DECODE_WARPS, DECODE_WARPS * 32,
                        DECODE_WARPS * decode_warp_bytes(Lmax), s>>>(gp);
-  grad_kernel<<<grid, GWARPS * 32, smem, s>>>(gp);
+  if (onchip) grad_kernel<true><<<grid, GWARPS * 32, smem, s>>>(gp);
+  else grad_kernel<false><<<grid, GWARPS * 32, smem, s>>>(gp);
   SR_CHECK_CUDA(ctx, cudaGetLastError());
   GradFinal gf{gp.partials, gp.flags, P, N, K, nchunks, mse, dconst};
   grad_finalize_kernel<<<(P + 255) / 256, 256, 0, s>>>(gf);
