@@ -822,24 +822,32 @@ __global__ void __launch_bounds__(PREP_THREADS) ycenter_kernel(const float *__re
 }
 
 // ---------------------------------------------------------------- finalize
+// The merges below run with a warp per program: lane l takes chunks l,
+// l + 32, ...; every sum over chunks is a per-lane sum followed by a fixed
+// xor-butterfly reduction (warp_sum), so the result is deterministic and
+// the same on every lane.  (A thread per program ran the FP64 chain of all
+// chunks serially: 0.7 % of a 4,096 x 100,000 generation.)
+
 // 1 - r^2 of one program from its chunk records.
 // chunk c: n_c cases, shift s_c, S1 = sum d, S2 = sum d^2, S3 = sum d yc with
 // d = yhat - s_c.  Chunk mean m_c = s_c + S1/n_c, chunk M2 = S2 - S1^2/n_c;
 // merged (Chan et al.): Shh = sum M2_c + n_c (m_c - m)^2.
 // sum yhat*yc = sum (S3_c + s_c Yc_c); Shy = that - m * Y1; Syy = Y2 - Y1^2/N.
 __device__ double corr_fitness(const double *rec, const double *ychunk, int Nc, int chunk,
-                               int nchunks) {
+                               int nchunks, int lane) {
   const double N = (double)Nc;
   double y1 = 0.0, y2 = 0.0, tot = 0.0;
-  for (int c = 0; c < nchunks; ++c) {
+  for (int c = lane; c < nchunks; c += 32) {
     y1 += ychunk[2 * c];
     y2 += ychunk[2 * c + 1];
     const double nc = (double)min(chunk, Nc - c * chunk);
     tot += nc * rec[c * PSTRIDE + 1] + rec[c * PSTRIDE + 2];
   }
-  const double m = tot / N;
+  y1 = warp_sum(y1);
+  y2 = warp_sum(y2);
+  const double m = warp_sum(tot) / N;
   double shh = 0.0, g = 0.0;
-  for (int c = 0; c < nchunks; ++c) {
+  for (int c = lane; c < nchunks; c += 32) {
     const double nc = (double)min(chunk, Nc - c * chunk);
     const double s = rec[c * PSTRIDE + 1], a = rec[c * PSTRIDE + 2];
     const double b = rec[c * PSTRIDE + 3], d = rec[c * PSTRIDE + 4];
@@ -847,7 +855,8 @@ __device__ double corr_fitness(const double *rec, const double *ychunk, int Nc, 
     shh += (b - a * a / nc) + nc * (mc - m) * (mc - m);
     g += d + s * ychunk[2 * c];
   }
-  const double shy = g - m * y1;
+  shh = warp_sum(shh);
+  const double shy = warp_sum(g) - m * y1;
   const double syy = y2 - y1 * y1 / N;
   double fit = 1.0;
   if (isfinite(shh) && isfinite(shy) && isfinite(syy) && shh > 0.0 && syy > 0.0 && Nc >= 2) {
@@ -864,9 +873,9 @@ __device__ double corr_fitness(const double *rec, const double *ychunk, int Nc, 
 // n_c = cases - c1 - c2.  Shh merges the chunks by Chan et al.; e shares one
 // centre, so See = E2 - E1^2 / n; Seh = sum (X_c + s_c E1_c) - m E1.
 __device__ double r4_score(const double *rec, int Nc, int chunk, int nchunks, double M, double *c1o,
-                           double *c2o) {
+                           double *c2o, int lane) {
   double c1 = 0.0, c2 = 0.0, n = 0.0, tot = 0.0, e1 = 0.0, e2 = 0.0;
-  for (int c = 0; c < nchunks; ++c) {
+  for (int c = lane; c < nchunks; c += 32) {
     const double *r = rec + c * PSTRIDE;
     const double nv = (double)min(chunk, Nc - c * chunk) - r[6] - r[7];
     c1 += r[6];
@@ -876,11 +885,17 @@ __device__ double r4_score(const double *rec, int Nc, int chunk, int nchunks, do
     e1 += r[4];
     e2 += r[5];
   }
+  c1 = warp_sum(c1);
+  c2 = warp_sum(c2);
+  n = warp_sum(n);
+  tot = warp_sum(tot);
+  e1 = warp_sum(e1);
+  e2 = warp_sum(e2);
   double r2 = 0.0;
   if (n >= 2.0) {
     const double m = tot / n;
     double shh = 0.0, seh = 0.0;
-    for (int c = 0; c < nchunks; ++c) {
+    for (int c = lane; c < nchunks; c += 32) {
       const double *r = rec + c * PSTRIDE;
       const double nv = (double)min(chunk, Nc - c * chunk) - r[6] - r[7];
       if (nv <= 0.0) continue;
@@ -888,7 +903,8 @@ __device__ double r4_score(const double *rec, int Nc, int chunk, int nchunks, do
       shh += (r[2] - r[1] * r[1] / nv) + nv * (mc - m) * (mc - m);
       seh += r[3] + r[0] * r[4];
     }
-    seh -= m * e1;
+    shh = warp_sum(shh);
+    seh = warp_sum(seh) - m * e1;
     const double see = e2 - e1 * e1 / n;
     if (isfinite(shh) && isfinite(seh) && isfinite(see) && shh > 0.0 && see > 0.0) {
       r2 = (seh * seh) / (shh * see);
@@ -900,47 +916,57 @@ __device__ double r4_score(const double *rec, int Nc, int chunk, int nchunks, do
   return M * (r2 * r2) * n - M * (c1 - c2);
 }
 
-// fitness of program p from its partial records (mode picks the outputs)
+// fitness of program p from its partial records (mode picks the outputs);
+// called by all 32 lanes of a warp, lane 0 writes
 __device__ void finalize_one(int mode, const double *partials, const int32_t *flags,
                              const double *ychunk, int P, int N, int chunk, int nchunks,
-                             double *fitness, int p, int M = 0, int32_t *counts = nullptr) {
+                             double *fitness, int p, int lane, int M = 0, int32_t *counts = nullptr) {
   const double INF = __longlong_as_double(0x7ff0000000000000ll);
   if (mode == MODE_R4 || mode == MODE_P2P) {
     double c1 = 0.0, c2 = 0.0, sc = -INF;
     if (!flags[p]) {
       const double *rec = partials + (size_t)p * nchunks * PSTRIDE;
       if (mode == MODE_R4) {
-        sc = r4_score(rec, N, chunk, nchunks, (double)M, &c1, &c2);
+        sc = r4_score(rec, N, chunk, nchunks, (double)M, &c1, &c2, lane);
       } else {
         sc = 0.0;
-        for (int c = 0; c < nchunks; ++c) {
+        for (int c = lane; c < nchunks; c += 32) {
           sc += rec[c * PSTRIDE];
           c1 += rec[c * PSTRIDE + 6];
           c2 += rec[c * PSTRIDE + 7];
         }
+        sc = warp_sum(sc);  // integers below 2^53: exact in any order
+        c1 = warp_sum(c1);
+        c2 = warp_sum(c2);
       }
     }
-    fitness[p] = sc;
-    if (counts) {
-      counts[2 * p] = (int32_t)c1;
-      counts[2 * p + 1] = (int32_t)c2;
+    if (lane == 0) {
+      fitness[p] = sc;
+      if (counts) {
+        counts[2 * p] = (int32_t)c1;
+        counts[2 * p + 1] = (int32_t)c2;
+      }
     }
     return;
   }
   double *mse_out = fitness;
   double *corr_out = mode == MODE_BOTH ? fitness + P : fitness;
   if (flags[p]) {
-    if (mode != MODE_CORR) mse_out[p] = INF;
-    if (mode != MODE_MSE) corr_out[p] = INF;
+    if (lane == 0 && mode != MODE_CORR) mse_out[p] = INF;
+    if (lane == 0 && mode != MODE_MSE) corr_out[p] = INF;
     return;
   }
   const double *rec = partials + (size_t)p * nchunks * PSTRIDE;
   if (mode != MODE_CORR) {
     double se = 0.0;
-    for (int c = 0; c < nchunks; ++c) se += rec[c * PSTRIDE];
-    mse_out[p] = isfinite(se) ? se / (double)N : INF;
+    for (int c = lane; c < nchunks; c += 32) se += rec[c * PSTRIDE];
+    se = warp_sum(se);
+    if (lane == 0) mse_out[p] = isfinite(se) ? se / (double)N : INF;
   }
-  if (mode != MODE_MSE) corr_out[p] = corr_fitness(rec, ychunk, N, chunk, nchunks);
+  if (mode != MODE_MSE) {
+    const double f = corr_fitness(rec, ychunk, N, chunk, nchunks, lane);
+    if (lane == 0) corr_out[p] = f;
+  }
 }
 
 struct FinalParams {
@@ -953,16 +979,14 @@ struct FinalParams {
   int32_t *counts;  // Beagle scores: [P][2] (c1, c2) or NULL
 };
 
-// One warp per block: the FP64 merges of a program are serial and FP64 is
-// slow, so the programs are spread over every SM (256-thread blocks kept
-// 4,096 programs on 16 SMs, 1.1 % of a generation).
-constexpr int FINAL_THREADS = 32;
+// a warp per program, FINAL_WARPS programs per block
+constexpr int FINAL_WARPS = 4;
 
 __global__ void finalize_kernel(FinalParams f) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = blockIdx.x * FINAL_WARPS + (threadIdx.x >> 5);
   if (p >= f.P) return;
-  finalize_one(f.mode, f.partials, f.flags, f.ychunk, f.P, f.N, f.chunk, f.nchunks, f.fitness, p, f.M,
-               f.counts);
+  finalize_one(f.mode, f.partials, f.flags, f.ychunk, f.P, f.N, f.chunk, f.nchunks, f.fitness, p,
+               threadIdx.x & 31, f.M, f.counts);
 }
 
 // ---------------------------------------------------------------- batched prep / finalize
@@ -987,11 +1011,12 @@ __global__ void __launch_bounds__(PREP_THREADS) ycenter_batched_kernel(const __g
                 q.ychunk, red);
 }
 
-// blocks (problem, FINAL_THREADS programs of it)
+// blocks (problem, FINAL_WARPS programs of it), a warp per program
 __global__ void finalize_batched_kernel(const __grid_constant__ BatchParams b) {
   const BatchProblem &q = b.prob[blockIdx.x];
-  for (int p = blockIdx.y * blockDim.x + threadIdx.x; p < q.P; p += gridDim.y * blockDim.x)
-    finalize_one(q.mode, q.partials, q.flags, q.ychunk, q.P, q.N, q.chunk, q.nchunks, q.fitness, p);
+  for (int p = blockIdx.y * FINAL_WARPS + (threadIdx.x >> 5); p < q.P; p += gridDim.y * FINAL_WARPS)
+    finalize_one(q.mode, q.partials, q.flags, q.ychunk, q.P, q.N, q.chunk, q.nchunks, q.fitness, p,
+                 threadIdx.x & 31);
 }
 
 // ---------------------------------------------------------------- host side
@@ -1189,7 +1214,7 @@ sr_status launch_eval(sr_ctx *ctx, int mode, const uint8_t *programs, const int3
   SR_CHECK_CUDA(ctx, cudaGetLastError());
   if (mode != MODE_PREDICT) {
     FinalParams fp{ep.partials, ep.flags, ych, P, N, pl.chunk, pl.nchunks, mode, fitness, M, counts};
-    finalize_kernel<<<(P + FINAL_THREADS - 1) / FINAL_THREADS, FINAL_THREADS, 0, s>>>(fp);
+    finalize_kernel<<<(P + FINAL_WARPS - 1) / FINAL_WARPS, FINAL_WARPS * 32, 0, s>>>(fp);
     SR_CHECK_CUDA(ctx, cudaGetLastError());
     ctx->launches += 1;
   }
@@ -1381,8 +1406,8 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
     }
     int maxP = 1;
     for (int r = 0; r < b.nprob; ++r) maxP = b.prob[r].P > maxP ? b.prob[r].P : maxP;
-    const int yblocks = std::min((maxP + FINAL_THREADS - 1) / FINAL_THREADS, 65535);
-    finalize_batched_kernel<<<dim3(b.nprob, yblocks), FINAL_THREADS, 0, s>>>(b);
+    const int yblocks = std::min((maxP + FINAL_WARPS - 1) / FINAL_WARPS, 65535);
+    finalize_batched_kernel<<<dim3(b.nprob, yblocks), FINAL_WARPS * 32, 0, s>>>(b);
     SR_CHECK_CUDA(ctx, cudaGetLastError());
     ctx->launches += 1;
   }

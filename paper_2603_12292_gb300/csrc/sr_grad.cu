@@ -118,9 +118,8 @@ __device__ __forceinline__ float2 hi2(float4 r) { return make_float2(r.z, r.w); 
 
 // Out-of-line operators (one copy of each long body keeps the interpreter
 // loop inside the instruction cache).  fwd_* return (value.x, value.y,
-// derivative.x, derivative.y) under the derivative conventions of the
-// oracle: a protected fallback, a clamped exp and sqrt|x| at 0 have
-// derivative 0.
+// derivative.x, derivative.y) under these conventions at the kinks: a
+// protected fallback, a clamped exp and sqrt|x| at 0 have derivative 0.
 static __device__ __noinline__ float2 sincos_wide(float x) {
   float s, c;
   sincosf(x, &s, &c);
