@@ -8,13 +8,15 @@
 // Eq. 1, scored here as 1 - r^2 (Sec. 2.1.5).
 //
 // Design on the device
-//   1. Decode pre-pass, one thread per program: validation, then the
-//      expression tree is rescheduled Sethi-Ullman style -- at every binary
-//      node the child that needs more stack is evaluated first (a reversed
-//      opcode keeps a - b and a / b exact when the right child goes first).
-//      The stack depth of any program is then at most floor(log2(leaves)) + 1
-//      (9 for 512 tokens), so floor(log2((Lmax + 1) / 2)) shared-memory slots
-//      always suffice (6 for Lmax = 128; fewer slots, more warps per SM).
+//   1. Decode pre-pass, a warp per program (lane 0 walks the tree in shared
+//      memory): validation, then the expression tree is rescheduled
+//      Sethi-Ullman style -- at every binary node the child that needs more
+//      stack is evaluated first (a reversed opcode keeps a - b and a / b
+//      exact when the right child goes first).  The stack depth of any
+//      program is then at most floor(log2(leaves)) + 1 (9 for 512 tokens), so
+//      floor(log2((Lmax + 1) / 2)) slots always suffice; most programs need
+//      far fewer, so the main passes give each warp only what fits 4 or 5
+//      CTAs per SM and the rare deeper programs run in a third pass.
 //      A terminal evaluated second is fused into its binary operator
 //      ("top = top op x_j"), and every operand is resolved here (constant
 //      value, X row offset, stack-slot byte offset): the interpreter does no
@@ -30,7 +32,7 @@
 //      below in shared memory [slot][half][lane] (conflict-free float4).
 //   3. Per lane, FP32 Kahan-compensated sums over the item's cases; FP64 warp
 //      reduction; one FP64 partial per (program, chunk); a finalize kernel
-//      merges the chunks of each program in a fixed order.
+//      merges the chunks of each program (a warp per program, fixed order).
 #include <math.h>
 #include <stdio.h>
 

@@ -2,7 +2,7 @@
 // kernels (sr_eval.cu) and the adjoint kernel (sr_grad.cu).
 //
 // A program (RPN, paper Sec. 2.1.4) is decoded once per call by a pre-pass,
-// one thread per program: validation, then the expression tree is
+// a warp per program (decode_warp): validation, then the expression tree is
 // rescheduled Sethi-Ullman style -- at every binary node the child that needs
 // more stack is evaluated first, with a reversed opcode keeping a - b and
 // a / b exact when the right child goes first.  The number of live values is
