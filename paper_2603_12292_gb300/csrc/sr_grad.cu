@@ -3,8 +3,8 @@
 //
 // The adjoint runs over the same scheduled instruction stream as evaluation
 // (sr_interp.cuh: Sethi-Ullman order, at most 8 stack slots, fused terminal
-// operators).  Work item = (case chunk, program), one warp, 2 cases per lane
-// (one float2 per value), 64 cases per step.  Per step:
+// operators).  Work item = (case chunk, program), one warp, 4 cases per lane
+// (one float4 per value), 128 cases per step.  Per step:
 //   forward  -- the program runs with the top of stack in registers and the
 //               slots below in shared memory.  What the reverse sweep needs
 //               goes on a LIFO tape: for a unary operator its local
@@ -36,19 +36,25 @@ namespace sr {
 namespace {
 
 constexpr int GWARPS = 8;                // warps per CTA
-constexpr int GCPL = 2;                  // cases per lane (one float2)
+#ifndef SR_GRAD_CPL
+#define SR_GRAD_CPL 4
+#endif
+constexpr int GCPL = SR_GRAD_CPL;        // cases per lane (2: one float2, 4: one float4)
+static_assert(GCPL == 2 || GCPL == 4, "2 or 4 cases per lane");
 constexpr int GSTEP = 32 * GCPL;         // cases per warp step
 constexpr int GSLOT = GSTEP * 4;         // bytes of one stack slot / tape entry of a warp
 constexpr int GSTRIDE = 32;              // doubles per partial record: [0] sum e^2, [1 + k] sum e dyhat/dc_k
 constexpr int GTARGET_ITEMS_PER_WARP = 24;
-// Shared-memory budget: 6 CTAs x 8 warps = 48 warps per SM (the register
-// limit at 40 registers).  Unless a whole tape fits in a warp's share, the
-// tape goes to the warp's scratch, which stays in L2 (~50 MB touched on the
-// 16,384 x 1e6 workload).  Measured on 2,048 x 131,072 (K = 8, L <= 96):
-// 12 warps per SM with a 56-entry shared tape 366 GPop/s, 24 -> 579, 32 ->
-// 674, 40 -> 747, 48 -> 791; 48 with the tape wholly in the scratch instead
-// of its first 2 entries in shared memory (no per-access choice) 831.
-constexpr int GCTAS_PER_SM = 6;
+// Shared-memory budget: GCTAS_PER_SM CTAs of 8 warps per SM, the register
+// limit (2 cases per lane: 40 registers, 48 warps; 4: 48 registers, 40
+// warps).  Unless a whole tape fits in a warp's share, the tape goes to the
+// warp's scratch, which stays mostly in L2.  Measured on 2,048 x 131,072
+// (K = 8, L <= 96), 2 cases per lane: 12 warps per SM with a 56-entry shared
+// tape 366 GPop/s, 24 -> 579, 32 -> 674, 40 -> 747, 48 -> 791; 48 with the
+// tape wholly in the scratch instead of its first 2 entries in shared memory
+// (no per-access choice) 831.  4 cases per lane (the dispatch of each
+// instruction shared by twice the cases) 980; 8 per lane 371.
+constexpr int GCTAS_PER_SM = GCPL == 2 ? 6 : 5;
 
 struct GradParams {
   const uint8_t *programs;
@@ -107,19 +113,42 @@ __global__ void grad_decode_kernel(GradParams p) {
   decode_warp(grad_decode_args(p), p.P, dsm);
 }
 
-// ---------------------------------------------------------------- float2 helpers
-__device__ __forceinline__ float2 splat2(float c) { return make_float2(c, c); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return make_float2(a.x * b.x, a.y * b.y); }
-__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
-__device__ __forceinline__ float2 lo2(float4 r) { return make_float2(r.x, r.y); }
-__device__ __forceinline__ float2 hi2(float4 r) { return make_float2(r.z, r.w); }
+// ---------------------------------------------------------------- per-lane vectors
+// VG: this lane's GCPL cases of one value (one float2 or float4 in memory)
+struct alignas(GCPL * 4) VG {
+  float v[GCPL];
+};
+__device__ __forceinline__ VG splatg(float c) {
+  VG r;
+#pragma unroll
+  for (int i = 0; i < GCPL; ++i) r.v[i] = c;
+  return r;
+}
+#define SR_VG_BINOP(name, expr)                                   \
+  __device__ __forceinline__ VG name(VG a, VG b) {                \
+    VG r;                                                         \
+    _Pragma("unroll") for (int i = 0; i < GCPL; ++i) r.v[i] = expr; \
+    return r;                                                     \
+  }
+SR_VG_BINOP(addg, a.v[i] + b.v[i])
+SR_VG_BINOP(subg, a.v[i] - b.v[i])
+SR_VG_BINOP(mulg, a.v[i] * b.v[i])
+#undef SR_VG_BINOP
+__device__ __forceinline__ VG negg(VG a) {
+  VG r;
+#pragma unroll
+  for (int i = 0; i < GCPL; ++i) r.v[i] = -a.v[i];
+  return r;
+}
+// a value and its local derivative, from the forward operators below
+struct VD {
+  VG v, d;
+};
 
 // Out-of-line operators (one copy of each long body keeps the interpreter
-// loop inside the instruction cache).  fwd_* return (value.x, value.y,
-// derivative.x, derivative.y) under these conventions at the kinks: a
-// protected fallback, a clamped exp and sqrt|x| at 0 have derivative 0.
+// loop inside the instruction cache).  fwd_* return the value and the local
+// derivative under these conventions at the kinks: a protected fallback, a
+// clamped exp and sqrt|x| at 0 have derivative 0.
 static __device__ __noinline__ float2 sincos_wide(float x) {
   float s, c;
   sincosf(x, &s, &c);
@@ -132,51 +161,62 @@ __device__ __forceinline__ float2 f_sincos(float x) {
   sincosf(x, &s, &c);
   return make_float2(s, c);
 }
-__device__ __noinline__ float4 fwd_sin(float2 x) {
-  const float2 a = f_sincos(x.x), b = f_sincos(x.y);
-  return make_float4(a.x, b.x, a.y, b.y);
+__device__ __noinline__ VD fwd_sin(VG x) {
+  VD r;
+#pragma unroll
+  for (int i = 0; i < GCPL; ++i) {
+    const float2 sc = f_sincos(x.v[i]);
+    r.v.v[i] = sc.x;
+    r.d.v[i] = sc.y;
+  }
+  return r;
 }
-__device__ __noinline__ float4 fwd_cos(float2 x) {
-  const float2 a = f_sincos(x.x), b = f_sincos(x.y);
-  return make_float4(a.y, b.y, -a.x, -b.x);
+__device__ __noinline__ VD fwd_cos(VG x) {
+  VD r;
+#pragma unroll
+  for (int i = 0; i < GCPL; ++i) {
+    const float2 sc = f_sincos(x.v[i]);
+    r.v.v[i] = sc.y;
+    r.d.v[i] = -sc.x;
+  }
+  return r;
 }
 __device__ __forceinline__ float d_exp(float x, float v) { return (x > 80.0f || x < -80.0f) ? 0.0f : v; }
-__device__ __noinline__ float4 fwd_exp(float2 x) {
-  const float a = op_exp(x.x), b = op_exp(x.y);
-  return make_float4(a, b, d_exp(x.x, a), d_exp(x.y, b));
+__device__ __noinline__ VD fwd_exp(VG x) {
+  VD r;
+#pragma unroll
+  for (int i = 0; i < GCPL; ++i) {
+    r.v.v[i] = op_exp(x.v[i]);
+    r.d.v[i] = d_exp(x.v[i], r.v.v[i]);
+  }
+  return r;
 }
 __device__ __forceinline__ float d_log(float x) { return fabsf(x) < 1e-3f ? 0.0f : 1.0f / x; }
-__device__ __noinline__ float4 fwd_log(float2 x) {
-  return make_float4(op_log(x.x), op_log(x.y), d_log(x.x), d_log(x.y));
+__device__ __noinline__ VD fwd_log(VG x) {
+  VD r;
+#pragma unroll
+  for (int i = 0; i < GCPL; ++i) {
+    r.v.v[i] = op_log(x.v[i]);
+    r.d.v[i] = d_log(x.v[i]);
+  }
+  return r;
 }
 __device__ __forceinline__ float d_sqrt(float x, float v) { return x == 0.0f ? 0.0f : copysignf(0.5f / v, x); }
-__device__ __noinline__ float4 fwd_sqrt(float2 x) {
-  const float a = f_sqrt(x.x), b = f_sqrt(x.y);
-  return make_float4(a, b, d_sqrt(x.x, a), d_sqrt(x.y, b));
+__device__ __noinline__ VD fwd_sqrt(VG x) {
+  VD r;
+#pragma unroll
+  for (int i = 0; i < GCPL; ++i) {
+    r.v.v[i] = f_sqrt(x.v[i]);
+    r.d.v[i] = d_sqrt(x.v[i], r.v.v[i]);
+  }
+  return r;
 }
 // the rest of Table 1: 1/x (derivative -1/x^2, 0 where the fallback was
 // taken), tan (1 + tan^2), asin (1/sqrt(1 - x^2)), acos (-1/sqrt(1 - x^2)),
 // atan (1/(1 + x^2)), tanh (sech^2)
 __device__ __forceinline__ float d_inv(float x, float v) { return fabsf(x) < 1e-3f ? 0.0f : -(v * v); }
-__device__ __forceinline__ float4 fwd_inv(float2 x) {
-  const float a = op_inv(x.x), b = op_inv(x.y);
-  return make_float4(a, b, d_inv(x.x, a), d_inv(x.y, b));
-}
-__device__ __forceinline__ float4 fwd_tan(float2 x) {
-  const float a = f_tan(x.x), b = f_tan(x.y);
-  return make_float4(a, b, 1.0f + a * a, 1.0f + b * b);
-}
 // 1 - x^2 as (1 - x)(1 + x): no cancellation near |x| = 1
 __device__ __forceinline__ float d_asin(float x) { return 1.0f / sqrtf((1.0f - x) * (1.0f + x)); }
-__device__ __forceinline__ float4 fwd_asin(float2 x) {
-  return make_float4(f_asin(x.x), f_asin(x.y), d_asin(x.x), d_asin(x.y));
-}
-__device__ __forceinline__ float4 fwd_acos(float2 x) {
-  return make_float4(f_acos(x.x), f_acos(x.y), -d_asin(x.x), -d_asin(x.y));
-}
-__device__ __forceinline__ float4 fwd_atan(float2 x) {
-  return make_float4(f_atan(x.x), f_atan(x.y), 1.0f / (1.0f + x.x * x.x), 1.0f / (1.0f + x.y * x.y));
-}
 // sech^2 x = 4e / (1 + e)^2 with e = exp(-2|x|): 1 - tanh^2 would cancel
 // to 0 long before the derivative underflows
 __device__ __forceinline__ float d_tanh(float x) {
@@ -184,25 +224,48 @@ __device__ __forceinline__ float d_tanh(float x) {
   const float q = 1.0f + e;
   return 4.0f * e / (q * q);
 }
-__device__ __forceinline__ float4 fwd_tanh(float2 x) {
-  return make_float4(f_tanh(x.x), f_tanh(x.y), d_tanh(x.x), d_tanh(x.y));
-}
-// one out-of-line entry for all of them keeps the forward switch small
-__device__ __noinline__ float4 fwd_ext(uint32_t op, float2 x) {
+__device__ __forceinline__ float2 fwd_ext1(uint32_t op, float x) {
   switch (op) {
-    case OP_INV: return fwd_inv(x);
-    case OP_TAN: return fwd_tan(x);
-    case OP_ASIN: return fwd_asin(x);
-    case OP_ACOS: return fwd_acos(x);
-    case OP_ATAN: return fwd_atan(x);
-    default: return fwd_tanh(x);
+    case OP_INV: {
+      const float a = op_inv(x);
+      return make_float2(a, d_inv(x, a));
+    }
+    case OP_TAN: {
+      const float a = f_tan(x);
+      return make_float2(a, 1.0f + a * a);
+    }
+    case OP_ASIN: return make_float2(f_asin(x), d_asin(x));
+    case OP_ACOS: return make_float2(f_acos(x), -d_asin(x));
+    case OP_ATAN: return make_float2(f_atan(x), 1.0f / (1.0f + x * x));
+    default: return make_float2(f_tanh(x), d_tanh(x));
   }
 }
+// one out-of-line entry for all of them keeps the forward switch small
+__device__ __noinline__ VD fwd_ext(uint32_t op, VG x) {
+  VD r;
+#pragma unroll 1
+  for (int i = 0; i < GCPL; ++i) {
+    const float2 vd = fwd_ext1(op, x.v[i]);
+    r.v.v[i] = vd.x;
+    r.d.v[i] = vd.y;
+  }
+  return r;
+}
 // protected quotient (the interpreter's operator)
-__device__ __noinline__ float2 pdiv2(float2 a, float2 b) { return make_float2(op_div(a.x, b.x), op_div(a.y, b.y)); }
+__device__ __noinline__ VG pdivg(VG a, VG b) {
+  VG r;
+#pragma unroll
+  for (int i = 0; i < GCPL; ++i) r.v[i] = op_div(a.v[i], b.v[i]);
+  return r;
+}
 // adjoint through a protected quotient: a / den, 0 where the fallback was taken
 __device__ __forceinline__ float qdiv(float a, float d) { return fabsf(d) < 1e-3f ? 0.0f : a / d; }
-__device__ __noinline__ float2 qdiv2(float2 a, float2 d) { return make_float2(qdiv(a.x, d.x), qdiv(a.y, d.y)); }
+__device__ __noinline__ VG qdivg(VG a, VG d) {
+  VG r;
+#pragma unroll
+  for (int i = 0; i < GCPL; ++i) r.v[i] = qdiv(a.v[i], d.v[i]);
+  return r;
+}
 
 struct Kahan {
   float s = 0.f, c = 0.f;
@@ -231,17 +294,20 @@ struct GradWarp {
   int lane;
 };
 
-__device__ __forceinline__ float2 *slot_at(const GradWarp &w, uint32_t off) {
-  return reinterpret_cast<float2 *>(w.slot + off);
+__device__ __forceinline__ VG *slot_at(const GradWarp &w, uint32_t off) {
+  return reinterpret_cast<VG *>(w.slot + off);
 }
 // ONCHIP: the whole tape is in shared memory, else wholly in the scratch
 template <bool ONCHIP>
-__device__ __forceinline__ float2 *tape_at(const GradWarp &w, int i) {
-  return reinterpret_cast<float2 *>((ONCHIP ? w.ts : w.tg) + (size_t)i * GSLOT);
+__device__ __forceinline__ VG *tape_at(const GradWarp &w, int i) {
+  return reinterpret_cast<VG *>((ONCHIP ? w.ts : w.tg) + (size_t)i * GSLOT);
 }
-// add this lane's valid cases of v into constant k's compensated sum
-__device__ __forceinline__ void gacc(const GradWarp &w, int k, float2 v, bool ok0, bool ok1) {
-  const float x = (ok0 ? v.x : 0.0f) + (ok1 ? v.y : 0.0f);
+// add this lane's valid cases of v (bit i of okm: case i is inside the
+// chunk) into constant k's compensated sum
+__device__ __forceinline__ void gacc(const GradWarp &w, int k, VG v, unsigned okm) {
+  float x = 0.0f;
+#pragma unroll
+  for (int i = 0; i < GCPL; ++i) x += ((okm >> i) & 1u) ? v.v[i] : 0.0f;
   float *s = w.gs + k * 32 + w.lane, *c = w.gc + k * 32 + w.lane;
   const float sv = *s, cv = *c;
   const float yv = x - cv;
@@ -249,8 +315,20 @@ __device__ __forceinline__ void gacc(const GradWarp &w, int k, float2 v, bool ok
   *c = (t - sv) - yv;
   *s = t;
 }
-__device__ __forceinline__ float2 ldx2(const float *xr, uint32_t off) {
-  return __ldg(reinterpret_cast<const float2 *>(xr + off));
+__device__ __forceinline__ VG ldxg(const float *xr, uint32_t off) {
+  VG r;
+  if (GCPL == 4) {
+    const float4 q = __ldg(reinterpret_cast<const float4 *>(xr + off));
+    r.v[0] = q.x;
+    r.v[1] = q.y;
+    r.v[GCPL > 2 ? 2 : 0] = q.z;
+    r.v[GCPL > 3 ? 3 : 1] = q.w;
+  } else {
+    const float2 q = __ldg(reinterpret_cast<const float2 *>(xr + off));
+    r.v[0] = q.x;
+    r.v[1] = q.y;
+  }
+  return r;
 }
 
 template <bool ONCHIP>
@@ -259,14 +337,14 @@ __global__ void __launch_bounds__(GWARPS * 32) grad_kernel(GradParams p) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned char *wb = smem + (size_t)warp * p.warp_bytes;
   GradWarp w;
-  w.slot = reinterpret_cast<char *>(wb) + lane * 8;
+  w.slot = reinterpret_cast<char *>(wb) + lane * (GCPL * 4);
   const int slot_bytes = slots_for(p.Lmax) * GSLOT;
   w.gs = reinterpret_cast<float *>(wb + slot_bytes);
   w.gc = w.gs + p.K * 32;
   w.code = reinterpret_cast<uint2 *>(wb + slot_bytes + 2 * p.K * 128);
-  w.ts = reinterpret_cast<char *>(wb + grad_fixed_bytes(p.Lmax, p.K)) + lane * 8;
+  w.ts = reinterpret_cast<char *>(wb + grad_fixed_bytes(p.Lmax, p.K)) + lane * (GCPL * 4);
   const int gw = blockIdx.x * GWARPS + warp;
-  w.tg = ONCHIP ? nullptr : p.gtape + (size_t)gw * p.Lmax * GSLOT + lane * 8;
+  w.tg = ONCHIP ? nullptr : p.gtape + (size_t)gw * p.Lmax * GSLOT + lane * (GCPL * 4);
   w.lane = lane;
 
   for (;;) {
@@ -288,65 +366,73 @@ __global__ void __launch_bounds__(GWARPS * 32) grad_kernel(GradParams p) {
     __syncwarp();
 
     const int cbeg = c * p.chunk, cend = min(p.N, cbeg + p.chunk);
-    const int last_pair = (cend - 1) & ~1;
+    const int last_group = (cend - 1) & ~(GCPL - 1);
     Kahan se;
     for (int base = cbeg; base < cend; base += GSTEP) {
-      const int c0 = base + 2 * lane;
-      const bool ok0 = c0 < cend, ok1 = c0 + 1 < cend;
-      const float *xr = p.X + (ok0 ? c0 : last_pair);
+      const int c0 = base + GCPL * lane;
+      unsigned okm = 0;  // bit i: case c0 + i is inside the chunk
+#pragma unroll
+      for (int i = 0; i < GCPL; ++i) okm |= (c0 + i < cend ? 1u : 0u) << i;
+      const float *xr = p.X + (okm ? c0 : last_group);
       int tp = 0;
-      auto push = [&](float2 v) { *tape_at<ONCHIP>(w, tp++) = v; };
+      auto push = [&](VG v) { *tape_at<ONCHIP>(w, tp++) = v; };
       auto pop = [&]() { return *tape_at<ONCHIP>(w, --tp); };
       // ---- forward
-      float2 T = splat2(0.f);
+      VG T = splatg(0.f);
       for (int ip = 0; ip < n; ++ip) {
         const uint2 ins = w.code[ip];
         const uint32_t off = ins_off(ins);
         const float cv = __uint_as_float(ins.y);
         switch (ins_op(ins)) {
-          case OP_LDV: T = ldx2(xr, ins.y); break;
-          case OP_LDC: T = splat2(cv); break;
-          case OP_PUSHV: *slot_at(w, off) = T; T = ldx2(xr, ins.y); break;
-          case OP_PUSHC: *slot_at(w, off) = T; T = splat2(cv); break;
-          case OP_ADD: { const float2 a = *slot_at(w, off); T = add2(a, T); } break;
-          case OP_SUB: { const float2 a = *slot_at(w, off); T = sub2(a, T); } break;
-          case OP_RSUB: { const float2 b = *slot_at(w, off); T = sub2(T, b); } break;
-          case OP_MUL: { const float2 a = *slot_at(w, off); push(a); push(T); T = mul2(a, T); } break;
-          case OP_DIV: { const float2 a = *slot_at(w, off); push(T); T = pdiv2(a, T); push(T); } break;
-          case OP_RDIV: { const float2 b = *slot_at(w, off); push(b); T = pdiv2(T, b); push(T); } break;
-          case OP_SIN: { const float4 r = fwd_sin(T); push(hi2(r)); T = lo2(r); } break;
-          case OP_COS: { const float4 r = fwd_cos(T); push(hi2(r)); T = lo2(r); } break;
-          case OP_EXP: { const float4 r = fwd_exp(T); push(hi2(r)); T = lo2(r); } break;
-          case OP_LOG: { const float4 r = fwd_log(T); push(hi2(r)); T = lo2(r); } break;
-          case OP_SQRT: { const float4 r = fwd_sqrt(T); push(hi2(r)); T = lo2(r); } break;
-          case OP_SQ: push(add2(T, T)); T = mul2(T, T); break;
+          case OP_LDV: T = ldxg(xr, ins.y); break;
+          case OP_LDC: T = splatg(cv); break;
+          case OP_PUSHV: *slot_at(w, off) = T; T = ldxg(xr, ins.y); break;
+          case OP_PUSHC: *slot_at(w, off) = T; T = splatg(cv); break;
+          case OP_ADD: { const VG a = *slot_at(w, off); T = addg(a, T); } break;
+          case OP_SUB: { const VG a = *slot_at(w, off); T = subg(a, T); } break;
+          case OP_RSUB: { const VG b = *slot_at(w, off); T = subg(T, b); } break;
+          case OP_MUL: { const VG a = *slot_at(w, off); push(a); push(T); T = mulg(a, T); } break;
+          case OP_DIV: { const VG a = *slot_at(w, off); push(T); T = pdivg(a, T); push(T); } break;
+          case OP_RDIV: { const VG b = *slot_at(w, off); push(b); T = pdivg(T, b); push(T); } break;
+          case OP_SIN: { const VD r = fwd_sin(T); push(r.d); T = r.v; } break;
+          case OP_COS: { const VD r = fwd_cos(T); push(r.d); T = r.v; } break;
+          case OP_EXP: { const VD r = fwd_exp(T); push(r.d); T = r.v; } break;
+          case OP_LOG: { const VD r = fwd_log(T); push(r.d); T = r.v; } break;
+          case OP_SQRT: { const VD r = fwd_sqrt(T); push(r.d); T = r.v; } break;
+          case OP_SQ: push(addg(T, T)); T = mulg(T, T); break;
           case OP_INV:
           case OP_TAN:
           case OP_ASIN:
           case OP_ACOS:
           case OP_ATAN:
-          case OP_TANH: { const float4 r = fwd_ext(ins_op(ins), T); push(hi2(r)); T = lo2(r); } break;
-          case OP_VADD: T = add2(T, ldx2(xr, ins.y)); break;
-          case OP_VSUB: T = sub2(T, ldx2(xr, ins.y)); break;
-          case OP_VRSUB: T = sub2(ldx2(xr, ins.y), T); break;
-          case OP_VMUL: T = mul2(T, ldx2(xr, ins.y)); break;
-          case OP_VDIV: T = pdiv2(T, ldx2(xr, ins.y)); break;
-          case OP_VRDIV: push(T); T = pdiv2(ldx2(xr, ins.y), T); push(T); break;
-          case OP_CADD: T = add2(T, splat2(cv)); break;
-          case OP_CSUB: T = sub2(T, splat2(cv)); break;
-          case OP_CRSUB: T = sub2(splat2(cv), T); break;
-          case OP_CMUL: push(T); T = mul2(T, splat2(cv)); break;
-          case OP_CDIV: T = pdiv2(T, splat2(cv)); push(T); break;
-          case OP_CRDIV: push(T); T = pdiv2(splat2(cv), T); push(T); break;
+          case OP_TANH: { const VD r = fwd_ext(ins_op(ins), T); push(r.d); T = r.v; } break;
+          case OP_VADD: T = addg(T, ldxg(xr, ins.y)); break;
+          case OP_VSUB: T = subg(T, ldxg(xr, ins.y)); break;
+          case OP_VRSUB: T = subg(ldxg(xr, ins.y), T); break;
+          case OP_VMUL: T = mulg(T, ldxg(xr, ins.y)); break;
+          case OP_VDIV: T = pdivg(T, ldxg(xr, ins.y)); break;
+          case OP_VRDIV: push(T); T = pdivg(ldxg(xr, ins.y), T); push(T); break;
+          case OP_CADD: T = addg(T, splatg(cv)); break;
+          case OP_CSUB: T = subg(T, splatg(cv)); break;
+          case OP_CRSUB: T = subg(splatg(cv), T); break;
+          case OP_CMUL: push(T); T = mulg(T, splatg(cv)); break;
+          case OP_CDIV: T = pdivg(T, splatg(cv)); push(T); break;
+          case OP_CRDIV: push(T); T = pdivg(splatg(cv), T); push(T); break;
           default: break;
         }
       }
       // ---- loss and seed: e = yhat - y on valid cases, 0 elsewhere
-      const float y0 = ok0 ? __ldg(p.y + c0) : 0.0f, y1 = ok1 ? __ldg(p.y + c0 + 1) : 0.0f;
-      const float2 e = make_float2(ok0 ? T.x - y0 : 0.0f, ok1 ? T.y - y1 : 0.0f);
-      se.add(e.x * e.x + e.y * e.y);
+      VG e;
+      float e2 = 0.0f;
+#pragma unroll
+      for (int i = 0; i < GCPL; ++i) {
+        const bool ok = (okm >> i) & 1u;
+        e.v[i] = ok ? T.v[i] - __ldg(p.y + c0 + i) : 0.0f;
+        e2 += e.v[i] * e.v[i];
+      }
+      se.add(e2);
       // ---- reverse
-      float2 aT = e;
+      VG aT = e;
       for (int ip = n - 1; ip >= 0; --ip) {
         const uint2 ins = w.code[ip];
         const uint32_t off = ins_off(ins);
@@ -354,27 +440,27 @@ __global__ void __launch_bounds__(GWARPS * 32) grad_kernel(GradParams p) {
         const int k = ins_k(ins);
         switch (ins_op(ins)) {
           case OP_LDV: break;
-          case OP_LDC: gacc(w, k, aT, ok0, ok1); break;
+          case OP_LDC: gacc(w, k, aT, okm); break;
           case OP_PUSHV: aT = *slot_at(w, off); break;
-          case OP_PUSHC: gacc(w, k, aT, ok0, ok1); aT = *slot_at(w, off); break;
+          case OP_PUSHC: gacc(w, k, aT, okm); aT = *slot_at(w, off); break;
           case OP_ADD: *slot_at(w, off) = aT; break;
-          case OP_SUB: *slot_at(w, off) = aT; aT = neg2(aT); break;
-          case OP_RSUB: *slot_at(w, off) = neg2(aT); break;
+          case OP_SUB: *slot_at(w, off) = aT; aT = negg(aT); break;
+          case OP_RSUB: *slot_at(w, off) = negg(aT); break;
           case OP_MUL: {  // T = a t
-            const float2 t = pop(), a = pop();
-            *slot_at(w, off) = mul2(aT, t);
-            aT = mul2(aT, a);
+            const VG t = pop(), a = pop();
+            *slot_at(w, off) = mulg(aT, t);
+            aT = mulg(aT, a);
           } break;
           case OP_DIV: {  // T = a / t: dT/da = 1/t, dT/dt = -T/t
-            const float2 Tn = pop(), t = pop();
-            const float2 q = qdiv2(aT, t);
+            const VG Tn = pop(), t = pop();
+            const VG q = qdivg(aT, t);
             *slot_at(w, off) = q;
-            aT = neg2(mul2(q, Tn));
+            aT = negg(mulg(q, Tn));
           } break;
           case OP_RDIV: {  // T = t / b
-            const float2 Tn = pop(), b = pop();
-            const float2 q = qdiv2(aT, b);
-            *slot_at(w, off) = neg2(mul2(q, Tn));
+            const VG Tn = pop(), b = pop();
+            const VG q = qdivg(aT, b);
+            *slot_at(w, off) = negg(mulg(q, Tn));
             aT = q;
           } break;
           case OP_SIN:
@@ -388,35 +474,35 @@ __global__ void __launch_bounds__(GWARPS * 32) grad_kernel(GradParams p) {
           case OP_ASIN:
           case OP_ACOS:
           case OP_ATAN:
-          case OP_TANH: { const float2 d = pop(); aT = mul2(aT, d); } break;
+          case OP_TANH: { const VG d = pop(); aT = mulg(aT, d); } break;
           case OP_VADD:
           case OP_VSUB: break;
-          case OP_VRSUB: aT = neg2(aT); break;
-          case OP_VMUL: aT = mul2(aT, ldx2(xr, ins.y)); break;
-          case OP_VDIV: aT = qdiv2(aT, ldx2(xr, ins.y)); break;
+          case OP_VRSUB: aT = negg(aT); break;
+          case OP_VMUL: aT = mulg(aT, ldxg(xr, ins.y)); break;
+          case OP_VDIV: aT = qdivg(aT, ldxg(xr, ins.y)); break;
           case OP_VRDIV: {  // T = v / t
-            const float2 Tn = pop(), t = pop();
-            aT = neg2(mul2(qdiv2(aT, t), Tn));
+            const VG Tn = pop(), t = pop();
+            aT = negg(mulg(qdivg(aT, t), Tn));
           } break;
-          case OP_CADD: gacc(w, k, aT, ok0, ok1); break;
-          case OP_CSUB: gacc(w, k, neg2(aT), ok0, ok1); break;
-          case OP_CRSUB: gacc(w, k, aT, ok0, ok1); aT = neg2(aT); break;
+          case OP_CADD: gacc(w, k, aT, okm); break;
+          case OP_CSUB: gacc(w, k, negg(aT), okm); break;
+          case OP_CRSUB: gacc(w, k, aT, okm); aT = negg(aT); break;
           case OP_CMUL: {  // T = t c
-            const float2 t = pop();
-            gacc(w, k, mul2(aT, t), ok0, ok1);
-            aT = mul2(aT, splat2(cv));
+            const VG t = pop();
+            gacc(w, k, mulg(aT, t), okm);
+            aT = mulg(aT, splatg(cv));
           } break;
           case OP_CDIV: {  // T = t / c: dT/dt = 1/c, dT/dc = -T/c
-            const float2 Tn = pop();
-            const float2 q = qdiv2(aT, splat2(cv));
-            gacc(w, k, neg2(mul2(q, Tn)), ok0, ok1);
+            const VG Tn = pop();
+            const VG q = qdivg(aT, splatg(cv));
+            gacc(w, k, negg(mulg(q, Tn)), okm);
             aT = q;
           } break;
           case OP_CRDIV: {  // T = c / t: dT/dc = 1/t, dT/dt = -T/t
-            const float2 Tn = pop(), t = pop();
-            const float2 q = qdiv2(aT, t);
-            gacc(w, k, q, ok0, ok1);
-            aT = neg2(mul2(q, Tn));
+            const VG Tn = pop(), t = pop();
+            const VG q = qdivg(aT, t);
+            gacc(w, k, q, okm);
+            aT = negg(mulg(q, Tn));
           } break;
           default: break;
         }
