@@ -43,9 +43,6 @@ EVAL_NCU = {"dram_bytes": 7.98e6 + 0.82e6, "issue_active": 0.846}
 # smsp__issue_active.  Traffic is reported for the captured workload, and for
 # another size only where it grows with the units (scale).
 KERNEL_NCU = {
-    # grad_kernel: the tape write-back evicted from L2 grows with the units
-    "grad": {"workload": "adjoint-2048x131072", "dram_bytes": 0.531e9 + 11.778e9, "units": 1.3324e10,
-             "issue_active": 0.819, "scale": True},
     # eval_kernel<R4>: inputs read once (L2-resident), at the full size
     "beagle": {"workload": "beagle-4096x100k", "dram_bytes": 7.60e6 + 0.85e6, "units": 2.3995e10,
                "issue_active": 0.776, "scale": False},
