@@ -50,7 +50,7 @@ constexpr int CPL = 8;          // cases per lane per dispatched instruction (tw
 constexpr int STEP = 32 * CPL;  // cases per warp step
 constexpr int SLOT_BYTES = 32 * CPL * 4;  // one stack slot of a warp: [2][32 lanes] float4
 constexpr int PSTRIDE = 8;      // doubles per partial record
-constexpr int TARGET_ITEMS_PER_WARP = 20;  // balances the launch tail; measured best of 8 to 28 at 4,096 x 100k
+constexpr int TARGET_ITEMS_PER_WARP = 16;  // balances the launch tail; measured best of 8 to 28 at 4,096 x 100k
 // Occupancy variants of the evaluation kernel: MINB CTAs of WARPS warps per
 // SM.  Shared memory per CTA that leaves room for MINB of them (228 KB per
 // SM, 1 KB of it reserved per CTA); the registers are bounded to match
