@@ -36,13 +36,16 @@ L2_BYTES = 129 * 1024 * 1024
 # eval_kernel<3, 0> on this workload, from one ncu --set full capture
 # (profiles/eval_kernel_paper-4096x100k.md): dram__bytes_read.sum +
 # dram__bytes_write.sum per launch, and smsp__issue_active
-EVAL_NCU = {"dram_bytes": 7.98e6 + 0.82e6, "issue_active": 0.846}
+EVAL_NCU = {"dram_bytes": 8.00e6 + 0.79e6, "issue_active": 0.848}
 # the other workloads' dominant kernels, each from one ncu --set full capture
 # (profiles/): the captured workload, DRAM bytes (read + write) of the
 # captured launch, the units (node-evaluations) it processed, and
 # smsp__issue_active.  Traffic is reported for the captured workload, and for
 # another size only where it grows with the units (scale).
 KERNEL_NCU = {
+    # grad_kernel: the tape write-back evicted from L2 grows with the units
+    "grad": {"workload": "adjoint-2048x131072", "dram_bytes": 7.554e9 + 23.945e9, "units": 1.3324e10,
+             "issue_active": 0.722, "scale": True},
     # eval_kernel<R4>: inputs read once (L2-resident), at the full size
     "beagle": {"workload": "beagle-4096x100k", "dram_bytes": 7.60e6 + 0.85e6, "units": 2.3995e10,
                "issue_active": 0.776, "scale": False},
