@@ -96,6 +96,38 @@ def test_vary_bit_exact(ctx, cfg):
         assert (flags == 0).all()
 
 
+def test_vary_bit_exact_long_rows(ctx):
+    """Rows of 509 tokens (the warp's shared-memory rows are padded to 512)
+    and a child count that does not fill the last block: children bit for
+    bit the oracle's, valid, and their outputs inside the oracle's enclosure
+    (the decoder's rows and constants at an odd Lmax)."""
+    P, Lmax, K, nv = 999, 509, 5, 4
+    prog, lens, c = oracle.random_programs(P, 1, Lmax, K, nv, -2.0, 2.0, 77, 3)
+    rng = np.random.default_rng(5)
+    par = rng.integers(0, P, size=(P, 2)).astype(np.int32)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    cfg = dict(p_cross=0.9, p_point=0.5, p_subtree=0.5, p_const=0.5, const_delta=1.0, max_subtree=12)
+    po, lo, co = binding.sr_vary(ctx, t(prog), t(lens), t(c), t(par), nv, binding.var_cfg(**cfg), 99, 4)
+    wp, wl, wc = oracle.vary(prog, lens, c, par, K, nv, seed=99, gen=4, **cfg)
+    np.testing.assert_array_equal(lo.cpu().numpy(), wl)
+    np.testing.assert_array_equal(po.cpu().numpy(), wp)
+    np.testing.assert_array_equal(co.cpu().numpy().view(np.uint32), wc.view(np.uint32))
+    flags, _ = oracle.validate_all(wp, wl, nv, K)
+    assert (flags == 0).all()
+    X = inputs.random_X(np.random.default_rng(6), nv, 37, 0.5, 1.5)
+    yh = binding.sr_predict(ctx, po, lo, co, t(X), 37)
+    torch.cuda.synchronize()
+    yh = yh.cpu().numpy()
+    checked = 0
+    for i in range(0, P, 7):
+        _, lo_i, hi_i, cf = oracle.predict_interval(wp[i, : wl[i]], wc[i], X, 37)
+        g = yh[i, :37].astype(np.float64)
+        ok = cf == 0
+        assert ((lo_i <= g) & (g <= hi_i))[ok].all(), i
+        checked += int(ok.sum())
+    assert checked > 0.5 * len(range(0, P, 7)) * 37
+
+
 def test_fifty_generation_chain_bit_exact(ctx):
     """Selection + variation for 50 generations: the device population equals
     the oracle's after every generation (fitness from the oracle, the same
