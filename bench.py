@@ -87,6 +87,14 @@ def parse():
 
 
 # ------------------------------------------------------------------ helpers
+def host_cores() -> int:
+    """Host cores this process may run on (its CPU affinity)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -163,11 +171,12 @@ def run_reference(args, rank, world):
         if np.all(np.isfinite(y64)) and np.abs(y64).max() < 1e15 and np.std(y64) > 1e-6 * (1 + np.abs(y64).max()):
             break
     y = inputs.add_noise(np.random.default_rng(pr.seed + 7), y64, pr.noise)
-    cores = os.cpu_count() or 1
+    # every host core, named explicitly: torchrun sets OMP_NUM_THREADS=1 for its ranks
+    cores = host_cores()
     # size each step to ~4 s of CPU work: programs sampled from the population, all cases
     t0 = time.perf_counter()
-    oracle.evaluate(pr.programs[:16], pr.lengths[:16], pr.consts[:16], pr.X, y, oracle.CORR, pr.N)
-    oracle.evaluate(pr.programs[:16], pr.lengths[:16], pr.consts[:16], pr.X, y, oracle.MSE, pr.N)
+    oracle.evaluate(pr.programs[:16], pr.lengths[:16], pr.consts[:16], pr.X, y, oracle.CORR, pr.N, nthreads=cores)
+    oracle.evaluate(pr.programs[:16], pr.lengths[:16], pr.consts[:16], pr.X, y, oracle.MSE, pr.N, nthreads=cores)
     dt16 = max(time.perf_counter() - t0, 1e-3)
     S = int(min(pr.P, max(16, 16 * 4.0 / dt16)))
     rng = np.random.default_rng(1)
@@ -175,8 +184,8 @@ def run_reference(args, rank, world):
     for step in range(args.warmup + args.steps):
         idx = np.sort(rng.choice(pr.P, S, replace=False))
         t0 = time.perf_counter()
-        oracle.evaluate(pr.programs[idx], pr.lengths[idx], pr.consts[idx], pr.X, y, oracle.MSE, pr.N)
-        oracle.evaluate(pr.programs[idx], pr.lengths[idx], pr.consts[idx], pr.X, y, oracle.CORR, pr.N)
+        oracle.evaluate(pr.programs[idx], pr.lengths[idx], pr.consts[idx], pr.X, y, oracle.MSE, pr.N, nthreads=cores)
+        oracle.evaluate(pr.programs[idx], pr.lengths[idx], pr.consts[idx], pr.X, y, oracle.CORR, pr.N, nthreads=cores)
         dt = time.perf_counter() - t0
         if step >= args.warmup:
             times.append(dt)
@@ -372,15 +381,15 @@ def run_ours(args, rank, world, local_rank):
 def cpu_baseline(pr, y):
     """The oracle as it stands on all host cores, on a bounded sample (~10-20 s)."""
     import oracle
-    cores = os.cpu_count() or 1
+    cores = host_cores()
     t0 = time.perf_counter()
-    oracle.evaluate(pr.programs[:16], pr.lengths[:16], pr.consts[:16], pr.X, y, oracle.MSE, pr.N)
+    oracle.evaluate(pr.programs[:16], pr.lengths[:16], pr.consts[:16], pr.X, y, oracle.MSE, pr.N, nthreads=cores)
     dt16 = max(time.perf_counter() - t0, 1e-3)
     S = int(min(pr.P, max(16, 16 * 6.0 / dt16)))
     idx = np.sort(np.random.default_rng(2).choice(pr.P, S, replace=False))
     t0 = time.perf_counter()
-    oracle.evaluate(pr.programs[idx], pr.lengths[idx], pr.consts[idx], pr.X, y, oracle.MSE, pr.N)
-    oracle.evaluate(pr.programs[idx], pr.lengths[idx], pr.consts[idx], pr.X, y, oracle.CORR, pr.N)
+    oracle.evaluate(pr.programs[idx], pr.lengths[idx], pr.consts[idx], pr.X, y, oracle.MSE, pr.N, nthreads=cores)
+    oracle.evaluate(pr.programs[idx], pr.lengths[idx], pr.consts[idx], pr.X, y, oracle.CORR, pr.N, nthreads=cores)
     dt = time.perf_counter() - t0
     units = float(pr.lengths[idx].astype(np.int64).sum()) * pr.N
     return {"value": units / dt / 1e9, "unit": "GPop/s", "cores": cores, "kind": "oracle",
