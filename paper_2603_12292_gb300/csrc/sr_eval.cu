@@ -45,7 +45,7 @@
 namespace sr {
 namespace {
 
-constexpr int WARPS = 8;        // warps per CTA (4 CTAs x 8 warps per SM at Lmax 128; measured best of 4, 8, 16)
+constexpr int WARPS = 8;        // warps per CTA (measured best of 4, 8, 16 warps per CTA)
 constexpr int CPL = 8;          // cases per lane per dispatched instruction (two float4)
 constexpr int STEP = 32 * CPL;  // cases per warp step
 constexpr int SLOT_BYTES = 32 * CPL * 4;  // one stack slot of a warp: [2][32 lanes] float4

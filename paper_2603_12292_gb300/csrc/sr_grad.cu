@@ -17,7 +17,7 @@
 //               re-read, c_k is in the instruction).  The tape lives in
 //               shared memory when a whole one (Lmax entries) fits there,
 //               else in this warp's global scratch: most of it is in L2, its
-//               latency hidden by 48 warps per SM.
+//               latency hidden by 40 warps per SM.
 //   reverse  -- the instructions are walked backwards with the adjoint of
 //               the top in registers; a binary operator writes the adjoint
 //               of the operand it popped into that operand's stack slot (the
