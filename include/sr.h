@@ -62,7 +62,8 @@ typedef enum {
   SR_ECUDA = 2,    /* a CUDA runtime call failed                          */
   SR_ETIMEOUT = 3, /* a bounded device wait gave up (latched error word)  */
   SR_EPROGRAM = 4, /* reserved: invalid programs are flagged, not errors  */
-  SR_ENOMEM = 5    /* workspace growth failed or was refused in capture   */
+  SR_ENOMEM = 5,   /* workspace growth failed or was refused in capture   */
+  SR_EABORTED = 6  /* the abort flag stopped a call (latched error word)  */
 } sr_status;
 
 /* Fitness kinds.  SR_MSE: mean((yhat - y)^2).  SR_CORR: 1 - r^2 with r the
@@ -120,8 +121,20 @@ sr_status sr_reserve(sr_ctx *ctx, int P, int Lmax, int N);
 uint64_t sr_kernel_launches(const sr_ctx *ctx);
 
 /* Wait for all work on the context's stream and report device-side errors
- * latched since the last sr_sync (SR_ETIMEOUT), else SR_OK. */
+ * latched since the last sr_sync (SR_EABORTED, SR_ETIMEOUT), else SR_OK.
+ * The latched word is cleared. */
 sr_status sr_sync(sr_ctx *ctx);
+
+/* Host-side cancellation of long calls.  flag: device int32 owned by the
+ * caller, or NULL (the default) for none.  While *flag is nonzero, the warps
+ * of sr_eval, sr_eval_score, sr_predict, sr_eval_batched and sr_eval_grad
+ * take no further work items: a call that sees the flag ends early, its
+ * outputs are undefined, and the next sr_sync returns SR_EABORTED.  The flag
+ * is read when a warp takes a work item (uncached), never waited on: setting
+ * it from another stream or the host while a call runs stops the call within
+ * one work item per warp.  Later calls run normally once the flag is zero.
+ * Errors: SR_EINVAL (ctx NULL). */
+sr_status sr_set_abort_flag(sr_ctx *ctx, const int32_t *flag);
 
 /*
  * sr_eval -- fitness of every program (Sec. 2.1.2 aggregation; Eq. 1 for

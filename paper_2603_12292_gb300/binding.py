@@ -15,7 +15,7 @@ import torch
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libsr.so")
 
-SR_OK, SR_EINVAL, SR_ECUDA, SR_ETIMEOUT, SR_EPROGRAM, SR_ENOMEM = range(6)
+SR_OK, SR_EINVAL, SR_ECUDA, SR_ETIMEOUT, SR_EPROGRAM, SR_ENOMEM, SR_EABORTED = range(7)
 SR_MSE, SR_CORR, SR_MSE_CORR = 0, 1, 2
 SR_SCORE_R4, SR_SCORE_P2P = 0, 1
 SR_MAX_LMAX, SR_MAX_VARS, SR_MAX_CONSTS = 512, 16, 16
@@ -26,7 +26,7 @@ EXPORTS = ["sr_create", "sr_destroy", "sr_set_stream", "sr_status_string", "sr_l
            "sr_eval_noalloc", "sr_philox4x32_10", "sr_select_tournament", "sr_vary",
            "sr_random_programs", "sr_eval_grad", "sr_adam_step", "sr_eval_batched", "sr_set_tile",
            "sr_eval_score", "sr_select_tournament_max", "sr_select_microcosm",
-           "sr_set_generation_source"]
+           "sr_set_generation_source", "sr_set_abort_flag"]
 
 _lib = None
 
@@ -91,6 +91,7 @@ def lib() -> ctypes.CDLL:
     L.sr_last_error.restype = ctypes.c_char_p
     L.sr_reserve.argtypes = [vp, i32, i32, i32]
     L.sr_sync.argtypes = [vp]
+    L.sr_set_abort_flag.argtypes = [vp, vp]
     L.sr_kernel_launches.argtypes = [vp]
     L.sr_kernel_launches.restype = u64
     L.sr_eval.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp, vp, i32, i32, i32, i32, vp, vp]
@@ -174,6 +175,18 @@ def sr_kernel_launches(ctx: Context) -> int:
 
 def sr_sync(ctx: Context):
     _check(ctx, lib().sr_sync(ctx.handle))
+
+
+def sr_set_abort_flag(ctx: Context, flag: torch.Tensor | None):
+    """Device int32 flag (one element) that stops the context's long calls
+    while nonzero (sr_sync then raises SR_EABORTED), or None.  The caller
+    keeps the tensor alive while it is set."""
+    if flag is not None:
+        _dev(flag, torch.int32, "flag")
+        ctx._abort_flag = flag  # keep it alive with the context
+    else:
+        ctx._abort_flag = None
+    _check(ctx, lib().sr_set_abort_flag(ctx.handle, ctypes.c_void_p(flag.data_ptr() if flag is not None else 0)))
 
 
 def sr_eval(ctx: Context, programs, lengths, consts, X, y, N: int, kind: int,

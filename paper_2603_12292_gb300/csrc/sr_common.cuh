@@ -20,6 +20,7 @@ struct sr_ctx {
   uint64_t launches = 0;  // kernels launched by this context
   int tile_cases = 0;     // cases per evaluation work item (0: automatic)
   const uint64_t *gen_dev = nullptr;  // device generation counter for selection / variation
+  const int32_t *abort_flag = nullptr;  // sr_set_abort_flag (device, or NULL)
 };
 
 namespace sr {
@@ -53,6 +54,25 @@ __host__ __device__ __forceinline__ int cls_effect(int c) {
 
 // device error word bits (latched; reported and cleared by sr_sync)
 constexpr unsigned ERR_TIMEOUT = 1u;
+constexpr unsigned ERR_ABORTED = 2u;
+
+// The next work item of a persistent warp (lane 0 draws it from the atomic
+// counter q and the warp shares it), or `total` (no more items) when the
+// abort flag is set; then the abort is latched in the error word.  Only
+// lane 0 touches memory.
+__device__ __forceinline__ long long next_item(unsigned long long *q, long long total, const int32_t *abort_flag,
+                                               unsigned *err_word, int lane) {
+  long long item = 0;
+  if (lane == 0) {
+    if (abort_flag && *reinterpret_cast<const volatile int32_t *>(abort_flag) != 0) {
+      atomicOr(err_word, ERR_ABORTED);
+      item = total;
+    } else {
+      item = (long long)atomicAdd(q, 1ull);
+    }
+  }
+  return __shfl_sync(FULL, item, 0);
+}
 
 // status helpers (sr_ctx.cu)
 sr_status fail(sr_ctx *ctx, sr_status s, const char *fmt, ...);

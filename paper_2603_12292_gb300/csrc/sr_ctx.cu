@@ -119,6 +119,7 @@ const char *sr_status_string(sr_status s) {
     case SR_ETIMEOUT: return "device wait timed out";
     case SR_EPROGRAM: return "invalid program";
     case SR_ENOMEM: return "out of workspace memory";
+    case SR_EABORTED: return "aborted by the abort flag";
   }
   return "unknown status";
 }
@@ -135,9 +136,18 @@ sr_status sr_sync(sr_ctx *ctx) {
   SR_CHECK_CUDA(ctx, cudaMemcpy(&word, ctx->dev_words, sizeof(word), cudaMemcpyDeviceToHost));
   if (word) {
     SR_CHECK_CUDA(ctx, cudaMemset(ctx->dev_words, 0, sizeof(word)));
+    if (word & sr::ERR_ABORTED)
+      return sr::fail(ctx, SR_EABORTED, "the abort flag stopped a call: its outputs are undefined (error word 0x%x)",
+                      word);
     if (word & sr::ERR_TIMEOUT)
       return sr::fail(ctx, SR_ETIMEOUT, "a bounded device wait gave up (error word 0x%x)", word);
   }
+  return SR_OK;
+}
+
+sr_status sr_set_abort_flag(sr_ctx *ctx, const int32_t *flag) {
+  if (!ctx) return SR_EINVAL;
+  ctx->abort_flag = flag;
   return SR_OK;
 }
 

@@ -90,6 +90,8 @@ struct EvalParams {
   int slots;               // stack slots per warp
   int deep;                // 1: this launch is the pass of the NCODE_DEEP programs
   int score_M;             // Beagle scores: the maximum score per case
+  const int32_t *abort;    // sr_set_abort_flag (or NULL)
+  unsigned *err;           // the context's latched error word
 };
 
 __host__ __device__ inline int code_smem_bytes(int Lmax) { return ((Lmax * 8 + 15) / 16) * 16; }
@@ -600,10 +602,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) eval_kernel(EvalParams p) {
   const WarpSmem w = warp_smem(smem, warp, p.warp_bytes, p.slots);
   unsigned long long *q = p.queue + (deep ? 3 : (EXT ? 1 : 0));
   for (;;) {
-    unsigned long long item = 0;
-    if (lane == 0) item = atomicAdd(q, 1ull);
-    item = __shfl_sync(FULL, item, 0);
-    if ((long long)item >= p.total_items) break;
+    const long long item = next_item(q, p.total_items, p.abort, p.err, lane);
+    if (item >= p.total_items) break;
     const int c = (int)(item / (unsigned long long)p.P);
     const int prog = (int)(item % (unsigned long long)p.P);
     const int nc = p.ncode[prog];
@@ -651,6 +651,8 @@ struct BatchParams {
   int warp_bytes;
   int slots;
   int deep;                   // as EvalParams::deep
+  const int32_t *abort;       // as EvalParams::abort
+  unsigned *err;
 };
 
 __device__ __forceinline__ EvalParams view(const BatchProblem &q) {
@@ -709,10 +711,8 @@ __global__ void __launch_bounds__(WARPS * 32, 4) eval_batched_kernel(const __gri
   const WarpSmem w = warp_smem(smem, warp, b.warp_bytes, b.slots);
   unsigned long long *qc = b.queue + (deep ? 3 : (EXT ? 1 : 0));
   for (;;) {
-    unsigned long long item = 0;
-    if (lane == 0) item = atomicAdd(qc, 1ull);
-    item = __shfl_sync(FULL, item, 0);
-    if ((long long)item >= b.total_items) break;
+    const long long item = next_item(qc, b.total_items, b.abort, b.err, lane);
+    if (item >= b.total_items) break;
     int lo = 0, hi = b.nprob - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
@@ -1177,6 +1177,8 @@ sr_status launch_eval(sr_ctx *ctx, int mode, const uint8_t *programs, const int3
   ep.slots = pl.slots;
   ep.warp_bytes = warp_smem_bytes(pl.slots, Lmax);
   ep.deep = 0;
+  ep.abort = ctx->abort_flag;
+  ep.err = ctx->dev_words;
   ep.score_M = M;
 
   int grid_ext = 0, grid_deep = 0;
@@ -1368,6 +1370,8 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
       bpar->slots = bslots;
       bpar->warp_bytes = warp_smem_bytes(bpar->slots, maxL);
       bpar->deep = 0;
+      bpar->abort = ctx->abort_flag;
+      bpar->err = ctx->dev_words;
     }
     return cv.off;
   };

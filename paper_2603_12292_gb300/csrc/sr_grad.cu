@@ -76,6 +76,8 @@ struct GradParams {
   int16_t *s_task;
   unsigned long long *queue;
   char *gtape;        // per warp: Lmax entries of GSLOT bytes (tape off chip), else NULL
+  const int32_t *abort;  // sr_set_abort_flag (or NULL)
+  unsigned *err;         // the context's latched error word
   int warp_bytes;
 };
 
@@ -348,10 +350,8 @@ __global__ void __launch_bounds__(GWARPS * 32) grad_kernel(GradParams p) {
   w.lane = lane;
 
   for (;;) {
-    unsigned long long item = 0;
-    if (lane == 0) item = atomicAdd(p.queue, 1ull);
-    item = __shfl_sync(FULL, item, 0);
-    if ((long long)item >= p.total_items) break;
+    const long long item = next_item(p.queue, p.total_items, p.abort, p.err, lane);
+    if (item >= p.total_items) break;
     const int c = (int)(item / (unsigned long long)p.P);
     const int prog = (int)(item % (unsigned long long)p.P);
     if (p.flags[prog]) continue;
@@ -639,6 +639,8 @@ sr_status sr_eval_grad(sr_ctx *ctx, const uint8_t *programs, const int32_t *leng
   gp.s_task = nullptr;
   gp.queue = reinterpret_cast<unsigned long long *>(ws + off_q);
   gp.gtape = onchip ? nullptr : ws + off_t;
+  gp.abort = ctx->abort_flag;
+  gp.err = ctx->dev_words;
   gp.warp_bytes = warp_bytes;
   cudaStream_t s = ctx->stream;
   SR_CHECK_CUDA(ctx, cudaMemsetAsync(gp.queue, 0, 8, s));
