@@ -36,7 +36,7 @@ L2_BYTES = 129 * 1024 * 1024
 # eval_kernel<3, 0> on this workload, from one ncu --set full capture
 # (profiles/eval_kernel_paper-4096x100k.md): dram__bytes_read.sum +
 # dram__bytes_write.sum per launch, and smsp__issue_active
-EVAL_NCU = {"dram_bytes": 8.00e6 + 0.79e6, "issue_active": 0.848}
+EVAL_NCU = {"dram_bytes": 7.98e6 + 0.76e6, "issue_active": 0.852}
 # the other workloads' dominant kernels, each from one ncu --set full capture
 # (profiles/): the captured workload, DRAM bytes (read + write) of the
 # captured launch, the units (node-evaluations) it processed, and
@@ -44,17 +44,17 @@ EVAL_NCU = {"dram_bytes": 8.00e6 + 0.79e6, "issue_active": 0.848}
 # another size only where it grows with the units (scale).
 KERNEL_NCU = {
     # grad_kernel: the tape write-back evicted from L2 grows with the units
-    "grad": {"workload": "adjoint-2048x131072", "dram_bytes": 7.554e9 + 23.945e9, "units": 1.3324e10,
-             "issue_active": 0.722, "scale": True},
+    "grad": {"workload": "adjoint-2048x131072", "dram_bytes": 7.589e9 + 23.968e9, "units": 1.3324e10,
+             "issue_active": 0.723, "scale": True},
     # eval_kernel<R4>: inputs read once (L2-resident), at the full size
-    "beagle": {"workload": "beagle-4096x100k", "dram_bytes": 7.60e6 + 0.85e6, "units": 2.3995e10,
-               "issue_active": 0.776, "scale": False},
+    "beagle": {"workload": "beagle-4096x100k", "dram_bytes": 7.27e6 + 0.80e6, "units": 2.3977e10,
+               "issue_active": 0.760, "scale": False},
     # eval_batched_kernel: the first 8 problems; inputs read once
-    "batched": {"workload": "batched-8", "dram_bytes": 45.13e6 + 1.41e6, "units": 4.0723e11,
-                "issue_active": 0.836, "scale": False},
+    "batched": {"workload": "batched-8", "dram_bytes": 45.01e6 + 1.31e6, "units": 4.0723e11,
+                "issue_active": 0.833, "scale": False},
     # eval_kernel<CORR> at Lmax 256: inputs read once
-    "large": {"workload": "large-16384x131072", "dram_bytes": 21.41e6 + 0.72e6, "units": 2.5087e11,
-              "issue_active": 0.824, "scale": False},
+    "large": {"workload": "large-16384x131072", "dram_bytes": 21.32e6 + 0.66e6, "units": 2.5087e11,
+              "issue_active": 0.822, "scale": False},
 }
 
 
