@@ -180,6 +180,42 @@ class Evolver:
         finally:
             binding.sr_set_generation_source(self.ctx, None)
 
+    # -- checkpoint / resume ----------------------------------------------------
+    def state_dict(self) -> dict:
+        """What a later run needs to continue bit for bit: each population's
+        current rows (tokens, lengths, constants), its size and initial size,
+        and the generation counters.  Selection and variation draw
+        counter-based Philox numbers from (seed, generation, individual), and
+        the per-generation buffers (fitness, parents, Adam moments) are
+        rebuilt every generation, so nothing else is kept.  Reads the device
+        generation counter (synchronises)."""
+        pops = []
+        for p in self.pops:
+            P_, L_, C_ = p.current
+            pops.append({"programs": P_.clone(), "lengths": L_.clone(), "consts": C_.clone(),
+                         "size": p.size, "initial": p.initial})
+        return {"gen": int(self.gen.item()), "host_gen": self.host_gen, "pops": pops}
+
+    def load_state_dict(self, state: dict):
+        """Continue from state_dict() output: the rows go into buffer 0 of
+        each population (same Lmax and K, capacity at least the saved size),
+        the counters are restored, and a captured graph is dropped (it refers
+        to the old buffer order; capture again)."""
+        if len(state["pops"]) != len(self.pops):
+            raise ValueError("checkpoint has %d populations, this run %d" % (len(state["pops"]), len(self.pops)))
+        for p, s in zip(self.pops, state["pops"]):
+            dst = p.buf[0]
+            n = int(s["size"])
+            if (n > dst[0].shape[0] or tuple(s["programs"].shape[1:]) != tuple(dst[0].shape[1:])
+                    or tuple(s["consts"].shape[1:]) != tuple(dst[2].shape[1:])):
+                raise ValueError("checkpoint rows do not fit this population's buffers")
+            for d, src in zip(dst, (s["programs"], s["lengths"], s["consts"])):
+                d[:n].copy_(src)
+            p.cur, p.size, p.initial = 0, n, int(s["initial"])
+        self.gen.fill_(int(state["gen"]))
+        self.host_gen = int(state["host_gen"])
+        self.graph, self.graph_gens, self.graph_sizes = None, 0, None
+
     # -- CUDA graph -----------------------------------------------------------
     def capture(self, gens: int = 2):
         """Capture `gens` generations (even, so the buffers return to where they
