@@ -427,9 +427,16 @@ def _roofline(dev, achieved, kernel, timing, workload, ncu_key=None, units_per_l
     traffic = None
     if cap is not None and (same or cap["scale"]):
         traffic = cap["dram_bytes"] * (units_per_launch / cap["units"] if units_per_launch else 1.0)
+    # the DRAM side of the same launch: traffic over the launch time (units /
+    # achieved), against the measured copy bandwidth
+    hbm = None
+    if traffic is not None and units_per_launch and achieved > 0:
+        pk, psrc = peaks()
+        gbs = traffic / (units_per_launch / (achieved * 1e9)) / 1e9
+        hbm = {"gbs": gbs, "peak_gbs": pk["hbm_gbs"], "frac": gbs / pk["hbm_gbs"], "peak_source": psrc}
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GPop/s", "frac": achieved / peak,
             "traffic": traffic, "kernel": kernel, "timing": timing,
-            "issue_active_ncu": cap["issue_active"] if same else None, "peak_source": src}
+            "issue_active_ncu": cap["issue_active"] if same else None, "peak_source": src, "hbm": hbm}
 
 
 class _Region:

@@ -75,6 +75,17 @@ def test_roofline_traffic_scaled_only_where_it_grows_with_the_units(fixed_peak):
         assert r["traffic"] is None
 
 
+def test_roofline_dram_side_of_the_launch(fixed_peak, monkeypatch):
+    monkeypatch.setattr(bench, "peaks", lambda: ({"hbm_gbs": 6000.0}, "test"))
+    g = bench.KERNEL_NCU["grad"]
+    units = 10 * g["units"]
+    r = bench._roofline(None, 1000.0, "k", "t", "adjoint-16384x1M", "grad", units)
+    seconds = units / 1000.0e9
+    assert r["hbm"]["gbs"] == pytest.approx(10 * g["dram_bytes"] / seconds / 1e9)
+    assert r["hbm"]["frac"] == pytest.approx(r["hbm"]["gbs"] / 6000.0)
+    assert bench._roofline(None, 100.0, "k", "t", "plain-256x1k")["hbm"] is None
+
+
 def test_roofline_without_a_capture(fixed_peak):
     r = bench._roofline(None, 100.0, "k", "t", "plain-256x1k")
     assert r["traffic"] is None and r["issue_active_ncu"] is None and r["peak"] == 40273.92
