@@ -6,8 +6,9 @@ depth), uniform FP32 inputs, constants and Gaussian noise with numpy's
 seeded generator.  Tests feed the same arrays to the CUDA library and to the
 oracle; the bench uses them to build its workload.
 
-Token format (uint8): 0..3 binary ops (+ - * /p), 4..9 unary ops
-(sin cos exp log|.| sqrt|.| sq), 16 + j variable x_j, 32 + k constant c_k.
+Token format (uint8): 0..3 binary ops (+ - * /p), 4..15 unary ops (sin cos
+exp log|.| sqrt|.| sq, then 1/x tan asin acos atan tanh: the rest of Table 1),
+16 + j variable x_j, 32 + k constant c_k.
 
 Workload shapes follow the paper's setting (Sec. 2.1.2: a whole population
 evaluated on a batch of fitness cases per generation; Sec. 2.4: symbolic
