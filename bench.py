@@ -33,29 +33,66 @@ sys.path.insert(0, ROOT)
 
 METRIC = "GPop/s (nodes x cases / s) at 1 GB300 vs plain eval; % of FP32 issue peak"
 L2_BYTES = 129 * 1024 * 1024
-# eval_kernel<3, 0> on this workload, from one ncu --set full capture
-# (profiles/eval_kernel_paper-4096x100k.md): dram__bytes_read.sum +
-# dram__bytes_write.sum per launch, and smsp__issue_active
-EVAL_NCU = {"dram_bytes": 7.98e6 + 0.76e6, "issue_active": 0.852}
-# the other workloads' dominant kernels, each from one ncu --set full capture
-# (profiles/): the captured workload, DRAM bytes (read + write) of the
-# captured launch, the units (node-evaluations) it processed, and
-# smsp__issue_active.  Traffic is reported for the captured workload, and for
-# another size only where it grows with the units (scale).
+CSRC = os.path.join(ROOT, "paper_2603_12292_gb300", "csrc")
+# The CUDA sources each dominant kernel is built from: an ncu figure below is
+# reported only while these files hash to what they were when it was captured.
+KERNEL_SOURCES = {
+    "eval": ("sr_eval.cu", "sr_interp.cuh", "sr_common.cuh"),
+    "grad": ("sr_grad.cu", "sr_interp.cuh", "sr_common.cuh"),
+}
+# Dominant kernels of the workloads, each from one ncu --set full capture
+# summarised under profiles/: the captured workload, DRAM bytes (read +
+# write) of the captured launch, the units (node-evaluations) it processed,
+# smsp__issue_active, the summary file, and the hash of the kernel's sources
+# (source_hash) when it was taken.  Traffic is reported for the captured
+# workload, and for another size only where it grows with the units (scale).
 KERNEL_NCU = {
+    # eval_kernel<MODE_BOTH> on the headline workload, inputs read once
+    "paper": {"workload": "paper-4096x100k", "dram_bytes": 7.98e6 + 0.76e6, "units": None,
+              "issue_active": 0.852, "scale": False, "sources": "eval",
+              "capture": "profiles/eval_kernel_paper-4096x100k.md", "src": None},
     # grad_kernel: the tape write-back evicted from L2 grows with the units
     "grad": {"workload": "adjoint-2048x131072", "dram_bytes": 7.589e9 + 23.968e9, "units": 1.3324e10,
-             "issue_active": 0.723, "scale": True},
+             "issue_active": 0.723, "scale": True, "sources": "grad",
+             "capture": "profiles/grad_kernel_adjoint-2048x131072.md", "src": None},
     # eval_kernel<R4>: inputs read once (L2-resident), at the full size
     "beagle": {"workload": "beagle-4096x100k", "dram_bytes": 7.27e6 + 0.80e6, "units": 2.3977e10,
-               "issue_active": 0.760, "scale": False},
+               "issue_active": 0.760, "scale": False, "sources": "eval",
+               "capture": "profiles/eval_kernel_r4_beagle-4096x100k.md", "src": None},
     # eval_batched_kernel: the first 8 problems; inputs read once
     "batched": {"workload": "batched-8", "dram_bytes": 45.01e6 + 1.31e6, "units": 4.0723e11,
-                "issue_active": 0.833, "scale": False},
+                "issue_active": 0.833, "scale": False, "sources": "eval",
+                "capture": "profiles/eval_batched_kernel_batched-8.md", "src": None},
     # eval_kernel<CORR> at Lmax 256: inputs read once
     "large": {"workload": "large-16384x131072", "dram_bytes": 21.32e6 + 0.66e6, "units": 2.5087e11,
-              "issue_active": 0.822, "scale": False},
+              "issue_active": 0.822, "scale": False, "sources": "eval",
+              "capture": "profiles/eval_kernel_corr_large-16384x131072.md", "src": None},
 }
+
+
+def source_hash(kind: str) -> str:
+    """SHA-256 (first 16 hex digits) of the CUDA sources a kernel is built from."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[kind]:
+        with open(os.path.join(CSRC, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_record(key: str):
+    """The capture of a kernel if it still describes the current sources, and
+    its provenance either way: (record or None, provenance dict)."""
+    cap = KERNEL_NCU.get(key)
+    if cap is None:
+        return None, None
+    now = source_hash(cap["sources"])
+    prov = {"capture": cap["capture"], "src_at_capture": cap["src"], "src_now": now}
+    if cap["src"] != now:
+        prov["stale"] = ("no capture of the current kernel source" if cap["src"] is None
+                         else "the kernel source changed since the capture")
+        return None, prov
+    return cap, prov
 
 
 def parse():
@@ -299,11 +336,14 @@ def run_ours(args, rank, world, local_rank):
     achieved = float(np.mean([n * pr.N / (ms / 1e3) / 1e9 for n, ms in zip(nodes, eval_ms)]))
     # DRAM bytes per launch and issue-slot use of this kernel: one ncu capture
     # of the same command (profiles/eval_kernel_paper-4096x100k.md)
+    cap, prov = ncu_record("paper")
+    if args.ops != "base":
+        cap = None  # the capture is of the base operator set
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GPop/s",
-                "frac": achieved / peak, "traffic": EVAL_NCU["dram_bytes"] if args.ops == "base" else None,
+                "frac": achieved / peak, "traffic": cap["dram_bytes"] if cap else None,
                 "kernel": "eval_kernel (sr_eval SR_MSE_CORR)",
                 "eval_ms": float(np.mean(eval_ms)),
-                "issue_active_ncu": EVAL_NCU["issue_active"] if args.ops == "base" else None,
+                "issue_active_ncu": cap["issue_active"] if cap else None, "ncu_provenance": prov,
                 "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz ({src} max clock)"}
 
     # end to end through the public API with the population held on the host:
@@ -422,7 +462,7 @@ def _roofline(dev, achieved, kernel, timing, workload, ncu_key=None, units_per_l
     kernel from CUDA events; traffic: DRAM bytes per launch from its ncu
     capture (scaled by units where it grows with them), else null."""
     peak, src = _alu_peak(dev)
-    cap = KERNEL_NCU.get(ncu_key) if ncu_key else None
+    cap, prov = ncu_record(ncu_key) if ncu_key else (None, None)
     same = cap is not None and workload.split(":")[0] == cap["workload"]
     traffic = None
     if cap is not None and (same or cap["scale"]):
@@ -436,7 +476,8 @@ def _roofline(dev, achieved, kernel, timing, workload, ncu_key=None, units_per_l
         hbm = {"gbs": gbs, "peak_gbs": pk["hbm_gbs"], "frac": gbs / pk["hbm_gbs"], "peak_source": psrc}
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GPop/s", "frac": achieved / peak,
             "traffic": traffic, "kernel": kernel, "timing": timing,
-            "issue_active_ncu": cap["issue_active"] if same else None, "peak_source": src, "hbm": hbm}
+            "issue_active_ncu": cap["issue_active"] if same else None, "ncu_provenance": prov,
+            "peak_source": src, "hbm": hbm}
 
 
 class _Region:

@@ -456,14 +456,29 @@ sr_status sr_adam_step(sr_ctx *ctx, float *consts, const double *grad,
  *   other arguments and results as for sr_eval.
  * The first call on each device looks up the array's device address (once,
  * with that device current); make that first call before capturing a stream
- * into a CUDA graph.  The scratch is shared by every call on a device and
- * keeps the previous call's contents (each call clears what it needs
- * cleared), so calls whose work overlaps on the GPU race: issue them on one
- * stream, or order them with events.
- * Errors: SR_EINVAL as for sr_eval; SR_ENOMEM when the problem's scratch
- * (partial sums per program and case chunk, the centred target for 1 - r^2,
- * stack slots for deep programs) does not fit in 16 MiB even with the
- * persistent grid shrunk to one SM -- use sr_eval then; SR_ECUDA.
+ * into a CUDA graph.  With CUDA's lazy module loading (the default), the
+ * library's device code -- and with it the 16 MiB array -- is loaded on a
+ * device by the first libsr call there, whichever it is; that load is the
+ * one device allocation this entry point can cause, and only on its first
+ * call in a process that has made no other libsr call on that device.  A
+ * caller that must not allocate at all makes any libsr call on each device
+ * during start-up (or sets CUDA_MODULE_LOADING=EAGER).  The scratch is shared
+ * by every call on a device and keeps the previous call's contents (each
+ * call clears what it needs cleared), so calls whose work overlaps on the
+ * GPU race: issue them on one stream, or order them with events.
+ * Scratch of one call, in bytes (each term rounded up to 256):
+ *     P * 8 * Lmax            decoded instructions
+ *   + P * 64 * nchunks        partial sums per program and case chunk
+ *   + P * 8                   per-program flags and instruction counts
+ *   + 4 * N (rounded up to 256 cases)   centred target (1 - r^2 only)
+ *   + 32 * nchunks + 256      target chunk sums, work counters
+ * where nchunks (case chunks per program) is chosen as for sr_eval and is
+ * lowered, by shrinking the persistent grid, down to 1 when needed; so a
+ * problem fits when P * (8 * Lmax + 72) + 4 * N stays somewhat below 16 MiB
+ * (for example P = 8,192 programs of Lmax = 128 with N up to 10^6).
+ * Errors: SR_EINVAL as for sr_eval; SR_ENOMEM when the scratch does not fit
+ * in 16 MiB even with one case chunk per program -- use sr_eval then;
+ * SR_ECUDA.
  */
 sr_status sr_eval_noalloc(void *cuda_stream, const uint8_t *programs,
                           const int32_t *lengths, const float *consts, int P,

@@ -127,6 +127,34 @@ def _check(ctx, st: int):
         raise SRError(st, (msg or b"").decode() or lib().sr_status_string(st).decode())
 
 
+def _need(t, n: int, name: str):
+    """Raise ValueError when tensor t (if given) holds fewer than n elements."""
+    if t is not None and t.numel() < n:
+        raise ValueError(f"{name} holds {t.numel()} elements, the call writes or reads {n}")
+
+
+def _shape_check(programs, lengths, consts, X, N: int, y=None):
+    """Sizes the C ABI cannot see (it takes bare pointers): the population
+    rows, the constant table, the case count and the target.  Raises
+    ValueError before anything is launched.  Returns (P, Lmax, K, nvars, ldx)."""
+    if programs.dim() != 2:
+        raise ValueError("programs must be [P, Lmax]")
+    P, Lmax = programs.shape
+    if lengths.dim() != 1 or lengths.shape[0] != P:
+        raise ValueError(f"lengths must be [P] = [{P}], got {tuple(lengths.shape)}")
+    K = 0 if consts is None else (consts.shape[1] if consts.dim() == 2 else 0)
+    if K and consts.shape[0] < P:
+        raise ValueError(f"consts has {consts.shape[0]} rows for {P} programs")
+    if X.dim() != 2:
+        raise ValueError("X must be [nvars, ldx]")
+    nvars, ldx = X.shape
+    if not 1 <= N <= ldx:
+        raise ValueError(f"N = {N} must lie in [1, ldx = {ldx}]")
+    if y is not None:
+        _need(y, N, "y")
+    return P, Lmax, K, nvars, ldx
+
+
 def _dev(t: torch.Tensor, dtype, name):
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError(f"{name} must be a CUDA tensor")
@@ -193,15 +221,15 @@ def sr_eval(ctx: Context, programs, lengths, consts, X, y, N: int, kind: int,
             fitness: torch.Tensor | None = None, prog_flags: torch.Tensor | None = None):
     """Fitness of every program (sr_eval in include/sr.h).  Returns fitness
     (float64 [P], or [2, P] for SR_MSE_CORR)."""
+    P, Lmax, K, nvars, ldx = _shape_check(programs, lengths, consts, X, N, y)
+    _need(fitness, (2 if kind == SR_MSE_CORR else 1) * P, "fitness")
+    _need(prog_flags, P, "prog_flags")
     _dev(programs, torch.uint8, "programs")
     _dev(lengths, torch.int32, "lengths")
     _dev(X, torch.float32, "X")
     _dev(y, torch.float32, "y")
-    P, Lmax = programs.shape
-    K = 0 if consts is None else (consts.shape[1] if consts.dim() == 2 else 0)
     if consts is not None and K > 0:
         _dev(consts, torch.float32, "consts")
-    nvars, ldx = X.shape
     if fitness is None:
         shape = (2, P) if kind == SR_MSE_CORR else (P,)
         fitness = torch.empty(shape, dtype=torch.float64, device=programs.device)
@@ -220,15 +248,16 @@ def sr_eval_score(ctx: Context, programs, lengths, consts, X, y, N: int, kind: i
     """Beagle's scores (sr_eval_score: Eq. 2 for SR_SCORE_R4, Eq. 3 for
     SR_SCORE_P2P).  Returns score (float64 [P], larger is better) and the
     pair counts (int32 [P, 2]: c1, c2)."""
+    P, Lmax, K, nvars, ldx = _shape_check(programs, lengths, consts, X, N, y)
+    _need(score, P, "score")
+    _need(pair_counts, 2 * P, "pair_counts")
+    _need(prog_flags, P, "prog_flags")
     _dev(programs, torch.uint8, "programs")
     _dev(lengths, torch.int32, "lengths")
     _dev(X, torch.float32, "X")
     _dev(y, torch.float32, "y")
-    P, Lmax = programs.shape
-    K = 0 if consts is None else (consts.shape[1] if consts.dim() == 2 else 0)
     if consts is not None and K > 0:
         _dev(consts, torch.float32, "consts")
-    nvars, ldx = X.shape
     if score is None:
         score = torch.empty(P, dtype=torch.float64, device=programs.device)
     if pair_counts is None:
@@ -247,14 +276,15 @@ def sr_predict(ctx: Context, programs, lengths, consts, X, N: int,
                yhat: torch.Tensor | None = None, prog_flags: torch.Tensor | None = None):
     """Outputs of every program on every case (sr_predict); returns yhat
     float32 [P, ldy]."""
+    P, Lmax, K, nvars, ldx = _shape_check(programs, lengths, consts, X, N)
+    if yhat is not None and (yhat.dim() != 2 or yhat.shape[0] < P or yhat.shape[1] < N):
+        raise ValueError(f"yhat must be [>= P, >= N] = [>= {P}, >= {N}], got {tuple(yhat.shape)}")
+    _need(prog_flags, P, "prog_flags")
     _dev(programs, torch.uint8, "programs")
     _dev(lengths, torch.int32, "lengths")
     _dev(X, torch.float32, "X")
-    P, Lmax = programs.shape
-    K = 0 if consts is None else (consts.shape[1] if consts.dim() == 2 else 0)
     if consts is not None and K > 0:
         _dev(consts, torch.float32, "consts")
-    nvars, ldx = X.shape
     if yhat is None:
         yhat = torch.empty((P, N), dtype=torch.float32, device=programs.device)
     _dev(yhat, torch.float32, "yhat")
@@ -270,23 +300,29 @@ def sr_eval_noalloc(programs, lengths, consts, X, y, N: int, kind: int, fitness:
                     prog_flags: torch.Tensor | None = None, stream: torch.cuda.Stream | None = None):
     """sr_eval without a context and without any device allocation (scratch
     comes from the library's static 16 MiB array).  Returns the status code;
-    fitness must be preallocated (float64 [P], or [2, P] for SR_MSE_CORR)."""
+    fitness must be preallocated (float64 [P], or [2, P] for SR_MSE_CORR).
+    The call runs with the tensors' device current (the library looks the
+    scratch array up on the current device); a stream of another device is
+    rejected."""
+    P, Lmax, K, nvars, ldx = _shape_check(programs, lengths, consts, X, N, y)
+    _need(fitness, (2 if kind == SR_MSE_CORR else 1) * P, "fitness")
+    _need(prog_flags, P, "prog_flags")
     _dev(programs, torch.uint8, "programs")
     _dev(lengths, torch.int32, "lengths")
     _dev(X, torch.float32, "X")
     _dev(y, torch.float32, "y")
     _dev(fitness, torch.float64, "fitness")
-    P, Lmax = programs.shape
-    K = 0 if consts is None else (consts.shape[1] if consts.dim() == 2 else 0)
     if consts is not None and K > 0:
         _dev(consts, torch.float32, "consts")
     if prog_flags is not None:
         _dev(prog_flags, torch.int32, "prog_flags")
-    nvars, ldx = X.shape
-    s = (stream or torch.cuda.current_stream(programs.device)).cuda_stream
-    return int(lib().sr_eval_noalloc(ctypes.c_void_p(s), _ptr(programs), _ptr(lengths),
-                                     _ptr(consts) if K else None, P, Lmax, K, _ptr(X), _ptr(y),
-                                     nvars, N, ldx, kind, _ptr(fitness), _ptr(prog_flags)))
+    stream = stream or torch.cuda.current_stream(programs.device)
+    if stream.device != programs.device:
+        raise ValueError(f"stream of {stream.device} for tensors on {programs.device}")
+    with torch.cuda.device(programs.device):
+        return int(lib().sr_eval_noalloc(ctypes.c_void_p(stream.cuda_stream), _ptr(programs), _ptr(lengths),
+                                         _ptr(consts) if K else None, P, Lmax, K, _ptr(X), _ptr(y),
+                                         nvars, N, ldx, kind, _ptr(fitness), _ptr(prog_flags)))
 
 
 def sr_philox4x32_10(ctx: Context, ctr: torch.Tensor, key0: int, key1: int) -> torch.Tensor:
@@ -299,8 +335,9 @@ def sr_philox4x32_10(ctx: Context, ctr: torch.Tensor, key0: int, key1: int) -> t
 
 def sr_select_tournament(ctx: Context, fitness, k: int, seed: int, gen: int,
                          parents: torch.Tensor | None = None) -> torch.Tensor:
-    _dev(fitness, torch.float64, "fitness")
     P = fitness.shape[0]
+    _need(parents, 2 * P, "parents")
+    _dev(fitness, torch.float64, "fitness")
     if parents is None:
         parents = torch.empty((P, 2), dtype=torch.int32, device=fitness.device)
     _dev(parents, torch.int32, "parents")
@@ -311,8 +348,9 @@ def sr_select_tournament(ctx: Context, fitness, k: int, seed: int, gen: int,
 def sr_select_tournament_max(ctx: Context, score, k: int, seed: int, gen: int,
                              parents: torch.Tensor | None = None) -> torch.Tensor:
     """The same draws as sr_select_tournament; the largest score wins."""
-    _dev(score, torch.float64, "score")
     P = score.shape[0]
+    _need(parents, 2 * P, "parents")
+    _dev(score, torch.float64, "score")
     if parents is None:
         parents = torch.empty((P, 2), dtype=torch.int32, device=score.device)
     _dev(parents, torch.int32, "parents")
@@ -325,12 +363,20 @@ def sr_vary(ctx: Context, programs, lengths, consts, parents, nvars: int, cfg: V
     """One child per row of parents ([P_out, 2], indices into the P_in rows of
     programs); returns (programs, lengths, consts) of the children (the
     first P_out rows of ``out`` when it is given)."""
-    _dev(programs, torch.uint8, "programs")
-    _dev(lengths, torch.int32, "lengths")
-    _dev(parents, torch.int32, "parents")
+    if programs.dim() != 2 or parents.dim() != 2 or parents.shape[1] != 2:
+        raise ValueError("programs must be [P_in, Lmax] and parents [P_out, 2]")
     P_in, Lmax = programs.shape
     P = parents.shape[0]
     K = consts.shape[1] if consts is not None and consts.dim() == 2 else 0
+    _need(lengths, P_in, "lengths")
+    if K and consts.shape[0] < P_in:
+        raise ValueError(f"consts has {consts.shape[0]} rows for {P_in} parents")
+    if out is not None and K and (out[2] is None or out[2].dim() != 2 or out[2].shape[0] < P
+                                  or out[2].shape[1] != K):
+        raise ValueError("output constants must be [>= P_out, K]")
+    _dev(programs, torch.uint8, "programs")
+    _dev(lengths, torch.int32, "lengths")
+    _dev(parents, torch.int32, "parents")
     if K:
         _dev(consts, torch.float32, "consts")
     if out is None:
@@ -351,8 +397,10 @@ def sr_select_microcosm(ctx: Context, fitness, P_out: int, sample: int, keep: fl
     """Beagle's microcosm selection (sr_select_microcosm): parents [P_out, 2]
     drawn from the P_in = len(fitness) programs; threshold (float64 [1]) gets
     the sample's keep-quantile when given."""
-    _dev(fitness, torch.float64, "fitness")
     P_in = fitness.shape[0]
+    _need(parents, 2 * P_out, "parents")
+    _need(threshold, 1, "threshold")
+    _dev(fitness, torch.float64, "fitness")
     if parents is None:
         parents = torch.empty((P_out, 2), dtype=torch.int32, device=fitness.device)
     _dev(parents, torch.int32, "parents")
@@ -379,14 +427,22 @@ def sr_random_programs(ctx: Context, P: int, Lmin: int, Lmax: int, K: int, nvars
 def sr_eval_grad(ctx: Context, programs, lengths, consts, X, y, N: int, mse=None, dconst=None,
                  prog_flags=None):
     """MSE [P] and dMSE/dconst [P, K] (float64)."""
+    if consts is None or consts.dim() != 2 or consts.shape[1] < 1:
+        raise ValueError("consts must be [P, K] with K >= 1")
+    P, Lmax, K, nvars, ldx = _shape_check(programs, lengths, consts, X, N, y)
+    _need(mse, P, "mse")
+    _need(dconst, P * K, "dconst")
+    _need(prog_flags, P, "prog_flags")
     _dev(programs, torch.uint8, "programs")
     _dev(lengths, torch.int32, "lengths")
     _dev(consts, torch.float32, "consts")
     _dev(X, torch.float32, "X")
     _dev(y, torch.float32, "y")
-    P, Lmax = programs.shape
-    K = consts.shape[1]
-    nvars, ldx = X.shape
+    for t, name in ((mse, "mse"), (dconst, "dconst")):
+        if t is not None:
+            _dev(t, torch.float64, name)
+    if prog_flags is not None:
+        _dev(prog_flags, torch.int32, "prog_flags")
     if mse is None:
         mse = torch.empty(P, dtype=torch.float64, device=programs.device)
     if dconst is None:
@@ -399,6 +455,8 @@ def sr_eval_grad(ctx: Context, programs, lengths, consts, X, y, N: int, mse=None
 
 def sr_adam_step(ctx: Context, consts, grad, m, v, t: int, cfg: AdamCfg):
     """In-place Adam update of consts (float32) with float64 grad / moments."""
+    for t, name in ((grad, "grad"), (m, "m"), (v, "v")):
+        _need(t, consts.numel(), name)
     _dev(consts, torch.float32, "consts")
     _dev(grad, torch.float64, "grad")
     _dev(m, torch.float64, "m")
@@ -414,19 +472,21 @@ def sr_set_tile(ctx: Context, cases_per_tile: int):
 def make_problem(programs, lengths, consts, X, y, N: int, kind: int, fitness=None, prog_flags=None,
                  cases_per_tile: int = 0):
     """An sr_problem over torch tensors (kept alive by the returned tuple)."""
+    P, Lmax, K, nvars, ldx = _shape_check(programs, lengths, consts, X, N, y)
+    _need(fitness, (2 if kind == SR_MSE_CORR else 1) * P, "fitness")
+    _need(prog_flags, P, "prog_flags")
     _dev(programs, torch.uint8, "programs")
     _dev(lengths, torch.int32, "lengths")
     _dev(X, torch.float32, "X")
     _dev(y, torch.float32, "y")
-    P, Lmax = programs.shape
-    K = 0 if consts is None else (consts.shape[1] if consts.dim() == 2 else 0)
     if K:
         _dev(consts, torch.float32, "consts")
     if fitness is None:
         shape = (2, P) if kind == SR_MSE_CORR else (P,)
         fitness = torch.empty(shape, dtype=torch.float64, device=programs.device)
     _dev(fitness, torch.float64, "fitness")
-    nvars, ldx = X.shape
+    if prog_flags is not None:
+        _dev(prog_flags, torch.int32, "prog_flags")
     pr = Problem(programs.data_ptr(), lengths.data_ptr(), consts.data_ptr() if K else None, P, Lmax, K,
                  X.data_ptr(), y.data_ptr(), nvars, N, ldx, kind, fitness.data_ptr(),
                  prog_flags.data_ptr() if prog_flags is not None else None, cases_per_tile)

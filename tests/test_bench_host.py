@@ -54,6 +54,9 @@ def test_clock_sampler_without_nvidia_smi():
 @pytest.fixture
 def fixed_peak(monkeypatch):
     monkeypatch.setattr(bench, "_alu_peak", lambda dev: (40273.92, "test peak"))
+    # every capture as if taken of the current sources
+    for key, cap in bench.KERNEL_NCU.items():
+        monkeypatch.setitem(bench.KERNEL_NCU, key, dict(cap, src=bench.source_hash(cap["sources"])))
 
 
 def test_roofline_traffic_for_the_captured_workload(fixed_peak):
@@ -89,6 +92,25 @@ def test_roofline_dram_side_of_the_launch(fixed_peak, monkeypatch):
 def test_roofline_without_a_capture(fixed_peak):
     r = bench._roofline(None, 100.0, "k", "t", "plain-256x1k")
     assert r["traffic"] is None and r["issue_active_ncu"] is None and r["peak"] == 40273.92
+
+
+def test_stale_capture_is_not_reported(monkeypatch):
+    """A capture taken of other kernel sources (or of unknown ones) gives no
+    traffic and no issue rate, and says why."""
+    monkeypatch.setattr(bench, "_alu_peak", lambda dev: (40273.92, "test peak"))
+    cap = bench.KERNEL_NCU["beagle"]
+    for src, why in ((None, "no capture"), ("0123456789abcdef", "changed")):
+        monkeypatch.setitem(bench.KERNEL_NCU, "beagle", dict(cap, src=src))
+        r = bench._roofline(None, 2000.0, "k", "t", cap["workload"], "beagle", cap["units"])
+        assert r["traffic"] is None and r["issue_active_ncu"] is None and r["hbm"] is None
+        prov = r["ncu_provenance"]
+        assert why in prov["stale"] and prov["capture"] == cap["capture"]
+        assert prov["src_now"] == bench.source_hash("eval")
+
+
+def test_source_hash_follows_the_kernel_files():
+    assert bench.source_hash("eval") != bench.source_hash("grad")
+    assert len(bench.source_hash("eval")) == 16
 
 
 def test_host_cores_is_the_affinity():

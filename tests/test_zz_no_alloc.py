@@ -6,7 +6,8 @@ context, code that must not cause the synchronisation an allocation can).
 This entry point takes its scratch from a static device array instead.  The
 test calls it through the C ABI twice in a row and checks both results
 against the context-based sr_eval with the parity tolerance used everywhere
-else (1e-4 relative + floor), and that an oversized problem is refused.
+else (1e-4 relative + floor), that the second call leaves the device's free
+memory unchanged, and that an oversized problem is refused.
 This file is named so that pytest collects it last.
 """
 import numpy as np
@@ -48,9 +49,15 @@ def test_noalloc_matches_sr_eval_on_two_calls(N):
     for call in range(2):
         out = torch.full((2, pr.P), -7.0, dtype=torch.float64, device="cuda")
         flags = torch.full((pr.P,), -1, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         st = binding.sr_eval_noalloc(prog, lens, cons, X, yy, N, binding.SR_MSE_CORR, out, flags)
         assert st == binding.SR_OK, f"call {call}: status {st}"
         torch.cuda.synchronize()
+        if call == 1:
+            # the device's free memory is what it was: the call allocated nothing
+            # (the first call of a process may load the library's module)
+            assert torch.cuda.mem_get_info()[0] == free0
         got = out.cpu().numpy()
         fin = np.isfinite(ref)
         assert np.array_equal(fin, np.isfinite(got)), call
