@@ -27,7 +27,8 @@ SCORE_R4, SCORE_P2P = 0, 1  # Eq. 2, Eq. 3
 PF_BAD_LENGTH, PF_BAD_TOKEN, PF_BAD_VAR = 1, 2, 4
 PF_BAD_CONST, PF_UNDERFLOW, PF_BAD_FINAL = 8, 16, 32
 # conditioning flag bits
-CF_RANGE, CF_FITRANGE = 1, 4
+CF_RANGE, CF_FITRANGE, CF_BRANCH, CF_NONLIN = 1, 4, 8, 16
+LAMBDA = 6.0  # standard units of the probabilistic bound: fails with probability <= 2 exp(-18)
 
 _lib = None
 
@@ -60,6 +61,8 @@ def _load():
     lib.or_predict_interval.argtypes = [P, i32, P, P, i64, i64, f64, P, P, P, P]
     lib.or_eval.argtypes = [P, P, P, i32, i32, i32, P, i64, P, i32, i64, i32, P, P, i32]
     lib.or_condition.argtypes = [P, P, P, i32, i32, i32, P, i64, P, i32, i64, i32, f64, P, P, P, i32]
+    lib.or_condition_fo.argtypes = [P, P, P, i32, i32, i32, P, i64, P, i32, i64, f64, f64, P, P, P, P, i32]
+    lib.or_first_order_cases.argtypes = [P, i32, P, P, i64, i64, f64, f64, i32, P, P, P, P, P]
     lib.or_grad.argtypes = [P, P, P, i32, i32, i32, P, i64, P, i32, i64, P, P, P, P, i32]
     lib.or_grad_one.argtypes = [P, i32, P, i32, P, i64, P, i64, P, P, P, P]
     lib.or_mse_fp64_consts.argtypes = [P, i32, P, P, i64, P, i64]
@@ -209,6 +212,53 @@ def condition(programs, lengths, consts, X, y, kind: int, N: int | None = None,
     _load().or_condition(_ptr(prog), _ptr(lens), _ptr(cons), P, Lmax, K, _ptr(X64), ldx,
                          _ptr(y64), nvars, N, kind, u, _ptr(errb), _ptr(cfl), _ptr(f0), nthreads)
     return errb, cfl, f0
+
+
+def condition_fo(programs, lengths, consts, X, y, N: int | None = None, u: float = U_FP32,
+                 lam: float = LAMBDA, nthreads: int = 0):
+    """Both fitness kinds of every program in one pass, with two
+    certificates of how far FP32 evaluation can move them
+    (or_condition_fo_one): the rigorous interval bound errb (the same as
+    condition()'s) and the probabilistic first-order bound errp; the range
+    flags (CF_RANGE, CF_FITRANGE) and the FP64 fitness.  Each is [2, P]:
+    row 0 MSE, row 1 1 - r^2."""
+    prog = _c(programs, np.uint8)
+    P, Lmax = prog.shape
+    lens = _c(lengths, np.int32)
+    cons = _c(consts, np.float32).reshape(P, -1)
+    K = cons.shape[1]
+    X64, ldx = _X(X)
+    nvars = X64.shape[0]
+    N = ldx if N is None else N
+    y64 = _c(np.asarray(y)[:N], np.float64)
+    errb = np.empty((2, P), np.float64)
+    errp = np.empty((2, P), np.float64)
+    cfl = np.empty((2, P), np.int32)
+    f0 = np.empty((2, P), np.float64)
+    _load().or_condition_fo(_ptr(prog), _ptr(lens), _ptr(cons), P, Lmax, K, _ptr(X64), ldx, _ptr(y64),
+                            nvars, N, u, lam, _ptr(errb), _ptr(errp), _ptr(cfl), _ptr(f0), nthreads)
+    return errb, errp, cfl, f0
+
+
+def first_order_cases(tokens, consts, X, N: int | None = None, u: float = U_FP32, lam: float = LAMBDA,
+                      raw: bool = False):
+    """Per case of one valid program: the FP64 output, its first-order
+    variance scale s2 = sum_j (u_j c_j)^2 (c_j = v_j dyhat/dv_j over the
+    operator nodes j), the linear worst case w1 = sum_j u_j |c_j|, the
+    systematic part w, and the case's flags.  raw=False applies the
+    fallback of untrusted cases (their rigorous half-width as w); raw=True
+    returns the expansion as it is, with its CF_BRANCH / CF_NONLIN flags."""
+    t = _c(tokens, np.uint8)
+    c = np.zeros(16, np.float64)
+    cc = np.asarray(consts, dtype=np.float64).ravel()
+    c[: len(cc)] = cc
+    X64, ldx = _X(X)
+    N = ldx if N is None else N
+    out = [np.empty(N, np.float64) for _ in range(4)]
+    cf = np.empty(N, np.int32)
+    _load().or_first_order_cases(_ptr(t), len(t), _ptr(c), _ptr(X64), ldx, N, u, lam, int(raw),
+                                 *[_ptr(a) for a in out], _ptr(cf))
+    return out[0], out[1], out[2], out[3], cf
 
 
 def grad(programs, lengths, consts, X, y, N: int | None = None, nthreads: int = 0):

@@ -74,6 +74,10 @@ enum {
 /* conditioning flag bits */
 #define CF_RANGE 1     /* an intermediate outside the FP32 normal range      */
 #define CF_FITRANGE 4  /* a fitness term whose FP32 partial sums may overflow */
+#define CF_BRANCH 8    /* FP32 rounding could flip a protected branch, a clamp
+                          or the sign inside sqrt|x| (derivative unbounded)  */
+#define CF_NONLIN 16   /* first-order error analysis not trusted: the rigorous
+                          enclosure is wider than the linear estimate allows  */
 
 #define PROTECT_EPS 1e-3
 #define EXP_CLAMP 80.0
@@ -616,6 +620,397 @@ void or_condition(const uint8_t *programs, const int32_t *lengths,
     free(yhat);
     free(cfl);
   }
+}
+
+/* ---- probabilistic first-order rounding-error bound ---------------------- */
+/*
+ * A second, tighter certificate of "well-conditioned", next to the rigorous
+ * interval bound above.  Model (first-order rounding-error analysis): the
+ * FP32 evaluation rounds every operator output once, v -> v (1 + d),
+ * |d| <= u_v (u_v = u for + - * / and the base library functions, 4u for
+ * tan, asin, acos, atan, tanh; inputs and constants are exact FP32 values).
+ * Probabilistic rounding-error analysis (N. J. Higham and T. Mary, "A New
+ * Approach to Probabilistic Rounding Error Analysis", SIAM J. Sci. Comput.
+ * 41(5), 2019) takes the d as independent and mean-zero; a sum sum_k a_k d_k
+ * then stays within lam sqrt(sum_k (a_k u_k)^2) except with probability
+ * 2 exp(-lam^2 / 2) (Hoeffding's inequality).  Here:
+ *   - every node carries, besides its FP64 value v, the first-order variance
+ *     scale s2(v) = sum over the operators j below it of (u_j c_j)^2 with
+ *     c_j = v_j dv/dv_j, propagated forward: s2 = sum_children
+ *     (dv/dchild)^2 s2(child) + (u_v v)^2;
+ *   - and a systematic part w(v), taken at its worst: a share BIAS of every
+ *     operator's bound (rounding errors of one operator across the cases are
+ *     allowed a common bias of BIAS u_j), plus the second-order term of every
+ *     nonlinear operator over the lam-sigma neighbourhood of its operands
+ *     (|f''| max / 2 times the squared reach, and the product of the reaches
+ *     for a product);
+ *   - a branch (protected division, 1/x, log, the exp clamp) whose argument
+ *     lies within lam sigma + w of its switch point could go either way in
+ *     FP32: the case is flagged CF_BRANCH, as is sqrt|x| within that reach
+ *     of 0 (unbounded derivative);
+ *   - the expansion is not trusted (CF_NONLIN) where an operand's reach
+ *     comes within a tenth of a singular point of the operator (0 for a
+ *     divisor, log or sqrt, +-1 for asin / acos, a pole of tan) or exceeds
+ *     0.1 in the argument of sin, cos, exp, tan or tanh, or where a value's
+ *     reach leaves the FP32 range.
+ * On a case flagged CF_BRANCH or CF_NONLIN the expansion is not used: that
+ * case's output error is taken at its worst, the half-width of its rigorous
+ * FP32 enclosure (case_interval), in the systematic part.
+ * A fitness F moves by sum_i g_i dyhat_i, g_i = dF/dyhat_i:
+ *     MSE:     g_i = (2/N) e_i,  e_i = yhat_i - y_i
+ *     1 - r^2: g_i = -(2 Sxy / (Sxx Syy)) (yc_i - (Sxy / Sxx) xc_i)
+ * with the centred sums of Eq. 1 (xc = yhat - mean yhat, yc = y - mean y),
+ * so errp = min(lam sqrt(sum_i g_i^2 s2_i), sum_i |g_i| w1_i) + sum_i |g_i| w_i
+ * (w1: the linear worst case sum_j u_j |c_ij|, which Hoeffding's bound
+ * never needs to exceed), plus the FP32
+ * reduction at its worst (8u of the sums it forms, as in the rigorous
+ * bound) and the fitness's own second-order terms.
+ */
+#define FO_BIAS 0.0625
+
+/* Local partial derivatives of one operator at FP64 operands (a, and b for
+ * binary ones) and result r, under the readings of the file header: the
+ * protected fallback, a clamped exp and sqrt|x| at 0 have derivative 0. */
+static void op_partials(int v, double a, double b, double r, double *pa, double *pb) {
+  *pa = 0.0;
+  *pb = 0.0;
+  switch (v) {
+    case TK_ADD: *pa = 1.0; *pb = 1.0; return;
+    case TK_SUB: *pa = 1.0; *pb = -1.0; return;
+    case TK_MUL: *pa = b; *pb = a; return;
+    case TK_DIV:
+      if (fabs(b) > PROTECT_EPS) {
+        *pa = 1.0 / b;
+        *pb = -r / b;
+      }
+      return;
+    case TK_SIN: *pa = cos(a); return;
+    case TK_COS: *pa = -sin(a); return;
+    case TK_EXP: *pa = (a > EXP_CLAMP || a < -EXP_CLAMP) ? 0.0 : r; return;
+    case TK_LOG: *pa = fabs(a) <= PROTECT_EPS ? 0.0 : 1.0 / a; return;
+    case TK_SQRT: *pa = a == 0.0 ? 0.0 : (a > 0.0 ? 0.5 / r : -0.5 / r); return;
+    case TK_SQ: *pa = 2.0 * a; return;
+    case TK_INV: *pa = fabs(a) <= PROTECT_EPS ? 0.0 : -r * r; return;
+    case TK_TAN: *pa = 1.0 + r * r; return;
+    case TK_ASIN: *pa = 1.0 / sqrt((1.0 - a) * (1.0 + a)); return;
+    case TK_ACOS: *pa = -1.0 / sqrt((1.0 - a) * (1.0 + a)); return;
+    case TK_ATAN: *pa = 1.0 / (1.0 + a * a); return;
+    default: {
+      double ch = cosh(a);
+      *pa = 1.0 / (ch * ch);
+      return;
+    }
+  }
+}
+
+/* |f''| / 2 of a unary operator, bounded over [x - r, x + r], or -1 when the
+ * expansion is not trusted there (see CF_NONLIN above). */
+static double unary_curvature(int v, double x, double r, double val) {
+  double m;
+  switch (v) {
+    case TK_SIN:
+    case TK_COS: return r <= 0.1 ? 0.5 : -1.0;
+    case TK_EXP: return r <= 0.1 ? 0.5 * fabs(val) * exp(r) : -1.0;
+    case TK_LOG:
+      m = fabs(x) - r;
+      return m >= 0.9 * fabs(x) && m > 0.0 ? 0.5 / (m * m) : -1.0;
+    case TK_SQRT:
+      m = fabs(x) - r;
+      return m >= 0.9 * fabs(x) && m > 0.0 ? 0.125 / (m * sqrt(m)) : -1.0;
+    case TK_SQ: return 1.0;
+    case TK_INV:
+      m = fabs(x) - r;
+      return m >= 0.9 * fabs(x) && m > 0.0 ? 1.0 / (m * m * m) : -1.0;
+    case TK_TAN: {
+      double cs = fabs(cos(x)) - r;
+      if (!(r <= 0.1 && cs >= 0.9 * fabs(cos(x)) && cs > 0.0)) return -1.0;
+      double t = (fabs(sin(x)) + r) / cs; /* |tan| over the reach */
+      return t * (1.0 + t * t);
+    }
+    case TK_ASIN:
+    case TK_ACOS:
+      m = 1.0 - (fabs(x) + r);
+      return m >= 0.9 * (1.0 - fabs(x)) && m > 0.0 ? 0.5 * (fabs(x) + r) / (m * sqrt(m * (2.0 - m))) : -1.0;
+    case TK_ATAN: return 0.65; /* |2x / (1 + x^2)^2| <= 3 sqrt(3) / 8 */
+    default: return r <= 0.1 ? 0.39 : -1.0; /* |sech^2 tanh| <= 4 / (3 sqrt(3)) */
+  }
+}
+
+/*
+ * First-order analysis of one valid program on case i.  Returns the FP64
+ * output; *s2, *w receive its variance scale and systematic part; *cond
+ * gets CF_RANGE, CF_BRANCH and CF_NONLIN.  Work arrays (len + 1 entries):
+ * val, s2v, wv.
+ */
+/* how far FP32 rounding can move a node, from its three error measures:
+ * the random part at lam sigma (never beyond the linear worst case) plus
+ * the systematic part */
+static double fo_reach(double lam, double s2, double w1, double w) { return dmin(lam * sqrt(s2), w1) + w; }
+
+static double case_first_order(const uint8_t *tok, int len, const double *c, const double *X, long ldx,
+                               long i, double u, double lam, double *val, double *s2v, double *w1v,
+                               double *wv, double *s2, double *w1, double *w, int *cond) {
+  int sp = 0, cf = 0;
+  for (int t = 0; t < len; ++t) {
+    int v = tok[t];
+    if (is_var(v) || is_const(v)) {
+      val[sp] = is_var(v) ? X[(long)(v - TK_VAR0) * ldx + i] : c[v - TK_CONST0];
+      s2v[sp] = 0.0;
+      w1v[sp] = 0.0;
+      wv[sp] = 0.0;
+      ++sp;
+      continue;
+    }
+    double uv = (v >= TK_TAN && v <= TK_TANH) ? 4.0 * u : u;
+    double r, q2, q1, l1;
+    if (is_binary(v)) {
+      --sp;
+      double a = val[sp - 1], b = val[sp];
+      double ra = fo_reach(lam, s2v[sp - 1], w1v[sp - 1], wv[sp - 1]);
+      double rb = fo_reach(lam, s2v[sp], w1v[sp], wv[sp]);
+      r = apply_binary(v, a, b);
+      double pa, pb, second = 0.0;
+      op_partials(v, a, b, r, &pa, &pb);
+      if (v == TK_MUL) second = ra * rb;
+      if (v == TK_DIV) {
+        double m = fabs(b) - rb;
+        if (fabs(fabs(b) - PROTECT_EPS) <= rb) cf |= CF_BRANCH;
+        if (!(m >= 0.9 * fabs(b) && m > 0.0)) cf |= CF_NONLIN;
+        else if (fabs(b) > PROTECT_EPS) second = (ra * rb + (fabs(a) + ra) * rb * rb / m) / (m * m);
+      }
+      q2 = pa * pa * s2v[sp - 1] + pb * pb * s2v[sp];
+      l1 = fabs(pa) * w1v[sp - 1] + fabs(pb) * w1v[sp];
+      q1 = fabs(pa) * wv[sp - 1] + fabs(pb) * wv[sp] + second;
+    } else {
+      double x = val[sp - 1];
+      double rx = fo_reach(lam, s2v[sp - 1], w1v[sp - 1], wv[sp - 1]);
+      r = apply_unary(v, x);
+      double pa, pb;
+      op_partials(v, x, 0.0, r, &pa, &pb);
+      if ((v == TK_LOG || v == TK_INV) && fabs(fabs(x) - PROTECT_EPS) <= rx) cf |= CF_BRANCH;
+      if (v == TK_EXP && fabs(fabs(x) - EXP_CLAMP) <= rx) cf |= CF_BRANCH;
+      if (v == TK_SQRT && fabs(x) <= rx) cf |= CF_BRANCH;
+      double k = unary_curvature(v, x, rx, r);
+      int flat = (v == TK_LOG || v == TK_INV) && fabs(x) <= PROTECT_EPS; /* the constant fallback */
+      if (k < 0.0 && !flat) cf |= CF_NONLIN;
+      q2 = pa * pa * s2v[sp - 1];
+      l1 = fabs(pa) * w1v[sp - 1];
+      q1 = fabs(pa) * wv[sp - 1] + (k > 0.0 && !flat ? k * rx * rx : 0.0);
+    }
+    val[sp - 1] = r;
+    s2v[sp - 1] = q2 + (uv * r) * (uv * r);
+    w1v[sp - 1] = l1 + uv * fabs(r);
+    wv[sp - 1] = q1 + FO_BIAS * uv * fabs(r);
+    /* a reach beyond the FP32 range (or NaN): not trusted, the rigorous
+     * enclosure decides (and flags CF_RANGE if it leaves the range too) */
+    if (!(fabs(r) + fo_reach(lam, s2v[sp - 1], w1v[sp - 1], wv[sp - 1]) <= FLT_MAX)) cf |= CF_NONLIN;
+  }
+  *s2 = s2v[0];
+  *w1 = w1v[0];
+  *w = wv[0];
+  *cond |= cf;
+  return val[0];
+}
+
+/* case_first_order and case_interval of one case (*lo, *hi: the rigorous
+ * enclosure), with the fallback for untrusted cases: on a case flagged
+ * CF_BRANCH or CF_NONLIN the output error is taken at its worst, the
+ * half-width of the rigorous enclosure, as systematic part (s2 = w1 = 0).
+ * *cond gets the range flags of both analyses.  Work arrays: val
+ * [4 (len + 1)], box [len + 1]. */
+static double case_analysis(const uint8_t *tok, int len, const double *c, const double *X, long ldx, long i,
+                            double u, double lam, double *val, ival *box, double *s2, double *w1, double *w,
+                            double *lo, double *hi, int *cond) {
+  size_t L = (size_t)len + 1;
+  int ci = 0, cr = 0;
+  double y0 = case_first_order(tok, len, c, X, ldx, i, u, lam, val, val + L, val + 2 * L, val + 3 * L, s2, w1,
+                               w, &ci);
+  case_interval(tok, len, c, X, ldx, i, u, val, box, &cr, lo, hi);
+  if (ci & (CF_BRANCH | CF_NONLIN)) {
+    *s2 = 0.0;
+    *w1 = 0.0;
+    *w = dmax(*hi - y0, y0 - *lo);
+    ci &= ~(CF_BRANCH | CF_NONLIN);
+    if (!isfinite(*w)) ci |= CF_RANGE;
+  }
+  *cond |= ci | cr;
+  return y0;
+}
+
+/*
+ * Both fitness kinds of one valid program with both certificates:
+ *   errb[k]  the rigorous bound of or_condition_one for kind k (0 MSE,
+ *            1 1 - r^2), from the per-case enclosures
+ *   errp[k]  the probabilistic first-order bound (see above), lam standard
+ *            units; never above errb[k] by construction of neither, so a
+ *            caller takes the smaller
+ *   cfl[k]   CF_RANGE (some case's enclosure or reach leaves the FP32 range)
+ *            and CF_FITRANGE (kind k's FP32 sums may overflow)
+ *   f0[k]    the FP64 fitness
+ * For 1 - r^2, when the reach of the outputs moves Sxy or Sxx by more than
+ * 1 % of them, r^2 is not expanded: its enclosure over the moved outputs is
+ * taken instead (the rigorous bound's formula with the reach as width).
+ * Work: yhat, s2, w1, w, lo, hi [N].
+ */
+void or_condition_fo_one(const uint8_t *tok, int len, const double *c, const double *X, long ldx,
+                         const double *y, long N, double u, double lam, double *work, double *errb,
+                         double *errp, int32_t *cfl, double *f0) {
+  size_t L = (size_t)len + 1, nn = (size_t)(N > 0 ? N : 1);
+  double *yh = work, *s2 = work + nn, *w1 = work + 2 * nn, *w = work + 3 * nn;
+  double *lo = work + 4 * nn, *hi = work + 5 * nn;
+  double *val = (double *)malloc(sizeof(double) * L * 4);
+  ival *box = (ival *)malloc(sizeof(ival) * L);
+  int cf = 0;
+  for (long i = 0; i < N; ++i)
+    yh[i] = case_analysis(tok, len, c, X, ldx, i, u, lam, val, box, &s2[i], &w1[i], &w[i], &lo[i], &hi[i], &cf);
+  free(val);
+  free(box);
+  const double lim = (double)FLT_MAX / (double)nn;
+  /* ---- MSE */
+  {
+    double base = or_mse(yh, y, N), rnd = 0.0, lin = 0.0, sys = 0.0, sec = 0.0, smin = 0.0, smax = 0.0;
+    int cfk = cf;
+    for (long i = 0; i < N; ++i) {
+      double e = yh[i] - y[i];
+      if (e * e > lim) cfk |= CF_FITRANGE;
+      double reach = fo_reach(lam, s2[i], w1[i], w[i]);
+      rnd += e * e * s2[i];
+      lin += fabs(e) * w1[i];
+      sys += fabs(e) * w[i];
+      sec += reach * reach;
+      double elo = lo[i] - y[i], ehi = hi[i] - y[i];
+      double qmax = dmax(elo * elo, ehi * ehi);
+      double qmin = (elo <= 0.0 && ehi >= 0.0) ? 0.0 : dmin(elo * elo, ehi * ehi);
+      smin += qmin * (1.0 - 4.0 * u);
+      smax += qmax * (1.0 + 4.0 * u);
+    }
+    double ep = (2.0 * (dmin(lam * sqrt(rnd), lin) + sys) + sec) / (double)N + 8.0 * u * base;
+    double eb = dmax(smax / (double)N - base, base - smin / (double)N);
+    errb[0] = !isfinite(base) ? 0.0 : (isfinite(eb) ? eb : INFINITY);
+    errp[0] = !isfinite(base) ? 0.0 : (isfinite(ep) ? ep : INFINITY);
+    cfl[0] = cfk & (CF_RANGE | CF_FITRANGE);
+    f0[0] = base;
+  }
+  /* ---- 1 - r^2 */
+  {
+    double base = or_corr(yh, y, N), ep = 0.0, eb = 0.0;
+    int cfk = cf;
+    if (N >= 2) {
+      double my = 0.0, mh = 0.0;
+      for (long i = 0; i < N; ++i) {
+        my += y[i];
+        mh += yh[i];
+      }
+      my /= (double)N;
+      mh /= (double)N;
+      double sxy = 0.0, syy = 0.0, sxx = 0.0, A = 0.0, B = 0.0, Ab = 0.0, Bb = 0.0, D2 = 0.0, DY = 0.0;
+      for (long i = 0; i < N; ++i) {
+        double yc = y[i] - my, xc = yh[i] - mh, d = yh[i] - yh[0];
+        double reach = fo_reach(lam, s2[i], w1[i], w[i]);
+        double b = dmax(hi[i] - yh[i], yh[i] - lo[i]);
+        if (d * d > lim || fabs(d * yc) > lim) cfk |= CF_FITRANGE;
+        sxy += yc * xc;
+        syy += yc * yc;
+        sxx += xc * xc;
+        A += fabs(yc) * reach;
+        B += 2.0 * fabs(xc) * reach + reach * reach;
+        Ab += fabs(yc) * b;
+        Bb += 2.0 * fabs(xc) * b + b * b;
+        D2 += d * d;
+        DY += fabs(d * yc);
+      }
+      if (sxx > 0.0 && syy > 0.0) {
+        double r2 = sxy * sxy / (sxx * syy);
+        /* enclosure of r^2 over outputs moved by up to width[i] (A, B) plus
+         * the FP32 moment reduction at its worst (8u of its sums) */
+#define R2_ENCLOSURE(A_, B_, out)                                                              \
+  do {                                                                                          \
+    double Ar_ = (A_) + 8.0 * u * DY, Br_ = (B_) + 8.0 * u * D2;                                \
+    double l_ = fabs(sxy) - Ar_;                                                                \
+    l_ = l_ > 0.0 ? l_ * l_ / ((sxx + Br_) * syy) : 0.0;                                         \
+    double h_ = sxx - Br_ > 0.0 ? (fabs(sxy) + Ar_) * (fabs(sxy) + Ar_) / ((sxx - Br_) * syy) : INFINITY; \
+    (out) = dmax(h_ - r2, r2 - l_) + 4.0 * u * r2;                                              \
+  } while (0)
+        R2_ENCLOSURE(Ab, Bb, eb);
+        double alpha = 2.0 * sxy / (sxx * syy), beta = sxy / sxx, rnd = 0.0, lin = 0.0, sys = 0.0;
+        for (long i = 0; i < N; ++i) {
+          double g = alpha * ((y[i] - my) - beta * (yh[i] - mh));
+          rnd += g * g * s2[i];
+          lin += fabs(g) * w1[i];
+          sys += fabs(g) * w[i];
+        }
+        double ra = fabs(sxy) > 0.0 ? A / fabs(sxy) : INFINITY, rb = B / sxx;
+        if (ra <= 1e-2 && rb <= 1e-2) {
+          double red;
+          R2_ENCLOSURE(0.0, 0.0, red);
+          ep = dmin(lam * sqrt(rnd), lin) + sys + red + 4.0 * r2 * (ra * ra + rb * rb);
+        } else {
+          /* too far for a linear expansion of r^2 */
+          R2_ENCLOSURE(A, B, ep);
+        }
+#undef R2_ENCLOSURE
+      }
+    }
+    errb[1] = !isfinite(base) ? 0.0 : (isfinite(eb) ? eb : INFINITY);
+    errp[1] = !isfinite(base) ? 0.0 : (isfinite(ep) ? ep : INFINITY);
+    cfl[1] = cfk & (CF_RANGE | CF_FITRANGE);
+    f0[1] = base;
+  }
+}
+
+/* or_condition_fo_one for every program; outputs [2][P] (row 0 MSE, row 1
+ * 1 - r^2).  Invalid programs: bounds 0, flags 0, fitness +inf. */
+void or_condition_fo(const uint8_t *programs, const int32_t *lengths, const float *consts, int P,
+                     int Lmax, int K, const double *X, long ldx, const double *y, int nvars, long N,
+                     double u, double lam, double *errb, double *errp, int32_t *cflags, double *f0,
+                     int nthreads) {
+  int nt = thread_count(nthreads);
+#pragma omp parallel num_threads(nt)
+  {
+    size_t nn = (size_t)(N > 0 ? N : 1);
+    double *work = (double *)malloc(sizeof(double) * nn * 6);
+#pragma omp for schedule(dynamic, 1)
+    for (int p = 0; p < P; ++p) {
+      const uint8_t *tok = programs + (size_t)p * Lmax;
+      int md;
+      double eb[2] = {0.0, 0.0}, ep[2] = {0.0, 0.0}, f[2] = {INFINITY, INFINITY};
+      int32_t cf[2] = {0, 0};
+      if (!or_validate(tok, lengths[p], Lmax, nvars, K, &md)) {
+        double c[TK_NSLOTS];
+        widen_consts(consts + (size_t)p * K, K, c);
+        or_condition_fo_one(tok, lengths[p], c, X, ldx, y, N, u, lam, work, eb, ep, cf, f);
+      }
+      for (int k = 0; k < 2; ++k) {
+        errb[(size_t)k * P + p] = eb[k];
+        errp[(size_t)k * P + p] = ep[k];
+        cflags[(size_t)k * P + p] = cf[k];
+        f0[(size_t)k * P + p] = f[k];
+      }
+    }
+    free(work);
+  }
+}
+
+/* Per case of one valid program: output, variance scale s2, linear worst
+ * case w1, systematic part w and the case's flags, after the fallback of
+ * untrusted cases (raw = 0), or straight from the expansion with the
+ * CF_BRANCH / CF_NONLIN flags it raised (raw = 1); for tests. */
+void or_first_order_cases(const uint8_t *tok, int len, const double *c, const double *X, long ldx, long N,
+                          double u, double lam, int raw, double *yhat, double *s2, double *w1, double *w,
+                          int32_t *cflags) {
+  size_t L = (size_t)len + 1;
+  double *val = (double *)malloc(sizeof(double) * L * 4);
+  ival *box = (ival *)malloc(sizeof(ival) * L);
+  for (long i = 0; i < N; ++i) {
+    int cf = 0;
+    double lo, hi;
+    yhat[i] = raw ? case_first_order(tok, len, c, X, ldx, i, u, lam, val, val + L, val + 2 * L, val + 3 * L,
+                                     &s2[i], &w1[i], &w[i], &cf)
+                  : case_analysis(tok, len, c, X, ldx, i, u, lam, val, box, &s2[i], &w1[i], &w[i], &lo, &hi, &cf);
+    cflags[i] = cf;
+  }
+  free(val);
+  free(box);
 }
 
 /* ---- Beagle's scores (Sec. 2.1.5, Eq. 2 and Eq. 3) ---------------------- */

@@ -1,5 +1,6 @@
 """Parity of the CUDA evaluation path (sr_predict / sr_eval through the C ABI)
 with the FP64 oracle, element by element and fitness by fitness."""
+import ctypes
 import itertools
 import os
 
@@ -317,8 +318,12 @@ def test_argument_errors(ctx):
         binding.sr_eval(ctx, progs, lens, None, x, y, 8, binding.SR_MSE)
     assert e.value.status == binding.SR_EINVAL
     X = torch.zeros((3, 8), device="cuda")
-    with pytest.raises(binding.SRError):
-        binding.sr_eval(ctx, progs, lens, None, X, y, 9, binding.SR_MSE)  # ldx < N
+    with pytest.raises(ValueError):  # ldx < N: the binding refuses it before the call
+        binding.sr_eval(ctx, progs, lens, None, X, y, 9, binding.SR_MSE)
+    f1 = torch.empty(1, dtype=torch.float64, device="cuda")
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+    assert binding.lib().sr_eval(ctx.handle, p(progs), p(lens), None, 1, 4, 0, p(X), p(y), 3, 9, 8,
+                                 binding.SR_MSE, p(f1), None) == binding.SR_EINVAL  # and so does the C ABI
     with pytest.raises(binding.SRError):
         binding.sr_eval(ctx, progs, lens, None, X, y, 8, 7)  # unknown kind
     # P = 0 launches nothing and succeeds
