@@ -662,9 +662,11 @@ void or_condition(const uint8_t *programs, const int32_t *lengths,
  * with the centred sums of Eq. 1 (xc = yhat - mean yhat, yc = y - mean y),
  * so errp = min(lam sqrt(sum_i g_i^2 s2_i), sum_i |g_i| w1_i) + sum_i |g_i| w_i
  * (w1: the linear worst case sum_j u_j |c_ij|, which Hoeffding's bound
- * never needs to exceed), plus the FP32
- * reduction at its worst (8u of the sums it forms, as in the rigorous
- * bound) and the fitness's own second-order terms.
+ * never needs to exceed), plus the FP32 reduction -- each case's terms
+ * (e^2; d^2 and d yc with d = yhat - shift) rounded within 2u and
+ * independently of the other cases, the compensated running sums within
+ * u / 2 of their terms' magnitudes -- and the fitness's own second-order
+ * terms.
  */
 #define FO_BIAS 0.0625
 
@@ -869,9 +871,11 @@ void or_condition_fo_one(const uint8_t *tok, int len, const double *c, const dou
   /* ---- MSE */
   {
     double base = or_mse(yh, y, N), rnd = 0.0, lin = 0.0, sys = 0.0, sec = 0.0, smin = 0.0, smax = 0.0;
+    double e4 = 0.0;
     int cfk = cf;
     for (long i = 0; i < N; ++i) {
       double e = yh[i] - y[i];
+      e4 += e * e * e * e;
       if (e * e > lim) cfk |= CF_FITRANGE;
       double reach = fo_reach(lam, s2[i], w1[i], w[i]);
       rnd += e * e * s2[i];
@@ -884,7 +888,14 @@ void or_condition_fo_one(const uint8_t *tok, int len, const double *c, const dou
       smin += qmin * (1.0 - 4.0 * u);
       smax += qmax * (1.0 + 4.0 * u);
     }
-    double ep = (2.0 * (dmin(lam * sqrt(rnd), lin) + sys) + sec) / (double)N + 8.0 * u * base;
+    /* the FP32 reduction: each case's term e^2 (the subtraction, the square
+     * and its share of an 8-term sum, within 2u of it) rounds independently
+     * of the others; the compensated (Kahan) running sums add at most 2
+     * FP32 unit roundoffs (u / 2) of the sum of their terms' magnitudes
+     * (N. J. Higham, Accuracy and Stability of Numerical Algorithms, 2nd ed.,
+     * Sec. 4.3) */
+    double red = (lam * 2.0 * u * sqrt(e4)) / (double)N + 0.5 * u * base;
+    double ep = (2.0 * (dmin(lam * sqrt(rnd), lin) + sys) + sec) / (double)N + red;
     double eb = dmax(smax / (double)N - base, base - smin / (double)N);
     errb[0] = !isfinite(base) ? 0.0 : (isfinite(eb) ? eb : INFINITY);
     errp[0] = !isfinite(base) ? 0.0 : (isfinite(ep) ? ep : INFINITY);
@@ -904,8 +915,13 @@ void or_condition_fo_one(const uint8_t *tok, int len, const double *c, const dou
       my /= (double)N;
       mh /= (double)N;
       double sxy = 0.0, syy = 0.0, sxx = 0.0, A = 0.0, B = 0.0, Ab = 0.0, Bb = 0.0, D2 = 0.0, DY = 0.0;
+      double D4 = 0.0, DY2 = 0.0, S1 = 0.0, D1 = 0.0;
       for (long i = 0; i < N; ++i) {
         double yc = y[i] - my, xc = yh[i] - mh, d = yh[i] - yh[0];
+        D4 += d * d * d * d;
+        DY2 += d * d * yc * yc;
+        S1 += d;
+        D1 += fabs(d);
         double reach = fo_reach(lam, s2[i], w1[i], w[i]);
         double b = dmax(hi[i] - yh[i], yh[i] - lo[i]);
         if (d * d > lim || fabs(d * yc) > lim) cfk |= CF_FITRANGE;
@@ -941,8 +957,19 @@ void or_condition_fo_one(const uint8_t *tok, int len, const double *c, const dou
         }
         double ra = fabs(sxy) > 0.0 ? A / fabs(sxy) : INFINITY, rb = B / sxx;
         if (ra <= 1e-2 && rb <= 1e-2) {
-          double red;
-          R2_ENCLOSURE(0.0, 0.0, red);
+          /* the FP32 moment reduction: per case the terms d yc and d^2 (with
+           * d = yhat - shift and yc = y - mean y rounded to FP32) are within 2u
+           * of exact and round independently of the other cases; the
+           * compensated running sums add at most u / 2 of the sum of their
+           * terms' magnitudes; Sxx = sum d^2 - (sum d)^2 / N also carries the
+           * error of sum d.  The merges and r^2 itself are FP64 (1e-15). */
+          double ea = lam * 2.0 * u * sqrt(DY2) + 0.5 * u * DY;
+          double es1 = lam * u * sqrt(D2) + 0.5 * u * D1;
+          double eb2 = lam * 2.0 * u * sqrt(D4) + 0.5 * u * D2 + 2.0 * fabs(S1) / (double)N * es1;
+          double l = fabs(sxy) - ea;
+          l = l > 0.0 ? l * l / ((sxx + eb2) * syy) : 0.0;
+          double h = sxx - eb2 > 0.0 ? (fabs(sxy) + ea) * (fabs(sxy) + ea) / ((sxx - eb2) * syy) : INFINITY;
+          double red = dmax(h - r2, r2 - l) + 1e-15 * r2;
           ep = dmin(lam * sqrt(rnd), lin) + sys + red + 4.0 * r2 * (ra * ra + rb * rb);
         } else {
           /* too far for a linear expansion of r^2 */

@@ -438,9 +438,9 @@ def sr_eval_grad(ctx: Context, programs, lengths, consts, X, y, N: int, mse=None
     _dev(consts, torch.float32, "consts")
     _dev(X, torch.float32, "X")
     _dev(y, torch.float32, "y")
-    for t, name in ((mse, "mse"), (dconst, "dconst")):
-        if t is not None:
-            _dev(t, torch.float64, name)
+    for buf, name in ((mse, "mse"), (dconst, "dconst")):
+        if buf is not None:
+            _dev(buf, torch.float64, name)
     if prog_flags is not None:
         _dev(prog_flags, torch.int32, "prog_flags")
     if mse is None:
@@ -455,8 +455,8 @@ def sr_eval_grad(ctx: Context, programs, lengths, consts, X, y, N: int, mse=None
 
 def sr_adam_step(ctx: Context, consts, grad, m, v, t: int, cfg: AdamCfg):
     """In-place Adam update of consts (float32) with float64 grad / moments."""
-    for t, name in ((grad, "grad"), (m, "m"), (v, "v")):
-        _need(t, consts.numel(), name)
+    for buf, name in ((grad, "grad"), (m, "m"), (v, "v")):
+        _need(buf, consts.numel(), name)
     _dev(consts, torch.float32, "consts")
     _dev(grad, torch.float64, "grad")
     _dev(m, torch.float64, "m")

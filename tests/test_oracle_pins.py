@@ -338,6 +338,132 @@ def test_fitness_error_bound_flags_hopeless_programs():
     assert cfl[2] & oracle.CF_RANGE
 
 
+# ---------------------------------------------------------------- first-order bound
+def test_first_order_chain_of_additions_closed_form():
+    """x0 + x0 + ... (n additions) at x0 = 1.5: node k holds s_k = 1.5 (k + 1)
+    and dyhat/dv_k = 1, so s2 = sum_k (u s_k)^2 and w1 = sum_k u s_k; the
+    systematic part is the bias share of w1 (additions have no curvature)."""
+    u, n = oracle.U_FP32, 9
+    X = np.full((1, 3), 1.5)
+    tok = parse("x0 " + "x0 + " * n)
+    yh, s2, w1, w, cf = oracle.first_order_cases(tok, [], X, raw=True)
+    sk = 1.5 * np.arange(2, n + 2)
+    assert yh[0] == 1.5 * (n + 1) and cf[0] == 0
+    assert s2[0] == pytest.approx(np.sum((u * sk) ** 2), rel=1e-12)
+    assert w1[0] == pytest.approx(np.sum(u * sk), rel=1e-12)
+    assert w[0] == pytest.approx(0.0625 * np.sum(u * sk), rel=1e-12)
+    # a product: c_j = v_j dyhat/dv_j; x0 x1 * x2 * has nodes p = x0 x1 and
+    # q = p x2, both with c = q
+    X3 = np.array([[1.25], [3.0], [-2.5]])
+    yh, s2, w1, w, cf = oracle.first_order_cases(parse("x0 x1 * x2 *"), [], X3, raw=True)
+    q = 1.25 * 3.0 * -2.5
+    assert s2[0] == pytest.approx(2 * (u * q) ** 2, rel=1e-12) and w1[0] == pytest.approx(2 * u * abs(q))
+
+
+def _perturbed_eval(tok, X, i, eps, rng, draws):
+    """FP64 evaluation of case i with every operator output multiplied by
+    (1 + d), d ~ U(-eps, eps) independently: draws samples (brute force)."""
+    out = np.empty(draws)
+    for k in range(draws):
+        st = []
+        for t in tok:
+            t = int(t)
+            if t >= 16:
+                st.append(float(X[t - 16, i]))
+                continue
+            if t < 4:
+                b, a = st.pop(), st.pop()
+                r = [a + b, a - b, a * b, 1.0 if abs(b) <= 1e-3 else a / b][t]
+            else:
+                x = st.pop()
+                r = [math.sin(x), math.cos(x), math.exp(min(max(x, -80), 80)),
+                     0.0 if abs(x) <= 1e-3 else math.log(abs(x)), math.sqrt(abs(x)), x * x][t - 4]
+            st.append(r * (1.0 + rng.uniform(-eps, eps)))
+        out[k] = st[0]
+    return out
+
+
+@pytest.mark.parametrize("text", ["x0 x1 * sin x2 exp +", "x0 x1 / log x2 sqrt * x0 cos -",
+                                  "x0 x0 * x1 - sq x2 / x1 sin *"])
+def test_first_order_variance_matches_brute_force(text):
+    """The variance scale s2 = sum_j (u c_j)^2 against Monte-Carlo: with every
+    operator output perturbed by an independent U(-eps, eps) relative error,
+    the output's variance is eps^2 / 3 sum_j c_j^2 to first order."""
+    rng = np.random.default_rng(11)
+    X = np.array([[1.3, 2.2], [0.7, 4.1], [1.9, 0.6]])
+    tok = parse(text)
+    eps = 1e-7
+    yh, s2, w1, w, cf = oracle.first_order_cases(tok, [], X, u=eps, raw=True)
+    for i in range(X.shape[1]):
+        samp = _perturbed_eval(tok, X, i, eps, rng, 3000)
+        var = np.var(samp - yh[i])
+        assert cf[i] == 0
+        assert var == pytest.approx(s2[i] / 3.0, rel=0.12), (text, i)
+        assert np.abs(samp - yh[i]).max() <= w1[i] * (1 + 1e-6)  # the linear worst case bounds every draw
+
+
+def test_first_order_flags_branches_and_falls_back_to_the_enclosure():
+    """A protected divisor within FP32 reach of 1e-3 could take either branch:
+    the raw expansion flags CF_BRANCH; the analysis then takes that case's
+    error at its worst, the rigorous enclosure's half-width."""
+    X = np.array([[2.0, 2.0], [1e-3 * (1 + 1e-7), 0.5]])
+    tok = parse("x0 x1 c0 * /")
+    _, _, _, _, cf = oracle.first_order_cases(tok, [1.0], X, raw=True)
+    assert cf[0] & oracle.CF_BRANCH and cf[1] == 0
+    yh, s2, w1, w, cf = oracle.first_order_cases(tok, [1.0], X)
+    ref, lo, hi, _ = oracle.predict_interval(tok, [1.0], X)
+    assert s2[0] == 0.0 and w1[0] == 0.0 and w[0] == max(hi[0] - ref[0], ref[0] - lo[0])
+    assert w[0] > 1e2  # 1 or 2000: the branch decides
+    # sin of ~1e6: FP32 rounding of the argument moves it by more than 0.1
+    _, _, _, _, cf = oracle.first_order_cases(parse("x0 c0 * sin"), [1e6], X, raw=True)
+    assert (cf & oracle.CF_NONLIN).all()
+
+
+@pytest.mark.parametrize("unary_ops", [6, 12])
+def test_first_order_bound_holds_for_rounded_fp32(unary_ops):
+    """Both fitness kinds of a correctly rounding FP32 evaluation stay within
+    the probabilistic bound errp of the FP64 fitness, on random programs
+    without range flags; errb (the rigorous bound) agrees with condition()."""
+    pr = inputs.make_problem("fo", 21, P=160, Lmin=1, Lmax=40, nvars=3, K=0, N=3000, xlo=-4, xhi=4,
+                             target_len=(3, 5), unary_ops=unary_ops)
+    y = inputs.add_noise(np.random.default_rng(3), np.sin(pr.X[0, : pr.N].astype(np.float64)) * 3
+                         + pr.X[1, : pr.N], 0.05)
+    errb, errp, cfl, f0 = oracle.condition_fo(pr.programs, pr.lengths, pr.consts, pr.X, y, pr.N)
+    for k in (oracle.MSE, oracle.CORR):
+        eb, cf, f = oracle.condition(pr.programs, pr.lengths, pr.consts, pr.X, y, k, pr.N)
+        np.testing.assert_array_equal(eb, errb[k])
+        np.testing.assert_array_equal(f, f0[k])
+    checked = 0
+    for p in range(pr.P):
+        tok = pr.programs[p, : pr.lengths[p]]
+        with np.errstate(all="ignore"):
+            emu = _round32_eval(tok, pr.X, pr.N)
+        for k, fit in ((oracle.MSE, oracle.mse), (oracle.CORR, oracle.corr)):
+            if cfl[k, p] or not np.isfinite(f0[k, p]) or not np.all(np.isfinite(emu)):
+                continue
+            assert abs(fit(emu, y) - f0[k, p]) <= errp[k, p], (p, k, fit(emu, y), f0[k, p], errp[k, p])
+            checked += 1
+    assert checked > (150 if unary_ops == 6 else 100)
+
+
+def test_first_order_bound_is_tighter_over_many_cases():
+    """Rounding errors of different cases are independent: over 20,000 cases
+    the probabilistic bound on a close fit (where the output's rounding, not
+    the reduction, decides) is far below the rigorous worst case, which adds
+    every case's error at its largest."""
+    rng = np.random.default_rng(8)
+    N = 20000
+    X = rng.uniform(1, 3, (3, N)).astype(np.float32)
+    progs, lens = pack([parse("x0 x1 * x2 sin + x0 x2 / -"), parse("x0 x1 * x2 x2 * + sqrt x1 log *")], 16)
+    for p in range(2):
+        f = oracle.predict(progs[p, : lens[p]], [], X)
+        y = (f + 1e-4 * rng.normal(size=N)).astype(np.float32)
+        errb, errp, cfl, f0 = oracle.condition_fo(progs[p:p + 1], lens[p:p + 1], np.zeros((1, 1), np.float32),
+                                                  X, y)
+        assert (cfl == 0).all()
+        assert (errp < 0.2 * errb).all(), (errp, errb)
+
+
 # ---------------------------------------------------------------- gradient
 def test_gradient_closed_form():
     """yhat = c0 * x0: dMSE/dc0 = (2/N) sum (c0 x0 - y) x0."""
