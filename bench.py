@@ -412,6 +412,7 @@ def run_ours(args, rank, world, local_rank):
 
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pr, y.cpu().numpy())
+        line["parity"] = parity_leg(pr, y, X, pop[state["cur"]], ctx, binding, cfg, nun, SEED, state["gen"])
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -434,6 +435,42 @@ def cpu_baseline(pr, y):
     units = float(pr.lengths[idx].astype(np.int64).sum()) * pr.N
     return {"value": units / dt / 1e9, "unit": "GPop/s", "cores": cores, "kind": "oracle",
             "sample": f"{S} of {pr.P} programs x {pr.N} cases, MSE and 1-r^2 (two passes), {dt:.1f} s"}
+
+
+def parity_leg(pr, y_dev, X_dev, population, ctx, binding, vcfg, nun, seed, gen, sample=512):
+    """The error report of this run against the FP64 oracle, outside the
+    timed region, on the population the timed generations produced: the
+    device fitness (both kinds) of a sample of its programs against the
+    oracle's, with the oracle's certificates (oracle.parity_report), and one
+    more generation's selection and variation from the device fitness,
+    bit for bit against the oracle's on the same fitness."""
+    import torch
+
+    import oracle
+    P_, L_, C_ = population
+    f = binding.sr_eval(ctx, P_, L_, C_, X_dev, y_dev, pr.N, binding.SR_MSE_CORR)
+    parents = binding.sr_select_tournament(ctx, f[1].contiguous(), 4, seed, gen)
+    kids = binding.sr_vary(ctx, P_, L_, C_, parents, pr.nvars, vcfg, seed, gen)
+    torch.cuda.synchronize()
+    f = f.cpu().numpy()
+    prog, lens, cons = P_.cpu().numpy(), L_.cpu().numpy(), C_.cpu().numpy()
+    y = y_dev.cpu().numpy()
+    par_or = oracle.tournament(f[1], 4, seed, gen)
+    kids_or = oracle.vary(prog, lens, cons, par_or, cons.shape[1], pr.nvars, seed=seed, gen=gen, unary_ops=nun)
+    t0 = time.perf_counter()
+    idx = np.sort(np.random.default_rng(3).choice(pr.P, min(sample, pr.P), replace=False))
+    errb, errp, cfl, f0 = oracle.condition_fo(prog[idx], lens[idx], cons[idx], pr.X, y, pr.N,
+                                              nthreads=host_cores())
+    reps = {name: oracle.parity_report(k, f[k, idx], f0[k], errb[k], errp[k], cfl[k], y)
+            for k, name in ((oracle.MSE, "mse"), (oracle.CORR, "corr"))}
+    return {"sample": f"{len(idx)} of the {pr.P} programs after the timed generations, all {pr.N} cases, "
+                      f"oracle {time.perf_counter() - t0:.1f} s on {host_cores()} cores",
+            "tolerance": "|f - f_oracle| <= 1e-4 |f_oracle| + floor (1e-7 var(y) MSE, 1e-6 1-r^2) on certified "
+                         "programs; max_rel_tol / p99_rel_tol are |f - f_oracle| / tol over them",
+            **reps,
+            "parents_bit_exact": bool(np.array_equal(parents.cpu().numpy(), par_or)),
+            "offspring_bit_exact": bool(all(np.array_equal(a.cpu().numpy().view(np.uint8), b.view(np.uint8))
+                                            for a, b in zip(kids, kids_or)))}
 
 
 # ------------------------------------------------------------------ other workloads

@@ -436,3 +436,59 @@ def tournament_max(score, k: int, seed: int, gen: int) -> np.ndarray:
     out = np.empty((P, 2), np.int32)
     _load().or_tournament_max(_ptr(f), P, k, seed, gen, _ptr(out))
     return out
+
+
+# ---------------------------------------------------------------- comparison with a device result
+def fitness_floor(kind: int, y) -> float:
+    """Absolute floor of the fitness tolerance (|df| <= 1e-4 |f| + floor):
+    1e-7 var(y) for MSE, 1e-6 for 1 - r^2, so that exact fits (f near 0)
+    are compared too."""
+    return 1e-7 * float(np.var(np.asarray(y, np.float64))) if kind == MSE else 1e-6
+
+
+def top_fraction_agree(f_gpu, f_or, tol, frac=0.01) -> bool:
+    """The device's top ceil(frac P) programs by fitness equal the oracle's
+    as an ordered list, adjacent oracle entries whose fitnesses are within
+    the sum of their tolerances counting as ties (NaN ranks last)."""
+    f_gpu, f_or = np.asarray(f_gpu, np.float64), np.asarray(f_or, np.float64)
+    P = len(f_or)
+    n = max(1, int(np.ceil(frac * P)))
+    key_or = np.where(np.isnan(f_or), np.inf, f_or)
+    key_gp = np.where(np.isnan(f_gpu), np.inf, f_gpu)
+    order_or = np.lexsort((np.arange(P), key_or))[:n]
+    order_gp = np.lexsort((np.arange(P), key_gp))[:n]
+    for i in range(n):
+        a, b = order_or[i], order_gp[i]
+        if a == b:
+            continue
+        if abs(key_or[a] - key_or[b]) <= tol[a] + tol[b]:
+            continue
+        return False
+    return True
+
+
+def parity_report(kind: int, f_gpu, f_or, errb, errp, cflags, y, rel: float = 1e-4) -> dict:
+    """How a device fitness vector compares with the oracle's, for reports:
+    the programs compared, those certified well-conditioned (the smaller
+    bound of errb / errp at most tol / 2, no range flag), those in range but
+    not certified, those whose FP32 evaluation may leave the range or whose
+    fitness is not finite; the largest and 99th-percentile relative error
+    |f_gpu - f| / tol on the certified ones (1 = at the tolerance), how many
+    of them exceed tol and how many in-range ones exceed tol + bound; and
+    whether the top 1 % agree."""
+    f_gpu, f_or = np.asarray(f_gpu, np.float64), np.asarray(f_or, np.float64)
+    tol = rel * np.abs(f_or) + fitness_floor(kind, y)
+    bound = np.minimum(errb, errp)
+    fin = np.isfinite(f_or)
+    well = (cflags == 0) & (bound <= 0.5 * tol) & fin
+    inr = (cflags == 0) & fin
+    with np.errstate(invalid="ignore"):
+        err = np.abs(f_gpu - f_or)
+        r = err[well] / tol[well]
+    return {"n_checked": int(len(f_or)), "n_certified": int(well.sum()), "n_ill": int((inr & ~well).sum()),
+            "n_out_of_range": int((~inr).sum()),
+            "max_rel_tol": float(r.max()) if r.size else None,
+            "p99_rel_tol": float(np.quantile(r, 0.99)) if r.size else None,
+            "n_certified_over_tol": int((err[well] > tol[well]).sum()),
+            "n_ill_over_bound": int((err[inr & ~well] > (tol + bound)[inr & ~well]).sum()),
+            "top1_agree": bool(top_fraction_agree(f_gpu, f_or, tol))}

@@ -35,44 +35,33 @@ def dev(pr, y=None, device="cuda"):
 
 def fitness_floor(kind, y):
     """Absolute floor of the fitness tolerance: 1e-7 var(y) for MSE, 1e-6 for 1 - r^2."""
-    return 1e-7 * float(np.var(np.asarray(y, np.float64))) if kind == oracle.MSE else 1e-6
+    return oracle.fitness_floor(kind, y)
 
 
-def check_fitness(kind, f_gpu, f_or, errb, cflags, y, rel=1e-4):
-    """Tolerance rule: tol = rel |f_oracle| + floor.  A program is
-    well-conditioned when no case can overflow in FP32 and the oracle's
-    bound on how far FP32 evaluation can move its fitness (from interval
-    enclosures of every case) is at most tol / 2; then |f_gpu - f_oracle| <=
-    tol.  Other programs without a range flag must stay within tol + their
-    bound.  Both non-finite counts as agreement.  Returns the number of
-    well-conditioned programs checked."""
+def check_fitness(kind, f_gpu, f_or, errb, cflags, y, rel=1e-4, errp=None):
+    """Tolerance rule: tol = rel |f_oracle| + floor.  A program's bound is the
+    oracle's rigorous interval bound errb, or the smaller of it and the
+    probabilistic first-order bound errp when that is given.  A program is
+    well-conditioned when no case can overflow in FP32 and its bound on how
+    far FP32 evaluation can move its fitness is at most tol / 2; then
+    |f_gpu - f_oracle| <= tol.  Other programs without a range flag must stay
+    within tol + their bound.  Both non-finite counts as agreement.  Returns
+    the number of well-conditioned programs checked."""
     floor = fitness_floor(kind, y)
     tol = rel * np.abs(f_or) + floor
+    bound = errb if errp is None else np.minimum(errb, errp)
     both_inf = ~np.isfinite(f_or) & ~np.isfinite(f_gpu)
-    well = (cflags == 0) & (errb <= 0.5 * tol) & np.isfinite(f_or)
+    well = (cflags == 0) & (bound <= 0.5 * tol) & np.isfinite(f_or)
     err = np.abs(f_gpu - f_or)
     bad = well & ~(err <= tol)
-    assert not bad.any(), (np.nonzero(bad)[0][:10], f_gpu[bad][:5], f_or[bad][:5], errb[bad][:5])
+    assert not bad.any(), (np.nonzero(bad)[0][:10], f_gpu[bad][:5], f_or[bad][:5], bound[bad][:5])
     ill = ~well & (cflags == 0) & np.isfinite(f_or) & ~both_inf
-    bad2 = ill & ~(err <= tol + errb)
-    assert not bad2.any(), (np.nonzero(bad2)[0][:10], f_gpu[bad2][:5], f_or[bad2][:5], errb[bad2][:5])
+    bad2 = ill & ~(err <= tol + bound)
+    assert not bad2.any(), (np.nonzero(bad2)[0][:10], f_gpu[bad2][:5], f_or[bad2][:5], bound[bad2][:5])
     return int(well.sum())
 
 
 def top_fraction_agree(f_gpu, f_or, tol, frac=0.01):
     """The GPU's top ceil(frac P) by fitness equals the oracle's as an ordered
     list, adjacent oracle entries closer than the tolerance counting as ties."""
-    P = len(f_or)
-    n = max(1, int(np.ceil(frac * P)))
-    key_or = np.where(np.isnan(f_or), np.inf, f_or)
-    key_gp = np.where(np.isnan(f_gpu), np.inf, f_gpu)
-    order_or = np.lexsort((np.arange(P), key_or))[:n]
-    order_gp = np.lexsort((np.arange(P), key_gp))[:n]
-    for i in range(n):
-        a, b = order_or[i], order_gp[i]
-        if a == b:
-            continue
-        if abs(key_or[a] - key_or[b]) <= tol[a] + tol[b]:
-            continue
-        return False
-    return True
+    return oracle.top_fraction_agree(f_gpu, f_or, tol, frac)
