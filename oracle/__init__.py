@@ -64,6 +64,7 @@ def _load():
     lib.or_condition_fo.argtypes = [P, P, P, i32, i32, i32, P, i64, P, i32, i64, f64, f64, P, P, P, P, i32]
     lib.or_first_order_cases.argtypes = [P, i32, P, P, i64, i64, f64, f64, i32, P, P, P, P, P]
     lib.or_grad.argtypes = [P, P, P, i32, i32, i32, P, i64, P, i32, i64, P, P, P, P, i32]
+    lib.or_grad_cert.argtypes = [P, P, P, i32, i32, i32, P, i64, P, i32, i64, f64, f64, P, P, P, P, P, i32]
     lib.or_grad_one.argtypes = [P, i32, P, i32, P, i64, P, i64, P, P, P, P]
     lib.or_mse_fp64_consts.argtypes = [P, i32, P, P, i64, P, i64]
     lib.or_mse_fp64_consts.restype = f64
@@ -283,6 +284,31 @@ def grad(programs, lengths, consts, X, y, N: int | None = None, nthreads: int = 
     return m, g, kink, gabs
 
 
+def grad_cert(programs, lengths, consts, X, y, N: int | None = None, u: float = U_FP32, lam: float = LAMBDA,
+              nthreads: int = 0):
+    """MSE, dMSE/dconst [P, K] (forward mode, FP64), gabs [P, K] (as grad()),
+    gerr [P, K] = (2/N) sum_i reach_i a_ik (how far the output's FP32
+    rounding can move the gradient) and nbranch [P] (cases whose branch FP32
+    rounding could flip): see or_grad_cert."""
+    prog = _c(programs, np.uint8)
+    P, Lmax = prog.shape
+    lens = _c(lengths, np.int32)
+    cons = _c(consts, np.float32).reshape(P, -1)
+    K = cons.shape[1]
+    X64, ldx = _X(X)
+    nvars = X64.shape[0]
+    N = ldx if N is None else N
+    y64 = _c(np.asarray(y)[:N], np.float64)
+    m = np.empty(P, np.float64)
+    g = np.empty((P, K), np.float64)
+    gabs = np.empty((P, K), np.float64)
+    gerr = np.empty((P, K), np.float64)
+    nb = np.empty(P, np.int32)
+    _load().or_grad_cert(_ptr(prog), _ptr(lens), _ptr(cons), P, Lmax, K, _ptr(X64), ldx, _ptr(y64), nvars, N,
+                         u, lam, _ptr(m), _ptr(g), _ptr(gabs), _ptr(gerr), _ptr(nb), nthreads)
+    return m, g, gabs, gerr, nb
+
+
 def grad_one_fp64(tokens, consts64, X, y, N: int | None = None):
     """MSE and gradient of one program with FP64 constants (no rounding of c)."""
     t = _c(tokens, np.uint8)
@@ -449,7 +475,9 @@ def fitness_floor(kind: int, y) -> float:
 def top_fraction_agree(f_gpu, f_or, tol, frac=0.01) -> bool:
     """The device's top ceil(frac P) programs by fitness equal the oracle's
     as an ordered list, adjacent oracle entries whose fitnesses are within
-    the sum of their tolerances counting as ties (NaN ranks last)."""
+    the sum of their tolerances counting as ties (NaN ranks last).  tol may
+    hold each program's own slack (its tolerance plus, for a program the
+    oracle does not certify, how far FP32 rounding can move it)."""
     f_gpu, f_or = np.asarray(f_gpu, np.float64), np.asarray(f_or, np.float64)
     P = len(f_or)
     n = max(1, int(np.ceil(frac * P)))
@@ -474,8 +502,11 @@ def parity_report(kind: int, f_gpu, f_or, errb, errp, cflags, y, rel: float = 1e
     not certified, those whose FP32 evaluation may leave the range or whose
     fitness is not finite; the largest and 99th-percentile relative error
     |f_gpu - f| / tol on the certified ones (1 = at the tolerance), how many
-    of them exceed tol and how many in-range ones exceed tol + bound; and
-    whether the top 1 % agree."""
+    of them exceed tol and how many in-range ones exceed tol + bound; and the
+    top 1 %: top1_certified_agree compares the certified programs' best 1 %
+    with ties only within the tolerance, top1_agree the whole population's
+    with each program's slack (tol, plus its bound when it is not certified,
+    unbounded when it may leave the FP32 range)."""
     f_gpu, f_or = np.asarray(f_gpu, np.float64), np.asarray(f_or, np.float64)
     tol = rel * np.abs(f_or) + fitness_floor(kind, y)
     bound = np.minimum(errb, errp)
@@ -485,10 +516,16 @@ def parity_report(kind: int, f_gpu, f_or, errb, errp, cflags, y, rel: float = 1e
     with np.errstate(invalid="ignore"):
         err = np.abs(f_gpu - f_or)
         r = err[well] / tol[well]
+    slack = np.where(well, tol, np.where(inr, tol + bound, np.inf))
+    n_top = max(1, int(np.ceil(0.01 * len(f_or))))
+    top = np.lexsort((np.arange(len(f_or)), np.where(np.isnan(f_or), np.inf, f_or)))[:n_top]
     return {"n_checked": int(len(f_or)), "n_certified": int(well.sum()), "n_ill": int((inr & ~well).sum()),
             "n_out_of_range": int((~inr).sum()),
             "max_rel_tol": float(r.max()) if r.size else None,
             "p99_rel_tol": float(np.quantile(r, 0.99)) if r.size else None,
             "n_certified_over_tol": int((err[well] > tol[well]).sum()),
             "n_ill_over_bound": int((err[inr & ~well] > (tol + bound)[inr & ~well]).sum()),
-            "top1_agree": bool(top_fraction_agree(f_gpu, f_or, tol))}
+            "top1_n": n_top, "top1_n_certified": int(well[top].sum()),
+            "top1_certified_agree": bool(well.sum() == 0 or
+                                         top_fraction_agree(f_gpu[well], f_or[well], tol[well])),
+            "top1_agree": bool(top_fraction_agree(f_gpu, f_or, slack))}

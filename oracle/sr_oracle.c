@@ -1264,9 +1264,10 @@ void or_p2p_range(const uint8_t *programs, const int32_t *lengths, const float *
  * for log, |x| for sqrt|x|, |x| - 80 for exp) or of an argument to a point
  * where the derivative explodes (|cos x| for tan, 1 - |x| for asin and acos).
  */
-void or_grad_one(const uint8_t *tok, int len, const double *c, int K,
-                 const double *X, long ldx, const double *y, long N,
-                 double *mse_out, double *grad, double *kink, double *gabs) {
+void or_grad_one_ex(const uint8_t *tok, int len, const double *c, int K,
+                    const double *X, long ldx, const double *y, long N,
+                    double *mse_out, double *grad, double *kink, double *gabs,
+                    const double *reach, double *gerr) {
   double *val = (double *)malloc(sizeof(double) * (size_t)(len + 1));
   double *tan_ = (double *)malloc(sizeof(double) * (size_t)(len + 1) *
                                   (size_t)(K > 0 ? K : 1));
@@ -1276,6 +1277,8 @@ void or_grad_one(const uint8_t *tok, int len, const double *c, int K,
   for (int k = 0; k < K; ++k) grad[k] = 0.0;
   if (gabs)
     for (int k = 0; k < K; ++k) gabs[k] = 0.0;
+  if (gerr)
+    for (int k = 0; k < K; ++k) gerr[k] = 0.0;
   int finite = 1;
   for (long i = 0; i < N; ++i) {
     int sp = 0;
@@ -1385,15 +1388,83 @@ void or_grad_one(const uint8_t *tok, int len, const double *c, int K,
     for (int k = 0; k < K; ++k) grad[k] += 2.0 * e * tan_[k];
     if (gabs)
       for (int k = 0; k < K; ++k) gabs[k] += 2.0 * fabs(e) * tab[k];
+    if (gerr && reach)
+      for (int k = 0; k < K; ++k) gerr[k] += 2.0 * reach[i] * tab[k];
   }
   for (int k = 0; k < K; ++k) grad[k] /= (double)N;
   if (gabs)
     for (int k = 0; k < K; ++k) gabs[k] /= (double)N;
+  if (gerr)
+    for (int k = 0; k < K; ++k) gerr[k] /= (double)N;
   *mse_out = (finite && isfinite(s)) ? s / (double)N : INFINITY;
   if (kink) *kink = kmin;
   free(val);
   free(tan_);
   free(tab);
+}
+
+void or_grad_one(const uint8_t *tok, int len, const double *c, int K, const double *X, long ldx,
+                 const double *y, long N, double *mse_out, double *grad, double *kink, double *gabs) {
+  or_grad_one_ex(tok, len, c, K, X, ldx, y, N, mse_out, grad, kink, gabs, NULL, NULL);
+}
+
+/*
+ * or_grad with what a comparison of a device gradient needs, per program:
+ *   nbranch  the cases on which FP32 rounding could flip a protected branch,
+ *            a clamp or the sign inside sqrt|x| (CF_BRANCH of the first-order
+ *            analysis, before its fallback): there the device's derivative
+ *            may belong to the other branch, so such a program's gradient is
+ *            not comparable;
+ *   gerr     [P][K] (2/N) sum_i reach_i a_ik: how far the output's FP32
+ *            rounding (reach_i: the first-order analysis's bound on case i,
+ *            or its rigorous enclosure where the expansion is not trusted)
+ *            can move the gradient through e_i, with a_ik the derivative
+ *            propagated with absolute partials.
+ */
+void or_grad_cert(const uint8_t *programs, const int32_t *lengths, const float *consts, int P, int Lmax, int K,
+                  const double *X, long ldx, const double *y, int nvars, long N, double u, double lam,
+                  double *mse, double *grad, double *gabs, double *gerr, int32_t *nbranch, int nthreads) {
+  int nt = thread_count(nthreads);
+#pragma omp parallel num_threads(nt)
+  {
+    size_t nn = (size_t)(N > 0 ? N : 1);
+    double *reach = (double *)malloc(sizeof(double) * nn);
+    double *val = (double *)malloc(sizeof(double) * (size_t)(Lmax + 1) * 4);
+    ival *box = (ival *)malloc(sizeof(ival) * (size_t)(Lmax + 1));
+#pragma omp for schedule(dynamic, 1)
+    for (int p = 0; p < P; ++p) {
+      const uint8_t *tok = programs + (size_t)p * Lmax;
+      int md;
+      double c[TK_NSLOTS];
+      if (or_validate(tok, lengths[p], Lmax, nvars, K, &md)) {
+        mse[p] = INFINITY;
+        for (int k = 0; k < K; ++k)
+          grad[(size_t)p * K + k] = gabs[(size_t)p * K + k] = gerr[(size_t)p * K + k] = 0.0;
+        nbranch[p] = 0;
+        continue;
+      }
+      widen_consts(consts + (size_t)p * K, K, c);
+      int len = lengths[p], nb = 0;
+      size_t L = (size_t)len + 1;
+      for (long i = 0; i < N; ++i) {
+        double s2, w1, w, lo, hi;
+        int cf = 0;
+        case_first_order(tok, len, c, X, ldx, i, u, lam, val, val + L, val + 2 * L, val + 3 * L, &s2, &w1, &w,
+                         &cf);
+        nb += (cf & CF_BRANCH) != 0;
+        int ca = 0;
+        double y0 = case_analysis(tok, len, c, X, ldx, i, u, lam, val, box, &s2, &w1, &w, &lo, &hi, &ca);
+        (void)y0;
+        reach[i] = fo_reach(lam, s2, w1, w);
+      }
+      nbranch[p] = nb;
+      or_grad_one_ex(tok, len, c, K, X, ldx, y, N, &mse[p], grad + (size_t)p * K, NULL, gabs + (size_t)p * K,
+                     reach, gerr + (size_t)p * K);
+    }
+    free(reach);
+    free(val);
+    free(box);
+  }
 }
 
 /* FP64-constant evaluation of MSE for one program (finite differences). */

@@ -70,43 +70,41 @@ def adjoint_problem():
     return pr, inputs.add_noise(np.random.default_rng(1), y, 0.01)
 
 
-def test_gradient_matches_oracle(ctx, adjoint_problem):
-    """On programs whose MSE the FP32 evaluation reproduces to 1e-5 (interval
-    bound) and whose branch arguments stay 1e-3 away from their switch
-    points (derivatives explode next to a protected log or sqrt), every constant's gradient agrees with the FP64 forward-mode
-    gradient within 2e-4 of its absolute-sum scale (2/N) sum |e dyhat/dc|."""
-    pr, y = adjoint_problem
-    d = dev(pr, y)
-    mse_g, g_g = binding.sr_eval_grad(ctx, d["programs"], d["lengths"], d["consts"], d["X"], d["y"], pr.N)
-    mse_g, g_g = mse_g.cpu().numpy(), g_g.cpu().numpy()
-    mse_o, g_o, kink, gabs = oracle.grad(pr.programs, pr.lengths, pr.consts, pr.X, y, pr.N)
-    errb, cfl, f0 = oracle.condition(pr.programs, pr.lengths, pr.consts, pr.X, y, oracle.MSE, pr.N)
-    well = (cfl == 0) & np.isfinite(f0) & (errb <= 1e-5 * np.abs(f0)) & (kink > 1e-3)
-    assert well.sum() > 100
-    err = np.abs(g_g - g_o)
-    tol = 2e-4 * gabs + 1e-12
-    bad = well[:, None] & ~(err <= tol)
-    assert not bad.any(), (np.argwhere(bad)[:5], g_g[bad][:5], g_o[bad][:5], gabs[bad][:5])
-    fin = np.isfinite(f0)
-    np.testing.assert_allclose(mse_g[well], mse_o[well], rtol=1e-5)
-    assert np.isinf(mse_g[~fin]).all() if (~fin).any() else True
+def _grad_tol(gabs, gerr):
+    """|g_gpu - g_oracle| <= 2e-4 gabs + gerr + 1e-12: gabs = (2/N) sum |e_i| a_ik
+    is the rounding scale of any evaluation order of the chain rule, gerr =
+    (2/N) sum reach_i a_ik what the output's own FP32 rounding adds (oracle
+    grad_cert)."""
+    return 2e-4 * gabs + gerr + 1e-12
 
 
-def test_gradient_matches_central_differences(ctx, adjoint_problem):
-    """The device gradient vs FP64 central differences (h = 1e-6) of the
-    oracle's MSE on 256 sampled programs (those away from kinks and not too
-    curved for h)."""
+def test_gradient_matches_oracle_and_central_differences(ctx, adjoint_problem):
+    """256 programs of the adjoint workload's shape (K = 8, L <= 96, 5
+    variables) at 4,099 cases.  A program is compared unless FP32 rounding
+    could flip one of its branches on some case (oracle grad_cert: nbranch;
+    the device derivative there may belong to the other branch) or its
+    values leave the FP32 range; at least half must be.  Each compared
+    program's gradient must agree (a) with the oracle's forward-mode FP64
+    gradient within _grad_tol, and (b) with FP64 central differences of the
+    oracle's MSE (h = 1e-6, constants in FP64) within _grad_tol plus the
+    differences' own truncation estimate (|d(h) - d(h/2)| 4/3), on every
+    constant whose difference the FP64 MSE can resolve."""
     pr, y = adjoint_problem
     d = dev(pr, y)
     _, g_g = binding.sr_eval_grad(ctx, d["programs"], d["lengths"], d["consts"], d["X"], d["y"], pr.N)
     g_g = g_g.cpu().numpy()
-    _, _, kink, gabs = oracle.grad(pr.programs, pr.lengths, pr.consts, pr.X, y, pr.N)
-    errb, cfl, f0 = oracle.condition(pr.programs, pr.lengths, pr.consts, pr.X, y, oracle.MSE, pr.N)
-    idx = np.random.default_rng(5).choice(pr.P, 256, replace=False)
-    h, tested = 1e-6, 0
-    for p in idx:
-        if cfl[p] or not np.isfinite(f0[p]) or errb[p] > 1e-5 * abs(f0[p]) or kink[p] < 1e-3:
-            continue
+    idx = np.sort(np.random.default_rng(5).choice(pr.P, 256, replace=False))
+    sub = (pr.programs[idx], pr.lengths[idx], pr.consts[idx])
+    mse_o, g_o, gabs, gerr, nb = oracle.grad_cert(*sub, pr.X, y, pr.N)
+    errb, errp, cfl, f0 = oracle.condition_fo(*sub, pr.X, y, pr.N)
+    ok = (nb == 0) & (cfl[0] == 0) & np.isfinite(f0[0])
+    assert ok.sum() >= 128, ok.sum()
+    tol = _grad_tol(gabs, gerr)
+    bad = ok[:, None] & ~(np.abs(g_g[idx] - g_o) <= tol)
+    assert not bad.any(), (np.argwhere(bad)[:5], g_g[idx][bad][:5], g_o[bad][:5], tol[bad][:5])
+    h, fd_checked = 1e-6, 0
+    for j in np.nonzero(ok)[0]:
+        p = idx[j]
         tok = pr.programs[p, : pr.lengths[p]]
         c = pr.consts[p].astype(np.float64)
 
@@ -117,18 +115,14 @@ def test_gradient_matches_central_differences(ctx, adjoint_problem):
             return (oracle.mse_fp64_consts(tok, cp, pr.X, y, pr.N)
                     - oracle.mse_fp64_consts(tok, cm, pr.X, y, pr.N)) / (2 * step)
 
-        ok = True
         for k in range(pr.K):
-            if gabs[p, k] * h < 1e-9 * abs(f0[p]):
+            if gabs[j, k] * h < 1e-9 * abs(f0[0, j]):
                 continue  # the difference would be below the FP64 resolution of the MSE
             d1, d2 = fd(k, h), fd(k, h / 2)
             trunc = abs(d1 - d2) * 4 / 3
-            if trunc > 1e-4 * max(abs(d1), gabs[p, k], 1e-12):
-                ok = False
-                break
-            assert abs(g_g[p, k] - d1) <= 2e-4 * gabs[p, k] + 2 * trunc + 1e-10, (p, k, g_g[p, k], d1)
-        tested += ok
-    assert tested >= 25
+            assert abs(g_g[p, k] - d1) <= tol[j, k] + 2 * trunc, (p, k, g_g[p, k], d1, tol[j, k], trunc)
+        fd_checked += 1
+    assert fd_checked >= 128
 
 
 def test_adam_bit_exact(ctx):
@@ -194,23 +188,32 @@ def test_invalid_programs_in_gradient(ctx):
 
 def test_full_size_adjoint_sampled(ctx):
     """16,384 programs x 1,000,000 cases, K = 8 (the adjoint workload and the
-    launch configuration the bench times): sampled programs against the
-    oracle's forward-mode gradient on every case.  Over 10^6 cases nearly
-    every program with a protected operator has some case next to a switch
-    point, so the sample is drawn from the short programs (<= 16 tokens)."""
+    launch configuration the bench times): a sample stratified over the
+    whole length range (12 programs from each of 4-24, 25-48, 49-72 and
+    73-96 tokens) against the oracle's forward-mode gradient on every case,
+    compared as in test_gradient_matches_oracle_and_central_differences.
+    Over 10^6 cases more programs have some case where FP32 could flip a
+    branch; at least 40 % of the sample, and some programs above 64 tokens,
+    must be compared."""
     pr = inputs.adjoint()
     y = oracle.predict(pr.target, pr.target_consts, pr.X, pr.N)
     y = inputs.add_noise(np.random.default_rng(3), y, 0.01)
     d = dev(pr, y)
     mse_g, g_g = binding.sr_eval_grad(ctx, d["programs"], d["lengths"], d["consts"], d["X"], d["y"], pr.N)
     mse_g, g_g = mse_g.cpu().numpy(), g_g.cpu().numpy()
-    short = np.nonzero(pr.lengths <= 16)[0]
-    idx = np.sort(np.random.default_rng(4).choice(short, 48, replace=False))
+    rng = np.random.default_rng(4)
+    bins = [(4, 24), (25, 48), (49, 72), (73, 96)]
+    idx = np.sort(np.concatenate([rng.choice(np.nonzero((pr.lengths >= a) & (pr.lengths <= b))[0], 12,
+                                             replace=False) for a, b in bins]))
     sub = (pr.programs[idx], pr.lengths[idx], pr.consts[idx])
-    mse_o, g_o, kink, gabs = oracle.grad(*sub, pr.X, y, pr.N)
-    errb, cfl, f0 = oracle.condition(*sub, pr.X, y, oracle.MSE, pr.N)
-    well = (cfl == 0) & np.isfinite(f0) & (errb <= 1e-5 * np.abs(f0)) & (kink > 1e-3)
-    assert well.sum() >= 8
-    bad = well[:, None] & ~(np.abs(g_g[idx] - g_o) <= 2e-4 * gabs + 1e-12)
-    assert not bad.any(), (np.argwhere(bad)[:5], g_g[idx][bad][:5], g_o[bad][:5])
-    np.testing.assert_allclose(mse_g[idx][well], mse_o[well], rtol=1e-5)
+    mse_o, g_o, gabs, gerr, nb = oracle.grad_cert(*sub, pr.X, y, pr.N)
+    errb, errp, cfl, f0 = oracle.condition_fo(*sub, pr.X, y, pr.N)
+    ok = (nb == 0) & (cfl[0] == 0) & np.isfinite(f0[0])
+    long_ = pr.lengths[idx] > 64
+    print(f"compared {int(ok.sum())} of {len(idx)}; above 64 tokens {int((ok & long_).sum())} of {int(long_.sum())}")
+    assert ok.sum() >= 0.4 * len(idx) and (ok & long_).sum() >= 2
+    tol = _grad_tol(gabs, gerr)
+    bad = ok[:, None] & ~(np.abs(g_g[idx] - g_o) <= tol)
+    assert not bad.any(), (np.argwhere(bad)[:5], g_g[idx][bad][:5], g_o[bad][:5], tol[bad][:5])
+    tol_m = 1e-4 * np.abs(f0[0]) + np.minimum(errb[0], errp[0]) + oracle.fitness_floor(oracle.MSE, y)
+    assert (np.abs(mse_g[idx] - mse_o) <= tol_m)[ok].all()

@@ -464,6 +464,29 @@ def test_first_order_bound_is_tighter_over_many_cases():
         assert (errp < 0.2 * errb).all(), (errp, errb)
 
 
+def test_gradient_certificate_closed_form():
+    """grad_cert: the same MSE, gradient and gabs as grad(); for yhat = c0 x0
+    the output's reach is u |yhat| (1 + 1/16) on every case (one rounding,
+    its systematic share), so gerr = (2/N) sum_i reach_i |x0_i|; a divisor
+    at 1e-3 within FP32 reach counts one branch case."""
+    rng = np.random.default_rng(12)
+    N = 400
+    X = rng.uniform(1, 5, (2, N)).astype(np.float32)
+    X[1, 7] = np.float32(1e-3)  # 1e-3 + 4.7e-11: a computed divisor there is within FP32 reach of 1e-3
+    y = rng.normal(size=N).astype(np.float32)
+    progs, lens = pack([parse("c0 x0 *"), parse("x0 x1 c1 * / c0 *")], 8)
+    consts = np.array([[1.75, 1.0], [0.5, 1.0]], np.float32)
+    m, g, gabs, gerr, nb = oracle.grad_cert(progs, lens, consts, X, y)
+    m2, g2, _, gabs2 = oracle.grad(progs, lens, consts, X, y)
+    np.testing.assert_array_equal(m, m2)
+    np.testing.assert_array_equal(g, g2)
+    np.testing.assert_array_equal(gabs, gabs2)
+    x0 = X[0].astype(np.float64)
+    reach = oracle.U_FP32 * np.abs(1.75 * x0) * (1 + 1 / 16)
+    assert gerr[0, 0] == pytest.approx(2.0 / N * np.sum(reach * x0), rel=1e-12)
+    assert nb.tolist() == [0, 1]
+
+
 # ---------------------------------------------------------------- gradient
 def test_gradient_closed_form():
     """yhat = c0 * x0: dMSE/dc0 = (2/N) sum (c0 x0 - y) x0."""
