@@ -579,55 +579,120 @@ def run_workload(args, local_rank):
             "vs_baseline": None, "steps": args.steps, "warmup": args.warmup}
 
     if args.workload == "batched":
-        shapes = inputs.batched_shapes()[: 8 if args.small else None]
-        pops, work = [], 0.0
-        for sh in shapes:
-            pr, pg, ln, cs, X, y = _device_problem(lambda a, sh=sh: inputs.batched_problem(sh, attempt=a),
-                                                   dev, binding, ctx)
-            kind = binding.SR_CORR if sh["kind"] else binding.SR_MSE
-            cfg = EvolveConfig(select_kind=kind, eval_kind=kind)
-            pops.append(Population(pg, ln, cs, X, y, pr.N, cfg))
-        nodes = lambda: sum(float(p.current[1].sum()) * p.N for p in pops)
-        # (a) plain loop: one sr_eval call per problem, eager
-        def plain_loop():
+        from paper_2603_12292_gb300.autotune import Autotuner
+        tuner = Autotuner(ctx)
+
+        def build(shapes):
+            pops = []
+            for sh in shapes:
+                pr, pg, ln, cs, X, y = _device_problem(lambda a, sh=sh: inputs.batched_problem(sh, attempt=a),
+                                                       dev, binding, ctx)
+                kind = binding.SR_CORR if sh["kind"] else binding.SR_MSE
+                cfg = EvolveConfig(select_kind=kind, eval_kind=kind)
+                pops.append(Population(pg, ln, cs, X, y, pr.N, cfg))
+            return pops
+
+        nodes = lambda pops: sum(float(p.current[1].sum()) * p.N for p in pops)
+
+        def compare_eval(pops):
+            """One evaluation of every problem: a loop of sr_eval calls, one
+            batched call with the library's automatic shape, and one with the
+            autotuned shape (cases per item x CTAs per SM)."""
+            def plain_loop():
+                for p in pops:
+                    binding.sr_eval(ctx, *p.current, p.X, p.y, p.N, p.cfg.eval_kind, fitness=p.fitness[0])
+            probs = [binding.make_problem(*p.current, p.X, p.y, p.N, p.cfg.eval_kind, fitness=p.fitness[0])
+                     for p in pops]
+            batched = lambda: binding.sr_eval_batched(ctx, probs)
+            for f in (plain_loop, batched):
+                for _ in range(max(1, args.warmup)):
+                    f()
+            t_plain = _timed(plain_loop, args.steps, stream)
+            binding.sr_set_occupancy(ctx, 0, 0)
+            t_auto = _timed(batched, args.steps, stream)
+            best = tuner.tune_batched(probs)
+            t_tuned = _timed(batched, args.steps, stream)
+            n = nodes(pops)
+            return {"problems": len(pops), "node_cases": n, "plain_loop_gpops": n / t_plain / 1e6,
+                    "batched_auto_gpops": n / t_auto / 1e6, "batched_tuned_gpops": n / t_tuned / 1e6,
+                    "batched_over_plain": t_plain / t_tuned, "tuned_over_auto": t_auto / t_tuned,
+                    "tuned": {"cases_per_tile": best["tile"] or "automatic", "ctas_per_sm": best["ctas"]},
+                    "ms": {"plain_loop": t_plain, "batched_auto": t_auto, "batched_tuned": t_tuned}}
+
+        def compare_adam(pops):
+            """One Adam step on every problem's constants: a loop of
+            sr_eval_grad + sr_adam_step per problem, against one
+            sr_eval_grad_batched + one sr_adam_step_batched."""
+            acfg = binding.adam_cfg()
+            bufs = []
             for p in pops:
-                binding.sr_eval(ctx, *p.current, p.X, p.y, p.N, p.cfg.eval_kind, fitness=p.fitness[0])
-        # (b) one persistent launch over all problems
-        probs = [binding.make_problem(*p.current, p.X, p.y, p.N, p.cfg.eval_kind, fitness=p.fitness[0])
-                 for p in pops]
-        def batched():
-            binding.sr_eval_batched(ctx, probs)
-        n0 = nodes()
-        for f in (plain_loop, batched):
-            for _ in range(args.warmup):
-                f()
-        t_plain = _timed(plain_loop, args.steps, stream)
-        t_batch = _timed(batched, args.steps, stream)
-        # (c) the whole generation loop, batched and captured as a CUDA graph
+                P_, L_, C_ = p.current
+                g = torch.empty((P_.shape[0], C_.shape[1]), dtype=torch.float64, device=dev)
+                bufs.append((torch.empty(P_.shape[0], dtype=torch.float64, device=dev), g, torch.zeros_like(g),
+                             torch.zeros_like(g), C_.clone()))
+            st = {"t": 0}
+
+            def loop():
+                st["t"] += 1
+                for p, (mse, g, m, v, c) in zip(pops, bufs):
+                    P_, L_, _ = p.current
+                    binding.sr_eval_grad(ctx, P_, L_, c, p.X, p.y, p.N, mse=mse, dconst=g)
+                    binding.sr_adam_step(ctx, c, g, m, v, st["t"], acfg)
+            gp = [binding.make_grad_problem(p.current[0], p.current[1], c, p.X, p.y, p.N, mse=mse, dconst=g)
+                  for p, (mse, g, m, v, c) in zip(pops, bufs)]
+            tables = [(c, g, m, v) for (mse, g, m, v, c) in bufs]
+
+            def batched():
+                st["t"] += 1
+                binding.sr_eval_grad_batched(ctx, gp)
+                binding.sr_adam_step_batched(ctx, tables, st["t"], acfg)
+            for f in (loop, batched):
+                for _ in range(max(1, args.warmup)):
+                    f()
+            t_loop = _timed(loop, args.steps, stream)
+            t_b = _timed(batched, args.steps, stream)
+            n = nodes(pops)
+            return {"problems": len(pops), "loop_steps_per_s": 1e3 / t_loop, "batched_steps_per_s": 1e3 / t_b,
+                    "batched_over_loop": t_loop / t_b, "loop_grad_gpops": n / t_loop / 1e6,
+                    "batched_grad_gpops": n / t_b / 1e6}
+
+        main_shapes = inputs.batched_shapes()[: 8 if args.small else None]
+        pops = build(main_shapes)
+        small = build(inputs.small_batch_shapes())
+        r_main = compare_eval(pops)
+        r_small = compare_eval(small)
+        r_adam = compare_adam(small)
+        # the whole generation loop of the main batch, batched, autotuned and
+        # captured as a CUDA graph
         ev = Evolver(ctx, pops, batched=True)
+        ev.autotune(tuner)
         l0 = binding.sr_kernel_launches(ctx)
         ev.step()  # one eager generation: the launches a replayed generation makes
         per_gen = binding.sr_kernel_launches(ctx) - l0
         ev.capture(2)
         torch.cuda.synchronize()
         gens = 2 * max(1, args.steps // 2)
-        n_gen = nodes()
+        n_gen = nodes(pops)
         with _Region(binding, ctx, local_rank) as region:
             t_graph = _timed(lambda: ev.run(gens), 1, stream) / gens
-        line.update(metric=f"GPop/s, {len(shapes)} problems per generation (batched + graph vs plain loop)",
+        binding.sr_set_occupancy(ctx, 0, 0)
+        line.update(metric=f"GPop/s, {len(main_shapes)} problems per generation (batched + graph vs plain loop)",
                     value=n_gen / (t_graph / 1e3) / 1e9, unit="GPop/s", ms_per_step=t_graph,
                     scaling="weak",
-                    config={"workload": f"batched-{len(shapes)}: nvars 1-10, N log-uniform 1k-1M, P 512-8192, "
-                                        "L 4-256, MSE/1-r^2 mixed",
-                            "problems": len(pops), "node_cases_per_eval": n0},
-                    roofline=_roofline(dev, n0 / (t_batch / 1e3) / 1e9, "eval_batched_kernel (sr_eval_batched)",
+                    config={"workload": f"batched-{len(main_shapes)}: nvars 1-10, N log-uniform 1k-1M, "
+                                        "P 512-8192, L 4-256, MSE/1-r^2 mixed",
+                            "problems": len(pops), "node_cases_per_eval": r_main["node_cases"],
+                            "step": "one generation: sr_eval_batched (autotuned) + tournament + variation per "
+                                    "problem, CUDA-graph replay"},
+                    roofline=_roofline(dev, r_main["batched_tuned_gpops"], "eval_batched_kernel (sr_eval_batched)",
                                        "one batched evaluation, CUDA events over a loop of calls",
-                                       f"batched-{len(shapes)}", "batched", n0),
+                                       f"batched-{len(main_shapes)}", "batched", r_main["node_cases"]),
                     clocks=region.clocks, gpu_launches=int(per_gen * gens),
-                    batched_eval_gpops=n0 / (t_batch / 1e3) / 1e9,
-                    plain_loop_eval_gpops=n0 / (t_plain / 1e3) / 1e9,
-                    batched_over_plain=t_plain / t_batch,
-                    generation_graph_ms=t_graph, eval_batched_ms=t_batch, eval_plain_loop_ms=t_plain)
+                    batched_eval=r_main, small_batch_eval=dict(r_small, workload="small-64: nvars 1-10, N 316-10k, "
+                                                                "P 64-1024, L 4-64, MSE/1-r^2 mixed"),
+                    small_batch_adam=dict(r_adam, workload="small-64, K = 4, one Adam step per problem"),
+                    batched_over_plain=r_main["batched_over_plain"],
+                    generation_graph_ms=t_graph)
     elif args.workload == "adjoint":
         pr, pg, ln, cs, X, y = _device_problem(
             lambda a: inputs.adjoint(attempt=a, P=2048, N=131072) if args.small else inputs.adjoint(attempt=a),

@@ -239,6 +239,16 @@ sr_status sr_eval_batched(sr_ctx *ctx, const sr_problem *problems, int nprob);
  * choice (about eight items per resident warp).  Set by the autotuner. */
 sr_status sr_set_tile(sr_ctx *ctx, int cases_per_tile);
 
+/* CTAs (of 8 warps) per SM of the persistent evaluation kernels, set by the
+ * autotuner.  eval_ctas_per_sm: sr_eval / sr_eval_score / sr_predict, 0
+ * (automatic: 5 where Lmax <= 200, else 4), 4 or 5 (5 only where it fits,
+ * else 4).  batched_ctas_per_sm: sr_eval_batched, 0 (automatic: 4), 3, 4 or
+ * 5.  Fewer CTAs give each warp more stack slots in shared memory (fewer
+ * programs in the deep pass) and more registers; more CTAs hide more
+ * latency.  Results do not depend on it (per-program sums do not depend on
+ * which warp runs an item).  Errors: SR_EINVAL. */
+sr_status sr_set_occupancy(sr_ctx *ctx, int eval_ctas_per_sm, int batched_ctas_per_sm);
+
 /*
  * sr_predict -- the output yhat of every program on every case (the value
  * left on the stack, Sec. 2.1.4), FP32.
@@ -420,6 +430,37 @@ sr_status sr_eval_grad(sr_ctx *ctx, const uint8_t *programs,
                        int nvars, int N, int ldx, double *mse, double *dconst,
                        int32_t *prog_flags);
 
+/* One problem of a batched gradient call: its own population, data and
+ * outputs (as the arguments of sr_eval_grad). */
+typedef struct {
+  const uint8_t *programs;  /* device [P][Lmax]                          */
+  const int32_t *lengths;   /* device [P]                                */
+  const float *consts;      /* device [P][K], K >= 1                     */
+  int P, Lmax, K;
+  const float *X;           /* device [nvars][ldx], 16-byte aligned      */
+  const float *y;           /* device [N]                                */
+  int nvars, N, ldx;
+  double *mse;              /* device [P], written                       */
+  double *dconst;           /* device [P][K], written                    */
+  int32_t *prog_flags;      /* device [P] or NULL                        */
+} sr_grad_problem;
+
+/*
+ * sr_eval_grad_batched -- sr_eval_grad of many independent problems
+ * (different populations, constant counts, lengths, variables and case
+ * counts) in one persistent launch: one atomic work counter hands out
+ * (problem, case chunk, program) items, longest first, to the warps of one
+ * grid, so that many small problems keep the whole GPU busy where a loop of
+ * sr_eval_grad calls would launch each on its own.  Up to 64 problems share
+ * a launch (more are split into groups of 64).  Each problem is cut into
+ * the case chunks sr_eval_grad would use for it alone, so its results are
+ * bit for bit those of its own sr_eval_grad call on the same context.
+ *   problems  host array of nprob entries (read during the call)
+ * Errors: SR_EINVAL (the first bad problem is named in sr_last_error),
+ * SR_ENOMEM, SR_ECUDA.
+ */
+sr_status sr_eval_grad_batched(sr_ctx *ctx, const sr_grad_problem *problems, int nprob);
+
 typedef struct {
   double lr;     /* step size (default 1e-2)  */
   double beta1;  /* default 0.9               */
@@ -439,6 +480,22 @@ typedef struct {
 sr_status sr_adam_step(sr_ctx *ctx, float *consts, const double *grad,
                        double *m, double *v, int n, int t,
                        const sr_adam_cfg *cfg);
+
+/* One table of constants updated by sr_adam_step_batched (as the arguments
+ * of sr_adam_step). */
+typedef struct {
+  float *consts;        /* device [n], updated */
+  const double *grad;   /* device [n]          */
+  double *m, *v;        /* device [n], updated */
+  int n;
+} sr_adam_table;
+
+/* sr_adam_step_batched -- sr_adam_step on many tables with one step number
+ * and configuration, in one launch per 64 tables: the constant update of
+ * every problem of a batched gradient (sr_eval_grad_batched).  Each table's
+ * result is bit for bit that of sr_adam_step on it.  Errors: SR_EINVAL. */
+sr_status sr_adam_step_batched(sr_ctx *ctx, const sr_adam_table *tables, int ntables, int t,
+                               const sr_adam_cfg *cfg);
 
 /*
  * sr_eval_noalloc -- sr_eval for callers that cannot allocate device memory.

@@ -473,26 +473,29 @@ def fitness_floor(kind: int, y) -> float:
 
 
 def top_fraction_agree(f_gpu, f_or, tol, frac=0.01) -> bool:
-    """The device's top ceil(frac P) programs by fitness equal the oracle's
-    as an ordered list, adjacent oracle entries whose fitnesses are within
-    the sum of their tolerances counting as ties (NaN ranks last).  tol may
-    hold each program's own slack (its tolerance plus, for a program the
+    """The device's top ceil(frac P) programs by fitness agree with the
+    oracle's: over the union of both top sets, no pair is in the opposite
+    order on the device by more than the two programs' slack, i.e. the
+    device may put i before j only if f_or[i] <= f_or[j] + tol[i] + tol[j]
+    (NaN ranks last).  With tol the tolerance this is the identical ranking
+    up to ties within the tolerance, and it covers membership: a program in
+    one top set but not the other must tie with those it displaces.  tol
+    may hold each program's own slack (its tolerance plus, for a program the
     oracle does not certify, how far FP32 rounding can move it)."""
     f_gpu, f_or = np.asarray(f_gpu, np.float64), np.asarray(f_or, np.float64)
+    tol = np.asarray(tol, np.float64)
     P = len(f_or)
     n = max(1, int(np.ceil(frac * P)))
     key_or = np.where(np.isnan(f_or), np.inf, f_or)
     key_gp = np.where(np.isnan(f_gpu), np.inf, f_gpu)
-    order_or = np.lexsort((np.arange(P), key_or))[:n]
-    order_gp = np.lexsort((np.arange(P), key_gp))[:n]
-    for i in range(n):
-        a, b = order_or[i], order_gp[i]
-        if a == b:
-            continue
-        if abs(key_or[a] - key_or[b]) <= tol[a] + tol[b]:
-            continue
-        return False
-    return True
+    top_or = np.lexsort((np.arange(P), key_or))[:n]
+    top_gp = np.lexsort((np.arange(P), key_gp))[:n]
+    cand = np.union1d(top_or, top_gp)
+    kg, ko, sl = key_gp[cand], key_or[cand], tol[cand]
+    before = (kg[:, None] < kg[None, :]) | ((kg[:, None] == kg[None, :]) & (cand[:, None] < cand[None, :]))
+    with np.errstate(invalid="ignore"):
+        inverted = before & (ko[:, None] > ko[None, :] + sl[:, None] + sl[None, :])
+    return not bool(inverted.any())
 
 
 def parity_report(kind: int, f_gpu, f_or, errb, errp, cflags, y, rel: float = 1e-4) -> dict:

@@ -26,7 +26,8 @@ EXPORTS = ["sr_create", "sr_destroy", "sr_set_stream", "sr_status_string", "sr_l
            "sr_eval_noalloc", "sr_philox4x32_10", "sr_select_tournament", "sr_vary",
            "sr_random_programs", "sr_eval_grad", "sr_adam_step", "sr_eval_batched", "sr_set_tile",
            "sr_eval_score", "sr_select_tournament_max", "sr_select_microcosm",
-           "sr_set_generation_source", "sr_set_abort_flag"]
+           "sr_set_generation_source", "sr_set_abort_flag", "sr_eval_grad_batched",
+           "sr_set_occupancy", "sr_adam_step_batched"]
 
 _lib = None
 
@@ -47,6 +48,21 @@ class Problem(ctypes.Structure):
                 ("nvars", ctypes.c_int), ("N", ctypes.c_int), ("ldx", ctypes.c_int),
                 ("kind", ctypes.c_int), ("fitness", ctypes.c_void_p), ("prog_flags", ctypes.c_void_p),
                 ("cases_per_tile", ctypes.c_int)]
+
+
+class GradProblem(ctypes.Structure):
+    """sr_grad_problem (include/sr.h)."""
+    _fields_ = [("programs", ctypes.c_void_p), ("lengths", ctypes.c_void_p), ("consts", ctypes.c_void_p),
+                ("P", ctypes.c_int), ("Lmax", ctypes.c_int), ("K", ctypes.c_int),
+                ("X", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("nvars", ctypes.c_int), ("N", ctypes.c_int), ("ldx", ctypes.c_int),
+                ("mse", ctypes.c_void_p), ("dconst", ctypes.c_void_p), ("prog_flags", ctypes.c_void_p)]
+
+
+class AdamTable(ctypes.Structure):
+    """sr_adam_table (include/sr.h)."""
+    _fields_ = [("consts", ctypes.c_void_p), ("grad", ctypes.c_void_p), ("m", ctypes.c_void_p),
+                ("v", ctypes.c_void_p), ("n", ctypes.c_int)]
 
 
 class AdamCfg(ctypes.Structure):
@@ -108,7 +124,10 @@ def lib() -> ctypes.CDLL:
     L.sr_adam_step.argtypes = [vp, vp, vp, vp, vp, i32, i32, ctypes.POINTER(AdamCfg)]
     L.sr_eval_batched.argtypes = [vp, ctypes.POINTER(Problem), i32]
     L.sr_set_tile.argtypes = [vp, i32]
+    L.sr_set_occupancy.argtypes = [vp, i32, i32]
+    L.sr_adam_step_batched.argtypes = [vp, ctypes.POINTER(AdamTable), i32, i32, ctypes.POINTER(AdamCfg)]
     L.sr_set_generation_source.argtypes = [vp, vp]
+    L.sr_eval_grad_batched.argtypes = [vp, ctypes.POINTER(GradProblem), i32]
     L.sr_eval_noalloc.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp, vp, i32, i32, i32, i32, vp, vp]
     for name in EXPORTS:
         if name not in ("sr_status_string", "sr_last_error", "sr_kernel_launches"):
@@ -453,6 +472,41 @@ def sr_eval_grad(ctx: Context, programs, lengths, consts, X, y, N: int, mse=None
     return mse, dconst
 
 
+def make_grad_problem(programs, lengths, consts, X, y, N: int, mse=None, dconst=None, prog_flags=None):
+    """An sr_grad_problem over torch tensors; returns (struct, tensors kept
+    alive: programs, lengths, consts, X, y, mse, dconst, prog_flags)."""
+    if consts is None or consts.dim() != 2 or consts.shape[1] < 1:
+        raise ValueError("consts must be [P, K] with K >= 1")
+    P, Lmax, K, nvars, ldx = _shape_check(programs, lengths, consts, X, N, y)
+    _need(mse, P, "mse")
+    _need(dconst, P * K, "dconst")
+    _need(prog_flags, P, "prog_flags")
+    _dev(programs, torch.uint8, "programs")
+    _dev(lengths, torch.int32, "lengths")
+    _dev(consts, torch.float32, "consts")
+    _dev(X, torch.float32, "X")
+    _dev(y, torch.float32, "y")
+    if mse is None:
+        mse = torch.empty(P, dtype=torch.float64, device=programs.device)
+    if dconst is None:
+        dconst = torch.empty((P, K), dtype=torch.float64, device=programs.device)
+    _dev(mse, torch.float64, "mse")
+    _dev(dconst, torch.float64, "dconst")
+    if prog_flags is not None:
+        _dev(prog_flags, torch.int32, "prog_flags")
+    pr = GradProblem(programs.data_ptr(), lengths.data_ptr(), consts.data_ptr(), P, Lmax, K, X.data_ptr(),
+                     y.data_ptr(), nvars, N, ldx, mse.data_ptr(), dconst.data_ptr(),
+                     prog_flags.data_ptr() if prog_flags is not None else None)
+    return pr, (programs, lengths, consts, X, y, mse, dconst, prog_flags)
+
+
+def sr_eval_grad_batched(ctx: Context, problems):
+    """problems: list of make_grad_problem results; returns [(mse, dconst)]."""
+    arr = (GradProblem * len(problems))(*[p[0] for p in problems])
+    _check(ctx, lib().sr_eval_grad_batched(ctx.handle, arr, len(problems)))
+    return [(p[1][5], p[1][6]) for p in problems]
+
+
 def sr_adam_step(ctx: Context, consts, grad, m, v, t: int, cfg: AdamCfg):
     """In-place Adam update of consts (float32) with float64 grad / moments."""
     for buf, name in ((grad, "grad"), (m, "m"), (v, "v")):
@@ -465,8 +519,29 @@ def sr_adam_step(ctx: Context, consts, grad, m, v, t: int, cfg: AdamCfg):
                                    consts.numel(), t, ctypes.byref(cfg)))
 
 
+def sr_adam_step_batched(ctx: Context, tables, t: int, cfg: AdamCfg):
+    """sr_adam_step on many (consts, grad, m, v) tables at once (float32
+    consts, float64 grad / moments of the same element count each)."""
+    arr = []
+    for consts, grad, m, v in tables:
+        for buf, name in ((grad, "grad"), (m, "m"), (v, "v")):
+            _need(buf, consts.numel(), name)
+        _dev(consts, torch.float32, "consts")
+        for buf, name in ((grad, "grad"), (m, "m"), (v, "v")):
+            _dev(buf, torch.float64, name)
+        arr.append(AdamTable(consts.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(), consts.numel()))
+    carr = (AdamTable * len(arr))(*arr)
+    _check(ctx, lib().sr_adam_step_batched(ctx.handle, carr, len(arr), t, ctypes.byref(cfg)))
+
+
 def sr_set_tile(ctx: Context, cases_per_tile: int):
     _check(ctx, lib().sr_set_tile(ctx.handle, cases_per_tile))
+
+
+def sr_set_occupancy(ctx: Context, eval_ctas_per_sm: int = 0, batched_ctas_per_sm: int = 0):
+    """CTAs per SM of the single-problem (0, 4, 5) and batched (0, 3, 4, 5)
+    evaluation kernels; 0 = automatic."""
+    _check(ctx, lib().sr_set_occupancy(ctx.handle, eval_ctas_per_sm, batched_ctas_per_sm))
 
 
 def make_problem(programs, lengths, consts, X, y, N: int, kind: int, fitness=None, prog_flags=None,

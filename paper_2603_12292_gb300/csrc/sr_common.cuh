@@ -19,6 +19,8 @@ struct sr_ctx {
   char msg[512] = {0};
   uint64_t launches = 0;  // kernels launched by this context
   int tile_cases = 0;     // cases per evaluation work item (0: automatic)
+  int eval_ctas = 0;      // CTAs per SM of the single-problem evaluation (0: automatic, 4, 5)
+  int batched_ctas = 0;   // CTAs per SM of the batched evaluation (0: automatic = 4, 3, 4, 5)
   const uint64_t *gen_dev = nullptr;  // device generation counter for selection / variation
   const int32_t *abort_flag = nullptr;  // sr_set_abort_flag (device, or NULL)
 };

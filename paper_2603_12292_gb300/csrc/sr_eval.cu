@@ -58,7 +58,9 @@ constexpr int TARGET_ITEMS_PER_WARP = 16;  // balances the launch tail; measured
 // (Lmax 128): 5 CTAs with 4 stack slots 2,579 -> 2,649 GPop/s, Table 1
 // operators 1,432 -> 1,592; at Lmax 256 the 48-register bound costs more than
 // it gives (2,810 -> 2,625), so there it stays at 4 CTAs.
-__host__ __device__ constexpr int smem_target(int minb) { return minb == 5 ? 45568 : 57344; }
+// (228 KB / MINB - 1 KB, rounded down to 512 bytes: 3 -> 76,800, 4 -> 57,344,
+// 5 -> 45,568)
+__host__ __device__ constexpr int smem_target(int minb) { return (233472 / minb - 1024) / 512 * 512; }
 
 enum Mode { MODE_PREDICT = 0, MODE_MSE = 1, MODE_CORR = 2, MODE_BOTH = 3, MODE_R4 = 4, MODE_P2P = 5 };
 
@@ -117,6 +119,13 @@ __host__ __device__ inline int shallow_slots(int Lmax, int minb) {
 // (Lmax <= 200), else 4.
 inline int minb_for(int Lmax) {
   return WARPS * warp_smem_bytes(shallow_slots(Lmax, 5), Lmax) <= smem_target(5) ? 5 : 4;
+}
+// The evaluation's CTAs per SM: the tuned choice where it fits, else the
+// automatic one
+inline int eval_minb(int Lmax, int tuned) {
+  if (tuned == 5) return minb_for(Lmax);
+  if (tuned == 4) return 4;
+  return minb_for(Lmax);
 }
 
 // ---------------------------------------------------------------- operators
@@ -702,8 +711,8 @@ __global__ void decode_batched_kernel(const __grid_constant__ BatchParams b) {
 // in a second launch, the deep ones in a third).
 // At most 64 registers, so that 4 CTAs fit an SM (75 unbounded, 3 CTAs):
 // 2,608 -> 2,949 GPop/s on the 64-problem batch despite a few spilled values.
-template <bool EXT>
-__global__ void __launch_bounds__(WARPS * 32, 4) eval_batched_kernel(const __grid_constant__ BatchParams b) {
+template <bool EXT, int MINB>
+__global__ void __launch_bounds__(WARPS * 32, MINB) eval_batched_kernel(const __grid_constant__ BatchParams b) {
   extern __shared__ __align__(16) unsigned char smem[];
   const bool deep = EXT && b.deep;
   if (deep ? b.queue[4] == 0 : (EXT && b.queue[2] == 0)) return;
@@ -1080,7 +1089,7 @@ struct Plan {
 };
 
 sr_status make_plan(sr_ctx *ctx, int mode, int P, int Lmax, int N, Plan *pl) {
-  pl->minb = minb_for(Lmax);
+  pl->minb = eval_minb(Lmax, ctx->eval_ctas);
   pl->slots = shallow_slots(Lmax, pl->minb);
   pl->smem = WARPS * warp_smem_bytes(pl->slots, Lmax);
   pl->smem_deep = slots_for(Lmax) > pl->slots ? WARPS * warp_smem_bytes(slots_for(Lmax), Lmax) : 0;
@@ -1226,16 +1235,29 @@ sr_status launch_eval(sr_ctx *ctx, int mode, const uint8_t *programs, const int3
 }
 
 // ---------------------------------------------------------------- batched host side
-template <bool EXT>
-sr_status batched_grid(sr_ctx *ctx, int smem, int *grid) {
-  sr_status st = allow_dynamic_smem(ctx, reinterpret_cast<const void *>(eval_batched_kernel<EXT>));
+template <bool EXT, int MINB>
+sr_status batched_grid_m(sr_ctx *ctx, int smem, int *grid) {
+  sr_status st = allow_dynamic_smem(ctx, reinterpret_cast<const void *>(eval_batched_kernel<EXT, MINB>));
   if (st != SR_OK) return st;
   int nb = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_batched_kernel<EXT>, WARPS * 32, smem);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_batched_kernel<EXT, MINB>, WARPS * 32, smem);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   if (nb < 1) return fail(ctx, SR_EINVAL, "Lmax too large for shared memory");
   *grid = nb * ctx->num_sms;
   return SR_OK;
+}
+
+template <bool EXT>
+sr_status batched_grid(sr_ctx *ctx, int minb, int smem, int *grid) {
+  return minb == 3 ? batched_grid_m<EXT, 3>(ctx, smem, grid)
+                   : (minb == 5 ? batched_grid_m<EXT, 5>(ctx, smem, grid) : batched_grid_m<EXT, 4>(ctx, smem, grid));
+}
+
+template <bool EXT>
+void launch_batched_kernel(int minb, int grid, int smem, cudaStream_t s, const BatchParams &b) {
+  if (minb == 3) eval_batched_kernel<EXT, 3><<<grid, WARPS * 32, smem, s>>>(b);
+  else if (minb == 5) eval_batched_kernel<EXT, 5><<<grid, WARPS * 32, smem, s>>>(b);
+  else eval_batched_kernel<EXT, 4><<<grid, WARPS * 32, smem, s>>>(b);
 }
 
 sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
@@ -1255,16 +1277,21 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
     maxL = q.Lmax > maxL ? q.Lmax : maxL;
     work += (double)q.P * (double)q.N;
   }
-  const int bslots = shallow_slots(maxL, 4);  // eval_batched_kernel: 4 CTAs per SM
+  // CTAs per SM of the main passes: 4 unless tuned (3 gives more stack slots
+  // and registers, 5 more warps); it must leave room for min(slots_for, 4)
+  // stack slots
+  int bminb = ctx->batched_ctas ? ctx->batched_ctas : 4;
+  if (bminb == 5 && WARPS * warp_smem_bytes(shallow_slots(maxL, 5), maxL) > smem_target(5)) bminb = 4;
+  const int bslots = shallow_slots(maxL, bminb);
   const int smem = WARPS * warp_smem_bytes(bslots, maxL);
   const int smem_deep = slots_for(maxL) > bslots ? WARPS * warp_smem_bytes(slots_for(maxL), maxL) : 0;
   int grid = 0, grid_ext = 0, grid_deep = 0;
-  sr_status st = batched_grid<false>(ctx, smem, &grid);
+  sr_status st = batched_grid<false>(ctx, bminb, smem, &grid);
   if (st != SR_OK) return st;
-  st = batched_grid<true>(ctx, smem, &grid_ext);
+  st = batched_grid<true>(ctx, bminb, smem, &grid_ext);
   if (st != SR_OK) return st;
   if (smem_deep) {
-    st = batched_grid<true>(ctx, smem_deep, &grid_deep);
+    st = batched_grid<true>(ctx, 4, smem_deep, &grid_deep);
     if (st != SR_OK) return st;
   }
   const long long warps = (long long)grid * WARPS;
@@ -1399,15 +1426,15 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
       ycenter_batched_kernel<<<corr_blocks, PREP_THREADS, 0, s>>>(b);
       ctx->launches += 2;
     }
-    eval_batched_kernel<false><<<grid, WARPS * 32, smem, s>>>(b);
-    eval_batched_kernel<true><<<grid_ext, WARPS * 32, smem, s>>>(b);
+    launch_batched_kernel<false>(bminb, grid, smem, s, b);
+    launch_batched_kernel<true>(bminb, grid_ext, smem, s, b);
     ctx->launches += 2;
     if (smem_deep) {
       BatchParams bd = b;
       bd.deep = 1;
       bd.slots = slots_for(maxL);
       bd.warp_bytes = warp_smem_bytes(bd.slots, maxL);
-      eval_batched_kernel<true><<<grid_deep, WARPS * 32, smem_deep, s>>>(bd);
+      launch_batched_kernel<true>(4, grid_deep, smem_deep, s, bd);
       ctx->launches += 1;
     }
     int maxP = 1;
@@ -1482,6 +1509,17 @@ sr_status sr_eval_batched(sr_ctx *ctx, const sr_problem *problems, int nprob) {
 sr_status sr_set_tile(sr_ctx *ctx, int cases_per_tile) {
   if (!ctx || cases_per_tile < 0) return SR_EINVAL;
   ctx->tile_cases = cases_per_tile;
+  return SR_OK;
+}
+
+sr_status sr_set_occupancy(sr_ctx *ctx, int eval_ctas_per_sm, int batched_ctas_per_sm) {
+  if (!ctx) return SR_EINVAL;
+  if (eval_ctas_per_sm != 0 && eval_ctas_per_sm != 4 && eval_ctas_per_sm != 5)
+    return sr::fail(ctx, SR_EINVAL, "eval_ctas_per_sm %d: 0, 4 or 5", eval_ctas_per_sm);
+  if (batched_ctas_per_sm != 0 && (batched_ctas_per_sm < 3 || batched_ctas_per_sm > 5))
+    return sr::fail(ctx, SR_EINVAL, "batched_ctas_per_sm %d: 0, 3, 4 or 5", batched_ctas_per_sm);
+  ctx->eval_ctas = eval_ctas_per_sm;
+  ctx->batched_ctas = batched_ctas_per_sm;
   return SR_OK;
 }
 

@@ -29,6 +29,12 @@
 // cases, FP64 across lanes (shuffles) and chunks (fixed-order finalize).
 #include <math.h>
 
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
 #include "sr_common.cuh"
 #include "sr_interp.cuh"
 
@@ -333,189 +339,262 @@ __device__ __forceinline__ VG ldxg(const float *xr, uint32_t off) {
   return r;
 }
 
+// One work item: program `prog` on case chunk `c` with the calling warp.
+// w's shared regions are laid out for the largest Lmax and K of the launch
+// (at least p's).
+template <bool ONCHIP>
+__device__ __forceinline__ void grad_item(const GradParams &p, int c, int prog, const GradWarp &w, int lane) {
+  if (p.flags[prog]) return;
+  const int n = ncode_count(p.ncode[prog]);
+  __syncwarp();
+  const uint2 *src = p.code + (size_t)prog * p.Lmax;
+  for (int i = lane; i < n; i += 32) w.code[i] = src[i];
+  for (int k = 0; k < p.K; ++k) {
+    w.gs[k * 32 + lane] = 0.f;
+    w.gc[k * 32 + lane] = 0.f;
+  }
+  __syncwarp();
+
+  const int cbeg = c * p.chunk, cend = min(p.N, cbeg + p.chunk);
+  const int last_group = (cend - 1) & ~(GCPL - 1);
+  Kahan se;
+  for (int base = cbeg; base < cend; base += GSTEP) {
+    const int c0 = base + GCPL * lane;
+    unsigned okm = 0;  // bit i: case c0 + i is inside the chunk
+#pragma unroll
+    for (int i = 0; i < GCPL; ++i) okm |= (c0 + i < cend ? 1u : 0u) << i;
+    const float *xr = p.X + (okm ? c0 : last_group);
+    int tp = 0;
+    auto push = [&](VG v) { *tape_at<ONCHIP>(w, tp++) = v; };
+    auto pop = [&]() { return *tape_at<ONCHIP>(w, --tp); };
+    // ---- forward
+    VG T = splatg(0.f);
+    for (int ip = 0; ip < n; ++ip) {
+      const uint2 ins = w.code[ip];
+      const uint32_t off = ins_off(ins);
+      const float cv = __uint_as_float(ins.y);
+      switch (ins_op(ins)) {
+        case OP_LDV: T = ldxg(xr, ins.y); break;
+        case OP_LDC: T = splatg(cv); break;
+        case OP_PUSHV: *slot_at(w, off) = T; T = ldxg(xr, ins.y); break;
+        case OP_PUSHC: *slot_at(w, off) = T; T = splatg(cv); break;
+        case OP_ADD: { const VG a = *slot_at(w, off); T = addg(a, T); } break;
+        case OP_SUB: { const VG a = *slot_at(w, off); T = subg(a, T); } break;
+        case OP_RSUB: { const VG b = *slot_at(w, off); T = subg(T, b); } break;
+        case OP_MUL: { const VG a = *slot_at(w, off); push(a); push(T); T = mulg(a, T); } break;
+        case OP_DIV: { const VG a = *slot_at(w, off); push(T); T = pdivg(a, T); push(T); } break;
+        case OP_RDIV: { const VG b = *slot_at(w, off); push(b); T = pdivg(T, b); push(T); } break;
+        case OP_SIN: { const VD r = fwd_sin(T); push(r.d); T = r.v; } break;
+        case OP_COS: { const VD r = fwd_cos(T); push(r.d); T = r.v; } break;
+        case OP_EXP: { const VD r = fwd_exp(T); push(r.d); T = r.v; } break;
+        case OP_LOG: { const VD r = fwd_log(T); push(r.d); T = r.v; } break;
+        case OP_SQRT: { const VD r = fwd_sqrt(T); push(r.d); T = r.v; } break;
+        case OP_SQ: push(addg(T, T)); T = mulg(T, T); break;
+        case OP_INV:
+        case OP_TAN:
+        case OP_ASIN:
+        case OP_ACOS:
+        case OP_ATAN:
+        case OP_TANH: { const VD r = fwd_ext(ins_op(ins), T); push(r.d); T = r.v; } break;
+        case OP_VADD: T = addg(T, ldxg(xr, ins.y)); break;
+        case OP_VSUB: T = subg(T, ldxg(xr, ins.y)); break;
+        case OP_VRSUB: T = subg(ldxg(xr, ins.y), T); break;
+        case OP_VMUL: T = mulg(T, ldxg(xr, ins.y)); break;
+        case OP_VDIV: T = pdivg(T, ldxg(xr, ins.y)); break;
+        case OP_VRDIV: push(T); T = pdivg(ldxg(xr, ins.y), T); push(T); break;
+        case OP_CADD: T = addg(T, splatg(cv)); break;
+        case OP_CSUB: T = subg(T, splatg(cv)); break;
+        case OP_CRSUB: T = subg(splatg(cv), T); break;
+        case OP_CMUL: push(T); T = mulg(T, splatg(cv)); break;
+        case OP_CDIV: T = pdivg(T, splatg(cv)); push(T); break;
+        case OP_CRDIV: push(T); T = pdivg(splatg(cv), T); push(T); break;
+        default: break;
+      }
+    }
+    // ---- loss and seed: e = yhat - y on valid cases, 0 elsewhere
+    VG e;
+    float e2 = 0.0f;
+#pragma unroll
+    for (int i = 0; i < GCPL; ++i) {
+      const bool ok = (okm >> i) & 1u;
+      e.v[i] = ok ? T.v[i] - __ldg(p.y + c0 + i) : 0.0f;
+      e2 += e.v[i] * e.v[i];
+    }
+    se.add(e2);
+    // ---- reverse
+    VG aT = e;
+    for (int ip = n - 1; ip >= 0; --ip) {
+      const uint2 ins = w.code[ip];
+      const uint32_t off = ins_off(ins);
+      const float cv = __uint_as_float(ins.y);
+      const int k = ins_k(ins);
+      switch (ins_op(ins)) {
+        case OP_LDV: break;
+        case OP_LDC: gacc(w, k, aT, okm); break;
+        case OP_PUSHV: aT = *slot_at(w, off); break;
+        case OP_PUSHC: gacc(w, k, aT, okm); aT = *slot_at(w, off); break;
+        case OP_ADD: *slot_at(w, off) = aT; break;
+        case OP_SUB: *slot_at(w, off) = aT; aT = negg(aT); break;
+        case OP_RSUB: *slot_at(w, off) = negg(aT); break;
+        case OP_MUL: {  // T = a t
+          const VG t = pop(), a = pop();
+          *slot_at(w, off) = mulg(aT, t);
+          aT = mulg(aT, a);
+        } break;
+        case OP_DIV: {  // T = a / t: dT/da = 1/t, dT/dt = -T/t
+          const VG Tn = pop(), t = pop();
+          const VG q = qdivg(aT, t);
+          *slot_at(w, off) = q;
+          aT = negg(mulg(q, Tn));
+        } break;
+        case OP_RDIV: {  // T = t / b
+          const VG Tn = pop(), b = pop();
+          const VG q = qdivg(aT, b);
+          *slot_at(w, off) = negg(mulg(q, Tn));
+          aT = q;
+        } break;
+        case OP_SIN:
+        case OP_COS:
+        case OP_EXP:
+        case OP_LOG:
+        case OP_SQRT:
+        case OP_SQ:
+        case OP_INV:
+        case OP_TAN:
+        case OP_ASIN:
+        case OP_ACOS:
+        case OP_ATAN:
+        case OP_TANH: { const VG d = pop(); aT = mulg(aT, d); } break;
+        case OP_VADD:
+        case OP_VSUB: break;
+        case OP_VRSUB: aT = negg(aT); break;
+        case OP_VMUL: aT = mulg(aT, ldxg(xr, ins.y)); break;
+        case OP_VDIV: aT = qdivg(aT, ldxg(xr, ins.y)); break;
+        case OP_VRDIV: {  // T = v / t
+          const VG Tn = pop(), t = pop();
+          aT = negg(mulg(qdivg(aT, t), Tn));
+        } break;
+        case OP_CADD: gacc(w, k, aT, okm); break;
+        case OP_CSUB: gacc(w, k, negg(aT), okm); break;
+        case OP_CRSUB: gacc(w, k, aT, okm); aT = negg(aT); break;
+        case OP_CMUL: {  // T = t c
+          const VG t = pop();
+          gacc(w, k, mulg(aT, t), okm);
+          aT = mulg(aT, splatg(cv));
+        } break;
+        case OP_CDIV: {  // T = t / c: dT/dt = 1/c, dT/dc = -T/c
+          const VG Tn = pop();
+          const VG q = qdivg(aT, splatg(cv));
+          gacc(w, k, negg(mulg(q, Tn)), okm);
+          aT = q;
+        } break;
+        case OP_CRDIV: {  // T = c / t: dT/dc = 1/t, dT/dt = -T/t
+          const VG Tn = pop(), t = pop();
+          const VG q = qdivg(aT, t);
+          gacc(w, k, q, okm);
+          aT = negg(mulg(q, Tn));
+        } break;
+        default: break;
+      }
+    }
+  }
+  double *rec = p.partials + ((size_t)prog * p.nchunks + c) * GSTRIDE;
+  const double sv = warp_sum(se.value());
+  if (lane == 0) rec[0] = sv;
+  __syncwarp();
+  for (int k = 0; k < p.K; ++k) {
+    const double g = warp_sum((double)w.gs[k * 32 + lane] - (double)w.gc[k * 32 + lane]);
+    if (lane == 0) rec[1 + k] = g;
+  }
+}
+
+// Shared memory of a warp, for the largest Lmax (Lw) and K (Kw) of a launch.
+__device__ __forceinline__ GradWarp grad_warp(unsigned char *smem, int warp_bytes, int Lw, int Kw, char *gtape,
+                                              bool onchip) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char *wb = smem + (size_t)warp * warp_bytes;
+  GradWarp w;
+  w.slot = reinterpret_cast<char *>(wb) + lane * (GCPL * 4);
+  const int slot_bytes = slots_for(Lw) * GSLOT;
+  w.gs = reinterpret_cast<float *>(wb + slot_bytes);
+  w.gc = w.gs + Kw * 32;
+  w.code = reinterpret_cast<uint2 *>(wb + slot_bytes + 2 * Kw * 128);
+  w.ts = reinterpret_cast<char *>(wb + grad_fixed_bytes(Lw, Kw)) + lane * (GCPL * 4);
+  const int gw = blockIdx.x * GWARPS + warp;
+  w.tg = onchip ? nullptr : gtape + (size_t)gw * Lw * GSLOT + lane * (GCPL * 4);
+  w.lane = lane;
+  return w;
+}
+
 template <bool ONCHIP>
 __global__ void __launch_bounds__(GWARPS * 32) grad_kernel(GradParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char *wb = smem + (size_t)warp * p.warp_bytes;
-  GradWarp w;
-  w.slot = reinterpret_cast<char *>(wb) + lane * (GCPL * 4);
-  const int slot_bytes = slots_for(p.Lmax) * GSLOT;
-  w.gs = reinterpret_cast<float *>(wb + slot_bytes);
-  w.gc = w.gs + p.K * 32;
-  w.code = reinterpret_cast<uint2 *>(wb + slot_bytes + 2 * p.K * 128);
-  w.ts = reinterpret_cast<char *>(wb + grad_fixed_bytes(p.Lmax, p.K)) + lane * (GCPL * 4);
-  const int gw = blockIdx.x * GWARPS + warp;
-  w.tg = ONCHIP ? nullptr : p.gtape + (size_t)gw * p.Lmax * GSLOT + lane * (GCPL * 4);
-  w.lane = lane;
-
+  const int lane = threadIdx.x & 31;
+  const GradWarp w = grad_warp(smem, p.warp_bytes, p.Lmax, p.K, p.gtape, ONCHIP);
   for (;;) {
     const long long item = next_item(p.queue, p.total_items, p.abort, p.err, lane);
     if (item >= p.total_items) break;
     const int c = (int)(item / (unsigned long long)p.P);
     const int prog = (int)(item % (unsigned long long)p.P);
-    if (p.flags[prog]) continue;
-    const int n = ncode_count(p.ncode[prog]);
-    __syncwarp();
-    const uint2 *src = p.code + (size_t)prog * p.Lmax;
-    for (int i = lane; i < n; i += 32) w.code[i] = src[i];
-    for (int k = 0; k < p.K; ++k) {
-      w.gs[k * 32 + lane] = 0.f;
-      w.gc[k * 32 + lane] = 0.f;
-    }
-    __syncwarp();
+    grad_item<ONCHIP>(p, c, prog, w, lane);
+  }
+}
 
-    const int cbeg = c * p.chunk, cend = min(p.N, cbeg + p.chunk);
-    const int last_group = (cend - 1) & ~(GCPL - 1);
-    Kahan se;
-    for (int base = cbeg; base < cend; base += GSTEP) {
-      const int c0 = base + GCPL * lane;
-      unsigned okm = 0;  // bit i: case c0 + i is inside the chunk
-#pragma unroll
-      for (int i = 0; i < GCPL; ++i) okm |= (c0 + i < cend ? 1u : 0u) << i;
-      const float *xr = p.X + (okm ? c0 : last_group);
-      int tp = 0;
-      auto push = [&](VG v) { *tape_at<ONCHIP>(w, tp++) = v; };
-      auto pop = [&]() { return *tape_at<ONCHIP>(w, --tp); };
-      // ---- forward
-      VG T = splatg(0.f);
-      for (int ip = 0; ip < n; ++ip) {
-        const uint2 ins = w.code[ip];
-        const uint32_t off = ins_off(ins);
-        const float cv = __uint_as_float(ins.y);
-        switch (ins_op(ins)) {
-          case OP_LDV: T = ldxg(xr, ins.y); break;
-          case OP_LDC: T = splatg(cv); break;
-          case OP_PUSHV: *slot_at(w, off) = T; T = ldxg(xr, ins.y); break;
-          case OP_PUSHC: *slot_at(w, off) = T; T = splatg(cv); break;
-          case OP_ADD: { const VG a = *slot_at(w, off); T = addg(a, T); } break;
-          case OP_SUB: { const VG a = *slot_at(w, off); T = subg(a, T); } break;
-          case OP_RSUB: { const VG b = *slot_at(w, off); T = subg(T, b); } break;
-          case OP_MUL: { const VG a = *slot_at(w, off); push(a); push(T); T = mulg(a, T); } break;
-          case OP_DIV: { const VG a = *slot_at(w, off); push(T); T = pdivg(a, T); push(T); } break;
-          case OP_RDIV: { const VG b = *slot_at(w, off); push(b); T = pdivg(T, b); push(T); } break;
-          case OP_SIN: { const VD r = fwd_sin(T); push(r.d); T = r.v; } break;
-          case OP_COS: { const VD r = fwd_cos(T); push(r.d); T = r.v; } break;
-          case OP_EXP: { const VD r = fwd_exp(T); push(r.d); T = r.v; } break;
-          case OP_LOG: { const VD r = fwd_log(T); push(r.d); T = r.v; } break;
-          case OP_SQRT: { const VD r = fwd_sqrt(T); push(r.d); T = r.v; } break;
-          case OP_SQ: push(addg(T, T)); T = mulg(T, T); break;
-          case OP_INV:
-          case OP_TAN:
-          case OP_ASIN:
-          case OP_ACOS:
-          case OP_ATAN:
-          case OP_TANH: { const VD r = fwd_ext(ins_op(ins), T); push(r.d); T = r.v; } break;
-          case OP_VADD: T = addg(T, ldxg(xr, ins.y)); break;
-          case OP_VSUB: T = subg(T, ldxg(xr, ins.y)); break;
-          case OP_VRSUB: T = subg(ldxg(xr, ins.y), T); break;
-          case OP_VMUL: T = mulg(T, ldxg(xr, ins.y)); break;
-          case OP_VDIV: T = pdivg(T, ldxg(xr, ins.y)); break;
-          case OP_VRDIV: push(T); T = pdivg(ldxg(xr, ins.y), T); push(T); break;
-          case OP_CADD: T = addg(T, splatg(cv)); break;
-          case OP_CSUB: T = subg(T, splatg(cv)); break;
-          case OP_CRSUB: T = subg(splatg(cv), T); break;
-          case OP_CMUL: push(T); T = mulg(T, splatg(cv)); break;
-          case OP_CDIV: T = pdivg(T, splatg(cv)); push(T); break;
-          case OP_CRDIV: push(T); T = pdivg(splatg(cv), T); push(T); break;
-          default: break;
-        }
-      }
-      // ---- loss and seed: e = yhat - y on valid cases, 0 elsewhere
-      VG e;
-      float e2 = 0.0f;
-#pragma unroll
-      for (int i = 0; i < GCPL; ++i) {
-        const bool ok = (okm >> i) & 1u;
-        e.v[i] = ok ? T.v[i] - __ldg(p.y + c0 + i) : 0.0f;
-        e2 += e.v[i] * e.v[i];
-      }
-      se.add(e2);
-      // ---- reverse
-      VG aT = e;
-      for (int ip = n - 1; ip >= 0; --ip) {
-        const uint2 ins = w.code[ip];
-        const uint32_t off = ins_off(ins);
-        const float cv = __uint_as_float(ins.y);
-        const int k = ins_k(ins);
-        switch (ins_op(ins)) {
-          case OP_LDV: break;
-          case OP_LDC: gacc(w, k, aT, okm); break;
-          case OP_PUSHV: aT = *slot_at(w, off); break;
-          case OP_PUSHC: gacc(w, k, aT, okm); aT = *slot_at(w, off); break;
-          case OP_ADD: *slot_at(w, off) = aT; break;
-          case OP_SUB: *slot_at(w, off) = aT; aT = negg(aT); break;
-          case OP_RSUB: *slot_at(w, off) = negg(aT); break;
-          case OP_MUL: {  // T = a t
-            const VG t = pop(), a = pop();
-            *slot_at(w, off) = mulg(aT, t);
-            aT = mulg(aT, a);
-          } break;
-          case OP_DIV: {  // T = a / t: dT/da = 1/t, dT/dt = -T/t
-            const VG Tn = pop(), t = pop();
-            const VG q = qdivg(aT, t);
-            *slot_at(w, off) = q;
-            aT = negg(mulg(q, Tn));
-          } break;
-          case OP_RDIV: {  // T = t / b
-            const VG Tn = pop(), b = pop();
-            const VG q = qdivg(aT, b);
-            *slot_at(w, off) = negg(mulg(q, Tn));
-            aT = q;
-          } break;
-          case OP_SIN:
-          case OP_COS:
-          case OP_EXP:
-          case OP_LOG:
-          case OP_SQRT:
-          case OP_SQ:
-          case OP_INV:
-          case OP_TAN:
-          case OP_ASIN:
-          case OP_ACOS:
-          case OP_ATAN:
-          case OP_TANH: { const VG d = pop(); aT = mulg(aT, d); } break;
-          case OP_VADD:
-          case OP_VSUB: break;
-          case OP_VRSUB: aT = negg(aT); break;
-          case OP_VMUL: aT = mulg(aT, ldxg(xr, ins.y)); break;
-          case OP_VDIV: aT = qdivg(aT, ldxg(xr, ins.y)); break;
-          case OP_VRDIV: {  // T = v / t
-            const VG Tn = pop(), t = pop();
-            aT = negg(mulg(qdivg(aT, t), Tn));
-          } break;
-          case OP_CADD: gacc(w, k, aT, okm); break;
-          case OP_CSUB: gacc(w, k, negg(aT), okm); break;
-          case OP_CRSUB: gacc(w, k, aT, okm); aT = negg(aT); break;
-          case OP_CMUL: {  // T = t c
-            const VG t = pop();
-            gacc(w, k, mulg(aT, t), okm);
-            aT = mulg(aT, splatg(cv));
-          } break;
-          case OP_CDIV: {  // T = t / c: dT/dt = 1/c, dT/dc = -T/c
-            const VG Tn = pop();
-            const VG q = qdivg(aT, splatg(cv));
-            gacc(w, k, negg(mulg(q, Tn)), okm);
-            aT = q;
-          } break;
-          case OP_CRDIV: {  // T = c / t: dT/dc = 1/t, dT/dt = -T/t
-            const VG Tn = pop(), t = pop();
-            const VG q = qdivg(aT, t);
-            gacc(w, k, q, okm);
-            aT = negg(mulg(q, Tn));
-          } break;
-          default: break;
-        }
-      }
-    }
-    double *rec = p.partials + ((size_t)prog * p.nchunks + c) * GSTRIDE;
-    const double sv = warp_sum(se.value());
-    if (lane == 0) rec[0] = sv;
-    __syncwarp();
-    for (int k = 0; k < p.K; ++k) {
-      const double g = warp_sum((double)w.gs[k * 32 + lane] - (double)w.gc[k * 32 + lane]);
-      if (lane == 0) rec[1 + k] = g;
-    }
+// ---------------------------------------------------------------- many problems, one launch
+constexpr int MAX_GBATCH = 64;
+
+struct GradBatch {
+  GradParams prob[MAX_GBATCH];    // per problem (queue / tape / abort fields unused)
+  long long item_begin[MAX_GBATCH];  // first work item of each problem
+  int prog_begin[MAX_GBATCH];     // first program of each problem in the decode launch
+  double *mse[MAX_GBATCH];
+  double *dconst[MAX_GBATCH];
+  int nprob, total_progs;
+  long long total_items;
+  unsigned long long *queue;
+  char *gtape;
+  const int32_t *abort;
+  unsigned *err;
+  int warp_bytes, Lw, Kw;         // shared layout: the largest Lmax and K
+};
+
+__device__ __forceinline__ int batch_problem(const long long *begin, int nprob, long long x) {
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (begin[mid] <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// a warp per program of every problem
+__global__ void grad_decode_batched_kernel(const __grid_constant__ GradBatch b) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  const int warp = threadIdx.x >> 5;
+  const int g = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (g >= b.total_progs) return;
+  int q = 0;
+  while (q + 1 < b.nprob && b.prog_begin[q + 1] <= g) ++q;
+  decode_warp_one(grad_decode_args(b.prob[q]), g - b.prog_begin[q],
+                  dsm + (size_t)warp * decode_warp_bytes(b.Lw));
+}
+
+// Work items of every problem from one atomic counter, longest items first
+// (problems ordered by cases per item x Lmax); problem q owns items
+// [item_begin_q, item_begin_q + P_q nchunks_q), chunk-major inside.
+template <bool ONCHIP>
+__global__ void __launch_bounds__(GWARPS * 32) grad_batched_kernel(const __grid_constant__ GradBatch b) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31;
+  const GradWarp w = grad_warp(smem, b.warp_bytes, b.Lw, b.Kw, b.gtape, ONCHIP);
+  for (;;) {
+    const long long item = next_item(b.queue, b.total_items, b.abort, b.err, lane);
+    if (item >= b.total_items) break;
+    const int q = batch_problem(b.item_begin, b.nprob, item);
+    const GradParams &p = b.prob[q];
+    const long long local = item - b.item_begin[q];
+    grad_item<ONCHIP>(p, (int)(local / p.P), (int)(local % p.P), w, lane);
   }
 }
 
@@ -526,9 +605,7 @@ struct GradFinal {
   double *mse, *dconst;
 };
 
-__global__ void grad_finalize_kernel(GradFinal f) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= f.P) return;
+__device__ void finalize_grad_one(const GradFinal &f, int p) {
   if (f.flags[p]) {
     f.mse[p] = __longlong_as_double(0x7ff0000000000000ll);
     for (int k = 0; k < f.K; ++k) f.dconst[(size_t)p * f.K + k] = 0.0;
@@ -545,13 +622,16 @@ __global__ void grad_finalize_kernel(GradFinal f) {
   }
 }
 
+__global__ void grad_finalize_kernel(GradFinal f) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < f.P) finalize_grad_one(f, p);
+}
+
 // Adam, FP64 moments, every operation rounded on its own in the written order
-__global__ void adam_kernel(float *c, const double *__restrict__ g, double *m, double *v, int n,
-                            double lr, double b1, double b2, double eps, double bc1, double bc2) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+__device__ __forceinline__ void adam_one(float *c, const double *__restrict__ g, double *m, double *v, int i,
+                                         double lr, double b1, double b2, double eps, double bc1, double bc2) {
   const double gi = g[i];
-  if (!isfinite(gi)) return;
+  if (!isfinite(gi)) return;  // leaves c, m, v unchanged
   const double mi = __dadd_rn(__dmul_rn(b1, m[i]), __dmul_rn(__dsub_rn(1.0, b1), gi));
   const double vi = __dadd_rn(__dmul_rn(b2, v[i]), __dmul_rn(__dmul_rn(__dsub_rn(1.0, b2), gi), gi));
   m[i] = mi;
@@ -559,6 +639,119 @@ __global__ void adam_kernel(float *c, const double *__restrict__ g, double *m, d
   const double mh = __ddiv_rn(mi, bc1), vh = __ddiv_rn(vi, bc2);
   const double step = __ddiv_rn(__dmul_rn(lr, mh), __dadd_rn(__dsqrt_rn(vh), eps));
   c[i] = __double2float_rn(__dsub_rn((double)c[i], step));
+}
+
+__global__ void adam_kernel(float *c, const double *__restrict__ g, double *m, double *v, int n,
+                            double lr, double b1, double b2, double eps, double bc1, double bc2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) adam_one(c, g, m, v, i, lr, b1, b2, eps, bc1, bc2);
+}
+
+// Adam of many constant tables in one launch: blocks (table, 256 entries)
+constexpr int MAX_ABATCH = 64;
+struct AdamBatch {
+  float *c[MAX_ABATCH];
+  const double *g[MAX_ABATCH];
+  double *m[MAX_ABATCH];
+  double *v[MAX_ABATCH];
+  int n[MAX_ABATCH];
+  int count;
+  double lr, b1, b2, eps, bc1, bc2;
+};
+
+__global__ void adam_batched_kernel(const __grid_constant__ AdamBatch a) {
+  const int q = blockIdx.x;
+  for (int i = blockIdx.y * blockDim.x + threadIdx.x; i < a.n[q]; i += gridDim.y * blockDim.x)
+    adam_one(a.c[q], a.g[q], a.m[q], a.v[q], i, a.lr, a.b1, a.b2, a.eps, a.bc1, a.bc2);
+}
+
+// blocks (problem, 256 programs of it), a thread per program
+__global__ void grad_finalize_batched_kernel(const __grid_constant__ GradBatch b) {
+  const GradParams &q = b.prob[blockIdx.x];
+  for (int p = blockIdx.y * blockDim.x + threadIdx.x; p < q.P; p += gridDim.y * blockDim.x) {
+    GradFinal f{q.partials, q.flags, q.P, q.N, q.K, q.nchunks, b.mse[blockIdx.x], b.dconst[blockIdx.x]};
+    finalize_grad_one(f, p);
+  }
+}
+
+// ---------------------------------------------------------------- host side
+// Launch shape of the gradient kernels for the largest Lmax and K of a
+// launch: whether the tape fits a warp's share of shared memory, the bytes
+// per warp and per block, and the persistent grid.
+struct GradShape {
+  bool onchip;
+  int warp_bytes, smem, grid;
+};
+
+sr_status grad_shape_uncached(sr_ctx *ctx, int Lw, int Kw, bool batched, GradShape *g) {
+  int sm_bytes = 0, blk_max = 0, blk_reserved = 0;
+  SR_CHECK_CUDA(ctx, cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device));
+  SR_CHECK_CUDA(ctx, cudaDeviceGetAttribute(&blk_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+  SR_CHECK_CUDA(ctx, cudaDeviceGetAttribute(&blk_reserved, cudaDevAttrReservedSharedMemoryPerBlock, ctx->device));
+  // tape entries in shared memory: what is left of a warp's share when
+  // GCTAS_PER_SM blocks fill the SM
+  const int fixed = grad_fixed_bytes(Lw, Kw);
+  const int budget = (sm_bytes / GCTAS_PER_SM - blk_reserved) / GWARPS;
+  g->onchip = fixed + Lw * GSLOT <= budget;  // a whole tape fits a warp's share
+  g->warp_bytes = fixed + (g->onchip ? Lw * GSLOT : 0);
+  g->smem = GWARPS * g->warp_bytes;
+  if (g->smem > blk_max) return fail(ctx, SR_EINVAL, "Lmax %d, K %d too large for the gradient kernel", Lw, Kw);
+  const void *kern = batched ? (g->onchip ? reinterpret_cast<const void *>(grad_batched_kernel<true>)
+                                          : reinterpret_cast<const void *>(grad_batched_kernel<false>))
+                             : (g->onchip ? reinterpret_cast<const void *>(grad_kernel<true>)
+                                          : reinterpret_cast<const void *>(grad_kernel<false>));
+  sr_status st = allow_dynamic_smem(ctx, kern);  // once per (kernel, device): every shape fits
+  if (st != SR_OK) return st;
+  int nb = 0;
+  SR_CHECK_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, GWARPS * 32, g->smem));
+  if (nb < 1) return fail(ctx, SR_EINVAL, "Lmax %d, K %d too large for the gradient kernel", Lw, Kw);
+  g->grid = nb * ctx->num_sms;
+  return SR_OK;
+}
+
+// grad_shape_uncached, remembered per (device, Lmax, K, kernel): the batched
+// call asks it for every problem of a batch
+sr_status grad_shape(sr_ctx *ctx, int Lw, int Kw, bool batched, GradShape *g) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int, int>, std::pair<GradShape, int>> memo;
+  const auto key = std::make_tuple(ctx->device, Lw, Kw, batched ? 1 : 0);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = memo.find(key);
+    if (it != memo.end()) {
+      *g = it->second.first;
+      g->grid = it->second.second * ctx->num_sms;  // blocks per SM x this context's SM count
+      return SR_OK;
+    }
+  }
+  sr_status st = grad_shape_uncached(ctx, Lw, Kw, batched, g);
+  if (st != SR_OK) return st;
+  std::lock_guard<std::mutex> lock(mu);
+  memo[key] = std::make_pair(*g, g->grid / ctx->num_sms);
+  return SR_OK;
+}
+
+// cases per work item: about `items` items of this problem, at least one
+// 1,024-case block each
+int grad_chunk(int N, double items_wanted, int P) {
+  int nch = (int)ceil(items_wanted / (P > 0 ? P : 1));
+  const int max_chunks = (N + 1023) / 1024;
+  nch = nch < 1 ? 1 : (nch > max_chunks ? max_chunks : nch);
+  int chunk = (N + nch - 1) / nch;
+  return (chunk + GSTEP - 1) / GSTEP * GSTEP;
+}
+
+sr_status check_grad(sr_ctx *ctx, const uint8_t *programs, const int32_t *lengths, const float *consts, int P,
+                     int Lmax, int K, const float *X, const float *y, int nvars, int N, int ldx, const double *mse,
+                     const double *dconst) {
+  if (P < 0 || Lmax < 1 || Lmax > SR_MAX_LMAX || K < 1 || K > SR_MAX_CONSTS || nvars < 1 ||
+      nvars > SR_MAX_VARS || N < 1 || ldx < N || ldx % 4 || (long long)ldx * nvars > 0xFFFFFFFFll)
+    return fail(ctx, SR_EINVAL, "bad sr_eval_grad shape");
+  if (P == 0) return SR_OK;
+  if (!programs || !lengths || !consts || !X || !y || !mse || !dconst)
+    return fail(ctx, SR_EINVAL, "NULL pointer");
+  if (((uintptr_t)X) & 15) return fail(ctx, SR_EINVAL, "X must be 16-byte aligned");
+  return SR_OK;
 }
 
 }  // namespace
@@ -571,39 +764,14 @@ sr_status sr_eval_grad(sr_ctx *ctx, const uint8_t *programs, const int32_t *leng
                        int nvars, int N, int ldx, double *mse, double *dconst, int32_t *prog_flags) {
   using namespace sr;
   if (!ctx) return SR_EINVAL;
-  if (P < 0 || Lmax < 1 || Lmax > SR_MAX_LMAX || K < 1 || K > SR_MAX_CONSTS || nvars < 1 ||
-      nvars > SR_MAX_VARS || N < 1 || ldx < N || ldx % 4 || (long long)ldx * nvars > 0xFFFFFFFFll)
-    return fail(ctx, SR_EINVAL, "bad sr_eval_grad shape");
-  if (P == 0) return SR_OK;
-  if (!programs || !lengths || !consts || !X || !y || !mse || !dconst)
-    return fail(ctx, SR_EINVAL, "NULL pointer");
-  if (((uintptr_t)X) & 15) return fail(ctx, SR_EINVAL, "X must be 16-byte aligned");
+  sr_status st = check_grad(ctx, programs, lengths, consts, P, Lmax, K, X, y, nvars, N, ldx, mse, dconst);
+  if (st != SR_OK || P == 0) return st;
   SR_CHECK_CUDA(ctx, cudaSetDevice(ctx->device));
-  // tape entries in shared memory: what is left of a warp's share when
-  // GCTAS_PER_SM blocks fill the SM
-  int sm_bytes = 0, blk_max = 0, blk_reserved = 0;
-  SR_CHECK_CUDA(ctx, cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device));
-  SR_CHECK_CUDA(ctx, cudaDeviceGetAttribute(&blk_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
-  SR_CHECK_CUDA(ctx, cudaDeviceGetAttribute(&blk_reserved, cudaDevAttrReservedSharedMemoryPerBlock, ctx->device));
-  const int fixed = grad_fixed_bytes(Lmax, K);
-  const int budget = (sm_bytes / GCTAS_PER_SM - blk_reserved) / GWARPS;
-  const bool onchip = fixed + Lmax * GSLOT <= budget;  // a whole tape fits a warp's share
-  const int warp_bytes = fixed + (onchip ? Lmax * GSLOT : 0);
-  const int smem = GWARPS * warp_bytes;
-  if (smem > blk_max) return fail(ctx, SR_EINVAL, "Lmax %d, K %d too large for the gradient kernel", Lmax, K);
-  const void *kern = onchip ? reinterpret_cast<const void *>(grad_kernel<true>)
-                            : reinterpret_cast<const void *>(grad_kernel<false>);
-  SR_CHECK_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  int nb = 0;
-  SR_CHECK_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, GWARPS * 32, smem));
-  if (nb < 1) return fail(ctx, SR_EINVAL, "Lmax %d, K %d too large for the gradient kernel", Lmax, K);
-  const int grid = nb * ctx->num_sms;
-  const long long warps = (long long)grid * GWARPS;
-  int nch = (int)((warps * GTARGET_ITEMS_PER_WARP + P - 1) / P);
-  const int max_chunks = (N + 1023) / 1024;
-  nch = nch < 1 ? 1 : (nch > max_chunks ? max_chunks : nch);
-  int chunk = (N + nch - 1) / nch;
-  chunk = (chunk + GSTEP - 1) / GSTEP * GSTEP;
+  GradShape gs;
+  st = grad_shape(ctx, Lmax, K, false, &gs);
+  if (st != SR_OK) return st;
+  const long long warps = (long long)gs.grid * GWARPS;
+  const int chunk = grad_chunk(N, (double)warps * GTARGET_ITEMS_PER_WARP, P);
   const int nchunks = (N + chunk - 1) / chunk;
   const long long items = (long long)P * nchunks;
   const size_t tokens = (size_t)P * Lmax;
@@ -611,8 +779,8 @@ sr_status sr_eval_grad(sr_ctx *ctx, const uint8_t *programs, const int32_t *leng
   const size_t off_q = cv.take(256), off_f = cv.take((size_t)P * 4), off_nc = cv.take((size_t)P * 4),
                off_code = cv.take(tokens * 8),
                off_p = cv.take((size_t)items * GSTRIDE * 8),
-               off_t = cv.take(onchip ? 0 : (size_t)warps * Lmax * GSLOT);
-  sr_status st = ensure_workspace(ctx, cv.off);
+               off_t = cv.take(gs.onchip ? 0 : (size_t)warps * Lmax * GSLOT);
+  st = ensure_workspace(ctx, cv.off);
   if (st != SR_OK) return st;
   char *ws = ctx->ws;
   GradParams gp;
@@ -638,23 +806,151 @@ sr_status sr_eval_grad(sr_ctx *ctx, const uint8_t *programs, const int32_t *leng
   gp.s_need = nullptr;
   gp.s_task = nullptr;
   gp.queue = reinterpret_cast<unsigned long long *>(ws + off_q);
-  gp.gtape = onchip ? nullptr : ws + off_t;
+  gp.gtape = gs.onchip ? nullptr : ws + off_t;
   gp.abort = ctx->abort_flag;
   gp.err = ctx->dev_words;
-  gp.warp_bytes = warp_bytes;
+  gp.warp_bytes = gs.warp_bytes;
   cudaStream_t s = ctx->stream;
   SR_CHECK_CUDA(ctx, cudaMemsetAsync(gp.queue, 0, 8, s));
   st = allow_dynamic_smem(ctx, reinterpret_cast<const void *>(grad_decode_kernel));
   if (st != SR_OK) return st;
   grad_decode_kernel<<<(P + DECODE_WARPS - 1) / DECODE_WARPS, DECODE_WARPS * 32,
                        DECODE_WARPS * decode_warp_bytes(Lmax), s>>>(gp);
-  if (onchip) grad_kernel<true><<<grid, GWARPS * 32, smem, s>>>(gp);
-  else grad_kernel<false><<<grid, GWARPS * 32, smem, s>>>(gp);
+  if (gs.onchip) grad_kernel<true><<<gs.grid, GWARPS * 32, gs.smem, s>>>(gp);
+  else grad_kernel<false><<<gs.grid, GWARPS * 32, gs.smem, s>>>(gp);
   SR_CHECK_CUDA(ctx, cudaGetLastError());
   GradFinal gf{gp.partials, gp.flags, P, N, K, nchunks, mse, dconst};
   grad_finalize_kernel<<<(P + 255) / 256, 256, 0, s>>>(gf);
   SR_CHECK_CUDA(ctx, cudaGetLastError());
   ctx->launches += 3;
+  return SR_OK;
+}
+
+sr_status sr_eval_grad_batched(sr_ctx *ctx, const sr_grad_problem *pr, int nprob) {
+  using namespace sr;
+  if (!ctx) return SR_EINVAL;
+  if (nprob < 0 || (nprob > 0 && !pr)) return fail(ctx, SR_EINVAL, "bad problem list");
+  int Lw = 1, Kw = 1;
+  for (int i = 0; i < nprob; ++i) {
+    const sr_grad_problem &q = pr[i];
+    sr_status st = check_grad(ctx, q.programs, q.lengths, q.consts, q.P, q.Lmax, q.K, q.X, q.y, q.nvars, q.N,
+                              q.ldx, q.mse, q.dconst);
+    if (st != SR_OK) return fail(ctx, st, "problem %d: %s", i, ctx->msg);
+    if (q.P == 0) continue;
+    Lw = q.Lmax > Lw ? q.Lmax : Lw;
+    Kw = q.K > Kw ? q.K : Kw;
+  }
+  std::vector<int> order;
+  for (int i = 0; i < nprob; ++i)
+    if (pr[i].P > 0) order.push_back(i);
+  if (order.empty()) return SR_OK;
+  SR_CHECK_CUDA(ctx, cudaSetDevice(ctx->device));
+  GradShape gs;
+  sr_status st = grad_shape(ctx, Lw, Kw, true, &gs);
+  if (st != SR_OK) return st;
+  const long long warps = (long long)gs.grid * GWARPS;
+  // cases per item per problem: the chunking sr_eval_grad would choose for
+  // the problem alone (so every problem's sums, and its results, are the
+  // same bits as its own call's); the batch shares one grid and one tail
+  std::vector<int> chunk(nprob, 0), nch(nprob, 0);
+  for (int i : order) {
+    const sr_grad_problem &q = pr[i];
+    GradShape alone;
+    st = grad_shape(ctx, q.Lmax, q.K, false, &alone);
+    if (st != SR_OK) return st;
+    chunk[i] = grad_chunk(q.N, (double)alone.grid * GWARPS * GTARGET_ITEMS_PER_WARP, q.P);
+    nch[i] = (q.N + chunk[i] - 1) / chunk[i];
+  }
+  // longest items first: the launch's tail is made of short items
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return (double)chunk[a] * pr[a].Lmax > (double)chunk[b] * pr[b].Lmax;
+  });
+  auto group_bytes = [&](size_t g0, size_t g1, GradBatch *b) -> size_t {
+    Carver cv;
+    const size_t off_q = cv.take(256);
+    const size_t off_t = cv.take(gs.onchip ? 0 : (size_t)warps * Lw * GSLOT);
+    long long items = 0;
+    int progs = 0;
+    for (size_t g = g0; g < g1; ++g) {
+      const int i = order[g];
+      const sr_grad_problem &q = pr[i];
+      const size_t off_f = q.prog_flags ? 0 : cv.take((size_t)q.P * 4);
+      const size_t off_nc = cv.take((size_t)q.P * 4);
+      const size_t off_code = cv.take((size_t)q.P * q.Lmax * 8);
+      const size_t off_p = cv.take((size_t)q.P * nch[i] * GSTRIDE * 8);
+      if (b) {
+        char *ws = ctx->ws;
+        GradParams &p = b->prob[g - g0];
+        p.programs = q.programs;
+        p.lengths = q.lengths;
+        p.consts = q.consts;
+        p.P = q.P;
+        p.Lmax = q.Lmax;
+        p.K = q.K;
+        p.X = q.X;
+        p.y = q.y;
+        p.nvars = q.nvars;
+        p.N = q.N;
+        p.ldx = q.ldx;
+        p.chunk = chunk[i];
+        p.nchunks = nch[i];
+        p.total_items = (long long)q.P * nch[i];
+        p.partials = reinterpret_cast<double *>(ws + off_p);
+        p.flags = q.prog_flags ? q.prog_flags : reinterpret_cast<int32_t *>(ws + off_f);
+        p.code = reinterpret_cast<uint2 *>(ws + off_code);
+        p.ncode = reinterpret_cast<int32_t *>(ws + off_nc);
+        p.s_start = nullptr;
+        p.s_need = nullptr;
+        p.s_task = nullptr;
+        p.queue = nullptr;
+        p.gtape = nullptr;
+        p.abort = nullptr;
+        p.err = nullptr;
+        p.warp_bytes = gs.warp_bytes;
+        b->item_begin[g - g0] = items;
+        b->prog_begin[g - g0] = progs;
+        b->mse[g - g0] = q.mse;
+        b->dconst[g - g0] = q.dconst;
+      }
+      items += (long long)q.P * nch[i];
+      progs += q.P;
+    }
+    if (b) {
+      b->nprob = (int)(g1 - g0);
+      b->total_progs = progs;
+      b->total_items = items;
+      b->queue = reinterpret_cast<unsigned long long *>(ctx->ws + off_q);
+      b->gtape = gs.onchip ? nullptr : ctx->ws + off_t;
+      b->abort = ctx->abort_flag;
+      b->err = ctx->dev_words;
+      b->warp_bytes = gs.warp_bytes;
+      b->Lw = Lw;
+      b->Kw = Kw;
+    }
+    return cv.off;
+  };
+  size_t need = 0;
+  for (size_t g0 = 0; g0 < order.size(); g0 += MAX_GBATCH)
+    need = std::max(need, group_bytes(g0, std::min(order.size(), g0 + MAX_GBATCH), nullptr));
+  st = ensure_workspace(ctx, need);
+  if (st != SR_OK) return st;
+  st = allow_dynamic_smem(ctx, reinterpret_cast<const void *>(grad_decode_batched_kernel));
+  if (st != SR_OK) return st;
+  cudaStream_t s = ctx->stream;
+  for (size_t g0 = 0; g0 < order.size(); g0 += MAX_GBATCH) {
+    GradBatch b;
+    group_bytes(g0, std::min(order.size(), g0 + MAX_GBATCH), &b);
+    SR_CHECK_CUDA(ctx, cudaMemsetAsync(b.queue, 0, 8, s));
+    grad_decode_batched_kernel<<<(b.total_progs + DECODE_WARPS - 1) / DECODE_WARPS, DECODE_WARPS * 32,
+                                 DECODE_WARPS * decode_warp_bytes(Lw), s>>>(b);
+    if (gs.onchip) grad_batched_kernel<true><<<gs.grid, GWARPS * 32, gs.smem, s>>>(b);
+    else grad_batched_kernel<false><<<gs.grid, GWARPS * 32, gs.smem, s>>>(b);
+    int maxP = 1;
+    for (int r = 0; r < b.nprob; ++r) maxP = b.prob[r].P > maxP ? b.prob[r].P : maxP;
+    grad_finalize_batched_kernel<<<dim3(b.nprob, std::min((maxP + 255) / 256, 65535)), 256, 0, s>>>(b);
+    SR_CHECK_CUDA(ctx, cudaGetLastError());
+    ctx->launches += 3;
+  }
   return SR_OK;
 }
 
@@ -676,6 +972,51 @@ sr_status sr_adam_step(sr_ctx *ctx, float *consts, const double *grad, double *m
                                                          cfg->beta2, cfg->eps, 1.0 - p1, 1.0 - p2);
   SR_CHECK_CUDA(ctx, cudaGetLastError());
   ctx->launches += 1;
+  return SR_OK;
+}
+
+sr_status sr_adam_step_batched(sr_ctx *ctx, const sr_adam_table *tables, int ntables, int t,
+                               const sr_adam_cfg *cfg) {
+  using namespace sr;
+  if (!ctx || !cfg) return SR_EINVAL;
+  if (ntables < 0 || (ntables > 0 && !tables) || t < 1) return fail(ctx, SR_EINVAL, "bad table list or t < 1");
+  for (int i = 0; i < ntables; ++i) {
+    const sr_adam_table &q = tables[i];
+    if (q.n < 0) return fail(ctx, SR_EINVAL, "table %d: n < 0", i);
+    if (q.n > 0 && (!q.consts || !q.grad || !q.m || !q.v)) return fail(ctx, SR_EINVAL, "table %d: NULL pointer", i);
+  }
+  SR_CHECK_CUDA(ctx, cudaSetDevice(ctx->device));
+  double p1 = 1.0, p2 = 1.0;
+  for (int s = 0; s < t; ++s) {
+    p1 *= cfg->beta1;
+    p2 *= cfg->beta2;
+  }
+  for (int g0 = 0; g0 < ntables; g0 += MAX_ABATCH) {
+    AdamBatch a;
+    a.count = 0;
+    int maxn = 0;
+    for (int i = g0; i < ntables && i < g0 + MAX_ABATCH; ++i) {
+      const sr_adam_table &q = tables[i];
+      if (q.n == 0) continue;
+      a.c[a.count] = q.consts;
+      a.g[a.count] = q.grad;
+      a.m[a.count] = q.m;
+      a.v[a.count] = q.v;
+      a.n[a.count] = q.n;
+      maxn = q.n > maxn ? q.n : maxn;
+      ++a.count;
+    }
+    if (a.count == 0) continue;
+    a.lr = cfg->lr;
+    a.b1 = cfg->beta1;
+    a.b2 = cfg->beta2;
+    a.eps = cfg->eps;
+    a.bc1 = 1.0 - p1;
+    a.bc2 = 1.0 - p2;
+    adam_batched_kernel<<<dim3(a.count, std::min((maxn + 255) / 256, 65535)), 256, 0, ctx->stream>>>(a);
+    SR_CHECK_CUDA(ctx, cudaGetLastError());
+    ctx->launches += 1;
+  }
   return SR_OK;
 }
 

@@ -264,12 +264,11 @@ __host__ __device__ inline int decode_warp_bytes(int Lmax) {
 }
 constexpr int DECODE_WARPS = 4;  // warps (programs) per block of the decode kernels
 
-__device__ inline void decode_warp(const DecodeArgs &p, int P, unsigned char *smem) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int prog = blockIdx.x * (blockDim.x >> 5) + warp;
-  if (prog >= P) return;
+// Program `prog` decoded by the calling warp in its shared region `base`
+// (decode_warp_bytes(Lmax) bytes for some Lmax >= p.Lmax).
+__device__ inline void decode_warp_one(const DecodeArgs &p, int prog, unsigned char *base) {
+  const int lane = threadIdx.x & 31;
   const int Lt = p.Lmax + 4, Ls = p.Lmax + 2;
-  unsigned char *base = smem + (size_t)warp * decode_warp_bytes(p.Lmax);
   uint8_t *toks = base;                                          // [Lt]
   uint8_t *need = base + Lt;                                     // [Lt]
   int16_t *start = reinterpret_cast<int16_t *>(base + 2 * Lt);   // [Ls]
@@ -281,6 +280,13 @@ __device__ inline void decode_warp(const DecodeArgs &p, int P, unsigned char *sm
   const int L = p.lengths[prog];
   __syncwarp();
   if (lane == 0) decode_one(p, prog, toks, start, need, task, cs, L);
+}
+
+__device__ inline void decode_warp(const DecodeArgs &p, int P, unsigned char *smem) {
+  const int warp = threadIdx.x >> 5;
+  const int prog = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (prog >= P) return;
+  decode_warp_one(p, prog, smem + (size_t)warp * decode_warp_bytes(p.Lmax));
 }
 
 // ---------------------------------------------------------------- operators (FP32)

@@ -19,6 +19,7 @@ from dataclasses import dataclass, field
 import torch
 
 from . import binding
+from .autotune import bucket
 
 
 @dataclass
@@ -79,6 +80,7 @@ class Population:
             self.mse = torch.empty(P, dtype=torch.float64, device=programs.device)
             self.grad = torch.empty((P, K), dtype=torch.float64, device=programs.device)
         self.cur = 0
+        self.tile = 0  # cases per work item in a batched evaluation (0: the library's choice)
 
     @property
     def current(self):
@@ -125,7 +127,7 @@ class Evolver:
             for p in self.pops:
                 P_, L_, C_ = p.current
                 probs.append(binding.make_problem(P_, L_, C_, p.X, p.y, p.N, p.cfg.eval_kind,
-                                                  fitness=p.fitness_out()))
+                                                  fitness=p.fitness_out(), cases_per_tile=p.tile))
             binding.sr_eval_batched(self.ctx, probs)
         else:
             for p in self.pops:
@@ -143,12 +145,41 @@ class Evolver:
             binding.sr_eval_grad(self.ctx, P_, L_, C_, p.X, p.y, p.N, mse=mse, dconst=grad)
             binding.sr_adam_step(self.ctx, C_, grad, m, v, t, p.cfg.adam)
 
+    def _const_opt_batched(self, pops: list[Population]):
+        """Adam steps for every population at once: one sr_eval_grad_batched
+        launch per step over all populations still stepping (results equal
+        _const_opt's bit for bit)."""
+        for p in pops:
+            n = p.size
+            p.m[:n].zero_()
+            p.v[:n].zero_()
+        for t in range(1, max(p.cfg.const_steps for p in pops) + 1):
+            live = [p for p in pops if p.cfg.const_steps >= t]
+            probs = []
+            for p in live:
+                P_, L_, C_ = p.current
+                n = p.size
+                probs.append(binding.make_grad_problem(P_, L_, C_, p.X, p.y, p.N, mse=p.mse[:n],
+                                                       dconst=p.grad[:n]))
+            binding.sr_eval_grad_batched(self.ctx, probs)
+            # one launch for every population sharing an Adam configuration
+            by_cfg = {}
+            for p in live:
+                a = p.cfg.adam
+                by_cfg.setdefault((a.lr, a.beta1, a.beta2, a.eps), (a, []))[1].append(p)
+            for a, group in by_cfg.values():
+                binding.sr_adam_step_batched(self.ctx, [(p.current[2], p.grad[:p.size], p.m[:p.size],
+                                                         p.v[:p.size]) for p in group], t, a)
+
     def step(self):
         """One generation for every population (reads the generation from self.gen)."""
         binding.sr_set_generation_source(self.ctx, self.gen)
         try:
-            for p in self.pops:
-                if p.cfg.const_steps:
+            opt = [p for p in self.pops if p.cfg.const_steps]
+            if self.batched and opt:
+                self._const_opt_batched(opt)
+            else:
+                for p in opt:
                     self._const_opt(p)
             if self.eval_events is not None:
                 stream = self.ctx.stream
@@ -179,6 +210,30 @@ class Evolver:
             self.host_gen += 1
         finally:
             binding.sr_set_generation_source(self.ctx, None)
+
+    # -- launch shape ------------------------------------------------------------
+    def autotune(self, tuner) -> dict:
+        """Tune the evaluation launch on the current populations (an
+        autotune.Autotuner; cached per shape) and keep the choice: the cases
+        per work item of every population and the context's occupancy for a
+        batched loop, the context's tile and occupancy for one population.
+        Returns the tuner's record."""
+        if self.batched:
+            probs = []
+            for p in self.pops:
+                P_, L_, C_ = p.current
+                probs.append(binding.make_problem(P_, L_, C_, p.X, p.y, p.N, p.cfg.eval_kind,
+                                                  fitness=p.fitness_out()))
+            best = tuner.tune_batched(probs)
+            for p, pr in zip(self.pops, probs):
+                p.tile = pr[0].cases_per_tile
+            return best
+        if len(self.pops) != 1:
+            raise ValueError("an unbatched loop shares one tile: tune one population, or batch them")
+        p = self.pops[0]
+        P_, L_, C_ = p.current
+        tuner.tune(P_, L_, C_, p.X, p.y, p.N, p.cfg.eval_kind)
+        return dict(tuner.cache[bucket(p.N, p.X.shape[0], float(L_.float().mean()), p.cfg.eval_kind)])
 
     # -- checkpoint / resume ----------------------------------------------------
     def state_dict(self) -> dict:

@@ -219,3 +219,21 @@ def batched_problem(shape: dict, attempt: int = 0) -> Problem:
     return make_problem(f"batched-{s['index']}", s["seed"] + 1000 * attempt, P=s["P"],
                         Lmin=s["Lmin"], Lmax=s["Lmax"], nvars=s["nvars"], K=4, N=s["N"],
                         xlo=1.0, xhi=10.0, target_len=(3, 25), kind=s["kind"])
+
+
+def small_batch_shapes(seed: int = ROOT_SEED + 5, nprob: int = 64):
+    """Shapes of a batch of many small problems -- where a loop of
+    single-problem launches is launch- and tail-bound: nvars U{1..10},
+    N = floor(10^U(2.5, 4)) rounded up to 4 (316 to 10,000 cases), P
+    U{64..1024}, lengths U{4..64}, K = 4, kind Bernoulli(0.5)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(nprob):
+        nvars = int(rng.integers(1, 11))
+        N = round_up(int(10 ** rng.uniform(2.5, 4)), 4)
+        P = int(rng.integers(64, 1025))
+        Lmax = int(rng.integers(4, 65))
+        kind = int(rng.random() < 0.5)
+        out.append(dict(index=i, nvars=nvars, N=N, P=P, Lmin=min(4, Lmax), Lmax=Lmax, kind=kind,
+                        seed=seed * 100 + i))
+    return out

@@ -84,17 +84,58 @@ def test_selection_improves_best_fitness(ctx):
 
 
 def test_autotuner_picks_a_tile(ctx, tmp_path):
+    """The single-problem sweep (cases per item x CTAs per SM) leaves its
+    choice on the context and is cached; fitness does not depend on it."""
     p = _pop(51, P=512, N=20000)
     P_, L_, C_ = p.current
     tuner = Autotuner(ctx, str(tmp_path / "tiles.json"))
-    tile = tuner.tune(P_, L_, C_, p.X, p.y, p.N, binding.SR_MSE)
-    assert tile in (0, 512, 1024, 2048, 4096, 8192, 16384)
-    f_tuned = binding.sr_eval(ctx, P_, L_, C_, p.X, p.y, p.N, binding.SR_MSE)
-    binding.sr_set_tile(ctx, 0)
-    f_auto = binding.sr_eval(ctx, P_, L_, C_, p.X, p.y, p.N, binding.SR_MSE)
-    fin = torch.isfinite(f_auto)
-    assert torch.allclose(f_tuned[fin], f_auto[fin], rtol=1e-6)
-    assert (tmp_path / "tiles.json").exists()
+    try:
+        tile = tuner.tune(P_, L_, C_, p.X, p.y, p.N, binding.SR_MSE)
+        assert tile in (0, 512, 1024, 2048, 4096, 8192, 16384)
+        assert tuner.last and len(tuner.last) >= 3 * 6
+        f_tuned = binding.sr_eval(ctx, P_, L_, C_, p.X, p.y, p.N, binding.SR_MSE)
+        binding.sr_set_tile(ctx, 0)
+        binding.sr_set_occupancy(ctx, 0, 0)
+        f_auto = binding.sr_eval(ctx, P_, L_, C_, p.X, p.y, p.N, binding.SR_MSE)
+        fin = torch.isfinite(f_auto)
+        assert torch.allclose(f_tuned[fin], f_auto[fin], rtol=1e-6)
+        assert (tmp_path / "tiles.json").exists()
+        assert Autotuner(ctx, str(tmp_path / "tiles.json")).tune(P_, L_, C_, p.X, p.y, p.N, binding.SR_MSE) == tile
+    finally:
+        binding.sr_set_tile(ctx, 0)
+        binding.sr_set_occupancy(ctx, 0, 0)
+
+
+def test_autotuner_batched_shape_and_evolver(ctx, tmp_path):
+    """The batched sweep (cases per item x CTAs per SM 3/4/5) on a batch of
+    problems: the winner is applied to every problem and the context, the
+    fitness equals the automatic launch's up to summation order, and an
+    Evolver tuned that way runs the same generations as an untuned one."""
+    pops = [_pop(60 + i, P=256 + 64 * i, N=3000 + 1000 * i) for i in range(6)]
+    probs = [binding.make_problem(*p.current, p.X, p.y, p.N, binding.SR_MSE) for p in pops]
+    tuner = Autotuner(ctx, str(tmp_path / "tiles.json"))
+    try:
+        auto = [f.clone() for f in binding.sr_eval_batched(ctx, probs)]
+        best = tuner.tune_batched(probs)
+        assert best["ctas"] in (3, 4, 5) and best["ms"] <= best["auto_ms"]
+        tuned = binding.sr_eval_batched(ctx, probs)
+        for a, b in zip(auto, tuned):
+            fin = torch.isfinite(a)
+            assert torch.equal(fin, torch.isfinite(b)) and torch.allclose(a[fin], b[fin], rtol=1e-6)
+        assert all(p[0].cases_per_tile == (min(best["tile"], (p[0].N + 255) // 256 * 256) if best["tile"] else 0)
+                   for p in probs)
+        cfg = EvolveConfig(select_kind=binding.SR_MSE, eval_kind=binding.SR_MSE)
+        ev = Evolver(ctx, [_pop(60 + i, P=256 + 64 * i, N=3000 + 1000 * i, cfg=cfg) for i in range(6)],
+                     batched=True)
+        assert ev.autotune(tuner) == best  # cached
+        assert all(p.tile == (min(best["tile"], (p.N + 255) // 256 * 256) if best["tile"] else 0) for p in ev.pops)
+        ev.step()
+        torch.cuda.synchronize()
+        for p, a in zip(ev.pops, auto):
+            f = binding.sr_eval(ctx, *p.current, p.X, p.y, p.N, binding.SR_MSE)  # the children evaluate
+            assert torch.isfinite(f).any()
+    finally:
+        binding.sr_set_occupancy(ctx, 0, 0)
 
 
 def test_schedule_with_microcosm_and_graph(ctx):

@@ -59,6 +59,15 @@ def test_batched_shapes():
     assert shapes == inputs.batched_shapes()  # deterministic
 
 
+def test_small_batch_shapes():
+    shapes = inputs.small_batch_shapes()
+    assert len(shapes) == 64
+    for sh in shapes:
+        assert 1 <= sh["nvars"] <= 10 and 316 <= sh["N"] <= 10000 and sh["N"] % 4 == 0
+        assert 64 <= sh["P"] <= 1024 and 4 <= sh["Lmax"] <= 64 and sh["kind"] in (0, 1)
+    assert shapes == inputs.small_batch_shapes()
+
+
 def test_recipes_are_deterministic_and_attempts_differ():
     a, b, c = inputs.plain(), inputs.plain(), inputs.plain(attempt=1)
     assert np.array_equal(a.programs, b.programs) and np.array_equal(a.X, b.X)
