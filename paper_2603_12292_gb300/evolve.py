@@ -108,8 +108,17 @@ class Population:
 class Evolver:
     """Runs generations for one or more populations on one context."""
 
-    def __init__(self, ctx: binding.Context, pops: list[Population], batched: bool = False):
+    def __init__(self, ctx: binding.Context, pops: list[Population], batched: bool = False,
+                 split: bool = False, group=None):
+        """split: one population split across the ranks of a torch.distributed
+        group (every rank holds all of it, evaluates and optimises its slice
+        of rows, and the results are all-gathered before the selection that
+        every rank then runs alike, Sec. 2.1.2); not with batched or a
+        captured graph."""
+        if split and batched:
+            raise ValueError("split and batched are exclusive")
         self.ctx, self.pops, self.batched = ctx, pops, batched
+        self.split, self.group = split, group
         dev = pops[0].X.device
         self.gen = torch.zeros(1, dtype=torch.int64, device=dev)  # Philox generation (device)
         self.host_gen = 0                                          # generations run (schedule)
@@ -121,8 +130,44 @@ class Evolver:
         self.eval_events = None
 
     # -- one generation, eager ------------------------------------------------
+    def _slice(self, p: Population):
+        """(offset, count) of this rank's rows of population p."""
+        import torch.distributed as dist
+
+        from .shard import shard_range
+        return shard_range(p.size, dist.get_rank(self.group), dist.get_world_size(self.group))
+
+    def _evaluate_split(self):
+        from .shard import gather_fitness
+        for p in self.pops:
+            P_, L_, C_ = p.current
+            off, cnt = self._slice(p)
+            local = torch.empty((p.rows, cnt), dtype=torch.float64, device=P_.device)
+            if cnt:
+                sl = slice(off, off + cnt)
+                binding.sr_eval(self.ctx, P_[sl], L_[sl], C_[sl], p.X, p.y, p.N, p.cfg.eval_kind,
+                                fitness=local if p.rows == 2 else local[0])
+            p.fitness.copy_(gather_fitness(local, p.size, self.group))
+
+    def _const_opt_split(self, p: Population):
+        from .shard import gather_rows
+        P_, L_, C_ = p.current
+        off, cnt = self._slice(p)
+        if cnt:
+            sl = slice(off, off + cnt)
+            c = C_[sl]
+            m, v, mse, grad = p.m[:cnt], p.v[:cnt], p.mse[:cnt], p.grad[:cnt]
+            m.zero_()
+            v.zero_()
+            for t in range(1, p.cfg.const_steps + 1):
+                binding.sr_eval_grad(self.ctx, P_[sl], L_[sl], c, p.X, p.y, p.N, mse=mse, dconst=grad)
+                binding.sr_adam_step(self.ctx, c, grad, m, v, t, p.cfg.adam)
+        C_.copy_(gather_rows(C_[off:off + cnt].clone(), p.size, self.group))
+
     def _evaluate(self):
-        if self.batched:
+        if self.split:
+            self._evaluate_split()
+        elif self.batched:
             probs = []
             for p in self.pops:
                 P_, L_, C_ = p.current
@@ -176,7 +221,10 @@ class Evolver:
         binding.sr_set_generation_source(self.ctx, self.gen)
         try:
             opt = [p for p in self.pops if p.cfg.const_steps]
-            if self.batched and opt:
+            if self.split:
+                for p in opt:
+                    self._const_opt_split(p)
+            elif self.batched and opt:
                 self._const_opt_batched(opt)
             else:
                 for p in opt:
@@ -277,6 +325,8 @@ class Evolver:
         started) into one CUDA graph.  Runs one eager generation first so the
         workspace has grown; that generation counts."""
         assert gens % 2 == 0
+        if self.split:
+            raise ValueError("a split population exchanges fitness between ranks every generation; run it eagerly")
         self.step()
         torch.cuda.synchronize()
         sizes = [p.size for p in self.pops]

@@ -7,11 +7,14 @@ ways to use several ranks follow from that:
 * independent populations (islands): every rank evolves its own population
   of the same problem with its own seed; no data crosses ranks.  This is
   what ``bench.py --gpus N`` times (weak scaling).
-* one population split into contiguous slices: rank r evaluates rows
+* one population split into contiguous slices (``Evolver(split=True)``):
+  every rank holds the whole population, evaluates rows
   ``shard_range(P, r, world)`` (the C-ABI takes the slice as pointers at
-  that row offset); tournament selection draws parents from the whole
-  population, so the fitness slices are all-gathered once per generation
-  (P doubles, :func:`gather_fitness`) before it.
+  that row offset) and optimises their constants; the fitness slices (P
+  doubles, :func:`gather_fitness`) and the optimised constants
+  (:func:`gather_rows`) are all-gathered once per generation, and every
+  rank then runs the same selection and variation from the same seed, so
+  the populations stay identical without sending programs.
 
 Timing over ranks is the maximum (:func:`max_over_ranks`), work the sum.
 """
@@ -44,6 +47,22 @@ def gather_fitness(local: torch.Tensor, P: int, group=None) -> torch.Tensor:
     parts = [torch.empty_like(buf) for _ in range(world)]
     dist.all_gather(parts, buf, group=group)
     return torch.cat([p[..., :c] for p, c in zip(parts, counts)], dim=-1)
+
+
+def gather_rows(local: torch.Tensor, P: int, group=None) -> torch.Tensor:
+    """All-gather per-rank row slices (first axis = this rank's programs)
+    into the whole population's rows, in program order."""
+    world = dist.get_world_size(group)
+    counts = [shard_range(P, r, world)[1] for r in range(world)]
+    rank = dist.get_rank(group)
+    if local.shape[0] != counts[rank]:
+        raise ValueError(f"rank {rank} holds {local.shape[0]} rows, its slice has {counts[rank]}")
+    width = max(counts)
+    buf = torch.zeros((width,) + tuple(local.shape[1:]), dtype=local.dtype, device=local.device)
+    buf[: local.shape[0]] = local
+    parts = [torch.empty_like(buf) for _ in range(world)]
+    dist.all_gather(parts, buf, group=group)
+    return torch.cat([p[:c] for p, c in zip(parts, counts)], dim=0)
 
 
 def _reduce(value: float, op, device=None, group=None) -> float:
