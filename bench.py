@@ -115,11 +115,12 @@ def parse():
                     help="reduced sizes of the adjoint / large / batched workloads (2,048 x 131,072; "
                          "16,384 x 131,072; the first 8 problems), for profiler captures")
     ap.add_argument("--workload", default="paper",
-                    choices=["paper", "batched", "adjoint", "large", "plain", "beagle"],
+                    choices=["paper", "batched", "adjoint", "large", "plain", "beagle", "opmix"],
                     help="paper (default, the headline): 4096 x 100k; batched: 64 problems in one launch "
                          "vs a loop of single calls; adjoint: Adam constant optimisation; large: "
                          "262,144 x 1M; plain: 256 x 1k, CUDA graph vs eager; beagle: 4096 x 100k with "
-                         "1%% invalid targets, the r^4 score of Eq. 2 (and Eq. 3 timed beside it)")
+                         "1%% invalid targets, the r^4 score of Eq. 2 (and Eq. 3 timed beside it); opmix: the "
+                         "paper-shaped population drawn from one operator class at a time")
     return ap.parse_args()
 
 
@@ -860,6 +861,32 @@ def run_workload(args, local_rank):
                     clocks=region.clocks, gpu_launches=region.launches,
                     r4_eval_gpops=n_cur / (t_r4 / 1e3) / 1e9, p2p_eval_gpops=n_cur / (t_p2p / 1e3) / 1e9,
                     mse_corr_eval_gpops=n_cur / (t_both / 1e3) / 1e9)
+    elif args.workload == "opmix":
+        # one evaluation (both kinds from one pass) of the paper-shaped
+        # population drawn from one operator class at a time
+        classes, runs = {}, {}
+        for cls in inputs.OPMIX_CLASSES:
+            pr, pg, ln, cs, X, y = _device_problem(lambda a, c=cls: inputs.opmix(c, attempt=a), dev, binding, ctx)
+            f2 = torch.empty((2, pr.P), dtype=torch.float64, device=dev)
+            runs[cls] = (lambda pg=pg, ln=ln, cs=cs, X=X, y=y, f2=f2, N=pr.N:
+                         binding.sr_eval(ctx, pg, ln, cs, X, y, N, binding.SR_MSE_CORR, fitness=f2))
+            for _ in range(max(1, args.warmup)):
+                runs[cls]()
+            classes[cls] = {"units": float(ln.sum()) * pr.N, "mean_length": float(ln.float().mean())}
+        with _Region(binding, ctx, local_rank) as region:
+            for cls, run in runs.items():
+                t = _timed(run, max(1, args.steps), stream)
+                g = classes[cls].pop("units") / t / 1e6
+                classes[cls].update(gpops=g, ms=t, frac_of_alu_peak=g / _alu_peak(dev)[0])
+        line.update(metric="GPop/s per operator class (paper-shaped population, one sr_eval of both kinds)",
+                    value=classes["base"]["gpops"], unit="GPop/s", ms_per_step=classes["base"]["ms"],
+                    scaling="weak",
+                    config={"workload": "opmix: 4,096 programs of length 8-128 x 100,000 cases per class",
+                            "classes": {c: ({k: v for k, v in d.items()} or "all base operators")
+                                        for c, d in inputs.OPMIX_CLASSES.items()}},
+                    roofline=_roofline(dev, classes["base"]["gpops"], "eval_kernel (sr_eval SR_MSE_CORR)",
+                                       "a loop of sr_eval calls per class, CUDA events", "opmix-base"),
+                    opmix=classes, clocks=region.clocks, gpu_launches=region.launches)
     else:  # plain: launch-bound, CUDA graph vs eager
         pr, pg, ln, cs, X, y = _device_problem(lambda a: inputs.plain(attempt=a), dev, binding, ctx)
         pe = Population(pg.clone(), ln.clone(), cs.clone(), X, y, pr.N,

@@ -523,9 +523,21 @@ void or_eval(const uint8_t *programs, const int32_t *lengths,
  *   *cflags = OR of the case flags, plus CF_FITRANGE when some per-case
  *             fitness term exceeds FLT_MAX / N, so an FP32 partial sum of
  *             such terms may overflow (MSE: e_i^2; correlation: d_i^2 and
- *             |d_i yc_i|).
+ *             |d_i yc_i|), or when the correlation's FP32 products d_i^2,
+ *             d_i yc_i are so small that their underflow (each term off by
+ *             up to 2^-149) could move the sums by 1e-6 of themselves.
  * Work arrays yhat, lo, hi [N], cfl [N].
  */
+/* 1 when the FP32 moment products of 1 - r^2 (d^2 and d yc, d = yhat minus
+ * a shift) are tiny enough that rounding them into the subnormal range or
+ * to 0 (an absolute error of up to 2^-149 each) could move sum d^2 or
+ * sum |d yc| by 1e-6 of themselves: then the device's moments, and with
+ * them 1 - r^2, are not determined by the outputs. */
+static int fp32_terms_underflow(long N, double D2, double DY) {
+  const double floor_err = (double)N * 1.401298464324817e-45 * 1e6;
+  return D2 < floor_err || DY < floor_err;
+}
+
 void or_condition_one(const uint8_t *tok, int len, const double *c,
                       const double *X, long ldx, const double *y, long N,
                       int kind, double u, double *yhat, double *lo, double *hi,
@@ -573,6 +585,7 @@ void or_condition_one(const uint8_t *tok, int len, const double *c,
     }
     A += 8.0 * u * DY;
     B += 8.0 * u * D2;
+    if (fp32_terms_underflow(N, D2, DY)) cf |= CF_FITRANGE;
     if (sxx > 0.0 && syy > 0.0) {
       double r2 = sxy * sxy / (sxx * syy);
       double l = fabs(sxy) - A;
@@ -847,7 +860,8 @@ static double case_analysis(const uint8_t *tok, int len, const double *c, const 
  *            units; never above errb[k] by construction of neither, so a
  *            caller takes the smaller
  *   cfl[k]   CF_RANGE (some case's enclosure or reach leaves the FP32 range)
- *            and CF_FITRANGE (kind k's FP32 sums may overflow)
+ *            and CF_FITRANGE (kind k's FP32 sums may overflow, or for
+ *            1 - r^2 underflow: or_condition_one)
  *   f0[k]    the FP64 fitness
  * For 1 - r^2, when the reach of the outputs moves Sxy or Sxx by more than
  * 1 % of them, r^2 is not expanded: its enclosure over the moved outputs is
@@ -935,6 +949,7 @@ void or_condition_fo_one(const uint8_t *tok, int len, const double *c, const dou
         D2 += d * d;
         DY += fabs(d * yc);
       }
+      if (fp32_terms_underflow(N, D2, DY)) cfk |= CF_FITRANGE;
       if (sxx > 0.0 && syy > 0.0) {
         double r2 = sxy * sxy / (sxx * syy);
         /* enclosure of r^2 over outputs moved by up to width[i] (A, B) plus

@@ -32,7 +32,7 @@ def round_up(n: int, m: int) -> int:
 
 def random_programs(rng: np.random.Generator, P: int, Lmin: int, Lmax: int, nvars: int,
                     K: int, width: int | None = None, var_weight: float | None = None,
-                    unary_ops: int = N_UNARY):
+                    unary_ops: int = N_UNARY, unary_tokens=None, binary_tokens=None):
     """P valid postfix programs with lengths uniform in [Lmin, Lmax].
 
     Each token is drawn as a random walk on the stack depth d with r tokens
@@ -42,12 +42,23 @@ def random_programs(rng: np.random.Generator, P: int, Lmin: int, Lmax: int, nvar
     allowed ones; the token is uniform inside its class (terminals over the
     nvars variables and K constants, or variables with probability
     ``var_weight`` when it is given; unary operators over the first
-    ``unary_ops`` of tokens 4-15).  Returns tokens [P, width] (zero padded),
+    ``unary_ops`` of tokens 4-15, or over ``unary_tokens`` when given --
+    an empty list allows no unary operator; binary operators over tokens
+    0-3, or ``binary_tokens``).  Returns tokens [P, width] (zero padded),
     lengths [P] int32.
     """
     width = Lmax if width is None else width
     assert Lmin >= 1 and Lmax >= Lmin and width >= Lmax
+    un_set = np.arange(4, 4 + unary_ops) if unary_tokens is None else np.asarray(unary_tokens, np.int64)
+    bi_set = np.arange(N_BINARY) if binary_tokens is None else np.asarray(binary_tokens, np.int64)
+    if len(bi_set) == 0:
+        raise ValueError("programs need a binary operator")
     lens = rng.integers(Lmin, Lmax + 1, size=P).astype(np.int32)
+    if len(un_set) == 0:  # terminals and binary operators only: an odd length
+        lens = lens | 1
+        lens = np.where(lens > Lmax, lens - 2, lens).astype(np.int32)
+        if (lens < 1).any():
+            raise ValueError("no odd length in [Lmin, Lmax]")
     prog = np.zeros((P, width), np.uint8)
     d = np.zeros(P, np.int64)
     for t in range(Lmax):
@@ -56,7 +67,7 @@ def random_programs(rng: np.random.Generator, P: int, Lmin: int, Lmax: int, nvar
             break
         r = lens.astype(np.int64) - t
         a_term = act & (d <= r - 1)
-        a_un = act & (d >= 1) & (d <= r)
+        a_un = act & (d >= 1) & (d <= r) & (len(un_set) > 0)
         a_bin = act & (d >= 2) & (d <= r + 1)
         n_allowed = a_term.astype(np.int64) + a_un + a_bin
         pick = (rng.random(P) * np.maximum(n_allowed, 1)).astype(np.int64)
@@ -74,8 +85,8 @@ def random_programs(rng: np.random.Generator, P: int, Lmin: int, Lmax: int, nvar
             isvar = rng.random(P) < var_weight
             term = np.where(isvar, VAR0 + rng.integers(0, nvars, P),
                             CONST0 + rng.integers(0, K, P))
-        un = 4 + rng.integers(0, unary_ops, P)
-        bi = rng.integers(0, N_BINARY, P)
+        un = un_set[rng.integers(0, max(len(un_set), 1), P)] if len(un_set) else np.zeros(P, np.int64)
+        bi = bi_set[rng.integers(0, len(bi_set), P)]
         tok = np.where(cls == 0, term, np.where(cls == 1, un, bi))
         prog[act, t] = tok[act].astype(np.uint8)
         d = d + np.where(act, np.where(cls == 0, 1, np.where(cls == 2, -1, 0)), 0)
@@ -146,10 +157,11 @@ class Problem:
 
 def make_problem(name: str, seed: int, P: int, Lmin: int, Lmax: int, nvars: int, K: int, N: int,
                  xlo: float, xhi: float, target_len: tuple[int, int], noise: float = 0.0,
-                 kind: int = 0, unary_ops: int = N_UNARY) -> Problem:
+                 kind: int = 0, unary_ops: int = N_UNARY, unary_tokens=None, binary_tokens=None) -> Problem:
     rng = np.random.default_rng(seed)
     X = random_X(rng, nvars, N, xlo, xhi)
-    prog, lens = random_programs(rng, P, Lmin, Lmax, nvars, K, unary_ops=unary_ops)
+    prog, lens = random_programs(rng, P, Lmin, Lmax, nvars, K, unary_ops=unary_ops, unary_tokens=unary_tokens,
+                                 binary_tokens=binary_tokens)
     consts = random_consts(rng, P, K)
     # target: a random program that reads at least one variable
     while True:
@@ -237,3 +249,26 @@ def small_batch_shapes(seed: int = ROOT_SEED + 5, nprob: int = 64):
         out.append(dict(index=i, nvars=nvars, N=N, P=P, Lmin=min(4, Lmax), Lmax=Lmax, kind=kind,
                         seed=seed * 100 + i))
     return out
+
+
+# Operator classes of the op-mix workload: the paper-shaped population drawn
+# from one group of operators at a time, to see what each costs per node.
+OPMIX_CLASSES = {
+    "add-sub-mul": dict(unary_tokens=[], binary_tokens=[0, 1, 2]),
+    "arith": dict(unary_tokens=[], binary_tokens=[0, 1, 2, 3]),
+    "sq": dict(unary_tokens=[9], binary_tokens=[0, 1, 2]),
+    "sin": dict(unary_tokens=[4], binary_tokens=[0, 1, 2]),
+    "cos": dict(unary_tokens=[5], binary_tokens=[0, 1, 2]),
+    "exp": dict(unary_tokens=[6], binary_tokens=[0, 1, 2]),
+    "log": dict(unary_tokens=[7], binary_tokens=[0, 1, 2]),
+    "sqrt": dict(unary_tokens=[8], binary_tokens=[0, 1, 2]),
+    "base": dict(),
+}
+
+
+def opmix(cls: str, attempt: int = 0) -> Problem:
+    """The paper-shaped population (4,096 programs of length 8..128, 10
+    variables, 100,000 cases) drawn from one operator class of OPMIX_CLASSES."""
+    return make_problem(f"opmix-{cls}", ROOT_SEED + 6 + 1000 * attempt, P=4096, Lmin=8, Lmax=128, nvars=10,
+                        K=4, N=100_000, xlo=1.0, xhi=10.0, target_len=(5, 25), noise=0.01, kind=1,
+                        **OPMIX_CLASSES[cls])

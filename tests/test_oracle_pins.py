@@ -464,6 +464,22 @@ def test_first_order_bound_is_tighter_over_many_cases():
         assert (errp < 0.2 * errb).all(), (errp, errb)
 
 
+def test_tiny_outputs_flag_the_correlation_sums():
+    """Outputs of ~1e-31 are normal FP32 values, but their squares underflow
+    in FP32 (the device's moment products d^2): 1 - r^2 of such a program is
+    flagged CF_FITRANGE by both certificates; MSE and larger outputs are not."""
+    rng = np.random.default_rng(13)
+    X = rng.uniform(1, 5, (1, 1000)).astype(np.float32)
+    y = (X[0] * 2.0).astype(np.float32)
+    progs, lens = pack([parse("x0 c0 *"), parse("x0 c1 *")], 4)
+    consts = np.array([[1e-31, 1e-10], [1e-31, 1e-10]], np.float32)
+    errb, errp, cfl, f0 = oracle.condition_fo(progs, lens, consts, X, y)
+    assert cfl[1, 0] & oracle.CF_FITRANGE and cfl[1, 1] == 0
+    assert cfl[0, 0] == 0 and cfl[0, 1] == 0
+    eb, cf, _ = oracle.condition(progs, lens, consts, X, y, oracle.CORR)
+    assert cf[0] & oracle.CF_FITRANGE and cf[1] == 0
+
+
 def test_gradient_certificate_closed_form():
     """grad_cert: the same MSE, gradient and gabs as grad(); for yhat = c0 x0
     the output's reach is u |yhat| (1 + 1/16) on every case (one rounding,
