@@ -64,7 +64,7 @@ def _load():
     lib.or_condition_fo.argtypes = [P, P, P, i32, i32, i32, P, i64, P, i32, i64, f64, f64, P, P, P, P, i32]
     lib.or_first_order_cases.argtypes = [P, i32, P, P, i64, i64, f64, f64, i32, P, P, P, P, P]
     lib.or_grad.argtypes = [P, P, P, i32, i32, i32, P, i64, P, i32, i64, P, P, P, P, i32]
-    lib.or_grad_cert.argtypes = [P, P, P, i32, i32, i32, P, i64, P, i32, i64, f64, f64, P, P, P, P, P, i32]
+    lib.or_grad_cert.argtypes = [P, P, P, i32, i32, i32, P, i64, P, i32, i64, f64, f64, P, P, P, P, P, P, i32]
     lib.or_grad_one.argtypes = [P, i32, P, i32, P, i64, P, i64, P, P, P, P]
     lib.or_mse_fp64_consts.argtypes = [P, i32, P, P, i64, P, i64]
     lib.or_mse_fp64_consts.restype = f64
@@ -288,8 +288,10 @@ def grad_cert(programs, lengths, consts, X, y, N: int | None = None, u: float = 
               nthreads: int = 0):
     """MSE, dMSE/dconst [P, K] (forward mode, FP64), gabs [P, K] (as grad()),
     gerr [P, K] = (2/N) sum_i reach_i a_ik (how far the output's FP32
-    rounding can move the gradient) and nbranch [P] (cases whose branch FP32
-    rounding could flip): see or_grad_cert."""
+    rounding can move the gradient), nbranch [P] (cases whose branch FP32
+    rounding could flip) and nnonlin [P] (cases where the first-order
+    expansion is not trusted): see or_grad_cert.  A program's device
+    gradient is comparable when both counts are 0."""
     prog = _c(programs, np.uint8)
     P, Lmax = prog.shape
     lens = _c(lengths, np.int32)
@@ -304,9 +306,10 @@ def grad_cert(programs, lengths, consts, X, y, N: int | None = None, u: float = 
     gabs = np.empty((P, K), np.float64)
     gerr = np.empty((P, K), np.float64)
     nb = np.empty(P, np.int32)
+    nl = np.empty(P, np.int32)
     _load().or_grad_cert(_ptr(prog), _ptr(lens), _ptr(cons), P, Lmax, K, _ptr(X64), ldx, _ptr(y64), nvars, N,
-                         u, lam, _ptr(m), _ptr(g), _ptr(gabs), _ptr(gerr), _ptr(nb), nthreads)
-    return m, g, gabs, gerr, nb
+                         u, lam, _ptr(m), _ptr(g), _ptr(gabs), _ptr(gerr), _ptr(nb), _ptr(nl), nthreads)
+    return m, g, gabs, gerr, nb, nl
 
 
 def grad_one_fp64(tokens, consts64, X, y, N: int | None = None):

@@ -1430,6 +1430,12 @@ void or_grad_one(const uint8_t *tok, int len, const double *c, int K, const doub
  *            analysis, before its fallback): there the device's derivative
  *            may belong to the other branch, so such a program's gradient is
  *            not comparable;
+ *   nnonlin  the cases on which the first-order expansion is not trusted
+ *            (CF_NONLIN: an operand's reach comes near a singular point, or
+ *            sin / cos / exp / tan / tanh of an argument FP32 moves by more
+ *            than 0.1): the device's local derivatives there carry errors
+ *            the linear scale gabs does not bound, so such a program's
+ *            gradient is not comparable either;
  *   gerr     [P][K] (2/N) sum_i reach_i a_ik: how far the output's FP32
  *            rounding (reach_i: the first-order analysis's bound on case i,
  *            or its rigorous enclosure where the expansion is not trusted)
@@ -1438,7 +1444,8 @@ void or_grad_one(const uint8_t *tok, int len, const double *c, int K, const doub
  */
 void or_grad_cert(const uint8_t *programs, const int32_t *lengths, const float *consts, int P, int Lmax, int K,
                   const double *X, long ldx, const double *y, int nvars, long N, double u, double lam,
-                  double *mse, double *grad, double *gabs, double *gerr, int32_t *nbranch, int nthreads) {
+                  double *mse, double *grad, double *gabs, double *gerr, int32_t *nbranch, int32_t *nnonlin,
+                  int nthreads) {
   int nt = thread_count(nthreads);
 #pragma omp parallel num_threads(nt)
   {
@@ -1455,11 +1462,11 @@ void or_grad_cert(const uint8_t *programs, const int32_t *lengths, const float *
         mse[p] = INFINITY;
         for (int k = 0; k < K; ++k)
           grad[(size_t)p * K + k] = gabs[(size_t)p * K + k] = gerr[(size_t)p * K + k] = 0.0;
-        nbranch[p] = 0;
+        nbranch[p] = nnonlin[p] = 0;
         continue;
       }
       widen_consts(consts + (size_t)p * K, K, c);
-      int len = lengths[p], nb = 0;
+      int len = lengths[p], nb = 0, nl = 0;
       size_t L = (size_t)len + 1;
       for (long i = 0; i < N; ++i) {
         double s2, w1, w, lo, hi;
@@ -1467,12 +1474,14 @@ void or_grad_cert(const uint8_t *programs, const int32_t *lengths, const float *
         case_first_order(tok, len, c, X, ldx, i, u, lam, val, val + L, val + 2 * L, val + 3 * L, &s2, &w1, &w,
                          &cf);
         nb += (cf & CF_BRANCH) != 0;
+        nl += (cf & CF_NONLIN) != 0;
         int ca = 0;
         double y0 = case_analysis(tok, len, c, X, ldx, i, u, lam, val, box, &s2, &w1, &w, &lo, &hi, &ca);
         (void)y0;
         reach[i] = fo_reach(lam, s2, w1, w);
       }
       nbranch[p] = nb;
+      nnonlin[p] = nl;
       or_grad_one_ex(tok, len, c, K, X, ldx, y, N, &mse[p], grad + (size_t)p * K, NULL, gabs + (size_t)p * K,
                      reach, gerr + (size_t)p * K);
     }

@@ -80,9 +80,6 @@ struct EvalParams {
   int32_t *flags;          // [P]
   uint2 *code;             // [P][Lmax] decoded instructions
   int32_t *ncode;          // [P]
-  int16_t *s_start;        // decode scratch [P][Lmax]: first token of each subtree
-  uint8_t *s_need;         // decode scratch [P][Lmax]: stack need of each subtree
-  int16_t *s_task;         // decode scratch [P][Lmax]: work stack
   // [0] work counter, [1] work counter of the EXT pass, [2] EXT programs,
   // [3] work counter of the deep pass, [4] deep programs
   unsigned long long *queue;
@@ -158,13 +155,11 @@ __device__ __forceinline__ DecodeArgs decode_args(const EvalParams &p, int cap_s
   a.code = p.code;
   a.ncode = p.ncode;
   a.flags = p.flags;
-  a.s_start = p.s_start;
-  a.s_need = p.s_need;
-  a.s_task = p.s_task;
   a.ext_count = p.queue ? p.queue + 2 : nullptr;
   a.max_slots = slots_for(p.Lmax);
   a.cap_slots = cap_slots;
   a.deep_count = deep_count;
+  a.fold = 1;  // constant-only subtrees are evaluated once, in the decoder
   return a;
 }
 
@@ -635,9 +630,6 @@ struct BatchProblem {
   int32_t *flags;      // [P]
   uint2 *code;         // [P][Lmax]
   int32_t *ncode;      // [P]
-  int16_t *s_start;
-  uint8_t *s_need;
-  int16_t *s_task;
   double *fitness;     // [P] or [2][P]
   double *ychunk;      // [nchunks][2]
   double *ysum;        // [nchunks][2]: FP64 sum and count of y per chunk
@@ -659,6 +651,7 @@ struct BatchParams {
   unsigned long long *queue;  // as EvalParams::queue
   int warp_bytes;
   int slots;
+  int maxL;                   // the largest Lmax of the batch
   int deep;                   // as EvalParams::deep
   const int32_t *abort;       // as EvalParams::abort
   unsigned *err;
@@ -684,15 +677,15 @@ __device__ __forceinline__ EvalParams view(const BatchProblem &q) {
   p.flags = q.flags;
   p.code = q.code;
   p.ncode = q.ncode;
-  p.s_start = q.s_start;
-  p.s_need = q.s_need;
-  p.s_task = q.s_task;
   return p;
 }
 
-// one thread per program of every problem in the batch
+// a warp per program of every problem in the batch (shared regions sized
+// for the batch's largest Lmax, b.maxL)
 __global__ void decode_batched_kernel(const __grid_constant__ BatchParams b) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  const int warp = threadIdx.x >> 5;
+  const int g = blockIdx.x * (blockDim.x >> 5) + warp;
   if (g >= b.total_progs) return;
   int lo = 0, hi = b.nprob - 1;
   while (lo < hi) {
@@ -702,7 +695,8 @@ __global__ void decode_batched_kernel(const __grid_constant__ BatchParams b) {
   }
   EvalParams p = view(b.prob[lo]);
   p.queue = b.queue;
-  decode_one(decode_args(p, b.slots, b.queue + 4), g - b.prob[lo].prog_begin);
+  decode_warp_one(decode_args(p, b.slots, b.queue + 4), g - b.prob[lo].prog_begin,
+                  dsm + (size_t)warp * decode_warp_bytes(b.maxL));
 }
 
 // Work items of every problem come from one atomic counter: problem q owns
@@ -1177,9 +1171,6 @@ sr_status launch_eval(sr_ctx *ctx, int mode, const uint8_t *programs, const int3
   ep.flags = prog_flags ? prog_flags : reinterpret_cast<int32_t *>(ws + pl.off_flags);
   ep.code = reinterpret_cast<uint2 *>(ws + pl.off_code);
   ep.ncode = reinterpret_cast<int32_t *>(ws + pl.off_ncode);
-  ep.s_start = nullptr;  // the warp decoder keeps its scratch in shared memory
-  ep.s_need = nullptr;
-  ep.s_task = nullptr;
   ep.queue = reinterpret_cast<unsigned long long *>(ws + pl.off_queue);
   ep.yhat = yhat;
   ep.ldy = ldy;
@@ -1337,9 +1328,6 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
       const size_t off_f = q.prog_flags ? 0 : cv.take((size_t)q.P * 4);
       const size_t off_nc = cv.take((size_t)q.P * 4);
       const size_t off_code = cv.take(tokens * 8);
-      const size_t off_start = cv.take(tokens * 2);
-      const size_t off_need = cv.take(tokens);
-      const size_t off_task = cv.take(tokens * 2);
       const size_t off_p = cv.take((size_t)q.P * nch[i] * PSTRIDE * 8);
       size_t off_yc = 0, off_ych = 0, off_st = 0;
       const bool corr = mode != MODE_MSE;
@@ -1361,9 +1349,6 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
         b.flags = q.prog_flags ? q.prog_flags : reinterpret_cast<int32_t *>(ws + off_f);
         b.code = reinterpret_cast<uint2 *>(ws + off_code);
         b.ncode = reinterpret_cast<int32_t *>(ws + off_nc);
-        b.s_start = reinterpret_cast<int16_t *>(ws + off_start);
-        b.s_need = reinterpret_cast<uint8_t *>(ws + off_need);
-        b.s_task = reinterpret_cast<int16_t *>(ws + off_task);
         b.fitness = q.fitness;
         b.ychunk = corr ? reinterpret_cast<double *>(ws + off_ych) : nullptr;
         b.ysum = corr ? reinterpret_cast<double *>(ws + off_st) : nullptr;
@@ -1395,6 +1380,7 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
       bpar->total_items = items;
       bpar->queue = reinterpret_cast<unsigned long long *>(ctx->ws + off_q);
       bpar->slots = bslots;
+      bpar->maxL = maxL;
       bpar->warp_bytes = warp_smem_bytes(bpar->slots, maxL);
       bpar->deep = 0;
       bpar->abort = ctx->abort_flag;
@@ -1419,7 +1405,8 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
     int corr_blocks = 0;
     for (int r = 0; r < b.ncorr; ++r) corr_blocks += b.prob[b.corr_list[r]].nchunks;
     SR_CHECK_CUDA(ctx, cudaMemsetAsync(b.queue, 0, 5 * sizeof(unsigned long long), s));
-    decode_batched_kernel<<<(b.total_progs + 127) / 128, 128, 0, s>>>(b);
+    decode_batched_kernel<<<(b.total_progs + DECODE_WARPS - 1) / DECODE_WARPS, DECODE_WARPS * 32,
+                            DECODE_WARPS * decode_warp_bytes(maxL), s>>>(b);
     ctx->launches += 1;
     if (b.ncorr > 0) {
       ysum_batched_kernel<<<corr_blocks, PREP_THREADS, 0, s>>>(b);

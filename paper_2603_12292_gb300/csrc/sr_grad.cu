@@ -77,9 +77,6 @@ struct GradParams {
   int32_t *flags;     // [P]
   uint2 *code;        // [P][Lmax] scheduled instructions (slot bytes GSLOT)
   int32_t *ncode;     // [P]
-  int16_t *s_start;
-  uint8_t *s_need;
-  int16_t *s_task;
   unsigned long long *queue;
   char *gtape;        // per warp: Lmax entries of GSLOT bytes (tape off chip), else NULL
   const int32_t *abort;  // sr_set_abort_flag (or NULL)
@@ -106,13 +103,11 @@ __device__ __forceinline__ DecodeArgs grad_decode_args(const GradParams &p) {
   a.code = p.code;
   a.ncode = p.ncode;
   a.flags = p.flags;
-  a.s_start = p.s_start;
-  a.s_need = p.s_need;
-  a.s_task = p.s_task;
   a.ext_count = nullptr;
   a.max_slots = slots_for(p.Lmax);
   a.cap_slots = a.max_slots;  // one pass: no program is deep
   a.deep_count = nullptr;
+  a.fold = 0;  // every constant keeps its own slot: its derivative is wanted
   return a;
 }
 
@@ -802,9 +797,6 @@ sr_status sr_eval_grad(sr_ctx *ctx, const uint8_t *programs, const int32_t *leng
   gp.flags = prog_flags ? prog_flags : reinterpret_cast<int32_t *>(ws + off_f);
   gp.code = reinterpret_cast<uint2 *>(ws + off_code);
   gp.ncode = reinterpret_cast<int32_t *>(ws + off_nc);
-  gp.s_start = nullptr;  // the warp decoder keeps its scratch in shared memory
-  gp.s_need = nullptr;
-  gp.s_task = nullptr;
   gp.queue = reinterpret_cast<unsigned long long *>(ws + off_q);
   gp.gtape = gs.onchip ? nullptr : ws + off_t;
   gp.abort = ctx->abort_flag;
@@ -899,9 +891,6 @@ sr_status sr_eval_grad_batched(sr_ctx *ctx, const sr_grad_problem *pr, int nprob
         p.flags = q.prog_flags ? q.prog_flags : reinterpret_cast<int32_t *>(ws + off_f);
         p.code = reinterpret_cast<uint2 *>(ws + off_code);
         p.ncode = reinterpret_cast<int32_t *>(ws + off_nc);
-        p.s_start = nullptr;
-        p.s_need = nullptr;
-        p.s_task = nullptr;
         p.queue = nullptr;
         p.gtape = nullptr;
         p.abort = nullptr;

@@ -29,6 +29,52 @@ __host__ __device__ inline int slots_for(int Lmax) {
   return s < 1 ? 1 : (s > DSM ? DSM : s);
 }
 
+// ---------------------------------------------------------------- operators (FP32)
+__device__ __forceinline__ float op_div(float a, float b) {
+  // |b| < 1e-3f in FP32 is exactly "|b| <= 1e-3" for FP32 values of b
+  return fabsf(b) < 1e-3f ? 1.0f : a / b;
+}
+__device__ __forceinline__ float op_log(float x) {
+  return fabsf(x) < 1e-3f ? 0.0f : logf(fabsf(x));
+}
+__device__ __forceinline__ float op_exp(float x) {
+  x = x > 80.0f ? 80.0f : (x < -80.0f ? -80.0f : x);  // NaN passes through
+  return expf(x);
+}
+__device__ __forceinline__ float f_sqrt(float x) { return sqrtf(fabsf(x)); }
+
+// sinf / cosf carry a long path for large arguments; keep one out-of-line
+// copy of it and let the inlined copies assume a moderate argument (NaN and
+// +-inf also take the out-of-line call)
+static __device__ __noinline__ float sin_wide(float x) { return sinf(x); }
+static __device__ __noinline__ float cos_wide(float x) { return cosf(x); }
+__device__ __forceinline__ float f_sin(float x) {
+  if (!(fabsf(x) <= 4.0e4f)) return sin_wide(x);
+  __builtin_assume(fabsf(x) <= 4.0e4f);
+  return sinf(x);
+}
+__device__ __forceinline__ float f_cos(float x) {
+  if (!(fabsf(x) <= 4.0e4f)) return cos_wide(x);
+  __builtin_assume(fabsf(x) <= 4.0e4f);
+  return cosf(x);
+}
+static __device__ __noinline__ float tan_wide(float x) { return tanf(x); }
+__device__ __forceinline__ float f_tan(float x) {
+  if (!(fabsf(x) <= 4.0e4f)) return tan_wide(x);
+  __builtin_assume(fabsf(x) <= 4.0e4f);
+  return tanf(x);
+}
+// The rest of Table 1: 1/x protected like division; tan, asin, acos, atan,
+// tanh as the FP32 library computes them (asin / acos outside [-1, 1] give
+// NaN: a non-real result, which the NaN-aware scores of Eq. 2 / Eq. 3 take
+// as an invalid output and MSE / 1 - r^2 as the worst fitness).
+__device__ __forceinline__ float op_inv(float x) { return op_div(1.0f, x); }
+__device__ __forceinline__ float f_asin(float x) { return asinf(x); }
+__device__ __forceinline__ float f_acos(float x) { return acosf(x); }
+__device__ __forceinline__ float f_atan(float x) { return atanf(x); }
+__device__ __forceinline__ float f_tanh(float x) { return tanhf(x); }
+
+
 // Instruction (uint2):
 //   x bits 0..7   opcode
 //   x bits 8..23  byte offset of the stack slot it pushes to / pops from
@@ -98,13 +144,11 @@ struct DecodeArgs {
   uint2 *code;              // [P][Lmax] out
   int32_t *ncode;           // [P] out
   int32_t *flags;           // [P] out
-  int16_t *s_start;         // scratch [P][Lmax]: first token of each subtree
-  uint8_t *s_need;          // scratch [P][Lmax]: stack need of each subtree
-  int16_t *s_task;          // scratch [P][Lmax]: work stack
   unsigned long long *ext_count;  // programs with NCODE_EXT are counted here (or NULL)
   int max_slots;            // stack slots the kernel provides (<= DSM)
   int cap_slots;            // programs that need more than this get NCODE_DEEP (<= max_slots)
   unsigned long long *deep_count;  // programs with NCODE_DEEP are counted here (or NULL)
+  int fold;                 // 1: fold constant-only subtrees into one constant (evaluation only)
 };
 
 __device__ __forceinline__ bool is_term(int v) {
@@ -118,6 +162,33 @@ __device__ __forceinline__ uint2 with_operand(uint32_t x, int v, const float *cr
   return make_uint2(x | ((uint32_t)k << 24), __float_as_uint(crow[k]));
 }
 
+// The FP32 value of an operator node whose operands are constants, by the
+// same functions the interpreter applies to every case, so that a folded
+// subtree gives the bits its per-case evaluation gives.  Each operation is
+// one function call: nothing is contracted across operations.
+static __device__ __noinline__ float fold_op(int v, float a, float b) {
+  switch (v) {
+    case TOK_ADD: return __fadd_rn(a, b);
+    case TOK_SUB: return __fsub_rn(a, b);
+    case TOK_MUL: return __fmul_rn(a, b);
+    case TOK_DIV: return op_div(a, b);
+    case TOK_SIN: return f_sin(a);
+    case TOK_COS: return f_cos(a);
+    case TOK_EXP: return op_exp(a);
+    case TOK_LOG: return op_log(a);
+    case TOK_SQRT: return f_sqrt(a);
+    case TOK_SQ: return __fmul_rn(a, a);
+    case TOK_INV: return op_inv(a);
+    case TOK_TAN: return f_tan(a);
+    case TOK_ASIN: return f_asin(a);
+    case TOK_ACOS: return f_acos(a);
+    case TOK_ATAN: return f_atan(a);
+    default: return f_tanh(a);
+  }
+}
+
+constexpr uint8_t NEED_FOLDED = 0x80;  // need[] bit: the subtree reads only constants (folded)
+
 // Validation and scheduled decoding of program `prog` (one thread), reading
 // its tokens from `tok`, its constants from `crow` and using the scratch rows
 // start / need / task (Lmax entries each).
@@ -125,7 +196,7 @@ __device__ __forceinline__ uint2 with_operand(uint32_t x, int v, const float *cr
 // out of range; depth (running sum of +1 terminal, 0 unary or bad byte, -1
 // binary) below 1 after some token; final depth not 1.
 __device__ inline void decode_one(const DecodeArgs &p, int prog, const uint8_t *tok, int16_t *start,
-                                  uint8_t *need, int16_t *task, const float *crow, int L) {
+                                  uint8_t *need, int16_t *task, const float *crow, float *fval, int L) {
   int flags = 0;
   if (L < 1 || L > p.Lmax) {
     flags = SR_PF_BAD_LENGTH;
@@ -149,25 +220,42 @@ __device__ inline void decode_one(const DecodeArgs &p, int prog, const uint8_t *
   }
   int ext = 0;
   // pass 1, postfix order is bottom-up: subtree starts and stack needs
-  // (terminal 1; unary as its child; binary max of the children, +1 on a tie)
+  // (terminal 1; unary as its child; binary max of the children, +1 on a tie).
+  // With p.fold, a subtree that reads only constants is evaluated here, once,
+  // and becomes a constant leaf (need 1, NEED_FOLDED, value in fval).
   int sp = 0;
   for (int t = 0; t < L; ++t) {
-    const int cls = tok_class(tok[t]);
+    const int v = tok[t];
+    const int cls = tok_class(v);
     if (cls == CLS_VAR || cls == CLS_CONST) {
       start[t] = (int16_t)t;
       need[t] = 1;
+      if (p.fold && cls == CLS_CONST) {
+        need[t] = 1 | NEED_FOLDED;
+        fval[t] = crow[v - TOK_CONST0];
+      }
       task[sp++] = (int16_t)t;
     } else if (cls == CLS_UNARY) {
-      ext |= tok[t] > TOK_SQ;
       const int c = task[sp - 1];
       start[t] = start[c];
-      need[t] = need[c];
+      if (need[c] & NEED_FOLDED) {
+        need[t] = 1 | NEED_FOLDED;
+        fval[t] = fold_op(v, fval[c], 0.0f);
+      } else {
+        ext |= v > TOK_SQ;
+        need[t] = need[c];
+      }
       task[sp - 1] = (int16_t)t;
     } else {
       const int b = task[--sp], a = task[sp - 1];
-      const int na = need[a], nb = need[b];
       start[t] = start[a];
-      need[t] = (uint8_t)(na == nb ? na + 1 : (na > nb ? na : nb));
+      if ((need[a] & need[b]) & NEED_FOLDED) {
+        need[t] = 1 | NEED_FOLDED;
+        fval[t] = fold_op(v, fval[a], fval[b]);
+      } else {
+        const int na = need[a] & 0x7f, nb = need[b] & 0x7f;
+        need[t] = (uint8_t)(na == nb ? na + 1 : (na > nb ? na : nb));
+      }
       task[sp - 1] = (int16_t)t;
     }
   }
@@ -179,11 +267,18 @@ __device__ inline void decode_one(const DecodeArgs &p, int prog, const uint8_t *
   int n = 0, d = 0, used = 0;
   sp = 0;
   task[sp++] = (int16_t)((L - 1) << 2);
+  // a leaf's operand: x_j, c_k, or a folded subtree's value (constant index
+  // 0: the evaluation kernels read only the value)
+  auto operand = [&](uint32_t x, int node) -> uint2 {
+    if (need[node] & NEED_FOLDED) return make_uint2(x, __float_as_uint(fval[node]));
+    return with_operand(x, tok[node], crow, p.ldx);
+  };
+  auto is_leaf = [&](int node) { return is_term(tok[node]) || (need[node] & NEED_FOLDED) != 0; };
   while (sp > 0) {
     const int e = task[sp - 1];
     const int node = e >> 2, ph = e & 3;
     const int v = tok[node];
-    const int cls = tok_class(v);
+    const int cls = is_leaf(node) ? (tok_class(v) == CLS_VAR ? CLS_VAR : CLS_CONST) : tok_class(v);
     if (cls == CLS_VAR || cls == CLS_CONST) {
       --sp;
       if (d > p.max_slots) {  // cannot happen for programs of <= Lmax tokens; never write past the slots
@@ -195,7 +290,7 @@ __device__ inline void decode_one(const DecodeArgs &p, int prog, const uint8_t *
       uint32_t op = var ? OP_LDV : OP_LDC;
       if (d > 0) op = (uint32_t)(var ? OP_PUSHV : OP_PUSHC) | ((uint32_t)((d - 1) * p.slot_bytes) << 8);
       used = d > used ? d : used;  // slots 0 .. d - 1 are in use
-      code[n++] = with_operand(op, v, crow, p.ldx);
+      code[n++] = operand(op, node);
       ++d;
     } else if (cls == CLS_UNARY) {
       if (ph == 0) {
@@ -207,20 +302,19 @@ __device__ inline void decode_one(const DecodeArgs &p, int prog, const uint8_t *
       }
     } else {
       const int b = node - 1, a = start[b] - 1;
-      const bool rev = need[b] > need[a];
+      const bool rev = (need[b] & 0x7f) > (need[a] & 0x7f);
       const int first = rev ? b : a, second = rev ? a : b;
       if (ph == 0) {
         task[sp - 1] = (int16_t)(e | 1);
         task[sp++] = (int16_t)(first << 2);
-      } else if (ph == 1 && is_term(tok[second])) {
+      } else if (ph == 1 && is_leaf(second)) {
         --sp;
-        const int w = tok[second];
-        const bool var = tok_class(w) == CLS_VAR;
+        const bool var = !(need[second] & NEED_FOLDED) && tok_class(tok[second]) == CLS_VAR;
         uint32_t op;
         if (rev && v == TOK_SUB) op = var ? OP_VRSUB : OP_CRSUB;
         else if (rev && v == TOK_DIV) op = var ? OP_VRDIV : OP_CRDIV;
         else op = (uint32_t)((var ? OP_VADD : OP_CADD) + v);  // + and * commute exactly
-        code[n++] = with_operand(op, w, crow, p.ldx);
+        code[n++] = operand(op, second);
       } else if (ph == 1) {
         task[sp - 1] = (int16_t)((e & ~3) | 2);
         task[sp++] = (int16_t)(second << 2);
@@ -241,13 +335,6 @@ __device__ inline void decode_one(const DecodeArgs &p, int prog, const uint8_t *
   if (deep && p.deep_count) atomicAdd(p.deep_count, 1ull);
 }
 
-// decode_one with the scratch of the global workspace
-__device__ inline void decode_one(const DecodeArgs &p, int prog) {
-  const size_t row = (size_t)prog * p.Lmax;
-  decode_one(p, prog, p.programs + row, p.s_start + row, p.s_need + row, p.s_task + row,
-             p.consts + (size_t)prog * p.K, p.lengths[prog]);
-}
-
 // Decoding by warps in shared memory: one warp per program.  The warp copies
 // the program's token row and constants with coalesced loads, then lane 0
 // decodes it with its scratch in shared memory.  The tree walk is serial and
@@ -257,10 +344,12 @@ __device__ inline void decode_one(const DecodeArgs &p, int prog) {
 // several warps per scheduler to hide the walk's latency.
 // Dynamic shared memory per warp: decode_warp_bytes.
 // layout: tokens [Lmax + 4] | need [Lmax + 4] | start [Lmax + 2] int16 |
-// task [Lmax + 2] int16 | constants [SR_MAX_CONSTS] float (4-byte aligned)
+// task [Lmax + 2] int16 | constants [SR_MAX_CONSTS] float (4-byte aligned) |
+// folded values [Lmax] float
 __host__ __device__ inline int decode_consts_offset(int Lmax) { return (6 * Lmax + 16 + 3) & ~3; }
+__host__ __device__ inline int decode_fval_offset(int Lmax) { return decode_consts_offset(Lmax) + SR_MAX_CONSTS * 4; }
 __host__ __device__ inline int decode_warp_bytes(int Lmax) {
-  return (decode_consts_offset(Lmax) + SR_MAX_CONSTS * 4 + 15) & ~15;
+  return (decode_fval_offset(Lmax) + 4 * Lmax + 15) & ~15;
 }
 constexpr int DECODE_WARPS = 4;  // warps (programs) per block of the decode kernels
 
@@ -274,12 +363,13 @@ __device__ inline void decode_warp_one(const DecodeArgs &p, int prog, unsigned c
   int16_t *start = reinterpret_cast<int16_t *>(base + 2 * Lt);   // [Ls]
   int16_t *task = start + Ls;                                    // [Ls]
   float *cs = reinterpret_cast<float *>(base + decode_consts_offset(p.Lmax));
+  float *fv = reinterpret_cast<float *>(base + decode_fval_offset(p.Lmax));
   const uint8_t *src = p.programs + (size_t)prog * p.Lmax;
   for (int b = lane; b < p.Lmax; b += 32) toks[b] = src[b];
   if (lane < p.K) cs[lane] = p.consts[(size_t)prog * p.K + lane];
   const int L = p.lengths[prog];
   __syncwarp();
-  if (lane == 0) decode_one(p, prog, toks, start, need, task, cs, L);
+  if (lane == 0) decode_one(p, prog, toks, start, need, task, cs, fv, L);
 }
 
 __device__ inline void decode_warp(const DecodeArgs &p, int P, unsigned char *smem) {
@@ -288,50 +378,5 @@ __device__ inline void decode_warp(const DecodeArgs &p, int P, unsigned char *sm
   if (prog >= P) return;
   decode_warp_one(p, prog, smem + (size_t)warp * decode_warp_bytes(p.Lmax));
 }
-
-// ---------------------------------------------------------------- operators (FP32)
-__device__ __forceinline__ float op_div(float a, float b) {
-  // |b| < 1e-3f in FP32 is exactly "|b| <= 1e-3" for FP32 values of b
-  return fabsf(b) < 1e-3f ? 1.0f : a / b;
-}
-__device__ __forceinline__ float op_log(float x) {
-  return fabsf(x) < 1e-3f ? 0.0f : logf(fabsf(x));
-}
-__device__ __forceinline__ float op_exp(float x) {
-  x = x > 80.0f ? 80.0f : (x < -80.0f ? -80.0f : x);  // NaN passes through
-  return expf(x);
-}
-__device__ __forceinline__ float f_sqrt(float x) { return sqrtf(fabsf(x)); }
-
-// sinf / cosf carry a long path for large arguments; keep one out-of-line
-// copy of it and let the inlined copies assume a moderate argument (NaN and
-// +-inf also take the out-of-line call)
-static __device__ __noinline__ float sin_wide(float x) { return sinf(x); }
-static __device__ __noinline__ float cos_wide(float x) { return cosf(x); }
-__device__ __forceinline__ float f_sin(float x) {
-  if (!(fabsf(x) <= 4.0e4f)) return sin_wide(x);
-  __builtin_assume(fabsf(x) <= 4.0e4f);
-  return sinf(x);
-}
-__device__ __forceinline__ float f_cos(float x) {
-  if (!(fabsf(x) <= 4.0e4f)) return cos_wide(x);
-  __builtin_assume(fabsf(x) <= 4.0e4f);
-  return cosf(x);
-}
-static __device__ __noinline__ float tan_wide(float x) { return tanf(x); }
-__device__ __forceinline__ float f_tan(float x) {
-  if (!(fabsf(x) <= 4.0e4f)) return tan_wide(x);
-  __builtin_assume(fabsf(x) <= 4.0e4f);
-  return tanf(x);
-}
-// The rest of Table 1: 1/x protected like division; tan, asin, acos, atan,
-// tanh as the FP32 library computes them (asin / acos outside [-1, 1] give
-// NaN: a non-real result, which the NaN-aware scores of Eq. 2 / Eq. 3 take
-// as an invalid output and MSE / 1 - r^2 as the worst fitness).
-__device__ __forceinline__ float op_inv(float x) { return op_div(1.0f, x); }
-__device__ __forceinline__ float f_asin(float x) { return asinf(x); }
-__device__ __forceinline__ float f_acos(float x) { return acosf(x); }
-__device__ __forceinline__ float f_atan(float x) { return atanf(x); }
-__device__ __forceinline__ float f_tanh(float x) { return tanhf(x); }
 
 }  // namespace sr

@@ -492,7 +492,7 @@ def test_gradient_certificate_closed_form():
     y = rng.normal(size=N).astype(np.float32)
     progs, lens = pack([parse("c0 x0 *"), parse("x0 x1 c1 * / c0 *")], 8)
     consts = np.array([[1.75, 1.0], [0.5, 1.0]], np.float32)
-    m, g, gabs, gerr, nb = oracle.grad_cert(progs, lens, consts, X, y)
+    m, g, gabs, gerr, nb, nl = oracle.grad_cert(progs, lens, consts, X, y)
     m2, g2, _, gabs2 = oracle.grad(progs, lens, consts, X, y)
     np.testing.assert_array_equal(m, m2)
     np.testing.assert_array_equal(g, g2)
@@ -500,7 +500,12 @@ def test_gradient_certificate_closed_form():
     x0 = X[0].astype(np.float64)
     reach = oracle.U_FP32 * np.abs(1.75 * x0) * (1 + 1 / 16)
     assert gerr[0, 0] == pytest.approx(2.0 / N * np.sum(reach * x0), rel=1e-12)
-    assert nb.tolist() == [0, 1]
+    assert nb.tolist() == [0, 1] and nl.tolist() == [0, 0]
+    # sin of a computed ~1e6: FP32 rounding of the argument moves it by more than 0.1
+    X2 = X.copy()
+    X2[0] *= 2e5
+    *_, nb2, nl2 = oracle.grad_cert(*pack([parse("x0 c1 * sin c0 *")], 8), consts[:1], X2, y)
+    assert nb2[0] == 0 and nl2[0] > N // 2  # every case whose argument passes ~4e5
 
 
 # ---------------------------------------------------------------- gradient
