@@ -18,7 +18,7 @@ OPS = ["+", "-", "*", "/", "sin", "cos", "exp", "log", "sqrt", "sq", "inv", "tan
 
 def _pair(text, consts):
     """(program, program with c_k read from variable x_{3+k})."""
-    swapped = " ".join(f"x{3 + int(t[1:])}" if t.startswith("c") else t for t in text.split())
+    swapped = " ".join(f"x{3 + int(t[1:])}" if t[0] == "c" and t[1:].isdigit() else t for t in text.split())
     return parse(text), parse(swapped)
 
 
