@@ -160,6 +160,7 @@ __device__ __forceinline__ DecodeArgs decode_args(const EvalParams &p, int cap_s
   a.cap_slots = cap_slots;
   a.deep_count = deep_count;
   a.fold = 1;  // constant-only subtrees are evaluated once, in the decoder
+  a.adj_info = 0;
   return a;
 }
 

@@ -108,6 +108,7 @@ __device__ __forceinline__ DecodeArgs grad_decode_args(const GradParams &p) {
   a.cap_slots = a.max_slots;  // one pass: no program is deep
   a.deep_count = nullptr;
   a.fold = 0;  // every constant keeps its own slot: its derivative is wanted
+  a.adj_info = 1;
   return a;
 }
 
@@ -254,6 +255,54 @@ __device__ __noinline__ VD fwd_ext(uint32_t op, VG x) {
   }
   return r;
 }
+// one out-of-line entry for the value and local derivative of any unary
+// operator (the forward sweep's tape entry)
+__device__ __noinline__ VD fwd_unary(uint32_t op, VG x) {
+  switch (op) {
+    case OP_SIN: return fwd_sin(x);
+    case OP_COS: return fwd_cos(x);
+    case OP_EXP: return fwd_exp(x);
+    case OP_LOG: return fwd_log(x);
+    case OP_SQRT: return fwd_sqrt(x);
+    case OP_SQ: {
+      VD r;
+#pragma unroll
+      for (int i = 0; i < GCPL; ++i) {
+        r.d.v[i] = x.v[i] + x.v[i];
+        r.v.v[i] = x.v[i] * x.v[i];
+      }
+      return r;
+    }
+    default: return fwd_ext(op, x);
+  }
+}
+// the value alone (a node whose subtree reads no constant), by the
+// interpreter's FP32 operators
+__device__ __noinline__ VG val_unary(uint32_t op, VG x) {
+  VG r;
+#pragma unroll 1
+  for (int i = 0; i < GCPL; ++i) {
+    const float a = x.v[i];
+    float v;
+    switch (op) {
+      case OP_SIN: v = f_sin(a); break;
+      case OP_COS: v = f_cos(a); break;
+      case OP_EXP: v = op_exp(a); break;
+      case OP_LOG: v = op_log(a); break;
+      case OP_SQRT: v = f_sqrt(a); break;
+      case OP_SQ: v = a * a; break;
+      case OP_INV: v = op_inv(a); break;
+      case OP_TAN: v = f_tan(a); break;
+      case OP_ASIN: v = f_asin(a); break;
+      case OP_ACOS: v = f_acos(a); break;
+      case OP_ATAN: v = f_atan(a); break;
+      default: v = f_tanh(a); break;
+    }
+    r.v[i] = v;
+  }
+  return r;
+}
+
 // protected quotient (the interpreter's operator)
 __device__ __noinline__ VG pdivg(VG a, VG b) {
   VG r;
@@ -376,27 +425,60 @@ __device__ __forceinline__ void grad_item(const GradParams &p, int c, int prog, 
         case OP_ADD: { const VG a = *slot_at(w, off); T = addg(a, T); } break;
         case OP_SUB: { const VG a = *slot_at(w, off); T = subg(a, T); } break;
         case OP_RSUB: { const VG b = *slot_at(w, off); T = subg(T, b); } break;
-        case OP_MUL: { const VG a = *slot_at(w, off); push(a); push(T); T = mulg(a, T); } break;
-        case OP_DIV: { const VG a = *slot_at(w, off); push(T); T = pdivg(a, T); push(T); } break;
-        case OP_RDIV: { const VG b = *slot_at(w, off); push(b); T = pdivg(T, b); push(T); } break;
-        case OP_SIN: { const VD r = fwd_sin(T); push(r.d); T = r.v; } break;
-        case OP_COS: { const VD r = fwd_cos(T); push(r.d); T = r.v; } break;
-        case OP_EXP: { const VD r = fwd_exp(T); push(r.d); T = r.v; } break;
-        case OP_LOG: { const VD r = fwd_log(T); push(r.d); T = r.v; } break;
-        case OP_SQRT: { const VD r = fwd_sqrt(T); push(r.d); T = r.v; } break;
-        case OP_SQ: push(addg(T, T)); T = mulg(T, T); break;
+        // the tape keeps only what the reverse sweep will use (INS_SA / INS_TA:
+        // which operands' adjoints are wanted; INS_NOADJ: none)
+        case OP_MUL: {
+          const VG a = *slot_at(w, off);
+          if (ins.x & INS_TA) push(a);
+          if (ins.x & INS_SA) push(T);
+          T = mulg(a, T);
+        } break;
+        case OP_DIV: {
+          const VG a = *slot_at(w, off);
+          if (ins.x & (INS_SA | INS_TA)) push(T);
+          T = pdivg(a, T);
+          if (ins.x & INS_TA) push(T);
+        } break;
+        case OP_RDIV: {
+          const VG b = *slot_at(w, off);
+          if (ins.x & (INS_SA | INS_TA)) push(b);
+          T = pdivg(T, b);
+          if (ins.x & INS_SA) push(T);
+        } break;
+        case OP_SIN:
+        case OP_COS:
+        case OP_EXP:
+        case OP_LOG:
+        case OP_SQRT:
+        case OP_SQ:
         case OP_INV:
         case OP_TAN:
         case OP_ASIN:
         case OP_ACOS:
         case OP_ATAN:
-        case OP_TANH: { const VD r = fwd_ext(ins_op(ins), T); push(r.d); T = r.v; } break;
+        case OP_TANH:
+          if (ins.x & INS_NOADJ) {
+            T = val_unary(ins_op(ins), T);  // no constant below: the value alone
+          } else {
+            const VD r = fwd_unary(ins_op(ins), T);
+            push(r.d);
+            T = r.v;
+          }
+          break;
         case OP_VADD: T = addg(T, ldxg(xr, ins.y)); break;
         case OP_VSUB: T = subg(T, ldxg(xr, ins.y)); break;
         case OP_VRSUB: T = subg(ldxg(xr, ins.y), T); break;
         case OP_VMUL: T = mulg(T, ldxg(xr, ins.y)); break;
         case OP_VDIV: T = pdivg(T, ldxg(xr, ins.y)); break;
-        case OP_VRDIV: push(T); T = pdivg(ldxg(xr, ins.y), T); push(T); break;
+        case OP_VRDIV:
+          if (ins.x & INS_NOADJ) {
+            T = pdivg(ldxg(xr, ins.y), T);
+          } else {
+            push(T);
+            T = pdivg(ldxg(xr, ins.y), T);
+            push(T);
+          }
+          break;
         case OP_CADD: T = addg(T, splatg(cv)); break;
         case OP_CSUB: T = subg(T, splatg(cv)); break;
         case OP_CRSUB: T = subg(splatg(cv), T); break;
@@ -419,7 +501,15 @@ __device__ __forceinline__ void grad_item(const GradParams &p, int c, int prog, 
     // ---- reverse
     VG aT = e;
     for (int ip = n - 1; ip >= 0; --ip) {
-      const uint2 ins = w.code[ip];
+      uint2 ins = w.code[ip];
+      if (ins.x & INS_NOADJ) {
+        // a subtree without constants: nothing of it is on the tape and no
+        // adjoint flows into it; go on from its first instruction (a
+        // variable load, whose reverse restores the outer adjoint)
+        const uint32_t o = ins_op(ins);
+        ip = (o >= OP_VADD && o <= OP_VRDIV) ? (int)ins_off(ins) : (int)ins.y;
+        ins = w.code[ip];
+      }
       const uint32_t off = ins_off(ins);
       const float cv = __uint_as_float(ins.y);
       const int k = ins_k(ins);
@@ -432,21 +522,27 @@ __device__ __forceinline__ void grad_item(const GradParams &p, int c, int prog, 
         case OP_SUB: *slot_at(w, off) = aT; aT = negg(aT); break;
         case OP_RSUB: *slot_at(w, off) = negg(aT); break;
         case OP_MUL: {  // T = a t
-          const VG t = pop(), a = pop();
-          *slot_at(w, off) = mulg(aT, t);
-          aT = mulg(aT, a);
+          const bool sa = ins.x & INS_SA, ta = ins.x & INS_TA;
+          const VG t = sa ? pop() : splatg(0.f);
+          const VG a = ta ? pop() : splatg(0.f);
+          if (sa) *slot_at(w, off) = mulg(aT, t);
+          if (ta) aT = mulg(aT, a);
         } break;
         case OP_DIV: {  // T = a / t: dT/da = 1/t, dT/dt = -T/t
-          const VG Tn = pop(), t = pop();
+          const bool sa = ins.x & INS_SA, ta = ins.x & INS_TA;
+          const VG Tn = ta ? pop() : splatg(0.f);
+          const VG t = (sa || ta) ? pop() : splatg(1.f);
           const VG q = qdivg(aT, t);
-          *slot_at(w, off) = q;
-          aT = negg(mulg(q, Tn));
+          if (sa) *slot_at(w, off) = q;
+          if (ta) aT = negg(mulg(q, Tn));
         } break;
         case OP_RDIV: {  // T = t / b
-          const VG Tn = pop(), b = pop();
+          const bool sa = ins.x & INS_SA, ta = ins.x & INS_TA;
+          const VG Tn = sa ? pop() : splatg(0.f);
+          const VG b = (sa || ta) ? pop() : splatg(1.f);
           const VG q = qdivg(aT, b);
-          *slot_at(w, off) = negg(mulg(q, Tn));
-          aT = q;
+          if (sa) *slot_at(w, off) = negg(mulg(q, Tn));
+          if (ta) aT = q;
         } break;
         case OP_SIN:
         case OP_COS:
@@ -522,7 +618,7 @@ __device__ __forceinline__ GradWarp grad_warp(unsigned char *smem, int warp_byte
 }
 
 template <bool ONCHIP>
-__global__ void __launch_bounds__(GWARPS * 32) grad_kernel(GradParams p) {
+__global__ void __launch_bounds__(GWARPS * 32, GCTAS_PER_SM) grad_kernel(GradParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const GradWarp w = grad_warp(smem, p.warp_bytes, p.Lmax, p.K, p.gtape, ONCHIP);
@@ -579,7 +675,7 @@ __global__ void grad_decode_batched_kernel(const __grid_constant__ GradBatch b) 
 // (problems ordered by cases per item x Lmax); problem q owns items
 // [item_begin_q, item_begin_q + P_q nchunks_q), chunk-major inside.
 template <bool ONCHIP>
-__global__ void __launch_bounds__(GWARPS * 32) grad_batched_kernel(const __grid_constant__ GradBatch b) {
+__global__ void __launch_bounds__(GWARPS * 32, GCTAS_PER_SM) grad_batched_kernel(const __grid_constant__ GradBatch b) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const GradWarp w = grad_warp(smem, b.warp_bytes, b.Lw, b.Kw, b.gtape, ONCHIP);

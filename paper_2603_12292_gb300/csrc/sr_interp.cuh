@@ -149,7 +149,22 @@ struct DecodeArgs {
   int cap_slots;            // programs that need more than this get NCODE_DEEP (<= max_slots)
   unsigned long long *deep_count;  // programs with NCODE_DEEP are counted here (or NULL)
   int fold;                 // 1: fold constant-only subtrees into one constant (evaluation only)
+  int adj_info;             // 1: mark what the adjoint sweep needs (INS_NOADJ / INS_SA / INS_TA)
 };
+
+// Instruction flags for the adjoint kernel (bits 28-30 of x; evaluation
+// ignores them).  A constant's derivative flows only through nodes whose
+// subtree reads a constant:
+//   INS_NOADJ  this operator's subtree reads no constant: the forward pass
+//              tapes nothing for it, and the reverse sweep jumps from it to
+//              the subtree's first instruction (a variable load, whose
+//              reverse restores the outer adjoint); the jump target is in y,
+//              or, for an operator fused with a variable (VADD ... VRDIV),
+//              in the slot-offset field
+//   INS_SA     (binary operator with a stack operand) the operand in the
+//              stack slot reads a constant: its adjoint is wanted
+//   INS_TA     the operand on top reads a constant: its adjoint is wanted
+constexpr uint32_t INS_NOADJ = 1u << 28, INS_SA = 1u << 29, INS_TA = 1u << 30;
 
 __device__ __forceinline__ bool is_term(int v) {
   const int c = tok_class(v);
@@ -188,6 +203,8 @@ static __device__ __noinline__ float fold_op(int v, float a, float b) {
 }
 
 constexpr uint8_t NEED_FOLDED = 0x80;  // need[] bit: the subtree reads only constants (folded)
+constexpr uint8_t NEED_HASC = 0x40;    // need[] bit: the subtree reads a constant (adjoint info)
+constexpr uint8_t NEED_COUNT = 0x3f;   // need[] bits: the stack need itself
 
 // Validation and scheduled decoding of program `prog` (one thread), reading
 // its tokens from `tok`, its constants from `crow` and using the scratch rows
@@ -234,6 +251,7 @@ __device__ inline void decode_one(const DecodeArgs &p, int prog, const uint8_t *
         need[t] = 1 | NEED_FOLDED;
         fval[t] = crow[v - TOK_CONST0];
       }
+      if (p.adj_info && cls == CLS_CONST) need[t] |= NEED_HASC;
       task[sp++] = (int16_t)t;
     } else if (cls == CLS_UNARY) {
       const int c = task[sp - 1];
@@ -253,8 +271,8 @@ __device__ inline void decode_one(const DecodeArgs &p, int prog, const uint8_t *
         need[t] = 1 | NEED_FOLDED;
         fval[t] = fold_op(v, fval[a], fval[b]);
       } else {
-        const int na = need[a] & 0x7f, nb = need[b] & 0x7f;
-        need[t] = (uint8_t)(na == nb ? na + 1 : (na > nb ? na : nb));
+        const int na = need[a] & NEED_COUNT, nb = need[b] & NEED_COUNT;
+        need[t] = (uint8_t)((na == nb ? na + 1 : (na > nb ? na : nb)) | ((need[a] | need[b]) & NEED_HASC));
       }
       task[sp - 1] = (int16_t)t;
     }
@@ -274,11 +292,27 @@ __device__ inline void decode_one(const DecodeArgs &p, int prog, const uint8_t *
     return with_operand(x, tok[node], crow, p.ldx);
   };
   auto is_leaf = [&](int node) { return is_term(tok[node]) || (need[node] & NEED_FOLDED) != 0; };
+  // adjoint info: the first instruction of every subtree (fval's storage,
+  // unused without folding) and the flags of an operator instruction
+  int32_t *first_ins = reinterpret_cast<int32_t *>(fval);
+  auto adj = [&](uint2 w, int node, bool fused_var, int slot_op, int top_op) -> uint2 {
+    if (!p.adj_info) return w;
+    if (!(need[node] & NEED_HASC)) {
+      w.x |= INS_NOADJ;
+      if (fused_var) w.x = (w.x & ~(0xffffu << 8)) | ((uint32_t)first_ins[node] << 8);
+      else w.y = (uint32_t)first_ins[node];
+      return w;
+    }
+    if (slot_op >= 0 && (need[slot_op] & NEED_HASC)) w.x |= INS_SA;
+    if (top_op >= 0 && (need[top_op] & NEED_HASC)) w.x |= INS_TA;
+    return w;
+  };
   while (sp > 0) {
     const int e = task[sp - 1];
     const int node = e >> 2, ph = e & 3;
     const int v = tok[node];
     const int cls = is_leaf(node) ? (tok_class(v) == CLS_VAR ? CLS_VAR : CLS_CONST) : tok_class(v);
+    if (p.adj_info && ph == 0) first_ins[node] = n;
     if (cls == CLS_VAR || cls == CLS_CONST) {
       --sp;
       if (d > p.max_slots) {  // cannot happen for programs of <= Lmax tokens; never write past the slots
@@ -298,11 +332,12 @@ __device__ inline void decode_one(const DecodeArgs &p, int prog, const uint8_t *
         task[sp++] = (int16_t)((node - 1) << 2);
       } else {
         --sp;
-        code[n++] = make_uint2((uint32_t)(OP_SIN + (v - TOK_SIN)), 0u);
+        code[n] = adj(make_uint2((uint32_t)(OP_SIN + (v - TOK_SIN)), 0u), node, false, -1, node - 1);
+        ++n;
       }
     } else {
       const int b = node - 1, a = start[b] - 1;
-      const bool rev = (need[b] & 0x7f) > (need[a] & 0x7f);
+      const bool rev = (need[b] & NEED_COUNT) > (need[a] & NEED_COUNT);
       const int first = rev ? b : a, second = rev ? a : b;
       if (ph == 0) {
         task[sp - 1] = (int16_t)(e | 1);
@@ -314,7 +349,8 @@ __device__ inline void decode_one(const DecodeArgs &p, int prog, const uint8_t *
         if (rev && v == TOK_SUB) op = var ? OP_VRSUB : OP_CRSUB;
         else if (rev && v == TOK_DIV) op = var ? OP_VRDIV : OP_CRDIV;
         else op = (uint32_t)((var ? OP_VADD : OP_CADD) + v);  // + and * commute exactly
-        code[n++] = operand(op, second);
+        code[n] = adj(operand(op, second), node, var, -1, first);
+        ++n;
       } else if (ph == 1) {
         task[sp - 1] = (int16_t)((e & ~3) | 2);
         task[sp++] = (int16_t)(second << 2);
@@ -324,7 +360,8 @@ __device__ inline void decode_one(const DecodeArgs &p, int prog, const uint8_t *
         if (rev && v == TOK_SUB) op = OP_RSUB;
         else if (rev && v == TOK_DIV) op = OP_RDIV;
         else op = (uint32_t)(OP_ADD + v);
-        code[n++] = make_uint2(op | ((uint32_t)((d - 2) * p.slot_bytes) << 8), 0u);
+        code[n] = adj(make_uint2(op | ((uint32_t)((d - 2) * p.slot_bytes) << 8), 0u), node, false, first, second);
+        ++n;
         --d;
       }
     }

@@ -37,6 +37,33 @@ def test_closed_form_linear_program(ctx):
     assert mse[0] == pytest.approx(np.mean((float(c[0, 0]) * x - yy) ** 2), rel=1e-5)
 
 
+def test_gradient_constant_free_subtrees(ctx):
+    """Subtrees that read no constant carry no adjoint: the forward sweep
+    tapes nothing for them and the reverse sweep jumps over them.  Programs
+    with such subtrees in every position (first or second operand, under a
+    unary operator, fused with a variable, the whole program) against the
+    oracle's forward-mode gradient."""
+    rng = np.random.default_rng(17)
+    N = 2051
+    X = inputs.random_X(rng, 3, N, 1.0, 3.0)
+    y = rng.normal(size=N).astype(np.float32)
+    texts = ["x0 x1 * sin c0 *", "c0 x0 x1 + sin *", "x0 x1 / c0 x2 * -", "x0 sin x1 cos * c0 c1 x2 * + /",
+             "x0 x1 x2 * + x0 /", "x2 x0 x1 - / c1 x0 exp * +", "c0 x0 x1 * x2 + sqrt / c1 -",
+             "x0 x1 x2 + / c0 /", "c0 x1 / x0 x2 / x1 x2 * / +", "x0 sq x1 sq + c0 c1 x2 * - *",
+             "c2 x0 x1 x2 * * x0 / -", "x0 x1 - sq c0 x2 / x1 x0 / x2 x2 * - * +"]
+    progs, lens = pack([parse(t) for t in texts], 16)
+    c = rng.uniform(0.5, 2.0, (len(texts), 3)).astype(np.float32)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    mse_g, g_g = binding.sr_eval_grad(ctx, t(progs), t(lens), t(c), t(X), t(y), N)
+    mse_g, g_g = mse_g.cpu().numpy(), g_g.cpu().numpy()
+    mse_o, g_o, kink, gabs = oracle.grad(progs, lens, c, X, y, N)
+    assert (kink > 1e-2).all()
+    assert g_g[4].tolist() == [0.0, 0.0, 0.0]  # no constant at all
+    bad = ~(np.abs(g_g - g_o) <= 2e-4 * gabs + 1e-12)
+    assert not bad.any(), (np.argwhere(bad), g_g[bad], g_o[bad])
+    np.testing.assert_allclose(mse_g, mse_o, rtol=1e-5)
+
+
 def test_gradient_table1_operators(ctx):
     """The adjoint through 1/x, tan, asin, acos, atan and tanh against the
     oracle's forward mode on well-conditioned programs away from poles,

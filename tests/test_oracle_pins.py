@@ -480,6 +480,26 @@ def test_tiny_outputs_flag_the_correlation_sums():
     assert cf[0] & oracle.CF_FITRANGE and cf[1] == 0
 
 
+def test_top_fraction_tie_rule():
+    """The top-1 % rule on hand vectors: identical order agrees; a swap of
+    two programs farther apart than their slacks disagrees, one within them
+    is a tie; an outsider entering the top set disagrees."""
+    f = np.array([1.0, 2.0, 3.0, 4.0, 100.0])
+    tol = np.full(5, 0.01)
+    assert oracle.top_fraction_agree(f, f, tol, 0.6)
+    g = f.copy()
+    g[0], g[1] = 2.0, 1.0
+    assert not oracle.top_fraction_agree(g, f, tol, 0.6)
+    assert oracle.top_fraction_agree(g, f, np.full(5, 0.6), 0.6)
+    g = f.copy()
+    g[4] = 0.5
+    assert not oracle.top_fraction_agree(g, f, tol, 0.6)
+    assert oracle.top_fraction_agree(g, f, np.array([0.01] * 4 + [np.inf]), 0.6)  # an unbounded slack
+    rep = oracle.parity_report(oracle.CORR, f * (1 + 1e-9), f, np.zeros(5), np.zeros(5), np.zeros(5, np.int32),
+                               np.arange(5.0))
+    assert rep["n_certified"] == 5 and rep["top1_agree"] and rep["max_rel_tol"] < 1e-3
+
+
 def test_gradient_certificate_closed_form():
     """grad_cert: the same MSE, gradient and gabs as grad(); for yhat = c0 x0
     the output's reach is u |yhat| (1 + 1/16) on every case (one rounding,
