@@ -48,13 +48,13 @@ KERNEL_SOURCES = {
 # workload, and for another size only where it grows with the units (scale).
 KERNEL_NCU = {
     # eval_kernel<MODE_BOTH> on the headline workload, inputs read once
-    "paper": {"workload": "paper-4096x100k", "dram_bytes": 7.98e6 + 0.76e6, "units": None,
-              "issue_active": 0.852, "scale": False, "sources": "eval",
-              "capture": "profiles/eval_kernel_paper-4096x100k.md", "src": None},
+    "paper": {"workload": "paper-4096x100k", "dram_bytes": 7.863e6 + 0.799e6, "units": None,
+              "issue_active": 0.833, "scale": False, "sources": "eval",
+              "capture": "profiles/eval_kernel_paper-4096x100k.md", "src": "a152560518dd8eb8"},
     # grad_kernel: the tape write-back evicted from L2 grows with the units
-    "grad": {"workload": "adjoint-2048x131072", "dram_bytes": 7.589e9 + 23.968e9, "units": 1.3324e10,
-             "issue_active": 0.723, "scale": True, "sources": "grad",
-             "capture": "profiles/grad_kernel_adjoint-2048x131072.md", "src": None},
+    "grad": {"workload": "adjoint-2048x131072", "dram_bytes": 3.383e9 + 17.207e9, "units": 1.3324e10,
+             "issue_active": 0.698, "scale": True, "sources": "grad",
+             "capture": "profiles/grad_kernel_adjoint-2048x131072.md", "src": "6ba6f75eda4b69ed"},
     # eval_kernel<R4>: inputs read once (L2-resident), at the full size
     "beagle": {"workload": "beagle-4096x100k", "dram_bytes": 7.27e6 + 0.80e6, "units": 2.3977e10,
                "issue_active": 0.760, "scale": False, "sources": "eval",

@@ -255,54 +255,6 @@ __device__ __noinline__ VD fwd_ext(uint32_t op, VG x) {
   }
   return r;
 }
-// one out-of-line entry for the value and local derivative of any unary
-// operator (the forward sweep's tape entry)
-__device__ __noinline__ VD fwd_unary(uint32_t op, VG x) {
-  switch (op) {
-    case OP_SIN: return fwd_sin(x);
-    case OP_COS: return fwd_cos(x);
-    case OP_EXP: return fwd_exp(x);
-    case OP_LOG: return fwd_log(x);
-    case OP_SQRT: return fwd_sqrt(x);
-    case OP_SQ: {
-      VD r;
-#pragma unroll
-      for (int i = 0; i < GCPL; ++i) {
-        r.d.v[i] = x.v[i] + x.v[i];
-        r.v.v[i] = x.v[i] * x.v[i];
-      }
-      return r;
-    }
-    default: return fwd_ext(op, x);
-  }
-}
-// the value alone (a node whose subtree reads no constant), by the
-// interpreter's FP32 operators
-__device__ __noinline__ VG val_unary(uint32_t op, VG x) {
-  VG r;
-#pragma unroll 1
-  for (int i = 0; i < GCPL; ++i) {
-    const float a = x.v[i];
-    float v;
-    switch (op) {
-      case OP_SIN: v = f_sin(a); break;
-      case OP_COS: v = f_cos(a); break;
-      case OP_EXP: v = op_exp(a); break;
-      case OP_LOG: v = op_log(a); break;
-      case OP_SQRT: v = f_sqrt(a); break;
-      case OP_SQ: v = a * a; break;
-      case OP_INV: v = op_inv(a); break;
-      case OP_TAN: v = f_tan(a); break;
-      case OP_ASIN: v = f_asin(a); break;
-      case OP_ACOS: v = f_acos(a); break;
-      case OP_ATAN: v = f_atan(a); break;
-      default: v = f_tanh(a); break;
-    }
-    r.v[i] = v;
-  }
-  return r;
-}
-
 // protected quotient (the interpreter's operator)
 __device__ __noinline__ VG pdivg(VG a, VG b) {
   VG r;
@@ -445,26 +397,21 @@ __device__ __forceinline__ void grad_item(const GradParams &p, int c, int prog, 
           T = pdivg(T, b);
           if (ins.x & INS_SA) push(T);
         } break;
-        case OP_SIN:
-        case OP_COS:
-        case OP_EXP:
-        case OP_LOG:
-        case OP_SQRT:
-        case OP_SQ:
+        // a unary operator with no constant below (INS_NOADJ) tapes nothing;
+        // its local derivative is computed all the same: one code path per
+        // operator keeps the loop inside the instruction cache
+        case OP_SIN: { const VD r = fwd_sin(T); if (!(ins.x & INS_NOADJ)) push(r.d); T = r.v; } break;
+        case OP_COS: { const VD r = fwd_cos(T); if (!(ins.x & INS_NOADJ)) push(r.d); T = r.v; } break;
+        case OP_EXP: { const VD r = fwd_exp(T); if (!(ins.x & INS_NOADJ)) push(r.d); T = r.v; } break;
+        case OP_LOG: { const VD r = fwd_log(T); if (!(ins.x & INS_NOADJ)) push(r.d); T = r.v; } break;
+        case OP_SQRT: { const VD r = fwd_sqrt(T); if (!(ins.x & INS_NOADJ)) push(r.d); T = r.v; } break;
+        case OP_SQ: if (!(ins.x & INS_NOADJ)) push(addg(T, T)); T = mulg(T, T); break;
         case OP_INV:
         case OP_TAN:
         case OP_ASIN:
         case OP_ACOS:
         case OP_ATAN:
-        case OP_TANH:
-          if (ins.x & INS_NOADJ) {
-            T = val_unary(ins_op(ins), T);  // no constant below: the value alone
-          } else {
-            const VD r = fwd_unary(ins_op(ins), T);
-            push(r.d);
-            T = r.v;
-          }
-          break;
+        case OP_TANH: { const VD r = fwd_ext(ins_op(ins), T); if (!(ins.x & INS_NOADJ)) push(r.d); T = r.v; } break;
         case OP_VADD: T = addg(T, ldxg(xr, ins.y)); break;
         case OP_VSUB: T = subg(T, ldxg(xr, ins.y)); break;
         case OP_VRSUB: T = subg(ldxg(xr, ins.y), T); break;

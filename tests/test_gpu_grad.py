@@ -56,10 +56,10 @@ def test_gradient_constant_free_subtrees(ctx):
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     mse_g, g_g = binding.sr_eval_grad(ctx, t(progs), t(lens), t(c), t(X), t(y), N)
     mse_g, g_g = mse_g.cpu().numpy(), g_g.cpu().numpy()
-    mse_o, g_o, kink, gabs = oracle.grad(progs, lens, c, X, y, N)
-    assert (kink > 1e-2).all()
+    mse_o, g_o, gabs, gerr, nb, nl = oracle.grad_cert(progs, lens, c, X, y, N)
+    assert (nb == 0).all() and (nl == 0).all()
     assert g_g[4].tolist() == [0.0, 0.0, 0.0]  # no constant at all
-    bad = ~(np.abs(g_g - g_o) <= 2e-4 * gabs + 1e-12)
+    bad = ~(np.abs(g_g - g_o) <= _grad_tol(gabs, gerr))
     assert not bad.any(), (np.argwhere(bad), g_g[bad], g_o[bad])
     np.testing.assert_allclose(mse_g, mse_o, rtol=1e-5)
 
