@@ -56,17 +56,17 @@ KERNEL_NCU = {
              "issue_active": 0.698, "scale": True, "sources": "grad",
              "capture": "profiles/grad_kernel_adjoint-2048x131072.md", "src": "6ba6f75eda4b69ed"},
     # eval_kernel<R4>: inputs read once (L2-resident), at the full size
-    "beagle": {"workload": "beagle-4096x100k", "dram_bytes": 7.27e6 + 0.80e6, "units": 2.3977e10,
-               "issue_active": 0.760, "scale": False, "sources": "eval",
-               "capture": "profiles/eval_kernel_r4_beagle-4096x100k.md", "src": None},
+    "beagle": {"workload": "beagle-4096x100k", "dram_bytes": 7.120e6 + 0.844e6, "units": 2.3977e10,
+               "issue_active": 0.732, "scale": False, "sources": "eval",
+               "capture": "profiles/eval_kernel_r4_beagle-4096x100k.md", "src": "a152560518dd8eb8"},
     # eval_batched_kernel: the first 8 problems; inputs read once
-    "batched": {"workload": "batched-8", "dram_bytes": 45.01e6 + 1.31e6, "units": 4.0723e11,
-                "issue_active": 0.833, "scale": False, "sources": "eval",
-                "capture": "profiles/eval_batched_kernel_batched-8.md", "src": None},
+    "batched": {"workload": "batched-8", "dram_bytes": 41.558e6 + 0.901e6, "units": 4.0723e11,
+                "issue_active": 0.814, "scale": False, "sources": "eval",
+                "capture": "profiles/eval_batched_kernel_batched-8.md", "src": "a152560518dd8eb8"},
     # eval_kernel<CORR> at Lmax 256: inputs read once
-    "large": {"workload": "large-16384x131072", "dram_bytes": 21.32e6 + 0.66e6, "units": 2.5087e11,
-              "issue_active": 0.822, "scale": False, "sources": "eval",
-              "capture": "profiles/eval_kernel_corr_large-16384x131072.md", "src": None},
+    "large": {"workload": "large-16384x131072", "dram_bytes": 20.052e6 + 0.662e6, "units": 2.5087e11,
+              "issue_active": 0.813, "scale": False, "sources": "eval",
+              "capture": "profiles/eval_kernel_corr_large-16384x131072.md", "src": "a152560518dd8eb8"},
 }
 
 
