@@ -60,10 +60,7 @@ constexpr int GTARGET_ITEMS_PER_WARP = 24;
 // tape wholly in the scratch instead of its first 2 entries in shared memory
 // (no per-access choice) 831.  4 cases per lane (the dispatch of each
 // instruction shared by twice the cases) 980; 8 per lane 371.
-#ifndef SR_GRAD_CTAS
-#define SR_GRAD_CTAS (GCPL == 2 ? 6 : 5)
-#endif
-constexpr int GCTAS_PER_SM = SR_GRAD_CTAS;
+constexpr int GCTAS_PER_SM = GCPL == 2 ? 6 : 5;
 
 struct GradParams {
   const uint8_t *programs;
