@@ -30,7 +30,7 @@
  *   any other byte is invalid.  A binary op pops b, then a, and pushes a op b
  *   ("x0 x1 -" computes x0 - x1).  Operator readings (the paper lists the
  *   operators but not their domains):
- *     a DIV b   = a / b      if |b| > 1e-3, else 1
+ *     a DIV b   = a / b      if |b| > 1e-3, else 1 (quotient within 2 ulp)
  *     LOG x     = log|x|     if |x| > 1e-3, else 0
  *     SQRT x    = sqrt(|x|)
  *     EXP x     = exp(min(max(x, -80), 80))

@@ -30,9 +30,20 @@ __host__ __device__ inline int slots_for(int Lmax) {
 }
 
 // ---------------------------------------------------------------- operators (FP32)
+// The quotient by PTX div.full.f32 (full range, at most 2 ulp off: within the
+// 2-ulp allowance the oracle's enclosure gives every operation), with the
+// IEEE quotient where that result would be subnormal or zero (div.full may
+// flush there).  Measured: +12 % on the paper-shaped population, whose loop
+// also fits the instruction cache better with the shorter quotient.
+static __device__ __noinline__ float fdiv_ieee(float a, float b) { return a / b; }  // one copy
+__device__ __forceinline__ float fdiv_full(float a, float b) {
+  float q;
+  asm("div.full.f32 %0, %1, %2;" : "=f"(q) : "f"(a), "f"(b));
+  return fabsf(q) < 1.17549435e-38f ? fdiv_ieee(a, b) : q;
+}
 __device__ __forceinline__ float op_div(float a, float b) {
   // |b| < 1e-3f in FP32 is exactly "|b| <= 1e-3" for FP32 values of b
-  return fabsf(b) < 1e-3f ? 1.0f : a / b;
+  return fabsf(b) < 1e-3f ? 1.0f : fdiv_full(a, b);
 }
 __device__ __forceinline__ float op_log(float x) {
   return fabsf(x) < 1e-3f ? 0.0f : logf(fabsf(x));
