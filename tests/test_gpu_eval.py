@@ -282,6 +282,43 @@ def test_programs_beyond_the_main_pass_slots(ctx):
                 assert abs(s[p] - want) <= 1e-4 * 1000 * n, (p, s[p], want)
 
 
+def test_protected_division_accuracy(ctx):
+    """The device quotient: within 2 ulp of the correctly rounded FP32 quotient
+    (numpy) on normal results, exactly it where the result is subnormal or a
+    nonzero dividend gives zero, 1 where |b| <= 1e-3, and exact zeros from a
+    zero dividend."""
+    rng = np.random.default_rng(23)
+    n = 4096
+    a = np.concatenate([rng.uniform(-50, 50, n // 2), rng.choice([1e-39, -3e-40, 5e-36, 1e-30, 0.0], n // 2)])
+    b = np.concatenate([rng.choice([1.5e-3, -2e-3, 7.0, -3e2, 1e6, 1e30, 3e37], n // 2),
+                        rng.choice([1.5e-3, 3.0, -1e3, 1e8, 2e38, 5e-4], n // 2)])
+    X = np.stack([a, b]).astype(np.float32)
+    progs, lens = pack([parse("x0 x1 /"), parse("x1 x0 x1 / /")], 8)
+    d = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in
+         (("p", progs), ("l", lens), ("X", X))}
+    out = binding.sr_predict(ctx, d["p"], d["l"], None, d["X"], n).cpu().numpy()
+    xa, xb = X[0], X[1]
+
+    def pdiv(u, v):
+        with np.errstate(all="ignore"):
+            return np.where(np.abs(v) < np.float32(1e-3), np.float32(1.0), u / v).astype(np.float32)
+
+    # one quotient: within 2 ulp, exact where subnormal or zero; a quotient of a
+    # quotient: the inner one's 2 ulp carry through (within 5 ulp)
+    for row, want, k in ((0, pdiv(xa, xb), 2), (1, pdiv(xb, pdiv(xa, xb)), 5)):
+        got = out[row]
+        fin = np.isfinite(want)
+        assert np.array_equal(fin, np.isfinite(got)), row
+        tiny = fin & (np.abs(want) < np.float32(1.17549435e-38))
+        if row == 0:
+            assert (got[tiny] == want[tiny]).all()  # subnormal results and zeros, exactly
+        norm = fin & ~tiny
+        ulp = np.spacing(np.abs(want[norm]).astype(np.float32))
+        assert (np.abs(got[norm].astype(np.float64) - want[norm]) <= k * ulp).all(), row
+    assert (out[0][np.abs(xb) < 1e-3] == 1.0).all()
+    assert ((np.abs(out[0]) < 1.17549435e-38) & (out[0] != 0)).sum() > 100  # subnormal results were tested
+
+
 def test_constant_and_single_token_programs(ctx):
     progs, lens = pack([parse("c0"), parse("x1"), parse("c0 sin c1 *")], 4)
     c = np.array([[2.5, -1.0]] * 3, np.float32)
