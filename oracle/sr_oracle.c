@@ -212,7 +212,7 @@ static double eval_case(const uint8_t *tok, int len, const double *c,
  * Every FP32 operator output is within a relative u of the exact operator
  * applied to its FP32 operands (u = 2^-22 covers correctly rounded arithmetic
  * and library functions accurate to 2 ulp; tan, asin, acos, atan and tanh
- * are allowed 4u), plus 2^-149 absolute for
+ * are allowed 4u), plus 2^-148 absolute (2 ulp of the subnormal spacing) for
  * subnormal results.  Inputs and constants are exact.  Evaluating the program
  * on intervals -- each operator's exact range over its operand intervals,
  * widened by that rounding -- therefore encloses the FP32 result of every
@@ -222,7 +222,7 @@ typedef struct {
   double lo, hi;
 } ival;
 
-#define SUBNORMAL_SLACK 1.401298464324817e-45 /* 2^-149 */
+#define SUBNORMAL_SLACK 2.802596928649634e-45 /* 2^-148: 2 ulp of the subnormal spacing */
 
 static ival iv(double lo, double hi) {
   ival r = {lo, hi};

@@ -264,21 +264,11 @@ __device__ __noinline__ V8 cos8s(V8 v) { return map8_base_small(v, FCos()); }
 __device__ __noinline__ V8 exp8s(V8 v) { return map8_base_small(v, FExp()); }
 __device__ __noinline__ V8 log8s(V8 v) { return map8_base_small(v, FLog()); }
 __device__ __noinline__ V8 sqrt8s(V8 v) { return map8_base_small(v, FSqrt()); }
-// the eight quotients by op_div, for the values op_div_fast marked
-__device__ __noinline__ V8 div8_redo(V8 a, V8 b) {
-  float x[8] = {a.a.x, a.a.y, a.a.z, a.a.w, a.b.x, a.b.y, a.b.z, a.b.w};
-  const float y[8] = {b.a.x, b.a.y, b.a.z, b.a.w, b.b.x, b.b.y, b.b.z, b.b.w};
-#pragma unroll 1
-  for (int i = 0; i < 8; ++i) x[i] = op_div(x[i], y[i]);
-  return V8{make_float4(x[0], x[1], x[2], x[3]), make_float4(x[4], x[5], x[6], x[7])};
-}
 __device__ __noinline__ V8 div8s(V8 a, V8 b) {
   float x[8] = {a.a.x, a.a.y, a.a.z, a.a.w, a.b.x, a.b.y, a.b.z, a.b.w};
   const float y[8] = {b.a.x, b.a.y, b.a.z, b.a.w, b.b.x, b.b.y, b.b.z, b.b.w};
-  bool redo = false;
 #pragma unroll 2
-  for (int i = 0; i < 8; ++i) x[i] = op_div_fast(x[i], y[i], redo);
-  if (redo) return div8_redo(a, b);
+  for (int i = 0; i < 8; ++i) x[i] = op_div(x[i], y[i]);
   return V8{make_float4(x[0], x[1], x[2], x[3]), make_float4(x[4], x[5], x[6], x[7])};
 }
 __device__ __noinline__ V8 ext8(uint32_t op, V8 v) {
@@ -294,10 +284,8 @@ __device__ __noinline__ V8 ext8(uint32_t op, V8 v) {
 __device__ __noinline__ V8 div8(V8 a, V8 b) {
   float x[8] = {a.a.x, a.a.y, a.a.z, a.a.w, a.b.x, a.b.y, a.b.z, a.b.w};
   const float y[8] = {b.a.x, b.a.y, b.a.z, b.a.w, b.b.x, b.b.y, b.b.z, b.b.w};
-  bool redo = false;
 #pragma unroll MATH_UNROLL
-  for (int i = 0; i < 8; ++i) x[i] = op_div_fast(x[i], y[i], redo);
-  if (redo) return div8_redo(a, b);
+  for (int i = 0; i < 8; ++i) x[i] = op_div(x[i], y[i]);
   return V8{make_float4(x[0], x[1], x[2], x[3]), make_float4(x[4], x[5], x[6], x[7])};
 }
 #define SIN8(v) sin8(v)

@@ -256,18 +256,11 @@ __device__ __noinline__ VD fwd_ext(uint32_t op, VG x) {
   return r;
 }
 // protected quotient (the interpreter's operator)
-__device__ __noinline__ VG pdivg_redo(VG a, VG b) {
-  VG r;
-#pragma unroll 1
-  for (int i = 0; i < GCPL; ++i) r.v[i] = op_div(a.v[i], b.v[i]);
-  return r;
-}
 __device__ __noinline__ VG pdivg(VG a, VG b) {
   VG r;
-  bool redo = false;
 #pragma unroll
-  for (int i = 0; i < GCPL; ++i) r.v[i] = op_div_fast(a.v[i], b.v[i], redo);
-  return redo ? pdivg_redo(a, b) : r;
+  for (int i = 0; i < GCPL; ++i) r.v[i] = op_div(a.v[i], b.v[i]);
+  return r;
 }
 // adjoint through a protected quotient: a / den, 0 where the fallback was taken
 __device__ __forceinline__ float qdiv(float a, float d) { return fabsf(d) < 1e-3f ? 0.0f : a / d; }

@@ -283,10 +283,9 @@ def test_programs_beyond_the_main_pass_slots(ctx):
 
 
 def test_protected_division_accuracy(ctx):
-    """The device quotient: within 2 ulp of the correctly rounded FP32 quotient
-    (numpy) on normal results, exactly it where the result is subnormal or a
-    nonzero dividend gives zero, 1 where |b| <= 1e-3, and exact zeros from a
-    zero dividend."""
+    """The device quotient (PTX div.full.f32): within 2 ulp of the correctly
+    rounded FP32 quotient (numpy) on normal results and within 2 units of
+    2^-149 on subnormal ones and zeros, 1 where |b| <= 1e-3."""
     rng = np.random.default_rng(23)
     n = 4096
     a = np.concatenate([rng.uniform(-50, 50, n // 2), rng.choice([1e-39, -3e-40, 5e-36, 1e-30, 0.0], n // 2)])
@@ -303,15 +302,15 @@ def test_protected_division_accuracy(ctx):
         with np.errstate(all="ignore"):
             return np.where(np.abs(v) < np.float32(1e-3), np.float32(1.0), u / v).astype(np.float32)
 
-    # one quotient: within 2 ulp, exact where subnormal or zero; a quotient of a
-    # quotient: the inner one's 2 ulp carry through (within 5 ulp)
+    # one quotient: within 2 ulp (of the subnormal spacing 2^-149 below 2^-126);
+    # a quotient of a quotient: the inner one's 2 ulp carry through (within 5 ulp)
     for row, want, k in ((0, pdiv(xa, xb), 2), (1, pdiv(xb, pdiv(xa, xb)), 5)):
         got = out[row]
         fin = np.isfinite(want)
         assert np.array_equal(fin, np.isfinite(got)), row
         tiny = fin & (np.abs(want) < np.float32(1.17549435e-38))
         if row == 0:
-            assert (got[tiny] == want[tiny]).all()  # subnormal results and zeros, exactly
+            assert (np.abs(got[tiny].astype(np.float64) - want[tiny]) <= 2 * 2.0 ** -149).all()
         norm = fin & ~tiny
         ulp = np.spacing(np.abs(want[norm]).astype(np.float32))
         assert (np.abs(got[norm].astype(np.float64) - want[norm]) <= k * ulp).all(), row

@@ -246,8 +246,9 @@ def test_nonfinite_output_scores_worst():
 # ---------------------------------------------------------------- conditioning
 def test_interval_hand_values():
     """Interval enclosure of the FP32 output: inputs exact, each operator's
-    exact range over its operand intervals widened by u |v| + 2^-149."""
-    u, s = oracle.U_FP32, 2.0 ** -149
+    exact range over its operand intervals widened by u |v| + 2^-148 (2 ulp of
+    the subnormal spacing)."""
+    u, s = oracle.U_FP32, 2.0 ** -148
     w = lambda lo, hi: (lo - u * abs(lo) - s, hi + u * abs(hi) + s)
     a, b, c = 1.7, 2.9, -0.4
     x = np.array([[a], [b], [c], [math.pi / 2], [1e-3]])
