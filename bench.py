@@ -298,6 +298,10 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.warmup):
         generation()
     torch.cuda.synchronize()
+    # the population the timed generations start from: the end-to-end leg
+    # below runs the same generations again from it
+    start_rows = tuple(t.clone() for t in pop[state["cur"]])
+    start_gen = state["gen"]
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -348,8 +352,9 @@ def run_ours(args, rank, world, local_rank):
                 "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz ({src} max clock)"}
 
     # end to end through the public API with the population held on the host:
-    # H2D population, evaluate + select + vary, D2H children and fitness
-    P_, L_, C_ = pop[state["cur"]]
+    # H2D population, evaluate + select + vary, D2H children and fitness; the
+    # same generations as the timed region (same populations, same work)
+    P_, L_, C_ = start_rows
     h_prog = P_.cpu().pin_memory()
     h_len = L_.cpu().pin_memory()
     h_con = C_.cpu().pin_memory()
@@ -372,22 +377,25 @@ def run_ours(args, rank, world, local_rank):
         h_con.copy_(d_out[2], non_blocking=True)
         h_fit.copy_(fitness, non_blocking=True)
 
-    for _ in range(2):
-        e2e_step(state["gen"])
-        state["gen"] += 1
+    for _ in range(2):  # warm the copies, then start again from the same rows
+        e2e_step(start_gen)
     torch.cuda.synchronize()
+    h_prog.copy_(P_)
+    h_len.copy_(L_)
+    h_con.copy_(C_)
     e2e_ms = []
-    for _ in range(max(3, args.steps // 2)):
+    for i in range(args.steps):
         n_in = int(h_len.sum())
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        e2e_step(state["gen"])
+        e2e_step(start_gen + i)
         b.record(stream)
         b.synchronize()
-        state["gen"] += 1
         e2e_ms.append(a.elapsed_time(b))
         e2e_nodes.append(n_in)
+    if e2e_nodes != nodes:
+        raise RuntimeError("the end-to-end generations did not repeat the timed ones")
     e2e_units, e2e_total = float(sum(e2e_nodes)) * pr.N, float(sum(e2e_ms))
     if world > 1:
         e2e_total = shard.max_over_ranks(e2e_total, dev)
