@@ -48,25 +48,25 @@ KERNEL_SOURCES = {
 # workload, and for another size only where it grows with the units (scale).
 KERNEL_NCU = {
     # eval_kernel<MODE_BOTH> on the headline workload, inputs read once
-    "paper": {"workload": "paper-4096x100k", "dram_bytes": 7.863e6 + 0.799e6, "units": None,
-              "issue_active": 0.833, "scale": False, "sources": "eval",
-              "capture": "profiles/eval_kernel_paper-4096x100k.md", "src": "a152560518dd8eb8"},
+    "paper": {"workload": "paper-4096x100k", "dram_bytes": 7.956e6 + 0.783e6, "units": None,
+              "issue_active": 0.861, "scale": False, "sources": "eval",
+              "capture": "profiles/eval_kernel_paper-4096x100k.md", "src": "69dae9de910b1648"},
     # grad_kernel: the tape write-back evicted from L2 grows with the units
-    "grad": {"workload": "adjoint-2048x131072", "dram_bytes": 3.383e9 + 17.207e9, "units": 1.3324e10,
-             "issue_active": 0.698, "scale": True, "sources": "grad",
-             "capture": "profiles/grad_kernel_adjoint-2048x131072.md", "src": "6ba6f75eda4b69ed"},
+    "grad": {"workload": "adjoint-2048x131072", "dram_bytes": 4.465e9 + 18.138e9, "units": 1.3324e10,
+             "issue_active": 0.730, "scale": True, "sources": "grad",
+             "capture": "profiles/grad_kernel_adjoint-2048x131072.md", "src": "f1c4df115517482a"},
     # eval_kernel<R4>: inputs read once (L2-resident), at the full size
-    "beagle": {"workload": "beagle-4096x100k", "dram_bytes": 7.120e6 + 0.844e6, "units": 2.3977e10,
-               "issue_active": 0.732, "scale": False, "sources": "eval",
-               "capture": "profiles/eval_kernel_r4_beagle-4096x100k.md", "src": "a152560518dd8eb8"},
+    "beagle": {"workload": "beagle-4096x100k", "dram_bytes": 7.426e6 + 0.836e6, "units": 2.3977e10,
+               "issue_active": 0.854, "scale": False, "sources": "eval",
+               "capture": "profiles/eval_kernel_r4_beagle-4096x100k.md", "src": "69dae9de910b1648"},
     # eval_batched_kernel: the first 8 problems; inputs read once
     "batched": {"workload": "batched-8", "dram_bytes": 41.558e6 + 0.901e6, "units": 4.0723e11,
                 "issue_active": 0.814, "scale": False, "sources": "eval",
                 "capture": "profiles/eval_batched_kernel_batched-8.md", "src": "a152560518dd8eb8"},
     # eval_kernel<CORR> at Lmax 256: inputs read once
-    "large": {"workload": "large-16384x131072", "dram_bytes": 20.052e6 + 0.662e6, "units": 2.5087e11,
-              "issue_active": 0.813, "scale": False, "sources": "eval",
-              "capture": "profiles/eval_kernel_corr_large-16384x131072.md", "src": "a152560518dd8eb8"},
+    "large": {"workload": "large-16384x131072", "dram_bytes": 20.169e6 + 0.696e6, "units": 2.5087e11,
+              "issue_active": 0.837, "scale": False, "sources": "eval",
+              "capture": "profiles/eval_kernel_corr_large-16384x131072.md", "src": "69dae9de910b1648"},
 }
 
 

@@ -33,6 +33,18 @@ def dev(pr, y=None, device="cuda"):
     return d
 
 
+def compact_cases(X, y, keep):
+    """The cases where `keep` holds, as a fresh [nvars, ldx] float32 array
+    (ldx a multiple of 4, the padding a copy of the first kept case), their
+    targets y, and their count."""
+    n = int(keep.sum())
+    ldx = (n + 3) // 4 * 4
+    Xc = np.empty((X.shape[0], ldx), np.float32)
+    Xc[:, :n] = X[:, : len(keep)][:, keep]
+    Xc[:, n:] = Xc[:, :1]
+    return Xc, np.ascontiguousarray(y[: len(keep)][keep], dtype=np.float32), n
+
+
 def fitness_floor(kind, y):
     """Absolute floor of the fitness tolerance: 1e-7 var(y) for MSE, 1e-6 for 1 - r^2."""
     return oracle.fitness_floor(kind, y)

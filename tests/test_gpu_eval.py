@@ -9,7 +9,7 @@ import pytest
 import torch
 
 import oracle
-from helpers import check_fitness, dev, fitness_floor, target_problem, top_fraction_agree
+from helpers import check_fitness, compact_cases, dev, fitness_floor, target_problem, top_fraction_agree
 from paper_2603_12292_gb300 import binding, inputs
 from progtext import load_hand_cases, pack, parse
 
@@ -398,10 +398,17 @@ def test_full_size_large_sampled(ctx):
     """262,144 programs of length <= 256 x 1,000,000 cases (the large
     workload and its launch configuration), 1 - r^2: a sample stratified
     over the whole length range (12 programs from each of 4-16, 17-32,
-    33-64, 65-128 and 129-256 tokens) against the oracle on every case.  At
-    least half of the sample, and a third of the programs above 64 tokens,
-    must be certified and compared at 1e-4 relative + floor; the others
-    within tol + their bound unless FP32 cannot hold their values."""
+    33-64, 65-128 and 129-256 tokens) against the oracle on every case,
+    within tol + their bound unless FP32 cannot hold their values.
+
+    A program the oracle cannot certify over all 10^6 cases is usually held
+    back by a few cases where the first-order expansion is not trusted or a
+    branch could flip (flagged per case; their rigorous enclosures are wide).
+    Those cases are left out on their own: the program is run again, alone,
+    over its unflagged cases only (compacted into a fresh X and y) and
+    compared with the oracle's 1 - r^2 over the same cases.  Counting both
+    ways, at least half of the sample and half of the programs above 64
+    tokens must be certified and compared at 1e-4 relative + floor."""
     pr, y = target_problem(inputs.large)  # the usable target the bench uses (attempt 1)
     d = dev(pr, y)
     f = binding.sr_eval(ctx, d["programs"], d["lengths"], d["consts"], d["X"], d["y"], pr.N, binding.SR_CORR)
@@ -418,7 +425,32 @@ def test_full_size_large_sampled(ctx):
     rep = oracle.parity_report(k, f[idx], f0[k], errb[k], errp[k], cfl[k], y)
     tol = 1e-4 * np.abs(f0[k]) + 1e-6
     cert = (cfl[k] == 0) & (np.minimum(errb[k], errp[k]) <= 0.5 * tol) & np.isfinite(f0[k])
+    assert n == int(cert.sum())
+
+    def cases(i):
+        p = idx[i]
+        L = int(pr.lengths[p])
+        keep = oracle.first_order_cases(pr.programs[p, :L], pr.consts[p], pr.X, pr.N, raw=True)[4] == 0
+        if keep.sum() < pr.N // 2:
+            return i, None
+        Xc, yc, nc = compact_cases(pr.X, y, keep)
+        one = (pr.programs[p:p + 1], pr.lengths[p:p + 1], pr.consts[p:p + 1], Xc, yc, nc)
+        return i, (one, oracle.condition_fo(*one, nthreads=1))
+
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=16) as ex:
+        sub = dict(ex.map(cases, np.nonzero(~cert)[0]))
+    cert_sub = np.zeros(len(idx), bool)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    for i, r in sub.items():
+        if r is None:
+            continue
+        one, (eb, ep, cf, fo) = r
+        fc = binding.sr_eval(ctx, *[t(a) for a in one[:5]], one[5], binding.SR_CORR).cpu().numpy()
+        cert_sub[i] = check_fitness(k, fc, fo[k], eb[k], cf[k], one[4], errp=ep[k]) == 1
     long_ = pr.lengths[idx] > 64
-    print(rep, "certified above 64 tokens:", int((cert & long_).sum()), "of", int(long_.sum()))
-    assert n >= len(idx) // 2
-    assert (cert & long_).sum() >= long_.sum() // 3
+    both = cert | cert_sub
+    print(rep, f"certified on every case {int(cert.sum())}, on the unflagged cases {int(cert_sub.sum())}; "
+          f"above 64 tokens {int((cert & long_).sum())} + {int((cert_sub & long_).sum())} of {int(long_.sum())}")
+    assert both.sum() >= len(idx) // 2
+    assert (both & long_).sum() >= long_.sum() // 2
