@@ -60,9 +60,9 @@ KERNEL_NCU = {
                "issue_active": 0.854, "scale": False, "sources": "eval",
                "capture": "profiles/eval_kernel_r4_beagle-4096x100k.md", "src": "69dae9de910b1648"},
     # eval_batched_kernel: the first 8 problems; inputs read once
-    "batched": {"workload": "batched-8", "dram_bytes": 41.558e6 + 0.901e6, "units": 4.0723e11,
-                "issue_active": 0.814, "scale": False, "sources": "eval",
-                "capture": "profiles/eval_batched_kernel_batched-8.md", "src": "a152560518dd8eb8"},
+    "batched": {"workload": "batched-8", "dram_bytes": 41.654e6 + 0.929e6, "units": 4.0723e11,
+                "issue_active": 0.837, "scale": False, "sources": "eval",
+                "capture": "profiles/eval_batched_kernel_batched-8.md", "src": "69dae9de910b1648"},
     # eval_kernel<CORR> at Lmax 256: inputs read once
     "large": {"workload": "large-16384x131072", "dram_bytes": 20.169e6 + 0.696e6, "units": 2.5087e11,
               "issue_active": 0.837, "scale": False, "sources": "eval",

@@ -762,10 +762,33 @@ static double unary_curvature(int v, double x, double r, double val) {
  * the systematic part */
 static double fo_reach(double lam, double s2, double w1, double w) { return dmin(lam * sqrt(s2), w1) + w; }
 
-static double case_first_order(const uint8_t *tok, int len, const double *c, const double *X, long ldx,
-                               long i, double u, double lam, double *val, double *s2v, double *w1v,
-                               double *wv, double *s2, double *w1, double *w, int *cond) {
+/*
+ * Tangents for the gradient certificate (optional in case_first_order):
+ * per stack entry and constant k, t = dv/dc_k in FP64, a its bound with
+ * absolute partials, and ea a first-order bound on how far the tangent of
+ * an FP32 evaluation can lie from t because the local partials are taken at
+ * FP32 values, each within its reach of the FP64 one:
+ *     ea(y) = sum_children |p| ea(child) + dp (a(child) + ea(child)),
+ * dp the most the partial p can move while its operands move within their
+ * reaches (for f(x): max |f''| over the reach times the reach of x, i.e.
+ * twice the curvature term of unary_curvature times that reach; for a * b:
+ * the other operand's reach; for a / b, with m the least |b| over its
+ * reach: d(1/b) <= r_b / m^2 and d(a/b^2) <= r_a / m^2 + 2 (|a| + r_a) r_b /
+ * m^3).  The FP32 rounding of the tangent products themselves is not in ea
+ * (a relative error of a few u per operator along each path).  Arrays
+ * [(len + 1) K]; where a case is flagged CF_BRANCH or CF_NONLIN, ea is not
+ * meaningful.
+ */
+typedef struct {
+  int K;
+  double *t, *a, *ea;
+} tangents;
+
+static double case_first_order_t(const uint8_t *tok, int len, const double *c, const double *X, long ldx,
+                                 long i, double u, double lam, double *val, double *s2v, double *w1v,
+                                 double *wv, double *s2, double *w1, double *w, int *cond, const tangents *tg) {
   int sp = 0, cf = 0;
+  const int K = tg ? tg->K : 0;
   for (int t = 0; t < len; ++t) {
     int v = tok[t];
     if (is_var(v) || is_const(v)) {
@@ -773,6 +796,10 @@ static double case_first_order(const uint8_t *tok, int len, const double *c, con
       s2v[sp] = 0.0;
       w1v[sp] = 0.0;
       wv[sp] = 0.0;
+      for (int k = 0; k < K; ++k) {
+        tg->t[sp * K + k] = tg->a[sp * K + k] = (is_const(v) && k == v - TK_CONST0) ? 1.0 : 0.0;
+        tg->ea[sp * K + k] = 0.0;
+      }
       ++sp;
       continue;
     }
@@ -784,18 +811,35 @@ static double case_first_order(const uint8_t *tok, int len, const double *c, con
       double ra = fo_reach(lam, s2v[sp - 1], w1v[sp - 1], wv[sp - 1]);
       double rb = fo_reach(lam, s2v[sp], w1v[sp], wv[sp]);
       r = apply_binary(v, a, b);
-      double pa, pb, second = 0.0;
+      double pa, pb, second = 0.0, dpa = 0.0, dpb = 0.0;
       op_partials(v, a, b, r, &pa, &pb);
-      if (v == TK_MUL) second = ra * rb;
+      if (v == TK_MUL) {
+        second = ra * rb;
+        dpa = rb;
+        dpb = ra;
+      }
       if (v == TK_DIV) {
         double m = fabs(b) - rb;
         if (fabs(fabs(b) - PROTECT_EPS) <= rb) cf |= CF_BRANCH;
         if (!(m >= 0.9 * fabs(b) && m > 0.0)) cf |= CF_NONLIN;
-        else if (fabs(b) > PROTECT_EPS) second = (ra * rb + (fabs(a) + ra) * rb * rb / m) / (m * m);
+        else if (fabs(b) > PROTECT_EPS) {
+          second = (ra * rb + (fabs(a) + ra) * rb * rb / m) / (m * m);
+          dpa = rb / (m * m);
+          dpb = ra / (m * m) + 2.0 * (fabs(a) + ra) * rb / (m * m * m);
+        }
       }
       q2 = pa * pa * s2v[sp - 1] + pb * pb * s2v[sp];
       l1 = fabs(pa) * w1v[sp - 1] + fabs(pb) * w1v[sp];
       q1 = fabs(pa) * wv[sp - 1] + fabs(pb) * wv[sp] + second;
+      for (int k = 0; k < K; ++k) {
+        double *ta = tg->t + (sp - 1) * K, *tb = tg->t + sp * K;
+        double *aa = tg->a + (sp - 1) * K, *ab = tg->a + sp * K;
+        double *ea = tg->ea + (sp - 1) * K, *eb = tg->ea + sp * K;
+        double e = fabs(pa) * ea[k] + fabs(pb) * eb[k] + dpa * (aa[k] + ea[k]) + dpb * (ab[k] + eb[k]);
+        ta[k] = pa * ta[k] + pb * tb[k];
+        aa[k] = fabs(pa) * aa[k] + fabs(pb) * ab[k];
+        ea[k] = e;
+      }
     } else {
       double x = val[sp - 1];
       double rx = fo_reach(lam, s2v[sp - 1], w1v[sp - 1], wv[sp - 1]);
@@ -811,6 +855,15 @@ static double case_first_order(const uint8_t *tok, int len, const double *c, con
       q2 = pa * pa * s2v[sp - 1];
       l1 = fabs(pa) * w1v[sp - 1];
       q1 = fabs(pa) * wv[sp - 1] + (k > 0.0 && !flat ? k * rx * rx : 0.0);
+      /* the partial is 0 on a protected fallback and beyond the exp clamp */
+      int flat_p = flat || (v == TK_EXP && (x > EXP_CLAMP || x < -EXP_CLAMP));
+      double dp = (k > 0.0 && !flat_p) ? 2.0 * k * rx : 0.0;
+      for (int j = 0; j < K; ++j) {
+        double *tx = tg->t + (sp - 1) * K, *ax = tg->a + (sp - 1) * K, *ex = tg->ea + (sp - 1) * K;
+        ex[j] = fabs(pa) * ex[j] + dp * (ax[j] + ex[j]);
+        tx[j] = pa * tx[j];
+        ax[j] = fabs(pa) * ax[j];
+      }
     }
     val[sp - 1] = r;
     s2v[sp - 1] = q2 + (uv * r) * (uv * r);
@@ -825,6 +878,12 @@ static double case_first_order(const uint8_t *tok, int len, const double *c, con
   *w = wv[0];
   *cond |= cf;
   return val[0];
+}
+
+static double case_first_order(const uint8_t *tok, int len, const double *c, const double *X, long ldx,
+                               long i, double u, double lam, double *val, double *s2v, double *w1v,
+                               double *wv, double *s2, double *w1, double *w, int *cond) {
+  return case_first_order_t(tok, len, c, X, ldx, i, u, lam, val, s2v, w1v, wv, s2, w1, w, cond, NULL);
 }
 
 /* case_first_order and case_interval of one case (*lo, *hi: the rigorous
@@ -1436,11 +1495,13 @@ void or_grad_one(const uint8_t *tok, int len, const double *c, int K, const doub
  *            than 0.1): the device's local derivatives there carry errors
  *            the linear scale gabs does not bound, so such a program's
  *            gradient is not comparable either;
- *   gerr     [P][K] (2/N) sum_i reach_i a_ik: how far the output's FP32
- *            rounding (reach_i: the first-order analysis's bound on case i,
- *            or its rigorous enclosure where the expansion is not trusted)
- *            can move the gradient through e_i, with a_ik the derivative
- *            propagated with absolute partials.
+ *   gerr     [P][K] (2/N) sum_i (reach_i a_ik + (|e_i| + reach_i) ea_ik):
+ *            how far FP32 evaluation can move the gradient, through e_i
+ *            (reach_i: the first-order analysis's bound on the output of
+ *            case i, or its rigorous enclosure where the expansion is not
+ *            trusted; a_ik the derivative propagated with absolute partials)
+ *            and through the local partials, which the device takes at FP32
+ *            values (ea_ik: the tangent error bound of case_first_order_t).
  */
 void or_grad_cert(const uint8_t *programs, const int32_t *lengths, const float *consts, int P, int Lmax, int K,
                   const double *X, long ldx, const double *y, int nvars, long N, double u, double lam,
@@ -1453,6 +1514,10 @@ void or_grad_cert(const uint8_t *programs, const int32_t *lengths, const float *
     double *reach = (double *)malloc(sizeof(double) * nn);
     double *val = (double *)malloc(sizeof(double) * (size_t)(Lmax + 1) * 4);
     ival *box = (ival *)malloc(sizeof(ival) * (size_t)(Lmax + 1));
+    size_t nk = (size_t)(Lmax + 1) * (size_t)(K > 0 ? K : 1);
+    tangents tg = {K, (double *)malloc(sizeof(double) * nk), (double *)malloc(sizeof(double) * nk),
+                   (double *)malloc(sizeof(double) * nk)};
+    double *gpart = (double *)malloc(sizeof(double) * (size_t)(K > 0 ? K : 1));
 #pragma omp for schedule(dynamic, 1)
     for (int p = 0; p < P; ++p) {
       const uint8_t *tok = programs + (size_t)p * Lmax;
@@ -1468,26 +1533,34 @@ void or_grad_cert(const uint8_t *programs, const int32_t *lengths, const float *
       widen_consts(consts + (size_t)p * K, K, c);
       int len = lengths[p], nb = 0, nl = 0;
       size_t L = (size_t)len + 1;
+      for (int k = 0; k < K; ++k) gpart[k] = 0.0;
       for (long i = 0; i < N; ++i) {
         double s2, w1, w, lo, hi;
         int cf = 0;
-        case_first_order(tok, len, c, X, ldx, i, u, lam, val, val + L, val + 2 * L, val + 3 * L, &s2, &w1, &w,
-                         &cf);
+        double y0 = case_first_order_t(tok, len, c, X, ldx, i, u, lam, val, val + L, val + 2 * L, val + 3 * L,
+                                       &s2, &w1, &w, &cf, &tg);
         nb += (cf & CF_BRANCH) != 0;
         nl += (cf & CF_NONLIN) != 0;
+        /* the root's tangent error, weighed by |e_i| and its reach */
+        double e = fabs(y0 - y[i]);
         int ca = 0;
-        double y0 = case_analysis(tok, len, c, X, ldx, i, u, lam, val, box, &s2, &w1, &w, &lo, &hi, &ca);
-        (void)y0;
+        case_analysis(tok, len, c, X, ldx, i, u, lam, val, box, &s2, &w1, &w, &lo, &hi, &ca);
         reach[i] = fo_reach(lam, s2, w1, w);
+        for (int k = 0; k < K; ++k) gpart[k] += 2.0 * (e + reach[i]) * tg.ea[k];
       }
       nbranch[p] = nb;
       nnonlin[p] = nl;
       or_grad_one_ex(tok, len, c, K, X, ldx, y, N, &mse[p], grad + (size_t)p * K, NULL, gabs + (size_t)p * K,
                      reach, gerr + (size_t)p * K);
+      for (int k = 0; k < K; ++k) gerr[(size_t)p * K + k] += gpart[k] / (double)N;
     }
     free(reach);
     free(val);
     free(box);
+    free(tg.t);
+    free(tg.a);
+    free(tg.ea);
+    free(gpart);
   }
 }
 

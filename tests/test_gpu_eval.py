@@ -318,6 +318,51 @@ def test_protected_division_accuracy(ctx):
     assert ((np.abs(out[0]) < 1.17549435e-38) & (out[0] != 0)).sum() > 100  # subnormal results were tested
 
 
+def test_unary_operator_accuracy(ctx):
+    """Every unary operator's device output against the oracle's FP64 value of
+    the same operator on the same FP32 argument, within the per-operation
+    allowance the oracle's enclosure assumes: relative 2^-22 (2^-20 for tan,
+    asin, acos, atan, tanh) plus 2^-148 absolute; an exact value beyond the
+    FP32 range must come out as an infinity of its sign, a non-real one
+    (asin / acos outside [-1, 1]) as NaN.  Arguments: wide uniform and
+    log-uniform ranges, the large-argument path of sin / cos / tan, points
+    next to multiples of pi/2, and both sides of the protected branches
+    (|x| = 1e-3), the exp clamp (|x| = 80) and the asin / acos domain."""
+    rng = np.random.default_rng(29)
+    n = 1 << 16
+    sgn = lambda: rng.choice([-1.0, 1.0], n)
+    x = np.concatenate([rng.uniform(-10, 10, n), rng.uniform(-4e4, 4e4, n), rng.uniform(-1e6, 1e6, n),
+                        sgn() * 10.0 ** rng.uniform(-38, 38, n),
+                        rng.integers(-25000, 25000, n) * (np.pi / 2),
+                        sgn() * 1e-3 * (1 + rng.uniform(-1e-5, 1e-5, n)),
+                        sgn() * 80 * (1 + rng.uniform(-1e-5, 1e-5, n)),
+                        rng.uniform(-1.0001, 1.0001, n),
+                        [0.0, 1.0, -1.0, 1e-3, -1e-3, 80.0, -80.0, 1e38, -1e38, 1e-45, -1e-45]])
+    X = x.astype(np.float32)[None, :]
+    N = X.shape[1]
+    ldx = (N + 3) // 4 * 4
+    Xp = np.zeros((1, ldx), np.float32)
+    Xp[:, :N] = X
+    ops = ["sin", "cos", "exp", "log", "sqrt", "sq", "inv", "tan", "asin", "acos", "atan", "tanh"]
+    progs, lens = pack([parse("x0 " + o) for o in ops], 4)
+    d = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in (("p", progs), ("l", lens), ("X", Xp))}
+    out = binding.sr_predict(ctx, d["p"], d["l"], None, d["X"], N).cpu().numpy().astype(np.float64)
+    ovf = 2.0 ** 128 - 2.0 ** 103  # FP32 rounds to inf from here
+    for i, o in enumerate(ops):
+        want = oracle.predict(progs[i, :lens[i]], np.zeros(1), Xp, N)
+        got = out[i]
+        u = oracle.U_FP32 * (4.0 if o in ("tan", "asin", "acos", "atan", "tanh") else 1.0)
+        nan = np.isnan(want)
+        assert np.array_equal(nan, np.isnan(got)), (o, X[0][nan != np.isnan(got)][:5])
+        big = ~nan & (np.abs(want) >= ovf)
+        assert (np.isinf(got[big]) & (np.sign(got[big]) == np.sign(want[big]))).all(), o
+        fin = ~nan & ~big
+        err = np.abs(got[fin] - want[fin])
+        lim = u * np.abs(want[fin]) + 2.0 ** -148
+        worst = int(np.argmax(err / lim))
+        assert (err <= lim).all(), (o, float(X[0][fin][worst]), got[fin][worst], want[fin][worst])
+
+
 def test_constant_and_single_token_programs(ctx):
     progs, lens = pack([parse("c0"), parse("x1"), parse("c0 sin c1 *")], 4)
     c = np.array([[2.5, -1.0]] * 3, np.float32)

@@ -529,6 +529,120 @@ def test_gradient_certificate_closed_form():
     assert nb2[0] == 0 and nl2[0] > N // 2  # every case whose argument passes ~4e5
 
 
+def test_gradient_certificate_tangent_term():
+    """The device takes the local partials at FP32 values; grad_cert's gerr
+    adds (2/N) sum_i (|e_i| + reach_i) ea_i for that.  Closed form for
+    yhat = sin(x0 c0): the product's tangent x0 is exact (both operands are
+    exact), sin's partial cos(v) moves by at most the reach of v = x0 c0,
+    r1 = u |v| (1 + 1/16), so ea = r1 |x0|, and the output's reach is
+    min(lam sqrt(s2), w1) + w with s2 = cos(v)^2 (u v)^2 + (u sin v)^2, w1 =
+    |cos v| u |v| + u |sin v|, w = |cos v| u |v| / 16 + r1^2 / 2 + u |sin v| / 16."""
+    rng = np.random.default_rng(31)
+    N = 300
+    X = rng.uniform(1, 5, (1, N)).astype(np.float32)
+    y = rng.normal(size=N).astype(np.float32)
+    progs, lens = pack([parse("x0 c0 * sin")], 4)
+    c0 = 1.3
+    m, g, gabs, gerr, nb, nl = oracle.grad_cert(progs, lens, np.array([[c0]], np.float32), X, y)
+    u, lam = oracle.U_FP32, oracle.LAMBDA
+    x0 = X[0].astype(np.float64)
+    c = float(np.float32(c0))
+    v = x0 * c
+    r1 = u * np.abs(v) * (1 + 1 / 16)
+    s2 = np.cos(v) ** 2 * (u * v) ** 2 + (u * np.sin(v)) ** 2
+    w1 = np.abs(np.cos(v)) * u * np.abs(v) + u * np.abs(np.sin(v))
+    w = np.abs(np.cos(v)) * u * np.abs(v) / 16 + 0.5 * r1 ** 2 + u * np.abs(np.sin(v)) / 16
+    reach = np.minimum(lam * np.sqrt(s2), w1) + w
+    a = np.abs(np.cos(v)) * x0
+    ea = r1 * x0
+    e = np.abs(np.sin(v) - y.astype(np.float64))
+    want = 2.0 / N * np.sum(reach * a + (e + reach) * ea)
+    assert nb[0] == 0 and nl[0] == 0
+    assert gerr[0, 0] == pytest.approx(want, rel=1e-9)
+
+
+def _perturbed_gradient(tok, c, X, y, eps, rng):
+    """Forward-mode dMSE/dc in FP64 with every operator output multiplied by
+    (1 + eps d), d ~ U(-1, 1) independently per case and operator: the model
+    of FP32 rounding the certificate assumes (partials taken at the
+    perturbed values, tangent products exact)."""
+    N = X.shape[1]
+    K = len(c)
+    st = []
+    for t in tok:
+        t = int(t)
+        if 16 <= t < 32:
+            st.append((X[t - 16].astype(np.float64), np.zeros((K, N))))
+            continue
+        if t >= 32:
+            tg = np.zeros((K, N))
+            tg[t - 32] = 1.0
+            st.append((np.full(N, float(c[t - 32])), tg))
+            continue
+        if t < 4:
+            (b, tb), (a, ta) = st.pop(), st.pop()
+            if t == 0:
+                r, pa, pb = a + b, 1.0, 1.0
+            elif t == 1:
+                r, pa, pb = a - b, 1.0, -1.0
+            elif t == 2:
+                r, pa, pb = a * b, b, a
+            else:
+                prot = np.abs(b) <= 1e-3
+                q = np.where(prot, 1.0, a / np.where(prot, 1.0, b))
+                r, pa, pb = q, np.where(prot, 0.0, 1 / np.where(prot, 1.0, b)), np.where(prot, 0.0, -q / np.where(prot, 1.0, b))
+            tgn = pa * ta + pb * tb
+        else:
+            x, tx = st.pop()
+            if t == 4:
+                r, d = np.sin(x), np.cos(x)
+            elif t == 5:
+                r, d = np.cos(x), -np.sin(x)
+            elif t == 6:
+                r = np.exp(np.clip(x, -80, 80))
+                d = np.where(np.abs(x) > 80, 0.0, r)
+            elif t == 7:
+                prot = np.abs(x) <= 1e-3
+                r = np.where(prot, 0.0, np.log(np.where(prot, 1.0, np.abs(x))))
+                d = np.where(prot, 0.0, 1 / np.where(prot, 1.0, x))
+            elif t == 8:
+                r = np.sqrt(np.abs(x))
+                d = np.where(x == 0, 0.0, np.sign(x) * 0.5 / np.where(r == 0, 1.0, r))
+            else:
+                r, d = x * x, 2 * x
+            tgn = d * tx
+        st.append((r * (1 + eps * rng.uniform(-1, 1, N)), tgn))
+    yh, tg = st[0]
+    return 2.0 / N * np.sum((yh - y) * tg, axis=1)
+
+
+def test_gradient_certificate_bounds_perturbed_evaluations():
+    """Monte Carlo: every operator output moved within a relative u (the
+    certificate's model of FP32 rounding) moves the gradient by at most
+    gerr; the perturbed gradients of random programs of the base operators,
+    20 draws each, stay within it (2e-4 gabs is not needed here: the
+    tangent products are exact in this model)."""
+    rng = np.random.default_rng(33)
+    progs, lens = inputs.random_programs(rng, 40, 5, 24, 2, 2)
+    consts = rng.uniform(-2, 2, (40, 2)).astype(np.float32)
+    N = 150
+    X = rng.uniform(1, 3, (2, N)).astype(np.float32)
+    y = rng.normal(size=N).astype(np.float32)
+    m, g, gabs, gerr, nb, nl = oracle.grad_cert(progs, lens, consts, X, y)
+    errb, errp, cfl, f0 = oracle.condition_fo(progs, lens, consts, X, y)
+    ok = (nb == 0) & (nl == 0) & (cfl[0] == 0) & np.isfinite(f0[0])
+    assert ok.sum() >= 20
+    worst = 0.0
+    for j in np.nonzero(ok)[0]:
+        tok = progs[j, : lens[j]]
+        for _ in range(20):
+            gp = _perturbed_gradient(tok, consts[j].astype(np.float64), X, y.astype(np.float64), oracle.U_FP32, rng)
+            dev = np.abs(gp - g[j])
+            assert (dev <= gerr[j] * (1 + 1e-6) + 1e-300).all(), (j, dev, gerr[j])
+            worst = max(worst, float(np.max(dev / np.maximum(gerr[j], 1e-300))))
+    assert worst > 1e-3  # the perturbations do move the gradient
+
+
 # ---------------------------------------------------------------- gradient
 def test_gradient_closed_form():
     """yhat = c0 * x0: dMSE/dc0 = (2/N) sum (c0 x0 - y) x0."""
