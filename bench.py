@@ -152,17 +152,25 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines: list[str] = []
+        self.first = 0
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except OSError:
             self.proc = None
+            return
+        # the timed region starts once the sampler is live (nvidia-smi takes a
+        # moment to start), so that its samples fall inside the region
+        t0 = time.time()
+        while not self.lines and self.proc.poll() is None and time.time() - t0 < 3.0:
+            time.sleep(0.01)
+        self.first = len(self.lines)  # samples from here on fall inside the region
 
     def _read(self):
         for line in self.proc.stdout:
@@ -178,7 +186,8 @@ class ClockSampler:
             self.proc.kill()
         sm, smax, reasons, power = [], [], set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        inside = self.lines[self.first:]
+        for line in inside or self.lines:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
                 continue

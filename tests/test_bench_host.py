@@ -46,6 +46,21 @@ def test_clock_sampler_reports_thermal_and_hardware_slowdown():
     assert c["sm_mhz"] == 1450.0
 
 
+def test_clock_sampler_uses_the_samples_inside_the_region():
+    # the first line arrived before the timed region began (start() waits for
+    # it); only the later ones count, unless there are none
+    lines = ["0, 900, 2070, 150.0, 0x1, Not Active, Not Active, Not Active, Not Active",
+             "0, 2070, 2070, 700.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "0, 2050, 2070, 710.0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    s = _sampler(lines)
+    s.first = 1
+    c = s.stop()
+    assert c["samples"] == 2 and c["sm_mhz"] == 2060.0
+    s = _sampler(lines[:1])
+    s.first = 1
+    assert s.stop()["samples"] == 1
+
+
 def test_clock_sampler_without_nvidia_smi():
     s = bench.ClockSampler(0)
     assert s.stop()["reasons"] == ["nvidia-smi unavailable"]
