@@ -27,7 +27,7 @@ EXPORTS = ["sr_create", "sr_destroy", "sr_set_stream", "sr_status_string", "sr_l
            "sr_random_programs", "sr_eval_grad", "sr_adam_step", "sr_eval_batched", "sr_set_tile",
            "sr_eval_score", "sr_select_tournament_max", "sr_select_microcosm",
            "sr_set_generation_source", "sr_set_abort_flag", "sr_eval_grad_batched",
-           "sr_set_occupancy", "sr_adam_step_batched"]
+           "sr_set_occupancy", "sr_adam_step_batched", "sr_set_transforms"]
 
 _lib = None
 
@@ -125,6 +125,7 @@ def lib() -> ctypes.CDLL:
     L.sr_eval_batched.argtypes = [vp, ctypes.POINTER(Problem), i32]
     L.sr_set_tile.argtypes = [vp, i32]
     L.sr_set_occupancy.argtypes = [vp, i32, i32]
+    L.sr_set_transforms.argtypes = [vp, i32]
     L.sr_adam_step_batched.argtypes = [vp, ctypes.POINTER(AdamTable), i32, i32, ctypes.POINTER(AdamCfg)]
     L.sr_set_generation_source.argtypes = [vp, vp]
     L.sr_eval_grad_batched.argtypes = [vp, ctypes.POINTER(GradProblem), i32]
@@ -542,6 +543,16 @@ def sr_set_occupancy(ctx: Context, eval_ctas_per_sm: int = 0, batched_ctas_per_s
     """CTAs per SM of the single-problem (0, 4, 5) and batched (0, 3, 4, 5)
     evaluation kernels; 0 = automatic."""
     _check(ctx, lib().sr_set_occupancy(ctx.handle, eval_ctas_per_sm, batched_ctas_per_sm))
+
+
+XFORM_NEVER, XFORM_AUTO, XFORM_ALWAYS = 0, 1, 2
+
+
+def sr_set_transforms(ctx: Context, mode: int = XFORM_AUTO):
+    """Variable transforms of the single-problem evaluation: 0 never, 1
+    automatic (calls of at least 16,384 cases), 2 always.  Results are bit
+    for bit the same either way."""
+    _check(ctx, lib().sr_set_transforms(ctx.handle, mode))
 
 
 def make_problem(programs, lengths, consts, X, y, N: int, kind: int, fitness=None, prog_flags=None,

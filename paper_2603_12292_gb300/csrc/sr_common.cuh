@@ -21,6 +21,7 @@ struct sr_ctx {
   int tile_cases = 0;     // cases per evaluation work item (0: automatic)
   int eval_ctas = 0;      // CTAs per SM of the single-problem evaluation (0: automatic, 4, 5)
   int batched_ctas = 0;   // CTAs per SM of the batched evaluation (0: automatic = 4, 3, 4, 5)
+  int xform = 1;          // variable transforms of the evaluation: 0 never, 1 automatic, 2 always
   const uint64_t *gen_dev = nullptr;  // device generation counter for selection / variation
   const int32_t *abort_flag = nullptr;  // sr_set_abort_flag (device, or NULL)
 };

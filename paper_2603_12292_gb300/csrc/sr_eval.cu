@@ -50,6 +50,10 @@ constexpr int CPL = 8;          // cases per lane per dispatched instruction (tw
 constexpr int STEP = 32 * CPL;  // cases per warp step
 constexpr int SLOT_BYTES = 32 * CPL * 4;  // one stack slot of a warp: [2][32 lanes] float4
 constexpr int PSTRIDE = 8;      // doubles per partial record
+// Calls of at least this many cases read the unary transforms of the
+// variables from a table (sr_set_transforms' automatic mode); below it the
+// table's launch and copy cost more than they save.
+constexpr int XFORM_MIN_N = 16384;
 constexpr int TARGET_ITEMS_PER_WARP = 16;  // balances the launch tail; measured best of 8 to 28 at 4,096 x 100k
 // Occupancy variants of the evaluation kernel: MINB CTAs of WARPS warps per
 // SM.  Shared memory per CTA that leaves room for MINB of them (228 KB per
@@ -91,6 +95,8 @@ struct EvalParams {
   int score_M;             // Beagle scores: the maximum score per case
   const int32_t *abort;    // sr_set_abort_flag (or NULL)
   unsigned *err;           // the context's latched error word
+  int xform;               // 1: X is the variable table with the unary transforms (DecodeArgs::xform)
+  uint8_t *xneed;          // the transforms some program reads
 };
 
 __host__ __device__ inline int code_smem_bytes(int Lmax) { return ((Lmax * 8 + 15) / 16) * 16; }
@@ -161,6 +167,8 @@ __device__ __forceinline__ DecodeArgs decode_args(const EvalParams &p, int cap_s
   a.deep_count = deep_count;
   a.fold = 1;  // constant-only subtrees are evaluated once, in the decoder
   a.adj_info = 0;
+  a.xform = p.xform;
+  a.xneed = p.xneed;
   return a;
 }
 
@@ -168,6 +176,30 @@ __device__ __forceinline__ DecodeArgs decode_args(const EvalParams &p, int cap_s
 __global__ void decode_kernel(EvalParams p) {
   extern __shared__ __align__(16) unsigned char dsm[];
   decode_warp(decode_args(p, p.slots, p.queue + 4), p.P, dsm);
+}
+
+// The variable table of an evaluation with transforms (DecodeArgs::xform):
+// row j < nvars is x_j, row xform_row(nvars, u, j) is u(x_j) for the
+// transforms some program reads (xneed, marked by the decoder), by the
+// interpreter's own FP32 functions (fold_op), so a program reads the bits
+// its own per-case evaluation of u(x_j) would give.  Blocks: (case group
+// of XF_THREADS * 4 cases, row).
+constexpr int XF_THREADS = 256;
+__global__ void __launch_bounds__(XF_THREADS)
+    xform_kernel(const float *__restrict__ X, long long ldx, int nvars, int N, int ldxt,
+                 const uint8_t *__restrict__ xneed, float *__restrict__ xt) {
+  const int r = blockIdx.y;
+  const int u = r < nvars ? -1 : (r - nvars) / nvars;
+  const int j = r < nvars ? r : (r - nvars) % nvars;
+  if (u >= 0 && !xneed[u * nvars + j]) return;
+  const int c = (blockIdx.x * XF_THREADS + threadIdx.x) * 4;
+  if (c >= N) return;  // c + 3 < ldx and < ldxt: both are multiples of 4 and >= N
+  float4 x = ldx4(X + (size_t)j * ldx + c);
+  if (u >= 0) {
+    const int v = TOK_SIN + u;
+    x = make_float4(fold_op(v, x.x, 0.f), fold_op(v, x.y, 0.f), fold_op(v, x.z, 0.f), fold_op(v, x.w, 0.f));
+  }
+  *reinterpret_cast<float4 *>(xt + (size_t)r * ldxt + c) = x;
 }
 
 // ---------------------------------------------------------------- interpreter
@@ -678,6 +710,8 @@ __device__ __forceinline__ EvalParams view(const BatchProblem &q) {
   p.flags = q.flags;
   p.code = q.code;
   p.ncode = q.ncode;
+  p.xform = 0;
+  p.xneed = nullptr;
   return p;
 }
 
@@ -1079,11 +1113,13 @@ struct Plan {
   int grid, smem, chunk, nchunks;
   int smem_deep;  // shared memory of the deep pass (0: none)
   long long items;
+  int xform;      // 1: the variable table with the unary transforms (rows of ldxt floats)
+  int ldxt;
   size_t off_queue, off_flags, off_ncode, off_code, off_part, off_yc,
-      off_ych, off_ysum, bytes;
+      off_ych, off_ysum, off_xt, off_xneed, bytes;
 };
 
-sr_status make_plan(sr_ctx *ctx, int mode, int P, int Lmax, int N, Plan *pl) {
+sr_status make_plan(sr_ctx *ctx, int mode, int P, int Lmax, int N, Plan *pl, int nvars = 1) {
   pl->minb = eval_minb(Lmax, ctx->eval_ctas);
   pl->slots = shallow_slots(Lmax, pl->minb);
   pl->smem = WARPS * warp_smem_bytes(pl->slots, Lmax);
@@ -1113,6 +1149,17 @@ sr_status make_plan(sr_ctx *ctx, int mode, int P, int Lmax, int N, Plan *pl) {
   pl->off_yc = cv.take(align_up((size_t)N, STEP) * 4);
   pl->off_ych = cv.take((size_t)pl->nchunks * 16);
   pl->off_ysum = cv.take((size_t)pl->nchunks * 16);
+  // the variable table: X's rows, then u(x_j) for the 12 unary operators
+  // (those some program reads are filled per call); where the call is large
+  // enough for it to pay and its row offsets fit the 32-bit operand
+  const long long rows = (long long)nvars * (1 + UNARY_ALL);
+  pl->ldxt = (N + 3) / 4 * 4;
+  pl->xform = (ctx->xform == 2 || (ctx->xform == 1 && N >= XFORM_MIN_N)) && rows * pl->ldxt < 0xFFFFFFFFll;
+  pl->off_xt = pl->off_xneed = 0;
+  if (pl->xform) {
+    pl->off_xt = cv.take((size_t)rows * pl->ldxt * 4);
+    pl->off_xneed = cv.take((size_t)nvars * UNARY_ALL);
+  }
   pl->bytes = cv.off;
   return SR_OK;
 }
@@ -1145,7 +1192,7 @@ sr_status launch_eval(sr_ctx *ctx, int mode, const uint8_t *programs, const int3
                       int ldy, int M = 0, int32_t *counts = nullptr) {
   SR_CHECK_CUDA(ctx, cudaSetDevice(ctx->device));
   Plan pl;
-  sr_status st = make_plan(ctx, mode, P, Lmax, N, &pl);
+  sr_status st = make_plan(ctx, mode, P, Lmax, N, &pl, nvars);
   if (st != SR_OK) return st;
   st = ensure_workspace(ctx, pl.bytes);
   if (st != SR_OK) return st;
@@ -1181,6 +1228,12 @@ sr_status launch_eval(sr_ctx *ctx, int mode, const uint8_t *programs, const int3
   ep.abort = ctx->abort_flag;
   ep.err = ctx->dev_words;
   ep.score_M = M;
+  ep.xform = pl.xform;
+  ep.xneed = pl.xform ? reinterpret_cast<uint8_t *>(ws + pl.off_xneed) : nullptr;
+  if (pl.xform) {  // the kernels read the variable table; the decoder writes its row offsets
+    ep.X = reinterpret_cast<const float *>(ws + pl.off_xt);
+    ep.ldx = pl.ldxt;
+  }
 
   int grid_ext = 0, grid_deep = 0;
   st = grid_for_t<true>(ctx, mode, pl.minb, pl.smem, &grid_ext);
@@ -1190,12 +1243,19 @@ sr_status launch_eval(sr_ctx *ctx, int mode, const uint8_t *programs, const int3
     if (st != SR_OK) return st;
   }
   SR_CHECK_CUDA(ctx, cudaMemsetAsync(ep.queue, 0, 5 * sizeof(unsigned long long), s));
+  if (pl.xform) SR_CHECK_CUDA(ctx, cudaMemsetAsync(ep.xneed, 0, (size_t)nvars * UNARY_ALL, s));
   // one warp per block spreads the serial per-program decode over the SMs
   st = allow_dynamic_smem(ctx, reinterpret_cast<const void *>(decode_kernel));
   if (st != SR_OK) return st;
   decode_kernel<<<(P + DECODE_WARPS - 1) / DECODE_WARPS, DECODE_WARPS * 32, DECODE_WARPS * decode_warp_bytes(Lmax),
                   s>>>(ep);
   ctx->launches += 1;
+  if (pl.xform) {
+    const dim3 g((unsigned)((N + XF_THREADS * 4 - 1) / (XF_THREADS * 4)), (unsigned)(nvars * (1 + UNARY_ALL)));
+    xform_kernel<<<g, XF_THREADS, 0, s>>>(X, ldx, nvars, N, pl.ldxt, ep.xneed,
+                                          reinterpret_cast<float *>(ws + pl.off_xt));
+    ctx->launches += 1;
+  }
   double *ych = reinterpret_cast<double *>(ws + pl.off_ych);
   if (mode == MODE_CORR || mode == MODE_BOTH || mode == MODE_R4) {
     double *ysum = reinterpret_cast<double *>(ws + pl.off_ysum);
@@ -1511,6 +1571,13 @@ sr_status sr_set_occupancy(sr_ctx *ctx, int eval_ctas_per_sm, int batched_ctas_p
   return SR_OK;
 }
 
+sr_status sr_set_transforms(sr_ctx *ctx, int mode) {
+  if (!ctx) return SR_EINVAL;
+  if (mode < 0 || mode > 2) return sr::fail(ctx, SR_EINVAL, "transform mode %d: 0, 1 or 2", mode);
+  ctx->xform = mode;
+  return SR_OK;
+}
+
 sr_status sr_reserve(sr_ctx *ctx, int P, int Lmax, int N) {
   using namespace sr;
   if (!ctx || P < 0 || Lmax < 1 || Lmax > SR_MAX_LMAX || N < 1) return SR_EINVAL;
@@ -1518,7 +1585,7 @@ sr_status sr_reserve(sr_ctx *ctx, int P, int Lmax, int N) {
   size_t need = 0;
   for (int mode = 0; mode < 4; ++mode) {
     Plan pl;
-    sr_status st = make_plan(ctx, mode, P, Lmax, N, &pl);
+    sr_status st = make_plan(ctx, mode, P, Lmax, N, &pl, SR_MAX_VARS);
     if (st != SR_OK) return st;
     need = pl.bytes > need ? pl.bytes : need;
   }
@@ -1578,6 +1645,7 @@ extern "C" sr_status sr_eval_noalloc(void *cuda_stream, const uint8_t *programs,
   // is the static array, so the workspace never needs to grow
   sr_ctx local;
   local.device = dev;
+  local.xform = 0;  // no variable table: the scratch stays within the terms sr.h lists
   local.stream = (cudaStream_t)cuda_stream;
   if (cudaDeviceGetAttribute(&local.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
     cudaGetLastError();

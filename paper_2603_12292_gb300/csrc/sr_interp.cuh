@@ -160,7 +160,17 @@ struct DecodeArgs {
   unsigned long long *deep_count;  // programs with NCODE_DEEP are counted here (or NULL)
   int fold;                 // 1: fold constant-only subtrees into one constant (evaluation only)
   int adj_info;             // 1: mark what the adjoint sweep needs (INS_NOADJ / INS_SA / INS_TA)
+  // 1 (evaluation only): a unary operator applied to a variable, u(x_j), reads
+  // row xform_row(nvars, u, j) of the variable table instead (the table's
+  // first nvars rows are X; the decoder marks in xneed[(u - TOK_SIN) * nvars
+  // + j] each transform that some program reads, and a kernel fills those
+  // rows before the evaluation).  ldx is then the table's row stride.
+  int xform;
+  uint8_t *xneed;
 };
+
+// Row of u(x_j) in the variable table of an evaluation with transforms.
+__host__ __device__ inline int xform_row(int nvars, int u, int j) { return nvars + (u - TOK_SIN) * nvars + j; }
 
 // Instruction flags for the adjoint kernel (bits 28-30 of x; evaluation
 // ignores them).  A constant's derivative flows only through nodes whose
@@ -214,7 +224,8 @@ static __device__ __noinline__ float fold_op(int v, float a, float b) {
 
 constexpr uint8_t NEED_FOLDED = 0x80;  // need[] bit: the subtree reads only constants (folded)
 constexpr uint8_t NEED_HASC = 0x40;    // need[] bit: the subtree reads a constant (adjoint info)
-constexpr uint8_t NEED_COUNT = 0x3f;   // need[] bits: the stack need itself
+constexpr uint8_t NEED_XVAR = 0x20;    // need[] bit: u(x_j), read from the variable table (xform)
+constexpr uint8_t NEED_COUNT = 0x1f;   // need[] bits: the stack need itself
 
 // Validation and scheduled decoding of program `prog` (one thread), reading
 // its tokens from `tok`, its constants from `crow` and using the scratch rows
@@ -269,9 +280,15 @@ __device__ inline void decode_one(const DecodeArgs &p, int prog, const uint8_t *
       if (need[c] & NEED_FOLDED) {
         need[t] = 1 | NEED_FOLDED;
         fval[t] = fold_op(v, fval[c], 0.0f);
+      } else if (p.xform && tok_class(tok[c]) == CLS_VAR) {
+        // u(x_j): a leaf reading the transformed variable's row (its index in fval)
+        const int j = tok[c] - TOK_VAR0;
+        need[t] = 1 | NEED_XVAR;
+        reinterpret_cast<int32_t *>(fval)[t] = xform_row(p.nvars, v, j);
+        p.xneed[(v - TOK_SIN) * p.nvars + j] = 1;
       } else {
         ext |= v > TOK_SQ;
-        need[t] = need[c];
+        need[t] = need[c] & (uint8_t)~NEED_XVAR;
       }
       task[sp - 1] = (int16_t)t;
     } else {
@@ -299,9 +316,15 @@ __device__ inline void decode_one(const DecodeArgs &p, int prog, const uint8_t *
   // 0: the evaluation kernels read only the value)
   auto operand = [&](uint32_t x, int node) -> uint2 {
     if (need[node] & NEED_FOLDED) return make_uint2(x, __float_as_uint(fval[node]));
+    if (need[node] & NEED_XVAR)
+      return make_uint2(x, (uint32_t)((long long)reinterpret_cast<const int32_t *>(fval)[node] * p.ldx));
     return with_operand(x, tok[node], crow, p.ldx);
   };
-  auto is_leaf = [&](int node) { return is_term(tok[node]) || (need[node] & NEED_FOLDED) != 0; };
+  auto is_leaf = [&](int node) { return is_term(tok[node]) || (need[node] & (NEED_FOLDED | NEED_XVAR)) != 0; };
+  // a leaf that reads a row of the variable table: x_j, or u(x_j) with transforms
+  auto reads_row = [&](int node) {
+    return (need[node] & NEED_XVAR) != 0 || (!(need[node] & NEED_FOLDED) && tok_class(tok[node]) == CLS_VAR);
+  };
   // adjoint info: the first instruction of every subtree (fval's storage,
   // unused without folding) and the flags of an operator instruction
   int32_t *first_ins = reinterpret_cast<int32_t *>(fval);
@@ -321,7 +344,7 @@ __device__ inline void decode_one(const DecodeArgs &p, int prog, const uint8_t *
     const int e = task[sp - 1];
     const int node = e >> 2, ph = e & 3;
     const int v = tok[node];
-    const int cls = is_leaf(node) ? (tok_class(v) == CLS_VAR ? CLS_VAR : CLS_CONST) : tok_class(v);
+    const int cls = is_leaf(node) ? (reads_row(node) ? CLS_VAR : CLS_CONST) : tok_class(v);
     if (p.adj_info && ph == 0) first_ins[node] = n;
     if (cls == CLS_VAR || cls == CLS_CONST) {
       --sp;
@@ -354,7 +377,7 @@ __device__ inline void decode_one(const DecodeArgs &p, int prog, const uint8_t *
         task[sp++] = (int16_t)(first << 2);
       } else if (ph == 1 && is_leaf(second)) {
         --sp;
-        const bool var = !(need[second] & NEED_FOLDED) && tok_class(tok[second]) == CLS_VAR;
+        const bool var = reads_row(second);
         uint32_t op;
         if (rev && v == TOK_SUB) op = var ? OP_VRSUB : OP_CRSUB;
         else if (rev && v == TOK_DIV) op = var ? OP_VRDIV : OP_CRDIV;

@@ -1,0 +1,96 @@
+"""Variable transforms in the decoder: a unary operator applied directly to
+a variable, u(x_j), reads row u(x_j) of a per-call table that one kernel
+fills with the interpreter's own FP32 functions.  Every output with
+transforms must be, bit for bit, the output without them (sr_set_transforms
+2 against 0): on hand programs that put u(x_j) in every position (alone,
+under another unary operator, as either operand of every binary operator,
+fused with a binary operator) at the operators' branch points, and on random
+populations of the base and Table 1 operators.  The automatic mode uses the
+table from 16,384 cases on, one more launch per call."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2603_12292_gb300 import binding, inputs
+from progtext import pack, parse
+
+pytestmark = pytest.mark.gpu
+
+UNARY = ["sin", "cos", "exp", "log", "sqrt", "sq", "inv", "tan", "asin", "acos", "atan", "tanh"]
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _same(a, b):
+    return (a.view(np.uint32) == b.view(np.uint32)) | (np.isnan(a) & np.isnan(b))
+
+
+def _predict(ctx, mode, progs, lens, consts, X, N):
+    binding.sr_set_transforms(ctx, mode)
+    try:
+        l0 = binding.sr_kernel_launches(ctx)
+        y = binding.sr_predict(ctx, _t(progs), _t(lens), _t(consts), _t(X), N).cpu().numpy()
+        return y, binding.sr_kernel_launches(ctx) - l0
+    finally:
+        binding.sr_set_transforms(ctx, binding.XFORM_AUTO)
+
+
+def test_transforms_hand_programs_bit_for_bit(ctx):
+    texts = []
+    for u in UNARY:
+        texts += [f"x0 {u}", f"x0 {u} x1 +", f"x1 x0 {u} -", f"x0 {u} x1 /", f"x1 x0 {u} /",
+                  f"x0 {u} x1 {u} *", f"x0 {u} sin", f"x0 {u} {u}", f"c0 x0 {u} /", f"x0 {u} c0 -",
+                  f"x1 x2 * {u}", f"x2 {u} x0 {u} x1 {u} + /", f"x0 x1 + x2 {u} * x0 {u} -"]
+    rng = np.random.default_rng(41)
+    N = 1030
+    ldx = 1032
+    X = rng.uniform(-3, 3, (3, ldx)).astype(np.float32)
+    edge = np.array([0.0, 1e-3, -1e-3, 1.0009e-3, 80.0, -80.0, 80.001, 1.0, -1.0, 0.9999, 1e4, 5e4, -7e4,
+                     1.5707964, 3.1415927, 1e-30, -2.5e-39], np.float32)
+    X[0, :len(edge)] = edge
+    X[1, 20:20 + len(edge)] = edge
+    progs, lens = pack([parse(t) for t in texts], 16)
+    consts = np.tile(np.array([0.75, -1.5], np.float32), (len(texts), 1))
+    a, la = _predict(ctx, binding.XFORM_NEVER, progs, lens, consts, X, N)
+    b, lb = _predict(ctx, binding.XFORM_ALWAYS, progs, lens, consts, X, N)
+    assert lb == la + 1  # the table's fill
+    same = _same(a, b)
+    assert same.all(), [texts[i] for i in np.nonzero(~same.all(1))[0]]
+
+
+@pytest.mark.parametrize("unary_ops", [6, 12])
+def test_transforms_random_populations_bit_for_bit(ctx, unary_ops):
+    """Outputs (sr_predict) and both fitness kinds (sr_eval, one pass) of a
+    random population, with and without transforms."""
+    pr = inputs.make_problem("xform", 43 + unary_ops, P=512, Lmin=1, Lmax=64, nvars=5, K=4, N=3001, xlo=-2.0,
+                             xhi=2.0, target_len=(3, 9), unary_ops=unary_ops)
+    a, _ = _predict(ctx, binding.XFORM_NEVER, pr.programs, pr.lengths, pr.consts, pr.X, pr.N)
+    b, _ = _predict(ctx, binding.XFORM_ALWAYS, pr.programs, pr.lengths, pr.consts, pr.X, pr.N)
+    assert _same(a, b).all()
+    y = _t(np.nan_to_num(a[0], nan=0.0, posinf=0.0, neginf=0.0).astype(np.float32))
+    f = []
+    for mode in (binding.XFORM_NEVER, binding.XFORM_ALWAYS):
+        binding.sr_set_transforms(ctx, mode)
+        try:
+            f.append(binding.sr_eval(ctx, _t(pr.programs), _t(pr.lengths), _t(pr.consts), _t(pr.X), y, pr.N,
+                                     binding.SR_MSE_CORR).cpu().numpy())
+        finally:
+            binding.sr_set_transforms(ctx, binding.XFORM_AUTO)
+    assert _same(f[0], f[1]).all()
+
+
+def test_transforms_automatic_from_16384_cases(ctx):
+    progs, lens = pack([parse("x0 sin x1 *")], 4)
+    consts = np.zeros((1, 1), np.float32)
+    for N, extra in ((16380, 0), (16384, 1)):
+        X = np.random.default_rng(N).uniform(-1, 1, (2, 16384)).astype(np.float32)
+        a, la = _predict(ctx, binding.XFORM_NEVER, progs, lens, consts, X, N)
+        b, lb = _predict(ctx, binding.XFORM_AUTO, progs, lens, consts, X, N)
+        assert lb == la + extra and _same(a, b).all()
+
+
+def test_transforms_mode_checked(ctx):
+    with pytest.raises(binding.SRError):
+        binding.sr_set_transforms(ctx, 3)
