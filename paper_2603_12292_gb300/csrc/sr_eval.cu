@@ -95,8 +95,8 @@ struct EvalParams {
   int score_M;             // Beagle scores: the maximum score per case
   const int32_t *abort;    // sr_set_abort_flag (or NULL)
   unsigned *err;           // the context's latched error word
-  int xform;               // 1: X is the variable table with the unary transforms (DecodeArgs::xform)
-  uint8_t *xneed;          // the transforms some program reads
+  int xform = 0;           // 1: X is the variable table with the unary transforms (DecodeArgs::xform)
+  uint8_t *xneed = nullptr;  // the transforms some program reads
 };
 
 __host__ __device__ inline int code_smem_bytes(int Lmax) { return ((Lmax * 8 + 15) / 16) * 16; }

@@ -109,6 +109,8 @@ __device__ __forceinline__ DecodeArgs grad_decode_args(const GradParams &p) {
   a.deep_count = nullptr;
   a.fold = 0;  // every constant keeps its own slot: its derivative is wanted
   a.adj_info = 1;
+  a.xform = 0;  // the adjoint reads X itself
+  a.xneed = nullptr;
   return a;
 }
 

@@ -165,8 +165,8 @@ struct DecodeArgs {
   // first nvars rows are X; the decoder marks in xneed[(u - TOK_SIN) * nvars
   // + j] each transform that some program reads, and a kernel fills those
   // rows before the evaluation).  ldx is then the table's row stride.
-  int xform;
-  uint8_t *xneed;
+  int xform = 0;
+  uint8_t *xneed = nullptr;
 };
 
 // Row of u(x_j) in the variable table of an evaluation with transforms.

@@ -24,7 +24,8 @@ def _t(a):
 
 
 def _same(a, b):
-    return (a.view(np.uint32) == b.view(np.uint32)) | (np.isnan(a) & np.isnan(b))
+    bits = np.uint64 if a.dtype == np.float64 else np.uint32
+    return (a.view(bits) == b.view(bits)) | (np.isnan(a) & np.isnan(b))
 
 
 def _predict(ctx, mode, progs, lens, consts, X, N):
@@ -79,6 +80,24 @@ def test_transforms_random_populations_bit_for_bit(ctx, unary_ops):
         finally:
             binding.sr_set_transforms(ctx, binding.XFORM_AUTO)
     assert _same(f[0], f[1]).all()
+
+
+def test_adjoint_after_transformed_calls(ctx):
+    """The adjoint decodes without transforms: a gradient after a transformed
+    evaluation on the same context equals the one after an untransformed one."""
+    pr = inputs.make_problem("xform-adj", 47, P=256, Lmin=3, Lmax=32, nvars=3, K=4, N=20_001, xlo=1.0, xhi=3.0,
+                             target_len=(3, 7))
+    y = _t(np.random.default_rng(5).normal(size=pr.N).astype(np.float32))
+    args = (_t(pr.programs), _t(pr.lengths), _t(pr.consts), _t(pr.X), y, pr.N)
+    g = []
+    for mode in (binding.XFORM_NEVER, binding.XFORM_ALWAYS):
+        binding.sr_set_transforms(ctx, mode)
+        try:
+            binding.sr_eval(ctx, *args, binding.SR_MSE_CORR)
+            g.append(binding.sr_eval_grad(ctx, *args)[1].cpu().numpy())
+        finally:
+            binding.sr_set_transforms(ctx, binding.XFORM_AUTO)
+    assert _same(g[0], g[1]).all()
 
 
 def test_transforms_automatic_from_16384_cases(ctx):
