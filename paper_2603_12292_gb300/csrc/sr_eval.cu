@@ -672,6 +672,8 @@ struct BatchProblem {
   int P, Lmax, K, nvars, N, chunk, nchunks;
   int mode;              // MODE_MSE, MODE_CORR or MODE_BOTH
   int corr_chunk_begin;  // first block of this problem in the batched centring launch (-1: none)
+  int xform;             // 1: X / ldx are the problem's variable table (EvalParams::xform)
+  uint8_t *xneed;
 };
 
 struct BatchParams {
@@ -689,6 +691,8 @@ struct BatchParams {
   const int32_t *abort;       // as EvalParams::abort
   unsigned *err;
 };
+
+static_assert(sizeof(BatchParams) <= 32764, "the problem table must fit the kernel parameters");
 
 __device__ __forceinline__ EvalParams view(const BatchProblem &q) {
   EvalParams p;
@@ -710,8 +714,8 @@ __device__ __forceinline__ EvalParams view(const BatchProblem &q) {
   p.flags = q.flags;
   p.code = q.code;
   p.ncode = q.ncode;
-  p.xform = 0;
-  p.xneed = nullptr;
+  p.xform = q.xform;
+  p.xneed = q.xneed;
   return p;
 }
 
@@ -1119,6 +1123,14 @@ struct Plan {
       off_ych, off_ysum, off_xt, off_xneed, bytes;
 };
 
+// Whether a call (or a batch's problem) of N cases over nvars variables reads
+// the variable table, and that table's row stride.
+inline bool use_xform(const sr_ctx *ctx, int nvars, int N, int *ldxt) {
+  *ldxt = (N + 3) / 4 * 4;
+  const long long rows = (long long)nvars * (1 + UNARY_ALL);
+  return (ctx->xform == 2 || (ctx->xform == 1 && N >= XFORM_MIN_N)) && rows * *ldxt < 0xFFFFFFFFll;
+}
+
 sr_status make_plan(sr_ctx *ctx, int mode, int P, int Lmax, int N, Plan *pl, int nvars = 1) {
   pl->minb = eval_minb(Lmax, ctx->eval_ctas);
   pl->slots = shallow_slots(Lmax, pl->minb);
@@ -1153,8 +1165,7 @@ sr_status make_plan(sr_ctx *ctx, int mode, int P, int Lmax, int N, Plan *pl, int
   // (those some program reads are filled per call); where the call is large
   // enough for it to pay and its row offsets fit the 32-bit operand
   const long long rows = (long long)nvars * (1 + UNARY_ALL);
-  pl->ldxt = (N + 3) / 4 * 4;
-  pl->xform = (ctx->xform == 2 || (ctx->xform == 1 && N >= XFORM_MIN_N)) && rows * pl->ldxt < 0xFFFFFFFFll;
+  pl->xform = use_xform(ctx, nvars, N, &pl->ldxt);
   pl->off_xt = pl->off_xneed = 0;
   if (pl->xform) {
     pl->off_xt = cv.take((size_t)rows * pl->ldxt * 4);
@@ -1390,12 +1401,18 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
       const size_t off_nc = cv.take((size_t)q.P * 4);
       const size_t off_code = cv.take(tokens * 8);
       const size_t off_p = cv.take((size_t)q.P * nch[i] * PSTRIDE * 8);
-      size_t off_yc = 0, off_ych = 0, off_st = 0;
+      size_t off_yc = 0, off_ych = 0, off_st = 0, off_xt = 0, off_xn = 0;
       const bool corr = mode != MODE_MSE;
       if (corr) {
         off_yc = cv.take(align_up((size_t)q.N, STEP) * 4);
         off_ych = cv.take((size_t)nch[i] * 16);
         off_st = cv.take((size_t)nch[i] * 16);
+      }
+      int ldxt = 0;
+      const bool xf = use_xform(ctx, q.nvars, q.N, &ldxt);
+      if (xf) {
+        off_xt = cv.take((size_t)q.nvars * (1 + UNARY_ALL) * ldxt * 4);
+        off_xn = cv.take((size_t)q.nvars * UNARY_ALL);
       }
       if (bpar) {
         BatchProblem &b = bpar->prob[g - g0];
@@ -1425,6 +1442,12 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
         b.nchunks = nch[i];
         b.mode = mode;
         b.corr_chunk_begin = corr ? corr_chunks : -1;
+        b.xform = xf;
+        b.xneed = xf ? reinterpret_cast<uint8_t *>(ws + off_xn) : nullptr;
+        if (xf) {
+          b.X = reinterpret_cast<const float *>(ws + off_xt);
+          b.ldx = ldxt;
+        }
         if (corr) bpar->corr_list[ncorr] = (int)(g - g0);
       }
       items += (long long)q.P * nch[i];
@@ -1466,9 +1489,21 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
     int corr_blocks = 0;
     for (int r = 0; r < b.ncorr; ++r) corr_blocks += b.prob[b.corr_list[r]].nchunks;
     SR_CHECK_CUDA(ctx, cudaMemsetAsync(b.queue, 0, 5 * sizeof(unsigned long long), s));
+    for (int r = 0; r < b.nprob; ++r)
+      if (b.prob[r].xform)
+        SR_CHECK_CUDA(ctx, cudaMemsetAsync(b.prob[r].xneed, 0, (size_t)b.prob[r].nvars * UNARY_ALL, s));
     decode_batched_kernel<<<(b.total_progs + DECODE_WARPS - 1) / DECODE_WARPS, DECODE_WARPS * 32,
                             DECODE_WARPS * decode_warp_bytes(maxL), s>>>(b);
     ctx->launches += 1;
+    for (size_t g = g0; g < g1; ++g) {  // the variable tables, from the problems' own X
+      const BatchProblem &q = b.prob[g - g0];
+      if (!q.xform) continue;
+      const sr_problem &o = pr[order[g]];
+      const dim3 xg((unsigned)((q.N + XF_THREADS * 4 - 1) / (XF_THREADS * 4)), (unsigned)(q.nvars * (1 + UNARY_ALL)));
+      xform_kernel<<<xg, XF_THREADS, 0, s>>>(o.X, o.ldx, q.nvars, q.N, (int)q.ldx, q.xneed,
+                                             const_cast<float *>(q.X));
+      ctx->launches += 1;
+    }
     if (b.ncorr > 0) {
       ysum_batched_kernel<<<corr_blocks, PREP_THREADS, 0, s>>>(b);
       ycenter_batched_kernel<<<corr_blocks, PREP_THREADS, 0, s>>>(b);

@@ -5,8 +5,9 @@ transforms must be, bit for bit, the output without them (sr_set_transforms
 2 against 0): on hand programs that put u(x_j) in every position (alone,
 under another unary operator, as either operand of every binary operator,
 fused with a binary operator) at the operators' branch points, and on random
-populations of the base and Table 1 operators.  The automatic mode uses the
-table from 16,384 cases on, one more launch per call."""
+populations of the base and Table 1 operators, single calls and batches.
+The automatic mode uses the table from 16,384 cases on, one more launch per
+call (per such problem of a batch)."""
 import numpy as np
 import pytest
 import torch
@@ -98,6 +99,31 @@ def test_adjoint_after_transformed_calls(ctx):
         finally:
             binding.sr_set_transforms(ctx, binding.XFORM_AUTO)
     assert _same(g[0], g[1]).all()
+
+
+def test_batched_transforms_bit_for_bit(ctx):
+    """A batch of problems of both sizes (with and without the table in the
+    automatic mode): every fitness with transforms equals the one without."""
+    probs = [inputs.make_problem(f"xform-b{i}", 50 + i, P=96, Lmin=1, Lmax=48, nvars=1 + i % 4, K=3,
+                                 N=n, xlo=-2.0, xhi=2.0, target_len=(3, 7))
+             for i, n in enumerate((3001, 20_000, 517, 40_003))]
+    ys = [_t(np.random.default_rng(i).normal(size=pr.N).astype(np.float32)) for i, pr in enumerate(probs)]
+    out = []
+    for mode in (binding.XFORM_NEVER, binding.XFORM_ALWAYS, binding.XFORM_AUTO):
+        binding.sr_set_transforms(ctx, mode)
+        try:
+            fits, keep = [], []
+            for pr, y in zip(probs, ys):
+                f = torch.empty((2, pr.P), dtype=torch.float64, device="cuda")
+                keep.append(binding.make_problem(_t(pr.programs), _t(pr.lengths), _t(pr.consts), _t(pr.X), y,
+                                                 pr.N, binding.SR_MSE_CORR, fitness=f))
+                fits.append(f)
+            binding.sr_eval_batched(ctx, keep)
+            out.append([f.cpu().numpy() for f in fits])
+        finally:
+            binding.sr_set_transforms(ctx, binding.XFORM_AUTO)
+    for a, b, c in zip(*out):
+        assert _same(a, b).all() and _same(a, c).all()
 
 
 def test_transforms_automatic_from_16384_cases(ctx):
