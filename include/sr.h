@@ -112,8 +112,9 @@ const char *sr_last_error(const sr_ctx *ctx);
 
 /* Grow the workspace now so that sr_eval / sr_predict on up to P programs
  * of up to Lmax tokens and up to N cases need no allocation later (for
- * example inside CUDA-graph capture).  Synchronous.  Errors: SR_EINVAL,
- * SR_ENOMEM. */
+ * example inside CUDA-graph capture), the variable table of the transforms
+ * (sr_set_transforms) included for up to 16 variables.  Synchronous.
+ * Errors: SR_EINVAL, SR_ENOMEM. */
 sr_status sr_reserve(sr_ctx *ctx, int P, int Lmax, int N);
 
 /* Number of kernels this context has launched so far (host counter,
