@@ -260,8 +260,8 @@ sr_status sr_set_occupancy(sr_ctx *ctx, int eval_ctas_per_sm, int batched_ctas_p
  * program's sin(x3), say, costs a load instead of the library routine.  The
  * paper has no counterpart (an evaluation-side common-subexpression
  * elimination, like the folding of constant-only subtrees).
- *   mode  0 never; 1 automatic (the default): calls of at least 16,384
- *         cases; 2 always
+ *   mode  0 never; 1 automatic (the default): calls (and problems of a
+ *         batch) of at least 64 programs and 16,384 cases; 2 always
  * The table adds nvars * 13 * N * 4 bytes to the workspace (sr_reserve
  * counts it for 16 variables).  Errors: SR_EINVAL. */
 sr_status sr_set_transforms(sr_ctx *ctx, int mode);

@@ -549,9 +549,9 @@ XFORM_NEVER, XFORM_AUTO, XFORM_ALWAYS = 0, 1, 2
 
 
 def sr_set_transforms(ctx: Context, mode: int = XFORM_AUTO):
-    """Variable transforms of the single-problem evaluation: 0 never, 1
-    automatic (calls of at least 16,384 cases), 2 always.  Results are bit
-    for bit the same either way."""
+    """Variable transforms of the evaluation: 0 never, 1 automatic (calls and
+    batch problems of at least 64 programs and 16,384 cases), 2 always.
+    Results are bit for bit the same either way."""
     _check(ctx, lib().sr_set_transforms(ctx.handle, mode))
 
 

@@ -50,10 +50,11 @@ constexpr int CPL = 8;          // cases per lane per dispatched instruction (tw
 constexpr int STEP = 32 * CPL;  // cases per warp step
 constexpr int SLOT_BYTES = 32 * CPL * 4;  // one stack slot of a warp: [2][32 lanes] float4
 constexpr int PSTRIDE = 8;      // doubles per partial record
-// Calls of at least this many cases read the unary transforms of the
-// variables from a table (sr_set_transforms' automatic mode); below it the
-// table's launch and copy cost more than they save.
-constexpr int XFORM_MIN_N = 16384;
+// Calls of at least this many cases and programs read the unary transforms
+// of the variables from a table (sr_set_transforms' automatic mode); below
+// that the table's launch and copy cost more than the few programs sharing
+// each row save.
+constexpr int XFORM_MIN_N = 16384, XFORM_MIN_P = 64;
 constexpr int TARGET_ITEMS_PER_WARP = 16;  // balances the launch tail; measured best of 8 to 28 at 4,096 x 100k
 // Occupancy variants of the evaluation kernel: MINB CTAs of WARPS warps per
 // SM.  Shared memory per CTA that leaves room for MINB of them (228 KB per
@@ -1123,12 +1124,13 @@ struct Plan {
       off_ych, off_ysum, off_xt, off_xneed, bytes;
 };
 
-// Whether a call (or a batch's problem) of N cases over nvars variables reads
+// Whether a call (or a batch's problem) of P programs and N cases over nvars variables reads
 // the variable table, and that table's row stride.
-inline bool use_xform(const sr_ctx *ctx, int nvars, int N, int *ldxt) {
+inline bool use_xform(const sr_ctx *ctx, int P, int nvars, int N, int *ldxt) {
   *ldxt = (N + 3) / 4 * 4;
   const long long rows = (long long)nvars * (1 + UNARY_ALL);
-  return (ctx->xform == 2 || (ctx->xform == 1 && N >= XFORM_MIN_N)) && rows * *ldxt < 0xFFFFFFFFll;
+  const bool automatic = ctx->xform == 1 && N >= XFORM_MIN_N && P >= XFORM_MIN_P;
+  return (ctx->xform == 2 || automatic) && rows * *ldxt < 0xFFFFFFFFll;
 }
 
 sr_status make_plan(sr_ctx *ctx, int mode, int P, int Lmax, int N, Plan *pl, int nvars = 1) {
@@ -1165,7 +1167,7 @@ sr_status make_plan(sr_ctx *ctx, int mode, int P, int Lmax, int N, Plan *pl, int
   // (those some program reads are filled per call); where the call is large
   // enough for it to pay and its row offsets fit the 32-bit operand
   const long long rows = (long long)nvars * (1 + UNARY_ALL);
-  pl->xform = use_xform(ctx, nvars, N, &pl->ldxt);
+  pl->xform = use_xform(ctx, P, nvars, N, &pl->ldxt);
   pl->off_xt = pl->off_xneed = 0;
   if (pl->xform) {
     pl->off_xt = cv.take((size_t)rows * pl->ldxt * 4);
@@ -1409,7 +1411,7 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
         off_st = cv.take((size_t)nch[i] * 16);
       }
       int ldxt = 0;
-      const bool xf = use_xform(ctx, q.nvars, q.N, &ldxt);
+      const bool xf = use_xform(ctx, q.P, q.nvars, q.N, &ldxt);
       if (xf) {
         off_xt = cv.take((size_t)q.nvars * (1 + UNARY_ALL) * ldxt * 4);
         off_xn = cv.take((size_t)q.nvars * UNARY_ALL);

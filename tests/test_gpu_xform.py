@@ -6,8 +6,8 @@ transforms must be, bit for bit, the output without them (sr_set_transforms
 under another unary operator, as either operand of every binary operator,
 fused with a binary operator) at the operators' branch points, and on random
 populations of the base and Table 1 operators, single calls and batches.
-The automatic mode uses the table from 16,384 cases on, one more launch per
-call (per such problem of a batch)."""
+The automatic mode uses the table from 64 programs and 16,384 cases on, one
+more launch per call (per such problem of a batch)."""
 import numpy as np
 import pytest
 import torch
@@ -126,10 +126,10 @@ def test_batched_transforms_bit_for_bit(ctx):
         assert _same(a, b).all() and _same(a, c).all()
 
 
-def test_transforms_automatic_from_16384_cases(ctx):
-    progs, lens = pack([parse("x0 sin x1 *")], 4)
-    consts = np.zeros((1, 1), np.float32)
-    for N, extra in ((16380, 0), (16384, 1)):
+def test_transforms_automatic_from_64_programs_and_16384_cases(ctx):
+    for P, N, extra in ((64, 16380, 0), (63, 16384, 0), (64, 16384, 1)):
+        progs, lens = pack([parse("x0 sin x1 *")] * P, 4)
+        consts = np.zeros((P, 1), np.float32)
         X = np.random.default_rng(N).uniform(-1, 1, (2, 16384)).astype(np.float32)
         a, la = _predict(ctx, binding.XFORM_NEVER, progs, lens, consts, X, N)
         b, lb = _predict(ctx, binding.XFORM_AUTO, progs, lens, consts, X, N)
