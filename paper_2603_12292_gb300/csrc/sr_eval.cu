@@ -239,7 +239,7 @@ __device__ __forceinline__ V8 ldX8(const float *xa, const float *xb, uint32_t of
 #define SR_MATH_UNROLL 8
 #endif
 constexpr int MATH_UNROLL = SR_MATH_UNROLL;
-// The costly operators (the FP32 math library routines and IEEE division)
+// The costly operators (the FP32 math library routines and the quotient)
 // live out of line, one copy each, so the interpreter's dispatch loop stays
 // small enough for the instruction cache; inside, SR_MATH_UNROLL values are
 // in flight at a time.  Measured on the 4096 x 100,000 mixed population:
@@ -1208,6 +1208,13 @@ sr_status launch_eval(sr_ctx *ctx, int mode, const uint8_t *programs, const int3
   sr_status st = make_plan(ctx, mode, P, Lmax, N, &pl, nvars);
   if (st != SR_OK) return st;
   st = ensure_workspace(ctx, pl.bytes);
+  if (st == SR_ENOMEM && pl.xform) {  // no room for the variable table: evaluate without it
+    const int mode_x = ctx->xform;
+    ctx->xform = 0;
+    st = make_plan(ctx, mode, P, Lmax, N, &pl, nvars);
+    ctx->xform = mode_x;
+    if (st == SR_OK) st = ensure_workspace(ctx, pl.bytes);
+  }
   if (st != SR_OK) return st;
   char *ws = ctx->ws;
   cudaStream_t s = ctx->stream;
@@ -1481,6 +1488,22 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
   }
   if (order.empty()) return SR_OK;
   st = ensure_workspace(ctx, need);
+  // no room for the variable tables: evaluate without them (the context's
+  // setting comes back when the call returns)
+  struct Restore {
+    sr_ctx *c;
+    int mode;
+    ~Restore() { c->xform = mode; }
+  } restore{ctx, ctx->xform};
+  if (st == SR_ENOMEM && ctx->xform != 0) {
+    ctx->xform = 0;
+    need = 0;
+    for (size_t g0 = 0; g0 < order.size(); g0 += MAX_BATCH) {
+      const size_t g1 = std::min(order.size(), g0 + MAX_BATCH);
+      need = std::max(need, group_bytes(g0, g1, nullptr));
+    }
+    st = ensure_workspace(ctx, need);
+  }
   if (st != SR_OK) return st;
 
   cudaStream_t s = ctx->stream;

@@ -136,6 +136,36 @@ def test_transforms_automatic_from_64_programs_and_16384_cases(ctx):
         assert lb == la + extra and _same(a, b).all()
 
 
+def test_table_left_out_when_the_workspace_cannot_grow(ctx):
+    """Inside stream capture the workspace cannot grow.  A call whose variable
+    table does not fit the workspace then evaluates without it, and the
+    captured graph gives the same bits as an eager call without transforms."""
+    pr = inputs.make_problem("xform-cap", 53, P=256, Lmin=3, Lmax=32, nvars=5, K=4, N=20_000, xlo=-2.0,
+                             xhi=2.0, target_len=(3, 7))
+    y = _t(np.random.default_rng(9).normal(size=pr.N).astype(np.float32))
+    args = (_t(pr.programs), _t(pr.lengths), _t(pr.consts), _t(pr.X), y, pr.N, binding.SR_MSE_CORR)
+    c = binding.Context(0)  # its own workspace: grown here only without the table
+    try:
+        binding.sr_set_transforms(c, binding.XFORM_NEVER)
+        ref = binding.sr_eval(c, *args).clone()
+        torch.cuda.synchronize()
+        binding.sr_set_transforms(c, binding.XFORM_ALWAYS)
+        out = torch.empty((2, pr.P), dtype=torch.float64, device="cuda")
+        stream = torch.cuda.Stream()
+        c.set_stream(stream)
+        g = torch.cuda.CUDAGraph()
+        try:
+            with torch.cuda.graph(g, stream=stream):
+                binding.sr_eval(c, *args, fitness=out)
+        finally:
+            c.set_stream(torch.cuda.current_stream())
+        g.replay()
+        torch.cuda.synchronize()
+        assert _same(out.cpu().numpy(), ref.cpu().numpy()).all()
+    finally:
+        c.close()
+
+
 def test_transforms_mode_checked(ctx):
     with pytest.raises(binding.SRError):
         binding.sr_set_transforms(ctx, 3)
