@@ -422,6 +422,9 @@ def run_ours(args, rank, world, local_rank):
                                   else "sr_select_tournament(k=4, on 1-r^2)")
                                + " + sr_vary(p_cross 0.9, p_point 0.1, p_subtree 0.05, p_const 0.1)",
                        "l2": "flushed between timed steps",
+                       "decoder": "constant-only subtrees folded; u(x_j) read from a per-call table of "
+                                  "the variables' unary transforms; outputs bit for bit those of "
+                                  "node-by-node evaluation; GPop/s counts every node as written",
                        "parallelism": f"islands x{world}: one population per rank, own seed, no exchange"},
             "roofline": roofline, "clocks": clocks,
             "e2e": {"value": e2e_val, "unit": "GPop/s", "h2d_bytes_per_step": int(h2d),
