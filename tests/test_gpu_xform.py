@@ -166,6 +166,46 @@ def test_table_left_out_when_the_workspace_cannot_grow(ctx):
         c.close()
 
 
+@pytest.mark.parametrize("batched", [False, True])
+def test_graph_replay_with_transforms(ctx, batched):
+    """The generation loop with transforms: the table's fill is captured with
+    the rest, graph replay equals eager execution bit for bit, and both equal
+    the loop without transforms."""
+    import oracle
+    from paper_2603_12292_gb300.evolve import Evolver, EvolveConfig, Population
+
+    def pops():
+        out = []
+        for i in range(3 if batched else 1):
+            pr = inputs.make_problem("xg", 60 + i, P=128, Lmin=1, Lmax=32, nvars=3, K=4, N=3000, xlo=1.0,
+                                     xhi=5.0, target_len=(5, 9))
+            y = oracle.predict(pr.target, pr.target_consts, pr.X, pr.N).astype(np.float32)
+            out.append(Population(_t(pr.programs), _t(pr.lengths), _t(pr.consts), _t(pr.X), _t(y), pr.N,
+                                  EvolveConfig()))
+        return out
+
+    def state(ev):
+        return [np.concatenate([x.cpu().numpy().ravel().view(np.uint8) for x in p.current]
+                               + [p.fitness.cpu().numpy().ravel().view(np.uint8)]) for p in ev.pops]
+
+    res = []
+    for mode, graph in ((binding.XFORM_NEVER, False), (binding.XFORM_ALWAYS, False), (binding.XFORM_ALWAYS, True)):
+        binding.sr_set_transforms(ctx, mode)
+        try:
+            ev = Evolver(ctx, pops(), batched=batched)
+            if graph:
+                ev.capture(2)
+                ev.run(4)
+            else:
+                ev.run(5)
+            torch.cuda.synchronize()
+            res.append(state(ev))
+        finally:
+            binding.sr_set_transforms(ctx, binding.XFORM_AUTO)
+    for a, b, c in zip(*res):
+        assert np.array_equal(a, b) and np.array_equal(a, c)
+
+
 def test_transforms_mode_checked(ctx):
     with pytest.raises(binding.SRError):
         binding.sr_set_transforms(ctx, 3)
