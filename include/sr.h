@@ -250,20 +250,25 @@ sr_status sr_set_tile(sr_ctx *ctx, int cases_per_tile);
  * which warp runs an item).  Errors: SR_EINVAL. */
 sr_status sr_set_occupancy(sr_ctx *ctx, int eval_ctas_per_sm, int batched_ctas_per_sm);
 
-/* Variable transforms of sr_eval / sr_eval_score / sr_predict on this
- * context.  A unary operator applied directly to a variable, u(x_j), is the
- * same column of values in every program of the population: with transforms
- * the decoder turns it into a read of row u(x_j) of a per-call table (X's
- * rows, then u(x_j) for each operator and variable some program uses),
- * which one kernel fills per call with the FP32 functions the interpreter
- * applies per case -- so results are bit for bit those without it, while a
- * program's sin(x3), say, costs a load instead of the library routine.  The
- * paper has no counterpart (an evaluation-side common-subexpression
- * elimination, like the folding of constant-only subtrees).
+/* Variable transforms of sr_eval / sr_eval_score / sr_predict /
+ * sr_eval_batched on this context.  A unary operator applied directly to a
+ * variable, u(x_j), is the same column of values in every program of the
+ * population: with transforms the decoder turns it into a read of row
+ * u(x_j) of a per-call table (X's rows, then u(x_j) for each of the twelve
+ * operators and each variable, then -- where the table stays within 256 MiB
+ * -- the compositions u(v(x_j)) of the six base operators), and one kernel
+ * fills the rows some program reads, per call, with the FP32 functions the
+ * interpreter applies per case: results are bit for bit those without it,
+ * while a program's sin(x3), say, costs a load instead of the library
+ * routine.  The paper has no counterpart (an evaluation-side
+ * common-subexpression elimination, like the folding of constant-only
+ * subtrees).
  *   mode  0 never; 1 automatic (the default): calls (and problems of a
  *         batch) of at least 64 programs and 16,384 cases; 2 always
- * The table adds nvars * 13 * N * 4 bytes to the workspace (sr_reserve
- * counts it for 16 variables).  Errors: SR_EINVAL. */
+ * The table adds nvars * 13 * N * 4 bytes to the workspace, nvars * 49 * N
+ * * 4 with the compositions (sr_reserve counts the largest for up to 16
+ * variables); a call whose table does not fit the workspace when it cannot
+ * grow (inside stream capture) runs without it.  Errors: SR_EINVAL. */
 sr_status sr_set_transforms(sr_ctx *ctx, int mode);
 
 /*

@@ -55,6 +55,8 @@ constexpr int PSTRIDE = 8;      // doubles per partial record
 // that the table's launch and copy cost more than the few programs sharing
 // each row save.
 constexpr int XFORM_MIN_N = 16384, XFORM_MIN_P = 64;
+// The compositions u(v(x_j)) join the table while it stays within this size.
+constexpr long long XFORM2_MAX_BYTES = 256ll << 20;
 constexpr int TARGET_ITEMS_PER_WARP = 16;  // balances the launch tail; measured best of 8 to 28 at 4,096 x 100k
 // Occupancy variants of the evaluation kernel: MINB CTAs of WARPS warps per
 // SM.  Shared memory per CTA that leaves room for MINB of them (228 KB per
@@ -96,7 +98,7 @@ struct EvalParams {
   int score_M;             // Beagle scores: the maximum score per case
   const int32_t *abort;    // sr_set_abort_flag (or NULL)
   unsigned *err;           // the context's latched error word
-  int xform = 0;           // 1: X is the variable table with the unary transforms (DecodeArgs::xform)
+  int xform = 0;           // >= 1: X is the variable table of this depth (DecodeArgs::xform)
   uint8_t *xneed = nullptr;  // the transforms some program reads
 };
 
@@ -180,26 +182,35 @@ __global__ void decode_kernel(EvalParams p) {
 }
 
 // The variable table of an evaluation with transforms (DecodeArgs::xform):
-// row j < nvars is x_j, row xform_row(nvars, u, j) is u(x_j) for the
-// transforms some program reads (xneed, marked by the decoder), by the
-// interpreter's own FP32 functions (fold_op), so a program reads the bits
-// its own per-case evaluation of u(x_j) would give.  Blocks: (case group
-// of XF_THREADS * 4 cases, row).
+// row j < nvars is x_j, row xform_row(nvars, u, j) is u(x_j) and row
+// xform_row2(nvars, u, v, j) is u(v(x_j)), for the rows some program reads
+// (xneed, marked by the decoder), by the interpreter's own FP32 functions
+// (fold_op), so a program reads the bits its own per-case evaluation would
+// give.  Blocks: (case group of XF_THREADS * 4 cases, row).
 constexpr int XF_THREADS = 256;
 __global__ void __launch_bounds__(XF_THREADS)
     xform_kernel(const float *__restrict__ X, long long ldx, int nvars, int N, int ldxt,
                  const uint8_t *__restrict__ xneed, float *__restrict__ xt) {
   const int r = blockIdx.y;
-  const int u = r < nvars ? -1 : (r - nvars) / nvars;
-  const int j = r < nvars ? r : (r - nvars) % nvars;
-  if (u >= 0 && !xneed[u * nvars + j]) return;
+  if (r >= nvars && !xneed[r - nvars]) return;
   const int c = (blockIdx.x * XF_THREADS + threadIdx.x) * 4;
   if (c >= N) return;  // c + 3 < ldx and < ldxt: both are multiples of 4 and >= N
-  float4 x = ldx4(X + (size_t)j * ldx + c);
-  if (u >= 0) {
-    const int v = TOK_SIN + u;
-    x = make_float4(fold_op(v, x.x, 0.f), fold_op(v, x.y, 0.f), fold_op(v, x.z, 0.f), fold_op(v, x.w, 0.f));
+  const int r2 = nvars * (1 + UNARY_ALL);  // first composition row
+  int u = -1, v = -1, j = r;
+  if (r >= r2) {
+    const int k = (r - r2) / nvars;
+    j = (r - r2) % nvars;
+    u = TOK_SIN + k / XFORM_BASE;
+    v = TOK_SIN + k % XFORM_BASE;
+  } else if (r >= nvars) {
+    u = TOK_SIN + (r - nvars) / nvars;
+    j = (r - nvars) % nvars;
   }
+  float4 x = ldx4(X + (size_t)j * ldx + c);
+  if (v >= 0)
+    x = make_float4(fold_op(v, x.x, 0.f), fold_op(v, x.y, 0.f), fold_op(v, x.z, 0.f), fold_op(v, x.w, 0.f));
+  if (u >= 0)
+    x = make_float4(fold_op(u, x.x, 0.f), fold_op(u, x.y, 0.f), fold_op(u, x.z, 0.f), fold_op(u, x.w, 0.f));
   *reinterpret_cast<float4 *>(xt + (size_t)r * ldxt + c) = x;
 }
 
@@ -673,7 +684,7 @@ struct BatchProblem {
   int P, Lmax, K, nvars, N, chunk, nchunks;
   int mode;              // MODE_MSE, MODE_CORR or MODE_BOTH
   int corr_chunk_begin;  // first block of this problem in the batched centring launch (-1: none)
-  int xform;             // 1: X / ldx are the problem's variable table (EvalParams::xform)
+  int xform;             // >= 1: X / ldx are the problem's variable table of this depth (EvalParams::xform)
   uint8_t *xneed;
 };
 
@@ -1118,7 +1129,7 @@ struct Plan {
   int grid, smem, chunk, nchunks;
   int smem_deep;  // shared memory of the deep pass (0: none)
   long long items;
-  int xform;      // 1: the variable table with the unary transforms (rows of ldxt floats)
+  int xform;      // the variable table's depth (0: none; rows of ldxt floats)
   int ldxt;
   size_t off_queue, off_flags, off_ncode, off_code, off_part, off_yc,
       off_ych, off_ysum, off_xt, off_xneed, bytes;
@@ -1126,11 +1137,15 @@ struct Plan {
 
 // Whether a call (or a batch's problem) of P programs and N cases over nvars variables reads
 // the variable table, and that table's row stride.
-inline bool use_xform(const sr_ctx *ctx, int P, int nvars, int N, int *ldxt) {
+// (0: no; 1: u(x_j); 2: also the compositions, where the table stays
+// within XFORM2_MAX_BYTES), and that table's row stride.
+inline int use_xform(const sr_ctx *ctx, int P, int nvars, int N, int *ldxt) {
   *ldxt = (N + 3) / 4 * 4;
-  const long long rows = (long long)nvars * (1 + UNARY_ALL);
   const bool automatic = ctx->xform == 1 && N >= XFORM_MIN_N && P >= XFORM_MIN_P;
-  return (ctx->xform == 2 || automatic) && rows * *ldxt < 0xFFFFFFFFll;
+  if (!(ctx->xform == 2 || automatic)) return 0;
+  const long long cells2 = (long long)xform_rows(nvars, 2) * *ldxt;
+  if (cells2 < 0xFFFFFFFFll && cells2 * 4 <= XFORM2_MAX_BYTES) return 2;
+  return (long long)xform_rows(nvars, 1) * *ldxt < 0xFFFFFFFFll ? 1 : 0;
 }
 
 sr_status make_plan(sr_ctx *ctx, int mode, int P, int Lmax, int N, Plan *pl, int nvars = 1) {
@@ -1166,12 +1181,12 @@ sr_status make_plan(sr_ctx *ctx, int mode, int P, int Lmax, int N, Plan *pl, int
   // the variable table: X's rows, then u(x_j) for the 12 unary operators
   // (those some program reads are filled per call); where the call is large
   // enough for it to pay and its row offsets fit the 32-bit operand
-  const long long rows = (long long)nvars * (1 + UNARY_ALL);
   pl->xform = use_xform(ctx, P, nvars, N, &pl->ldxt);
   pl->off_xt = pl->off_xneed = 0;
   if (pl->xform) {
-    pl->off_xt = cv.take((size_t)rows * pl->ldxt * 4);
-    pl->off_xneed = cv.take((size_t)nvars * UNARY_ALL);
+    const size_t rows = (size_t)xform_rows(nvars, pl->xform);
+    pl->off_xt = cv.take(rows * pl->ldxt * 4);
+    pl->off_xneed = cv.take(rows - nvars);
   }
   pl->bytes = cv.off;
   return SR_OK;
@@ -1263,7 +1278,7 @@ sr_status launch_eval(sr_ctx *ctx, int mode, const uint8_t *programs, const int3
     if (st != SR_OK) return st;
   }
   SR_CHECK_CUDA(ctx, cudaMemsetAsync(ep.queue, 0, 5 * sizeof(unsigned long long), s));
-  if (pl.xform) SR_CHECK_CUDA(ctx, cudaMemsetAsync(ep.xneed, 0, (size_t)nvars * UNARY_ALL, s));
+  if (pl.xform) SR_CHECK_CUDA(ctx, cudaMemsetAsync(ep.xneed, 0, (size_t)(xform_rows(nvars, pl.xform) - nvars), s));
   // one warp per block spreads the serial per-program decode over the SMs
   st = allow_dynamic_smem(ctx, reinterpret_cast<const void *>(decode_kernel));
   if (st != SR_OK) return st;
@@ -1271,7 +1286,7 @@ sr_status launch_eval(sr_ctx *ctx, int mode, const uint8_t *programs, const int3
                   s>>>(ep);
   ctx->launches += 1;
   if (pl.xform) {
-    const dim3 g((unsigned)((N + XF_THREADS * 4 - 1) / (XF_THREADS * 4)), (unsigned)(nvars * (1 + UNARY_ALL)));
+    const dim3 g((unsigned)((N + XF_THREADS * 4 - 1) / (XF_THREADS * 4)), (unsigned)xform_rows(nvars, pl.xform));
     xform_kernel<<<g, XF_THREADS, 0, s>>>(X, ldx, nvars, N, pl.ldxt, ep.xneed,
                                           reinterpret_cast<float *>(ws + pl.off_xt));
     ctx->launches += 1;
@@ -1418,10 +1433,11 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
         off_st = cv.take((size_t)nch[i] * 16);
       }
       int ldxt = 0;
-      const bool xf = use_xform(ctx, q.P, q.nvars, q.N, &ldxt);
+      const int xf = use_xform(ctx, q.P, q.nvars, q.N, &ldxt);
       if (xf) {
-        off_xt = cv.take((size_t)q.nvars * (1 + UNARY_ALL) * ldxt * 4);
-        off_xn = cv.take((size_t)q.nvars * UNARY_ALL);
+        const size_t rows = (size_t)xform_rows(q.nvars, xf);
+        off_xt = cv.take(rows * ldxt * 4);
+        off_xn = cv.take(rows - q.nvars);
       }
       if (bpar) {
         BatchProblem &b = bpar->prob[g - g0];
@@ -1516,7 +1532,8 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
     SR_CHECK_CUDA(ctx, cudaMemsetAsync(b.queue, 0, 5 * sizeof(unsigned long long), s));
     for (int r = 0; r < b.nprob; ++r)
       if (b.prob[r].xform)
-        SR_CHECK_CUDA(ctx, cudaMemsetAsync(b.prob[r].xneed, 0, (size_t)b.prob[r].nvars * UNARY_ALL, s));
+        SR_CHECK_CUDA(ctx, cudaMemsetAsync(b.prob[r].xneed, 0,
+                                           (size_t)(xform_rows(b.prob[r].nvars, b.prob[r].xform) - b.prob[r].nvars), s));
     decode_batched_kernel<<<(b.total_progs + DECODE_WARPS - 1) / DECODE_WARPS, DECODE_WARPS * 32,
                             DECODE_WARPS * decode_warp_bytes(maxL), s>>>(b);
     ctx->launches += 1;
@@ -1524,7 +1541,7 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
       const BatchProblem &q = b.prob[g - g0];
       if (!q.xform) continue;
       const sr_problem &o = pr[order[g]];
-      const dim3 xg((unsigned)((q.N + XF_THREADS * 4 - 1) / (XF_THREADS * 4)), (unsigned)(q.nvars * (1 + UNARY_ALL)));
+      const dim3 xg((unsigned)((q.N + XF_THREADS * 4 - 1) / (XF_THREADS * 4)), (unsigned)xform_rows(q.nvars, q.xform));
       xform_kernel<<<xg, XF_THREADS, 0, s>>>(o.X, o.ldx, q.nvars, q.N, (int)q.ldx, q.xneed,
                                              const_cast<float *>(q.X));
       ctx->launches += 1;
@@ -1645,9 +1662,11 @@ sr_status sr_reserve(sr_ctx *ctx, int P, int Lmax, int N) {
   size_t need = 0;
   for (int mode = 0; mode < 4; ++mode) {
     Plan pl;
-    sr_status st = make_plan(ctx, mode, P, Lmax, N, &pl, SR_MAX_VARS);
-    if (st != SR_OK) return st;
-    need = pl.bytes > need ? pl.bytes : need;
+    for (int nv = 1; nv <= SR_MAX_VARS; ++nv) {  // the table's size depends on the variable count
+      sr_status st = make_plan(ctx, mode, P, Lmax, N, &pl, nv);
+      if (st != SR_OK) return st;
+      need = pl.bytes > need ? pl.bytes : need;
+    }
   }
   return ensure_workspace(ctx, need);
 }

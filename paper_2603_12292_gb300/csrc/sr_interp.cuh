@@ -160,17 +160,28 @@ struct DecodeArgs {
   unsigned long long *deep_count;  // programs with NCODE_DEEP are counted here (or NULL)
   int fold;                 // 1: fold constant-only subtrees into one constant (evaluation only)
   int adj_info;             // 1: mark what the adjoint sweep needs (INS_NOADJ / INS_SA / INS_TA)
-  // 1 (evaluation only): a unary operator applied to a variable, u(x_j), reads
-  // row xform_row(nvars, u, j) of the variable table instead (the table's
-  // first nvars rows are X; the decoder marks in xneed[(u - TOK_SIN) * nvars
-  // + j] each transform that some program reads, and a kernel fills those
-  // rows before the evaluation).  ldx is then the table's row stride.
+  // >= 1 (evaluation only): a unary operator applied to a variable, u(x_j),
+  // reads row xform_row(nvars, u, j) of the variable table instead (the
+  // table's first nvars rows are X); with 2, also a base unary operator
+  // applied to a base u(x_j), u(v(x_j)), reads row xform_row2(nvars, u, v, j).
+  // The decoder marks in xneed[row - nvars] each row some program reads, and
+  // a kernel fills those rows before the evaluation.  ldx is then the
+  // table's row stride.
   int xform = 0;
   uint8_t *xneed = nullptr;
 };
 
-// Row of u(x_j) in the variable table of an evaluation with transforms.
+// The variable table of an evaluation with transforms: X's nvars rows, then
+// u(x_j) for the twelve unary operators, then (depth 2) u(v(x_j)) for the
+// 36 pairs of the six base ones (sin cos exp log sqrt sq).
+constexpr int XFORM_BASE = TOK_SQ - TOK_SIN + 1;
 __host__ __device__ inline int xform_row(int nvars, int u, int j) { return nvars + (u - TOK_SIN) * nvars + j; }
+__host__ __device__ inline int xform_row2(int nvars, int u, int v, int j) {
+  return nvars * (1 + UNARY_ALL) + ((u - TOK_SIN) * XFORM_BASE + (v - TOK_SIN)) * nvars + j;
+}
+__host__ __device__ inline int xform_rows(int nvars, int depth) {
+  return nvars * (1 + UNARY_ALL + (depth > 1 ? XFORM_BASE * XFORM_BASE : 0));
+}
 
 // Instruction flags for the adjoint kernel (bits 28-30 of x; evaluation
 // ignores them).  A constant's derivative flows only through nodes whose
@@ -283,9 +294,18 @@ __device__ inline void decode_one(const DecodeArgs &p, int prog, const uint8_t *
       } else if (p.xform && tok_class(tok[c]) == CLS_VAR) {
         // u(x_j): a leaf reading the transformed variable's row (its index in fval)
         const int j = tok[c] - TOK_VAR0;
+        const int row = xform_row(p.nvars, v, j);
         need[t] = 1 | NEED_XVAR;
-        reinterpret_cast<int32_t *>(fval)[t] = xform_row(p.nvars, v, j);
-        p.xneed[(v - TOK_SIN) * p.nvars + j] = 1;
+        reinterpret_cast<int32_t *>(fval)[t] = row;
+        p.xneed[row - p.nvars] = 1;
+      } else if (p.xform > 1 && (need[c] & NEED_XVAR) && v <= TOK_SQ &&
+                 reinterpret_cast<const int32_t *>(fval)[c] < xform_row(p.nvars, TOK_SQ + 1, 0)) {
+        // u(v(x_j)) of base operators: the row of the composition
+        const int k = reinterpret_cast<const int32_t *>(fval)[c] - p.nvars;
+        const int row = xform_row2(p.nvars, v, TOK_SIN + k / p.nvars, k % p.nvars);
+        need[t] = 1 | NEED_XVAR;
+        reinterpret_cast<int32_t *>(fval)[t] = row;
+        p.xneed[row - p.nvars] = 1;
       } else {
         ext |= v > TOK_SQ;
         need[t] = need[c] & (uint8_t)~NEED_XVAR;
