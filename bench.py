@@ -52,9 +52,9 @@ KERNEL_NCU = {
               "issue_active": 0.838, "scale": False, "sources": "eval",
               "capture": "profiles/eval_kernel_paper-4096x100k.md", "src": "8641b1e3f78c06b2"},
     # grad_kernel: the tape write-back evicted from L2 grows with the units
-    "grad": {"workload": "adjoint-2048x131072", "dram_bytes": 4.487e9 + 18.153e9, "units": 1.3324e10,
-             "issue_active": 0.731, "scale": True, "sources": "grad",
-             "capture": "profiles/grad_kernel_adjoint-2048x131072.md", "src": "b20328fdc65cd482"},
+    "grad": {"workload": "adjoint-2048x131072", "dram_bytes": 4.489e9 + 18.163e9, "units": 1.3324e10,
+             "issue_active": 0.726, "scale": True, "sources": "grad",
+             "capture": "profiles/grad_kernel_adjoint-2048x131072.md", "src": "9914c98e792aff67"},
     # eval_kernel<R4>: inputs read once (L2-resident), at the full size
     "beagle": {"workload": "beagle-4096x100k", "dram_bytes": 170.597e6 + 11.642e6, "units": 2.3977e10,
                "issue_active": 0.818, "scale": False, "sources": "eval",
