@@ -255,8 +255,9 @@ sr_status sr_set_occupancy(sr_ctx *ctx, int eval_ctas_per_sm, int batched_ctas_p
  * variable, u(x_j), is the same column of values in every program of the
  * population: with transforms the decoder turns it into a read of row
  * u(x_j) of a per-call table (X's rows, then u(x_j) for each of the twelve
- * operators and each variable, then -- where the table stays within 256 MiB
- * -- the compositions u(v(x_j)) of the six base operators), and one kernel
+ * operators and each variable, then -- where the table stays within 2 GiB,
+ * and a batch's tables with them within 16 GiB -- the compositions u(v(x_j))
+ * of the six base operators), and one kernel
  * fills the rows some program reads, per call, with the FP32 functions the
  * interpreter applies per case: results are bit for bit those without it,
  * while a program's sin(x3), say, costs a load instead of the library

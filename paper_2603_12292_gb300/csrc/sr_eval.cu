@@ -55,8 +55,9 @@ constexpr int PSTRIDE = 8;      // doubles per partial record
 // that the table's launch and copy cost more than the few programs sharing
 // each row save.
 constexpr int XFORM_MIN_N = 16384, XFORM_MIN_P = 64;
-// The compositions u(v(x_j)) join the table while it stays within this size.
-constexpr long long XFORM2_MAX_BYTES = 256ll << 20;
+// The compositions u(v(x_j)) join the table while it stays within this size
+// (a call), and while a batch's tables with them stay within the second.
+constexpr long long XFORM2_MAX_BYTES = 2ll << 30, XFORM2_BATCH_BYTES = 16ll << 30;
 // A work item's slice of the table (its rows over the item's cases) is kept
 // within this size when the library picks the cases per item, so that the
 // items running at one time share a part of the table that stays in L2:
@@ -1430,6 +1431,7 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
   // workspace: the largest group decides (all groups reuse it in turn)
   auto group_bytes = [&](size_t g0, size_t g1, BatchParams *bpar) -> size_t {
     Carver cv;
+    long long depth2 = 0;  // bytes of the group's tables with compositions
     const size_t off_q = cv.take(256);
     long long items = 0;
     int corr_chunks = 0, ncorr = 0, progs = 0;
@@ -1450,7 +1452,12 @@ sr_status launch_batched(sr_ctx *ctx, const sr_problem *pr, int nprob) {
         off_st = cv.take((size_t)nch[i] * 16);
       }
       int ldxt = 0;
-      const int xf = use_xform(ctx, q.P, q.nvars, q.N, &ldxt);
+      int xf = use_xform(ctx, q.P, q.nvars, q.N, &ldxt);
+      if (xf == 2) {
+        const long long b2 = (long long)xform_rows(q.nvars, 2) * ldxt * 4;
+        if (depth2 + b2 > XFORM2_BATCH_BYTES) xf = 1;
+        else depth2 += b2;
+      }
       if (xf) {
         const size_t rows = (size_t)xform_rows(q.nvars, xf);
         off_xt = cv.take(rows * ldxt * 4);
