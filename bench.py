@@ -48,25 +48,25 @@ KERNEL_SOURCES = {
 # workload, and for another size only where it grows with the units (scale).
 KERNEL_NCU = {
     # eval_kernel<MODE_BOTH> on the headline workload, inputs read once
-    "paper": {"workload": "paper-4096x100k", "dram_bytes": 173.587e6 + 11.108e6, "units": None,
-              "issue_active": 0.838, "scale": False, "sources": "eval",
-              "capture": "profiles/eval_kernel_paper-4096x100k.md", "src": "e3877b34a5f4c848"},
+    "paper": {"workload": "paper-4096x100k", "dram_bytes": 173.062e6 + 11.567e6, "units": None,
+              "issue_active": 0.839, "scale": False, "sources": "eval",
+              "capture": "profiles/eval_kernel_paper-4096x100k.md", "src": "a0bec70a9304581f"},
     # grad_kernel: the tape write-back evicted from L2 grows with the units
     "grad": {"workload": "adjoint-2048x131072", "dram_bytes": 4.489e9 + 18.163e9, "units": 1.3324e10,
              "issue_active": 0.726, "scale": True, "sources": "grad",
              "capture": "profiles/grad_kernel_adjoint-2048x131072.md", "src": "9914c98e792aff67"},
     # eval_kernel<R4>: inputs read once (L2-resident), at the full size
-    "beagle": {"workload": "beagle-4096x100k", "dram_bytes": 172.161e6 + 12.077e6, "units": 2.3977e10,
-               "issue_active": 0.818, "scale": False, "sources": "eval",
-               "capture": "profiles/eval_kernel_r4_beagle-4096x100k.md", "src": "e3877b34a5f4c848"},
+    "beagle": {"workload": "beagle-4096x100k", "dram_bytes": 171.088e6 + 11.973e6, "units": 2.3977e10,
+               "issue_active": 0.817, "scale": False, "sources": "eval",
+               "capture": "profiles/eval_kernel_r4_beagle-4096x100k.md", "src": "a0bec70a9304581f"},
     # eval_batched_kernel: the first 8 problems; inputs read once
-    "batched": {"workload": "batched-8", "dram_bytes": 552.424e6 + 29.023e6, "units": 4.0723e11,
-                "issue_active": 0.819, "scale": False, "sources": "eval",
-                "capture": "profiles/eval_batched_kernel_batched-8.md", "src": "e3877b34a5f4c848"},
+    "batched": {"workload": "batched-8", "dram_bytes": 1625.761e6 + 47.885e6, "units": 4.0723e11,
+                "issue_active": 0.816, "scale": False, "sources": "eval",
+                "capture": "profiles/eval_batched_kernel_batched-8.md", "src": "a0bec70a9304581f"},
     # eval_kernel<CORR> at Lmax 256: inputs read once
-    "large": {"workload": "large-16384x131072", "dram_bytes": 405.005e6 + 20.901e6, "units": 2.5087e11,
+    "large": {"workload": "large-16384x131072", "dram_bytes": 402.477e6 + 20.297e6, "units": 2.5087e11,
               "issue_active": 0.820, "scale": False, "sources": "eval",
-              "capture": "profiles/eval_kernel_corr_large-16384x131072.md", "src": "e3877b34a5f4c848"},
+              "capture": "profiles/eval_kernel_corr_large-16384x131072.md", "src": "a0bec70a9304581f"},
 }
 
 
