@@ -360,6 +360,30 @@ def run_ours(args, rank, world, local_rank):
                 "issue_active_ncu": cap["issue_active"] if cap else None, "ncu_provenance": prov,
                 "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz ({src} max clock)"}
 
+    # the evaluation alone on the first timed population, with and without the
+    # decoder's variable transforms (outside the timed region, no L2 flush):
+    # what the table saves, and that the fitness is the same bits either way
+    def eval_rate(mode, reps=5):
+        binding.sr_set_transforms(ctx, mode)
+        try:
+            P_, L_, C_ = start_rows
+            f = torch.empty_like(fitness)
+            binding.sr_eval(ctx, P_, L_, C_, X, y, pr.N, binding.SR_MSE_CORR, fitness=f)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                binding.sr_eval(ctx, P_, L_, C_, X, y, pr.N, binding.SR_MSE_CORR, fitness=f)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return float(L_.sum().item()) * pr.N * reps / (e0.elapsed_time(e1) / 1e3) / 1e9, f
+        finally:
+            binding.sr_set_transforms(ctx, binding.XFORM_AUTO)
+
+    g_on, f_on = eval_rate(binding.XFORM_AUTO)
+    g_off, f_off = eval_rate(binding.XFORM_NEVER)
+    transforms = {"eval_gpops": g_on, "eval_gpops_without": g_off,
+                  "fitness_bit_identical": bool(torch.equal(f_on.view(torch.int64), f_off.view(torch.int64)))}
+
     # end to end through the public API with the population held on the host:
     # H2D population, evaluate + select + vary, D2H children and fitness; the
     # same generations as the timed region (same populations, same work)
@@ -429,7 +453,7 @@ def run_ours(args, rank, world, local_rank):
             "roofline": roofline, "clocks": clocks,
             "e2e": {"value": e2e_val, "unit": "GPop/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": int(launches)}
+            "gpu_launches": int(launches), "decoder_transforms": transforms}
 
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pr, y.cpu().numpy())
