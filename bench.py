@@ -381,7 +381,8 @@ def run_ours(args, rank, world, local_rank):
 
     g_on, f_on = eval_rate(binding.XFORM_AUTO)
     g_off, f_off = eval_rate(binding.XFORM_NEVER)
-    transforms = {"eval_gpops": g_on, "eval_gpops_without": g_off,
+    transforms = {"population": f"generation {start_gen} (the first timed one), sr_eval(SR_MSE_CORR) x5",
+                  "eval_gpops": g_on, "eval_gpops_without": g_off,
                   "fitness_bit_identical": bool(torch.equal(f_on.view(torch.int64), f_off.view(torch.int64)))}
 
     # end to end through the public API with the population held on the host:
